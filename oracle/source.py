@@ -1,0 +1,372 @@
+"""CPU oracle of the PSL source stage (TEST INFRASTRUCTURE).
+
+Only the tests, the package smoke check and the CPU-baseline leg of the
+benchmark may import this module.  It shares no code with the CUDA path.
+
+It follows the paper's steps in order:
+
+* PSL generation, Sec. 2.3.2: split the records by particle type (photon;
+  electron/positron), then by energy bin, then by dx x dy position bin.  The
+  PSL store is one array sorted by the PSL id plus its bin offsets.
+* PSL selection, Sec. 2.3.3 and Fig. 1: back-project the jaw opening (plus a
+  margin) from SAD to the PSL plane; keep every PSL whose area overlaps it.
+* Histories per PSL, Sec. 2.3.3 (the equations for N_total^psl and P_ij):
+  histories proportional to the records of each selected PSL of each field.
+* Reading order, Sec. 2.3.3: energy division by energy division; inside one,
+  a few particles from each PSL in turn; the first read of a PSL starts at a
+  random record and wraps to its start (recycling, Sec. 2.6).
+* Jaw model, Sec. 2.2: accept a particle if its straight line passes inside
+  both jaw openings, otherwise terminate it.
+* Fluence map, Sec. 2.2 and 2.4: project to the map plane, multiply the weight
+  by the map value; MU weight w' = w MU_i / MU_total (Sec. 2.3.3).
+* Rotations and projection to the phantom surface, Sec. 2.3.3.
+
+Readings where the paper is silent (also listed in the design notes): the
+jaw, fluence and ROI decisions are taken in float32, the precision of the
+kernel; every other quantity is float64.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import _lib
+
+F32 = np.float32
+
+# source status codes (per history)
+ST_TRANSPORT, ST_JAW, ST_FLUENCE, ST_ZERO_WEIGHT, ST_MISS = 0, 1, 2, 3, 4
+
+TAG_OFFSET = 1
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3.2: PSL generation
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Store:
+    keys: np.ndarray         # int64 [n] PSL id per input record (n_bins = invalid)
+    perm: np.ndarray         # int64 [n_valid] input index of each sorted record
+    offsets: np.ndarray      # int64 [n_bins + 1]
+    n_bins: int
+    nx: int
+    ny: int
+    n_ebins: int
+    x_edges: np.ndarray
+    y_edges: np.ndarray
+
+    @property
+    def n_valid(self) -> int:
+        return int(self.offsets[-1])
+
+
+def psl_keys(x, y, e, q, x_edges, y_edges, e_edges) -> np.ndarray:
+    """PSL id of every record: (type * N_E + energy bin) * (nx ny) + position.
+
+    Bins are half-open [edge_k, edge_k+1).  Positions outside the extent and
+    energies <= 0 get the sentinel id n_bins.  Energies are binned by the
+    interior edges only, so E below the first or above the last edge fall in
+    the first or last energy bin."""
+    nx, ny, ne = len(x_edges) - 1, len(y_edges) - 1, len(e_edges) - 1
+    n_bins = 2 * ne * nx * ny
+    bx = np.searchsorted(x_edges, x, side="right") - 1
+    by = np.searchsorted(y_edges, y, side="right") - 1
+    eb = np.searchsorted(e_edges[1:-1], e, side="right")
+    t = (q != 0).astype(np.int64)
+    valid = (bx >= 0) & (bx < nx) & (by >= 0) & (by < ny) & (e > 0)
+    key = (t * ne + eb) * (nx * ny) + by * nx + bx
+    return np.where(valid, key, n_bins).astype(np.int64)
+
+
+def psl_build(records, binning) -> Store:
+    """Sort the phase space into PSLs: stable sort by PSL id, bin offsets."""
+    keys = psl_keys(records.x, records.y, records.e, records.q,
+                    binning.x_edges, binning.y_edges, binning.e_edges)
+    n_bins = binning.n_bins
+    order = np.argsort(keys, kind="stable")
+    counts = np.bincount(keys, minlength=n_bins + 1)
+    offsets = np.zeros(n_bins + 1, np.int64)
+    offsets[1:] = np.cumsum(counts[:n_bins])
+    perm = order[: offsets[-1]].astype(np.int64)
+    return Store(keys, perm, offsets, n_bins, binning.nx, binning.ny, binning.n_ebins,
+                 binning.x_edges, binning.y_edges)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3.3: selection, counts, reading order
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Plan:
+    field: np.ndarray        # int64 [n_entries] field index of entry
+    psl: np.ndarray          # int64 PSL id
+    start: np.ndarray        # int64 first sorted record of the PSL
+    nrec: np.ndarray         # int64 records in the PSL
+    count: np.ndarray        # int64 histories assigned to the entry
+    offset: np.ndarray       # int64 random start record inside the PSL
+    group: np.ndarray        # int64 reading group (energy division major, type minor)
+    n_total_psl: int
+    n_sim: int
+    group_start: np.ndarray  # int64 [n_groups + 1] first history of each group
+    group_order: List[np.ndarray]   # per group: entries in visiting order
+    n_ebins: int
+    _literal: Dict[int, tuple] = dataclasses.field(default_factory=dict)
+
+
+def roi_select(x_edges, y_edges, beam, z_psl, sad) -> np.ndarray:
+    """Boolean [ny, nx]: PSL positions whose area overlaps the field's ROI.
+
+    ROI: the jaw opening at SAD widened by the margin, back-projected from the
+    source to the PSL plane (scaled by z_psl/SAD).  Overlap is strict: a PSL
+    that only touches the ROI edge is not selected."""
+    s = F32(z_psl) / F32(sad)
+    m = F32(beam.roi_margin)
+    xlo, xhi = (F32(beam.x1) - m) * s, (F32(beam.x2) + m) * s
+    ylo, yhi = (F32(beam.y1) - m) * s, (F32(beam.y2) + m) * s
+    sx = (x_edges[:-1] < xhi) & (x_edges[1:] > xlo)
+    sy = (y_edges[:-1] < yhi) & (y_edges[1:] > ylo)
+    return sy[:, None] & sx[None, :]
+
+
+def psl_offset(seed: int, field: int, psl: int, nrec: int) -> int:
+    """Random first record of a PSL for one field: Philox(seed; field, tag, psl)."""
+    if nrec <= 0:
+        return 0
+    ctr = np.array([[field, TAG_OFFSET, psl & 0xFFFFFFFF, psl >> 32]], np.uint32)
+    key = np.array([[seed & 0xFFFFFFFF, seed >> 32]], np.uint32)
+    r = _lib.philox(ctr, key)[0]
+    r64 = int(r[0]) | (int(r[1]) << 32)
+    return (r64 * nrec) >> 64
+
+
+def make_plan(store: Store, beams, n_sim: int, seed: int, z_psl: float, sad: float) -> Plan:
+    npos = store.nx * store.ny
+    ne = store.n_ebins
+    nrec_psl = np.diff(store.offsets)
+    fields, psls = [], []
+    for i, b in enumerate(beams):
+        sel = np.flatnonzero(roi_select(store.x_edges, store.y_edges, b, z_psl, sad).ravel())
+        # every type and energy division of every selected position, in PSL-id order
+        ids = (np.arange(2 * ne)[:, None] * npos + sel[None, :]).ravel()
+        fields.append(np.full(len(ids), i, np.int64))
+        psls.append(ids.astype(np.int64))
+    field = np.concatenate(fields)
+    psl = np.concatenate(psls)
+    start = store.offsets[psl]
+    nrec = nrec_psl[psl].astype(np.int64)
+    n_total = int(nrec.sum())
+    if n_total == 0:
+        raise ValueError("no phase-space records inside the selected PSLs")
+    # N_ij = N_sim N_j / N_total, rounded by differencing the floor of the
+    # cumulative share (exact integers; the counts sum to N_sim)
+    cum = [0]
+    acc = 0
+    for c in nrec.tolist():
+        acc += c
+        cum.append(acc)
+    fl = [(n_sim * c) // n_total for c in cum]
+    count = np.array([fl[k + 1] - fl[k] for k in range(len(nrec))], np.int64)
+    offset = np.array([psl_offset(seed, int(f), int(p), int(n))
+                       for f, p, n in zip(field, psl, nrec)], np.int64)
+    t = psl // (ne * npos)
+    e = (psl // npos) % ne
+    group = e * 2 + t
+    n_groups = 2 * ne
+    group_order = []
+    sizes = np.zeros(n_groups, np.int64)
+    for g in range(n_groups):
+        idx = np.flatnonzero((group == g) & (count > 0))
+        # visiting order inside one round: larger counts first, then list order
+        o = idx[np.lexsort((idx, -count[idx]))]
+        group_order.append(o)
+        sizes[g] = count[o].sum()
+    gs = np.zeros(n_groups + 1, np.int64)
+    gs[1:] = np.cumsum(sizes)
+    return Plan(field, psl, start, nrec, count, offset, group, n_total, n_sim, gs, group_order, ne)
+
+
+def _literal_group(plan: Plan, g: int):
+    """All (entry, use) pairs of group g in reading order: round k visits, in
+    the group's visiting order, every entry that still has more than k
+    histories to give."""
+    if g not in plan._literal:
+        o = plan.group_order[g]
+        c = plan.count[o]
+        pos = np.repeat(np.arange(len(o)), c)
+        k = np.concatenate([np.arange(n) for n in c]) if len(c) else np.zeros(0, np.int64)
+        order = np.lexsort((pos, k))
+        plan._literal[g] = (o[pos[order]], k[order])
+    return plan._literal[g]
+
+
+def _group_lookup(plan: Plan, g: int, hl: int):
+    """(entry, use) of the hl-th history of group g: the round is the largest
+    r with sum_e min(count_e, r) <= hl."""
+    o = plan.group_order[g]
+    c = plan.count[o]
+    lo, hi = 0, int(c.max())
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if int(np.minimum(c, mid).sum()) <= hl:
+            lo = mid
+        else:
+            hi = mid
+    p = hl - int(np.minimum(c, lo).sum())
+    return int(o[p]), lo
+
+
+def history_map(plan: Plan, h: np.ndarray, literal_limit: int = 4_000_000):
+    """Entry index and use number (k-th read of that entry) of each history."""
+    h = np.asarray(h, np.int64)
+    g = np.searchsorted(plan.group_start, h, side="right") - 1
+    entry = np.empty(len(h), np.int64)
+    use = np.empty(len(h), np.int64)
+    for gg in np.unique(g):
+        m = g == gg
+        hl = h[m] - plan.group_start[gg]
+        size = plan.group_start[gg + 1] - plan.group_start[gg]
+        if size <= literal_limit:
+            ent, k = _literal_group(plan, int(gg))
+            entry[m], use[m] = ent[hl], k[hl]
+        else:
+            r = [_group_lookup(plan, int(gg), int(x)) for x in hl]
+            entry[m] = [a for a, _ in r]
+            use[m] = [b for _, b in r]
+    return entry, use
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2 / 2.3.3 / 2.4: per-particle source transform
+# --------------------------------------------------------------------------
+def _sincosd(deg: float):
+    """sin and cos of an angle in degrees, exact at multiples of 90."""
+    n = int(round(deg / 90.0))
+    r = math.radians(deg - 90.0 * n)
+    s, c = math.sin(r), math.cos(r)
+    for _ in range(n % 4):
+        s, c = c, -s
+    return s, c
+
+
+def beam_matrix(beam) -> np.ndarray:
+    """Rotation from the beam frame to the patient frame: couch (about z),
+    gantry (about y) and collimator (about z), applied collimator first."""
+    sc, cc = _sincosd(beam.collimator)
+    sg, cg = _sincosd(beam.gantry)
+    st, ct = _sincosd(beam.couch)
+    Rc = np.array([[cc, -sc, 0.0], [sc, cc, 0.0], [0.0, 0.0, 1.0]])
+    Rg = np.array([[cg, 0.0, sg], [0.0, 1.0, 0.0], [-sg, 0.0, cg]])
+    Rt = np.array([[ct, -st, 0.0], [st, ct, 0.0], [0.0, 0.0, 1.0]])
+    return Rt @ Rg @ Rc
+
+
+@dataclasses.dataclass
+class SourceOut:
+    status: np.ndarray       # int8
+    entry: np.ndarray        # int64
+    use: np.ndarray          # int64
+    rec: np.ndarray          # int64 sorted record index
+    beam: np.ndarray         # int64
+    ptype: np.ndarray        # int32 0 photon, 1 electron, 2 positron
+    pos: np.ndarray          # float64 [n, 3] phantom-local entry point
+    dir: np.ndarray          # float64 [n, 3]
+    e: np.ndarray            # float64 MeV
+    wt: np.ndarray           # float32 weight after jaw/fluence/MU
+    emitted_fp: int          # sum of fixed-point E*wt over accepted histories
+    missed_fp: int           # part of it that missed the phantom
+
+
+def mu_ratios(beams) -> np.ndarray:
+    tot = 0.0
+    for b in beams:
+        tot += float(b.mu)
+    return np.array([F32(float(b.mu) / tot) for b in beams], F32)
+
+
+def source(plan: Plan, store: Store, records, beams, phantom, h: np.ndarray,
+           z_psl: float, sad: float) -> SourceOut:
+    h = np.asarray(h, np.int64)
+    entry, use = history_map(plan, h)
+    nrec = plan.nrec[entry]
+    rec = plan.start[entry] + (plan.offset[entry] + use) % nrec
+    beam = plan.field[entry]
+    src = store.perm[rec]
+    x, y, u, v = records.x[src], records.y[src], records.u[src], records.v[src]
+    e, wt0, q = records.e[src], records.wt[src], records.q[src]
+    n = len(h)
+    status = np.zeros(n, np.int8)
+    wt = np.zeros(n, F32)
+    murat = mu_ratios(beams)
+    one = F32(1.0)
+    # direction cosine w in float32 (decides acceptance)
+    s = (one - u * u) - v * v
+    ok = s > 0
+    w32 = np.sqrt(np.where(ok, s, one)).astype(F32)
+    status[~ok] = ST_JAW
+    for i, b in enumerate(beams):
+        m = (beam == i) & ok
+        if not m.any():
+            continue
+        zjx, zjy, sadf, zp = F32(b.z_jaw_x), F32(b.z_jaw_y), F32(sad), F32(z_psl)
+        xlo, xhi = (F32(b.x1) * zjx) / sadf, (F32(b.x2) * zjx) / sadf
+        ylo, yhi = (F32(b.y1) * zjy) / sadf, (F32(b.y2) * zjy) / sadf
+        xj = x[m] + u[m] * ((zjx - zp) / w32[m])
+        yj = y[m] + v[m] * ((zjy - zp) / w32[m])
+        acc = (xj >= xlo) & (xj <= xhi) & (yj >= ylo) & (yj <= yhi)
+        ww = wt0[m].copy()
+        st = np.where(acc, ST_TRANSPORT, ST_JAW).astype(np.int8)
+        if b.fluence is not None:
+            fny, fnx = b.fluence.shape
+            ti = (sadf - zp) / w32[m]
+            fx = ((x[m] + u[m] * ti) - F32(b.fx0)) / F32(b.fdx)
+            fy = ((y[m] + v[m] * ti) - F32(b.fy0)) / F32(b.fdy)
+            ix, iy = np.floor(fx), np.floor(fy)
+            inside = (ix >= 0) & (ix < fnx) & (iy >= 0) & (iy < fny)
+            st = np.where(acc & ~inside, ST_FLUENCE, st).astype(np.int8)
+            ixc = np.clip(ix, 0, fnx - 1).astype(np.int64)
+            iyc = np.clip(iy, 0, fny - 1).astype(np.int64)
+            ww = ww * b.fluence[iyc, ixc]
+        ww = ww * murat[i]
+        st = np.where((st == ST_TRANSPORT) & (ww == 0), ST_ZERO_WEIGHT, st).astype(np.int8)
+        status[m] = st
+        wt[m] = ww
+    # rotations and projection to the phantom surface (float64)
+    pos = np.zeros((n, 3))
+    dirs = np.zeros((n, 3))
+    ud, vd = u.astype(np.float64), v.astype(np.float64)
+    wd = np.sqrt(np.maximum(1.0 - ud * ud - vd * vd, 0.0))
+    L = np.array(phantom.shape[::-1], np.float64) * np.array(phantom.voxel, np.float64)
+    origin = np.array(phantom.origin, np.float64)
+    for i, b in enumerate(beams):
+        m = (beam == i) & (status == ST_TRANSPORT)
+        if not m.any():
+            continue
+        R = beam_matrix(b)
+        pb = np.stack([x[m].astype(np.float64), y[m].astype(np.float64),
+                       np.full(m.sum(), float(z_psl))], 1)
+        pb[:, 2] -= float(sad)
+        pp = pb @ R.T + np.array(b.iso, np.float64) - origin
+        dd = np.stack([ud[m], vd[m], wd[m]], 1) @ R.T
+        # full-line slab intersection with the box [0, L]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t0 = (0.0 - pp) / dd
+            t1 = (L - pp) / dd
+        tmin = np.where(dd != 0, np.minimum(t0, t1), -np.inf)
+        tmax = np.where(dd != 0, np.maximum(t0, t1), np.inf)
+        outside_par = (dd == 0) & ((pp < 0) | (pp > L))
+        t_in = tmin.max(1)
+        t_out = tmax.min(1)
+        hit = (t_in < t_out) & ~outside_par.any(1)
+        idx = np.flatnonzero(m)
+        status[idx[~hit]] = ST_MISS
+        pos[idx] = pp + t_in[:, None] * dd
+        dirs[idx] = dd
+    ptype = np.where(q == 0, 0, np.where(q < 0, 1, 2)).astype(np.int32)
+    accepted = (status == ST_TRANSPORT) | (status == ST_MISS)
+    e64 = e.astype(np.float64)
+    fp = np.rint(e64 * wt.astype(np.float64) * 4294967296.0).astype(np.int64)
+    emitted = int(fp[accepted].sum())
+    missed = int(fp[status == ST_MISS].sum())
+    return SourceOut(status, entry, use, rec, beam, ptype, pos, dirs, e64, wt, emitted, missed)
