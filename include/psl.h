@@ -1,0 +1,268 @@
+/*
+ * psl.h -- C ABI of the B300 phase-space-let (PSL) Monte Carlo dose path.
+ *
+ * The calls follow the paper's statement of the problem (Townson et al.,
+ * "GPU-based Monte Carlo radiotherapy dose calculation using phase-space
+ * sources"):
+ *
+ *   psl_build          Sec. 2.3.2  commission a phase space once: sort its
+ *                                  records into PSLs by particle type, energy
+ *                                  bin and position bin.
+ *   psl_plan_create    Sec. 2.3.3  per treatment plan: select the PSLs inside
+ *                                  each field's region of interest (Fig. 1)
+ *                                  and give each selected PSL its share of the
+ *                                  histories (the N_total^psl and P_ij
+ *                                  equations).
+ *   psl_source_batch   Sec. 2.2, 2.3.3, 2.4  read the particles of a range of
+ *                                  histories in the paper's order (energy
+ *                                  division by division, PSLs interleaved,
+ *                                  random start and wrap), apply the jaw
+ *                                  model, fluence map and MU weight, rotate
+ *                                  and project them to the phantom surface.
+ *   transport_run      Sec. 2.3.3  photon/electron transport with dose tallied
+ *                                  by atomic counters, one tally per batch.
+ *   dose_readout       Sec. 2.3.3, 2.5  dose, batch uncertainty and the
+ *                                  normalisation factor.
+ *
+ * Conventions common to every call:
+ *   - Return PSL_OK (0) on success or a negative PSL_E* code; the text of the
+ *     last error of the calling thread is in psl_last_error().
+ *   - Arrays in the structs below are DEVICE pointers owned by the caller
+ *     unless a field says "host".  They must stay valid until the call that
+ *     uses them has completed on its stream.
+ *   - Handles (psl_store_t, psl_plan_t, psl_batch_t, psl_tally_t) are owned
+ *     by the library and freed with the matching *_destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on it unless stated otherwise; calls
+ *     that size an allocation from device data synchronise that stream.
+ *   - Determinism: the same inputs and seed give bitwise-identical integer
+ *     tallies whatever the launch shape, the number of batches a history
+ *     range is split into, or the order the ranges are run in.
+ *   - Units: cm, MeV, g/cm^3, Gy, degrees.  The beam frame has the source at
+ *     the origin and the beam travelling along +z; the isocentre is at
+ *     (0, 0, SAD).
+ */
+#ifndef PSL_H
+#define PSL_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PSL_API __attribute__((visibility("default")))
+#else
+#define PSL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSL_OK 0
+#define PSL_EINVAL (-1)     /* bad argument or handle */
+#define PSL_ENOMEM (-2)     /* device allocation failed */
+#define PSL_ECUDA (-3)      /* a CUDA call failed (text in psl_last_error) */
+#define PSL_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define PSL_EOVERFLOW (-5)  /* a particle queue or tally headroom overflowed */
+
+/* physics switches used by the tests; 0 in production */
+#define PSL_PHYS_LOCAL_SECONDARIES 1u  /* secondaries deposit their energy in place */
+#define PSL_PHYS_FIRST_INTERACTION 2u  /* photons deposit all at the first real interaction */
+#define PSL_PHYS_NO_MSC 4u             /* electrons are not deflected by multiple scattering */
+#define PSL_PHYS_NO_HARD 8u            /* electrons make no hard delta rays or bremsstrahlung */
+
+/* source status of one history (psl_source_trace) */
+#define PSL_SRC_TRANSPORT 0   /* accepted and entering the phantom */
+#define PSL_SRC_JAW 1         /* stopped by a jaw (Sec. 2.2) */
+#define PSL_SRC_FLUENCE 2     /* outside the fluence map (weight 0) */
+#define PSL_SRC_ZERO_WEIGHT 3 /* fluence or weight zero */
+#define PSL_SRC_MISS 4        /* accepted but its line misses the phantom */
+
+/* Phase-space records at the PSL plane, structure of arrays (device, n each).
+ * q: 0 photon, -1 electron, +1 positron.  w = +sqrt(1 - u^2 - v^2). */
+typedef struct psl_records {
+    const float *x, *y, *u, *v, *e, *wt;
+    const int8_t *q;
+    int64_t n;                 /* 0 <= n < 2^30 */
+} psl_records_t;
+
+/* PSL binning (Sec. 2.3.2).  Bins are half-open [edge_k, edge_k+1).  Records
+ * outside [x_edges[0], x_edges[nx]) x [y_edges[0], y_edges[ny]) or with
+ * e <= 0 belong to no PSL and are dropped.  Energies are binned by the
+ * interior edges only (below e_edges[1]: bin 0; at or above
+ * e_edges[n_ebins-1]: the last bin).  PSL id =
+ * (type * n_ebins + energy bin) * nx * ny + y bin * nx + x bin, type 0 for
+ * photons and 1 for electrons and positrons. */
+typedef struct psl_params {
+    int32_t nx, ny;            /* position bins, nx*ny*n_ebins*2 < 2^31 */
+    int32_t n_ebins;           /* energy bins per type, >= 1 */
+    int32_t apr_copies;        /* azimuthal redistribution copies; must be 1 */
+    const float *x_edges;      /* host, nx+1 ascending */
+    const float *y_edges;      /* host, ny+1 ascending */
+    const float *e_edges;      /* host, n_ebins+1 ascending */
+    float z_psl;               /* PSL plane, cm from the source */
+} psl_params_t;
+
+/* One treatment field (Sec. 2.2, 2.3.3, 2.4). */
+typedef struct psl_beam {
+    float x1, x2, y1, y2;      /* jaw edges projected to SAD, cm; x1 < x2, y1 < y2 */
+    float z_jaw_x, z_jaw_y;    /* planes of the X and Y jaws, cm from the source */
+    float gantry, collimator, couch;   /* degrees */
+    float mu;                  /* monitor units, > 0 */
+    float roi_margin;          /* cm added around the jaw opening at SAD for PSL selection */
+    float iso[3];              /* isocentre in patient coordinates, cm */
+    int32_t fnx, fny;          /* fluence map cells; 0 = no map */
+    float fx0, fy0, fdx, fdy;  /* map corner and cell size at SAD, cm */
+    const float *fluence;      /* device, fny*fnx row-major, or NULL */
+} psl_beam_t;
+
+/* Voxel phantom.  Voxel (ix, iy, iz) is element (iz*ny + iy)*nx + ix and
+ * spans origin + [i, i+1) * voxel size. */
+typedef struct psl_phantom {
+    int32_t nx, ny, nz;
+    float vx, vy, vz;          /* voxel size, cm */
+    float origin[3];           /* patient coordinates of the (0,0,0) corner */
+    const uint8_t *mat;        /* device, 0 water-like medium, 1 bone */
+    const float *rho;          /* device, mass density g/cm^3, > 0 */
+} psl_phantom_t;
+
+/* Transport cut-offs (Sec. 2.6) and class-II thresholds.  psl_physics_default
+ * fills photon_cut 0.010 MeV, electron_cut 0.700 MeV total energy (0.18900105
+ * MeV kinetic), wcc = wcb = 0.200 MeV, flags 0. */
+typedef struct psl_physics {
+    float photon_cut, electron_cut, wcc, wcb;
+    uint32_t flags;            /* PSL_PHYS_* */
+} psl_physics_t;
+
+typedef struct psl_store psl_store_t;
+typedef struct psl_plan psl_plan_t;
+typedef struct psl_batch psl_batch_t;
+typedef struct psl_tally psl_tally_t;
+
+PSL_API void psl_physics_default(psl_physics_t *out);
+
+/* Sec. 2.3.2.  Compute every record's PSL id, sort the records stably by it
+ * (LSD onesweep radix sort) and gather them into the store as 32-byte records
+ * (x, y, u, v, e, wt, input index, q), with the bin offsets
+ * offsets[0..n_bins] (offsets[n_bins] = records kept).  The store is
+ * independent of the caller's arrays once the call has completed.
+ * Errors: PSL_EINVAL (sizes, edges, apr_copies != 1), PSL_ENOMEM, PSL_ECUDA,
+ * PSL_ETIMEOUT (a look-back wait of the sort gave up). Synchronises stream. */
+PSL_API int psl_build(const psl_params_t *params, const psl_records_t *records, psl_store_t **out, void *stream);
+
+/* Sizes of a store (host outputs). */
+PSL_API int psl_store_info(const psl_store_t *store, int64_t *n_records, int64_t *n_valid, int64_t *n_bins);
+
+/* Copy the store out (device outputs, NULL to skip): offsets (n_bins+1
+ * int64), perm (n_valid int64: input index of each sorted record), records
+ * (n_valid x 8 float32: x y u v e wt, then the input index and q as int32
+ * bit patterns). */
+PSL_API int psl_store_read(const psl_store_t *store, int64_t *offsets, int64_t *perm, float *records, void *stream);
+
+/* Sec. 2.3.3.  Select, for every beam, the PSLs whose position bin overlaps
+ * the ROI: the jaw opening at SAD widened by roi_margin and scaled by
+ * z_psl / sad (strict overlap: touching edges do not count).  Entry list =
+ * beams in order, each beam's selected PSLs in PSL-id order.  With N_j the
+ * records of the entry's PSL and C_k the sum of N_j over the entries before
+ * entry k, entry k gets floor(N C_{k+1} / N_total) - floor(N C_k / N_total)
+ * histories (N = n_histories, N_total = sum of N_j over all entries), so the
+ * counts sum to N exactly.  Each entry reads its PSL from a random record
+ * offset drawn from Philox(seed; beam, PSL id).  `beams` is a host array.
+ * Requires 0 < n_histories < 2^32.  Synchronises stream. */
+PSL_API int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams, int32_t n_beams, float sad,
+                    int64_t n_histories, uint64_t seed, psl_plan_t **out, void *stream);
+
+/* Plan sizes: entries, N_total^psl and the histories of the plan (host). */
+PSL_API int psl_plan_info(const psl_plan_t *plan, int64_t *n_entries, int64_t *n_total_psl, int64_t *n_histories);
+
+/* Copy per-entry arrays out (device int64 [n_entries] each, NULL to skip):
+ * beam, PSL id, histories assigned, random start offset. */
+PSL_API int psl_plan_read(const psl_plan_t *plan, int64_t *beam, int64_t *psl, int64_t *count, int64_t *offset,
+                  void *stream);
+
+/* Sec. 2.2, 2.3.3, 2.4.  Source stage for histories [first, first+n) of the
+ * plan.  History h is mapped to (entry, read number k): energy divisions in
+ * order, photons before electrons inside one; within that group, round r
+ * reads one particle from every entry still owed more than r histories,
+ * entries visited in order of decreasing count (ties: entry order).  The
+ * record read is start + (offset + k) mod N_j.  Jaw test, fluence map and MU
+ * weight are decided in float32 (round-to-nearest, no fused multiply-add):
+ *   w   = sqrt((1 - u*u) - v*v)
+ *   xj  = x + u * ((z_jaw_x - z_psl) / w), accepted if (x1*z_jaw_x)/sad <= xj <= (x2*z_jaw_x)/sad
+ *   (same for y), fluence cell floor((x + u*((sad - z_psl)/w) - fx0) / fdx),
+ *   weight = (wt * F) * mu_i/mu_total.
+ * Survivors are rotated (collimator about z, gantry about y, couch about z,
+ * about the isocentre) and moved along their line to its entry into the
+ * phantom box.  The batch holds the particles for transport_run; the phantom
+ * is read for its box only.  Synchronises stream. */
+PSL_API int psl_source_batch(const psl_plan_t *plan, const psl_phantom_t *phantom, int64_t first_history,
+                     int64_t n_histories, psl_batch_t **out, void *stream);
+
+/* The source stage of histories [first, first+n) written out per history
+ * (device outputs, NULL to skip): entry, read number k, sorted record
+ * index, beam, status (PSL_SRC_*), state (n x 8 float32: x y z u v w e wt,
+ * phantom-local entry point, only for PSL_SRC_TRANSPORT), particle type
+ * (0 photon, 1 electron, 2 positron). */
+PSL_API int psl_source_trace(const psl_plan_t *plan, const psl_phantom_t *phantom, int64_t first_history,
+                     int64_t n_histories, int64_t *entry, int64_t *use, int64_t *rec, int32_t *beam,
+                     int8_t *status, float *state, int32_t *ptype, void *stream);
+
+/* A batch made from caller particles (device arrays, n each): state n x 8
+ * float32 (x y z u v w e wt, phantom-local), type (0/1/2) and particle id;
+ * `seed` keys their random streams.  Used to transport given particles
+ * (tests, other sources). */
+PSL_API int psl_batch_from_particles(const float *state, const int32_t *ptype, const uint64_t *pid, int64_t n,
+                             uint64_t seed, psl_batch_t **out, void *stream);
+
+/* Histories (or particles) in a batch and the fixed-point energy they emit. */
+PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64_t *n_photons, int64_t *n_electrons);
+
+/* One int64 tally of nz*ny*nx voxels per batch, plus an 8-slot ledger:
+ * emitted, escaped, deposited (fixed point, 2^-32 MeV per unit weight),
+ * Compton, photoelectric and pair events, electron steps, errors. */
+PSL_API int psl_tally_create(const psl_phantom_t *phantom, int32_t n_batches, psl_tally_t **out);
+PSL_API int psl_tally_reset(psl_tally_t *tally, void *stream);
+
+/* Copy raw tallies (device int64 [n_batches * nvox]) and ledger (device int64
+ * [8]) out; NULL to skip. */
+PSL_API int psl_tally_read(const psl_tally_t *tally, int64_t *tallies, int64_t *ledger, void *stream);
+
+/* Sec. 2.3.3.  Transport every particle of the batch and its secondaries
+ * through the phantom and add the deposits to tally slice `batch_index`.
+ * Photons: Woodcock tracking, Klein-Nishina Compton (Kahn), photoelectric,
+ * pair.  Electrons/positrons: class-II condensed history, restricted Bethe
+ * stopping, hard Moller and bremsstrahlung, Highland multiple scattering.
+ * Electrons are grouped by energy band before each transport pass so that a
+ * warp steps one band.  Deposits are rounded to int64 in units of 2^-32
+ * MeV and added atomically.  The batch is consumed (transport it once).
+ * Errors: PSL_EOVERFLOW if a secondary queue overflowed (tally incomplete).
+ * Synchronises stream. */
+PSL_API int transport_run(const psl_phantom_t *phantom, const psl_physics_t *physics, psl_batch_t *batch,
+                  psl_tally_t *tally, int32_t batch_index, void *stream);
+
+/* transport_run that also adds, per history (or caller particle) i of the
+ * batch, its deposited and escaped fixed-point energy and its event count
+ * (device arrays of the batch's n_histories, added to). */
+PSL_API int transport_trace(const psl_phantom_t *phantom, const psl_physics_t *physics, psl_batch_t *batch,
+                    psl_tally_t *tally, int32_t batch_index, int64_t *hist_dep, int64_t *hist_esc,
+                    int32_t *hist_events, void *stream);
+
+/* Sec. 2.3.3 and 2.5.  dose[v] = norm * sum_b T_bv * 2^-32 MeV * 1.602176634e-13
+ * J/MeV / (rho_v * voxel volume * 1e-3 kg), sigma[v] = the standard error of
+ * the mean of the N_b batch estimates, ledger[0..2] = emitted, escaped,
+ * deposited energy in MeV (FP64).  dose, sigma: device float64 [nvox];
+ * ledger: device float64 [3]; any may be NULL. */
+PSL_API int dose_readout(const psl_tally_t *tally, const psl_phantom_t *phantom, double norm, double *dose,
+                 double *sigma, double *ledger, void *stream);
+
+PSL_API void psl_store_destroy(psl_store_t *store);
+PSL_API void psl_plan_destroy(psl_plan_t *plan);
+PSL_API void psl_batch_destroy(psl_batch_t *batch);
+PSL_API void psl_tally_destroy(psl_tally_t *tally);
+
+/* Text of the calling thread's last error ("" if none). */
+PSL_API const char *psl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSL_H */

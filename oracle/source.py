@@ -130,15 +130,20 @@ def roi_select(x_edges, y_edges, beam, z_psl, sad) -> np.ndarray:
     return sy[:, None] & sx[None, :]
 
 
-def psl_offset(seed: int, field: int, psl: int, nrec: int) -> int:
-    """Random first record of a PSL for one field: Philox(seed; field, tag, psl)."""
-    if nrec <= 0:
-        return 0
-    ctr = np.array([[field, TAG_OFFSET, psl & 0xFFFFFFFF, psl >> 32]], np.uint32)
-    key = np.array([[seed & 0xFFFFFFFF, seed >> 32]], np.uint32)
-    r = _lib.philox(ctr, key)[0]
-    r64 = int(r[0]) | (int(r[1]) << 32)
-    return (r64 * nrec) >> 64
+def psl_offsets(seed: int, field: np.ndarray, psl: np.ndarray, nrec: np.ndarray) -> np.ndarray:
+    """Random first record of each (field, PSL): the 64-bit word of
+    Philox(seed; field, tag, psl) scaled to [0, nrec) by (r * nrec) >> 64."""
+    n = len(psl)
+    ctr = np.zeros((n, 4), np.uint32)
+    ctr[:, 0] = field
+    ctr[:, 1] = TAG_OFFSET
+    ctr[:, 2] = psl & 0xFFFFFFFF
+    ctr[:, 3] = psl >> 32
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    r = _lib.philox(ctr, key) if n else np.zeros((0, 4), np.uint32)
+    r64 = r[:, 0].astype(object) + (r[:, 1].astype(object) << 32)
+    off = (r64 * nrec.astype(object)) >> 64
+    return np.array(list(off), np.int64) if n else np.zeros(0, np.int64)
 
 
 def make_plan(store: Store, beams, n_sim: int, seed: int, z_psl: float, sad: float) -> Plan:
@@ -160,16 +165,12 @@ def make_plan(store: Store, beams, n_sim: int, seed: int, z_psl: float, sad: flo
     if n_total == 0:
         raise ValueError("no phase-space records inside the selected PSLs")
     # N_ij = N_sim N_j / N_total, rounded by differencing the floor of the
-    # cumulative share (exact integers; the counts sum to N_sim)
-    cum = [0]
-    acc = 0
-    for c in nrec.tolist():
-        acc += c
-        cum.append(acc)
-    fl = [(n_sim * c) // n_total for c in cum]
-    count = np.array([fl[k + 1] - fl[k] for k in range(len(nrec))], np.int64)
-    offset = np.array([psl_offset(seed, int(f), int(p), int(n))
-                       for f, p, n in zip(field, psl, nrec)], np.int64)
+    # cumulative share (exact Python integers; the counts sum to N_sim)
+    cum = np.zeros(len(nrec) + 1, dtype=object)
+    cum[1:] = np.cumsum(nrec.astype(object))
+    fl = (cum * int(n_sim)) // n_total
+    count = np.array(list(fl[1:] - fl[:-1]), np.int64)
+    offset = psl_offsets(seed, field, psl, nrec)
     t = psl // (ne * npos)
     e = (psl // npos) % ne
     group = e * 2 + t
@@ -279,10 +280,13 @@ class SourceOut:
 
 
 def mu_ratios(beams) -> np.ndarray:
+    """w'/w = MU_i / MU_total (Sec. 2.3.3), from the float32 MU values the
+    plan carries, summed in beam order in double and rounded to float32."""
+    mus = [float(F32(b.mu)) for b in beams]
     tot = 0.0
-    for b in beams:
-        tot += float(b.mu)
-    return np.array([F32(float(b.mu) / tot) for b in beams], F32)
+    for m in mus:
+        tot += m
+    return np.array([F32(m / tot) for m in mus], F32)
 
 
 def source(plan: Plan, store: Store, records, beams, phantom, h: np.ndarray,

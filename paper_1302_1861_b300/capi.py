@@ -1,0 +1,265 @@
+"""Thin ctypes binding of the C ABI in include/psl.h (argument marshalling only).
+
+Every step of the path runs in libpsl_b300.so; this module only turns torch
+tensors into device pointers, Python numbers into C structs and status codes
+into exceptions.  It never falls back to anything else: if the library is
+missing or CUDA is unavailable the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpsl_b300.so")
+
+PSL_OK, PSL_EINVAL, PSL_ENOMEM, PSL_ECUDA, PSL_ETIMEOUT, PSL_EOVERFLOW = 0, -1, -2, -3, -4, -5
+PHYS_LOCAL_SECONDARIES, PHYS_FIRST_INTERACTION, PHYS_NO_MSC, PHYS_NO_HARD = 1, 2, 4, 8
+SRC_TRANSPORT, SRC_JAW, SRC_FLUENCE, SRC_ZERO_WEIGHT, SRC_MISS = 0, 1, 2, 3, 4
+
+EXPORTS = (
+    "psl_physics_default", "psl_build", "psl_store_info", "psl_store_read", "psl_plan_create",
+    "psl_plan_info", "psl_plan_read", "psl_source_batch", "psl_source_trace", "psl_batch_from_particles",
+    "psl_batch_info", "psl_tally_create", "psl_tally_reset", "psl_tally_read", "transport_run",
+    "transport_trace", "dose_readout", "psl_store_destroy", "psl_plan_destroy", "psl_batch_destroy",
+    "psl_tally_destroy", "psl_last_error",
+)
+
+vp = ctypes.c_void_p
+f32, i32, i64, u32, u64, f64 = (ctypes.c_float, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                ctypes.c_uint64, ctypes.c_double)
+
+
+class Records(ctypes.Structure):
+    _fields_ = [("x", vp), ("y", vp), ("u", vp), ("v", vp), ("e", vp), ("wt", vp), ("q", vp), ("n", i64)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", i32), ("ny", i32), ("n_ebins", i32), ("apr_copies", i32), ("x_edges", vp),
+                ("y_edges", vp), ("e_edges", vp), ("z_psl", f32)]
+
+
+class Beam(ctypes.Structure):
+    _fields_ = [("x1", f32), ("x2", f32), ("y1", f32), ("y2", f32), ("z_jaw_x", f32), ("z_jaw_y", f32),
+                ("gantry", f32), ("collimator", f32), ("couch", f32), ("mu", f32), ("roi_margin", f32),
+                ("iso", f32 * 3), ("fnx", i32), ("fny", i32), ("fx0", f32), ("fy0", f32), ("fdx", f32),
+                ("fdy", f32), ("fluence", vp)]
+
+
+class Phantom(ctypes.Structure):
+    _fields_ = [("nx", i32), ("ny", i32), ("nz", i32), ("vx", f32), ("vy", f32), ("vz", f32),
+                ("origin", f32 * 3), ("mat", vp), ("rho", vp)]
+
+
+class Physics(ctypes.Structure):
+    _fields_ = [("photon_cut", f32), ("electron_cut", f32), ("wcc", f32), ("wcb", f32), ("flags", u32)]
+
+
+class PslError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"PSL error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libpsl_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not built: run python -m paper_1302_1861_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name in EXPORTS:
+            getattr(L, name)
+        L.psl_last_error.restype = ctypes.c_char_p
+        L.psl_last_error.argtypes = []
+        L.psl_physics_default.restype = None
+        L.psl_physics_default.argtypes = [vp]
+        for name in ("psl_store_destroy", "psl_plan_destroy", "psl_batch_destroy", "psl_tally_destroy"):
+            getattr(L, name).restype = None
+            getattr(L, name).argtypes = [vp]
+        sig = {
+            "psl_build": [vp, vp, vp, vp],
+            "psl_store_info": [vp, vp, vp, vp],
+            "psl_store_read": [vp, vp, vp, vp, vp],
+            "psl_plan_create": [vp, vp, i32, f32, i64, u64, vp, vp],
+            "psl_plan_info": [vp, vp, vp, vp],
+            "psl_plan_read": [vp, vp, vp, vp, vp, vp],
+            "psl_source_batch": [vp, vp, i64, i64, vp, vp],
+            "psl_source_trace": [vp, vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp],
+            "psl_batch_from_particles": [vp, vp, vp, i64, u64, vp, vp],
+            "psl_batch_info": [vp, vp, vp, vp],
+            "psl_tally_create": [vp, i32, vp],
+            "psl_tally_reset": [vp, vp],
+            "psl_tally_read": [vp, vp, vp, vp],
+            "transport_run": [vp, vp, vp, vp, i32, vp],
+            "transport_trace": [vp, vp, vp, vp, i32, vp, vp, vp, vp],
+            "dose_readout": [vp, vp, f64, vp, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code: int):
+    if code != PSL_OK:
+        raise PslError(code, lib().psl_last_error().decode())
+
+
+def ptr(t) -> Optional[int]:
+    """Device (or host) address of a torch tensor / numpy array; None passes NULL."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def stream_ptr(stream=None) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+def physics(flags: int = 0, **kw) -> Physics:
+    p = Physics()
+    lib().psl_physics_default(ctypes.byref(p))
+    p.flags = flags
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Handle:
+    """Owns a library handle and destroys it with the matching call."""
+    _destroy = None
+
+    def __init__(self, h: int):
+        self.h = ctypes.c_void_p(h)
+
+    def close(self):
+        if self.h and self.h.value:
+            getattr(lib(), self._destroy)(self.h)
+            self.h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Store(Handle):
+    _destroy = "psl_store_destroy"
+
+    def info(self):
+        a, b, c = i64(), i64(), i64()
+        check(lib().psl_store_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+
+class Plan(Handle):
+    _destroy = "psl_plan_destroy"
+
+    def info(self):
+        a, b, c = i64(), i64(), i64()
+        check(lib().psl_plan_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+
+class Batch(Handle):
+    _destroy = "psl_batch_destroy"
+
+    def info(self):
+        a, b, c = i64(), i64(), i64()
+        check(lib().psl_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+
+class Tally(Handle):
+    _destroy = "psl_tally_destroy"
+
+
+def _out_handle():
+    return ctypes.c_void_p(0)
+
+
+def psl_build(params: Params, records: Records, stream=None) -> Store:
+    h = _out_handle()
+    check(lib().psl_build(ctypes.byref(params), ctypes.byref(records), ctypes.byref(h), stream_ptr(stream)))
+    return Store(h.value)
+
+
+def psl_store_read(store: Store, offsets=None, perm=None, records=None, stream=None):
+    check(lib().psl_store_read(store.h, ptr(offsets), ptr(perm), ptr(records), stream_ptr(stream)))
+
+
+def psl_plan_create(store: Store, beams: Sequence[Beam], sad: float, n_histories: int, seed: int,
+                    stream=None) -> Plan:
+    arr = (Beam * len(beams))(*beams)
+    h = _out_handle()
+    check(lib().psl_plan_create(store.h, arr, len(beams), sad, int(n_histories), int(seed), ctypes.byref(h),
+                                stream_ptr(stream)))
+    return Plan(h.value)
+
+
+def psl_plan_read(plan: Plan, beam=None, psl=None, count=None, offset=None, stream=None):
+    check(lib().psl_plan_read(plan.h, ptr(beam), ptr(psl), ptr(count), ptr(offset), stream_ptr(stream)))
+
+
+def psl_source_batch(plan: Plan, phantom: Phantom, first: int, n: int, stream=None) -> Batch:
+    h = _out_handle()
+    check(lib().psl_source_batch(plan.h, ctypes.byref(phantom), int(first), int(n), ctypes.byref(h),
+                                 stream_ptr(stream)))
+    return Batch(h.value)
+
+
+def psl_source_trace(plan: Plan, phantom: Phantom, first: int, n: int, entry=None, use=None, rec=None,
+                     beam=None, status=None, state=None, ptype=None, stream=None):
+    check(lib().psl_source_trace(plan.h, ctypes.byref(phantom), int(first), int(n), ptr(entry), ptr(use),
+                                 ptr(rec), ptr(beam), ptr(status), ptr(state), ptr(ptype), stream_ptr(stream)))
+
+
+def psl_batch_from_particles(state, ptype, pid, seed: int, stream=None) -> Batch:
+    h = _out_handle()
+    check(lib().psl_batch_from_particles(ptr(state), ptr(ptype), ptr(pid), int(ptype.shape[0]), int(seed),
+                                         ctypes.byref(h), stream_ptr(stream)))
+    return Batch(h.value)
+
+
+def psl_tally_create(phantom: Phantom, n_batches: int) -> Tally:
+    h = _out_handle()
+    check(lib().psl_tally_create(ctypes.byref(phantom), int(n_batches), ctypes.byref(h)))
+    return Tally(h.value)
+
+
+def psl_tally_reset(tally: Tally, stream=None):
+    check(lib().psl_tally_reset(tally.h, stream_ptr(stream)))
+
+
+def psl_tally_read(tally: Tally, tallies=None, ledger=None, stream=None):
+    check(lib().psl_tally_read(tally.h, ptr(tallies), ptr(ledger), stream_ptr(stream)))
+
+
+def transport_run(phantom: Phantom, phys: Physics, batch: Batch, tally: Tally, batch_index: int, stream=None):
+    check(lib().transport_run(ctypes.byref(phantom), ctypes.byref(phys), batch.h, tally.h, int(batch_index),
+                              stream_ptr(stream)))
+
+
+def transport_trace(phantom: Phantom, phys: Physics, batch: Batch, tally: Tally, batch_index: int,
+                    hist_dep=None, hist_esc=None, hist_events=None, stream=None):
+    check(lib().transport_trace(ctypes.byref(phantom), ctypes.byref(phys), batch.h, tally.h, int(batch_index),
+                                ptr(hist_dep), ptr(hist_esc), ptr(hist_events), stream_ptr(stream)))
+
+
+def dose_readout(tally: Tally, phantom: Phantom, norm: float, dose=None, sigma=None, ledger=None, stream=None):
+    check(lib().dose_readout(tally.h, ctypes.byref(phantom), float(norm), ptr(dose), ptr(sigma), ptr(ledger),
+                             stream_ptr(stream)))

@@ -1,0 +1,248 @@
+// psl_build (Sec. 2.3.2): PSL id per record, stable LSD onesweep radix sort of
+// (id, input index), gather of the records into 32-byte sorted records and
+// the bin-offset table.
+//
+// Sort design (B300): 8-bit digits.  One upsweep pass computes the ids and
+// the digit histograms of every pass at once; each digit pass is a single
+// onesweep kernel: tiles of 4096 keys are ranked inside the block with warp
+// match/ballot multisplit, the block's per-digit counts are published to a
+// decoupled look-back table (one 32-bit word per tile and digit holding a
+// 2-bit state and a 30-bit count), and the keys are scattered through shared
+// memory so that each digit run is written contiguously.  Tiles are taken in
+// order from an atomic counter so a tile only ever waits on tiles already
+// running; every wait has an iteration limit after which the kernel records
+// a timeout and proceeds.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "psl_internal.cuh"
+#include "sort.cuh"
+
+namespace {
+
+constexpr int RADIX = 256;
+constexpr int MAX_PASSES = SORT_MAX_PASSES;
+
+struct Edges {
+    int nx, ny, ne;
+    const float *xe, *ye, *ee;
+};
+
+// number of entries of a[0..n) that are <= v (a ascending)
+__device__ __forceinline__ int count_le(const float *a, int n, float v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// PSL id of every record + digit histograms of all passes (upsweep)
+__global__ void __launch_bounds__(256) k_key(psl_records_t r, Edges ed, uint32_t n_bins, uint32_t *keys,
+                                             int passes, uint32_t *hist) {
+    extern __shared__ float sh[];
+    float *xe = sh, *ye = xe + ed.nx + 1, *ee = ye + ed.ny + 1;
+    __shared__ uint32_t h[MAX_PASSES * RADIX];
+    for (int i = threadIdx.x; i <= ed.nx; i += blockDim.x) xe[i] = ed.xe[i];
+    for (int i = threadIdx.x; i <= ed.ny; i += blockDim.x) ye[i] = ed.ye[i];
+    for (int i = threadIdx.x; i <= ed.ne; i += blockDim.x) ee[i] = ed.ee[i];
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t n = r.n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float x = __ldg(r.x + i), y = __ldg(r.y + i), e = __ldg(r.e + i);
+        int q = __ldg(r.q + i);
+        int bx = count_le(xe, ed.nx + 1, x) - 1;
+        int by = count_le(ye, ed.ny + 1, y) - 1;
+        uint32_t key = n_bins;
+        if (bx >= 0 && bx < ed.nx && by >= 0 && by < ed.ny && e > 0.f) {
+            int eb = count_le(ee + 1, ed.ne - 1, e);
+            int t = q != 0;
+            key = (uint32_t)((t * ed.ne + eb) * (ed.nx * ed.ny) + by * ed.nx + bx);
+        }
+        keys[i] = key;
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p * RADIX + ((key >> (8 * p)) & 0xFF)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// sorted records (AoS, 32 B) from the permutation
+__global__ void __launch_bounds__(256) k_gather(psl_records_t r, const uint32_t *__restrict__ perm, int64_t n_valid,
+                                                PslRecord *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_valid; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t s = perm[i];
+        PslRecord o;
+        o.x = __ldg(r.x + s); o.y = __ldg(r.y + s); o.u = __ldg(r.u + s); o.v = __ldg(r.v + s);
+        o.e = __ldg(r.e + s); o.wt = __ldg(r.wt + s); o.src = s; o.q = (int32_t)__ldg(r.q + s);
+        float4 *d = reinterpret_cast<float4 *>(out + i);
+        const float4 *sp = reinterpret_cast<const float4 *>(&o);
+        d[0] = sp[0]; d[1] = sp[1];
+    }
+}
+
+// offsets[k] = first sorted position with key >= k, from the boundaries of the sorted keys
+__global__ void __launch_bounds__(256) k_offsets(const uint32_t *__restrict__ keys, int64_t n, int64_t n_bins,
+                                                 int64_t *__restrict__ offsets) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t prev = i == 0 ? -1 : (int64_t)keys[i - 1];
+        int64_t cur = i == n ? n_bins : (int64_t)keys[i];
+        if (cur > n_bins) cur = n_bins;
+        for (int64_t k = prev + 1; k <= cur; ++k) offsets[k] = i;
+    }
+}
+
+__global__ void k_count_valid(const int64_t *offsets, int64_t n_bins, int64_t *out) { *out = offsets[n_bins]; }
+
+}  // namespace
+
+int psl_sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_store_t **out, void *stream_) {
+    if (!prm || !rec || !out) return psl_fail(PSL_EINVAL, "psl_build: null argument");
+    *out = nullptr;
+    if (prm->apr_copies != 1) return psl_fail(PSL_EINVAL, "psl_build: apr_copies must be 1");
+    if (prm->nx <= 0 || prm->ny <= 0 || prm->n_ebins <= 0) return psl_fail(PSL_EINVAL, "psl_build: bad bin counts");
+    const int64_t n_bins = 2ll * prm->n_ebins * prm->nx * prm->ny;
+    if (n_bins >= (1ll << 31) - 1) return psl_fail(PSL_EINVAL, "psl_build: too many bins");
+    if (rec->n < 0 || rec->n >= (1ll << 30)) return psl_fail(PSL_EINVAL, "psl_build: record count out of range");
+    if (!prm->x_edges || !prm->y_edges || !prm->e_edges) return psl_fail(PSL_EINVAL, "psl_build: null edges");
+    for (int i = 0; i < prm->nx; ++i)
+        if (!(prm->x_edges[i] < prm->x_edges[i + 1])) return psl_fail(PSL_EINVAL, "psl_build: x edges not ascending");
+    for (int i = 0; i < prm->ny; ++i)
+        if (!(prm->y_edges[i] < prm->y_edges[i + 1])) return psl_fail(PSL_EINVAL, "psl_build: y edges not ascending");
+    for (int i = 0; i < prm->n_ebins; ++i)
+        if (!(prm->e_edges[i] < prm->e_edges[i + 1])) return psl_fail(PSL_EINVAL, "psl_build: e edges not ascending");
+    if (rec->n > 0 && (!rec->x || !rec->y || !rec->u || !rec->v || !rec->e || !rec->wt || !rec->q))
+        return psl_fail(PSL_EINVAL, "psl_build: null record array");
+
+    cudaStream_t st = as_stream(stream_);
+    const uint32_t n = (uint32_t)rec->n;
+    psl_store *s = new psl_store();
+    s->n_records = rec->n; s->n_bins = n_bins; s->nx = prm->nx; s->ny = prm->ny; s->n_ebins = prm->n_ebins;
+    s->z_psl = prm->z_psl;
+    cudaGetDevice(&s->device);
+    std::vector<float> edges;
+    edges.insert(edges.end(), prm->x_edges, prm->x_edges + prm->nx + 1);
+    edges.insert(edges.end(), prm->y_edges, prm->y_edges + prm->ny + 1);
+    edges.insert(edges.end(), prm->e_edges, prm->e_edges + prm->n_ebins + 1);
+
+    int bits = 1;
+    while ((1ll << bits) <= n_bins) ++bits;              // ids 0..n_bins inclusive
+    const int passes = (bits + 7) / 8;
+
+    uint32_t *keys[2] = {nullptr, nullptr}, *vals[2] = {nullptr, nullptr}, *hist = nullptr;
+    void *scratch = nullptr;
+    int64_t *nvalid_d = nullptr;
+    int rc = PSL_OK;
+    auto fail = [&](int code, const std::string &m) { rc = psl_fail(code, m); };
+    do {
+        cudaError_t e;
+        if ((e = cudaMalloc((void **)&s->edges, edges.size() * sizeof(float))) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if ((e = cudaMemcpyAsync(s->edges, edges.data(), edges.size() * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
+        if ((e = cudaMalloc((void **)&s->offsets, (n_bins + 1) * sizeof(int64_t))) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        size_t nn = std::max<uint32_t>(n, 1);
+        bool ok = true;
+        for (int b = 0; b < 2 && ok; ++b) {
+            ok &= cudaMallocAsync((void **)&keys[b], nn * 4, st) == cudaSuccess;
+            ok &= cudaMallocAsync((void **)&vals[b], nn * 4, st) == cudaSuccess;
+        }
+        ok &= cudaMallocAsync(&scratch, sort_pairs_scratch_bytes(n), st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&hist, MAX_PASSES * RADIX * 4 + 16, st) == cudaSuccess;
+        if (!ok) { fail(PSL_ENOMEM, "psl_build: sort buffers"); break; }
+        nvalid_d = reinterpret_cast<int64_t *>(hist + MAX_PASSES * RADIX);
+        cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, st);
+        Edges ed{prm->nx, prm->ny, prm->n_ebins, s->edges, s->edges + prm->nx + 1, s->edges + prm->nx + prm->ny + 2};
+        const int sms = psl_sm_count();
+        if (n == 0) {
+            cudaMemsetAsync(s->offsets, 0, (n_bins + 1) * sizeof(int64_t), st);
+            cudaMalloc((void **)&s->rec, sizeof(PslRecord));
+            break;
+        }
+        int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+        k_key<<<grid, 256, edges.size() * sizeof(float), st>>>(*rec, ed, (uint32_t)n_bins, keys[0], passes, hist);
+        int alt = 0;
+        sort_pairs_u32(keys[0], vals[0], keys[1], vals[1], n, bits, hist, true, scratch, &alt, st);
+        // after an odd number of passes the result is in the alternate buffers
+        uint32_t *skeys = alt ? keys[1] : keys[0], *svals = alt ? vals[1] : vals[0];
+        int g2 = (int)std::min<int64_t>((int64_t)n / 256 + 1, (int64_t)sms * 8);
+        k_offsets<<<g2, 256, 0, st>>>(skeys, n, n_bins, s->offsets);
+        k_count_valid<<<1, 1, 0, st>>>(s->offsets, n_bins, nvalid_d);
+        int64_t nvalid = 0;
+        uint32_t herr = 0;
+        cudaMemcpyAsync(&nvalid, nvalid_d, 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(&herr, sort_err_word(scratch), 4, cudaMemcpyDeviceToHost, st);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
+        if (herr & PSL_DEV_ERR_TIMEOUT) { fail(PSL_ETIMEOUT, "psl_build: look-back wait gave up"); break; }
+        s->n_valid = nvalid;
+        if ((e = cudaMalloc((void **)&s->rec, std::max<int64_t>(nvalid, 1) * sizeof(PslRecord))) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if (nvalid > 0) {
+            int g3 = (int)std::min<int64_t>((nvalid + 255) / 256, (int64_t)sms * 16);
+            k_gather<<<g3, 256, 0, st>>>(*rec, svals, nvalid, s->rec);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
+    } while (0);
+    for (int b = 0; b < 2; ++b) { if (keys[b]) cudaFreeAsync(keys[b], st); if (vals[b]) cudaFreeAsync(vals[b], st); }
+    if (scratch) cudaFreeAsync(scratch, st);
+    if (hist) cudaFreeAsync(hist, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (rc == PSL_OK && e2 != cudaSuccess) rc = psl_fail(PSL_ECUDA, cudaGetErrorString(e2));
+    if (rc != PSL_OK) { psl_store_destroy(s); return rc; }
+    *out = s;
+    return PSL_OK;
+}
+
+extern "C" int psl_store_info(const psl_store_t *s, int64_t *n_records, int64_t *n_valid, int64_t *n_bins) {
+    if (!s) return psl_fail(PSL_EINVAL, "psl_store_info: null store");
+    if (n_records) *n_records = s->n_records;
+    if (n_valid) *n_valid = s->n_valid;
+    if (n_bins) *n_bins = s->n_bins;
+    return PSL_OK;
+}
+
+namespace {
+__global__ void k_store_read(const PslRecord *rec, int64_t n, int64_t *perm, float *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        PslRecord r = rec[i];
+        if (perm) perm[i] = r.src;
+        if (out) {
+            const float *f = reinterpret_cast<const float *>(&r);
+            for (int k = 0; k < 8; ++k) out[8 * i + k] = f[k];
+        }
+    }
+}
+}  // namespace
+
+extern "C" int psl_store_read(const psl_store_t *s, int64_t *offsets, int64_t *perm, float *records, void *stream_) {
+    if (!s) return psl_fail(PSL_EINVAL, "psl_store_read: null store");
+    cudaStream_t st = as_stream(stream_);
+    if (offsets) PSL_CUDA(cudaMemcpyAsync(offsets, s->offsets, (s->n_bins + 1) * 8, cudaMemcpyDeviceToDevice, st));
+    if ((perm || records) && s->n_valid > 0) {
+        int g = (int)std::min<int64_t>((s->n_valid + 255) / 256, 4096);
+        k_store_read<<<g, 256, 0, st>>>(s->rec, s->n_valid, perm, records);
+        PSL_CUDA(cudaGetLastError());
+    }
+    return PSL_OK;
+}
+
+extern "C" void psl_store_destroy(psl_store_t *s) {
+    if (!s) return;
+    if (s->rec) cudaFree(s->rec);
+    if (s->offsets) cudaFree(s->offsets);
+    if (s->edges) cudaFree(s->edges);
+    delete s;
+}

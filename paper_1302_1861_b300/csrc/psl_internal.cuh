@@ -1,0 +1,208 @@
+// Internal declarations of the B300 PSL library: handles, particle layout,
+// device helpers (Philox, warp-aggregated queue pushes), error reporting.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/psl.h"
+
+// ------------------------------------------------------------------ errors --
+void psl_set_error(const std::string &msg);
+int psl_fail(int code, const std::string &msg);
+
+#define PSL_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return psl_fail(e_ == cudaErrorMemoryAllocation ? PSL_ENOMEM : PSL_ECUDA,       \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+#define PSL_CHECK_LAUNCH(name) PSL_CUDA(cudaGetLastError())
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// device error word bits
+#define PSL_DEV_ERR_TIMEOUT 1u
+#define PSL_DEV_ERR_QUEUE 2u
+#define PSL_DEV_ERR_STEPS 4u
+
+// ------------------------------------------------------------- particles --
+// 48-byte particle: three 16-byte words, loaded and stored as float4.
+struct __align__(16) Particle {
+    float x, y, z, e;        // phantom-local position (cm), kinetic energy (MeV)
+    float u, v, w, wt;       // direction cosines, statistical weight
+    uint32_t pid_lo, pid_hi; // Philox stream id
+    uint32_t type;           // 0 photon, 1 electron, 2 positron
+    uint32_t root;           // history index inside its batch (per-history traces)
+};
+static_assert(sizeof(Particle) == 48, "particle layout");
+
+// ----------------------------------------------------------------- store --
+struct PslRecord {           // 32-byte sorted record
+    float x, y, u, v, e, wt;
+    uint32_t src;            // input index
+    int32_t q;
+};
+static_assert(sizeof(PslRecord) == 32, "record layout");
+
+struct psl_store {
+    int64_t n_records = 0, n_valid = 0, n_bins = 0;
+    int32_t nx = 0, ny = 0, n_ebins = 0;
+    float z_psl = 0.f;
+    PslRecord *rec = nullptr;        // [n_valid]
+    int64_t *offsets = nullptr;      // [n_bins + 1]
+    float *edges = nullptr;          // device: x_edges | y_edges | e_edges
+    int device = 0;
+};
+
+// Per-beam constants precomputed on the device (float32, fixed op order).
+struct BeamDev {
+    float xlo, xhi, ylo, yhi;        // jaw bounds at the jaw planes
+    float dzx, dzy, diso;            // z_jaw_x - z_psl, z_jaw_y - z_psl, sad - z_psl
+    float mu_ratio;                  // mu_i / mu_total
+    float fx0, fy0, fdx, fdy;
+    int32_t fnx, fny;
+    const float *fluence;
+    float r[9];                      // beam-to-patient rotation (row major)
+    float iso[3];
+    float sad;
+};
+
+struct psl_plan {
+    const psl_store *store = nullptr;
+    int32_t n_beams = 0;
+    float sad = 100.f;
+    int64_t n_histories = 0, n_entries = 0, n_total_psl = 0;
+    uint64_t seed = 0;
+    int32_t n_groups = 0;
+    BeamDev *beams = nullptr;        // [n_beams]
+    // per entry (entry-list order)
+    int32_t *e_beam = nullptr;
+    int32_t *e_psl = nullptr;
+    int64_t *e_start = nullptr, *e_nrec = nullptr, *e_count = nullptr, *e_offset = nullptr;
+    // reading order
+    int64_t *group_start = nullptr;  // [n_groups + 1] first history of each group
+    int64_t *group_seg = nullptr;    // [n_groups + 1] first segment of each group
+    uint32_t *sorted = nullptr;      // [n_active] entries in visiting order, grouped
+    int64_t *seg_h = nullptr;        // [n_active] group-local first history of segment
+    int64_t *seg_r0 = nullptr;       // first round of segment
+    int32_t *seg_w = nullptr;        // active entries in the segment's rounds
+    int64_t n_active = 0;
+};
+
+struct psl_batch {
+    int64_t n_histories = 0;         // histories (or caller particles) covered
+    int64_t first_history = 0;
+    uint64_t seed = 0;               // keys the particles' random streams
+    Particle *p = nullptr;           // photons from the front, electrons from the back
+    int64_t cap = 0;
+    uint32_t *counts = nullptr;      // device [2]: photons, electrons
+    int64_t n_photons = 0, n_electrons = 0;
+    int consumed = 0;
+};
+
+struct Workspace;
+struct psl_tally {
+    int32_t nx = 0, ny = 0, nz = 0, n_batches = 0;
+    int64_t nvox = 0;
+    unsigned long long *t = nullptr;  // [n_batches * nvox]
+    unsigned long long *ledger = nullptr;  // [8]
+    Workspace *ws = nullptr;
+};
+
+// ----------------------------------------------------------------- Philox --
+#define TAG_PARTICLE 0u
+#define TAG_OFFSET 1u
+#define TAG_CHILD 2u
+
+struct u32x4 { uint32_t a, b, c, d; };
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products
+// with the key bumped by the Weyl constants between rounds.
+__host__ __device__ __forceinline__ u32x4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                   uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = mulhi32(m0, c0), lo0 = m0 * c0;
+        uint32_t hi1 = mulhi32(m1, c2), lo1 = m1 * c2;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Per-particle random stream: draw d uses word d%4 of block d/4 of
+// Philox(key = seed; counter = (d/4, TAG_PARTICLE, pid)).
+struct Rng {
+    uint32_t k0, k1, p0, p1;
+    uint32_t draw;
+    u32x4 blk;
+    __device__ __forceinline__ void init(uint64_t seed, uint32_t pid_lo, uint32_t pid_hi) {
+        k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32); p0 = pid_lo; p1 = pid_hi; draw = 0;
+    }
+    // ((r >> 9) + 0.5) * 2^-23: 24 significant bits, exact in float
+    __device__ __forceinline__ float uniform() {
+        uint32_t w = draw & 3u;
+        if (w == 0) blk = philox10(draw >> 2, TAG_PARTICLE, p0, p1, k0, k1);
+        uint32_t r = w == 0 ? blk.a : (w == 1 ? blk.b : (w == 2 ? blk.c : blk.d));
+        ++draw;
+        return ((float)(r >> 9) + 0.5f) * (1.0f / 8388608.0f);
+    }
+};
+
+__device__ __forceinline__ void child_id(uint64_t seed, uint32_t p0, uint32_t p1, uint32_t ordinal,
+                                         uint32_t &c0, uint32_t &c1) {
+    u32x4 o = philox10(ordinal, TAG_CHILD, p0, p1, (uint32_t)seed, (uint32_t)(seed >> 32));
+    c0 = o.a;
+    c1 = o.b | 0x80000000u;
+}
+
+// ------------------------------------------------------------ queue push --
+struct Queue {
+    Particle *data;
+    uint32_t *count;
+    uint32_t cap;
+};
+
+__device__ __forceinline__ void store_particle(Particle *dst, const Particle &p) {
+    const float4 *s = reinterpret_cast<const float4 *>(&p);
+    float4 *d = reinterpret_cast<float4 *>(dst);
+    d[0] = s[0]; d[1] = s[1]; d[2] = s[2];
+}
+
+__device__ __forceinline__ Particle load_particle(const Particle *src) {
+    Particle p;
+    const float4 *s = reinterpret_cast<const float4 *>(src);
+    float4 *d = reinterpret_cast<float4 *>(&p);
+    d[0] = __ldg(s); d[1] = __ldg(s + 1); d[2] = __ldg(s + 2);
+    return p;
+}
+
+// Append with one atomic per group of converged lanes.
+__device__ __forceinline__ void queue_push(const Queue &q, const Particle &p, uint32_t *err) {
+    unsigned mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(q.count, (uint32_t)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    uint32_t idx = base + __popc(mask & ((1u << lane) - 1u));
+    if (idx < q.cap) store_particle(q.data + idx, p);
+    else atomicOr(err, PSL_DEV_ERR_QUEUE);
+}
+
+// grid size for a memory-bound kernel: multiple of the SM count
+int psl_sm_count();

@@ -1,0 +1,111 @@
+// Tallies and dose readout (Sec. 2.3.3 batches and uncertainty, Sec. 2.5
+// normalisation).  The int64 fixed-point counters are the only place where
+// FP64 is used on the device: the final conversion to dose and its batch
+// standard error, and the energy-ledger sums.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "psl_internal.cuh"
+
+void workspace_free(Workspace *w);
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_readout(const unsigned long long *t, int64_t nvox, int nb, const float *rho,
+                                                 double scale, double *dose, double *sigma, unsigned long long *dep) {
+    unsigned long long local = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
+        long long sum = 0;
+        for (int b = 0; b < nb; ++b) sum += (long long)t[(size_t)b * nvox + v];
+        local += (unsigned long long)sum;
+        const double r = (double)rho[v];
+        const double c = r > 0.0 ? scale / r : 0.0;     // Gy per fixed-point unit
+        const double tot = (double)sum;
+        if (dose) dose[v] = tot * c;
+        if (sigma) {
+            double s = 0.0;
+            if (nb > 1) {
+                const double mean = tot / nb;
+                double var = 0.0;
+                for (int b = 0; b < nb; ++b) {
+                    const double d = (double)(long long)t[(size_t)b * nvox + v] - mean;
+                    var += d * d;
+                }
+                s = c * sqrt((double)nb / (nb - 1.0) * var);
+            }
+            sigma[v] = s;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(dep, local);
+}
+
+__global__ void k_ledger_out(const unsigned long long *ledger, const unsigned long long *dep, double *out) {
+    const double s = 1.0 / 4294967296.0;
+    out[0] = (double)(long long)ledger[0] * s;
+    out[1] = (double)(long long)ledger[1] * s;
+    out[2] = (double)(long long)dep[0] * s;
+}
+
+}  // namespace
+
+extern "C" int psl_tally_create(const psl_phantom_t *ph, int32_t n_batches, psl_tally_t **out) {
+    if (!ph || !out || n_batches <= 0 || ph->nx <= 0 || ph->ny <= 0 || ph->nz <= 0)
+        return psl_fail(PSL_EINVAL, "psl_tally_create: bad argument");
+    *out = nullptr;
+    psl_tally *t = new psl_tally();
+    t->nx = ph->nx; t->ny = ph->ny; t->nz = ph->nz; t->n_batches = n_batches;
+    t->nvox = (int64_t)ph->nx * ph->ny * ph->nz;
+    cudaError_t e1 = cudaMalloc((void **)&t->t, (size_t)n_batches * t->nvox * 8);
+    cudaError_t e2 = cudaMalloc((void **)&t->ledger, 16 * 8);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) { psl_tally_destroy(t); return psl_fail(PSL_ENOMEM, "psl_tally_create: allocation"); }
+    cudaMemset(t->t, 0, (size_t)n_batches * t->nvox * 8);
+    cudaMemset(t->ledger, 0, 16 * 8);
+    PSL_CUDA(cudaDeviceSynchronize());
+    *out = t;
+    return PSL_OK;
+}
+
+extern "C" int psl_tally_reset(psl_tally_t *t, void *stream_) {
+    if (!t) return psl_fail(PSL_EINVAL, "psl_tally_reset: null tally");
+    cudaStream_t st = as_stream(stream_);
+    PSL_CUDA(cudaMemsetAsync(t->t, 0, (size_t)t->n_batches * t->nvox * 8, st));
+    PSL_CUDA(cudaMemsetAsync(t->ledger, 0, 16 * 8, st));
+    return PSL_OK;
+}
+
+extern "C" int psl_tally_read(const psl_tally_t *t, int64_t *tallies, int64_t *ledger, void *stream_) {
+    if (!t) return psl_fail(PSL_EINVAL, "psl_tally_read: null tally");
+    cudaStream_t st = as_stream(stream_);
+    if (tallies) PSL_CUDA(cudaMemcpyAsync(tallies, t->t, (size_t)t->n_batches * t->nvox * 8, cudaMemcpyDeviceToDevice, st));
+    if (ledger) PSL_CUDA(cudaMemcpyAsync(ledger, t->ledger, 8 * 8, cudaMemcpyDeviceToDevice, st));
+    return PSL_OK;
+}
+
+extern "C" int dose_readout(const psl_tally_t *t, const psl_phantom_t *ph, double norm, double *dose, double *sigma,
+                            double *ledger, void *stream_) {
+    if (!t || !ph || !ph->rho) return psl_fail(PSL_EINVAL, "dose_readout: null argument");
+    if (ph->nx != t->nx || ph->ny != t->ny || ph->nz != t->nz) return psl_fail(PSL_EINVAL, "dose_readout: phantom mismatch");
+    cudaStream_t st = as_stream(stream_);
+    // Gy per fixed-point unit at unit density: 2^-32 MeV * J/MeV / (V cm^3 * 1e-3 kg/g)
+    const double vol = (double)ph->vx * (double)ph->vy * (double)ph->vz;
+    const double scale = norm * (1.0 / 4294967296.0) * 1.602176634e-13 / (vol * 1e-3);
+    unsigned long long *dep = t->ledger + 8;          // scratch slot for the deposited sum
+    PSL_CUDA(cudaMemsetAsync(dep, 0, 8, st));
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>((t->nvox + 255) / 256, (int64_t)psl_sm_count() * 8));
+    k_readout<<<grid, 256, 0, st>>>(t->t, t->nvox, t->n_batches, ph->rho, scale, dose, sigma, dep);
+    if (ledger) k_ledger_out<<<1, 1, 0, st>>>(t->ledger, dep, ledger);
+    PSL_CUDA(cudaGetLastError());
+    return PSL_OK;
+}
+
+extern "C" void psl_tally_destroy(psl_tally_t *t) {
+    if (!t) return;
+    if (t->t) cudaFree(t->t);
+    if (t->ledger) cudaFree(t->ledger);
+    if (t->ws) workspace_free(t->ws);
+    delete t;
+}

@@ -1,0 +1,792 @@
+// transport_run (Sec. 2.3.3): photon and electron transport through the voxel
+// phantom with 64-bit fixed-point dose counters.
+//
+// Work is organised as generations of typed queues.  A photon pass moves
+// every photon of its queue to the end of its life (Woodcock tracking) and
+// appends the charged secondaries to the electron queue; the electron queue
+// is then regrouped by energy band (counting sort on 32 log bands) so that
+// consecutive particles - and therefore warps - step one type and one band;
+// an electron pass moves each electron to its cut-off, appending delta rays
+// to the next electron queue and bremsstrahlung / annihilation photons to
+// the next photon queue.  Passes repeat until the queues are empty.
+//
+// Inside a pass each lane owns one particle and runs one event per loop
+// iteration; a lane whose particle ends takes the next queue entry
+// (warp-aggregated atomic), so warps stay full until the queue drains.
+// Every particle draws from its own Philox stream keyed by its id, and
+// secondaries get ids derived from (parent id, ordinal), so the integer tally
+// does not depend on how particles are scheduled.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "physics.cuh"
+#include "psl_internal.cuh"
+
+namespace {
+
+constexpr int NT = 2048;                  // table nodes
+constexpr double T_LO = 1.0e-3, T_HI = 30.0;
+constexpr int NBANDS = 32;
+constexpr float F_ME = 0.51099895f;
+constexpr float F_TWO_PI = 6.28318530717958647692f;
+constexpr int MAX_E_STEPS = 100000;
+constexpr int MAX_GEN = 64;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+struct Tables {
+    const float4 *ph0, *ph1;   // material 0/1: mu_c, mu_pe, mu_pp, mu_total (cm^2/g)
+    const float4 *el;          // S_restricted (MeV cm^2/g), sigma_moller, sigma_brem (cm^2/g), 0
+    const float *mumax;        // majorant (1/cm), phantom dependent
+    float lnE0, inv_dln;
+};
+
+struct Acc {
+    unsigned long long dep, esc, compton, photo, pair, steps;
+};
+
+struct Args {
+    int nx, ny, nz;
+    float vx, vy, vz, ivx, ivy, ivz;
+    const uint8_t *mat;
+    const float *rho;
+    float pcut, ecut, wcc, wcb;
+    uint32_t flags;
+    uint64_t seed;
+    Tables tab;
+    unsigned long long *tally;
+    unsigned long long *ledger;
+    unsigned long long *hist_dep, *hist_esc;
+    int32_t *hist_events;
+    uint32_t *err;
+    Queue e_out, p_out;
+    float band_ln0, band_scale;
+};
+
+// ----------------------------------------------------------- tables ------
+__global__ void k_tables(float4 *ph0, float4 *ph1, float4 *el, double wcc, double wcb) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NT) return;
+    const double lnE = log(T_LO) + (log(T_HI) - log(T_LO)) * i / (NT - 1);
+    const double E = exp(lnE);
+    double mc, mpe, mpp;
+    ph_mu_rho(E, 0, mc, mpe, mpp);
+    ph0[i] = make_float4((float)mc, (float)mpe, (float)mpp, (float)(mc + mpe + mpp));
+    ph_mu_rho(E, 1, mc, mpe, mpp);
+    ph1[i] = make_float4((float)mc, (float)mpe, (float)mpp, (float)(mc + mpe + mpp));
+    el[i] = make_float4((float)el_stop_restricted(E, wcc, wcb), (float)el_moller_sigma(E, wcc),
+                        (float)el_brem_sigma(E, wcb), 0.f);
+}
+
+__global__ void k_rho_max(const uint8_t *mat, const float *rho, int64_t n, int *out) {
+    __shared__ int m[2];
+    if (threadIdx.x < 2) m[threadIdx.x] = 0;
+    __syncthreads();
+    int l0 = 0, l1 = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int r = __float_as_int(fmaxf(rho[i], 0.f));    // non-negative floats order as ints
+        if (mat[i]) l1 = max(l1, r); else l0 = max(l0, r);
+    }
+    atomicMax(&m[0], l0);
+    atomicMax(&m[1], l1);
+    __syncthreads();
+    if (threadIdx.x < 2) atomicMax(&out[threadIdx.x], m[threadIdx.x]);
+}
+
+__global__ void k_majorant(const float4 *ph0, const float4 *ph1, const int *rmax, float *mumax) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NT) return;
+    float r0 = __int_as_float(rmax[0]), r1 = __int_as_float(rmax[1]);
+    // 1e-6 relative head-room over the interpolated material coefficients
+    mumax[i] = fmaxf(r0 * ph0[i].w, r1 * ph1[i].w) * 1.000001f;
+}
+
+__device__ __forceinline__ void tab_pos(const Tables &T, float E, int &i, float &f) {
+    float x = (__logf(E) - T.lnE0) * T.inv_dln;
+    x = fminf(fmaxf(x, 0.0f), (float)(NT - 1) - 1e-3f);
+    i = (int)x;
+    f = x - (float)i;
+}
+
+__device__ __forceinline__ float4 lerp4(const float4 *a, int i, float f) {
+    float4 p = __ldg(a + i), q = __ldg(a + i + 1);
+    return make_float4(p.x + f * (q.x - p.x), p.y + f * (q.y - p.y), p.z + f * (q.z - p.z), p.w + f * (q.w - p.w));
+}
+
+__device__ __forceinline__ float lerp1(const float *a, int i, float f) {
+    float p = __ldg(a + i), q = __ldg(a + i + 1);
+    return p + f * (q - p);
+}
+
+__device__ __forceinline__ float stop_of(const Tables &T, float E) {
+    int i; float f;
+    tab_pos(T, E, i, f);
+    float p = __ldg(&T.el[i].x), q = __ldg(&T.el[i + 1].x);
+    return p + f * (q - p);
+}
+
+// ------------------------------------------------------------- helpers ---
+__device__ __forceinline__ unsigned long long fixed_point(float e, float wt) {
+    return (unsigned long long)__float2ll_rn(__fmul_rn(e, wt) * 4294967296.0f);
+}
+
+__device__ __forceinline__ void deposit(const Args &A, Acc &acc, int64_t iv, float e, float wt, uint32_t root) {
+    unsigned long long q = fixed_point(e, wt);
+    if (!q) return;
+    atomicAdd(&A.tally[iv], q);
+    acc.dep += q;
+    if (A.hist_dep) atomicAdd(&A.hist_dep[root], q);
+}
+
+__device__ __forceinline__ void escape(const Args &A, Acc &acc, float e, float wt, uint32_t root) {
+    unsigned long long q = fixed_point(e, wt);
+    acc.esc += q;
+    if (A.hist_esc) atomicAdd(&A.hist_esc[root], q);
+}
+
+__device__ __forceinline__ void count_event(const Args &A, uint32_t root) {
+    if (A.hist_events) atomicAdd(&A.hist_events[root], 1);
+}
+
+// rotate unit direction by polar cosine c and azimuth phi (renormalised)
+__device__ __forceinline__ void rotate_dir(float &u, float &v, float &w, float c, float phi) {
+    float st = sqrtf(fmaxf(0.0f, 1.0f - c * c)), sp, cp;
+    sincosf(phi, &sp, &cp);
+    float nu, nv, nw;
+    if (fabsf(w) > 0.99999f) {
+        nu = st * cp; nv = st * sp; nw = w > 0.0f ? c : -c;
+    } else {
+        float t = sqrtf(1.0f - w * w);
+        nu = u * c + st * (u * w * cp - v * sp) / t;
+        nv = v * c + st * (v * w * cp + u * sp) / t;
+        nw = w * c - st * cp * t;
+    }
+    float n = rsqrtf(nu * nu + nv * nv + nw * nw);
+    u = nu * n; v = nv * n; w = nw * n;
+}
+
+__device__ __forceinline__ void push_particle(const Queue &q, const Args &A, uint32_t type, float x, float y, float z,
+                                              float u, float v, float w, float e, float wt, uint32_t p0, uint32_t p1,
+                                              uint32_t &nchild, uint32_t root) {
+    Particle c;
+    c.x = x; c.y = y; c.z = z; c.e = e; c.u = u; c.v = v; c.w = w; c.wt = wt;
+    child_id(A.seed, p0, p1, nchild++, c.pid_lo, c.pid_hi);
+    c.type = type; c.root = root;
+    queue_push(q, c, A.err);
+}
+
+__device__ void annihilate(const Args &A, Rng &rng, float x, float y, float z, float wt, uint32_t p0, uint32_t p1,
+                           uint32_t &nchild, uint32_t root) {
+    float cth = 2.0f * rng.uniform() - 1.0f, phi = F_TWO_PI * rng.uniform();
+    float sth = sqrtf(fmaxf(0.0f, 1.0f - cth * cth)), sp, cp;
+    sincosf(phi, &sp, &cp);
+    float a0 = sth * cp, a1 = sth * sp, a2 = cth;
+    push_particle(A.p_out, A, 0, x, y, z, a0, a1, a2, F_ME, wt, p0, p1, nchild, root);
+    push_particle(A.p_out, A, 0, x, y, z, -a0, -a1, -a2, F_ME, wt, p0, p1, nchild, root);
+}
+
+// a charged secondary: queued for transport, or deposited in place
+__device__ void emit_charged(const Args &A, Acc &acc, Rng &rng, uint32_t type, float T, float x, float y, float z,
+                             float u, float v, float w, float wt, int64_t iv, uint32_t p0, uint32_t p1, uint32_t &nchild,
+                             uint32_t root) {
+    if (T > A.ecut && !(A.flags & PSL_PHYS_LOCAL_SECONDARIES)) {
+        push_particle(A.e_out, A, type, x, y, z, u, v, w, T, wt, p0, p1, nchild, root);
+        return;
+    }
+    deposit(A, acc, iv, T, wt, root);
+    if (type == 2) {
+        if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) deposit(A, acc, iv, 2.0f * F_ME, wt, root);
+        else annihilate(A, rng, x, y, z, wt, p0, p1, nchild, root);
+    }
+}
+
+__device__ __forceinline__ void flush_acc(const Args &A, Acc &a) {
+    unsigned long long v[6] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (v[0]) atomicAdd(&A.ledger[2], v[0]);
+        if (v[1]) atomicAdd(&A.ledger[1], v[1]);
+        if (v[2]) atomicAdd(&A.ledger[3], v[2]);
+        if (v[3]) atomicAdd(&A.ledger[4], v[3]);
+        if (v[4]) atomicAdd(&A.ledger[5], v[4]);
+        if (v[5]) atomicAdd(&A.ledger[6], v[5]);
+    }
+}
+
+// ------------------------------------------------------------- photons ---
+struct Photon {
+    float x, y, z, u, v, w, e, wt;
+    uint32_t p0, p1, root, nchild;
+    Rng rng;
+    float mumax;
+    int ti;
+    float tf;
+};
+
+__device__ __forceinline__ void photon_energy(const Args &A, Photon &g) {
+    tab_pos(A.tab, g.e, g.ti, g.tf);
+    g.mumax = lerp1(A.tab.mumax, g.ti, g.tf);
+}
+
+// one Woodcock step (+ interaction); returns false when the photon ends
+__device__ bool photon_event(const Args &A, Acc &acc, Photon &g) {
+    const float s = -logf(g.rng.uniform()) / g.mumax;
+    g.x += s * g.u; g.y += s * g.v; g.z += s * g.w;
+    const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
+    if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)A.nx && fy < (float)A.ny && fz < (float)A.nz)) {
+        escape(A, acc, g.e, g.wt, g.root);
+        return false;
+    }
+    const int64_t iv = ((int64_t)fz * A.ny + (int64_t)fy) * A.nx + (int64_t)fx;
+    const int m = __ldg(A.mat + iv);
+    const float rho = __ldg(A.rho + iv);
+    const float4 c = lerp4(m ? A.tab.ph1 : A.tab.ph0, g.ti, g.tf);
+    const float mc = rho * c.x, mpe = rho * c.y, mpp = rho * c.z;
+    const float mu = mc + mpe + mpp;
+    if (mu > g.mumax) atomicOr(A.err, 8u);
+    if (g.rng.uniform() * g.mumax >= mu) return true;           // virtual interaction
+    count_event(A, g.root);
+    const float r = g.rng.uniform() * mu;
+    const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
+    if (r < mc) {                                                 // Compton (Kahn's method)
+        acc.compton++;
+        if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
+        const float k = g.e / F_ME;
+        float x = 1.0f;
+        for (int it = 0; it < 1000; ++it) {
+            const float r1 = g.rng.uniform(), r2 = g.rng.uniform(), r3 = g.rng.uniform();
+            if (r1 <= (1.0f + 2.0f * k) / (9.0f + 2.0f * k)) {
+                x = 1.0f + 2.0f * k * r2;
+                if (r3 <= 4.0f * (1.0f / x - 1.0f / (x * x))) break;
+            } else {
+                x = (1.0f + 2.0f * k) / (1.0f + 2.0f * k * r2);
+                const float cc = 1.0f - (x - 1.0f) / k;
+                if (r3 <= 0.5f * (cc * cc + 1.0f / x)) break;
+            }
+        }
+        const float cth = fminf(1.0f, fmaxf(-1.0f, 1.0f - (x - 1.0f) / k));
+        const float ep = g.e / x, phi = F_TWO_PI * g.rng.uniform();
+        float nu = g.u, nv = g.v, nw = g.w;
+        rotate_dir(nu, nv, nw, cth, phi);
+        const float te = g.e - ep;
+        float du = g.e * g.u - ep * nu, dv = g.e * g.v - ep * nv, dw = g.e * g.w - ep * nw;
+        const float nn = sqrtf(du * du + dv * dv + dw * dw);
+        if (nn > 0.0f) { du /= nn; dv /= nn; dw /= nn; } else { du = g.u; dv = g.v; dw = g.w; }
+        emit_charged(A, acc, g.rng, 1, te, g.x, g.y, g.z, du, dv, dw, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+        g.e = ep; g.u = nu; g.v = nv; g.w = nw;
+        if (g.e < A.pcut) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
+        photon_energy(A, g);
+        return true;
+    } else if (r < mc + mpe) {                                    // photoelectric
+        acc.photo++;
+        if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
+        emit_charged(A, acc, g.rng, 1, g.e, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+        return false;
+    }
+    acc.pair++;                                                    // pair production
+    if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
+    const float avail = g.e - 2.0f * F_ME, eps = g.rng.uniform();
+    const float t1 = eps * avail, t2 = avail - t1;
+    emit_charged(A, acc, g.rng, 1, t1, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+    emit_charged(A, acc, g.rng, 2, t2, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+    return false;
+}
+
+__global__ void __launch_bounds__(256) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
+                                                uint32_t cap, uint32_t *head) {
+    const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    Acc acc = {0, 0, 0, 0, 0, 0};
+    Photon g;
+    bool alive = false, done = false;
+    for (;;) {
+        const unsigned need = __ballot_sync(FULL, !alive && !done);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(head, (uint32_t)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (!alive && !done) {
+                const uint32_t idx = base + __popc(need & lt);
+                if (idx < n) {
+                    const Particle p = load_particle(src + idx);
+                    g.x = p.x; g.y = p.y; g.z = p.z; g.u = p.u; g.v = p.v; g.w = p.w; g.e = p.e; g.wt = p.wt;
+                    g.p0 = p.pid_lo; g.p1 = p.pid_hi; g.root = p.root; g.nchild = 0;
+                    g.rng.init(A.seed, p.pid_lo, p.pid_hi);
+                    photon_energy(A, g);
+                    alive = true;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, alive)) break;
+        if (alive) alive = photon_event(A, acc, g);
+    }
+    flush_acc(A, acc);
+}
+
+// ----------------------------------------------------------- electrons ---
+struct Electron {
+    float x, y, z, u, v, w, t, wt, nlam;
+    int ix, iy, iz;
+    uint32_t p0, p1, root, nchild;
+    int steps;
+    bool pos;
+    Rng rng;
+};
+
+__device__ __forceinline__ float highland(float T, float s, float rho) {
+    const float t = s * rho * (1.0f / 36.08f);
+    if (!(t > 0.0f)) return 0.0f;
+    const float bcp = T * (T + 2.0f * F_ME) / (T + F_ME);
+    const float f = 1.0f + 0.038f * logf(t);
+    if (!(f > 0.0f)) return 0.0f;
+    return 13.6f / bcp * sqrtf(t) * f;
+}
+
+// path (g/cm^2) to slow from T to Tl: 3-point Gauss-Legendre of 1/S
+__device__ __forceinline__ float path_between(const Tables &T, float Tl, float Th) {
+    const float m = 0.5f * (Th + Tl), h = 0.5f * (Th - Tl), a = 0.7745966692414834f * h;
+    return h * (0.5555555555555556f / stop_of(T, m - a) + 0.8888888888888889f / stop_of(T, m) +
+                0.5555555555555556f / stop_of(T, m + a));
+}
+
+// energy after a path h (g/cm^2): RK4 on dT/dh = -S(T)
+__device__ __forceinline__ float energy_after(const Tables &T, float t, float h) {
+    const float k1 = stop_of(T, t);
+    const float k2 = stop_of(T, fmaxf(t - 0.5f * h * k1, 1e-3f));
+    const float k3 = stop_of(T, fmaxf(t - 0.5f * h * k2, 1e-3f));
+    const float k4 = stop_of(T, fmaxf(t - h * k3, 1e-3f));
+    return t - h * (k1 + 2.0f * k2 + 2.0f * k3 + k4) * (1.0f / 6.0f);
+}
+
+__device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, uint32_t *err) {
+    const float tau = T / F_ME, ec = wcc / T;
+    const float g = (tau / (tau + 1.0f)) * (tau / (tau + 1.0f));
+    const float a = (2.0f * tau + 1.0f) / ((tau + 1.0f) * (tau + 1.0f));
+    const float w1 = 1.0f / ec - 2.0f, w2 = 5.0f * (0.5f - ec);
+    for (int it = 0; it < 1000; ++it) {
+        const float r1 = rng.uniform(), r2 = rng.uniform(), r3 = rng.uniform();
+        const float e = (r1 * (w1 + w2) < w1) ? ec / (1.0f - r2 * (1.0f - 2.0f * ec)) : ec + r2 * (0.5f - ec);
+        const float q = e / (1.0f - e);
+        const float f = 1.0f + q * q + g * e * e - a * q;
+        if (r3 * (1.0f + 5.0f * e * e) <= f) return e;
+    }
+    atomicOr(err, PSL_DEV_ERR_STEPS);
+    return ec;
+}
+
+__device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &s, int64_t iv) {
+    deposit(A, acc, iv, s.t, s.wt, s.root);
+    if (s.pos) {
+        if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) deposit(A, acc, iv, 2.0f * F_ME, s.wt, s.root);
+        else annihilate(A, s.rng, s.x, s.y, s.z, s.wt, s.p0, s.p1, s.nchild, s.root);
+    }
+}
+
+// one condensed-history step (+ hard event); returns false when the electron ends
+__device__ bool electron_event(const Args &A, Acc &acc, Electron &s) {
+    const int64_t iv = ((int64_t)s.iz * A.ny + s.iy) * A.nx + s.ix;
+    if (s.t <= A.ecut || ++s.steps > MAX_E_STEPS) {
+        if (s.steps > MAX_E_STEPS) atomicOr(A.err, PSL_DEV_ERR_STEPS);
+        electron_end(A, acc, s, iv);
+        return false;
+    }
+    acc.steps++;
+    count_event(A, s.root);
+    const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
+    const float rho = __ldg(A.rho + iv);
+    int ti; float tf;
+    tab_pos(A.tab, s.t, ti, tf);
+    const float4 el = lerp4(A.tab.el, ti, tf);
+    // hard cross sections vanish below their thresholds (guard the interpolation)
+    const float sig = hard_on ? rho * ((s.t > 2.0f * A.wcc ? el.y : 0.0f) + (s.t > A.wcb ? el.z : 0.0f)) : 0.0f;
+    const float s_hard = sig > 0.0f ? s.nlam / sig : INFINITY;
+    // distance to the voxel boundary
+    float s_bound = INFINITY;
+    int axis = -1, cross = 0;
+    {
+        const float d[3] = {s.u, s.v, s.w}, p[3] = {s.x, s.y, s.z}, vv[3] = {A.vx, A.vy, A.vz};
+        const int ii[3] = {s.ix, s.iy, s.iz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float t;
+            if (d[k] > 0.0f) t = ((float)(ii[k] + 1) * vv[k] - p[k]) / d[k];
+            else if (d[k] < 0.0f) t = ((float)ii[k] * vv[k] - p[k]) / d[k];
+            else continue;
+            t = fmaxf(t, 0.0f);
+            if (t < s_bound) { s_bound = t; axis = k; cross = d[k] > 0.0f ? 1 : -1; }
+        }
+    }
+    const float tlim = fmaxf(0.9f * s.t, A.ecut);
+    const float s_max = path_between(A.tab, tlim, s.t) / rho;
+    int which;
+    float step;
+    if (s_hard <= s_bound && s_hard <= s_max) { which = 0; step = s_hard; }
+    else if (s_bound <= s_max) { which = 1; step = s_bound; }
+    else { which = 2; step = s_max; }
+    float tend = which == 2 ? tlim : fmaxf(energy_after(A.tab, s.t, rho * step), tlim);
+    const float th0 = highland(s.t, step, rho);
+    deposit(A, acc, iv, s.t - tend, s.wt, s.root);
+    s.t = tend;
+    s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
+    s.nlam -= step * sig;
+    if (!(A.flags & PSL_PHYS_NO_MSC) && step > 0.0f) {
+        const float th = th0 * sqrtf(-2.0f * logf(s.rng.uniform()));
+        const float phi = F_TWO_PI * s.rng.uniform();
+        rotate_dir(s.u, s.v, s.w, cosf(th), phi);
+    }
+    if (which == 1) {
+        int out = 0;
+        if (axis == 0) { s.x = (float)(cross > 0 ? s.ix + 1 : s.ix) * A.vx; s.ix += cross; out = s.ix < 0 || s.ix >= A.nx; }
+        else if (axis == 1) { s.y = (float)(cross > 0 ? s.iy + 1 : s.iy) * A.vy; s.iy += cross; out = s.iy < 0 || s.iy >= A.ny; }
+        else { s.z = (float)(cross > 0 ? s.iz + 1 : s.iz) * A.vz; s.iz += cross; out = s.iz < 0 || s.iz >= A.nz; }
+        if (out) {
+            escape(A, acc, s.t + (s.pos ? 2.0f * F_ME : 0.0f), s.wt, s.root);
+            return false;
+        }
+    } else if (which == 0) {
+        int tj; float tg;
+        tab_pos(A.tab, s.t, tj, tg);
+        const float4 e2 = lerp4(A.tab.el, tj, tg);
+        const float sm = s.t > 2.0f * A.wcc ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
+        const float r = s.rng.uniform() * (sm + sb);
+        if (sm + sb > 0.0f) {
+            if (r < sm) {                                         // hard Moller
+                const float eps = sample_moller(s.t, A.wcc, s.rng, A.err);
+                const float W = eps * s.t, tp = s.t - W;
+                const float cp = sqrtf(tp * (s.t + 2.0f * F_ME) / (s.t * (tp + 2.0f * F_ME)));
+                const float cd = sqrtf(W * (s.t + 2.0f * F_ME) / (s.t * (W + 2.0f * F_ME)));
+                const float phi = F_TWO_PI * s.rng.uniform();
+                float du = s.u, dv = s.v, dw = s.w;
+                rotate_dir(du, dv, dw, cd, phi + 3.14159265358979f);
+                rotate_dir(s.u, s.v, s.w, cp, phi);
+                emit_charged(A, acc, s.rng, 1, W, s.x, s.y, s.z, du, dv, dw, s.wt, iv, s.p0, s.p1, s.nchild, s.root);
+                s.t = tp;
+            } else {                                              // hard bremsstrahlung
+                const float kph = A.wcb * expf(s.rng.uniform() * logf(s.t / A.wcb));
+                if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) deposit(A, acc, iv, kph, s.wt, s.root);
+                else push_particle(A.p_out, A, 0, s.x, s.y, s.z, s.u, s.v, s.w, kph, s.wt, s.p0, s.p1, s.nchild, s.root);
+                s.t -= kph;
+            }
+        }
+        s.nlam = -logf(s.rng.uniform());
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
+                                                  uint32_t *head) {
+    const uint32_t n = min(*n_ptr, cap);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    Acc acc = {0, 0, 0, 0, 0, 0};
+    Electron s;
+    bool alive = false, done = false;
+    for (;;) {
+        const unsigned need = __ballot_sync(FULL, !alive && !done);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(head, (uint32_t)__popc(need));
+            base = __shfl_sync(FULL, base, leader);
+            if (!alive && !done) {
+                const uint32_t idx = base + __popc(need & lt);
+                if (idx < n) {
+                    const Particle p = load_particle(src + idx);
+                    s.x = p.x; s.y = p.y; s.z = p.z; s.u = p.u; s.v = p.v; s.w = p.w; s.t = p.e; s.wt = p.wt;
+                    s.p0 = p.pid_lo; s.p1 = p.pid_hi; s.root = p.root; s.nchild = 0; s.steps = 0;
+                    s.pos = p.type == 2;
+                    s.ix = min(max((int)floorf(s.x * A.ivx), 0), A.nx - 1);
+                    s.iy = min(max((int)floorf(s.y * A.ivy), 0), A.ny - 1);
+                    s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
+                    s.rng.init(A.seed, p.pid_lo, p.pid_hi);
+                    s.nlam = -logf(s.rng.uniform());
+                    alive = true;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, alive)) break;
+        if (alive) alive = electron_event(A, acc, s);
+    }
+    flush_acc(A, acc);
+}
+
+// ------------------------------------------------------------ band sort ---
+__device__ __forceinline__ int band_of(const Args &A, float e) {
+    int b = (int)((__logf(e) - A.band_ln0) * A.band_scale);
+    return min(max(b, 0), NBANDS - 1);
+}
+
+__device__ __forceinline__ const Particle *pick(const Particle *a, uint32_t na, const Particle *b, uint32_t i) {
+    return i < na ? a + i : b + (i - na);
+}
+
+__global__ void __launch_bounds__(256) k_band_count(Args A, const Particle *a, uint32_t na, const Particle *b,
+                                                    const uint32_t *nb_ptr, uint32_t capb, uint32_t *hist) {
+    __shared__ uint32_t h[NBANDS];
+    if (threadIdx.x < NBANDS) h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t n = na + min(*nb_ptr, capb);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[band_of(A, __ldg(&pick(a, na, b, i)->e))], 1u);
+    __syncthreads();
+    if (threadIdx.x < NBANDS && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_band_scan(uint32_t *hist, uint32_t *cursor, uint32_t *out_count) {
+    const int t = threadIdx.x;                  // one warp
+    uint32_t v = hist[t], x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (t >= o) x += y;
+    }
+    cursor[t] = x - v;
+    hist[t] = 0;
+    if (t == 31) *out_count = x;
+}
+
+__global__ void __launch_bounds__(256) k_band_scatter(Args A, const Particle *a, uint32_t na, const Particle *b,
+                                                      const uint32_t *nb_ptr, uint32_t capb, uint32_t *cursor,
+                                                      Particle *dst, uint32_t capd) {
+    __shared__ uint32_t h[NBANDS], base[NBANDS];
+    const uint32_t n = na + min(*nb_ptr, capb);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        if (threadIdx.x < NBANDS) h[threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t i = i0 + threadIdx.x;
+        Particle p;
+        int bnd = 0;
+        uint32_t local = 0;
+        if (i < n) {
+            p = load_particle(pick(a, na, b, i));
+            bnd = band_of(A, p.e);
+            local = atomicAdd(&h[bnd], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < NBANDS && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]);
+        __syncthreads();
+        if (i < n) {
+            uint32_t d = base[bnd] + local;
+            if (d < capd) store_particle(dst + d, p);
+            else atomicOr(A.err, PSL_DEV_ERR_QUEUE);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_ledger_add(unsigned long long *ledger, const unsigned long long *src) {
+    ledger[0] += src[0];
+    ledger[1] += src[1];
+}
+
+// --------------------------------------------------------------- state ---
+struct TableCache {
+    int device = -1;
+    float wcc = -1.f, wcb = -1.f;
+    float4 *ph0 = nullptr, *ph1 = nullptr, *el = nullptr;
+};
+std::mutex g_tab_mu;
+std::vector<TableCache> g_tabs;
+
+int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    for (auto &t : g_tabs)
+        if (t.device == dev && t.wcc == wcc && t.wcb == wcb) { out = t; return PSL_OK; }
+    TableCache t;
+    t.device = dev; t.wcc = wcc; t.wcb = wcb;
+    PSL_CUDA(cudaMalloc((void **)&t.ph0, NT * sizeof(float4)));
+    PSL_CUDA(cudaMalloc((void **)&t.ph1, NT * sizeof(float4)));
+    PSL_CUDA(cudaMalloc((void **)&t.el, NT * sizeof(float4)));
+    k_tables<<<(NT + 255) / 256, 256, 0, st>>>(t.ph0, t.ph1, t.el, (double)wcc, (double)wcb);
+    PSL_CUDA(cudaGetLastError());
+    PSL_CUDA(cudaStreamSynchronize(st));
+    g_tabs.push_back(t);
+    out = t;
+    return PSL_OK;
+}
+
+}  // namespace
+
+struct Workspace {
+    int64_t chunk = 0;                 // primaries per chunk
+    uint32_t cap_p = 0, cap_e = 0, cap_s = 0;
+    Particle *P[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr}, *S = nullptr;
+    uint32_t *cnt = nullptr;           // [0..1] P counts, [2..3] E counts, [4] S count, [5..8] heads,
+                                       // [9] err, [16..47] band hist, [48..79] cursors
+    float *mumax = nullptr;
+    int *rmax = nullptr;
+    uint32_t *host = nullptr;          // pinned: counts read back per generation
+};
+
+void workspace_free(Workspace *w) {
+    if (!w) return;
+    for (int k = 0; k < 2; ++k) { if (w->P[k]) cudaFree(w->P[k]); if (w->E[k]) cudaFree(w->E[k]); }
+    if (w->S) cudaFree(w->S);
+    if (w->cnt) cudaFree(w->cnt);
+    if (w->mumax) cudaFree(w->mumax);
+    if (w->rmax) cudaFree(w->rmax);
+    if (w->host) cudaFreeHost(w->host);
+    delete w;
+}
+
+static int workspace_ensure(psl_tally *t, int64_t chunk) {
+    Workspace *w = t->ws;
+    if (w && w->chunk >= chunk) return PSL_OK;
+    if (w) { cudaDeviceSynchronize(); workspace_free(w); t->ws = nullptr; }
+    w = new Workspace();
+    t->ws = w;
+    w->chunk = chunk;
+    const int64_t base = std::max<int64_t>(chunk, 4096);
+    w->cap_p = (uint32_t)std::min<int64_t>(3 * base, 0xF0000000ll);
+    w->cap_e = (uint32_t)std::min<int64_t>(8 * base, 0xF0000000ll);
+    w->cap_s = w->cap_e + (uint32_t)base;
+    PSL_CUDA(cudaMalloc((void **)&w->P[0], (size_t)w->cap_p * sizeof(Particle)));
+    PSL_CUDA(cudaMalloc((void **)&w->P[1], (size_t)w->cap_p * sizeof(Particle)));
+    PSL_CUDA(cudaMalloc((void **)&w->E[0], (size_t)w->cap_e * sizeof(Particle)));
+    PSL_CUDA(cudaMalloc((void **)&w->E[1], (size_t)w->cap_e * sizeof(Particle)));
+    PSL_CUDA(cudaMalloc((void **)&w->S, (size_t)w->cap_s * sizeof(Particle)));
+    PSL_CUDA(cudaMalloc((void **)&w->cnt, 128 * sizeof(uint32_t)));
+    PSL_CUDA(cudaMemset(w->cnt, 0, 128 * sizeof(uint32_t)));
+    PSL_CUDA(cudaMalloc((void **)&w->mumax, NT * sizeof(float)));
+    PSL_CUDA(cudaMalloc((void **)&w->rmax, 2 * sizeof(int)));
+    PSL_CUDA(cudaMallocHost((void **)&w->host, 16 * sizeof(uint32_t)));
+    return PSL_OK;
+}
+
+static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, psl_batch_t *batch, psl_tally_t *tally,
+                          int32_t b, int64_t *hist_dep, int64_t *hist_esc, int32_t *hist_events, void *stream_) {
+    if (!ph || !batch || !tally) return psl_fail(PSL_EINVAL, "transport_run: null argument");
+    if (ph->nx != tally->nx || ph->ny != tally->ny || ph->nz != tally->nz || !ph->mat || !ph->rho)
+        return psl_fail(PSL_EINVAL, "transport_run: phantom does not match the tally");
+    if (b < 0 || b >= tally->n_batches) return psl_fail(PSL_EINVAL, "transport_run: batch index out of range");
+    if (batch->consumed) return psl_fail(PSL_EINVAL, "transport_run: batch already transported");
+    psl_physics_t P;
+    psl_physics_default(&P);
+    if (phys) P = *phys;
+    if (!(P.electron_cut > 0.f) || !(P.photon_cut > 0.f) || !(P.wcc > P.electron_cut) || !(P.wcb > P.photon_cut))
+        return psl_fail(PSL_EINVAL, "transport_run: bad physics thresholds");
+    cudaStream_t st = as_stream(stream_);
+    TableCache tc;
+    int rc = get_tables(P.wcc, P.wcb, st, tc);
+    if (rc) return rc;
+    const int64_t nph = batch->n_photons, nel = batch->n_electrons;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::max(nph, nel), 1 << 21));
+    if ((rc = workspace_ensure(tally, chunk))) return rc;
+    Workspace *w = tally->ws;
+    batch->consumed = 1;
+
+    // majorant for this phantom
+    const int64_t nvox = tally->nvox;
+    cudaMemsetAsync(w->rmax, 0, 2 * sizeof(int), st);
+    k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax);
+    k_majorant<<<(NT + 255) / 256, 256, 0, st>>>(tc.ph0, tc.ph1, w->rmax, w->mumax);
+
+    Args A;
+    A.nx = ph->nx; A.ny = ph->ny; A.nz = ph->nz;
+    A.vx = ph->vx; A.vy = ph->vy; A.vz = ph->vz;
+    A.ivx = 1.0f / ph->vx; A.ivy = 1.0f / ph->vy; A.ivz = 1.0f / ph->vz;
+    A.mat = ph->mat; A.rho = ph->rho;
+    A.pcut = P.photon_cut; A.ecut = P.electron_cut; A.wcc = P.wcc; A.wcb = P.wcb; A.flags = P.flags;
+    A.seed = batch->seed;
+    A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.mumax = w->mumax;
+    A.tab.lnE0 = (float)log(T_LO);
+    A.tab.inv_dln = (float)((NT - 1) / (log(T_HI) - log(T_LO)));
+    A.tally = tally->t + (size_t)b * nvox;
+    A.ledger = tally->ledger;
+    A.hist_dep = (unsigned long long *)hist_dep;
+    A.hist_esc = (unsigned long long *)hist_esc;
+    A.hist_events = hist_events;
+    A.err = w->cnt + 9;
+    A.band_ln0 = logf(P.electron_cut);
+    A.band_scale = (float)(NBANDS / log(20.0 / P.electron_cut));
+
+    cudaMemsetAsync(w->cnt, 0, 128 * sizeof(uint32_t), st);
+    k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2));
+
+    const int sms = psl_sm_count();
+    const int grid_t = sms * 4;                     // persistent transport grid
+    const int grid_m = sms * 8;                     // memory passes
+    uint32_t *cP[2] = {w->cnt + 0, w->cnt + 1}, *cE[2] = {w->cnt + 2, w->cnt + 3}, *cS = w->cnt + 4;
+    uint32_t *head = w->cnt + 5, *hist = w->cnt + 16, *cursor = w->cnt + 48;
+    int pc = 0, ec = 0;                             // index of the "current" buffers
+
+    auto band_sort = [&](const Particle *a, uint32_t na, const Particle *bq, const uint32_t *nb, uint32_t capb) {
+        k_band_count<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, hist);
+        k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS);
+        k_band_scatter<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s);
+    };
+    auto photon_pass = [&](const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
+        Args a2 = A;
+        a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
+        a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
+        cudaMemsetAsync(head, 0, 4, st);
+        k_photon<<<grid_t, 256, 0, st>>>(a2, src, nptr, nfix, cap, head);
+    };
+    auto electron_pass = [&]() {
+        Args a2 = A;
+        a2.e_out = Queue{w->E[ec ^ 1], cE[ec ^ 1], w->cap_e};
+        a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
+        cudaMemsetAsync(head + 1, 0, 4, st);
+        k_electron<<<grid_t, 256, 0, st>>>(a2, w->S, cS, w->cap_s, head + 1);
+    };
+
+    const int64_t cap = batch->cap;
+    for (int64_t a0 = 0; a0 < std::max(nph, nel); a0 += chunk) {
+        const uint32_t cp = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(nph - a0, chunk));
+        const uint32_t ce = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(nel - a0, chunk));
+        pc = 0; ec = 0;
+        cudaMemsetAsync(w->cnt, 0, 5 * sizeof(uint32_t), st);
+        if (cp) photon_pass(batch->p + a0, nullptr, cp, cp);
+        band_sort(batch->p + (cap - a0 - ce), ce, w->E[ec], cE[ec], w->cap_e);
+        electron_pass();
+        int gen = 0;
+        for (;; ++gen) {
+            cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport_run: ") + cudaGetErrorString(e));
+            if (w->host[9] & (PSL_DEV_ERR_QUEUE)) return psl_fail(PSL_EOVERFLOW, "transport_run: particle queue overflow");
+            const uint32_t np = w->host[pc ^ 1], ne = w->host[2 + (ec ^ 1)];
+            if (np == 0 && ne == 0) break;
+            if (gen >= MAX_GEN) return psl_fail(PSL_EOVERFLOW, "transport_run: too many secondary generations");
+            // next generation: swap current/next, clear the new "next"
+            pc ^= 1; ec ^= 1;
+            cudaMemsetAsync(cP[pc ^ 1], 0, 4, st);
+            cudaMemsetAsync(cE[ec ^ 1], 0, 4, st);
+            photon_pass(w->P[pc], cP[pc], 0, w->cap_p);
+            band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
+            electron_pass();
+        }
+    }
+    cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport_run: ") + cudaGetErrorString(e));
+    if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport_run: particle queue overflow");
+    return PSL_OK;
+}
+
+extern "C" int transport_run(const psl_phantom_t *ph, const psl_physics_t *phys, psl_batch_t *batch, psl_tally_t *tally,
+                             int32_t b, void *stream) {
+    return transport_impl(ph, phys, batch, tally, b, nullptr, nullptr, nullptr, stream);
+}
+
+extern "C" int transport_trace(const psl_phantom_t *ph, const psl_physics_t *phys, psl_batch_t *batch,
+                               psl_tally_t *tally, int32_t b, int64_t *hist_dep, int64_t *hist_esc,
+                               int32_t *hist_events, void *stream) {
+    return transport_impl(ph, phys, batch, tally, b, hist_dep, hist_esc, hist_events, stream);
+}

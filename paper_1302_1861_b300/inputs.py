@@ -315,8 +315,9 @@ def config4(n_records: int = 40_000_000, n_histories: int = 500_000_000) -> Work
         for _ in range(int(rng.integers(10, 61))):
             side = rng.uniform(2.0, 20.0)
             cx, cy = rng.uniform(-2.0, 2.0, 2)
-            beams.append(Beam(cx - side / 2, cx + side / 2, cy - side / 2, cy + side / 2,
-                              gantry=gantry, mu=float(rng.uniform(0.5, 2.0)),
+            f32 = lambda v: float(np.float32(v))          # beam parameters are float32 in the plan
+            beams.append(Beam(f32(cx - side / 2), f32(cx + side / 2), f32(cy - side / 2), f32(cy + side / 2),
+                              gantry=f32(gantry), mu=f32(rng.uniform(0.5, 2.0)),
                               roi_margin=1.0, fluence=smooth_field(rng, 40, 6)))
     return Workload("psl-imrt-ct128x100", 4, rec, binning, beams,
                     ct_phantom(4, (100, 128, 128), 0.25), n_histories)

@@ -1,0 +1,190 @@
+"""GPU parity of transport, tally and readout against the oracle
+(Sec. 2.3.3 dose counters and batches, Sec. 2.5 normalisation).
+
+Bars (FP32 transport against the FP64 oracle on the same Philox streams):
+* closed forms: narrow-beam attenuation exp(-mu x) and channel fractions
+  within 5 binomial standard deviations; CSDA path of a straight electron
+  within 1e-4 relative; energy ledger deposited + escaped = emitted within
+  1e-6 relative;
+* event level: per-history deposited energy equal to the oracle's within
+  1e-4 relative for >= 97 % of histories (the rest are histories in which an
+  FP32/FP64 rounding difference flipped a branch: they must still conserve
+  energy);
+* dose (config 1, 1e5 histories): mean relative difference < 0.5 % over
+  voxels above 10 % of the maximum, >= 99 % of them within 3 combined
+  standard deviations, gamma 2 %/2 mm >= 99 %.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from oracle import _lib, readout, source  # noqa: E402
+from paper_1302_1861_b300 import capi, engine, inputs  # noqa: E402
+from tests.gpu_util import transport_particles  # noqa: E402
+
+FP = 2.0 ** 32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _column_workload(nz, vz, rho=None, mat=None, nxy=1, vxy=1.0):
+    w = inputs.config1(n_records=100, n_histories=100)
+    m = np.zeros((nz, nxy, nxy), np.uint8) if mat is None else mat
+    r = np.ones((nz, nxy, nxy), np.float32) if rho is None else rho
+    w.phantom = inputs.Phantom(m, r, (vxy, vxy, vz), (0.0, 0.0, 0.0))
+    return w
+
+
+def _pencil(n, ptype, E, x=0.5, y=0.5):
+    return (np.full(n, ptype, np.int32), np.tile([x, y, 0.0], (n, 1)), np.tile([0.0, 0.0, 1.0], (n, 1)),
+            np.full(n, E), np.ones(n), np.arange(n, dtype=np.uint64))
+
+
+@pytest.mark.parametrize("E", [0.1, 1.0, 6.0])
+def test_narrow_beam_attenuation(E):
+    w = _column_workload(40, 1.0)
+    dw = engine.upload(w)
+    n = 400_000
+    t, lg = transport_particles(dw, *_pencil(n, 0, E), seed=21, flags=capi.PHYS_FIRST_INTERACTION)
+    mu = _lib.lib().ora_mu_rho(E, 0, 3)
+    beyond = n - np.cumsum(t[:, 0, 0] / (np.float32(E) * FP))
+    p = np.exp(-mu * np.arange(1, 41))
+    sd = np.sqrt(n * p * (1 - p)) + 1
+    assert (np.abs(beyond - n * p) < 5 * sd).all()
+
+
+@pytest.mark.parametrize("E,mat", [(0.04, 0), (0.04, 1), (6.0, 0), (3.0, 1)])
+def test_channel_fractions(E, mat):
+    w = _column_workload(20, 1.0, mat=np.full((20, 1, 1), mat, np.uint8))
+    dw = engine.upload(w)
+    n = 400_000
+    _, lg = transport_particles(dw, *_pencil(n, 0, E), seed=22, flags=capi.PHYS_FIRST_INTERACTION)
+    k = lg[3:6].astype(float)
+    mus = np.array([_lib.lib().ora_mu_rho(E, mat, c) for c in range(3)])
+    p = mus / mus.sum()
+    sd = np.sqrt(k.sum() * p * (1 - p)) + 1
+    assert (np.abs(k - k.sum() * p) < 5 * sd).all()
+
+
+@pytest.mark.parametrize("T0,rho", [(2.0, 1.0), (0.9, 0.26), (5.0, 1.85)])
+def test_csda_range_and_track(T0, rho):
+    """Straight electron, no hard events: the dose profile ends where the
+    oracle's does (both follow the CSDA range), all on the track."""
+    nz = 200
+    w = _column_workload(nz, 0.05, rho=np.full((nz, 1, 1), rho, np.float32))
+    dw = engine.upload(w)
+    n = 8
+    flags = capi.PHYS_NO_MSC | capi.PHYS_NO_HARD | capi.PHYS_LOCAL_SECONDARIES
+    t, lg = transport_particles(dw, *_pencil(n, 1, T0), seed=3, flags=flags)
+    to, lo, ho = oracle.transport(*_pencil(n, 1, T0), w.phantom, seed=3, flags=flags, per_history=True)
+    csda = ho["path"][0]
+    last = int(math.floor(csda / 0.05))
+    prof = t[:, 0, 0].astype(float)
+    assert prof[last + 2:].sum() == 0 and (prof[: last - 1] > 0).all()
+    # energy per voxel along the track agrees with the oracle to 1e-4 (relative to the total)
+    assert np.abs(prof - to[:, 0, 0]).sum() < 1e-4 * prof.sum() + 4
+    assert abs(int(lg[2]) - n * np.float32(T0) * FP) < 1e-6 * n * T0 * FP
+
+
+def test_energy_ledger_heterogeneous_with_pairs():
+    w = _column_workload(32, 0.5, nxy=32, vxy=0.5)
+    w.phantom = inputs.slab_phantom(2, 32, 0.5)
+    w.phantom.origin = (0.0, 0.0, 0.0)
+    dw = engine.upload(w)
+    n = 20000
+    t, lg = transport_particles(dw, *_pencil(n, 0, 6.0, 8.0, 8.0), seed=5)
+    assert lg[5] > 0 and lg[7] == 0
+    emitted = n * 6.0 * FP
+    assert abs(int(lg[2]) + int(lg[1]) - emitted) <= 1e-6 * emitted
+    assert int(t.sum()) == int(lg[2])
+
+
+def _event_parity(w, n_hist, first=0, min_match=0.97):
+    """Per-history comparison on the same Philox streams."""
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
+    ost = source.psl_build(w.records, w.binning)
+    opl = source.make_plan(ost, w.beams, w.n_histories, w.seed, w.z_psl, w.sad)
+    hs = np.arange(first, first + n_hist)
+    s = source.source(opl, ost, w.records, w.beams, w.phantom, hs, w.z_psl, w.sad)
+    m = s.status == source.ST_TRANSPORT
+    _, lgo, ho = oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
+                                  hs[m].astype(np.uint64), w.phantom, w.seed, per_history=True)
+    batch = capi.psl_source_batch(plan, dw.phantom, first, n_hist)
+    tally = capi.psl_tally_create(dw.phantom, 1)
+    hd = torch.zeros(n_hist, dtype=torch.int64, device="cuda")
+    he = torch.zeros(n_hist, dtype=torch.int64, device="cuda")
+    hv = torch.zeros(n_hist, dtype=torch.int32, device="cuda")
+    capi.transport_trace(dw.phantom, capi.physics(), batch, tally, 0, hd, he, hv)
+    gd, ge, gv = hd.cpu().numpy()[m], he.cpu().numpy()[m], hv.cpu().numpy()[m]
+    od, oe, ov = ho["dep"], ho["esc"], ho["events"]
+    tot_g = (gd + ge).astype(float)
+    match = (np.abs(gd - od) <= 1e-4 * np.maximum(tot_g, 1.0) + 16) & (gv == ov)
+    # every history conserves its own energy on the GPU
+    e_in = np.rint(s.e[m] * s.wt[m].astype(float) * FP)
+    assert np.all(np.abs(tot_g - e_in) <= 1e-5 * e_in + 64)
+    return match.mean(), match
+
+
+def test_brute_force_ten_histories():
+    w = inputs.config1()
+    rate, match = _event_parity(w, 10)
+    assert rate >= 0.9
+
+
+def test_event_parity_config1_block():
+    w = inputs.config1()
+    rate, _ = _event_parity(w, 3000, first=40_000)
+    assert rate >= 0.97
+
+
+def test_event_parity_config2_sampled():
+    """Full-size 1e8-history plan, a sampled range deep inside it."""
+    w = inputs.config2()
+    rate, _ = _event_parity(w, 2000, first=63_000_000)
+    assert rate >= 0.95
+
+
+def test_dose_parity_config1():
+    w = inputs.config1()
+    dw = engine.upload(w)
+    g = engine.run(dw)
+    torch.cuda.synchronize()
+    nz, ny, nx = w.phantom.shape
+    dg, sg = g["dose"].cpu().numpy().reshape(nz, ny, nx), g["sigma"].cpu().numpy().reshape(nz, ny, nx)
+    o = oracle.run_plan(w)
+    do, so = readout.dose(o["tallies"], w.phantom.rho, w.phantom.voxel, g["norm"])
+    m = do > 0.1 * do.max()
+    rel = np.abs(dg[m] - do[m]).mean() / do[m].mean()
+    assert rel < 0.005
+    within = np.abs(dg[m] - do[m]) <= 3 * np.sqrt(sg[m] ** 2 + so[m] ** 2)
+    assert within.mean() >= 0.99
+    gamma, _ = readout.gamma_pass_rate(do, dg, w.phantom.voxel)
+    assert gamma >= 0.99
+    # energy ledger on the GPU, FP64 sums of the fixed-point counters
+    lg = g["ledger"].cpu().numpy()
+    assert abs(lg[2] + lg[1] - lg[0]) <= 1e-6 * lg[0]
+
+
+def test_determinism_and_batch_split():
+    w = inputs.config1(n_histories=30_000)
+    dw = engine.upload(w)
+    a = engine.run(dw, n_batches=1, readout=False)
+    ta, la = engine.raw_tallies(dw, a["tally"], 1)
+    b = engine.run(dw, n_batches=3, readout=False, store=a["store"], plan=a["plan"])
+    tb, lb = engine.raw_tallies(dw, b["tally"], 3)
+    assert np.array_equal(ta[0], tb.sum(0))
+    assert np.array_equal(la[:7], lb[:7])
+    c = engine.run(dw, n_batches=1, readout=False, store=a["store"], plan=a["plan"])
+    tc, _ = engine.raw_tallies(dw, c["tally"], 1)
+    assert np.array_equal(ta, tc)
