@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the PSL Monte Carlo dose path on one B300 (or N, one rank per GPU).
+
+Workload (the 10x10 cm^2 configuration): 1e7 phase-space records (2 types x
+32 log-energy x 12 x 12 1-cm PSL bins), a 64^3 x 0.25 cm water phantom with a
+lung and a bone slab, 1e8 histories in 10 batches.  One step is the whole path
+on that input: psl_build (sort the phase space into PSLs), psl_plan_create,
+10 x (psl_source_batch + transport_run) and dose_readout.  The metric is
+histories per second (whole job, all ranks); inputs (250 MB of records) are
+resident in HBM and larger than L2, and L2 is also flushed between steps.
+
+Extra keys: `e2e` (the same step through the C ABI from pinned host buffers,
+with the records/phantom uploaded and dose/sigma/ledger read back inside the
+timed region), `roofline` (dominant kernel, timed live with CUDA events on its
+stream), `cpu_baseline` (the oracle on a bounded sample on the host cores),
+`time_to_1pct` (histories and seconds for 1 % isocentre uncertainty,
+extrapolated from the measured standard error), `clocks`, `gpu_launches`.
+
+`--impl reference` times the CPU oracle (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "histories/s (PSL source + transport + dose readout)"
+PEAKS_FALLBACK = {"hbm_gbs": 6400.0}
+# FP32 CUDA-core peak: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm: each step transports a bounded
+    sample of the workload's histories on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    from oracle import source
+    from paper_1302_1861_b300 import inputs
+
+    w = inputs.config2()
+    t0 = time.perf_counter()
+    st = source.psl_build(w.records, w.binning)
+    pl = source.make_plan(st, w.beams, w.n_histories, w.seed, w.z_psl, w.sad)
+    t_setup = time.perf_counter() - t0
+    n_s = args.ref_sample
+    rng = np.random.default_rng(7)
+
+    def step(k):
+        h0 = int(rng.integers(0, w.n_histories - n_s))
+        t = time.perf_counter()
+        s = source.source(pl, st, w.records, w.beams, w.phantom, np.arange(h0, h0 + n_s), w.z_psl, w.sad)
+        m = s.status == source.ST_TRANSPORT
+        oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
+                         np.arange(h0, h0 + n_s)[m].astype(np.uint64), w.phantom, w.seed)
+        return time.perf_counter() - t
+
+    for k in range(args.warmup):
+        step(k)
+    times = [step(k) for k in range(args.steps)]
+    t_h = float(np.mean(times)) / n_s
+    value = w.n_histories / (t_setup + t_h * w.n_histories)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * (t_setup + t_h * w.n_histories), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "records": w.records.n, "histories": w.n_histories,
+                       "phantom": "64^3 x 0.25 cm slab", "batches": w.n_batches},
+            "cpu_baseline": {"value": value, "unit": "histories/s", "cores": cores, "kind": "oracle",
+                             "sample": f"psl_build+plan on all {w.records.n} records ({t_setup:.2f} s) + "
+                                       f"{args.steps} x {n_s} histories at random offsets, scaled to 1e8"},
+            "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline(n_sample=40_000):
+    """The oracle as it stands on a bounded sample of the same workload."""
+    import oracle
+    from oracle import source
+    from paper_1302_1861_b300 import inputs
+    w = inputs.config2()
+    t0 = time.perf_counter()
+    st = source.psl_build(w.records, w.binning)
+    pl = source.make_plan(st, w.beams, w.n_histories, w.seed, w.z_psl, w.sad)
+    t_setup = time.perf_counter() - t0
+    h0 = 50_000_000
+    hs = np.arange(h0, h0 + n_sample)
+    t1 = time.perf_counter()
+    s = source.source(pl, st, w.records, w.beams, w.phantom, hs, w.z_psl, w.sad)
+    m = s.status == source.ST_TRANSPORT
+    oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
+                     hs[m].astype(np.uint64), w.phantom, w.seed)
+    t_h = (time.perf_counter() - t1) / n_sample
+    value = w.n_histories / (t_setup + t_h * w.n_histories)
+    return {"value": value, "unit": "histories/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"psl_build+plan of all {w.records.n} records ({t_setup:.2f} s) + {n_sample} histories "
+                      f"from history {h0} ({t_h * n_sample:.2f} s), scaled to {w.n_histories} histories"}
+
+
+# --------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--histories", type=int, default=None, help="override histories per rank (profiling only)")
+    ap.add_argument("--ref-sample", type=int, default=20_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1302_1861_b300 import capi, engine, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # cpu baseline before any heavy GPU work (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    w = inputs.config2()
+    per_rank = w.n_histories if args.histories is None else args.histories
+    # weak scaling: rank r transports histories [r*N, (r+1)*N) of a plan of world*N histories
+    n_plan = per_rank * world
+    first = rank * per_rank
+    nb = w.n_batches
+    dw = engine.upload(w)
+    stream = torch.cuda.current_stream()
+    nz, ny, nx = w.phantom.shape
+    nvox = nx * ny * nz
+    dose = torch.empty(nvox, dtype=torch.float64, device="cuda")
+    sigma = torch.empty_like(dose)
+    ledger = torch.empty(3, dtype=torch.float64, device="cuda")
+    phys = capi.physics()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    edges = engine.batch_edges(first, per_rank, nb)
+
+    tally = capi.psl_tally_create(dw.phantom, nb)       # device buffers held across steps
+
+    def step(dwx, out_dose):
+        store = capi.psl_build(dwx.params, dwx.records)
+        plan = capi.psl_plan_create(store, dwx.beams, w.sad, n_plan, w.seed)
+        capi.psl_tally_reset(tally)
+        for b in range(nb):
+            batch = capi.psl_source_batch(plan, dwx.phantom, int(edges[b]), int(edges[b + 1] - edges[b]))
+            capi.transport_run(dwx.phantom, phys, batch, tally, b)
+            batch.close()
+        _, n_total, _ = plan.info()
+        norm = engine.normalisation(n_total, per_rank, w.records.n)
+        capi.dose_readout(tally, dwx.phantom, norm, out_dose[0], out_dose[1], out_dose[2])
+        return store, plan, tally
+
+    for _ in range(args.warmup):
+        step(dw, (dose, sigma, ledger))
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    times = []
+    capi.profile(True)
+    n_launch0 = capi.kernel_launches()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(dw, (dose, sigma, ledger))
+        e1.record(stream)
+        barrier()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clk = clocks.stop()
+    launches = capi.kernel_launches() - n_launch0
+    prof = capi.profile_read()
+    capi.profile(False)
+
+    t_step = float(np.mean(times))
+    if world > 1:
+        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = per_rank * world / t_step
+
+    # ledger and isocentre uncertainty of the last step
+    lg = ledger.cpu().numpy()
+    d = dose.view(nz, ny, nx).cpu().numpy()
+    s = sigma.view(nz, ny, nx).cpu().numpy()
+    iso = np.array(w.beams[0].iso) - np.array(w.phantom.origin)
+    ic = (iso / np.array(w.phantom.voxel)).astype(int)[::-1]
+    sl = tuple(slice(c - 1, c + 2) for c in ic)
+    rel = float((s[sl] / d[sl]).mean())
+    n_1pct = per_rank * (rel / 0.01) ** 2
+
+    # e2e: pinned host records/phantom uploaded and results read back inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.records.arrays()]
+        host_mat = torch.from_numpy(np.ascontiguousarray(w.phantom.mat)).pin_memory()
+        host_rho = torch.from_numpy(np.ascontiguousarray(w.phantom.rho)).pin_memory()
+        dev = [torch.empty_like(h, device="cuda") for h in host]
+        out_h = torch.empty(2 * nvox + 3, dtype=torch.float64).pin_memory()
+        dw2 = engine.upload(w, records=dev)
+        bi = sum(h.numel() * h.element_size() for h in host) + host_mat.numel() + host_rho.numel() * 4
+        bo = out_h.numel() * 8
+        e2e_times = []
+        for it in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            barrier()
+            t0 = time.perf_counter()
+            for h, dd in zip(host, dev):
+                dd.copy_(h, non_blocking=True)
+            dw2.mat_t.copy_(host_mat, non_blocking=True)
+            dw2.rho_t.copy_(host_rho, non_blocking=True)
+            step(dw2, (dose, sigma, ledger))
+            out_h[:nvox].copy_(dose, non_blocking=True)
+            out_h[nvox:2 * nvox].copy_(sigma, non_blocking=True)
+            out_h[2 * nvox:].copy_(ledger, non_blocking=True)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                e2e_times.append(time.perf_counter() - t0)
+        te = float(np.mean(e2e_times))
+        if world > 1:
+            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": per_rank * world / te, "unit": "histories/s", "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo)}
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    peaks, pk_kind = measured_peaks()
+    name, (ms_tot, nl) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_s = ms_tot / 1e3 / max(nl, 1)
+    roof = roofline_for(name, per_launch_s, nl, args.steps, w, per_rank, peaks, pk_kind)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded 6 MV-like phase space, slab phantom)",
+                "config": {"workload": w.name, "records": w.records.n, "psl_bins": w.binning.n_bins,
+                           "phantom": "64^3 x 0.25 cm water + lung/bone slabs", "histories_per_gpu": per_rank,
+                           "batches": nb, "l2": "inputs > L2 and L2 flushed between steps",
+                           "parallelism": f"history-range shards x{world}"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+                "time_to_1pct": {"histories": n_1pct, "seconds": n_1pct / (per_rank / t_step),
+                                 "isocentre_rel_sigma_at_run": rel, "kind": "extrapolated from the run's sigma"},
+                "energy_balance": float((lg[1] + lg[2] - lg[0]) / lg[0]),
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kind):
+    """Algorithmic bytes (HBM-bound kernels) or operations per launch over the
+    measured launch duration."""
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    n = w.records.n
+    per_step = max(launches // max(steps, 1), 1)
+    if name in ("onesweep", "key", "gather", "source", "band_sort", "readout"):
+        if name == "onesweep":
+            byts = n * 16.0                          # read key+value, write key+value
+        elif name == "key":
+            byts = n * (13.0 + 4.0)                  # read x, y, e, q; write the PSL id
+        elif name == "gather":
+            byts = n * (4.0 + 25.0 + 32.0)           # permutation, SoA record, sorted record
+        elif name == "source":
+            byts = per_rank / per_step * (32.0 + 48.0)
+        else:
+            byts = 0.0
+        ach = byts / per_launch_s / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_kind": pk_kind, "launches": launches}
+    return {"kernel": name, "bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": None, "traffic": None, "per_launch_ms": per_launch_s * 1e3, "launches": launches,
+            "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+
+
+if __name__ == "__main__":
+    main()

@@ -31,7 +31,9 @@
  *     unless a field says "host".  They must stay valid until the call that
  *     uses them has completed on its stream.
  *   - Handles (psl_store_t, psl_plan_t, psl_batch_t, psl_tally_t) are owned
- *     by the library and freed with the matching *_destroy call.
+ *     by the library and freed with the matching *_destroy call.  Store, plan
+ *     and batch memory is allocated and freed stream-ordered on the stream of
+ *     the call that created the handle: destroy them before that stream.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are asynchronous on it unless stated otherwise; calls
  *     that size an allocation from device data synchronise that stream.
@@ -258,6 +260,20 @@ PSL_API void psl_store_destroy(psl_store_t *store);
 PSL_API void psl_plan_destroy(psl_plan_t *plan);
 PSL_API void psl_batch_destroy(psl_batch_t *batch);
 PSL_API void psl_tally_destroy(psl_tally_t *tally);
+
+/* Opt-in timing of the main kernels with CUDA events recorded on the stream
+ * each kernel is launched on.  psl_profile(1) clears the totals and starts
+ * recording, psl_profile(0) stops; psl_profile_read returns, for kernel
+ * index 0 <= k < PSL_NK (key, onesweep, gather, source, photon, electron,
+ * band_sort, readout), the summed device time in ms, the launches timed and
+ * the kernel's name (static string).  Reading waits for the recorded events. */
+#define PSL_NK 8
+PSL_API int psl_profile(int enable);
+PSL_API int psl_profile_read(int32_t kernel, double *total_ms, int64_t *launches, const char **name);
+
+/* Number of kernels this library has launched in this process (all threads);
+ * a diagnostic for counting the launches of a timed region. */
+PSL_API int64_t psl_kernel_launches(void);
 
 /* Text of the calling thread's last error ("" if none). */
 PSL_API const char *psl_last_error(void);

@@ -25,7 +25,7 @@ EXPORTS = (
     "psl_plan_info", "psl_plan_read", "psl_source_batch", "psl_source_trace", "psl_batch_from_particles",
     "psl_batch_info", "psl_tally_create", "psl_tally_reset", "psl_tally_read", "transport_run",
     "transport_trace", "dose_readout", "psl_store_destroy", "psl_plan_destroy", "psl_batch_destroy",
-    "psl_tally_destroy", "psl_last_error",
+    "psl_tally_destroy", "psl_last_error", "psl_kernel_launches", "psl_profile", "psl_profile_read",
 )
 
 vp = ctypes.c_void_p
@@ -76,6 +76,8 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         for name in EXPORTS:
             getattr(L, name)
+        L.psl_kernel_launches.restype = ctypes.c_int64
+        L.psl_kernel_launches.argtypes = []
         L.psl_last_error.restype = ctypes.c_char_p
         L.psl_last_error.argtypes = []
         L.psl_physics_default.restype = None
@@ -100,6 +102,8 @@ def lib():
             "transport_run": [vp, vp, vp, vp, i32, vp],
             "transport_trace": [vp, vp, vp, vp, i32, vp, vp, vp, vp],
             "dose_readout": [vp, vp, f64, vp, vp, vp, vp],
+            "psl_profile": [ctypes.c_int],
+            "psl_profile_read": [i32, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -127,6 +131,27 @@ def stream_ptr(stream=None) -> Optional[int]:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream or None
+
+
+def kernel_launches() -> int:
+    return int(lib().psl_kernel_launches())
+
+
+PSL_NK = 8
+
+
+def profile(enable: bool):
+    check(lib().psl_profile(1 if enable else 0))
+
+
+def profile_read():
+    """{kernel name: (total ms, launches)} of the timed launches."""
+    out = {}
+    for k in range(PSL_NK):
+        ms, n, name = f64(), i64(), ctypes.c_char_p()
+        check(lib().psl_profile_read(k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(name)))
+        out[name.value.decode()] = (ms.value, n.value)
+    return out
 
 
 def physics(flags: int = 0, **kw) -> Physics:

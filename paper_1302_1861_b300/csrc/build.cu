@@ -135,6 +135,7 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
     psl_store *s = new psl_store();
     s->n_records = rec->n; s->n_bins = n_bins; s->nx = prm->nx; s->ny = prm->ny; s->n_ebins = prm->n_ebins;
     s->z_psl = prm->z_psl;
+    s->stream = st;
     cudaGetDevice(&s->device);
     std::vector<float> edges;
     edges.insert(edges.end(), prm->x_edges, prm->x_edges + prm->nx + 1);
@@ -152,9 +153,9 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
     auto fail = [&](int code, const std::string &m) { rc = psl_fail(code, m); };
     do {
         cudaError_t e;
-        if ((e = cudaMalloc((void **)&s->edges, edges.size() * sizeof(float))) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if ((e = cudaMallocAsync((void **)&s->edges, edges.size() * sizeof(float), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
         if ((e = cudaMemcpyAsync(s->edges, edges.data(), edges.size() * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
-        if ((e = cudaMalloc((void **)&s->offsets, (n_bins + 1) * sizeof(int64_t))) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if ((e = cudaMallocAsync((void **)&s->offsets, (n_bins + 1) * sizeof(int64_t), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
         size_t nn = std::max<uint32_t>(n, 1);
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b) {
@@ -170,18 +171,18 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         const int sms = psl_sm_count();
         if (n == 0) {
             cudaMemsetAsync(s->offsets, 0, (n_bins + 1) * sizeof(int64_t), st);
-            cudaMalloc((void **)&s->rec, sizeof(PslRecord));
+            cudaMallocAsync((void **)&s->rec, sizeof(PslRecord), st);
             break;
         }
         int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-        k_key<<<grid, 256, edges.size() * sizeof(float), st>>>(*rec, ed, (uint32_t)n_bins, keys[0], passes, hist);
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_KEY, st, &tk_); k_key<<<grid, 256, edges.size() * sizeof(float), st>>>(*rec, ed, (uint32_t)n_bins, keys[0], passes, hist); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_KEY, st, tk_); }
         int alt = 0;
         sort_pairs_u32(keys[0], vals[0], keys[1], vals[1], n, bits, hist, true, scratch, &alt, st);
         // after an odd number of passes the result is in the alternate buffers
         uint32_t *skeys = alt ? keys[1] : keys[0], *svals = alt ? vals[1] : vals[0];
         int g2 = (int)std::min<int64_t>((int64_t)n / 256 + 1, (int64_t)sms * 8);
-        k_offsets<<<g2, 256, 0, st>>>(skeys, n, n_bins, s->offsets);
-        k_count_valid<<<1, 1, 0, st>>>(s->offsets, n_bins, nvalid_d);
+        k_offsets<<<g2, 256, 0, st>>>(skeys, n, n_bins, s->offsets); PSL_NOTE_LAUNCH();
+        k_count_valid<<<1, 1, 0, st>>>(s->offsets, n_bins, nvalid_d); PSL_NOTE_LAUNCH();
         int64_t nvalid = 0;
         uint32_t herr = 0;
         cudaMemcpyAsync(&nvalid, nvalid_d, 8, cudaMemcpyDeviceToHost, st);
@@ -189,10 +190,10 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
         if (herr & PSL_DEV_ERR_TIMEOUT) { fail(PSL_ETIMEOUT, "psl_build: look-back wait gave up"); break; }
         s->n_valid = nvalid;
-        if ((e = cudaMalloc((void **)&s->rec, std::max<int64_t>(nvalid, 1) * sizeof(PslRecord))) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if ((e = cudaMallocAsync((void **)&s->rec, std::max<int64_t>(nvalid, 1) * sizeof(PslRecord), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
         if (nvalid > 0) {
             int g3 = (int)std::min<int64_t>((nvalid + 255) / 256, (int64_t)sms * 16);
-            k_gather<<<g3, 256, 0, st>>>(*rec, svals, nvalid, s->rec);
+            { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_GATHER, st, &tk_); k_gather<<<g3, 256, 0, st>>>(*rec, svals, nvalid, s->rec); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_GATHER, st, tk_); }
         }
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
     } while (0);
@@ -233,7 +234,7 @@ extern "C" int psl_store_read(const psl_store_t *s, int64_t *offsets, int64_t *p
     if (offsets) PSL_CUDA(cudaMemcpyAsync(offsets, s->offsets, (s->n_bins + 1) * 8, cudaMemcpyDeviceToDevice, st));
     if ((perm || records) && s->n_valid > 0) {
         int g = (int)std::min<int64_t>((s->n_valid + 255) / 256, 4096);
-        k_store_read<<<g, 256, 0, st>>>(s->rec, s->n_valid, perm, records);
+        k_store_read<<<g, 256, 0, st>>>(s->rec, s->n_valid, perm, records); PSL_NOTE_LAUNCH();
         PSL_CUDA(cudaGetLastError());
     }
     return PSL_OK;
@@ -241,8 +242,8 @@ extern "C" int psl_store_read(const psl_store_t *s, int64_t *offsets, int64_t *p
 
 extern "C" void psl_store_destroy(psl_store_t *s) {
     if (!s) return;
-    if (s->rec) cudaFree(s->rec);
-    if (s->offsets) cudaFree(s->offsets);
-    if (s->edges) cudaFree(s->edges);
+    if (s->rec) cudaFreeAsync(s->rec, s->stream);
+    if (s->offsets) cudaFreeAsync(s->offsets, s->stream);
+    if (s->edges) cudaFreeAsync(s->edges, s->stream);
     delete s;
 }

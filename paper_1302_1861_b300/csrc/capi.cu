@@ -5,7 +5,14 @@
 
 #include "psl_internal.cuh"
 
+#include <atomic>
+
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void psl_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" int64_t psl_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void psl_set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -23,4 +30,88 @@ extern "C" void psl_physics_default(psl_physics_t *out) {
     out->wcc = 0.200f;
     out->wcb = 0.200f;
     out->flags = 0u;
+}
+
+// ------------------------------------------------------------------------
+// Opt-in per-kernel timing: CUDA events recorded on the launching stream
+// around the launches of the main kernels, resolved when read.
+#include <mutex>
+#include <vector>
+
+namespace {
+const char *K_NAMES[PSL_NK] = {"key", "onesweep", "gather", "source", "photon", "electron", "band_sort", "readout"};
+struct TimerState {
+    std::mutex mu;
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[PSL_NK];
+    std::vector<cudaEvent_t> pool;
+    double ms[PSL_NK] = {0};
+    long long n[PSL_NK] = {0};
+};
+TimerState &timers() {
+    static TimerState t;
+    return t;
+}
+cudaEvent_t take_event(TimerState &t) {
+    if (!t.pool.empty()) {
+        cudaEvent_t e = t.pool.back();
+        t.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+void resolve(TimerState &t) {
+    for (int k = 0; k < PSL_NK; ++k) {
+        for (auto &pr : t.pending[k]) {
+            cudaEventSynchronize(pr.second);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, pr.first, pr.second);
+            t.ms[k] += ms;
+            t.n[k] += 1;
+            t.pool.push_back(pr.first);
+            t.pool.push_back(pr.second);
+        }
+        t.pending[k].clear();
+    }
+}
+}  // namespace
+
+bool psl_timer_on() { return timers().on; }
+
+void psl_timer_begin(int k, cudaStream_t st, void **tok) {
+    TimerState &t = timers();
+    std::lock_guard<std::mutex> lk(t.mu);
+    cudaEvent_t a = take_event(t);
+    cudaEventRecord(a, st);
+    *tok = a;
+}
+
+void psl_timer_end(int k, cudaStream_t st, void *tok) {
+    TimerState &t = timers();
+    std::lock_guard<std::mutex> lk(t.mu);
+    cudaEvent_t b = take_event(t);
+    cudaEventRecord(b, st);
+    t.pending[k].push_back({(cudaEvent_t)tok, b});
+}
+
+extern "C" int psl_profile(int enable) {
+    TimerState &t = timers();
+    std::lock_guard<std::mutex> lk(t.mu);
+    resolve(t);
+    for (int k = 0; k < PSL_NK; ++k) { t.ms[k] = 0; t.n[k] = 0; }
+    t.on = enable != 0;
+    return PSL_OK;
+}
+
+extern "C" int psl_profile_read(int32_t kernel, double *total_ms, int64_t *launches, const char **name) {
+    if (kernel < 0 || kernel >= PSL_NK) return psl_fail(PSL_EINVAL, "psl_profile_read: kernel index out of range");
+    TimerState &t = timers();
+    std::lock_guard<std::mutex> lk(t.mu);
+    resolve(t);
+    if (total_ms) *total_ms = t.ms[kernel];
+    if (launches) *launches = t.n[kernel];
+    if (name) *name = K_NAMES[kernel];
+    return PSL_OK;
 }

@@ -228,7 +228,7 @@ extern "C" void psl_plan_destroy(psl_plan_t *p) {
     void *ptrs[] = {p->beams, p->e_beam, p->e_psl, p->e_start, p->e_nrec, p->e_count, p->e_offset,
                     p->group_start, p->group_seg, p->sorted, p->seg_h, p->seg_r0, p->seg_w};
     for (void *q : ptrs)
-        if (q) cudaFree(q);
+        if (q) cudaFreeAsync(q, p->stream);
     delete p;
 }
 
@@ -249,6 +249,7 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
     cudaStream_t st = as_stream(stream_);
     psl_plan *p = new psl_plan();
     p->store = store; p->n_beams = n_beams; p->sad = sad; p->n_histories = n_histories; p->seed = seed;
+    p->stream = st;
     const int nx = store->nx, ny = store->ny, ne = store->n_ebins;
     const int64_t npos = (int64_t)nx * ny;
     const int n_te = 2 * ne;
@@ -263,37 +264,37 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
         int64_t *cnt = tmp.get<int64_t>(n_beams), *ebase = tmp.get<int64_t>(n_beams + 1);
         int32_t *selpos = tmp.get<int32_t>(nflag);
         void *sscr = tmp.raw(scan_i64_scratch_bytes(std::max<int64_t>(nflag, 1 << 20)));
-        cudaError_t e = cudaMalloc((void **)&p->beams, n_beams * sizeof(BeamDev));
+        cudaError_t e = cudaMallocAsync((void **)&p->beams, n_beams * sizeof(BeamDev), st);
         if (!tmp.ok || e != cudaSuccess) { psl_plan_destroy(p); return psl_fail(PSL_ENOMEM, "psl_plan_create: allocation"); }
         cudaMemcpyAsync(bd, beams, n_beams * sizeof(psl_beam_t), cudaMemcpyHostToDevice, st);
-        k_beams<<<1, 32, 0, st>>>(bd, n_beams, sad, store->z_psl, p->beams);
-        k_roi<<<grid_for(nflag), 256, 0, st>>>(bd, n_beams, xe, ye, nx, ny, store->z_psl, sad, flags);
+        k_beams<<<1, 32, 0, st>>>(bd, n_beams, sad, store->z_psl, p->beams); PSL_NOTE_LAUNCH();
+        k_roi<<<grid_for(nflag), 256, 0, st>>>(bd, n_beams, xe, ye, nx, ny, store->z_psl, sad, flags); PSL_NOTE_LAUNCH();
         scan_i64(flags, X, nflag, sscr, st);
-        k_beam_entries<<<(n_beams + 255) / 256, 256, 0, st>>>(X, n_beams, npos, n_te, cnt);
+        k_beam_entries<<<(n_beams + 255) / 256, 256, 0, st>>>(X, n_beams, npos, n_te, cnt); PSL_NOTE_LAUNCH();
         scan_i64(cnt, ebase, n_beams, sscr, st);
-        k_selpos<<<grid_for(nflag), 256, 0, st>>>(flags, X, nflag, npos, selpos);
+        k_selpos<<<grid_for(nflag), 256, 0, st>>>(flags, X, nflag, npos, selpos); PSL_NOTE_LAUNCH();
         int64_t n_entries = 0;
         cudaMemcpyAsync(&n_entries, ebase + n_beams, 8, cudaMemcpyDeviceToHost, st);
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { psl_plan_destroy(p); return psl_fail(PSL_ECUDA, cudaGetErrorString(e)); }
         if (n_entries <= 0 || n_entries >= (1ll << 32)) { psl_plan_destroy(p); return psl_fail(PSL_EINVAL, "psl_plan_create: no PSL selected (or too many)"); }
         p->n_entries = n_entries;
         bool ok = true;
-        ok &= cudaMalloc((void **)&p->e_beam, n_entries * 4) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->e_psl, n_entries * 4) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->e_start, n_entries * 8) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->e_nrec, n_entries * 8) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->e_count, n_entries * 8) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->e_offset, n_entries * 8) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->e_beam, n_entries * 4, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->e_psl, n_entries * 4, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->e_start, n_entries * 8, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->e_nrec, n_entries * 8, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->e_count, n_entries * 8, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->e_offset, n_entries * 8, st) == cudaSuccess;
         int32_t *e_group = tmp.get<int32_t>(n_entries);
         int64_t *C = tmp.get<int64_t>(n_entries + 1), *act = tmp.get<int64_t>(n_entries), *A = tmp.get<int64_t>(n_entries + 1);
         void *sscr2 = tmp.raw(scan_i64_scratch_bytes(n_entries + 1));
         if (!ok || !tmp.ok) { psl_plan_destroy(p); return psl_fail(PSL_ENOMEM, "psl_plan_create: entry arrays"); }
         k_entries<<<grid_for(n_entries), 256, 0, st>>>(ebase, n_beams, X, selpos, npos, ne, store->offsets, n_entries,
-                                                       p->e_beam, p->e_psl, p->e_start, p->e_nrec, e_group);
+                                                       p->e_beam, p->e_psl, p->e_start, p->e_nrec, e_group); PSL_NOTE_LAUNCH();
         scan_i64(p->e_nrec, C, n_entries, sscr2, st);
         cudaMemcpyAsync(&p->n_total_psl, C + n_entries, 8, cudaMemcpyDeviceToHost, st);
         k_counts<<<grid_for(n_entries), 256, 0, st>>>(C, n_entries, (uint64_t)n_histories, p->e_beam, p->e_psl, p->e_nrec,
-                                                      seed, p->e_count, p->e_offset, act);
+                                                      seed, p->e_count, p->e_offset, act); PSL_NOTE_LAUNCH();
         scan_i64(act, A, n_entries, sscr2, st);
         int64_t n_active = 0;
         cudaMemcpyAsync(&n_active, A + n_entries, 8, cudaMemcpyDeviceToHost, st);
@@ -307,20 +308,20 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
         int64_t *ghist = tmp.get<int64_t>(n_te), *lens = tmp.get<int64_t>(n_active), *X2 = tmp.get<int64_t>(n_active + 1);
         int32_t *seg_g = tmp.get<int32_t>(n_active);
         ok = tmp.ok;
-        ok &= cudaMalloc((void **)&p->sorted, n_active * 4) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->seg_h, n_active * 8) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->seg_r0, n_active * 8) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->seg_w, n_active * 4) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->group_seg, (n_te + 1) * 8) == cudaSuccess;
-        ok &= cudaMalloc((void **)&p->group_start, (n_te + 1) * 8) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->sorted, n_active * 4, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->seg_h, n_active * 8, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->seg_r0, n_active * 8, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->seg_w, n_active * 4, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->group_seg, (n_te + 1) * 8, st) == cudaSuccess;
+        ok &= cudaMallocAsync((void **)&p->group_start, (n_te + 1) * 8, st) == cudaSuccess;
         void *sscr3 = tmp.raw(scan_i64_scratch_bytes(n_active + 1));
         if (!ok || !tmp.ok) { psl_plan_destroy(p); return psl_fail(PSL_ENOMEM, "psl_plan_create: order arrays"); }
-        k_compact<<<grid_for(n_entries), 256, 0, st>>>(act, A, p->e_count, n_entries, k0, v0);
+        k_compact<<<grid_for(n_entries), 256, 0, st>>>(act, A, p->e_count, n_entries, k0, v0); PSL_NOTE_LAUNCH();
         int alt = 0;
         sort_pairs_u32(k0, v0, k1, v1, (uint32_t)n_active, 32, nullptr, false, sort_scr, &alt, st);
         uint32_t *kk = alt ? k1 : k0, *vv = alt ? v1 : v0, *ka = alt ? k0 : k1, *va = alt ? v0 : v1;
         cudaMemsetAsync(ghist, 0, n_te * 8, st);
-        k_group_keys<<<grid_for(n_active), 256, 0, st>>>(vv, n_active, e_group, kk, ghist);
+        k_group_keys<<<grid_for(n_active), 256, 0, st>>>(vv, n_active, e_group, kk, ghist); PSL_NOTE_LAUNCH();
         int gbits = 1;
         while ((1 << gbits) < n_te) ++gbits;
         int alt2 = 0;
@@ -329,10 +330,10 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
         cudaMemcpyAsync(p->sorted, sorted_vals, n_active * 4, cudaMemcpyDeviceToDevice, st);
         scan_i64(ghist, p->group_seg, n_te, sscr3, st);
         k_segments<<<grid_for(n_active), 256, 0, st>>>(p->sorted, n_active, e_group, p->e_count, p->group_seg, lens,
-                                                       p->seg_r0, p->seg_w, seg_g);
+                                                       p->seg_r0, p->seg_w, seg_g); PSL_NOTE_LAUNCH();
         scan_i64(lens, X2, n_active, sscr3, st);
-        k_seg_h<<<grid_for(n_active), 256, 0, st>>>(X2, p->group_seg, seg_g, n_active, p->seg_h);
-        k_group_start<<<(n_te + 256) / 256, 256, 0, st>>>(X2, p->group_seg, n_te, p->group_start);
+        k_seg_h<<<grid_for(n_active), 256, 0, st>>>(X2, p->group_seg, seg_g, n_active, p->seg_h); PSL_NOTE_LAUNCH();
+        k_group_start<<<(n_te + 256) / 256, 256, 0, st>>>(X2, p->group_seg, n_te, p->group_start); PSL_NOTE_LAUNCH();
         uint32_t herr = 0;
         cudaMemcpyAsync(&herr, sort_err_word(sort_scr), 4, cudaMemcpyDeviceToHost, st);
         if ((e = cudaGetLastError()) != cudaSuccess) rc = psl_fail(PSL_ECUDA, cudaGetErrorString(e));
@@ -357,7 +358,7 @@ extern "C" int psl_plan_read(const psl_plan_t *p, int64_t *beam, int64_t *psl, i
                              void *stream_) {
     if (!p) return psl_fail(PSL_EINVAL, "psl_plan_read: null plan");
     k_plan_read<<<grid_for(p->n_entries), 256, 0, as_stream(stream_)>>>(p->n_entries, p->e_beam, p->e_psl, p->e_count,
-                                                                         p->e_offset, beam, psl, count, offset);
+                                                                         p->e_offset, beam, psl, count, offset); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());
     return PSL_OK;
 }

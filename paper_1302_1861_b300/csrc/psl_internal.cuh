@@ -22,6 +22,16 @@ int psl_fail(int code, const std::string &msg);
 
 #define PSL_CHECK_LAUNCH(name) PSL_CUDA(cudaGetLastError())
 
+// opt-in event timing of the main kernels (psl_profile)
+enum { PK_KEY = 0, PK_ONESWEEP, PK_GATHER, PK_SOURCE, PK_PHOTON, PK_ELECTRON, PK_BAND, PK_READOUT };
+bool psl_timer_on();
+void psl_timer_begin(int k, cudaStream_t st, void **tok);
+void psl_timer_end(int k, cudaStream_t st, void *tok);
+
+// host-side count of kernel launches (psl_kernel_launches)
+void psl_note_launch();
+#define PSL_NOTE_LAUNCH() psl_note_launch()
+
 static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // device error word bits
@@ -56,6 +66,7 @@ struct psl_store {
     int64_t *offsets = nullptr;      // [n_bins + 1]
     float *edges = nullptr;          // device: x_edges | y_edges | e_edges
     int device = 0;
+    cudaStream_t stream = nullptr;   // allocations are stream ordered on it
 };
 
 // Per-beam constants precomputed on the device (float32, fixed op order).
@@ -91,6 +102,7 @@ struct psl_plan {
     int64_t *seg_r0 = nullptr;       // first round of segment
     int32_t *seg_w = nullptr;        // active entries in the segment's rounds
     int64_t n_active = 0;
+    cudaStream_t stream = nullptr;
 };
 
 struct psl_batch {
@@ -102,6 +114,7 @@ struct psl_batch {
     uint32_t *counts = nullptr;      // device [2]: photons, electrons
     int64_t n_photons = 0, n_electrons = 0;
     int consumed = 0;
+    cudaStream_t stream = nullptr;
 };
 
 struct Workspace;

@@ -96,8 +96,8 @@ extern "C" int dose_readout(const psl_tally_t *t, const psl_phantom_t *ph, doubl
     unsigned long long *dep = t->ledger + 8;          // scratch slot for the deposited sum
     PSL_CUDA(cudaMemsetAsync(dep, 0, 8, st));
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((t->nvox + 255) / 256, (int64_t)psl_sm_count() * 8));
-    k_readout<<<grid, 256, 0, st>>>(t->t, t->nvox, t->n_batches, ph->rho, scale, dose, sigma, dep);
-    if (ledger) k_ledger_out<<<1, 1, 0, st>>>(t->ledger, dep, ledger);
+    { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_READOUT, st, &tk_); k_readout<<<grid, 256, 0, st>>>(t->t, t->nvox, t->n_batches, ph->rho, scale, dose, sigma, dep); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_READOUT, st, tk_); }
+    if (ledger) { k_ledger_out<<<1, 1, 0, st>>>(t->ledger, dep, ledger); PSL_NOTE_LAUNCH(); }
     PSL_CUDA(cudaGetLastError());
     return PSL_OK;
 }

@@ -201,15 +201,15 @@ int sort_pairs_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t 
     uint32_t *tile_ctr = err + 1, *lookback = err + 4;
     cudaMemsetAsync(scratch, 0, (2 * SORT_MAX_PASSES * RADIX + 4) * 4, st);
     if (hist_in) cudaMemcpyAsync(hist, hist_in, passes * RADIX * 4, cudaMemcpyDeviceToDevice, st);
-    else k_digit_hist<<<std::min<uint32_t>((n + 255) / 256, 1184), 256, 0, st>>>(keys, n, passes, hist);
-    k_digit_offsets<<<1, RADIX, 0, st>>>(hist, doffs, passes);
+    else { k_digit_hist<<<std::min<uint32_t>((n + 255) / 256, 1184), 256, 0, st>>>(keys, n, passes, hist); PSL_NOTE_LAUNCH(); }
+    k_digit_offsets<<<1, RADIX, 0, st>>>(hist, doffs, passes); PSL_NOTE_LAUNCH();
     uint32_t *kb[2] = {keys, keys_alt}, *vb[2] = {vals, vals_alt};
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         cudaMemsetAsync(tile_ctr, 0, 4, st);
         cudaMemsetAsync(lookback, 0, (size_t)n_tiles * RADIX * 4, st);
-        k_onesweep<<<n_tiles, SORT_THREADS, 0, st>>>(kb[cur], (p == 0 && vals_identity) ? nullptr : vb[cur], kb[cur ^ 1],
-                                                     vb[cur ^ 1], n, 8 * p, doffs + p * RADIX, lookback, tile_ctr, err);
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_ONESWEEP, st, &tk_); k_onesweep<<<n_tiles, SORT_THREADS, 0, st>>>(kb[cur], (p == 0 && vals_identity) ? nullptr : vb[cur], kb[cur ^ 1],
+                                                     vb[cur ^ 1], n, 8 * p, doffs + p * RADIX, lookback, tile_ctr, err); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_ONESWEEP, st, tk_); }
         cur ^= 1;
     }
     *result_in_alt = cur;
@@ -300,10 +300,10 @@ __global__ void k_zero1(int64_t *p) { *p = 0; }
 size_t scan_i64_scratch_bytes(int64_t n) { return (size_t)(std::max<int64_t>((n + SCAN_TILE - 1) / SCAN_TILE, 1)) * 8; }
 
 void scan_i64(const int64_t *in, int64_t *out, int64_t n, void *scratch, cudaStream_t st) {
-    if (n <= 0) { k_zero1<<<1, 1, 0, st>>>(out); return; }
+    if (n <= 0) { k_zero1<<<1, 1, 0, st>>>(out); PSL_NOTE_LAUNCH(); return; }
     int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     int64_t *sums = (int64_t *)scratch;
-    k_tile_sums<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, n, sums);
-    k_scan_sums<<<1, 1024, 0, st>>>(sums, tiles);
-    k_tile_scan<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, n, sums, out);
+    k_tile_sums<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, n, sums); PSL_NOTE_LAUNCH();
+    k_scan_sums<<<1, 1024, 0, st>>>(sums, tiles); PSL_NOTE_LAUNCH();
+    k_tile_scan<<<(unsigned)tiles, SCAN_THREADS, 0, st>>>(in, n, sums, out); PSL_NOTE_LAUNCH();
 }

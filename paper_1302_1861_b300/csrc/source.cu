@@ -229,8 +229,9 @@ __global__ void k_from_particles(const float *state, const int32_t *ptype, const
 static int alloc_batch(int64_t n, int64_t first, cudaStream_t st, psl_batch **out) {
     psl_batch *b = new psl_batch();
     b->n_histories = n; b->first_history = first; b->cap = std::max<int64_t>(n, 1);
-    cudaError_t e1 = cudaMalloc((void **)&b->p, b->cap * sizeof(Particle));
-    cudaError_t e2 = cudaMalloc((void **)&b->counts, 32);
+    b->stream = st;
+    cudaError_t e1 = cudaMallocAsync((void **)&b->p, b->cap * sizeof(Particle), st);
+    cudaError_t e2 = cudaMallocAsync((void **)&b->counts, 32, st);
     if (e1 != cudaSuccess || e2 != cudaSuccess) { psl_batch_destroy(b); return psl_fail(PSL_ENOMEM, "batch allocation"); }
     cudaMemsetAsync(b->counts, 0, 32, st);
     *out = b;
@@ -261,7 +262,7 @@ extern "C" int psl_source_batch(const psl_plan_t *plan, const psl_phantom_t *pha
     PlanDev P = make_plan_dev(plan, phantom);
     if (n > 0) {
         int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)psl_sm_count() * 16));
-        k_source<<<grid, 256, 0, st>>>(P, first, n, b->p, b->cap, b->counts, (unsigned long long *)(b->counts + 2));
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_SOURCE, st, &tk_); k_source<<<grid, 256, 0, st>>>(P, first, n, b->p, b->cap, b->counts, (unsigned long long *)(b->counts + 2)); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_SOURCE, st, tk_); }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { psl_batch_destroy(b); return psl_fail(PSL_ECUDA, cudaGetErrorString(e)); }
@@ -281,7 +282,7 @@ extern "C" int psl_source_trace(const psl_plan_t *plan, const psl_phantom_t *pha
     if (n == 0) return PSL_OK;
     PlanDev P = make_plan_dev(plan, phantom);
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)psl_sm_count() * 16));
-    k_source_trace<<<grid, 256, 0, as_stream(stream_)>>>(P, first, n, entry, use, rec, beam, status, state, ptype);
+    k_source_trace<<<grid, 256, 0, as_stream(stream_)>>>(P, first, n, entry, use, rec, beam, status, state, ptype); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());
     return PSL_OK;
 }
@@ -297,7 +298,7 @@ extern "C" int psl_batch_from_particles(const float *state, const int32_t *ptype
     b->seed = seed;
     if (n > 0) {
         int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
-        k_from_particles<<<grid, 256, 0, st>>>(state, ptype, pid, n, b->p, b->cap, b->counts);
+        k_from_particles<<<grid, 256, 0, st>>>(state, ptype, pid, n, b->p, b->cap, b->counts); PSL_NOTE_LAUNCH();
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { psl_batch_destroy(b); return psl_fail(PSL_ECUDA, cudaGetErrorString(e)); }
@@ -316,7 +317,7 @@ extern "C" int psl_batch_info(const psl_batch_t *b, int64_t *n_histories, int64_
 
 extern "C" void psl_batch_destroy(psl_batch_t *b) {
     if (!b) return;
-    if (b->p) cudaFree(b->p);
-    if (b->counts) cudaFree(b->counts);
+    if (b->p) cudaFreeAsync(b->p, b->stream);
+    if (b->counts) cudaFreeAsync(b->counts, b->stream);
     delete b;
 }

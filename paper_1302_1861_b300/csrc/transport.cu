@@ -613,7 +613,7 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
     PSL_CUDA(cudaMalloc((void **)&t.ph0, NT * sizeof(float4)));
     PSL_CUDA(cudaMalloc((void **)&t.ph1, NT * sizeof(float4)));
     PSL_CUDA(cudaMalloc((void **)&t.el, NT * sizeof(float4)));
-    k_tables<<<(NT + 255) / 256, 256, 0, st>>>(t.ph0, t.ph1, t.el, (double)wcc, (double)wcb);
+    k_tables<<<(NT + 255) / 256, 256, 0, st>>>(t.ph0, t.ph1, t.el, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());
     PSL_CUDA(cudaStreamSynchronize(st));
     g_tabs.push_back(t);
@@ -694,8 +694,8 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     // majorant for this phantom
     const int64_t nvox = tally->nvox;
     cudaMemsetAsync(w->rmax, 0, 2 * sizeof(int), st);
-    k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax);
-    k_majorant<<<(NT + 255) / 256, 256, 0, st>>>(tc.ph0, tc.ph1, w->rmax, w->mumax);
+    k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax); PSL_NOTE_LAUNCH();
+    k_majorant<<<(NT + 255) / 256, 256, 0, st>>>(tc.ph0, tc.ph1, w->rmax, w->mumax); PSL_NOTE_LAUNCH();
 
     Args A;
     A.nx = ph->nx; A.ny = ph->ny; A.nz = ph->nz;
@@ -717,7 +717,7 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     A.band_scale = (float)(NBANDS / log(20.0 / P.electron_cut));
 
     cudaMemsetAsync(w->cnt, 0, 128 * sizeof(uint32_t), st);
-    k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2));
+    k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2)); PSL_NOTE_LAUNCH();
 
     const int sms = psl_sm_count();
     const int grid_t = sms * 4;                     // persistent transport grid
@@ -727,23 +727,23 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     int pc = 0, ec = 0;                             // index of the "current" buffers
 
     auto band_sort = [&](const Particle *a, uint32_t na, const Particle *bq, const uint32_t *nb, uint32_t capb) {
-        k_band_count<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, hist);
-        k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS);
-        k_band_scatter<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s);
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_BAND, st, &tk_); k_band_count<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, hist); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_BAND, st, tk_); }
+        k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_BAND, st, &tk_); k_band_scatter<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_BAND, st, tk_); }
     };
     auto photon_pass = [&](const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
         Args a2 = A;
         a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
         a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
         cudaMemsetAsync(head, 0, 4, st);
-        k_photon<<<grid_t, 256, 0, st>>>(a2, src, nptr, nfix, cap, head);
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_PHOTON, st, &tk_); k_photon<<<grid_t, 256, 0, st>>>(a2, src, nptr, nfix, cap, head); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_PHOTON, st, tk_); }
     };
     auto electron_pass = [&]() {
         Args a2 = A;
         a2.e_out = Queue{w->E[ec ^ 1], cE[ec ^ 1], w->cap_e};
         a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
         cudaMemsetAsync(head + 1, 0, 4, st);
-        k_electron<<<grid_t, 256, 0, st>>>(a2, w->S, cS, w->cap_s, head + 1);
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_ELECTRON, st, &tk_); k_electron<<<grid_t, 256, 0, st>>>(a2, w->S, cS, w->cap_s, head + 1); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_ELECTRON, st, tk_); }
     };
 
     const int64_t cap = batch->cap;
