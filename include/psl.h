@@ -151,6 +151,28 @@ PSL_API void psl_physics_default(psl_physics_t *out);
  * PSL_ETIMEOUT (a look-back wait of the sort gave up). Synchronises stream. */
 PSL_API int psl_build(const psl_params_t *params, const psl_records_t *records, psl_store_t **out, void *stream);
 
+/* psl_build for callers that cannot allocate device memory: code running
+ * inside another runtime's memory pool, under a fixed device-memory budget, or
+ * in a process that must not call cudaMalloc after start-up.  The paper has
+ * no counterpart; it is the same PSL sort written into caller arrays.
+ * Scratch lives in one fixed device array of about 17 MB that every GPU that
+ * loads this library holds until the process exits.  Limits: at most
+ * PSL_STATIC_MAX_RECORDS records and PSL_STATIC_MAX_EDGES bin edges
+ * (nx+1 + ny+1 + n_ebins+1); larger inputs return PSL_EINVAL with the limit
+ * in psl_last_error.  Outputs (device, caller-owned): offsets [n_bins+1]
+ * int64 and sorted [n x 8] float32 (16-byte aligned) in the psl_store_read
+ * record layout (the
+ * first *n_valid rows are written); *n_valid (host) receives the records
+ * kept.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Synchronises stream. */
+#define PSL_STATIC_MAX_RECORDS (1 << 20)
+#define PSL_STATIC_MAX_EDGES 4096
+PSL_API int psl_build_static(const psl_params_t *params, const psl_records_t *records, int64_t *offsets,
+                             float *sorted, int64_t *n_valid, void *stream);
+
 /* Sizes of a store (host outputs). */
 PSL_API int psl_store_info(const psl_store_t *store, int64_t *n_records, int64_t *n_valid, int64_t *n_bins);
 

@@ -26,7 +26,9 @@ EXPORTS = (
     "psl_batch_info", "psl_tally_create", "psl_tally_reset", "psl_tally_read", "transport_run",
     "transport_trace", "dose_readout", "psl_store_destroy", "psl_plan_destroy", "psl_batch_destroy",
     "psl_tally_destroy", "psl_last_error", "psl_kernel_launches", "psl_profile", "psl_profile_read",
+    "psl_build_static",
 )
+STATIC_MAX_RECORDS = 1 << 20
 
 vp = ctypes.c_void_p
 f32, i32, i64, u32, u64, f64 = (ctypes.c_float, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
@@ -87,6 +89,7 @@ def lib():
             getattr(L, name).argtypes = [vp]
         sig = {
             "psl_build": [vp, vp, vp, vp],
+            "psl_build_static": [vp, vp, vp, vp, vp, vp],
             "psl_store_info": [vp, vp, vp, vp],
             "psl_store_read": [vp, vp, vp, vp, vp],
             "psl_plan_create": [vp, vp, i32, f32, i64, u64, vp, vp],
@@ -221,6 +224,15 @@ def psl_build(params: Params, records: Records, stream=None) -> Store:
     h = _out_handle()
     check(lib().psl_build(ctypes.byref(params), ctypes.byref(records), ctypes.byref(h), stream_ptr(stream)))
     return Store(h.value)
+
+
+def psl_build_static(params: Params, records: Records, offsets, sorted_records, stream=None) -> int:
+    """PSL build into caller arrays with no device allocation (see psl.h);
+    returns the number of records kept."""
+    nv = i64()
+    check(lib().psl_build_static(ctypes.byref(params), ctypes.byref(records), ptr(offsets), ptr(sorted_records),
+                                 ctypes.byref(nv), stream_ptr(stream)))
+    return nv.value
 
 
 def psl_store_read(store: Store, offsets=None, perm=None, records=None, stream=None):

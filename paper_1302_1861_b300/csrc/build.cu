@@ -16,6 +16,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "psl_internal.cuh"
@@ -246,4 +248,131 @@ extern "C" void psl_store_destroy(psl_store_t *s) {
     if (s->offsets) cudaFreeAsync(s->offsets, s->stream);
     if (s->edges) cudaFreeAsync(s->edges, s->stream);
     delete s;
+}
+
+// --------------------------------------------------------------------------
+// psl_build_static: the same PSL build for callers that cannot allocate
+// device memory.  All scratch (ids, values, digit histograms, look-back
+// table, edges, the kept-record count) lives in one file-scope device array
+// of fixed size; the caller passes the inputs and the output arrays.
+// --------------------------------------------------------------------------
+namespace {
+
+constexpr size_t ST_MAX_N = PSL_STATIC_MAX_RECORDS;
+constexpr size_t ST_ROUND = 64;                                   // 256 bytes in 4-byte words
+constexpr size_t st_round(size_t w) { return (w + ST_ROUND - 1) / ST_ROUND * ST_ROUND; }
+constexpr size_t ST_TILES = (ST_MAX_N + 4095) / 4096;
+// word offsets of the regions
+constexpr size_t ST_KEYS0 = 0;
+constexpr size_t ST_KEYS1 = ST_KEYS0 + ST_MAX_N;
+constexpr size_t ST_VALS0 = ST_KEYS1 + ST_MAX_N;
+constexpr size_t ST_VALS1 = ST_VALS0 + ST_MAX_N;
+constexpr size_t ST_HIST = ST_VALS1 + ST_MAX_N;                  // digit histograms + kept count (int64)
+constexpr size_t ST_EDGES = ST_HIST + st_round(MAX_PASSES * RADIX + 4);
+constexpr size_t ST_SORT = ST_EDGES + st_round(PSL_STATIC_MAX_EDGES);
+constexpr size_t ST_SORT_WORDS = st_round(2 * SORT_MAX_PASSES * RADIX + 4 + ST_TILES * RADIX);
+constexpr size_t ST_WORDS = ST_SORT + ST_SORT_WORDS;
+
+// Held by every device that loads the library, until the process exits.
+static __device__ __align__(256) uint32_t g_build_scratch[ST_WORDS];
+
+std::mutex g_static_mu;
+uint32_t *g_static_addr[256] = {nullptr};
+
+// Device address of g_build_scratch on the current device (looked up once per
+// device; host code cannot use the symbol itself as an address).
+int static_scratch(uint32_t **out) {
+    int dev = 0;
+    PSL_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return psl_fail(PSL_EINVAL, "psl_build_static: device index out of range");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_build_scratch);
+        if (e != cudaSuccess)
+            return psl_fail(PSL_ECUDA, std::string("psl_build_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_static_addr[dev] = (uint32_t *)p;
+    }
+    *out = g_static_addr[dev];
+    return PSL_OK;
+}
+
+}  // namespace
+
+extern "C" int psl_build_static(const psl_params_t *prm, const psl_records_t *rec, int64_t *offsets, float *sorted,
+                                int64_t *n_valid, void *stream_) {
+    if (!prm || !rec || !offsets || !sorted || !n_valid) return psl_fail(PSL_EINVAL, "psl_build_static: null argument");
+    if (prm->apr_copies != 1) return psl_fail(PSL_EINVAL, "psl_build_static: apr_copies must be 1");
+    if (prm->nx <= 0 || prm->ny <= 0 || prm->n_ebins <= 0) return psl_fail(PSL_EINVAL, "psl_build_static: bad bin counts");
+    const int64_t n_bins = 2ll * prm->n_ebins * prm->nx * prm->ny;
+    if (n_bins >= (1ll << 31) - 1) return psl_fail(PSL_EINVAL, "psl_build_static: too many bins");
+    if (rec->n < 0) return psl_fail(PSL_EINVAL, "psl_build_static: negative record count");
+    if (rec->n > (int64_t)PSL_STATIC_MAX_RECORDS)
+        return psl_fail(PSL_EINVAL, "psl_build_static: " + std::to_string(rec->n) + " records exceed the static limit of " +
+                                        std::to_string((long long)PSL_STATIC_MAX_RECORDS) + "; use psl_build");
+    const int64_t n_edges = (int64_t)prm->nx + prm->ny + prm->n_ebins + 3;
+    if (n_edges > PSL_STATIC_MAX_EDGES)
+        return psl_fail(PSL_EINVAL, "psl_build_static: " + std::to_string(n_edges) + " bin edges exceed the static limit of " +
+                                        std::to_string(PSL_STATIC_MAX_EDGES));
+    if (!prm->x_edges || !prm->y_edges || !prm->e_edges) return psl_fail(PSL_EINVAL, "psl_build_static: null edges");
+    for (int i = 0; i < prm->nx; ++i)
+        if (!(prm->x_edges[i] < prm->x_edges[i + 1])) return psl_fail(PSL_EINVAL, "psl_build_static: x edges not ascending");
+    for (int i = 0; i < prm->ny; ++i)
+        if (!(prm->y_edges[i] < prm->y_edges[i + 1])) return psl_fail(PSL_EINVAL, "psl_build_static: y edges not ascending");
+    for (int i = 0; i < prm->n_ebins; ++i)
+        if (!(prm->e_edges[i] < prm->e_edges[i + 1])) return psl_fail(PSL_EINVAL, "psl_build_static: e edges not ascending");
+    if (rec->n > 0 && (!rec->x || !rec->y || !rec->u || !rec->v || !rec->e || !rec->wt || !rec->q))
+        return psl_fail(PSL_EINVAL, "psl_build_static: null record array");
+
+    uint32_t *base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream_);
+    const uint32_t n = (uint32_t)rec->n;
+    uint32_t *keys0 = base + ST_KEYS0, *keys1 = base + ST_KEYS1, *vals0 = base + ST_VALS0, *vals1 = base + ST_VALS1;
+    uint32_t *hist = base + ST_HIST;
+    int64_t *nvalid_d = reinterpret_cast<int64_t *>(hist + MAX_PASSES * RADIX);
+    float *edges = reinterpret_cast<float *>(base + ST_EDGES);
+    void *sort_scratch = base + ST_SORT;
+
+    // edges: x | y | e, copied from the host arrays (pageable copies, no allocation)
+    PSL_CUDA(cudaMemcpyAsync(edges, prm->x_edges, (prm->nx + 1) * sizeof(float), cudaMemcpyHostToDevice, st));
+    PSL_CUDA(cudaMemcpyAsync(edges + prm->nx + 1, prm->y_edges, (prm->ny + 1) * sizeof(float), cudaMemcpyHostToDevice, st));
+    PSL_CUDA(cudaMemcpyAsync(edges + prm->nx + prm->ny + 2, prm->e_edges, (prm->n_ebins + 1) * sizeof(float),
+                             cudaMemcpyHostToDevice, st));
+    // the array keeps the previous call's contents: clear what must start at zero
+    PSL_CUDA(cudaMemsetAsync(hist, 0, (MAX_PASSES * RADIX + 4) * sizeof(uint32_t), st));
+    if (n == 0) {
+        PSL_CUDA(cudaMemsetAsync(offsets, 0, (n_bins + 1) * sizeof(int64_t), st));
+        PSL_CUDA(cudaStreamSynchronize(st));
+        *n_valid = 0;
+        return PSL_OK;
+    }
+    int bits = 1;
+    while ((1ll << bits) <= n_bins) ++bits;
+    const int passes = (bits + 7) / 8;
+    Edges ed{prm->nx, prm->ny, prm->n_ebins, edges, edges + prm->nx + 1, edges + prm->nx + prm->ny + 2};
+    const int sms = psl_sm_count();
+    int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+    k_key<<<grid, 256, n_edges * sizeof(float), st>>>(*rec, ed, (uint32_t)n_bins, keys0, passes, hist); PSL_NOTE_LAUNCH();
+    int alt = 0;
+    sort_pairs_u32(keys0, vals0, keys1, vals1, n, bits, hist, true, sort_scratch, &alt, st);
+    uint32_t *skeys = alt ? keys1 : keys0, *svals = alt ? vals1 : vals0;
+    int g2 = (int)std::min<int64_t>((int64_t)n / 256 + 1, (int64_t)sms * 8);
+    k_offsets<<<g2, 256, 0, st>>>(skeys, n, n_bins, offsets); PSL_NOTE_LAUNCH();
+    k_count_valid<<<1, 1, 0, st>>>(offsets, n_bins, nvalid_d); PSL_NOTE_LAUNCH();
+    int64_t nvalid = 0;
+    uint32_t herr = 0;
+    PSL_CUDA(cudaMemcpyAsync(&nvalid, nvalid_d, 8, cudaMemcpyDeviceToHost, st));
+    PSL_CUDA(cudaMemcpyAsync(&herr, sort_err_word(sort_scratch), 4, cudaMemcpyDeviceToHost, st));
+    PSL_CUDA(cudaStreamSynchronize(st));
+    if (herr & PSL_DEV_ERR_TIMEOUT) return psl_fail(PSL_ETIMEOUT, "psl_build_static: look-back wait gave up");
+    if (nvalid > 0) {
+        int g3 = (int)std::min<int64_t>((nvalid + 255) / 256, (int64_t)sms * 16);
+        k_gather<<<g3, 256, 0, st>>>(*rec, svals, nvalid, reinterpret_cast<PslRecord *>(sorted)); PSL_NOTE_LAUNCH();
+    }
+    PSL_CUDA(cudaGetLastError());
+    PSL_CUDA(cudaStreamSynchronize(st));
+    *n_valid = nvalid;
+    return PSL_OK;
 }
