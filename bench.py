@@ -218,7 +218,6 @@ def main():
     ledger = torch.empty(3, dtype=torch.float64, device="cuda")
     phys = capi.physics()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    edges = engine.batch_edges(first, per_rank, nb)
 
     tally = capi.psl_tally_create(dw.phantom, nb)       # device buffers held across steps
 
@@ -227,7 +226,8 @@ def main():
         plan = capi.psl_plan_create(store, dwx.beams, w.sad, n_plan, w.seed)
         capi.psl_tally_reset(tally)
         for b in range(nb):
-            batch = capi.psl_source_batch(plan, dwx.phantom, int(edges[b]), int(edges[b + 1] - edges[b]))
+            f0, cnt, stride = engine.batch_histories(first, per_rank, nb, b)
+            batch = capi.psl_source_batch(plan, dwx.phantom, f0, cnt, stride)
             capi.transport_run(dwx.phantom, phys, batch, tally, b)
             batch.close()
         _, n_total, _ = plan.info()
@@ -273,6 +273,10 @@ def main():
 
     # ledger and isocentre uncertainty of the last step
     lg = ledger.cpu().numpy()
+    raw = torch.empty(12, dtype=torch.int64, device="cuda")
+    capi.psl_tally_read(tally, None, raw)
+    counts = raw.cpu().numpy()            # event and atomic counters of the last step
+    atom_peak = capi.atomic_peak(nvox, 1 << 30)
     d = dose.view(nz, ny, nx).cpu().numpy()
     s = sigma.view(nz, ny, nx).cpu().numpy()
     iso = np.array(w.beams[0].iso) - np.array(w.phantom.origin)
@@ -320,7 +324,15 @@ def main():
     peaks, pk_kind = measured_peaks()
     name, (ms_tot, nl) = max(prof.items(), key=lambda kv: kv[1][0])
     per_launch_s = ms_tot / 1e3 / max(nl, 1)
-    roof = roofline_for(name, per_launch_s, nl, args.steps, w, per_rank, peaks, pk_kind)
+    roof = roofline_for(name, per_launch_s, nl, args.steps, w, per_rank, peaks, pk_kind, counts)
+    ms_e = prof["electron"][0] / args.steps / 1e3
+    ms_p = prof["photon"][0] / args.steps / 1e3
+    transport = {"electron_steps": int(counts[6]), "woodcock_steps": int(counts[10]),
+                 "photon_interactions": int(counts[3] + counts[4] + counts[5]),
+                 "tally_atomics": {"photon": int(counts[8]), "electron": int(counts[9])},
+                 "atomics_per_s": {"photon": counts[8] / ms_p, "electron": counts[9] / ms_e},
+                 "atomic_peak_per_s": atom_peak, "atomic_peak_kind": "measured: psl_atomic_peak, int64 adds into "
+                                                                    f"{nvox} cells"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
@@ -335,13 +347,23 @@ def main():
                 "time_to_1pct": {"histories": n_1pct, "seconds": n_1pct / (per_rank / t_step),
                                  "isocentre_rel_sigma_at_run": rel, "kind": "extrapolated from the run's sigma"},
                 "energy_balance": float((lg[1] + lg[2] - lg[0]) / lg[0]),
+                "transport": transport,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
 
 
-def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kind):
+# Thread instructions per event of the transport kernels, measured with ncu
+# (smsp__thread_inst_executed.sum over all launches of a run / events of the
+# run); see profiles/.  None until measured for the current kernels.
+THREAD_INST_PER_ELECTRON_STEP = None
+THREAD_INST_PER_WOODCOCK_STEP = None
+# issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
+THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
+
+
+def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kind, counts):
     """Algorithmic bytes (HBM-bound kernels) or operations per launch over the
     measured launch duration."""
     hbm = float(peaks.get("hbm_gbs", 6400.0))
@@ -361,9 +383,18 @@ def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kin
         ach = byts / per_launch_s / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": None, "peak_kind": pk_kind, "launches": launches}
-    return {"kernel": name, "bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": None, "traffic": None, "per_launch_ms": per_launch_s * 1e3, "launches": launches,
-            "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+    # transport: events per second against the instruction-issue speed of light
+    per_step = max(launches // max(steps, 1), 1)
+    if name == "electron":
+        events, ipe = counts[6], THREAD_INST_PER_ELECTRON_STEP
+    else:
+        events, ipe = counts[10], THREAD_INST_PER_WOODCOCK_STEP
+    ach = events / per_step / per_launch_s / 1e9
+    peak = THREAD_INST_PEAK / ipe / 1e9 if ipe else None
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gevents/s",
+            "frac": ach / peak if peak else None, "traffic": None, "per_launch_ms": per_launch_s * 1e3,
+            "launches": launches, "events": "electron steps" if name == "electron" else "Woodcock steps",
+            "peak_kind": "derived: 148 SMs x 4 issue/clk x 32 lanes x 2.032 GHz / thread instructions per event"}
 
 
 if __name__ == "__main__":

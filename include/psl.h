@@ -203,8 +203,11 @@ PSL_API int psl_plan_info(const psl_plan_t *plan, int64_t *n_entries, int64_t *n
 PSL_API int psl_plan_read(const psl_plan_t *plan, int64_t *beam, int64_t *psl, int64_t *count, int64_t *offset,
                   void *stream);
 
-/* Sec. 2.2, 2.3.3, 2.4.  Source stage for histories [first, first+n) of the
- * plan.  History h is mapped to (entry, read number k): energy divisions in
+/* Sec. 2.2, 2.3.3, 2.4.  Source stage for histories h = first + i * stride,
+ * 0 <= i < n, of the plan (stride >= 1; the last must be < the plan's
+ * histories).  Independent batches for the uncertainty estimate of Sec. 2.3.3
+ * take first = b, stride = N_b, so that every batch samples every energy
+ * division.  History h is mapped to (entry, read number k): energy divisions in
  * order, photons before electrons inside one; within that group, round r
  * reads one particle from every entry still owed more than r histories,
  * entries visited in order of decreasing count (ties: entry order).  The
@@ -219,16 +222,16 @@ PSL_API int psl_plan_read(const psl_plan_t *plan, int64_t *beam, int64_t *psl, i
  * phantom box.  The batch holds the particles for transport_run; the phantom
  * is read for its box only.  Synchronises stream. */
 PSL_API int psl_source_batch(const psl_plan_t *plan, const psl_phantom_t *phantom, int64_t first_history,
-                     int64_t n_histories, psl_batch_t **out, void *stream);
+                     int64_t n_histories, int64_t stride, psl_batch_t **out, void *stream);
 
-/* The source stage of histories [first, first+n) written out per history
+/* The source stage of histories first + i * stride, 0 <= i < n, written out per history
  * (device outputs, NULL to skip): entry, read number k, sorted record
  * index, beam, status (PSL_SRC_*), state (n x 8 float32: x y z u v w e wt,
  * phantom-local entry point, only for PSL_SRC_TRANSPORT), particle type
  * (0 photon, 1 electron, 2 positron). */
 PSL_API int psl_source_trace(const psl_plan_t *plan, const psl_phantom_t *phantom, int64_t first_history,
-                     int64_t n_histories, int64_t *entry, int64_t *use, int64_t *rec, int32_t *beam,
-                     int8_t *status, float *state, int32_t *ptype, void *stream);
+                     int64_t n_histories, int64_t stride, int64_t *entry, int64_t *use, int64_t *rec,
+                     int32_t *beam, int8_t *status, float *state, int32_t *ptype, void *stream);
 
 /* A batch made from caller particles (device arrays, n each): state n x 8
  * float32 (x y z u v w e wt, phantom-local), type (0/1/2) and particle id;
@@ -240,14 +243,16 @@ PSL_API int psl_batch_from_particles(const float *state, const int32_t *ptype, c
 /* Histories (or particles) in a batch and the fixed-point energy they emit. */
 PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64_t *n_photons, int64_t *n_electrons);
 
-/* One int64 tally of nz*ny*nx voxels per batch, plus an 8-slot ledger:
- * emitted, escaped, deposited (fixed point, 2^-32 MeV per unit weight),
- * Compton, photoelectric and pair events, electron steps, errors. */
+/* One int64 tally of nz*ny*nx voxels per batch, plus a 12-slot ledger:
+ * 0 emitted, 1 escaped, 2 deposited (fixed point, 2^-32 MeV per unit
+ * weight), 3 Compton, 4 photoelectric and 5 pair events, 6 electron steps,
+ * 7 errors, 8 tally atomics issued by photon passes, 9 by electron passes,
+ * 10 Woodcock (photon) steps, 11 reserved. */
 PSL_API int psl_tally_create(const psl_phantom_t *phantom, int32_t n_batches, psl_tally_t **out);
 PSL_API int psl_tally_reset(psl_tally_t *tally, void *stream);
 
 /* Copy raw tallies (device int64 [n_batches * nvox]) and ledger (device int64
- * [8]) out; NULL to skip. */
+ * [12]) out; NULL to skip. */
 PSL_API int psl_tally_read(const psl_tally_t *tally, int64_t *tallies, int64_t *ledger, void *stream);
 
 /* Sec. 2.3.3.  Transport every particle of the batch and its secondaries
@@ -292,6 +297,12 @@ PSL_API void psl_tally_destroy(psl_tally_t *tally);
 #define PSL_NK 8
 PSL_API int psl_profile(int enable);
 PSL_API int psl_profile_read(int32_t kernel, double *total_ms, int64_t *launches, const char **name);
+
+/* Diagnostic: measured throughput (updates/s) of int64 atomic adds into an
+ * array of n_cells int64 counters (pseudo-random cells, as dose deposits
+ * land), used as the peak of the transport kernels' tally roofline.
+ * Allocates and frees the cells on `stream`; synchronises it. */
+PSL_API int psl_atomic_peak(int64_t n_cells, int64_t n_updates, double *updates_per_s, void *stream);
 
 /* Number of kernels this library has launched in this process (all threads);
  * a diagnostic for counting the launches of a timed region. */

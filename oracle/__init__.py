@@ -84,9 +84,10 @@ def run_plan(w, n_histories=None, first=0, n_batches=None, nthreads=0, flags=0,
     nz, ny, nx = w.phantom.shape
     tallies = np.zeros((nb, nz, ny, nx), np.int64)
     ledger = np.zeros(8, np.int64)
-    edges = np.linspace(first, first + n_h, nb + 1).astype(np.int64)
     for b in range(nb):
-        h = np.arange(edges[b], edges[b + 1], dtype=np.int64)
+        # batch b: every nb-th history, so that each batch samples every
+        # energy division (independent batches, Sec. 2.3.3)
+        h = np.arange(first + b, first + n_h, nb, dtype=np.int64)
         s = source.source(plan, store, w.records, w.beams, w.phantom, h, w.z_psl, w.sad)
         ledger[L_EMITTED] += s.emitted_fp
         ledger[L_ESCAPED] += s.missed_fp

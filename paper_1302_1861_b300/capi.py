@@ -14,7 +14,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpsl_b300.so")
+LIB_PATH = os.environ.get("PSL_B300_LIB") or os.path.join(HERE, "libpsl_b300.so")
 
 PSL_OK, PSL_EINVAL, PSL_ENOMEM, PSL_ECUDA, PSL_ETIMEOUT, PSL_EOVERFLOW = 0, -1, -2, -3, -4, -5
 PHYS_LOCAL_SECONDARIES, PHYS_FIRST_INTERACTION, PHYS_NO_MSC, PHYS_NO_HARD = 1, 2, 4, 8
@@ -26,7 +26,7 @@ EXPORTS = (
     "psl_batch_info", "psl_tally_create", "psl_tally_reset", "psl_tally_read", "transport_run",
     "transport_trace", "dose_readout", "psl_store_destroy", "psl_plan_destroy", "psl_batch_destroy",
     "psl_tally_destroy", "psl_last_error", "psl_kernel_launches", "psl_profile", "psl_profile_read",
-    "psl_build_static",
+    "psl_build_static", "psl_atomic_peak",
 )
 STATIC_MAX_RECORDS = 1 << 20
 
@@ -95,8 +95,8 @@ def lib():
             "psl_plan_create": [vp, vp, i32, f32, i64, u64, vp, vp],
             "psl_plan_info": [vp, vp, vp, vp],
             "psl_plan_read": [vp, vp, vp, vp, vp, vp],
-            "psl_source_batch": [vp, vp, i64, i64, vp, vp],
-            "psl_source_trace": [vp, vp, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp],
+            "psl_source_batch": [vp, vp, i64, i64, i64, vp, vp],
+            "psl_source_trace": [vp, vp, i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp],
             "psl_batch_from_particles": [vp, vp, vp, i64, u64, vp, vp],
             "psl_batch_info": [vp, vp, vp, vp],
             "psl_tally_create": [vp, i32, vp],
@@ -106,6 +106,7 @@ def lib():
             "transport_trace": [vp, vp, vp, vp, i32, vp, vp, vp, vp],
             "dose_readout": [vp, vp, f64, vp, vp, vp, vp],
             "psl_profile": [ctypes.c_int],
+            "psl_atomic_peak": [i64, i64, vp, vp],
             "psl_profile_read": [i32, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -141,6 +142,13 @@ def kernel_launches() -> int:
 
 
 PSL_NK = 8
+
+
+def atomic_peak(n_cells: int, n_updates: int = 1 << 30, stream=None) -> float:
+    """Measured int64 atomic-add throughput (updates/s) into n_cells counters."""
+    v = f64()
+    check(lib().psl_atomic_peak(int(n_cells), int(n_updates), ctypes.byref(v), stream_ptr(stream)))
+    return v.value
 
 
 def profile(enable: bool):
@@ -252,16 +260,16 @@ def psl_plan_read(plan: Plan, beam=None, psl=None, count=None, offset=None, stre
     check(lib().psl_plan_read(plan.h, ptr(beam), ptr(psl), ptr(count), ptr(offset), stream_ptr(stream)))
 
 
-def psl_source_batch(plan: Plan, phantom: Phantom, first: int, n: int, stream=None) -> Batch:
+def psl_source_batch(plan: Plan, phantom: Phantom, first: int, n: int, stride: int = 1, stream=None) -> Batch:
     h = _out_handle()
-    check(lib().psl_source_batch(plan.h, ctypes.byref(phantom), int(first), int(n), ctypes.byref(h),
+    check(lib().psl_source_batch(plan.h, ctypes.byref(phantom), int(first), int(n), int(stride), ctypes.byref(h),
                                  stream_ptr(stream)))
     return Batch(h.value)
 
 
 def psl_source_trace(plan: Plan, phantom: Phantom, first: int, n: int, entry=None, use=None, rec=None,
-                     beam=None, status=None, state=None, ptype=None, stream=None):
-    check(lib().psl_source_trace(plan.h, ctypes.byref(phantom), int(first), int(n), ptr(entry), ptr(use),
+                     beam=None, status=None, state=None, ptype=None, stride: int = 1, stream=None):
+    check(lib().psl_source_trace(plan.h, ctypes.byref(phantom), int(first), int(n), int(stride), ptr(entry), ptr(use),
                                  ptr(rec), ptr(beam), ptr(status), ptr(state), ptr(ptype), stream_ptr(stream)))
 
 

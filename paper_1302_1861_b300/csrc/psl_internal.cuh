@@ -158,16 +158,14 @@ __host__ __device__ __forceinline__ u32x4 philox10(uint32_t c0, uint32_t c1, uin
 }
 
 // Per-particle random stream: draw d uses word d%4 of block d/4 of
-// Philox(key = seed; counter = (d/4, TAG_PARTICLE, pid)).
+// Philox(key = seed (k0, k1); counter = (d/4, TAG_PARTICLE, pid (p0, p1))).
+// Only the draw counter and the current block live in registers; the key and
+// the particle id are passed in.
 struct Rng {
-    uint32_t k0, k1, p0, p1;
     uint32_t draw;
     u32x4 blk;
-    __device__ __forceinline__ void init(uint64_t seed, uint32_t pid_lo, uint32_t pid_hi) {
-        k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32); p0 = pid_lo; p1 = pid_hi; draw = 0;
-    }
     // ((r >> 9) + 0.5) * 2^-23: 24 significant bits, exact in float
-    __device__ __forceinline__ float uniform() {
+    __device__ __forceinline__ float next(uint32_t k0, uint32_t k1, uint32_t p0, uint32_t p1) {
         uint32_t w = draw & 3u;
         if (w == 0) blk = philox10(draw >> 2, TAG_PARTICLE, p0, p1, k0, k1);
         uint32_t r = w == 0 ? blk.a : (w == 1 ? blk.b : (w == 2 ? blk.c : blk.d));

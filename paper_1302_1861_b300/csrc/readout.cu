@@ -81,7 +81,7 @@ extern "C" int psl_tally_read(const psl_tally_t *t, int64_t *tallies, int64_t *l
     if (!t) return psl_fail(PSL_EINVAL, "psl_tally_read: null tally");
     cudaStream_t st = as_stream(stream_);
     if (tallies) PSL_CUDA(cudaMemcpyAsync(tallies, t->t, (size_t)t->n_batches * t->nvox * 8, cudaMemcpyDeviceToDevice, st));
-    if (ledger) PSL_CUDA(cudaMemcpyAsync(ledger, t->ledger, 8 * 8, cudaMemcpyDeviceToDevice, st));
+    if (ledger) PSL_CUDA(cudaMemcpyAsync(ledger, t->ledger, 12 * 8, cudaMemcpyDeviceToDevice, st));
     return PSL_OK;
 }
 
@@ -93,7 +93,7 @@ extern "C" int dose_readout(const psl_tally_t *t, const psl_phantom_t *ph, doubl
     // Gy per fixed-point unit at unit density: 2^-32 MeV * J/MeV / (V cm^3 * 1e-3 kg/g)
     const double vol = (double)ph->vx * (double)ph->vy * (double)ph->vz;
     const double scale = norm * (1.0 / 4294967296.0) * 1.602176634e-13 / (vol * 1e-3);
-    unsigned long long *dep = t->ledger + 8;          // scratch slot for the deposited sum
+    unsigned long long *dep = t->ledger + 12;         // scratch slot for the deposited sum
     PSL_CUDA(cudaMemsetAsync(dep, 0, 8, st));
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((t->nvox + 255) / 256, (int64_t)psl_sm_count() * 8));
     { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_READOUT, st, &tk_); k_readout<<<grid, 256, 0, st>>>(t->t, t->nvox, t->n_batches, ph->rho, scale, dose, sigma, dep); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_READOUT, st, tk_); }
@@ -108,4 +108,43 @@ extern "C" void psl_tally_destroy(psl_tally_t *t) {
     if (t->ledger) cudaFree(t->ledger);
     if (t->ws) workspace_free(t->ws);
     delete t;
+}
+
+// --------------------------------------------------------------------------
+// Diagnostic: throughput of int64 atomic adds into an L2-resident array, the
+// operation every dose deposit performs.  Each thread adds 1 to pseudo-random
+// cells (a multiplicative hash of its update index), return values unused.
+namespace {
+__global__ void __launch_bounds__(256) k_atomic_peak(unsigned long long *cells, uint64_t n_cells, uint64_t n_updates) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_updates; i += stride) {
+        uint64_t h = (i + 1) * 0x9E3779B97F4A7C15ull;
+        atomicAdd(cells + (h >> 32) % n_cells, 1ull);
+    }
+}
+}  // namespace
+
+extern "C" int psl_atomic_peak(int64_t n_cells, int64_t n_updates, double *updates_per_s, void *stream_) {
+    if (n_cells <= 0 || n_updates <= 0 || !updates_per_s) return psl_fail(PSL_EINVAL, "psl_atomic_peak: bad argument");
+    cudaStream_t st = as_stream(stream_);
+    unsigned long long *cells = nullptr;
+    PSL_CUDA(cudaMallocAsync((void **)&cells, n_cells * 8, st));
+    PSL_CUDA(cudaMemsetAsync(cells, 0, n_cells * 8, st));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int grid = psl_sm_count() * 8;
+    k_atomic_peak<<<grid, 256, 0, st>>>(cells, n_cells, n_updates / 8 + 1); PSL_NOTE_LAUNCH();   // warm-up
+    cudaEventRecord(a, st);
+    k_atomic_peak<<<grid, 256, 0, st>>>(cells, n_cells, n_updates); PSL_NOTE_LAUNCH();
+    cudaEventRecord(b, st);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFreeAsync(cells, st);
+    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, cudaGetErrorString(e));
+    *updates_per_s = (double)n_updates / (ms * 1e-3);
+    return PSL_OK;
 }

@@ -126,18 +126,18 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 }
 
 // production: write the primaries of histories [first, first+n) to the batch
-__global__ void __launch_bounds__(256) k_source(PlanDev P, int64_t first, int64_t n, Particle *out, int64_t cap,
-                                                uint32_t *counts, unsigned long long *ledger) {
+__global__ void __launch_bounds__(256) k_source(PlanDev P, int64_t first, int64_t n, int64_t stride, Particle *out,
+                                                int64_t cap, uint32_t *counts, unsigned long long *ledger) {
     __shared__ int64_t gs[1025];
     for (int i = threadIdx.x; i <= P.n_groups; i += blockDim.x) gs[i] = P.group_start[i];
     __syncthreads();
     unsigned long long emitted = 0, missed = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_round = (n + stride - 1) / stride * stride;     // whole warps iterate together
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_round = (n + gstride - 1) / gstride * gstride;   // whole warps iterate together
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += gstride) {
         SrcOut o;
         o.status = -1;
-        if (i < n) source_one(P, gs, first + i, o);
+        if (i < n) source_one(P, gs, first + i * stride, o);
         if (o.status == PSL_SRC_TRANSPORT || o.status == PSL_SRC_MISS) {
             unsigned long long q = fixed_point(o.s[6], o.s[7]);
             emitted += q;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) k_source(PlanDev P, int64_t first, int64_
             Particle pt;
             pt.x = o.s[0]; pt.y = o.s[1]; pt.z = o.s[2]; pt.e = o.s[6];
             pt.u = o.s[3]; pt.v = o.s[4]; pt.w = o.s[5]; pt.wt = o.s[7];
-            const uint64_t pid = (uint64_t)(first + i);
+            const uint64_t pid = (uint64_t)(first + i * stride);
             pt.pid_lo = (uint32_t)pid; pt.pid_hi = (uint32_t)(pid >> 32);
             pt.type = o.ptype; pt.root = (uint32_t)i;
             const bool is_ph = o.ptype == 0;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_source(PlanDev P, int64_t first, int64_
     }
 }
 
-__global__ void __launch_bounds__(256) k_source_trace(PlanDev P, int64_t first, int64_t n, int64_t *entry, int64_t *use,
+__global__ void __launch_bounds__(256) k_source_trace(PlanDev P, int64_t first, int64_t n, int64_t stride, int64_t *entry, int64_t *use,
                                                       int64_t *rec, int32_t *beam, int8_t *status, float *state,
                                                       int32_t *ptype) {
     __shared__ int64_t gs[1025];
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_source_trace(PlanDev P, int64_t first, 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         SrcOut o;
         for (int k = 0; k < 8; ++k) o.s[k] = 0.f;
-        source_one(P, gs, first + i, o);
+        source_one(P, gs, first + i * stride, o);
         if (entry) entry[i] = o.entry;
         if (use) use[i] = o.use;
         if (rec) rec[i] = o.rec;
@@ -247,9 +247,15 @@ static int finish_batch(psl_batch *b, cudaStream_t st) {
     return PSL_OK;
 }
 
+static bool range_ok(const psl_plan_t *plan, int64_t first, int64_t n, int64_t stride) {
+    if (n < 0 || first < 0 || stride < 1) return false;
+    if (n == 0) return true;
+    return first < plan->n_histories && (n - 1) <= (plan->n_histories - 1 - first) / stride;
+}
+
 extern "C" int psl_source_batch(const psl_plan_t *plan, const psl_phantom_t *phantom, int64_t first, int64_t n,
-                                psl_batch_t **out, void *stream_) {
-    if (!plan || !out || n < 0 || first < 0 || first + n > plan->n_histories)
+                                int64_t stride, psl_batch_t **out, void *stream_) {
+    if (!plan || !out || !range_ok(plan, first, n, stride))
         return psl_fail(PSL_EINVAL, "psl_source_batch: bad argument or history range");
     if (n >= (1ll << 32)) return psl_fail(PSL_EINVAL, "psl_source_batch: batch too large");
     int rc = check_phantom(phantom);
@@ -262,7 +268,7 @@ extern "C" int psl_source_batch(const psl_plan_t *plan, const psl_phantom_t *pha
     PlanDev P = make_plan_dev(plan, phantom);
     if (n > 0) {
         int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)psl_sm_count() * 16));
-        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_SOURCE, st, &tk_); k_source<<<grid, 256, 0, st>>>(P, first, n, b->p, b->cap, b->counts, (unsigned long long *)(b->counts + 2)); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_SOURCE, st, tk_); }
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_SOURCE, st, &tk_); k_source<<<grid, 256, 0, st>>>(P, first, n, stride, b->p, b->cap, b->counts, (unsigned long long *)(b->counts + 2)); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_SOURCE, st, tk_); }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { psl_batch_destroy(b); return psl_fail(PSL_ECUDA, cudaGetErrorString(e)); }
@@ -272,9 +278,9 @@ extern "C" int psl_source_batch(const psl_plan_t *plan, const psl_phantom_t *pha
 }
 
 extern "C" int psl_source_trace(const psl_plan_t *plan, const psl_phantom_t *phantom, int64_t first, int64_t n,
-                                int64_t *entry, int64_t *use, int64_t *rec, int32_t *beam, int8_t *status, float *state,
-                                int32_t *ptype, void *stream_) {
-    if (!plan || n < 0 || first < 0 || first + n > plan->n_histories)
+                                int64_t stride, int64_t *entry, int64_t *use, int64_t *rec, int32_t *beam,
+                                int8_t *status, float *state, int32_t *ptype, void *stream_) {
+    if (!plan || !range_ok(plan, first, n, stride))
         return psl_fail(PSL_EINVAL, "psl_source_trace: bad argument or history range");
     int rc = check_phantom(phantom);
     if (rc) return rc;
@@ -282,7 +288,7 @@ extern "C" int psl_source_trace(const psl_plan_t *plan, const psl_phantom_t *pha
     if (n == 0) return PSL_OK;
     PlanDev P = make_plan_dev(plan, phantom);
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)psl_sm_count() * 16));
-    k_source_trace<<<grid, 256, 0, as_stream(stream_)>>>(P, first, n, entry, use, rec, beam, status, state, ptype); PSL_NOTE_LAUNCH();
+    k_source_trace<<<grid, 256, 0, as_stream(stream_)>>>(P, first, n, stride, entry, use, rec, beam, status, state, ptype); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());
     return PSL_OK;
 }

@@ -36,16 +36,20 @@ constexpr float F_TWO_PI = 6.28318530717958647692f;
 constexpr int MAX_E_STEPS = 100000;
 constexpr int MAX_GEN = 64;
 constexpr unsigned FULL = 0xFFFFFFFFu;
+#ifndef PSL_TRANSPORT_MIN_BLOCKS
+#define PSL_TRANSPORT_MIN_BLOCKS 4     // resident 256-thread blocks per SM (register cap 64)
+#endif
 
 struct Tables {
     const float4 *ph0, *ph1;   // material 0/1: mu_c, mu_pe, mu_pp, mu_total (cm^2/g)
     const float4 *el;          // S_restricted (MeV cm^2/g), sigma_moller, sigma_brem (cm^2/g), 0
+    const float2 *rng;         // CSDA range R (g/cm^2) and dR/dlnT * dlnT at each node
     const float *mumax;        // majorant (1/cm), phantom dependent
     float lnE0, inv_dln;
 };
 
 struct Acc {
-    unsigned long long dep, esc, compton, photo, pair, steps;
+    unsigned long long dep, esc, compton, photo, pair, steps, atomics, wsteps;
 };
 
 struct Args {
@@ -56,6 +60,7 @@ struct Args {
     float pcut, ecut, wcc, wcb;
     uint32_t flags;
     uint64_t seed;
+    uint32_t k0, k1;          // the seed's two words (Philox key)
     Tables tab;
     unsigned long long *tally;
     unsigned long long *ledger;
@@ -79,6 +84,28 @@ __global__ void k_tables(float4 *ph0, float4 *ph1, float4 *el, double wcc, doubl
     ph1[i] = make_float4((float)mc, (float)mpe, (float)mpp, (float)(mc + mpe + mpp));
     el[i] = make_float4((float)el_stop_restricted(E, wcc, wcb), (float)el_moller_sigma(E, wcc),
                         (float)el_brem_sigma(E, wcb), 0.f);
+}
+
+// CSDA range with the restricted stopping power: R_i = integral from T_0 to
+// T_i of dT/S (8-point Gauss-Legendre per interval, double), one thread
+__global__ void k_range_table(float2 *rt, double wcc, double wcb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double x8[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+    const double w8[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+    const double l0 = log(T_LO), dl = (log(T_HI) - log(T_LO)) / (NT - 1);
+    double R = 0.0, Tprev = T_LO;
+    for (int i = 0; i < NT; ++i) {
+        const double T = exp(l0 + dl * i);
+        if (i > 0) {
+            const double m = 0.5 * (T + Tprev), h = 0.5 * (T - Tprev);
+            double acc = 0.0;
+            for (int k = 0; k < 4; ++k)
+                acc += w8[k] * (1.0 / el_stop_restricted(m - h * x8[k], wcc, wcb) + 1.0 / el_stop_restricted(m + h * x8[k], wcc, wcb));
+            R += h * acc;
+        }
+        rt[i] = make_float2((float)R, (float)(T * dl / el_stop_restricted(T, wcc, wcb)));
+        Tprev = T;
+    }
 }
 
 __global__ void k_rho_max(const uint8_t *mat, const float *rho, int64_t n, int *out) {
@@ -121,6 +148,15 @@ __device__ __forceinline__ float lerp1(const float *a, int i, float f) {
     return p + f * (q - p);
 }
 
+// R(E): cubic Hermite in ln E with the exact node derivatives dR/dlnE = E/S
+__device__ __forceinline__ float range_of(const Tables &T, float E) {
+    int i; float f;
+    tab_pos(T, E, i, f);
+    const float2 a = __ldg(T.rng + i), b = __ldg(T.rng + i + 1);
+    const float f2 = f * f, f3 = f2 * f;
+    return (2.f * f3 - 3.f * f2 + 1.f) * a.x + (f3 - 2.f * f2 + f) * a.y + (3.f * f2 - 2.f * f3) * b.x + (f3 - f2) * b.y;
+}
+
 __device__ __forceinline__ float stop_of(const Tables &T, float E) {
     int i; float f;
     tab_pos(T, E, i, f);
@@ -138,6 +174,7 @@ __device__ __forceinline__ void deposit(const Args &A, Acc &acc, int64_t iv, flo
     if (!q) return;
     atomicAdd(&A.tally[iv], q);
     acc.dep += q;
+    acc.atomics++;
     if (A.hist_dep) atomicAdd(&A.hist_dep[root], q);
 }
 
@@ -154,14 +191,14 @@ __device__ __forceinline__ void count_event(const Args &A, uint32_t root) {
 // rotate unit direction by polar cosine c and azimuth phi (renormalised)
 __device__ __forceinline__ void rotate_dir(float &u, float &v, float &w, float c, float phi) {
     float st = sqrtf(fmaxf(0.0f, 1.0f - c * c)), sp, cp;
-    sincosf(phi, &sp, &cp);
+    __sincosf(phi, &sp, &cp);
     float nu, nv, nw;
     if (fabsf(w) > 0.99999f) {
         nu = st * cp; nv = st * sp; nw = w > 0.0f ? c : -c;
     } else {
-        float t = sqrtf(1.0f - w * w);
-        nu = u * c + st * (u * w * cp - v * sp) / t;
-        nv = v * c + st * (v * w * cp + u * sp) / t;
+        const float it = rsqrtf(1.0f - w * w), t = (1.0f - w * w) * it;
+        nu = u * c + st * (u * w * cp - v * sp) * it;
+        nv = v * c + st * (v * w * cp + u * sp) * it;
         nw = w * c - st * cp * t;
     }
     float n = rsqrtf(nu * nu + nv * nv + nw * nw);
@@ -178,18 +215,18 @@ __device__ __forceinline__ void push_particle(const Queue &q, const Args &A, uin
     queue_push(q, c, A.err);
 }
 
-__device__ void annihilate(const Args &A, Rng &rng, float x, float y, float z, float wt, uint32_t p0, uint32_t p1,
+__device__ __forceinline__ void annihilate(const Args &A, Rng &rng, float x, float y, float z, float wt, uint32_t p0, uint32_t p1,
                            uint32_t &nchild, uint32_t root) {
-    float cth = 2.0f * rng.uniform() - 1.0f, phi = F_TWO_PI * rng.uniform();
+    float cth = 2.0f * rng.next(A.k0, A.k1, p0, p1) - 1.0f, phi = F_TWO_PI * rng.next(A.k0, A.k1, p0, p1);
     float sth = sqrtf(fmaxf(0.0f, 1.0f - cth * cth)), sp, cp;
-    sincosf(phi, &sp, &cp);
+    __sincosf(phi, &sp, &cp);
     float a0 = sth * cp, a1 = sth * sp, a2 = cth;
     push_particle(A.p_out, A, 0, x, y, z, a0, a1, a2, F_ME, wt, p0, p1, nchild, root);
     push_particle(A.p_out, A, 0, x, y, z, -a0, -a1, -a2, F_ME, wt, p0, p1, nchild, root);
 }
 
 // a charged secondary: queued for transport, or deposited in place
-__device__ void emit_charged(const Args &A, Acc &acc, Rng &rng, uint32_t type, float T, float x, float y, float z,
+__device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, uint32_t type, float T, float x, float y, float z,
                              float u, float v, float w, float wt, int64_t iv, uint32_t p0, uint32_t p1, uint32_t &nchild,
                              uint32_t root) {
     if (T > A.ecut && !(A.flags & PSL_PHYS_LOCAL_SECONDARIES)) {
@@ -203,10 +240,13 @@ __device__ void emit_charged(const Args &A, Acc &acc, Rng &rng, uint32_t type, f
     }
 }
 
-__device__ __forceinline__ void flush_acc(const Args &A, Acc &a) {
-    unsigned long long v[6] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps};
+// ledger slots: 0 emitted, 1 escaped, 2 deposited (fixed point), 3 Compton,
+// 4 photoelectric, 5 pair, 6 electron steps, 7 errors, 8 tally atomics of
+// photon passes, 9 tally atomics of electron passes, 10 Woodcock steps
+__device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int atomics_slot) {
+    unsigned long long v[8] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps, a.atomics, a.wsteps};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 8; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
     }
@@ -217,6 +257,8 @@ __device__ __forceinline__ void flush_acc(const Args &A, Acc &a) {
         if (v[3]) atomicAdd(&A.ledger[4], v[3]);
         if (v[4]) atomicAdd(&A.ledger[5], v[4]);
         if (v[5]) atomicAdd(&A.ledger[6], v[5]);
+        if (v[6]) atomicAdd(&A.ledger[atomics_slot], v[6]);
+        if (v[7]) atomicAdd(&A.ledger[10], v[7]);
     }
 }
 
@@ -225,7 +267,7 @@ struct Photon {
     float x, y, z, u, v, w, e, wt;
     uint32_t p0, p1, root, nchild;
     Rng rng;
-    float mumax;
+    float mumax, inv_mumax;
     int ti;
     float tf;
 };
@@ -233,11 +275,13 @@ struct Photon {
 __device__ __forceinline__ void photon_energy(const Args &A, Photon &g) {
     tab_pos(A.tab, g.e, g.ti, g.tf);
     g.mumax = lerp1(A.tab.mumax, g.ti, g.tf);
+    g.inv_mumax = __frcp_rn(g.mumax);
 }
 
 // one Woodcock step (+ interaction); returns false when the photon ends
-__device__ bool photon_event(const Args &A, Acc &acc, Photon &g) {
-    const float s = -logf(g.rng.uniform()) / g.mumax;
+__device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g) {
+    acc.wsteps++;
+    const float s = -__logf(g.rng.next(A.k0, A.k1, g.p0, g.p1)) * g.inv_mumax;
     g.x += s * g.u; g.y += s * g.v; g.z += s * g.w;
     const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
     if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)A.nx && fy < (float)A.ny && fz < (float)A.nz)) {
@@ -251,34 +295,37 @@ __device__ bool photon_event(const Args &A, Acc &acc, Photon &g) {
     const float mc = rho * c.x, mpe = rho * c.y, mpp = rho * c.z;
     const float mu = mc + mpe + mpp;
     if (mu > g.mumax) atomicOr(A.err, 8u);
-    if (g.rng.uniform() * g.mumax >= mu) return true;           // virtual interaction
+    if (g.rng.next(A.k0, A.k1, g.p0, g.p1) * g.mumax >= mu) return true;           // virtual interaction
     count_event(A, g.root);
-    const float r = g.rng.uniform() * mu;
+    const float r = g.rng.next(A.k0, A.k1, g.p0, g.p1) * mu;
     const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
     if (r < mc) {                                                 // Compton (Kahn's method)
         acc.compton++;
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
-        const float k = g.e / F_ME;
-        float x = 1.0f;
+        const float k = g.e * (1.0f / F_ME), ik = __frcp_rn(k);
+        const float p_first = __fdividef(1.0f + 2.0f * k, 9.0f + 2.0f * k);
+        float x = 1.0f, ix = 1.0f;
         for (int it = 0; it < 1000; ++it) {
-            const float r1 = g.rng.uniform(), r2 = g.rng.uniform(), r3 = g.rng.uniform();
-            if (r1 <= (1.0f + 2.0f * k) / (9.0f + 2.0f * k)) {
+            const float r1 = g.rng.next(A.k0, A.k1, g.p0, g.p1), r2 = g.rng.next(A.k0, A.k1, g.p0, g.p1), r3 = g.rng.next(A.k0, A.k1, g.p0, g.p1);
+            if (r1 <= p_first) {
                 x = 1.0f + 2.0f * k * r2;
-                if (r3 <= 4.0f * (1.0f / x - 1.0f / (x * x))) break;
+                ix = __frcp_rn(x);
+                if (r3 <= 4.0f * (ix - ix * ix)) break;
             } else {
-                x = (1.0f + 2.0f * k) / (1.0f + 2.0f * k * r2);
-                const float cc = 1.0f - (x - 1.0f) / k;
-                if (r3 <= 0.5f * (cc * cc + 1.0f / x)) break;
+                ix = __fdividef(1.0f + 2.0f * k * r2, 1.0f + 2.0f * k);
+                x = __frcp_rn(ix);
+                const float cc = 1.0f - (x - 1.0f) * ik;
+                if (r3 <= 0.5f * (cc * cc + ix)) break;
             }
         }
-        const float cth = fminf(1.0f, fmaxf(-1.0f, 1.0f - (x - 1.0f) / k));
-        const float ep = g.e / x, phi = F_TWO_PI * g.rng.uniform();
+        const float cth = fminf(1.0f, fmaxf(-1.0f, 1.0f - (x - 1.0f) * ik));
+        const float ep = g.e * ix, phi = F_TWO_PI * g.rng.next(A.k0, A.k1, g.p0, g.p1);
         float nu = g.u, nv = g.v, nw = g.w;
         rotate_dir(nu, nv, nw, cth, phi);
         const float te = g.e - ep;
         float du = g.e * g.u - ep * nu, dv = g.e * g.v - ep * nv, dw = g.e * g.w - ep * nw;
-        const float nn = sqrtf(du * du + dv * dv + dw * dw);
-        if (nn > 0.0f) { du /= nn; dv /= nn; dw /= nn; } else { du = g.u; dv = g.v; dw = g.w; }
+        const float nn2 = du * du + dv * dv + dw * dw;
+        if (nn2 > 0.0f) { const float in = rsqrtf(nn2); du *= in; dv *= in; dw *= in; } else { du = g.u; dv = g.v; dw = g.w; }
         emit_charged(A, acc, g.rng, 1, te, g.x, g.y, g.z, du, dv, dw, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
         g.e = ep; g.u = nu; g.v = nv; g.w = nw;
         if (g.e < A.pcut) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
@@ -292,19 +339,19 @@ __device__ bool photon_event(const Args &A, Acc &acc, Photon &g) {
     }
     acc.pair++;                                                    // pair production
     if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
-    const float avail = g.e - 2.0f * F_ME, eps = g.rng.uniform();
+    const float avail = g.e - 2.0f * F_ME, eps = g.rng.next(A.k0, A.k1, g.p0, g.p1);
     const float t1 = eps * avail, t2 = avail - t1;
     emit_charged(A, acc, g.rng, 1, t1, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
     emit_charged(A, acc, g.rng, 2, t2, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
     return false;
 }
 
-__global__ void __launch_bounds__(256) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
+__global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
                                                 uint32_t cap, uint32_t *head) {
     const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0};
     Photon g;
     bool alive = false, done = false;
     for (;;) {
@@ -320,7 +367,7 @@ __global__ void __launch_bounds__(256) k_photon(Args A, const Particle *src, con
                     const Particle p = load_particle(src + idx);
                     g.x = p.x; g.y = p.y; g.z = p.z; g.u = p.u; g.v = p.v; g.w = p.w; g.e = p.e; g.wt = p.wt;
                     g.p0 = p.pid_lo; g.p1 = p.pid_hi; g.root = p.root; g.nchild = 0;
-                    g.rng.init(A.seed, p.pid_lo, p.pid_hi);
+                    g.rng.draw = 0;
                     photon_energy(A, g);
                     alive = true;
                 } else {
@@ -331,7 +378,7 @@ __global__ void __launch_bounds__(256) k_photon(Args A, const Particle *src, con
         if (!__any_sync(FULL, alive)) break;
         if (alive) alive = photon_event(A, acc, g);
     }
-    flush_acc(A, acc);
+    flush_acc(A, acc, 8);
 }
 
 // ----------------------------------------------------------- electrons ---
@@ -347,35 +394,28 @@ struct Electron {
 __device__ __forceinline__ float highland(float T, float s, float rho) {
     const float t = s * rho * (1.0f / 36.08f);
     if (!(t > 0.0f)) return 0.0f;
-    const float bcp = T * (T + 2.0f * F_ME) / (T + F_ME);
-    const float f = 1.0f + 0.038f * logf(t);
+    const float bcp = __fdividef(T * (T + 2.0f * F_ME), T + F_ME);
+    const float f = 1.0f + 0.038f * __logf(t);
     if (!(f > 0.0f)) return 0.0f;
-    return 13.6f / bcp * sqrtf(t) * f;
+    return __fdividef(13.6f, bcp) * sqrtf(t) * f;
 }
 
-// path (g/cm^2) to slow from T to Tl: 3-point Gauss-Legendre of 1/S
-__device__ __forceinline__ float path_between(const Tables &T, float Tl, float Th) {
-    const float m = 0.5f * (Th + Tl), h = 0.5f * (Th - Tl), a = 0.7745966692414834f * h;
-    return h * (0.5555555555555556f / stop_of(T, m - a) + 0.8888888888888889f / stop_of(T, m) +
-                0.5555555555555556f / stop_of(T, m + a));
-}
-
-// energy after a path h (g/cm^2): RK4 on dT/dh = -S(T)
-__device__ __forceinline__ float energy_after(const Tables &T, float t, float h) {
-    const float k1 = stop_of(T, t);
+// energy after a path h (g/cm^2): RK4 on dT/dh = -S(T), k1 = S(t) given
+__device__ __forceinline__ float energy_after(const Tables &T, float t, float h, float k1) {
     const float k2 = stop_of(T, fmaxf(t - 0.5f * h * k1, 1e-3f));
     const float k3 = stop_of(T, fmaxf(t - 0.5f * h * k2, 1e-3f));
     const float k4 = stop_of(T, fmaxf(t - h * k3, 1e-3f));
     return t - h * (k1 + 2.0f * k2 + 2.0f * k3 + k4) * (1.0f / 6.0f);
 }
 
-__device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, uint32_t *err) {
+__device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, uint32_t k0, uint32_t k1, uint32_t p0,
+                                               uint32_t p1, uint32_t *err) {
     const float tau = T / F_ME, ec = wcc / T;
     const float g = (tau / (tau + 1.0f)) * (tau / (tau + 1.0f));
     const float a = (2.0f * tau + 1.0f) / ((tau + 1.0f) * (tau + 1.0f));
     const float w1 = 1.0f / ec - 2.0f, w2 = 5.0f * (0.5f - ec);
     for (int it = 0; it < 1000; ++it) {
-        const float r1 = rng.uniform(), r2 = rng.uniform(), r3 = rng.uniform();
+        const float r1 = rng.next(k0, k1, p0, p1), r2 = rng.next(k0, k1, p0, p1), r3 = rng.next(k0, k1, p0, p1);
         const float e = (r1 * (w1 + w2) < w1) ? ec / (1.0f - r2 * (1.0f - 2.0f * ec)) : ec + r2 * (0.5f - ec);
         const float q = e / (1.0f - e);
         const float f = 1.0f + q * q + g * e * e - a * q;
@@ -394,7 +434,7 @@ __device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &
 }
 
 // one condensed-history step (+ hard event); returns false when the electron ends
-__device__ bool electron_event(const Args &A, Acc &acc, Electron &s) {
+__device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron &s) {
     const int64_t iv = ((int64_t)s.iz * A.ny + s.iy) * A.nx + s.ix;
     if (s.t <= A.ecut || ++s.steps > MAX_E_STEPS) {
         if (s.steps > MAX_E_STEPS) atomicOr(A.err, PSL_DEV_ERR_STEPS);
@@ -410,7 +450,7 @@ __device__ bool electron_event(const Args &A, Acc &acc, Electron &s) {
     const float4 el = lerp4(A.tab.el, ti, tf);
     // hard cross sections vanish below their thresholds (guard the interpolation)
     const float sig = hard_on ? rho * ((s.t > 2.0f * A.wcc ? el.y : 0.0f) + (s.t > A.wcb ? el.z : 0.0f)) : 0.0f;
-    const float s_hard = sig > 0.0f ? s.nlam / sig : INFINITY;
+    const float s_hard = sig > 0.0f ? __fdividef(s.nlam, sig) : INFINITY;
     // distance to the voxel boundary
     float s_bound = INFINITY;
     int axis = -1, cross = 0;
@@ -420,30 +460,30 @@ __device__ bool electron_event(const Args &A, Acc &acc, Electron &s) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             float t;
-            if (d[k] > 0.0f) t = ((float)(ii[k] + 1) * vv[k] - p[k]) / d[k];
-            else if (d[k] < 0.0f) t = ((float)ii[k] * vv[k] - p[k]) / d[k];
+            if (d[k] > 0.0f) t = __fdividef((float)(ii[k] + 1) * vv[k] - p[k], d[k]);
+            else if (d[k] < 0.0f) t = __fdividef((float)ii[k] * vv[k] - p[k], d[k]);
             else continue;
             t = fmaxf(t, 0.0f);
             if (t < s_bound) { s_bound = t; axis = k; cross = d[k] > 0.0f ? 1 : -1; }
         }
     }
     const float tlim = fmaxf(0.9f * s.t, A.ecut);
-    const float s_max = path_between(A.tab, tlim, s.t) / rho;
+    const float s_max = (range_of(A.tab, s.t) - range_of(A.tab, tlim)) * __frcp_rn(rho);
     int which;
     float step;
     if (s_hard <= s_bound && s_hard <= s_max) { which = 0; step = s_hard; }
     else if (s_bound <= s_max) { which = 1; step = s_bound; }
     else { which = 2; step = s_max; }
-    float tend = which == 2 ? tlim : fmaxf(energy_after(A.tab, s.t, rho * step), tlim);
+    float tend = which == 2 ? tlim : fmaxf(energy_after(A.tab, s.t, rho * step, el.x), tlim);
     const float th0 = highland(s.t, step, rho);
     deposit(A, acc, iv, s.t - tend, s.wt, s.root);
     s.t = tend;
     s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
     s.nlam -= step * sig;
     if (!(A.flags & PSL_PHYS_NO_MSC) && step > 0.0f) {
-        const float th = th0 * sqrtf(-2.0f * logf(s.rng.uniform()));
-        const float phi = F_TWO_PI * s.rng.uniform();
-        rotate_dir(s.u, s.v, s.w, cosf(th), phi);
+        const float th = th0 * sqrtf(-2.0f * __logf(s.rng.next(A.k0, A.k1, s.p0, s.p1)));
+        const float phi = F_TWO_PI * s.rng.next(A.k0, A.k1, s.p0, s.p1);
+        rotate_dir(s.u, s.v, s.w, __cosf(th), phi);
     }
     if (which == 1) {
         int out = 0;
@@ -459,37 +499,37 @@ __device__ bool electron_event(const Args &A, Acc &acc, Electron &s) {
         tab_pos(A.tab, s.t, tj, tg);
         const float4 e2 = lerp4(A.tab.el, tj, tg);
         const float sm = s.t > 2.0f * A.wcc ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
-        const float r = s.rng.uniform() * (sm + sb);
+        const float r = s.rng.next(A.k0, A.k1, s.p0, s.p1) * (sm + sb);
         if (sm + sb > 0.0f) {
             if (r < sm) {                                         // hard Moller
-                const float eps = sample_moller(s.t, A.wcc, s.rng, A.err);
+                const float eps = sample_moller(s.t, A.wcc, s.rng, A.k0, A.k1, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
                 const float cp = sqrtf(tp * (s.t + 2.0f * F_ME) / (s.t * (tp + 2.0f * F_ME)));
                 const float cd = sqrtf(W * (s.t + 2.0f * F_ME) / (s.t * (W + 2.0f * F_ME)));
-                const float phi = F_TWO_PI * s.rng.uniform();
+                const float phi = F_TWO_PI * s.rng.next(A.k0, A.k1, s.p0, s.p1);
                 float du = s.u, dv = s.v, dw = s.w;
                 rotate_dir(du, dv, dw, cd, phi + 3.14159265358979f);
                 rotate_dir(s.u, s.v, s.w, cp, phi);
                 emit_charged(A, acc, s.rng, 1, W, s.x, s.y, s.z, du, dv, dw, s.wt, iv, s.p0, s.p1, s.nchild, s.root);
                 s.t = tp;
             } else {                                              // hard bremsstrahlung
-                const float kph = A.wcb * expf(s.rng.uniform() * logf(s.t / A.wcb));
+                const float kph = A.wcb * expf(s.rng.next(A.k0, A.k1, s.p0, s.p1) * logf(s.t / A.wcb));
                 if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) deposit(A, acc, iv, kph, s.wt, s.root);
                 else push_particle(A.p_out, A, 0, s.x, s.y, s.z, s.u, s.v, s.w, kph, s.wt, s.p0, s.p1, s.nchild, s.root);
                 s.t -= kph;
             }
         }
-        s.nlam = -logf(s.rng.uniform());
+        s.nlam = -__logf(s.rng.next(A.k0, A.k1, s.p0, s.p1));
     }
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
+__global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
                                                   uint32_t *head) {
     const uint32_t n = min(*n_ptr, cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0};
     Electron s;
     bool alive = false, done = false;
     for (;;) {
@@ -509,8 +549,8 @@ __global__ void __launch_bounds__(256) k_electron(Args A, const Particle *src, c
                     s.ix = min(max((int)floorf(s.x * A.ivx), 0), A.nx - 1);
                     s.iy = min(max((int)floorf(s.y * A.ivy), 0), A.ny - 1);
                     s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
-                    s.rng.init(A.seed, p.pid_lo, p.pid_hi);
-                    s.nlam = -logf(s.rng.uniform());
+                    s.rng.draw = 0;
+                    s.nlam = -__logf(s.rng.next(A.k0, A.k1, s.p0, s.p1));
                     alive = true;
                 } else {
                     done = true;
@@ -520,7 +560,7 @@ __global__ void __launch_bounds__(256) k_electron(Args A, const Particle *src, c
         if (!__any_sync(FULL, alive)) break;
         if (alive) alive = electron_event(A, acc, s);
     }
-    flush_acc(A, acc);
+    flush_acc(A, acc, 9);
 }
 
 // ------------------------------------------------------------ band sort ---
@@ -598,6 +638,7 @@ struct TableCache {
     int device = -1;
     float wcc = -1.f, wcb = -1.f;
     float4 *ph0 = nullptr, *ph1 = nullptr, *el = nullptr;
+    float2 *rng = nullptr;
 };
 std::mutex g_tab_mu;
 std::vector<TableCache> g_tabs;
@@ -613,7 +654,9 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
     PSL_CUDA(cudaMalloc((void **)&t.ph0, NT * sizeof(float4)));
     PSL_CUDA(cudaMalloc((void **)&t.ph1, NT * sizeof(float4)));
     PSL_CUDA(cudaMalloc((void **)&t.el, NT * sizeof(float4)));
+    PSL_CUDA(cudaMalloc((void **)&t.rng, NT * sizeof(float2)));
     k_tables<<<(NT + 255) / 256, 256, 0, st>>>(t.ph0, t.ph1, t.el, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    k_range_table<<<1, 32, 0, st>>>(t.rng, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());
     PSL_CUDA(cudaStreamSynchronize(st));
     g_tabs.push_back(t);
@@ -686,7 +729,7 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     int rc = get_tables(P.wcc, P.wcb, st, tc);
     if (rc) return rc;
     const int64_t nph = batch->n_photons, nel = batch->n_electrons;
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::max(nph, nel), 1 << 21));
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::max(nph, nel), 1 << 24));
     if ((rc = workspace_ensure(tally, chunk))) return rc;
     Workspace *w = tally->ws;
     batch->consumed = 1;
@@ -704,7 +747,8 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     A.mat = ph->mat; A.rho = ph->rho;
     A.pcut = P.photon_cut; A.ecut = P.electron_cut; A.wcc = P.wcc; A.wcb = P.wcb; A.flags = P.flags;
     A.seed = batch->seed;
-    A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.mumax = w->mumax;
+    A.k0 = (uint32_t)A.seed; A.k1 = (uint32_t)(A.seed >> 32);
+    A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.rng = tc.rng; A.tab.mumax = w->mumax;
     A.tab.lnE0 = (float)log(T_LO);
     A.tab.inv_dln = (float)((NT - 1) / (log(T_HI) - log(T_LO)));
     A.tally = tally->t + (size_t)b * nvox;

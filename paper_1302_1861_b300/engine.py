@@ -65,8 +65,12 @@ def upload(w: Workload, device: str = "cuda", records=None) -> DeviceWorkload:
                           [xe, ye, ee])
 
 
-def batch_edges(first: int, n: int, n_batches: int) -> np.ndarray:
-    return np.linspace(first, first + n, n_batches + 1).astype(np.int64)
+def batch_histories(first: int, n: int, n_batches: int, b: int):
+    """(first, count, stride) of batch b of the histories [first, first+n):
+    every n_batches-th history, so each batch samples every energy division
+    (independent batches, Sec. 2.3.3)."""
+    cnt = max(0, (n - b + n_batches - 1) // n_batches)
+    return first + b, cnt, n_batches
 
 
 def normalisation(n_total_psl: int, n_histories: int, n_incident: int) -> float:
@@ -89,9 +93,9 @@ def run(dw: DeviceWorkload, n_histories: Optional[int] = None, n_batches: Option
     if tally is None:
         tally = capi.psl_tally_create(dw.phantom, nb)
     phys = capi.physics(flags)
-    edges = batch_edges(0, n_h, nb)
     for b in range(nb):
-        batch = capi.psl_source_batch(plan, dw.phantom, int(edges[b]), int(edges[b + 1] - edges[b]), stream)
+        f0, cnt, stride = batch_histories(0, n_h, nb, b)
+        batch = capi.psl_source_batch(plan, dw.phantom, f0, cnt, stride, stream)
         capi.transport_run(dw.phantom, phys, batch, tally, b, stream)
         batch.close()
     out = dict(store=store, plan=plan, tally=tally)
@@ -110,7 +114,7 @@ def run(dw: DeviceWorkload, n_histories: Optional[int] = None, n_batches: Option
 def raw_tallies(dw: DeviceWorkload, tally, n_batches: int):
     nz, ny, nx = dw.w.phantom.shape
     t = torch.empty(n_batches * nz * ny * nx, dtype=torch.int64, device=dw.mat_t.device)
-    lg = torch.empty(8, dtype=torch.int64, device=t.device)
+    lg = torch.empty(12, dtype=torch.int64, device=t.device)
     capi.psl_tally_read(tally, t, lg)
     torch.cuda.synchronize()
     return t.view(n_batches, nz, ny, nx).cpu().numpy(), lg.cpu().numpy()

@@ -22,7 +22,7 @@ def plan_arrays(plan):
     return [x.cpu().numpy() for x in a], n_total
 
 
-def source_trace(dw, plan, h0, n):
+def source_trace(dw, plan, h0, n, stride=1):
     d = dict(entry=torch.empty(n, dtype=torch.int64, device="cuda"),
              use=torch.empty(n, dtype=torch.int64, device="cuda"),
              rec=torch.empty(n, dtype=torch.int64, device="cuda"),
@@ -30,7 +30,7 @@ def source_trace(dw, plan, h0, n):
              status=torch.empty(n, dtype=torch.int8, device="cuda"),
              state=torch.empty(n * 8, dtype=torch.float32, device="cuda"),
              ptype=torch.empty(n, dtype=torch.int32, device="cuda"))
-    capi.psl_source_trace(plan, dw.phantom, h0, n, **d)
+    capi.psl_source_trace(plan, dw.phantom, h0, n, stride=stride, **d)
     torch.cuda.synchronize()
     out = {k: v.cpu().numpy() for k, v in d.items()}
     out["state"] = out["state"].reshape(n, 8)

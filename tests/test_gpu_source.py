@@ -136,3 +136,21 @@ def test_source_full_size_sampled(cfg):
         assert np.array_equal(g["entry"], ent) and np.array_equal(g["use"], use)
         rec = opl.start[ent] + (opl.offset[ent] + use) % opl.nrec[ent]
         assert np.array_equal(g["rec"], rec)
+
+
+def test_source_strided_batches():
+    """Independent batches: batch b reads histories b, b + N_b, ... (bit-exact)."""
+    w = inputs.config1()
+    dw, store, ost, n_valid, n_bins = _build_both(w)
+    dw, plan, opl = _plan_both(w, store, ost)
+    for b in (0, 3, 9):
+        hs = np.arange(b, w.n_histories, 10)
+        g = source_trace(dw, plan, b, len(hs), stride=10)
+        o = source.source(opl, ost, w.records, w.beams, w.phantom, hs, w.z_psl, w.sad)
+        assert np.array_equal(g["rec"], o.rec) and np.array_equal(g["status"], o.status)
+        ok = o.status == source.ST_TRANSPORT
+        assert np.array_equal(g["state"][ok, 7], o.wt[ok])
+    # every energy division appears in every batch
+    for b in (0, 9):
+        ent, _ = source.history_map(opl, np.arange(b, w.n_histories, 10))
+        assert set(np.unique(opl.group[ent])) == set(np.unique(opl.group[opl.count > 0]))
