@@ -98,6 +98,12 @@ static double uniform(stream_t *s) {
     return ((double)(r >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
+/* Start the next draw at a fresh Philox block.  Every event (a Woodcock step,
+ * an interaction, an electron step, a hard event, an annihilation) begins on
+ * a block boundary, so the draws of one event come from as few blocks as
+ * possible (and a GPU warp refills its blocks together). */
+static void align_stream(stream_t *s) { s->draw = (s->draw + 3u) & ~3u; }
+
 /* id of the ordinal-th secondary of particle `parent` (top bit set) */
 static uint64_t child_pid(uint64_t seed, uint64_t parent, uint32_t ordinal) {
     uint32_t ctr[4] = {ordinal, TAG_CHILD, (uint32_t)parent, (uint32_t)(parent >> 32)};
@@ -377,6 +383,7 @@ static double mu_max_of(const ctx_t *c, double E) {
 
 static void annihilate(const ctx_t *c, stream_t *s, uint32_t *nchild, uint64_t pid, const double p[3],
                        double wt, pstack_t *st) {
+    align_stream(s);
     double cth = 2.0 * uniform(s) - 1.0, phi = 2.0 * PI_D * uniform(s);
     double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
     double a[3] = {sth * cos(phi), sth * sin(phi), cth};
@@ -408,6 +415,7 @@ static void photon(const ctx_t *c, acc_t *a, part_t *g, pstack_t *st) {
     double E = g->E, wt = g->wt, p[3] = {g->p[0], g->p[1], g->p[2]}, d[3] = {g->d[0], g->d[1], g->d[2]};
     for (;;) {
         double mumax = mu_max_of(c, E);
+        align_stream(&s);                                  /* Woodcock step: step, virtual, channel */
         double step = -log(uniform(&s)) / mumax;
         for (int k = 0; k < 3; ++k) p[k] += step * d[k];
         int64_t iv;
@@ -420,6 +428,7 @@ static void photon(const ctx_t *c, acc_t *a, part_t *g, pstack_t *st) {
         if (uniform(&s) * mumax >= mu) continue;          /* virtual (delta) interaction */
         a->events++;
         double r = uniform(&s) * mu;
+        align_stream(&s);                                  /* the interaction's draws */
         if (r < mc) {                                      /* Compton */
             a->ledger[L_COMPTON]++;
             if (c->flags & F_FIRST_INTERACTION) { deposit(c, a, iv, E, wt); return; }
@@ -492,6 +501,7 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
         }
         a->ledger[L_ESTEPS]++;
         a->events++;
+        align_stream(&s);                                  /* the step's draws (scattering) */
         double rho = c->rho[iv];
         double sig = hard_on ? rho * (ora_moller_sigma(T, c->wcc) + ora_brem_sigma(T, c->wcb)) : 0.0;
         double s_hard = sig > 0.0 ? nlam / sig : INFINITY;
@@ -538,6 +548,7 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
             }
         } else if (which == 0) {
             double sm = ora_moller_sigma(T, c->wcc), sb = ora_brem_sigma(T, c->wcb);
+            align_stream(&s);                              /* the hard event's draws */
             double r = uniform(&s) * (sm + sb);
             if (sm + sb > 0.0) {
                 if (r < sm) {                                /* hard Moller */

@@ -164,6 +164,9 @@ __host__ __device__ __forceinline__ u32x4 philox10(uint32_t c0, uint32_t c1, uin
 struct Rng {
     uint32_t draw;
     u32x4 blk;
+    // start the next draw at a fresh block: every event begins on a block
+    // boundary, so the lanes of a warp compute their blocks together
+    __device__ __forceinline__ void align() { draw = (draw + 3u) & ~3u; }
     // ((r >> 9) + 0.5) * 2^-23: 24 significant bits, exact in float
     __device__ __forceinline__ float next(uint32_t k0, uint32_t k1, uint32_t p0, uint32_t p1) {
         uint32_t w = draw & 3u;

@@ -217,6 +217,7 @@ __device__ __forceinline__ void push_particle(const Queue &q, const Args &A, uin
 
 __device__ __forceinline__ void annihilate(const Args &A, Rng &rng, float x, float y, float z, float wt, uint32_t p0, uint32_t p1,
                            uint32_t &nchild, uint32_t root) {
+    rng.align();
     float cth = 2.0f * rng.next(A.k0, A.k1, p0, p1) - 1.0f, phi = F_TWO_PI * rng.next(A.k0, A.k1, p0, p1);
     float sth = sqrtf(fmaxf(0.0f, 1.0f - cth * cth)), sp, cp;
     __sincosf(phi, &sp, &cp);
@@ -281,6 +282,7 @@ __device__ __forceinline__ void photon_energy(const Args &A, Photon &g) {
 // one Woodcock step (+ interaction); returns false when the photon ends
 __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g) {
     acc.wsteps++;
+    g.rng.align();                                                // Woodcock step: step, virtual, channel
     const float s = -__logf(g.rng.next(A.k0, A.k1, g.p0, g.p1)) * g.inv_mumax;
     g.x += s * g.u; g.y += s * g.v; g.z += s * g.w;
     const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
@@ -298,6 +300,7 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
     if (g.rng.next(A.k0, A.k1, g.p0, g.p1) * g.mumax >= mu) return true;           // virtual interaction
     count_event(A, g.root);
     const float r = g.rng.next(A.k0, A.k1, g.p0, g.p1) * mu;
+    g.rng.align();                                                // the interaction's draws
     const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
     if (r < mc) {                                                 // Compton (Kahn's method)
         acc.compton++;
@@ -443,6 +446,7 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
     }
     acc.steps++;
     count_event(A, s.root);
+    s.rng.align();                                                // the step's draws (scattering)
     const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
     const float rho = __ldg(A.rho + iv);
     int ti; float tf;
@@ -499,6 +503,7 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
         tab_pos(A.tab, s.t, tj, tg);
         const float4 e2 = lerp4(A.tab.el, tj, tg);
         const float sm = s.t > 2.0f * A.wcc ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
+        s.rng.align();                                            // the hard event's draws
         const float r = s.rng.next(A.k0, A.k1, s.p0, s.p1) * (sm + sb);
         if (sm + sb > 0.0f) {
             if (r < sm) {                                         // hard Moller
