@@ -219,8 +219,11 @@ PSL_API int psl_plan_read(const psl_plan_t *plan, int64_t *beam, int64_t *psl, i
  *   weight = (wt * F) * mu_i/mu_total.
  * Survivors are rotated (collimator about z, gantry about y, couch about z,
  * about the isocentre) and moved along their line to its entry into the
- * phantom box.  The batch holds the particles for transport_run; the phantom
- * is read for its box only.  Synchronises stream. */
+ * phantom box.  The call only records the range: the source stage runs inside
+ * transport_run, fused with the first photon pass (each lane that needs work
+ * sources the next history), so the plan must stay alive until the batch has
+ * been transported.  The phantom is read for its box only.  No device work,
+ * no synchronisation. */
 PSL_API int psl_source_batch(const psl_plan_t *plan, const psl_phantom_t *phantom, int64_t first_history,
                      int64_t n_histories, int64_t stride, psl_batch_t **out, void *stream);
 
@@ -240,7 +243,9 @@ PSL_API int psl_source_trace(const psl_plan_t *plan, const psl_phantom_t *phanto
 PSL_API int psl_batch_from_particles(const float *state, const int32_t *ptype, const uint64_t *pid, int64_t n,
                              uint64_t seed, psl_batch_t **out, void *stream);
 
-/* Histories (or particles) in a batch and the fixed-point energy they emit. */
+/* Histories (or caller particles) in a batch, and its photon and charged
+ * particle counts (-1 for a batch from psl_source_batch: known only once
+ * transported). */
 PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64_t *n_photons, int64_t *n_electrons);
 
 /* One int64 tally of nz*ny*nx voxels per batch, plus a 12-slot ledger:

@@ -108,6 +108,10 @@ struct psl_plan {
 struct psl_batch {
     int64_t n_histories = 0;         // histories (or caller particles) covered
     int64_t first_history = 0;
+    int64_t stride = 1;              // histories first + i * stride
+    int lazy = 0;                    // 1: source stage runs inside transport_run
+    const psl_plan *plan = nullptr;  // lazy batches: the plan to read
+    psl_phantom_t phantom{};         // lazy batches: the phantom box
     uint64_t seed = 0;               // keys the particles' random streams
     Particle *p = nullptr;           // photons from the front, electrons from the back
     int64_t cap = 0;

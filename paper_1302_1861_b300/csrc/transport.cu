@@ -25,6 +25,7 @@
 
 #include "physics.cuh"
 #include "psl_internal.cuh"
+#include "source.cuh"
 
 namespace {
 
@@ -49,7 +50,7 @@ struct Tables {
 };
 
 struct Acc {
-    unsigned long long dep, esc, compton, photo, pair, steps, atomics, wsteps;
+    unsigned long long dep, esc, compton, photo, pair, steps, atomics, wsteps, emitted;
 };
 
 struct Args {
@@ -245,9 +246,9 @@ __device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, 
 // 4 photoelectric, 5 pair, 6 electron steps, 7 errors, 8 tally atomics of
 // photon passes, 9 tally atomics of electron passes, 10 Woodcock steps
 __device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int atomics_slot) {
-    unsigned long long v[8] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps, a.atomics, a.wsteps};
+    unsigned long long v[9] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps, a.atomics, a.wsteps, a.emitted};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 9; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
     }
@@ -260,6 +261,7 @@ __device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int atomics_slo
         if (v[5]) atomicAdd(&A.ledger[6], v[5]);
         if (v[6]) atomicAdd(&A.ledger[atomics_slot], v[6]);
         if (v[7]) atomicAdd(&A.ledger[10], v[7]);
+        if (v[8]) atomicAdd(&A.ledger[0], v[8]);
     }
 }
 
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
     const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     Photon g;
     bool alive = false, done = false;
     for (;;) {
@@ -366,15 +368,15 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
             base = __shfl_sync(FULL, base, leader);
             if (!alive && !done) {
                 const uint32_t idx = base + __popc(need & lt);
-                if (idx < n) {
+                if (idx >= n) {
+                    done = true;
+                } else {
                     const Particle p = load_particle(src + idx);
                     g.x = p.x; g.y = p.y; g.z = p.z; g.u = p.u; g.v = p.v; g.w = p.w; g.e = p.e; g.wt = p.wt;
                     g.p0 = p.pid_lo; g.p1 = p.pid_hi; g.root = p.root; g.nchild = 0;
                     g.rng.draw = 0;
                     photon_energy(A, g);
                     alive = true;
-                } else {
-                    done = true;
                 }
             }
         }
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
     const uint32_t n = min(*n_ptr, cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     Electron s;
     bool alive = false, done = false;
     for (;;) {
@@ -566,6 +568,52 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
         if (alive) alive = electron_event(A, acc, s);
     }
     flush_acc(A, acc, 9);
+}
+
+// ---------------------------------------------------------------- source ---
+// Source stage of a lazy batch (histories first + i * stride): accepted
+// photons are written to the primary buffer, charged primaries go straight to
+// the electron queue.  Each warp locates its first history and its lanes
+// reuse that (group, segment) when it is also theirs.
+__global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first, int64_t stride, uint32_t n,
+                                                uint32_t root0, Particle *out, uint32_t *count) {
+    __shared__ int64_t gs[1025];
+    for (int i = threadIdx.x; i <= P.n_groups; i += blockDim.x) gs[i] = P.group_start[i];
+    __syncthreads();
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int lane = threadIdx.x & 31;
+    const uint32_t gstride = gridDim.x * blockDim.x;
+    const uint32_t n_round = (n + 31u) & ~31u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += gstride) {
+        const bool ok = i < n;
+        const int64_t h = first + (int64_t)i * stride;
+        int g = -1;
+        int64_t q = -1;
+        if (lane == 0 && ok) locate(P, gs, h, g, q);
+        g = __shfl_sync(FULL, g, 0);
+        q = __shfl_sync(FULL, q, 0);
+        SrcOut o;
+        o.status = -1;
+        if (ok) {
+            locate_hinted(P, gs, h, g, q);
+            source_at(P, gs, h, g, q, o);
+        }
+        if (o.status == PSL_SRC_TRANSPORT || o.status == PSL_SRC_MISS) {
+            const unsigned long long e = fixed_point(o.s[6], o.s[7]);
+            acc.emitted += e;
+            if (o.status == PSL_SRC_MISS) acc.esc += e;
+        }
+        if (o.status == PSL_SRC_TRANSPORT) {
+            Particle c;
+            c.x = o.s[0]; c.y = o.s[1]; c.z = o.s[2]; c.e = o.s[6];
+            c.u = o.s[3]; c.v = o.s[4]; c.w = o.s[5]; c.wt = o.s[7];
+            c.pid_lo = (uint32_t)h; c.pid_hi = (uint32_t)((uint64_t)h >> 32);
+            c.type = (uint32_t)o.ptype; c.root = root0 + i;
+            if (o.ptype == 0) queue_push(Queue{out, count, n}, c, A.err);
+            else queue_push(A.e_out, c, A.err);
+        }
+    }
+    flush_acc(A, acc, 8);
 }
 
 // ------------------------------------------------------------ band sort ---
@@ -674,8 +722,9 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
 struct Workspace {
     int64_t chunk = 0;                 // primaries per chunk
     uint32_t cap_p = 0, cap_e = 0, cap_s = 0;
-    Particle *P[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr}, *S = nullptr;
-    uint32_t *cnt = nullptr;           // [0..1] P counts, [2..3] E counts, [4] S count, [5..8] heads,
+    Particle *P[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr}, *S = nullptr, *Q = nullptr;
+    uint32_t *cnt = nullptr;           // [0..1] P counts, [2..3] E counts, [4] S count, [5..6] heads,
+                                       // [7] primary photons,
                                        // [9] err, [16..47] band hist, [48..79] cursors
     float *mumax = nullptr;
     int *rmax = nullptr;
@@ -686,6 +735,7 @@ void workspace_free(Workspace *w) {
     if (!w) return;
     for (int k = 0; k < 2; ++k) { if (w->P[k]) cudaFree(w->P[k]); if (w->E[k]) cudaFree(w->E[k]); }
     if (w->S) cudaFree(w->S);
+    if (w->Q) cudaFree(w->Q);
     if (w->cnt) cudaFree(w->cnt);
     if (w->mumax) cudaFree(w->mumax);
     if (w->rmax) cudaFree(w->rmax);
@@ -709,6 +759,7 @@ static int workspace_ensure(psl_tally *t, int64_t chunk) {
     PSL_CUDA(cudaMalloc((void **)&w->E[0], (size_t)w->cap_e * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->E[1], (size_t)w->cap_e * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->S, (size_t)w->cap_s * sizeof(Particle)));
+    PSL_CUDA(cudaMalloc((void **)&w->Q, (size_t)base * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->cnt, 128 * sizeof(uint32_t)));
     PSL_CUDA(cudaMemset(w->cnt, 0, 128 * sizeof(uint32_t)));
     PSL_CUDA(cudaMalloc((void **)&w->mumax, NT * sizeof(float)));
@@ -724,6 +775,8 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
         return psl_fail(PSL_EINVAL, "transport_run: phantom does not match the tally");
     if (b < 0 || b >= tally->n_batches) return psl_fail(PSL_EINVAL, "transport_run: batch index out of range");
     if (batch->consumed) return psl_fail(PSL_EINVAL, "transport_run: batch already transported");
+    if (batch->lazy && (batch->phantom.nx != ph->nx || batch->phantom.ny != ph->ny || batch->phantom.nz != ph->nz))
+        return psl_fail(PSL_EINVAL, "transport_run: batch was sourced for another phantom");
     psl_physics_t P;
     psl_physics_default(&P);
     if (phys) P = *phys;
@@ -733,7 +786,8 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     TableCache tc;
     int rc = get_tables(P.wcc, P.wcb, st, tc);
     if (rc) return rc;
-    const int64_t nph = batch->n_photons, nel = batch->n_electrons;
+    const bool lazy = batch->lazy != 0;
+    const int64_t nph = lazy ? batch->n_histories : batch->n_photons, nel = lazy ? 0 : batch->n_electrons;
     const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::max(nph, nel), 1 << 24));
     if ((rc = workspace_ensure(tally, chunk))) return rc;
     Workspace *w = tally->ws;
@@ -766,7 +820,9 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     A.band_scale = (float)(NBANDS / log(20.0 / P.electron_cut));
 
     cudaMemsetAsync(w->cnt, 0, 128 * sizeof(uint32_t), st);
-    k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2)); PSL_NOTE_LAUNCH();
+    if (!lazy) { k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2)); PSL_NOTE_LAUNCH(); }
+    PlanDev srcP{};
+    if (lazy) srcP = make_plan_dev(batch->plan, &batch->phantom);
 
     const int sms = psl_sm_count();
     const int grid_t = sms * 4;                     // persistent transport grid
@@ -785,7 +841,11 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
         a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
         a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
         cudaMemsetAsync(head, 0, 4, st);
-        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_PHOTON, st, &tk_); k_photon<<<grid_t, 256, 0, st>>>(a2, src, nptr, nfix, cap, head); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_PHOTON, st, tk_); }
+        void *tk_ = nullptr;
+        if (psl_timer_on()) psl_timer_begin(PK_PHOTON, st, &tk_);
+        k_photon<<<grid_t, 256, 0, st>>>(a2, src, nptr, nfix, cap, head);
+        PSL_NOTE_LAUNCH();
+        if (tk_) psl_timer_end(PK_PHOTON, st, tk_);
     };
     auto electron_pass = [&]() {
         Args a2 = A;
@@ -801,8 +861,25 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
         const uint32_t ce = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(nel - a0, chunk));
         pc = 0; ec = 0;
         cudaMemsetAsync(w->cnt, 0, 5 * sizeof(uint32_t), st);
-        if (cp) photon_pass(batch->p + a0, nullptr, cp, cp);
-        band_sort(batch->p + (cap - a0 - ce), ce, w->E[ec], cE[ec], w->cap_e);
+        if (lazy) {
+            // source stage of histories first + (a0 + i) * stride
+            Args a2 = A;
+            a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
+            cudaMemsetAsync(w->cnt + 7, 0, 4, st);
+            {
+                void *tk_ = nullptr;
+                if (psl_timer_on()) psl_timer_begin(PK_SOURCE, st, &tk_);
+                k_source<<<grid_m, 256, 0, st>>>(a2, srcP, batch->first_history + a0 * batch->stride, batch->stride, cp,
+                                                 (uint32_t)a0, w->Q, w->cnt + 7);
+                PSL_NOTE_LAUNCH();
+                if (tk_) psl_timer_end(PK_SOURCE, st, tk_);
+            }
+            photon_pass(w->Q, w->cnt + 7, 0, cp);
+            band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
+        } else {
+            if (cp) photon_pass(batch->p + a0, nullptr, cp, cp);
+            band_sort(batch->p + (cap - a0 - ce), ce, w->E[ec], cE[ec], w->cap_e);
+        }
         electron_pass();
         int gen = 0;
         for (;; ++gen) {
