@@ -280,6 +280,29 @@ PSL_API int transport_trace(const psl_phantom_t *phantom, const psl_physics_t *p
                     psl_tally_t *tally, int32_t batch_index, int64_t *hist_dep, int64_t *hist_esc,
                     int32_t *hist_events, void *stream);
 
+/* Sec. 2.3.3, all fields of a plan in one call (the batched IMRT launch).
+ * Runs histories [first, first+n) of the plan as the tally's N_b batches
+ * (batch b takes histories first + b + k N_b, into tally slice b): source
+ * stage and transport of every beam/segment, with no host synchronisation
+ * between batches or secondary generations.  Each pass is followed by a fixed
+ * budget of 12 secondary generations whose kernels exit at once when their
+ * queue is empty.  use_graph = 1 records the whole sequence once as a CUDA
+ * graph (kept in the tally for this plan, range, phantom and settings) and
+ * replays it with a single launch on `stream`; the first such call sets up
+ * outside the capture.  Synchronises stream at the end; PSL_EOVERFLOW if a
+ * queue overflowed or secondaries were left after the budget. */
+PSL_API int psl_run(const psl_plan_t *plan, const psl_phantom_t *phantom, const psl_physics_t *physics,
+                    psl_tally_t *tally, int64_t first, int64_t n, int32_t use_graph, void *stream);
+
+/* Autotuner for psl_run: times n_probe histories of the plan with each
+ * candidate persistent-grid size (2, 3, 4, 6 blocks of 256 threads per SM)
+ * and queue depth (2^21 ... 2^24 primaries per transport pass), keeps the
+ * fastest in the tally (used by later transport calls on it), clears the
+ * tally, and returns the choice (host outputs, may be NULL). */
+PSL_API int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *phantom, const psl_physics_t *physics,
+                         psl_tally_t *tally, int64_t n_probe, int32_t *blocks_per_sm, int64_t *queue_depth,
+                         void *stream);
+
 /* Sec. 2.3.3 and 2.5.  dose[v] = norm * sum_b T_bv * 2^-32 MeV * 1.602176634e-13
  * J/MeV / (rho_v * voxel volume * 1e-3 kg), sigma[v] = the standard error of
  * the mean of the N_b batch estimates, ledger[0..2] = emitted, escaped,

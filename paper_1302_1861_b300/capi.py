@@ -26,7 +26,7 @@ EXPORTS = (
     "psl_batch_info", "psl_tally_create", "psl_tally_reset", "psl_tally_read", "transport_run",
     "transport_trace", "dose_readout", "psl_store_destroy", "psl_plan_destroy", "psl_batch_destroy",
     "psl_tally_destroy", "psl_last_error", "psl_kernel_launches", "psl_profile", "psl_profile_read",
-    "psl_build_static", "psl_atomic_peak",
+    "psl_build_static", "psl_atomic_peak", "psl_run", "psl_autotune",
 )
 STATIC_MAX_RECORDS = 1 << 20
 
@@ -107,6 +107,8 @@ def lib():
             "dose_readout": [vp, vp, f64, vp, vp, vp, vp],
             "psl_profile": [ctypes.c_int],
             "psl_atomic_peak": [i64, i64, vp, vp],
+            "psl_run": [vp, vp, vp, vp, i64, i64, i32, vp],
+            "psl_autotune": [vp, vp, vp, vp, i64, vp, vp, vp],
             "psl_profile_read": [i32, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -308,3 +310,16 @@ def transport_trace(phantom: Phantom, phys: Physics, batch: Batch, tally: Tally,
 def dose_readout(tally: Tally, phantom: Phantom, norm: float, dose=None, sigma=None, ledger=None, stream=None):
     check(lib().dose_readout(tally.h, ctypes.byref(phantom), float(norm), ptr(dose), ptr(sigma), ptr(ledger),
                              stream_ptr(stream)))
+
+
+def psl_run(plan: Plan, phantom: Phantom, phys: Physics, tally: Tally, first: int, n: int, use_graph: bool = False,
+            stream=None):
+    check(lib().psl_run(plan.h, ctypes.byref(phantom), ctypes.byref(phys), tally.h, int(first), int(n),
+                        1 if use_graph else 0, stream_ptr(stream)))
+
+
+def psl_autotune(plan: Plan, phantom: Phantom, phys: Physics, tally: Tally, n_probe: int, stream=None):
+    g, d = i32(), i64()
+    check(lib().psl_autotune(plan.h, ctypes.byref(phantom), ctypes.byref(phys), tally.h, int(n_probe),
+                             ctypes.byref(g), ctypes.byref(d), stream_ptr(stream)))
+    return g.value, d.value

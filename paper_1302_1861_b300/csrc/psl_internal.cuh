@@ -125,6 +125,8 @@ struct Workspace;
 struct psl_tally {
     int32_t nx = 0, ny = 0, nz = 0, n_batches = 0;
     int64_t nvox = 0;
+    int32_t grid_mult = 4;            // persistent transport grid: blocks per SM
+    int64_t chunk_cap = 1 << 24;      // primaries per transport pass (queue depth)
     unsigned long long *t = nullptr;  // [n_batches * nvox]
     unsigned long long *ledger = nullptr;  // [8]
     Workspace *ws = nullptr;

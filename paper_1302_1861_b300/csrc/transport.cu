@@ -20,7 +20,9 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "physics.cuh"
@@ -681,6 +683,9 @@ __global__ void __launch_bounds__(256) k_band_scatter(Args A, const Particle *a,
     }
 }
 
+// after a fixed generation budget: count particles that were left undone
+__global__ void k_accumulate_leftover(uint32_t *cnt) { cnt[12] += cnt[10] + cnt[11]; }
+
 __global__ void k_ledger_add(unsigned long long *ledger, const unsigned long long *src) {
     ledger[0] += src[0];
     ledger[1] += src[1];
@@ -720,19 +725,22 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
 }  // namespace
 
 struct Workspace {
-    int64_t chunk = 0;                 // primaries per chunk
+    int64_t chunk = 0;                 // primaries per pass the buffers are sized for
     uint32_t cap_p = 0, cap_e = 0, cap_s = 0;
     Particle *P[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr}, *S = nullptr, *Q = nullptr;
     uint32_t *cnt = nullptr;           // [0..1] P counts, [2..3] E counts, [4] S count, [5..6] heads,
-                                       // [7] primary photons,
-                                       // [9] err, [16..47] band hist, [48..79] cursors
+                                       // [7] primary photons, [9] err, [16..47] band hist, [48..79] cursors
     float *mumax = nullptr;
     int *rmax = nullptr;
-    uint32_t *host = nullptr;          // pinned: counts read back per generation
+    uint32_t *host = nullptr;          // pinned: counts read back
+    // cached CUDA graph of one psl_run call
+    cudaGraphExec_t graph = nullptr;
+    uint64_t graph_key[8] = {0};
 };
 
 void workspace_free(Workspace *w) {
     if (!w) return;
+    if (w->graph) cudaGraphExecDestroy(w->graph);
     for (int k = 0; k < 2; ++k) { if (w->P[k]) cudaFree(w->P[k]); if (w->E[k]) cudaFree(w->E[k]); }
     if (w->S) cudaFree(w->S);
     if (w->Q) cudaFree(w->Q);
@@ -768,142 +776,210 @@ static int workspace_ensure(psl_tally *t, int64_t chunk) {
     return PSL_OK;
 }
 
+// Secondary generations launched per pass when no host check is made
+#define RUN_GENERATIONS 12
+
+// One batch of work: either a lazy history range (source stage inside) or
+// caller / materialised particles.
+struct Job {
+    bool lazy = false;
+    PlanDev P{};
+    int64_t first = 0, stride = 1, n = 0;            // lazy
+    const Particle *p = nullptr;                     // materialised
+    int64_t nph = 0, nel = 0, cap = 0;
+    int32_t slice = 0;
+};
+
+struct Runner {
+    cudaStream_t st = nullptr;
+    psl_tally *tally = nullptr;
+    Workspace *w = nullptr;
+    Args A{};
+    bool timing = false;
+    int grid_t = 0, grid_m = 0;
+    int64_t chunk = 0;
+
+    int prepare(const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally *t, uint64_t seed, int64_t need,
+                cudaStream_t stream, bool capturing) {
+        psl_physics_t P;
+        psl_physics_default(&P);
+        if (phys) P = *phys;
+        if (!(P.electron_cut > 0.f) || !(P.photon_cut > 0.f) || !(P.wcc > P.electron_cut) || !(P.wcb > P.photon_cut))
+            return psl_fail(PSL_EINVAL, "transport: bad physics thresholds");
+        st = stream;
+        tally = t;
+        TableCache tc;
+        int rc;
+        if ((rc = get_tables(P.wcc, P.wcb, st, tc))) return rc;
+        chunk = std::max<int64_t>(1, std::min<int64_t>(need, t->chunk_cap));
+        if ((rc = workspace_ensure(t, chunk))) return rc;
+        w = t->ws;
+        const int64_t nvox = t->nvox;
+        cudaMemsetAsync(w->rmax, 0, 2 * sizeof(int), st);
+        k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax); PSL_NOTE_LAUNCH();
+        k_majorant<<<(NT + 255) / 256, 256, 0, st>>>(tc.ph0, tc.ph1, w->rmax, w->mumax); PSL_NOTE_LAUNCH();
+        A.nx = ph->nx; A.ny = ph->ny; A.nz = ph->nz;
+        A.vx = ph->vx; A.vy = ph->vy; A.vz = ph->vz;
+        A.ivx = 1.0f / ph->vx; A.ivy = 1.0f / ph->vy; A.ivz = 1.0f / ph->vz;
+        A.mat = ph->mat; A.rho = ph->rho;
+        A.pcut = P.photon_cut; A.ecut = P.electron_cut; A.wcc = P.wcc; A.wcb = P.wcb; A.flags = P.flags;
+        A.seed = seed;
+        A.k0 = (uint32_t)seed; A.k1 = (uint32_t)(seed >> 32);
+        A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.rng = tc.rng; A.tab.mumax = w->mumax;
+        A.tab.lnE0 = (float)log(T_LO);
+        A.tab.inv_dln = (float)((NT - 1) / (log(T_HI) - log(T_LO)));
+        A.ledger = t->ledger;
+        A.hist_dep = nullptr; A.hist_esc = nullptr; A.hist_events = nullptr;
+        A.err = w->cnt + 9;
+        A.band_ln0 = logf(P.electron_cut);
+        A.band_scale = (float)(NBANDS / log(20.0 / P.electron_cut));
+        cudaMemsetAsync(w->cnt, 0, 128 * sizeof(uint32_t), st);
+        timing = psl_timer_on() && !capturing;
+        grid_t = psl_sm_count() * t->grid_mult;
+        grid_m = psl_sm_count() * 8;
+        return PSL_OK;
+    }
+
+    // one batch; sync_gens: read the queue counts after each generation and
+    // stop when they are empty, else launch RUN_GENERATIONS generations
+    int run(const Job &J, bool sync_gens) {
+        A.tally = tally->t + (size_t)J.slice * tally->nvox;
+        uint32_t *cP[2] = {w->cnt + 0, w->cnt + 1}, *cE[2] = {w->cnt + 2, w->cnt + 3}, *cS = w->cnt + 4;
+        uint32_t *head = w->cnt + 5, *hist = w->cnt + 16, *cursor = w->cnt + 48;
+        int pc = 0, ec = 0;
+        auto tb = [&](int k, void **tok) { if (timing) psl_timer_begin(k, st, tok); };
+        auto te = [&](int k, void *tok) { if (tok) psl_timer_end(k, st, tok); };
+        auto band_sort = [&](const Particle *a, uint32_t na, const Particle *bq, const uint32_t *nb, uint32_t capb) {
+            void *tk = nullptr;
+            tb(PK_BAND, &tk);
+            k_band_count<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, hist); PSL_NOTE_LAUNCH();
+            k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
+            k_band_scatter<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH();
+            te(PK_BAND, tk);
+        };
+        auto photon_pass = [&](const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
+            Args a2 = A;
+            a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
+            a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
+            cudaMemsetAsync(head, 0, 4, st);
+            void *tk = nullptr;
+            tb(PK_PHOTON, &tk);
+            k_photon<<<grid_t, 256, 0, st>>>(a2, src, nptr, nfix, cap, head); PSL_NOTE_LAUNCH();
+            te(PK_PHOTON, tk);
+        };
+        auto electron_pass = [&]() {
+            Args a2 = A;
+            a2.e_out = Queue{w->E[ec ^ 1], cE[ec ^ 1], w->cap_e};
+            a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
+            cudaMemsetAsync(head + 1, 0, 4, st);
+            void *tk = nullptr;
+            tb(PK_ELECTRON, &tk);
+            k_electron<<<grid_t, 256, 0, st>>>(a2, w->S, cS, w->cap_s, head + 1); PSL_NOTE_LAUNCH();
+            te(PK_ELECTRON, tk);
+        };
+        const int64_t total = J.lazy ? J.n : std::max(J.nph, J.nel);
+        for (int64_t a0 = 0; a0 < total; a0 += chunk) {
+            pc = 0; ec = 0;
+            cudaMemsetAsync(w->cnt, 0, 5 * sizeof(uint32_t), st);
+            if (J.lazy) {
+                const uint32_t cp = (uint32_t)std::min<int64_t>(J.n - a0, chunk);
+                Args a2 = A;
+                a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
+                cudaMemsetAsync(w->cnt + 7, 0, 4, st);
+                void *tk = nullptr;
+                tb(PK_SOURCE, &tk);
+                k_source<<<grid_m, 256, 0, st>>>(a2, J.P, J.first + a0 * J.stride, J.stride, cp, (uint32_t)a0, w->Q,
+                                                 w->cnt + 7); PSL_NOTE_LAUNCH();
+                te(PK_SOURCE, tk);
+                photon_pass(w->Q, w->cnt + 7, 0, cp);
+                band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
+            } else {
+                const uint32_t cp = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(J.nph - a0, chunk));
+                const uint32_t ce = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(J.nel - a0, chunk));
+                if (cp) photon_pass(J.p + a0, nullptr, cp, cp);
+                band_sort(J.p + (J.cap - a0 - ce), ce, w->E[ec], cE[ec], w->cap_e);
+            }
+            electron_pass();
+            for (int gen = 0;; ++gen) {
+                if (sync_gens) {
+                    cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+                    cudaError_t e = cudaStreamSynchronize(st);
+                    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport: ") + cudaGetErrorString(e));
+                    if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport: particle queue overflow");
+                    if (w->host[pc ^ 1] == 0 && w->host[2 + (ec ^ 1)] == 0) break;
+                    if (gen >= MAX_GEN) return psl_fail(PSL_EOVERFLOW, "transport: too many secondary generations");
+                } else if (gen >= RUN_GENERATIONS) {
+                    break;
+                }
+                // next generation: swap current/next, clear the new "next"
+                pc ^= 1; ec ^= 1;
+                cudaMemsetAsync(cP[pc ^ 1], 0, 4, st);
+                cudaMemsetAsync(cE[ec ^ 1], 0, 4, st);
+                photon_pass(w->P[pc], cP[pc], 0, w->cap_p);
+                band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
+                electron_pass();
+            }
+            if (!sync_gens) {
+                // the last generation's output must be empty (checked by finish())
+                cudaMemcpyAsync(w->cnt + 10, cP[pc ^ 1], 4, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(w->cnt + 11, cE[ec ^ 1], 4, cudaMemcpyDeviceToDevice, st);
+                k_accumulate_leftover<<<1, 1, 0, st>>>(w->cnt); PSL_NOTE_LAUNCH();
+            }
+        }
+        return PSL_OK;
+    }
+
+    // wait, then report device-side errors and undrained queues
+    int finish() {
+        cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport: ") + cudaGetErrorString(e));
+        if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport: particle queue overflow");
+        if (w->host[12]) return psl_fail(PSL_EOVERFLOW, "transport: secondaries left after the generation budget");
+        return PSL_OK;
+    }
+};
+
+static int check_transport_args(const psl_phantom_t *ph, psl_tally_t *tally) {
+    if (!ph || !tally) return psl_fail(PSL_EINVAL, "transport: null argument");
+    if (ph->nx != tally->nx || ph->ny != tally->ny || ph->nz != tally->nz || !ph->mat || !ph->rho)
+        return psl_fail(PSL_EINVAL, "transport: phantom does not match the tally");
+    return PSL_OK;
+}
+
+static Job job_of(psl_batch_t *batch, int32_t slice) {
+    Job J;
+    J.slice = slice;
+    if (batch->lazy) {
+        J.lazy = true;
+        J.P = make_plan_dev(batch->plan, &batch->phantom);
+        J.first = batch->first_history; J.stride = batch->stride; J.n = batch->n_histories;
+    } else {
+        J.p = batch->p; J.nph = batch->n_photons; J.nel = batch->n_electrons; J.cap = batch->cap;
+    }
+    return J;
+}
+
 static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, psl_batch_t *batch, psl_tally_t *tally,
                           int32_t b, int64_t *hist_dep, int64_t *hist_esc, int32_t *hist_events, void *stream_) {
-    if (!ph || !batch || !tally) return psl_fail(PSL_EINVAL, "transport_run: null argument");
-    if (ph->nx != tally->nx || ph->ny != tally->ny || ph->nz != tally->nz || !ph->mat || !ph->rho)
-        return psl_fail(PSL_EINVAL, "transport_run: phantom does not match the tally");
+    int rc = check_transport_args(ph, tally);
+    if (rc) return rc;
+    if (!batch) return psl_fail(PSL_EINVAL, "transport_run: null batch");
     if (b < 0 || b >= tally->n_batches) return psl_fail(PSL_EINVAL, "transport_run: batch index out of range");
     if (batch->consumed) return psl_fail(PSL_EINVAL, "transport_run: batch already transported");
     if (batch->lazy && (batch->phantom.nx != ph->nx || batch->phantom.ny != ph->ny || batch->phantom.nz != ph->nz))
         return psl_fail(PSL_EINVAL, "transport_run: batch was sourced for another phantom");
-    psl_physics_t P;
-    psl_physics_default(&P);
-    if (phys) P = *phys;
-    if (!(P.electron_cut > 0.f) || !(P.photon_cut > 0.f) || !(P.wcc > P.electron_cut) || !(P.wcb > P.photon_cut))
-        return psl_fail(PSL_EINVAL, "transport_run: bad physics thresholds");
     cudaStream_t st = as_stream(stream_);
-    TableCache tc;
-    int rc = get_tables(P.wcc, P.wcb, st, tc);
-    if (rc) return rc;
-    const bool lazy = batch->lazy != 0;
-    const int64_t nph = lazy ? batch->n_histories : batch->n_photons, nel = lazy ? 0 : batch->n_electrons;
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(std::max(nph, nel), 1 << 24));
-    if ((rc = workspace_ensure(tally, chunk))) return rc;
-    Workspace *w = tally->ws;
+    Runner R;
+    const int64_t need = batch->lazy ? batch->n_histories : std::max(batch->n_photons, batch->n_electrons);
+    if ((rc = R.prepare(ph, phys, tally, batch->seed, need, st, false))) return rc;
+    R.A.hist_dep = (unsigned long long *)hist_dep;
+    R.A.hist_esc = (unsigned long long *)hist_esc;
+    R.A.hist_events = hist_events;
     batch->consumed = 1;
-
-    // majorant for this phantom
-    const int64_t nvox = tally->nvox;
-    cudaMemsetAsync(w->rmax, 0, 2 * sizeof(int), st);
-    k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax); PSL_NOTE_LAUNCH();
-    k_majorant<<<(NT + 255) / 256, 256, 0, st>>>(tc.ph0, tc.ph1, w->rmax, w->mumax); PSL_NOTE_LAUNCH();
-
-    Args A;
-    A.nx = ph->nx; A.ny = ph->ny; A.nz = ph->nz;
-    A.vx = ph->vx; A.vy = ph->vy; A.vz = ph->vz;
-    A.ivx = 1.0f / ph->vx; A.ivy = 1.0f / ph->vy; A.ivz = 1.0f / ph->vz;
-    A.mat = ph->mat; A.rho = ph->rho;
-    A.pcut = P.photon_cut; A.ecut = P.electron_cut; A.wcc = P.wcc; A.wcb = P.wcb; A.flags = P.flags;
-    A.seed = batch->seed;
-    A.k0 = (uint32_t)A.seed; A.k1 = (uint32_t)(A.seed >> 32);
-    A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.rng = tc.rng; A.tab.mumax = w->mumax;
-    A.tab.lnE0 = (float)log(T_LO);
-    A.tab.inv_dln = (float)((NT - 1) / (log(T_HI) - log(T_LO)));
-    A.tally = tally->t + (size_t)b * nvox;
-    A.ledger = tally->ledger;
-    A.hist_dep = (unsigned long long *)hist_dep;
-    A.hist_esc = (unsigned long long *)hist_esc;
-    A.hist_events = hist_events;
-    A.err = w->cnt + 9;
-    A.band_ln0 = logf(P.electron_cut);
-    A.band_scale = (float)(NBANDS / log(20.0 / P.electron_cut));
-
-    cudaMemsetAsync(w->cnt, 0, 128 * sizeof(uint32_t), st);
-    if (!lazy) { k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2)); PSL_NOTE_LAUNCH(); }
-    PlanDev srcP{};
-    if (lazy) srcP = make_plan_dev(batch->plan, &batch->phantom);
-
-    const int sms = psl_sm_count();
-    const int grid_t = sms * 4;                     // persistent transport grid
-    const int grid_m = sms * 8;                     // memory passes
-    uint32_t *cP[2] = {w->cnt + 0, w->cnt + 1}, *cE[2] = {w->cnt + 2, w->cnt + 3}, *cS = w->cnt + 4;
-    uint32_t *head = w->cnt + 5, *hist = w->cnt + 16, *cursor = w->cnt + 48;
-    int pc = 0, ec = 0;                             // index of the "current" buffers
-
-    auto band_sort = [&](const Particle *a, uint32_t na, const Particle *bq, const uint32_t *nb, uint32_t capb) {
-        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_BAND, st, &tk_); k_band_count<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, hist); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_BAND, st, tk_); }
-        k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
-        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_BAND, st, &tk_); k_band_scatter<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_BAND, st, tk_); }
-    };
-    auto photon_pass = [&](const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
-        Args a2 = A;
-        a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
-        a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
-        cudaMemsetAsync(head, 0, 4, st);
-        void *tk_ = nullptr;
-        if (psl_timer_on()) psl_timer_begin(PK_PHOTON, st, &tk_);
-        k_photon<<<grid_t, 256, 0, st>>>(a2, src, nptr, nfix, cap, head);
-        PSL_NOTE_LAUNCH();
-        if (tk_) psl_timer_end(PK_PHOTON, st, tk_);
-    };
-    auto electron_pass = [&]() {
-        Args a2 = A;
-        a2.e_out = Queue{w->E[ec ^ 1], cE[ec ^ 1], w->cap_e};
-        a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
-        cudaMemsetAsync(head + 1, 0, 4, st);
-        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_ELECTRON, st, &tk_); k_electron<<<grid_t, 256, 0, st>>>(a2, w->S, cS, w->cap_s, head + 1); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_ELECTRON, st, tk_); }
-    };
-
-    const int64_t cap = batch->cap;
-    for (int64_t a0 = 0; a0 < std::max(nph, nel); a0 += chunk) {
-        const uint32_t cp = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(nph - a0, chunk));
-        const uint32_t ce = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(nel - a0, chunk));
-        pc = 0; ec = 0;
-        cudaMemsetAsync(w->cnt, 0, 5 * sizeof(uint32_t), st);
-        if (lazy) {
-            // source stage of histories first + (a0 + i) * stride
-            Args a2 = A;
-            a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
-            cudaMemsetAsync(w->cnt + 7, 0, 4, st);
-            {
-                void *tk_ = nullptr;
-                if (psl_timer_on()) psl_timer_begin(PK_SOURCE, st, &tk_);
-                k_source<<<grid_m, 256, 0, st>>>(a2, srcP, batch->first_history + a0 * batch->stride, batch->stride, cp,
-                                                 (uint32_t)a0, w->Q, w->cnt + 7);
-                PSL_NOTE_LAUNCH();
-                if (tk_) psl_timer_end(PK_SOURCE, st, tk_);
-            }
-            photon_pass(w->Q, w->cnt + 7, 0, cp);
-            band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
-        } else {
-            if (cp) photon_pass(batch->p + a0, nullptr, cp, cp);
-            band_sort(batch->p + (cap - a0 - ce), ce, w->E[ec], cE[ec], w->cap_e);
-        }
-        electron_pass();
-        int gen = 0;
-        for (;; ++gen) {
-            cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-            cudaError_t e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport_run: ") + cudaGetErrorString(e));
-            if (w->host[9] & (PSL_DEV_ERR_QUEUE)) return psl_fail(PSL_EOVERFLOW, "transport_run: particle queue overflow");
-            const uint32_t np = w->host[pc ^ 1], ne = w->host[2 + (ec ^ 1)];
-            if (np == 0 && ne == 0) break;
-            if (gen >= MAX_GEN) return psl_fail(PSL_EOVERFLOW, "transport_run: too many secondary generations");
-            // next generation: swap current/next, clear the new "next"
-            pc ^= 1; ec ^= 1;
-            cudaMemsetAsync(cP[pc ^ 1], 0, 4, st);
-            cudaMemsetAsync(cE[ec ^ 1], 0, 4, st);
-            photon_pass(w->P[pc], cP[pc], 0, w->cap_p);
-            band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
-            electron_pass();
-        }
-    }
-    cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport_run: ") + cudaGetErrorString(e));
-    if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport_run: particle queue overflow");
-    return PSL_OK;
+    if (!batch->lazy) { k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2)); PSL_NOTE_LAUNCH(); }
+    if ((rc = R.run(job_of(batch, b), true))) return rc;
+    return R.finish();
 }
 
 extern "C" int transport_run(const psl_phantom_t *ph, const psl_physics_t *phys, psl_batch_t *batch, psl_tally_t *tally,
@@ -915,4 +991,122 @@ extern "C" int transport_trace(const psl_phantom_t *ph, const psl_physics_t *phy
                                psl_tally_t *tally, int32_t b, int64_t *hist_dep, int64_t *hist_esc,
                                int32_t *hist_events, void *stream) {
     return transport_impl(ph, phys, batch, tally, b, hist_dep, hist_esc, hist_events, stream);
+}
+
+// ---------------------------------------------------------------- psl_run --
+// All batches of a plan's history range, without host synchronisation.
+static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
+                    int64_t first, int64_t n, cudaStream_t st, bool capturing, Runner &R) {
+    const int nb = tally->n_batches;
+    const int64_t per_batch = (n + nb - 1) / nb;
+    int rc = R.prepare(ph, phys, tally, plan->seed, per_batch, st, capturing);
+    if (rc) return rc;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t cnt = std::max<int64_t>(0, (n - b + nb - 1) / nb);
+        if (!cnt) continue;
+        Job J;
+        J.lazy = true;
+        J.P = make_plan_dev(plan, ph);
+        J.first = first + b; J.stride = nb; J.n = cnt; J.slice = b;
+        if ((rc = R.run(J, false))) return rc;
+    }
+    return PSL_OK;
+}
+
+extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
+                       int64_t first, int64_t n, int32_t use_graph, void *stream_) {
+    int rc = check_transport_args(ph, tally);
+    if (rc) return rc;
+    if (!plan || first < 0 || n <= 0 || first + n > plan->n_histories)
+        return psl_fail(PSL_EINVAL, "psl_run: bad plan or history range");
+    if (plan->n_groups > 1024) return psl_fail(PSL_EINVAL, "psl_run: too many energy divisions");
+    cudaStream_t st = as_stream(stream_);
+    Runner R;
+    if (!use_graph) {
+        if ((rc = run_body(plan, ph, phys, tally, first, n, st, false, R))) return rc;
+        return R.finish();
+    }
+    psl_physics_t P;
+    psl_physics_default(&P);
+    if (phys) P = *phys;
+    uint64_t key[8] = {(uint64_t)(uintptr_t)plan, (uint64_t)first, (uint64_t)n, (uint64_t)(uintptr_t)ph->rho,
+                       (uint64_t)(uintptr_t)ph->mat, ((uint64_t)P.flags << 32) | (uint64_t)tally->grid_mult,
+                       (uint64_t)tally->chunk_cap, (uint64_t)plan->seed};
+    // workspace and tables are set up outside the capture
+    const int64_t per_batch = (n + tally->n_batches - 1) / tally->n_batches;
+    {
+        Runner pre;
+        if ((rc = pre.prepare(ph, phys, tally, plan->seed, per_batch, st, false))) return rc;
+        PSL_CUDA(cudaStreamSynchronize(st));
+    }
+    Workspace *w = tally->ws;
+    if (!w->graph || memcmp(w->graph_key, key, sizeof(key)) != 0) {
+        if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }
+        cudaStream_t cs;
+        PSL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            Runner C;
+            rc = run_body(plan, ph, phys, tally, first, n, cs, true, C);
+            e = cudaStreamEndCapture(cs, &g);
+        }
+        cudaStreamDestroy(cs);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("psl_run: capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&w->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { w->graph = nullptr; return psl_fail(PSL_ECUDA, std::string("psl_run: instantiate: ") + cudaGetErrorString(e)); }
+        memcpy(w->graph_key, key, sizeof(key));
+    }
+    PSL_CUDA(cudaGraphLaunch(w->graph, st));
+    PSL_NOTE_LAUNCH();
+    R.st = st; R.w = w; R.tally = tally;
+    return R.finish();
+}
+
+// ---------------------------------------------------------------- tuning --
+extern "C" int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys,
+                            psl_tally_t *tally, int64_t n_probe, int32_t *blocks_per_sm, int64_t *queue_depth,
+                            void *stream_) {
+    int rc = check_transport_args(ph, tally);
+    if (rc) return rc;
+    if (!plan || n_probe <= 0) return psl_fail(PSL_EINVAL, "psl_autotune: bad argument");
+    n_probe = std::min<int64_t>(n_probe, plan->n_histories);
+    cudaStream_t st = as_stream(stream_);
+    const int grids[] = {2, 3, 4, 6};
+    const int64_t depths[] = {1 << 21, 1 << 22, 1 << 23, 1 << 24};
+    float best = 1e30f;
+    int bg = tally->grid_mult;
+    int64_t bd = tally->chunk_cap;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (int gi : grids) {
+        for (int64_t d : depths) {
+            if (d > 2 * ((n_probe + tally->n_batches - 1) / tally->n_batches) && d != depths[0]) continue;
+            tally->grid_mult = gi;
+            tally->chunk_cap = d;
+            cudaEventRecord(a, st);
+            Runner R;
+            rc = run_body(plan, ph, phys, tally, 0, n_probe, st, false, R);
+            if (!rc) rc = R.finish();
+            cudaEventRecord(b, st);
+            if (rc) break;
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < best) { best = ms; bg = gi; bd = d; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    tally->grid_mult = bg;
+    tally->chunk_cap = bd;
+    if (rc) return rc;
+    if ((rc = psl_tally_reset(tally, stream_))) return rc;
+    if (blocks_per_sm) *blocks_per_sm = bg;
+    if (queue_depth) *queue_depth = bd;
+    return PSL_OK;
 }

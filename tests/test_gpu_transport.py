@@ -188,3 +188,57 @@ def test_determinism_and_batch_split():
     c = engine.run(dw, n_batches=1, readout=False, store=a["store"], plan=a["plan"])
     tc, _ = engine.raw_tallies(dw, c["tally"], 1)
     assert np.array_equal(ta, tc)
+
+
+def _tallies_of(dw, tally, nb):
+    t, lg = engine.raw_tallies(dw, tally, nb)
+    return t, lg
+
+
+@pytest.mark.parametrize("cfg", [1, 4])
+def test_psl_run_and_graph_match_per_batch_path(cfg):
+    """All batches in one call (no host synchronisation) and as one CUDA-graph
+    launch give the same integer tallies as batch-by-batch transport."""
+    w = inputs.config1(n_histories=60_000) if cfg == 1 else inputs.config4(n_records=300_000, n_histories=200_000)
+    w.n_batches = 4
+    dw = engine.upload(w)
+    ref = engine.run(dw, readout=False)
+    t_ref, l_ref = _tallies_of(dw, ref["tally"], 4)
+    phys = capi.physics()
+    tally = capi.psl_tally_create(dw.phantom, 4)
+    capi.psl_run(ref["plan"], dw.phantom, phys, tally, 0, w.n_histories, use_graph=False)
+    t1, l1 = _tallies_of(dw, tally, 4)
+    assert np.array_equal(t1, t_ref) and np.array_equal(l1[:11], l_ref[:11])
+    for _ in range(2):                                   # capture once, replay
+        capi.psl_tally_reset(tally)
+        capi.psl_run(ref["plan"], dw.phantom, phys, tally, 0, w.n_histories, use_graph=True)
+        t2, l2 = _tallies_of(dw, tally, 4)
+        assert np.array_equal(t2, t_ref) and np.array_equal(l2[:11], l_ref[:11])
+    emitted, escaped, deposited = l2[0], l2[1], l2[2]
+    assert abs(int(deposited) + int(escaped) - int(emitted)) <= 1e-6 * emitted
+
+
+def test_autotune_picks_a_candidate_and_clears_the_tally():
+    w = inputs.config1(n_histories=200_000)
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
+    tally = capi.psl_tally_create(dw.phantom, 10)
+    g, d = capi.psl_autotune(plan, dw.phantom, capi.physics(), tally, 100_000)
+    assert g in (2, 3, 4, 6) and d in (1 << 21, 1 << 22, 1 << 23, 1 << 24)
+    t, lg = _tallies_of(dw, tally, 10)
+    assert t.sum() == 0 and lg[:11].sum() == 0
+    # the tuned settings give the same integers as the defaults
+    capi.psl_run(plan, dw.phantom, capi.physics(), tally, 0, w.n_histories)
+    t1, _ = _tallies_of(dw, tally, 10)
+    ref = engine.run(dw, readout=False, store=store, plan=plan)
+    t2, _ = _tallies_of(dw, ref["tally"], 10)
+    assert np.array_equal(t1, t2)
+
+
+def test_imrt_plan_event_parity_sampled():
+    """Multi-segment IMRT plan (config-4 recipe, small phase space): per-history
+    parity with the oracle on a sampled range."""
+    w = inputs.config4(n_records=300_000, n_histories=1_000_000)
+    rate, _ = _event_parity(w, 1500, first=400_000)
+    assert rate >= 0.95
