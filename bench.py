@@ -179,6 +179,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-imrt", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -221,15 +223,21 @@ def main():
 
     tally = capi.psl_tally_create(dw.phantom, nb)       # device buffers held across steps
 
-    def step(dwx, out_dose):
+    def step(dwx, out_dose, plain=False):
+        """psl_build + psl_plan_create + all batches + dose_readout.  Default:
+        all batches in one psl_run call (no host synchronisation); plain:
+        psl_source_batch + transport_run batch by batch."""
         store = capi.psl_build(dwx.params, dwx.records)
         plan = capi.psl_plan_create(store, dwx.beams, w.sad, n_plan, w.seed)
         capi.psl_tally_reset(tally)
-        for b in range(nb):
-            f0, cnt, stride = engine.batch_histories(first, per_rank, nb, b)
-            batch = capi.psl_source_batch(plan, dwx.phantom, f0, cnt, stride)
-            capi.transport_run(dwx.phantom, phys, batch, tally, b)
-            batch.close()
+        if plain:
+            for b in range(nb):
+                f0, cnt, stride = engine.batch_histories(first, per_rank, nb, b)
+                batch = capi.psl_source_batch(plan, dwx.phantom, f0, cnt, stride)
+                capi.transport_run(dwx.phantom, phys, batch, tally, b)
+                batch.close()
+        else:
+            capi.psl_run(plan, dwx.phantom, phys, tally, first, per_rank)
         _, n_total, _ = plan.info()
         norm = engine.normalisation(n_total, per_rank, w.records.n)
         capi.dose_readout(tally, dwx.phantom, norm, out_dose[0], out_dose[1], out_dose[2])
@@ -270,6 +278,20 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
     value = per_rank * world / t_step
+
+    # the plain form (batch by batch, host checks per generation), for comparison
+    plain_times = []
+    for _ in range(0 if args.no_plain else 2):
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(dw, (dose, sigma, ledger), plain=True)
+        e1.record(stream)
+        barrier()
+        plain_times.append(e0.elapsed_time(e1) / 1e3)
+    t_plain = float(np.mean(plain_times[1:])) if plain_times else float("nan")
 
     # ledger and isocentre uncertainty of the last step
     lg = ledger.cpu().numpy()
@@ -334,6 +356,10 @@ def main():
                  "atomic_peak_per_s": atom_peak, "atomic_peak_kind": "measured: psl_atomic_peak, int64 adds into "
                                                                     f"{nvox} cells"}
 
+    imrt = None
+    if rank == 0 and world == 1 and not args.no_imrt:
+        imrt = imrt_run(capi, engine, inputs, torch)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
@@ -348,6 +374,9 @@ def main():
                                  "isocentre_rel_sigma_at_run": rel, "kind": "extrapolated from the run's sigma"},
                 "energy_balance": float((lg[1] + lg[2] - lg[0]) / lg[0]),
                 "transport": transport,
+                "modes": {"batched_psl_run": value, "plain_per_batch": per_rank * world / t_plain,
+                          "unit": "histories/s"},
+                "imrt_batched_graph": imrt,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
         print(json.dumps(line))
     if world > 1:
@@ -361,6 +390,50 @@ THREAD_INST_PER_ELECTRON_STEP = None
 THREAD_INST_PER_WOODCOCK_STEP = None
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
+
+
+def imrt_run(capi, engine, inputs, torch):
+    """The batched IMRT plan (7 gantry angles x 10-60 segments, per-segment
+    fluence, 4e7-record phase space, 128x128x100 CT-like phantom, 5e8
+    histories) as one CUDA-graph launch of psl_run: capture once, then time
+    the replays."""
+    w = inputs.config4()
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
+    tally = capi.psl_tally_create(dw.phantom, w.n_batches)
+    phys = capi.physics()
+    capi.psl_run(plan, dw.phantom, phys, tally, 0, w.n_histories, use_graph=True)     # capture + first run
+    times = []
+    for _ in range(2):
+        capi.psl_tally_reset(tally)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        capi.psl_run(plan, dw.phantom, phys, tally, 0, w.n_histories, use_graph=True)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    nz, ny, nx = w.phantom.shape
+    dose = torch.empty(nx * ny * nz, dtype=torch.float64, device="cuda")
+    sigma = torch.empty_like(dose)
+    lg = torch.empty(3, dtype=torch.float64, device="cuda")
+    n_entries, n_total, _ = plan.info()
+    capi.dose_readout(tally, dw.phantom, engine.normalisation(n_total, w.n_histories, w.records.n), dose, sigma, lg)
+    d = dose.view(nz, ny, nx).cpu().numpy()
+    sg = sigma.view(nz, ny, nx).cpu().numpy()
+    ic = ((np.array(w.beams[0].iso) - np.array(w.phantom.origin)) / np.array(w.phantom.voxel)).astype(int)[::-1]
+    sl = tuple(slice(c - 1, c + 2) for c in ic)
+    rel = float((sg[sl] / d[sl]).mean())
+    t = float(np.mean(times))
+    rate = w.n_histories / t
+    n1 = w.n_histories * (rel / 0.01) ** 2
+    lgh = lg.cpu().numpy()
+    return {"workload": w.name, "segments": len(w.beams), "psl_entries": n_entries, "histories": w.n_histories,
+            "seconds_per_plan": t, "histories_per_s": rate, "launch": "one CUDA graph (psl_run, use_graph=1)",
+            "isocentre_rel_sigma": rel, "time_to_1pct_s": n1 / rate,
+            "energy_balance": float((lgh[1] + lgh[2] - lgh[0]) / lgh[0])}
 
 
 def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kind, counts):

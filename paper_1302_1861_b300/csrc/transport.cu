@@ -52,7 +52,8 @@ struct Tables {
 };
 
 struct Acc {
-    unsigned long long dep, esc, compton, photo, pair, steps, atomics, wsteps, emitted;
+    unsigned long long dep, esc, emitted;                      // fixed-point energy
+    uint32_t compton, photo, pair, steps, atomics, wsteps;     // per-thread event counts
 };
 
 struct Args {
@@ -60,6 +61,7 @@ struct Args {
     float vx, vy, vz, ivx, ivy, ivz;
     const uint8_t *mat;
     const float *rho;
+    const float *mrho;        // rho, negated for bone (one load per lookup)
     float pcut, ecut, wcc, wcb;
     uint32_t flags;
     uint64_t seed;
@@ -90,35 +92,45 @@ __global__ void k_tables(float4 *ph0, float4 *ph1, float4 *el, double wcc, doubl
 }
 
 // CSDA range with the restricted stopping power: R_i = integral from T_0 to
-// T_i of dT/S (8-point Gauss-Legendre per interval, double), one thread
-__global__ void k_range_table(float2 *rt, double wcc, double wcb) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// T_i of dT/S, each interval by 8-point Gauss-Legendre in double (one thread
+// per interval), then a running sum
+__global__ void k_range_intervals(double *iv, double wcc, double wcb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NT) return;
     const double x8[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
     const double w8[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
     const double l0 = log(T_LO), dl = (log(T_HI) - log(T_LO)) / (NT - 1);
-    double R = 0.0, Tprev = T_LO;
+    if (i == 0) { iv[0] = 0.0; return; }
+    const double T = exp(l0 + dl * i), Tp = exp(l0 + dl * (i - 1));
+    const double m = 0.5 * (T + Tp), h = 0.5 * (T - Tp);
+    double acc = 0.0;
+    for (int k = 0; k < 4; ++k)
+        acc += w8[k] * (1.0 / el_stop_restricted(m - h * x8[k], wcc, wcb) + 1.0 / el_stop_restricted(m + h * x8[k], wcc, wcb));
+    iv[i] = h * acc;
+}
+
+__global__ void k_range_table(const double *iv, float2 *rt, double wcc, double wcb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double l0 = log(T_LO), dl = (log(T_HI) - log(T_LO)) / (NT - 1);
+    double R = 0.0;
     for (int i = 0; i < NT; ++i) {
+        R += iv[i];
         const double T = exp(l0 + dl * i);
-        if (i > 0) {
-            const double m = 0.5 * (T + Tprev), h = 0.5 * (T - Tprev);
-            double acc = 0.0;
-            for (int k = 0; k < 4; ++k)
-                acc += w8[k] * (1.0 / el_stop_restricted(m - h * x8[k], wcc, wcb) + 1.0 / el_stop_restricted(m + h * x8[k], wcc, wcb));
-            R += h * acc;
-        }
         rt[i] = make_float2((float)R, (float)(T * dl / el_stop_restricted(T, wcc, wcb)));
-        Tprev = T;
     }
 }
 
-__global__ void k_rho_max(const uint8_t *mat, const float *rho, int64_t n, int *out) {
+__global__ void k_rho_max(const uint8_t *mat, const float *rho, int64_t n, int *out, float *mrho) {
     __shared__ int m[2];
     if (threadIdx.x < 2) m[threadIdx.x] = 0;
     __syncthreads();
     int l0 = 0, l1 = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int r = __float_as_int(fmaxf(rho[i], 0.f));    // non-negative floats order as ints
-        if (mat[i]) l1 = max(l1, r); else l0 = max(l0, r);
+        const float ri = fmaxf(rho[i], 0.f);
+        int r = __float_as_int(ri);                     // non-negative floats order as ints
+        const bool bone = mat[i] != 0;
+        if (bone) l1 = max(l1, r); else l0 = max(l0, r);
+        mrho[i] = bone ? -ri : ri;
     }
     atomicMax(&m[0], l0);
     atomicMax(&m[1], l1);
@@ -152,12 +164,16 @@ __device__ __forceinline__ float lerp1(const float *a, int i, float f) {
 }
 
 // R(E): cubic Hermite in ln E with the exact node derivatives dR/dlnE = E/S
-__device__ __forceinline__ float range_of(const Tables &T, float E) {
-    int i; float f;
-    tab_pos(T, E, i, f);
+__device__ __forceinline__ float range_at(const Tables &T, int i, float f) {
     const float2 a = __ldg(T.rng + i), b = __ldg(T.rng + i + 1);
     const float f2 = f * f, f3 = f2 * f;
     return (2.f * f3 - 3.f * f2 + 1.f) * a.x + (f3 - 2.f * f2 + f) * a.y + (3.f * f2 - 2.f * f3) * b.x + (f3 - f2) * b.y;
+}
+
+__device__ __forceinline__ float range_of(const Tables &T, float E) {
+    int i; float f;
+    tab_pos(T, E, i, f);
+    return range_at(T, i, f);
 }
 
 __device__ __forceinline__ float stop_of(const Tables &T, float E) {
@@ -249,6 +265,7 @@ __device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, 
 // photon passes, 9 tally atomics of electron passes, 10 Woodcock steps
 __device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int atomics_slot) {
     unsigned long long v[9] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps, a.atomics, a.wsteps, a.emitted};
+    // (the 32-bit event counts widen here)
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
 #pragma unroll
@@ -295,9 +312,9 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
         return false;
     }
     const int64_t iv = ((int64_t)fz * A.ny + (int64_t)fy) * A.nx + (int64_t)fx;
-    const int m = __ldg(A.mat + iv);
-    const float rho = __ldg(A.rho + iv);
-    const float4 c = lerp4(m ? A.tab.ph1 : A.tab.ph0, g.ti, g.tf);
+    const float mr = __ldg(A.mrho + iv);
+    const float rho = fabsf(mr);
+    const float4 c = lerp4(mr < 0.0f ? A.tab.ph1 : A.tab.ph0, g.ti, g.tf);
     const float mc = rho * c.x, mpe = rho * c.y, mpp = rho * c.z;
     const float mu = mc + mpe + mpp;
     if (mu > g.mumax) atomicOr(A.err, 8u);
@@ -452,7 +469,7 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
     count_event(A, s.root);
     s.rng.align();                                                // the step's draws (scattering)
     const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
-    const float rho = __ldg(A.rho + iv);
+    const float rho = fabsf(__ldg(A.mrho + iv));
     int ti; float tf;
     tab_pos(A.tab, s.t, ti, tf);
     const float4 el = lerp4(A.tab.el, ti, tf);
@@ -476,7 +493,7 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
         }
     }
     const float tlim = fmaxf(0.9f * s.t, A.ecut);
-    const float s_max = (range_of(A.tab, s.t) - range_of(A.tab, tlim)) * __frcp_rn(rho);
+    const float s_max = (range_at(A.tab, ti, tf) - range_of(A.tab, tlim)) * __frcp_rn(rho);
     int which;
     float step;
     if (s_hard <= s_bound && s_hard <= s_max) { which = 0; step = s_hard; }
@@ -714,7 +731,12 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
     PSL_CUDA(cudaMalloc((void **)&t.el, NT * sizeof(float4)));
     PSL_CUDA(cudaMalloc((void **)&t.rng, NT * sizeof(float2)));
     k_tables<<<(NT + 255) / 256, 256, 0, st>>>(t.ph0, t.ph1, t.el, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
-    k_range_table<<<1, 32, 0, st>>>(t.rng, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    double *iv = nullptr;
+    PSL_CUDA(cudaMalloc((void **)&iv, NT * sizeof(double)));
+    k_range_intervals<<<(NT + 127) / 128, 128, 0, st>>>(iv, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    k_range_table<<<1, 32, 0, st>>>(iv, t.rng, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaStreamSynchronize(st));
+    cudaFree(iv);
     PSL_CUDA(cudaGetLastError());
     PSL_CUDA(cudaStreamSynchronize(st));
     g_tabs.push_back(t);
@@ -732,6 +754,8 @@ struct Workspace {
                                        // [7] primary photons, [9] err, [16..47] band hist, [48..79] cursors
     float *mumax = nullptr;
     int *rmax = nullptr;
+    float *mrho = nullptr;             // packed material/density of the phantom
+    int64_t nvox = 0;
     uint32_t *host = nullptr;          // pinned: counts read back
     // cached CUDA graph of one psl_run call
     cudaGraphExec_t graph = nullptr;
@@ -747,6 +771,7 @@ void workspace_free(Workspace *w) {
     if (w->cnt) cudaFree(w->cnt);
     if (w->mumax) cudaFree(w->mumax);
     if (w->rmax) cudaFree(w->rmax);
+    if (w->mrho) cudaFree(w->mrho);
     if (w->host) cudaFreeHost(w->host);
     delete w;
 }
@@ -772,12 +797,14 @@ static int workspace_ensure(psl_tally *t, int64_t chunk) {
     PSL_CUDA(cudaMemset(w->cnt, 0, 128 * sizeof(uint32_t)));
     PSL_CUDA(cudaMalloc((void **)&w->mumax, NT * sizeof(float)));
     PSL_CUDA(cudaMalloc((void **)&w->rmax, 2 * sizeof(int)));
+    PSL_CUDA(cudaMalloc((void **)&w->mrho, t->nvox * sizeof(float)));
+    w->nvox = t->nvox;
     PSL_CUDA(cudaMallocHost((void **)&w->host, 16 * sizeof(uint32_t)));
     return PSL_OK;
 }
 
 // Secondary generations launched per pass when no host check is made
-#define RUN_GENERATIONS 12
+#define RUN_GENERATIONS 10
 
 // One batch of work: either a lazy history range (source stage inside) or
 // caller / materialised particles.
@@ -816,12 +843,12 @@ struct Runner {
         w = t->ws;
         const int64_t nvox = t->nvox;
         cudaMemsetAsync(w->rmax, 0, 2 * sizeof(int), st);
-        k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax); PSL_NOTE_LAUNCH();
+        k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax, w->mrho); PSL_NOTE_LAUNCH();
         k_majorant<<<(NT + 255) / 256, 256, 0, st>>>(tc.ph0, tc.ph1, w->rmax, w->mumax); PSL_NOTE_LAUNCH();
         A.nx = ph->nx; A.ny = ph->ny; A.nz = ph->nz;
         A.vx = ph->vx; A.vy = ph->vy; A.vz = ph->vz;
         A.ivx = 1.0f / ph->vx; A.ivy = 1.0f / ph->vy; A.ivz = 1.0f / ph->vz;
-        A.mat = ph->mat; A.rho = ph->rho;
+        A.mat = ph->mat; A.rho = ph->rho; A.mrho = w->mrho;
         A.pcut = P.photon_cut; A.ecut = P.electron_cut; A.wcc = P.wcc; A.wcb = P.wcb; A.flags = P.flags;
         A.seed = seed;
         A.k0 = (uint32_t)seed; A.k1 = (uint32_t)(seed >> 32);
@@ -849,12 +876,16 @@ struct Runner {
         int pc = 0, ec = 0;
         auto tb = [&](int k, void **tok) { if (timing) psl_timer_begin(k, st, tok); };
         auto te = [&](int k, void *tok) { if (tok) psl_timer_end(k, st, tok); };
+        // generations after the first two are small: a smaller grid starts faster
+        int gen_now = 0;
+        auto gm = [&]() { return gen_now >= 2 ? psl_sm_count() : grid_m; };
+        auto gt = [&]() { return gen_now >= 2 ? psl_sm_count() : grid_t; };
         auto band_sort = [&](const Particle *a, uint32_t na, const Particle *bq, const uint32_t *nb, uint32_t capb) {
             void *tk = nullptr;
             tb(PK_BAND, &tk);
-            k_band_count<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, hist); PSL_NOTE_LAUNCH();
+            k_band_count<<<gm(), 256, 0, st>>>(A, a, na, bq, nb, capb, hist); PSL_NOTE_LAUNCH();
             k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
-            k_band_scatter<<<grid_m, 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH();
+            k_band_scatter<<<gm(), 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH();
             te(PK_BAND, tk);
         };
         auto photon_pass = [&](const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
@@ -864,7 +895,7 @@ struct Runner {
             cudaMemsetAsync(head, 0, 4, st);
             void *tk = nullptr;
             tb(PK_PHOTON, &tk);
-            k_photon<<<grid_t, 256, 0, st>>>(a2, src, nptr, nfix, cap, head); PSL_NOTE_LAUNCH();
+            k_photon<<<gt(), 256, 0, st>>>(a2, src, nptr, nfix, cap, head); PSL_NOTE_LAUNCH();
             te(PK_PHOTON, tk);
         };
         auto electron_pass = [&]() {
@@ -874,12 +905,13 @@ struct Runner {
             cudaMemsetAsync(head + 1, 0, 4, st);
             void *tk = nullptr;
             tb(PK_ELECTRON, &tk);
-            k_electron<<<grid_t, 256, 0, st>>>(a2, w->S, cS, w->cap_s, head + 1); PSL_NOTE_LAUNCH();
+            k_electron<<<gt(), 256, 0, st>>>(a2, w->S, cS, w->cap_s, head + 1); PSL_NOTE_LAUNCH();
             te(PK_ELECTRON, tk);
         };
         const int64_t total = J.lazy ? J.n : std::max(J.nph, J.nel);
         for (int64_t a0 = 0; a0 < total; a0 += chunk) {
             pc = 0; ec = 0;
+            gen_now = 0;
             cudaMemsetAsync(w->cnt, 0, 5 * sizeof(uint32_t), st);
             if (J.lazy) {
                 const uint32_t cp = (uint32_t)std::min<int64_t>(J.n - a0, chunk);
@@ -912,6 +944,7 @@ struct Runner {
                     break;
                 }
                 // next generation: swap current/next, clear the new "next"
+                gen_now = gen + 1;
                 pc ^= 1; ec ^= 1;
                 cudaMemsetAsync(cP[pc ^ 1], 0, 4, st);
                 cudaMemsetAsync(cE[ec ^ 1], 0, 4, st);
