@@ -208,8 +208,7 @@ def main():
     w = inputs.config2()
     per_rank = w.n_histories if args.histories is None else args.histories
     # weak scaling: rank r transports histories [r*N, (r+1)*N) of a plan of world*N histories
-    n_plan = per_rank * world
-    first = rank * per_rank
+    first, per_rank, n_plan = engine.shard_histories(rank, world, per_rank)
     nb = w.n_batches
     dw = engine.upload(w)
     stream = torch.cuda.current_stream()

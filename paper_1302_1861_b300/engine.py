@@ -65,6 +65,14 @@ def upload(w: Workload, device: str = "cuda", records=None) -> DeviceWorkload:
                           [xe, ye, ee])
 
 
+def shard_histories(rank: int, world: int, per_rank: int):
+    """Weak scaling over ranks: rank r transports histories [r N, (r+1) N) of
+    a plan of world * N histories.  Histories are independent, their random
+    streams are keyed by history id and the tally is an integer sum, so the
+    shards' tallies add up to the unsharded one exactly."""
+    return rank * per_rank, per_rank, world * per_rank
+
+
 def batch_histories(first: int, n: int, n_batches: int, b: int):
     """(first, count, stride) of batch b of the histories [first, first+n):
     every n_batches-th history, so each batch samples every energy division
