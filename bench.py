@@ -382,11 +382,15 @@ def main():
         dist.destroy_process_group()
 
 
-# Thread instructions per event of the transport kernels, measured with ncu
-# (smsp__thread_inst_executed.sum over all launches of a run / events of the
-# run); see profiles/.  None until measured for the current kernels.
-THREAD_INST_PER_ELECTRON_STEP = None
-THREAD_INST_PER_WOODCOCK_STEP = None
+# Per-event figures of the transport kernels measured with ncu on the 1e7-
+# history case of this workload (all launches of one run; the counts scale
+# with histories): thread instructions per event (smsp__thread_inst_executed
+# / events) and DRAM bytes per history (dram__bytes_read + write).  See
+# profiles/transport_k_electron_k_photon_psl-10x10-slab64.md.  They hold for
+# the kernels they were measured on; re-measure after changing the kernels.
+THREAD_INST_PER_ELECTRON_STEP = 537.1
+THREAD_INST_PER_WOODCOCK_STEP = 439.6
+DRAM_BYTES_PER_HISTORY = {"electron": 28.22, "photon": 40.06}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
 
@@ -463,10 +467,14 @@ def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kin
         events, ipe = counts[10], THREAD_INST_PER_WOODCOCK_STEP
     ach = events / per_step / per_launch_s / 1e9
     peak = THREAD_INST_PEAK / ipe / 1e9 if ipe else None
+    traffic = DRAM_BYTES_PER_HISTORY.get(name, 0.0) * per_rank / per_step
     return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gevents/s",
-            "frac": ach / peak if peak else None, "traffic": None, "per_launch_ms": per_launch_s * 1e3,
+            "frac": ach / peak if peak else None, "traffic": traffic, "per_launch_ms": per_launch_s * 1e3,
             "launches": launches, "events": "electron steps" if name == "electron" else "Woodcock steps",
-            "peak_kind": "derived: 148 SMs x 4 issue/clk x 32 lanes x 2.032 GHz / thread instructions per event"}
+            "events_per_launch": events / per_step,
+            "peak_kind": "derived: 148 SMs x 4 issue/clk x 32 lanes x 2.032 GHz / %.1f thread instructions "
+                         "per event (ncu)" % ipe,
+            "traffic_kind": "ncu dram bytes on the 1e7-history case scaled to the launch's histories"}
 
 
 if __name__ == "__main__":

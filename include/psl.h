@@ -284,12 +284,13 @@ PSL_API int transport_trace(const psl_phantom_t *phantom, const psl_physics_t *p
  * Runs histories [first, first+n) of the plan as the tally's N_b batches
  * (batch b takes histories first + b + k N_b, into tally slice b): source
  * stage and transport of every beam/segment, with no host synchronisation
- * between batches or secondary generations.  Each pass is followed by a fixed
- * budget of 12 secondary generations whose kernels exit at once when their
- * queue is empty.  use_graph = 1 records the whole sequence once as a CUDA
- * graph (kept in the tally for this plan, range, phantom and settings) and
- * replays it with a single launch on `stream`; the first such call sets up
- * outside the capture.  Synchronises stream at the end; PSL_EOVERFLOW if a
+ * between batches: each pass is followed by 3 secondary generations launched
+ * unchecked, after which the host reads the queue counts once per further
+ * generation (usually once per batch).  use_graph = 1 records the whole
+ * sequence once as a CUDA graph with a fixed budget of 10 generations per
+ * pass (kernels of an empty generation exit at once), keeps it in the tally
+ * for this plan, range, phantom and settings, and replays it with a single
+ * launch on `stream`; the first such call sets up outside the capture.  Synchronises stream at the end; PSL_EOVERFLOW if a
  * queue overflowed or secondaries were left after the budget. */
 PSL_API int psl_run(const psl_plan_t *plan, const psl_phantom_t *phantom, const psl_physics_t *physics,
                     psl_tally_t *tally, int64_t first, int64_t n, int32_t use_graph, void *stream);

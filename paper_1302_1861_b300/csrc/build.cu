@@ -74,9 +74,23 @@ __global__ void __launch_bounds__(256) k_key(psl_records_t r, Edges ed, uint32_t
         if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-// sorted records (AoS, 32 B) from the permutation
-__global__ void __launch_bounds__(256) k_gather(psl_records_t r, const uint32_t *__restrict__ perm, int64_t n_valid,
-                                                PslRecord *__restrict__ out) {
+// records packed as 32-byte AoS in input order (coalesced reads and writes),
+// so that the gather below reads one 32-byte record per sorted position
+// instead of seven scattered SoA elements
+__global__ void __launch_bounds__(256) k_pack(psl_records_t r, int64_t n, PslRecord *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        PslRecord o;
+        o.x = __ldg(r.x + i); o.y = __ldg(r.y + i); o.u = __ldg(r.u + i); o.v = __ldg(r.v + i);
+        o.e = __ldg(r.e + i); o.wt = __ldg(r.wt + i); o.src = (uint32_t)i; o.q = (int32_t)__ldg(r.q + i);
+        float4 *d = reinterpret_cast<float4 *>(out + i);
+        const float4 *sp = reinterpret_cast<const float4 *>(&o);
+        d[0] = sp[0]; d[1] = sp[1];
+    }
+}
+
+// sorted records straight from the caller's SoA arrays (no staging copy)
+__global__ void __launch_bounds__(256) k_gather_soa(psl_records_t r, const uint32_t *__restrict__ perm, int64_t n_valid,
+                                                    PslRecord *__restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_valid; i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t s = perm[i];
         PslRecord o;
@@ -85,6 +99,17 @@ __global__ void __launch_bounds__(256) k_gather(psl_records_t r, const uint32_t 
         float4 *d = reinterpret_cast<float4 *>(out + i);
         const float4 *sp = reinterpret_cast<const float4 *>(&o);
         d[0] = sp[0]; d[1] = sp[1];
+    }
+}
+
+// sorted records (AoS, 32 B) from the permutation
+__global__ void __launch_bounds__(256) k_gather(const PslRecord *__restrict__ packed, const uint32_t *__restrict__ perm,
+                                                int64_t n_valid, PslRecord *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_valid; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 *sp = reinterpret_cast<const float4 *>(packed + perm[i]);
+        float4 *d = reinterpret_cast<float4 *>(out + i);
+        const float4 a = __ldg(sp), b = __ldg(sp + 1);
+        d[0] = a; d[1] = b;
     }
 }
 
@@ -150,6 +175,7 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
 
     uint32_t *keys[2] = {nullptr, nullptr}, *vals[2] = {nullptr, nullptr}, *hist = nullptr;
     void *scratch = nullptr;
+    PslRecord *packed = nullptr;
     int64_t *nvalid_d = nullptr;
     int rc = PSL_OK;
     auto fail = [&](int code, const std::string &m) { rc = psl_fail(code, m); };
@@ -185,6 +211,13 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         int g2 = (int)std::min<int64_t>((int64_t)n / 256 + 1, (int64_t)sms * 8);
         k_offsets<<<g2, 256, 0, st>>>(skeys, n, n_bins, s->offsets); PSL_NOTE_LAUNCH();
         k_count_valid<<<1, 1, 0, st>>>(s->offsets, n_bins, nvalid_d); PSL_NOTE_LAUNCH();
+        if ((e = cudaMallocAsync((void **)&packed, (size_t)n * sizeof(PslRecord), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        {
+            void *tk_ = nullptr;
+            if (psl_timer_on()) psl_timer_begin(PK_GATHER, st, &tk_);
+            k_pack<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16), 256, 0, st>>>(*rec, n, packed); PSL_NOTE_LAUNCH();
+            if (tk_) psl_timer_end(PK_GATHER, st, tk_);
+        }
         int64_t nvalid = 0;
         uint32_t herr = 0;
         cudaMemcpyAsync(&nvalid, nvalid_d, 8, cudaMemcpyDeviceToHost, st);
@@ -195,13 +228,14 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         if ((e = cudaMallocAsync((void **)&s->rec, std::max<int64_t>(nvalid, 1) * sizeof(PslRecord), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
         if (nvalid > 0) {
             int g3 = (int)std::min<int64_t>((nvalid + 255) / 256, (int64_t)sms * 16);
-            { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_GATHER, st, &tk_); k_gather<<<g3, 256, 0, st>>>(*rec, svals, nvalid, s->rec); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_GATHER, st, tk_); }
+            { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_GATHER, st, &tk_); k_gather<<<g3, 256, 0, st>>>(packed, svals, nvalid, s->rec); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_GATHER, st, tk_); }
         }
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
     } while (0);
     for (int b = 0; b < 2; ++b) { if (keys[b]) cudaFreeAsync(keys[b], st); if (vals[b]) cudaFreeAsync(vals[b], st); }
     if (scratch) cudaFreeAsync(scratch, st);
     if (hist) cudaFreeAsync(hist, st);
+    if (packed) cudaFreeAsync(packed, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (rc == PSL_OK && e2 != cudaSuccess) rc = psl_fail(PSL_ECUDA, cudaGetErrorString(e2));
     if (rc != PSL_OK) { psl_store_destroy(s); return rc; }
@@ -369,7 +403,7 @@ extern "C" int psl_build_static(const psl_params_t *prm, const psl_records_t *re
     if (herr & PSL_DEV_ERR_TIMEOUT) return psl_fail(PSL_ETIMEOUT, "psl_build_static: look-back wait gave up");
     if (nvalid > 0) {
         int g3 = (int)std::min<int64_t>((nvalid + 255) / 256, (int64_t)sms * 16);
-        k_gather<<<g3, 256, 0, st>>>(*rec, svals, nvalid, reinterpret_cast<PslRecord *>(sorted)); PSL_NOTE_LAUNCH();
+        k_gather_soa<<<g3, 256, 0, st>>>(*rec, svals, nvalid, reinterpret_cast<PslRecord *>(sorted)); PSL_NOTE_LAUNCH();
     }
     PSL_CUDA(cudaGetLastError());
     PSL_CUDA(cudaStreamSynchronize(st));

@@ -867,9 +867,11 @@ struct Runner {
         return PSL_OK;
     }
 
-    // one batch; sync_gens: read the queue counts after each generation and
-    // stop when they are empty, else launch RUN_GENERATIONS generations
-    int run(const Job &J, bool sync_gens) {
+    // One batch.  check_from: the first generation after which the host reads
+    // the queue counts (and stops when they are empty); a negative value
+    // launches RUN_GENERATIONS generations with no host check (graph capture).
+    int run(const Job &J, int check_from) {
+        const bool sync_gens = check_from >= 0;
         A.tally = tally->t + (size_t)J.slice * tally->nvox;
         uint32_t *cP[2] = {w->cnt + 0, w->cnt + 1}, *cE[2] = {w->cnt + 2, w->cnt + 3}, *cS = w->cnt + 4;
         uint32_t *head = w->cnt + 5, *hist = w->cnt + 16, *cursor = w->cnt + 48;
@@ -933,14 +935,14 @@ struct Runner {
             }
             electron_pass();
             for (int gen = 0;; ++gen) {
-                if (sync_gens) {
+                if (sync_gens && gen >= check_from) {
                     cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
                     cudaError_t e = cudaStreamSynchronize(st);
                     if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport: ") + cudaGetErrorString(e));
                     if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport: particle queue overflow");
                     if (w->host[pc ^ 1] == 0 && w->host[2 + (ec ^ 1)] == 0) break;
                     if (gen >= MAX_GEN) return psl_fail(PSL_EOVERFLOW, "transport: too many secondary generations");
-                } else if (gen >= RUN_GENERATIONS) {
+                } else if (!sync_gens && gen >= RUN_GENERATIONS) {
                     break;
                 }
                 // next generation: swap current/next, clear the new "next"
@@ -1011,7 +1013,7 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     R.A.hist_events = hist_events;
     batch->consumed = 1;
     if (!batch->lazy) { k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2)); PSL_NOTE_LAUNCH(); }
-    if ((rc = R.run(job_of(batch, b), true))) return rc;
+    if ((rc = R.run(job_of(batch, b), 0))) return rc;
     return R.finish();
 }
 
@@ -1028,6 +1030,10 @@ extern "C" int transport_trace(const psl_phantom_t *ph, const psl_physics_t *phy
 
 // ---------------------------------------------------------------- psl_run --
 // All batches of a plan's history range, without host synchronisation.
+// Generations launched before the first host check in psl_run without a graph:
+// most batches finish within them, so a batch usually costs one host check.
+#define UNCHECKED_GENERATIONS 3
+
 static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
                     int64_t first, int64_t n, cudaStream_t st, bool capturing, Runner &R) {
     const int nb = tally->n_batches;
@@ -1041,7 +1047,7 @@ static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_p
         J.lazy = true;
         J.P = make_plan_dev(plan, ph);
         J.first = first + b; J.stride = nb; J.n = cnt; J.slice = b;
-        if ((rc = R.run(J, false))) return rc;
+        if ((rc = R.run(J, capturing ? -1 : UNCHECKED_GENERATIONS))) return rc;
     }
     return PSL_OK;
 }
