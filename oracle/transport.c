@@ -485,7 +485,7 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
         ix[k] = f < 0 ? 0 : (f >= n[k] ? n[k] - 1 : (int)f);
     }
     int hard_on = !(c->flags & F_NO_HARD);
-    double nlam = -log(uniform(&s));
+    double nlam = -1.0;             /* mean free paths to the next hard event; < 0: draw at the next step */
     double R = range_of(T, c->wcc, c->wcb);
     int steps = 0;
     for (;;) {
@@ -501,7 +501,8 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
         }
         a->ledger[L_ESTEPS]++;
         a->events++;
-        align_stream(&s);                                  /* the step's draws (scattering) */
+        align_stream(&s);                                  /* the step's draws */
+        if (nlam < 0.0) nlam = -log(uniform(&s));          /* a new mean free path count */
         double rho = c->rho[iv];
         double sig = hard_on ? rho * (ora_moller_sigma(T, c->wcc) + ora_brem_sigma(T, c->wcb)) : 0.0;
         double s_hard = sig > 0.0 ? nlam / sig : INFINITY;
@@ -572,7 +573,7 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
                 }
                 R = range_of(T, c->wcc, c->wcb);
             }
-            nlam = -log(uniform(&s));
+            nlam = -1.0;                                   /* drawn at the next step */
         }
     }
 }

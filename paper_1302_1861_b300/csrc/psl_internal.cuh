@@ -163,10 +163,24 @@ __host__ __device__ __forceinline__ u32x4 philox10(uint32_t c0, uint32_t c1, uin
     return {c0, c1, c2, c3};
 }
 
+// Philox4x32-10 with a precomputed key schedule rk[2r], rk[2r+1] = the key
+// of round r (the seed's words plus r times the Weyl constants).
+__device__ __forceinline__ u32x4 philox10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t *rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c0), lo0 = m0 * c0;
+        uint32_t hi1 = __umulhi(m1, c2), lo1 = m1 * c2;
+        uint32_t n0 = hi1 ^ c1 ^ rk[2 * r], n2 = hi0 ^ c3 ^ rk[2 * r + 1];
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return {c0, c1, c2, c3};
+}
+
 // Per-particle random stream: draw d uses word d%4 of block d/4 of
-// Philox(key = seed (k0, k1); counter = (d/4, TAG_PARTICLE, pid (p0, p1))).
-// Only the draw counter and the current block live in registers; the key and
-// the particle id are passed in.
+// Philox(key = seed; counter = (d/4, TAG_PARTICLE, pid (p0, p1))).
+// Only the draw counter and the current block live in registers; the key
+// schedule and the particle id are passed in.
 struct Rng {
     uint32_t draw;
     u32x4 blk;
@@ -174,9 +188,9 @@ struct Rng {
     // boundary, so the lanes of a warp compute their blocks together
     __device__ __forceinline__ void align() { draw = (draw + 3u) & ~3u; }
     // ((r >> 9) + 0.5) * 2^-23: 24 significant bits, exact in float
-    __device__ __forceinline__ float next(uint32_t k0, uint32_t k1, uint32_t p0, uint32_t p1) {
+    __device__ __forceinline__ float next(const uint32_t *rk, uint32_t p0, uint32_t p1) {
         uint32_t w = draw & 3u;
-        if (w == 0) blk = philox10(draw >> 2, TAG_PARTICLE, p0, p1, k0, k1);
+        if (w == 0) blk = philox10_rk(draw >> 2, TAG_PARTICLE, p0, p1, rk);
         uint32_t r = w == 0 ? blk.a : (w == 1 ? blk.b : (w == 2 ? blk.c : blk.d));
         ++draw;
         return ((float)(r >> 9) + 0.5f) * (1.0f / 8388608.0f);

@@ -47,8 +47,10 @@ struct Tables {
     const float4 *ph0, *ph1;   // material 0/1: mu_c, mu_pe, mu_pp, mu_total (cm^2/g)
     const float4 *el;          // S_restricted (MeV cm^2/g), sigma_moller, sigma_brem (cm^2/g), 0
     const float2 *rng;         // CSDA range R (g/cm^2) and dR/dlnT * dlnT at each node
+    const float *irng;         // ln T at uniform steps of ln R (inverse range)
     const float *mumax;        // majorant (1/cm), phantom dependent
     float lnE0, inv_dln;
+    float lnR0, inv_dlnR;      // grid of the inverse range table
 };
 
 struct Acc {
@@ -66,6 +68,7 @@ struct Args {
     uint32_t flags;
     uint64_t seed;
     uint32_t k0, k1;          // the seed's two words (Philox key)
+    uint32_t rk[20];          // Philox key schedule of the seed
     Tables tab;
     unsigned long long *tally;
     unsigned long long *ledger;
@@ -109,15 +112,29 @@ __global__ void k_range_intervals(double *iv, double wcc, double wcb) {
     iv[i] = h * acc;
 }
 
-__global__ void k_range_table(const double *iv, float2 *rt, double wcc, double wcb) {
+__global__ void k_range_table(double *iv, float2 *rt, float *irt, float *igrid, double wcc, double wcb) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double l0 = log(T_LO), dl = (log(T_HI) - log(T_LO)) / (NT - 1);
     double R = 0.0;
     for (int i = 0; i < NT; ++i) {
         R += iv[i];
+        iv[i] = R;                                   // keep the cumulative range for the inverse
         const double T = exp(l0 + dl * i);
         rt[i] = make_float2((float)R, (float)(T * dl / el_stop_restricted(T, wcc, wcb)));
     }
+    // inverse: ln T at NT uniform points of ln R over [R_1, R_{NT-1}], by
+    // interpolating ln T linearly in ln R between the forward nodes
+    const double a = log(iv[1]), b = log(iv[NT - 1]), dr = (b - a) / (NT - 1);
+    int i = 1;
+    for (int j = 0; j < NT; ++j) {
+        const double lr = a + dr * j;
+        while (i < NT - 2 && log(iv[i + 1]) < lr) ++i;
+        const double r0 = log(iv[i]), r1 = log(iv[i + 1]);
+        const double f = (lr - r0) / (r1 - r0);
+        irt[j] = (float)(l0 + dl * (i + f));
+    }
+    igrid[0] = (float)a;
+    igrid[1] = (float)(1.0 / dr);
 }
 
 __global__ void k_rho_max(const uint8_t *mat, const float *rho, int64_t n, int *out, float *mrho) {
@@ -237,7 +254,7 @@ __device__ __forceinline__ void push_particle(const Queue &q, const Args &A, uin
 __device__ __forceinline__ void annihilate(const Args &A, Rng &rng, float x, float y, float z, float wt, uint32_t p0, uint32_t p1,
                            uint32_t &nchild, uint32_t root) {
     rng.align();
-    float cth = 2.0f * rng.next(A.k0, A.k1, p0, p1) - 1.0f, phi = F_TWO_PI * rng.next(A.k0, A.k1, p0, p1);
+    float cth = 2.0f * rng.next(A.rk, p0, p1) - 1.0f, phi = F_TWO_PI * rng.next(A.rk, p0, p1);
     float sth = sqrtf(fmaxf(0.0f, 1.0f - cth * cth)), sp, cp;
     __sincosf(phi, &sp, &cp);
     float a0 = sth * cp, a1 = sth * sp, a2 = cth;
@@ -304,7 +321,7 @@ __device__ __forceinline__ void photon_energy(const Args &A, Photon &g) {
 __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g) {
     acc.wsteps++;
     g.rng.align();                                                // Woodcock step: step, virtual, channel
-    const float s = -__logf(g.rng.next(A.k0, A.k1, g.p0, g.p1)) * g.inv_mumax;
+    const float s = -__logf(g.rng.next(A.rk, g.p0, g.p1)) * g.inv_mumax;
     g.x += s * g.u; g.y += s * g.v; g.z += s * g.w;
     const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
     if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)A.nx && fy < (float)A.ny && fz < (float)A.nz)) {
@@ -318,9 +335,9 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
     const float mc = rho * c.x, mpe = rho * c.y, mpp = rho * c.z;
     const float mu = mc + mpe + mpp;
     if (mu > g.mumax) atomicOr(A.err, 8u);
-    if (g.rng.next(A.k0, A.k1, g.p0, g.p1) * g.mumax >= mu) return true;           // virtual interaction
+    if (g.rng.next(A.rk, g.p0, g.p1) * g.mumax >= mu) return true;           // virtual interaction
     count_event(A, g.root);
-    const float r = g.rng.next(A.k0, A.k1, g.p0, g.p1) * mu;
+    const float r = g.rng.next(A.rk, g.p0, g.p1) * mu;
     g.rng.align();                                                // the interaction's draws
     const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
     if (r < mc) {                                                 // Compton (Kahn's method)
@@ -330,7 +347,7 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
         const float p_first = __fdividef(1.0f + 2.0f * k, 9.0f + 2.0f * k);
         float x = 1.0f, ix = 1.0f;
         for (int it = 0; it < 1000; ++it) {
-            const float r1 = g.rng.next(A.k0, A.k1, g.p0, g.p1), r2 = g.rng.next(A.k0, A.k1, g.p0, g.p1), r3 = g.rng.next(A.k0, A.k1, g.p0, g.p1);
+            const float r1 = g.rng.next(A.rk, g.p0, g.p1), r2 = g.rng.next(A.rk, g.p0, g.p1), r3 = g.rng.next(A.rk, g.p0, g.p1);
             if (r1 <= p_first) {
                 x = 1.0f + 2.0f * k * r2;
                 ix = __frcp_rn(x);
@@ -343,7 +360,7 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
             }
         }
         const float cth = fminf(1.0f, fmaxf(-1.0f, 1.0f - (x - 1.0f) * ik));
-        const float ep = g.e * ix, phi = F_TWO_PI * g.rng.next(A.k0, A.k1, g.p0, g.p1);
+        const float ep = g.e * ix, phi = F_TWO_PI * g.rng.next(A.rk, g.p0, g.p1);
         float nu = g.u, nv = g.v, nw = g.w;
         rotate_dir(nu, nv, nw, cth, phi);
         const float te = g.e - ep;
@@ -363,7 +380,7 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
     }
     acc.pair++;                                                    // pair production
     if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
-    const float avail = g.e - 2.0f * F_ME, eps = g.rng.next(A.k0, A.k1, g.p0, g.p1);
+    const float avail = g.e - 2.0f * F_ME, eps = g.rng.next(A.rk, g.p0, g.p1);
     const float t1 = eps * avail, t2 = avail - t1;
     emit_charged(A, acc, g.rng, 1, t1, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
     emit_charged(A, acc, g.rng, 2, t2, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
@@ -421,7 +438,17 @@ __device__ __forceinline__ float highland(float T, float s, float rho) {
     const float bcp = __fdividef(T * (T + 2.0f * F_ME), T + F_ME);
     const float f = 1.0f + 0.038f * __logf(t);
     if (!(f > 0.0f)) return 0.0f;
-    return __fdividef(13.6f, bcp) * sqrtf(t) * f;
+    return __fdividef(13.6f, bcp) * (t * rsqrtf(t)) * f;
+}
+
+// energy whose CSDA range is r (g/cm^2): the inverse range table
+__device__ __forceinline__ float energy_of_range(const Tables &T, float r) {
+    float x = (__logf(r) - T.lnR0) * T.inv_dlnR;
+    x = fminf(fmaxf(x, 0.0f), (float)(NT - 1) - 1e-3f);
+    const int i = (int)x;
+    const float f = x - (float)i;
+    const float a = __ldg(T.irng + i), b = __ldg(T.irng + i + 1);
+    return __expf(a + f * (b - a));
 }
 
 // energy after a path h (g/cm^2): RK4 on dT/dh = -S(T), k1 = S(t) given
@@ -432,14 +459,14 @@ __device__ __forceinline__ float energy_after(const Tables &T, float t, float h,
     return t - h * (k1 + 2.0f * k2 + 2.0f * k3 + k4) * (1.0f / 6.0f);
 }
 
-__device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, uint32_t k0, uint32_t k1, uint32_t p0,
+__device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, const uint32_t *rk, uint32_t p0,
                                                uint32_t p1, uint32_t *err) {
     const float tau = T / F_ME, ec = wcc / T;
     const float g = (tau / (tau + 1.0f)) * (tau / (tau + 1.0f));
     const float a = (2.0f * tau + 1.0f) / ((tau + 1.0f) * (tau + 1.0f));
     const float w1 = 1.0f / ec - 2.0f, w2 = 5.0f * (0.5f - ec);
     for (int it = 0; it < 1000; ++it) {
-        const float r1 = rng.next(k0, k1, p0, p1), r2 = rng.next(k0, k1, p0, p1), r3 = rng.next(k0, k1, p0, p1);
+        const float r1 = rng.next(rk, p0, p1), r2 = rng.next(rk, p0, p1), r3 = rng.next(rk, p0, p1);
         const float e = (r1 * (w1 + w2) < w1) ? ec / (1.0f - r2 * (1.0f - 2.0f * ec)) : ec + r2 * (0.5f - ec);
         const float q = e / (1.0f - e);
         const float f = 1.0f + q * q + g * e * e - a * q;
@@ -467,7 +494,8 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
     }
     acc.steps++;
     count_event(A, s.root);
-    s.rng.align();                                                // the step's draws (scattering)
+    s.rng.align();                                                // the step's draws
+    if (s.nlam < 0.0f) s.nlam = -__logf(s.rng.next(A.rk, s.p0, s.p1));   // a new mean free path count
     const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
     const float rho = fabsf(__ldg(A.mrho + iv));
     int ti; float tf;
@@ -493,21 +521,24 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
         }
     }
     const float tlim = fmaxf(0.9f * s.t, A.ecut);
-    const float s_max = (range_at(A.tab, ti, tf) - range_of(A.tab, tlim)) * __frcp_rn(rho);
+    const float r_t = range_at(A.tab, ti, tf);
+    const float s_max = (r_t - range_of(A.tab, tlim)) * __frcp_rn(rho);
     int which;
     float step;
     if (s_hard <= s_bound && s_hard <= s_max) { which = 0; step = s_hard; }
     else if (s_bound <= s_max) { which = 1; step = s_bound; }
     else { which = 2; step = s_max; }
-    float tend = which == 2 ? tlim : fmaxf(energy_after(A.tab, s.t, rho * step, el.x), tlim);
+    // energy at the end of the step: the 10 % limit exactly, else from the range
+    float tend = which == 2 ? tlim : fmaxf(energy_of_range(A.tab, r_t - rho * step), tlim);
     const float th0 = highland(s.t, step, rho);
     deposit(A, acc, iv, s.t - tend, s.wt, s.root);
     s.t = tend;
     s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
     s.nlam -= step * sig;
     if (!(A.flags & PSL_PHYS_NO_MSC) && step > 0.0f) {
-        const float th = th0 * sqrtf(-2.0f * __logf(s.rng.next(A.k0, A.k1, s.p0, s.p1)));
-        const float phi = F_TWO_PI * s.rng.next(A.k0, A.k1, s.p0, s.p1);
+        const float l2 = -2.0f * __logf(s.rng.next(A.rk, s.p0, s.p1));
+        const float th = th0 * (l2 * rsqrtf(l2));
+        const float phi = F_TWO_PI * s.rng.next(A.rk, s.p0, s.p1);
         rotate_dir(s.u, s.v, s.w, __cosf(th), phi);
     }
     if (which == 1) {
@@ -525,27 +556,27 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
         const float4 e2 = lerp4(A.tab.el, tj, tg);
         const float sm = s.t > 2.0f * A.wcc ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
         s.rng.align();                                            // the hard event's draws
-        const float r = s.rng.next(A.k0, A.k1, s.p0, s.p1) * (sm + sb);
+        const float r = s.rng.next(A.rk, s.p0, s.p1) * (sm + sb);
         if (sm + sb > 0.0f) {
             if (r < sm) {                                         // hard Moller
-                const float eps = sample_moller(s.t, A.wcc, s.rng, A.k0, A.k1, s.p0, s.p1, A.err);
+                const float eps = sample_moller(s.t, A.wcc, s.rng, A.rk, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
                 const float cp = sqrtf(tp * (s.t + 2.0f * F_ME) / (s.t * (tp + 2.0f * F_ME)));
                 const float cd = sqrtf(W * (s.t + 2.0f * F_ME) / (s.t * (W + 2.0f * F_ME)));
-                const float phi = F_TWO_PI * s.rng.next(A.k0, A.k1, s.p0, s.p1);
+                const float phi = F_TWO_PI * s.rng.next(A.rk, s.p0, s.p1);
                 float du = s.u, dv = s.v, dw = s.w;
                 rotate_dir(du, dv, dw, cd, phi + 3.14159265358979f);
                 rotate_dir(s.u, s.v, s.w, cp, phi);
                 emit_charged(A, acc, s.rng, 1, W, s.x, s.y, s.z, du, dv, dw, s.wt, iv, s.p0, s.p1, s.nchild, s.root);
                 s.t = tp;
             } else {                                              // hard bremsstrahlung
-                const float kph = A.wcb * expf(s.rng.next(A.k0, A.k1, s.p0, s.p1) * logf(s.t / A.wcb));
+                const float kph = A.wcb * expf(s.rng.next(A.rk, s.p0, s.p1) * logf(s.t / A.wcb));
                 if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) deposit(A, acc, iv, kph, s.wt, s.root);
                 else push_particle(A.p_out, A, 0, s.x, s.y, s.z, s.u, s.v, s.w, kph, s.wt, s.p0, s.p1, s.nchild, s.root);
                 s.t -= kph;
             }
         }
-        s.nlam = -__logf(s.rng.next(A.k0, A.k1, s.p0, s.p1));
+        s.nlam = -1.0f;                                           // drawn at the next step
     }
     return true;
 }
@@ -576,7 +607,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     s.iy = min(max((int)floorf(s.y * A.ivy), 0), A.ny - 1);
                     s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
                     s.rng.draw = 0;
-                    s.nlam = -__logf(s.rng.next(A.k0, A.k1, s.p0, s.p1));
+                    s.nlam = -1.0f;                               // drawn at the first step
                     alive = true;
                 } else {
                     done = true;
@@ -714,6 +745,8 @@ struct TableCache {
     float wcc = -1.f, wcb = -1.f;
     float4 *ph0 = nullptr, *ph1 = nullptr, *el = nullptr;
     float2 *rng = nullptr;
+    float *irng = nullptr;
+    float igrid[2] = {0.f, 0.f};
 };
 std::mutex g_tab_mu;
 std::vector<TableCache> g_tabs;
@@ -732,11 +765,16 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
     PSL_CUDA(cudaMalloc((void **)&t.rng, NT * sizeof(float2)));
     k_tables<<<(NT + 255) / 256, 256, 0, st>>>(t.ph0, t.ph1, t.el, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
     double *iv = nullptr;
+    float *ig = nullptr;
     PSL_CUDA(cudaMalloc((void **)&iv, NT * sizeof(double)));
+    PSL_CUDA(cudaMalloc((void **)&ig, 2 * sizeof(float)));
+    PSL_CUDA(cudaMalloc((void **)&t.irng, NT * sizeof(float)));
     k_range_intervals<<<(NT + 127) / 128, 128, 0, st>>>(iv, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
-    k_range_table<<<1, 32, 0, st>>>(iv, t.rng, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    k_range_table<<<1, 32, 0, st>>>(iv, t.rng, t.irng, ig, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaMemcpyAsync(t.igrid, ig, 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
     PSL_CUDA(cudaStreamSynchronize(st));
     cudaFree(iv);
+    cudaFree(ig);
     PSL_CUDA(cudaGetLastError());
     PSL_CUDA(cudaStreamSynchronize(st));
     g_tabs.push_back(t);
@@ -852,7 +890,12 @@ struct Runner {
         A.pcut = P.photon_cut; A.ecut = P.electron_cut; A.wcc = P.wcc; A.wcb = P.wcb; A.flags = P.flags;
         A.seed = seed;
         A.k0 = (uint32_t)seed; A.k1 = (uint32_t)(seed >> 32);
+        for (int r = 0; r < 10; ++r) {
+            A.rk[2 * r] = A.k0 + (uint32_t)r * 0x9E3779B9u;
+            A.rk[2 * r + 1] = A.k1 + (uint32_t)r * 0xBB67AE85u;
+        }
         A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.rng = tc.rng; A.tab.mumax = w->mumax;
+        A.tab.irng = tc.irng; A.tab.lnR0 = tc.igrid[0]; A.tab.inv_dlnR = tc.igrid[1];
         A.tab.lnE0 = (float)log(T_LO);
         A.tab.inv_dln = (float)((NT - 1) / (log(T_HI) - log(T_LO)));
         A.ledger = t->ledger;
