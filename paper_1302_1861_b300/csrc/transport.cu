@@ -301,6 +301,114 @@ __device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int atomics_slo
     }
 }
 
+// ------------------------------------------------------------ warp feed ---
+// A warp claims queue entries 32 at a time and stages each chunk in shared
+// memory with one bulk asynchronous copy (cp.async.bulk completing on an
+// mbarrier), one chunk ahead of use.  A lane that needs a new particle then
+// reads it from shared memory instead of waiting on HBM.  The current chunk
+// is always resident; its successor is in flight or resident.
+#define FEED_CHUNK 32
+#define FEED_WARPS 8                     // 256-thread blocks
+#define FEED_SPIN (1u << 22)
+
+struct FeedSmem {
+    Particle buf[FEED_WARPS][2][FEED_CHUNK];
+    unsigned long long bar[FEED_WARPS][2];
+};
+
+// Per-warp state, packed in one register: bits 0-5 and 6-11 the particle
+// counts of buffers 0 and 1, 12-17 the read position in the current buffer,
+// 18 the current buffer, 19-20 the mbarrier phase of each buffer.
+struct Feed {
+    uint32_t st;
+
+    __device__ __forceinline__ uint32_t cnt(uint32_t b) const { return (st >> (6u * b)) & 63u; }
+    __device__ __forceinline__ void set_cnt(uint32_t b, uint32_t c) { st = (st & ~(63u << (6u * b))) | (c << (6u * b)); }
+    __device__ __forceinline__ uint32_t pos() const { return (st >> 12) & 63u; }
+    __device__ __forceinline__ uint32_t cur() const { return (st >> 18) & 1u; }
+    __device__ __forceinline__ static uint32_t bar_addr(FeedSmem &sm, uint32_t b) {
+        return (uint32_t)__cvta_generic_to_shared(&sm.bar[threadIdx.x >> 5][b]);
+    }
+    __device__ __forceinline__ static Particle *slot(FeedSmem &sm, uint32_t b, uint32_t i) {
+        return &sm.buf[threadIdx.x >> 5][b][i];
+    }
+
+    __device__ __forceinline__ void init(FeedSmem &sm, const Particle *src, uint32_t n, uint32_t *head, uint32_t *err) {
+        st = 0;
+        if ((threadIdx.x & 31) == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_addr(sm, 0)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_addr(sm, 1)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();
+        set_cnt(0, claim(sm, 0, src, n, head));
+        set_cnt(1, claim(sm, 1, src, n, head));
+        if (cnt(0)) wait(sm, 0, err);
+    }
+    // claim the next chunk into buffer b; returns its particle count
+    __device__ __forceinline__ static uint32_t claim(FeedSmem &sm, uint32_t b, const Particle *src, uint32_t n,
+                                                     uint32_t *head) {
+        uint32_t base = 0;
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(head, (uint32_t)FEED_CHUNK);
+        base = __shfl_sync(FULL, base, 0);
+        const uint32_t c = base < n ? min(n - base, (uint32_t)FEED_CHUNK) : 0u;
+        if (c && (threadIdx.x & 31) == 0) {
+            const uint32_t bytes = c * (uint32_t)sizeof(Particle);
+            const uint32_t mb = bar_addr(sm, b);
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slot(sm, b, 0));
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(dst), "l"(src + base), "r"(bytes), "r"(mb) : "memory");
+        }
+        return c;
+    }
+    // wait (bounded) until buffer b's copy has landed
+    __device__ __forceinline__ void wait(FeedSmem &sm, uint32_t b, uint32_t *err) {
+        const uint32_t mb = bar_addr(sm, b), par = (st >> (19u + b)) & 1u;
+        uint32_t ok = 0;
+        for (uint32_t it = 0; it < FEED_SPIN && !ok; ++it)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(ok) : "r"(mb), "r"(par) : "memory");
+        st ^= 1u << (19u + b);
+        if (!ok) {
+            atomicOr(err, PSL_DEV_ERR_TIMEOUT);
+            st &= ~4095u;                     // nothing more is read from this warp's buffers
+        }
+    }
+    // Hand particles to the lanes in `need` (ranked by lane order).  Returns
+    // true and fills p for a lane in `need` that got one; a lane in `need`
+    // that got none finds the queue exhausted.
+    __device__ __forceinline__ bool take(FeedSmem &sm, unsigned need, unsigned lt, bool mine, Particle &p,
+                                         const Particle *src, uint32_t n, uint32_t *head, uint32_t *err) {
+        const uint32_t k = __popc(need), rank = __popc(need & lt);
+        const uint32_t c = cur(), nx = c ^ 1u, avail = cnt(c) - pos();
+        if (k >= avail && cnt(nx)) wait(sm, nx, err);
+        const uint32_t cn = cnt(nx);                    // after a failed wait this is 0
+        bool got = false;
+        if (mine) {
+            const Particle *q = nullptr;
+            if (rank < avail) q = slot(sm, c, pos() + rank);
+            else if (rank - avail < cn) q = slot(sm, nx, rank - avail);
+            if (q) {
+                const float4 *s4 = reinterpret_cast<const float4 *>(q);
+                float4 *d4 = reinterpret_cast<float4 *>(&p);
+                d4[0] = s4[0]; d4[1] = s4[1]; d4[2] = s4[2];
+                got = true;
+            }
+        }
+        if (k >= avail) {                               // the current chunk is used up
+            __syncwarp();                               // every lane has read it
+            const uint32_t np = min(k - avail, cn);
+            st = (st & ~((63u << 12) | (1u << 18))) | (np << 12) | (nx << 18);
+            set_cnt(c, cn ? claim(sm, c, src, n, head) : 0u);   // a short chunk means the queue is exhausted
+        } else {
+            st += k << 12;
+        }
+        return got;
+    }
+};
+
 // ------------------------------------------------------------- photons ---
 struct Photon {
     float x, y, z, u, v, w, e, wt;
@@ -389,25 +497,25 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
 
 __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
                                                 uint32_t cap, uint32_t *head) {
+    __shared__ FeedSmem sm;
     const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     Photon g;
+    Feed F;
+    F.init(sm, src, n, head, A.err);
     bool alive = false, done = false;
     for (;;) {
         const unsigned need = __ballot_sync(FULL, !alive && !done);
         if (need) {
-            const int leader = __ffs(need) - 1;
-            uint32_t base = 0;
-            if (lane == leader) base = atomicAdd(head, (uint32_t)__popc(need));
-            base = __shfl_sync(FULL, base, leader);
-            if (!alive && !done) {
-                const uint32_t idx = base + __popc(need & lt);
-                if (idx >= n) {
+            Particle p;
+            const bool mine = !alive && !done;
+            const bool got = F.take(sm, need, lt, mine, p, src, n, head, A.err);
+            if (mine) {
+                if (!got) {
                     done = true;
                 } else {
-                    const Particle p = load_particle(src + idx);
                     g.x = p.x; g.y = p.y; g.z = p.z; g.u = p.u; g.v = p.v; g.w = p.w; g.e = p.e; g.wt = p.wt;
                     g.p0 = p.pid_lo; g.p1 = p.pid_hi; g.root = p.root; g.nchild = 0;
                     g.rng.draw = 0;
@@ -583,6 +691,8 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
 
 __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
                                                   uint32_t *head) {
+    // electrons live for several steps and their queue reads hit L1, so
+    // refills load directly (a staged feed measured 2 % slower here)
     const uint32_t n = min(*n_ptr, cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
