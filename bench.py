@@ -181,6 +181,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-imrt", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-apr", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -238,7 +239,7 @@ def main():
         else:
             capi.psl_run(plan, dwx.phantom, phys, tally, first, per_rank)
         _, n_total, _ = plan.info()
-        norm = engine.normalisation(n_total, per_rank, w.records.n)
+        norm = engine.normalisation(n_total, per_rank, w.records.n * w.binning.apr_copies)
         capi.dose_readout(tally, dwx.phantom, norm, out_dose[0], out_dose[1], out_dose[2])
         return store, plan, tally
 
@@ -358,6 +359,9 @@ def main():
     imrt = None
     if rank == 0 and world == 1 and not args.no_imrt:
         imrt = imrt_run(capi, engine, inputs, torch)
+    apr = None
+    if rank == 0 and world == 1 and not args.no_apr:
+        apr = apr_build(capi, engine, inputs, torch, flush)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
@@ -376,6 +380,7 @@ def main():
                 "modes": {"batched_psl_run": value, "plain_per_batch": per_rank * world / t_plain,
                           "unit": "histories/s"},
                 "imrt_batched_graph": imrt,
+                "apr_build": apr,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
         print(json.dumps(line))
     if world > 1:
@@ -393,6 +398,32 @@ THREAD_INST_PER_WOODCOCK_STEP = 439.6
 DRAM_BYTES_PER_HISTORY = {"electron": 28.22, "photon": 40.06}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
+
+
+def apr_build(capi, engine, inputs, torch, flush, k=4):
+    """Commissioning with azimuthal redistribution (Sec. 2.3.1): psl_build of
+    the 1e7-record phase space with k copies per record (k x 1e7 rotated,
+    sorted records), timed with CUDA events after one warm-up build."""
+    w = inputs.config2(n_histories=1000)
+    w.binning.apr_copies, w.binning.apr_seed = k, 0x5EED
+    dw = engine.upload(w)
+    capi.psl_build(dw.params, dw.records).close()
+    times = []
+    for _ in range(3):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        store = capi.psl_build(dw.params, dw.records)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        n_records, n_valid, _ = store.info()
+        store.close()
+    t = float(np.median(times))
+    return {"copies": k, "records_in": w.records.n, "records_sorted": int(n_records), "records_kept": int(n_valid),
+            "ms": 1e3 * t, "sorted_records_per_s": n_records / t}
 
 
 def imrt_run(capi, engine, inputs, torch):
@@ -423,7 +454,7 @@ def imrt_run(capi, engine, inputs, torch):
     sigma = torch.empty_like(dose)
     lg = torch.empty(3, dtype=torch.float64, device="cuda")
     n_entries, n_total, _ = plan.info()
-    capi.dose_readout(tally, dw.phantom, engine.normalisation(n_total, w.n_histories, w.records.n), dose, sigma, lg)
+    capi.dose_readout(tally, dw.phantom, engine.normalisation(n_total, w.n_histories, w.records.n * w.binning.apr_copies), dose, sigma, lg)
     d = dose.view(nz, ny, nx).cpu().numpy()
     sg = sigma.view(nz, ny, nx).cpu().numpy()
     ic = ((np.array(w.beams[0].iso) - np.array(w.phantom.origin)) / np.array(w.phantom.voxel)).astype(int)[::-1]

@@ -97,12 +97,34 @@ typedef struct psl_records {
 typedef struct psl_params {
     int32_t nx, ny;            /* position bins, nx*ny*n_ebins*2 < 2^31 */
     int32_t n_ebins;           /* energy bins per type, >= 1 */
-    int32_t apr_copies;        /* azimuthal redistribution copies; must be 1 */
+    int32_t apr_copies;        /* K >= 1: copies per record (azimuthal redistribution) */
     const float *x_edges;      /* host, nx+1 ascending */
     const float *y_edges;      /* host, ny+1 ascending */
     const float *e_edges;      /* host, n_ebins+1 ascending */
     float z_psl;               /* PSL plane, cm from the source */
+    uint64_t apr_seed;         /* Philox key of the redistribution angles */
 } psl_params_t;
+
+/* Azimuthal particle redistribution (Sec. 2.3.1), applied by psl_build
+ * before the PSL sort when apr_copies = K > 1.  Record i of the caller's
+ * phase space becomes the K records j = i*K + c, c = 0..K-1: copy 0 is the
+ * record as given, copy c > 0 is the record rotated about the beam axis
+ * (x = y = 0) by its own uniform azimuth phi, position (x, y) and direction
+ * cosines (u, v) alike, energy, weight and charge unchanged.  The angle:
+ * Philox4x32-10 with key apr_seed and counter (b, PSL_TAG_APR, i, c) gives,
+ * for b = 0, 1, ..., two candidate points per block, (a, b) = (2 U0 - 1,
+ * 2 U1 - 1) and (2 U2 - 1, 2 U3 - 1) with U = ((word >> 9) + 0.5) 2^-23; the
+ * first with a*a + b*b <= 1 gives cos phi = (a*a - b*b) / (a*a + b*b) and
+ * sin phi = 2 a b / (a*a + b*b) (the doubled angle of a uniform point of the
+ * disc is uniform); after 64 blocks without one, phi = 0.  Every operation
+ * is one IEEE float32 operation rounded to nearest (no fused multiply-add),
+ * so the rotated records are reproducible bit for bit on any IEEE machine:
+ *   x' = x cos - y sin,  y' = x sin + y cos  (the same for u, v).
+ * The store's input index of a copy is j, and a phase space of N records
+ * with K copies stands for K*N incident particles in the dose normalisation
+ * (Sec. 2.5).  K = 1 leaves the records as given. */
+#define PSL_TAG_APR 3u
+#define PSL_APR_MAX_BLOCKS 64
 
 /* One treatment field (Sec. 2.2, 2.3.3, 2.4). */
 typedef struct psl_beam {
@@ -147,7 +169,9 @@ PSL_API void psl_physics_default(psl_physics_t *out);
  * (x, y, u, v, e, wt, input index, q), with the bin offsets
  * offsets[0..n_bins] (offsets[n_bins] = records kept).  The store is
  * independent of the caller's arrays once the call has completed.
- * Errors: PSL_EINVAL (sizes, edges, apr_copies != 1), PSL_ENOMEM, PSL_ECUDA,
+ * With apr_copies K > 1 the sorted records are the K redistributed copies
+ * of every record (see PSL_TAG_APR above); records->n * K < 2^30.
+ * Errors: PSL_EINVAL (sizes, edges, apr_copies < 1), PSL_ENOMEM, PSL_ECUDA,
  * PSL_ETIMEOUT (a look-back wait of the sort gave up). Synchronises stream. */
 PSL_API int psl_build(const psl_params_t *params, const psl_records_t *records, psl_store_t **out, void *stream);
 
@@ -157,7 +181,8 @@ PSL_API int psl_build(const psl_params_t *params, const psl_records_t *records, 
  * no counterpart; it is the same PSL sort written into caller arrays.
  * Scratch lives in one fixed device array of about 17 MB that every GPU that
  * loads this library holds until the process exits.  Limits: at most
- * PSL_STATIC_MAX_RECORDS records and PSL_STATIC_MAX_EDGES bin edges
+ * PSL_STATIC_MAX_RECORDS records, apr_copies = 1 (no redistribution) and
+ * PSL_STATIC_MAX_EDGES bin edges
  * (nx+1 + ny+1 + n_ebins+1); larger inputs return PSL_EINVAL with the limit
  * in psl_last_error.  Outputs (device, caller-owned): offsets [n_bins+1]
  * int64 and sorted [n x 8] float32 (16-byte aligned) in the psl_store_read
@@ -173,7 +198,8 @@ PSL_API int psl_build(const psl_params_t *params, const psl_records_t *records, 
 PSL_API int psl_build_static(const psl_params_t *params, const psl_records_t *records, int64_t *offsets,
                              float *sorted, int64_t *n_valid, void *stream);
 
-/* Sizes of a store (host outputs). */
+/* Sizes of a store (host outputs): records after redistribution (input
+ * records x apr_copies), records kept in some PSL, PSL bins. */
 PSL_API int psl_store_info(const psl_store_t *store, int64_t *n_records, int64_t *n_valid, int64_t *n_bins);
 
 /* Copy the store out (device outputs, NULL to skip): offsets (n_bins+1

@@ -5,6 +5,9 @@ benchmark may import this module.  It shares no code with the CUDA path.
 
 It follows the paper's steps in order:
 
+* Azimuthal particle redistribution, Sec. 2.3.1 (before PSL generation):
+  each record is also used as K-1 copies rotated about the beam axis by
+  independent uniform azimuths, position and direction cosines together.
 * PSL generation, Sec. 2.3.2: split the records by particle type (photon;
   electron/positron), then by energy bin, then by dx x dy position bin.  The
   PSL store is one array sorted by the PSL id plus its bin offsets.
@@ -41,6 +44,83 @@ F32 = np.float32
 ST_TRANSPORT, ST_JAW, ST_FLUENCE, ST_ZERO_WEIGHT, ST_MISS = 0, 1, 2, 3, 4
 
 TAG_OFFSET = 1
+TAG_APR = 3
+APR_MAX_BLOCKS = 64
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.3.1: azimuthal particle redistribution
+# --------------------------------------------------------------------------
+def _apr_coord(w: np.ndarray) -> np.ndarray:
+    """2 U - 1 in float32 for U = ((w >> 9) + 0.5) 2^-23 (exact)."""
+    u = ((w >> np.uint32(9)).astype(F32) + F32(0.5)) * F32(2.0 ** -23)
+    return F32(2.0) * u - F32(1.0)
+
+
+def apr_angles(n_records: int, k: int, seed: int):
+    """cos and sin (float32, [n_records, k]) of the azimuth of every copy.
+
+    Copy 0 is the record itself (angle 0).  For copy c > 0 of record i the
+    angle is the doubled polar angle of a uniform point (a, b) of the unit
+    disc, found by rejection: Philox blocks with counter (blk, TAG_APR, i, c)
+    under key seed, two candidate points per block, the first with
+    a^2 + b^2 <= 1 taken; none in APR_MAX_BLOCKS blocks gives angle 0.  Then
+    cos = (a^2 - b^2) / r^2 and sin = 2ab / r^2.  Every operation is a
+    float32 operation rounded to nearest, the precision the PSL records are
+    stored in."""
+    cs = np.ones((n_records, k), F32)
+    sn = np.zeros((n_records, k), F32)
+    if k <= 1 or n_records == 0:
+        return cs, sn
+    ii, cc = np.meshgrid(np.arange(n_records, dtype=np.int64), np.arange(1, k, dtype=np.int64), indexing="ij")
+    ii, cc = ii.ravel(), cc.ravel()
+    oc = np.ones(len(ii), F32)
+    os_ = np.zeros(len(ii), F32)
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], np.uint32)
+    pending = np.arange(len(ii))
+    for blk in range(APR_MAX_BLOCKS):
+        if len(pending) == 0:
+            break
+        ctr = np.stack([np.full(len(pending), blk), np.full(len(pending), TAG_APR), ii[pending], cc[pending]],
+                       1).astype(np.uint32)
+        w = _lib.philox(ctr, key)
+        done = np.zeros(len(pending), bool)
+        for h in range(2):
+            a, b = _apr_coord(w[:, 2 * h]), _apr_coord(w[:, 2 * h + 1])
+            aa, bb = a * a, b * b
+            r2 = aa + bb
+            take = (r2 <= F32(1.0)) & ~done
+            sel = pending[take]
+            oc[sel] = (aa[take] - bb[take]) / r2[take]
+            os_[sel] = (F32(2.0) * (a[take] * b[take])) / r2[take]
+            done |= take
+        pending = pending[~done]
+    cs[:, 1:] = oc.reshape(n_records, k - 1)
+    sn[:, 1:] = os_.reshape(n_records, k - 1)
+    return cs, sn
+
+
+def apr_expand(records, k: int, seed: int):
+    """The phase space after redistribution: record i becomes records
+    i*k + c, c = 0..k-1; copy 0 unchanged, the others rotated about the beam
+    axis: x' = x cos - y sin, y' = x sin + y cos, the same for (u, v)."""
+    from paper_1302_1861_b300.inputs import Records
+    if k <= 1:
+        return records
+    n = records.n
+    cs, sn = apr_angles(n, k, seed)
+    out = {}
+    for name in ("e", "wt", "q"):
+        out[name] = np.repeat(getattr(records, name), k)
+    for a_name, b_name in (("x", "y"), ("u", "v")):
+        a = np.asarray(getattr(records, a_name), F32)[:, None]
+        b = np.asarray(getattr(records, b_name), F32)[:, None]
+        ra = a * cs - b * sn
+        rb = a * sn + b * cs
+        ra[:, 0] = a[:, 0]                 # copy 0: the record as given, bit for bit
+        rb[:, 0] = b[:, 0]
+        out[a_name], out[b_name] = ra.ravel(), rb.ravel()
+    return Records(out["x"], out["y"], out["u"], out["v"], out["e"], out["wt"], out["q"])
 
 
 # --------------------------------------------------------------------------

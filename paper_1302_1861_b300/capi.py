@@ -41,7 +41,7 @@ class Records(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("nx", i32), ("ny", i32), ("n_ebins", i32), ("apr_copies", i32), ("x_edges", vp),
-                ("y_edges", vp), ("e_edges", vp), ("z_psl", f32)]
+                ("y_edges", vp), ("e_edges", vp), ("z_psl", f32), ("apr_seed", ctypes.c_uint64)]
 
 
 class Beam(ctypes.Structure):

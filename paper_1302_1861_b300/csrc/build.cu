@@ -43,9 +43,56 @@ __device__ __forceinline__ int count_le(const float *a, int n, float v) {
     return lo;
 }
 
-// PSL id of every record + digit histograms of all passes (upsweep)
-__global__ void __launch_bounds__(256) k_key(psl_records_t r, Edges ed, uint32_t n_bins, uint32_t *keys,
-                                             int passes, uint32_t *hist) {
+// Azimuthal redistribution (Sec. 2.3.1): cos and sin of copy c's angle for
+// record i.  A uniform point of the unit disc by rejection from Philox pairs;
+// its doubled angle is uniform.  Each step is one float32 operation rounded
+// to nearest, so the result is the same on any IEEE machine.
+struct Apr {
+    int32_t k;                 // copies per record
+    uint32_t s0, s1;           // Philox key
+};
+
+__device__ __forceinline__ float apr_coord(uint32_t w) {
+    // 2 U - 1 with U = ((w >> 9) + 0.5) 2^-23: both steps exact in float
+    const float u = __fmul_rn(__fadd_rn((float)(w >> 9), 0.5f), 1.0f / 8388608.0f);
+    return __fsub_rn(__fmul_rn(2.0f, u), 1.0f);
+}
+
+__device__ __forceinline__ void apr_angle(const Apr &A, uint32_t i, uint32_t c, float &cs, float &sn) {
+    cs = 1.0f; sn = 0.0f;
+    for (uint32_t b = 0; b < PSL_APR_MAX_BLOCKS; ++b) {
+        const u32x4 o = philox10(b, PSL_TAG_APR, i, c, A.s0, A.s1);
+        const uint32_t w[4] = {o.a, o.b, o.c, o.d};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float a = apr_coord(w[2 * h]), d = apr_coord(w[2 * h + 1]);
+            const float aa = __fmul_rn(a, a), dd = __fmul_rn(d, d);
+            const float r2 = __fadd_rn(aa, dd);
+            if (r2 <= 1.0f) {
+                cs = __fdiv_rn(__fsub_rn(aa, dd), r2);
+                sn = __fdiv_rn(__fmul_rn(2.0f, __fmul_rn(a, d)), r2);
+                return;
+            }
+        }
+    }
+}
+
+// record and copy of redistributed index j (< 2^30)
+__device__ __forceinline__ void apr_split(const Apr &A, int64_t j, uint32_t &i, uint32_t &c) {
+    if (A.k == 1) { i = (uint32_t)j; c = 0; return; }
+    i = (uint32_t)j / (uint32_t)A.k;
+    c = (uint32_t)j - i * (uint32_t)A.k;
+}
+
+__device__ __forceinline__ void apr_rotate(float cs, float sn, float &x, float &y) {
+    const float nx = __fsub_rn(__fmul_rn(x, cs), __fmul_rn(y, sn));
+    const float ny = __fadd_rn(__fmul_rn(x, sn), __fmul_rn(y, cs));
+    x = nx; y = ny;
+}
+
+// PSL id of every (copy of a) record + digit histograms of all passes (upsweep)
+__global__ void __launch_bounds__(256) k_key(psl_records_t r, Edges ed, Apr apr, int64_t n, uint32_t n_bins,
+                                             uint32_t *keys, int passes, uint32_t *hist) {
     extern __shared__ float sh[];
     float *xe = sh, *ye = xe + ed.nx + 1, *ee = ye + ed.ny + 1;
     __shared__ uint32_t h[MAX_PASSES * RADIX];
@@ -54,10 +101,16 @@ __global__ void __launch_bounds__(256) k_key(psl_records_t r, Edges ed, uint32_t
     for (int i = threadIdx.x; i <= ed.ne; i += blockDim.x) ee[i] = ed.ee[i];
     for (int i = threadIdx.x; i < passes * RADIX; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int64_t n = r.n;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t i, c;
+        apr_split(apr, j, i, c);
         float x = __ldg(r.x + i), y = __ldg(r.y + i), e = __ldg(r.e + i);
         int q = __ldg(r.q + i);
+        if (c) {
+            float cs, sn;
+            apr_angle(apr, i, c, cs, sn);
+            apr_rotate(cs, sn, x, y);
+        }
         int bx = count_le(xe, ed.nx + 1, x) - 1;
         int by = count_le(ye, ed.ny + 1, y) - 1;
         uint32_t key = n_bins;
@@ -66,7 +119,7 @@ __global__ void __launch_bounds__(256) k_key(psl_records_t r, Edges ed, uint32_t
             int t = q != 0;
             key = (uint32_t)((t * ed.ne + eb) * (ed.nx * ed.ny) + by * ed.nx + bx);
         }
-        keys[i] = key;
+        keys[j] = key;
         for (int p = 0; p < passes; ++p) atomicAdd(&h[p * RADIX + ((key >> (8 * p)) & 0xFF)], 1u);
     }
     __syncthreads();
@@ -77,12 +130,20 @@ __global__ void __launch_bounds__(256) k_key(psl_records_t r, Edges ed, uint32_t
 // records packed as 32-byte AoS in input order (coalesced reads and writes),
 // so that the gather below reads one 32-byte record per sorted position
 // instead of seven scattered SoA elements
-__global__ void __launch_bounds__(256) k_pack(psl_records_t r, int64_t n, PslRecord *__restrict__ out) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_pack(psl_records_t r, Apr apr, int64_t n, PslRecord *__restrict__ out) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t i, c;
+        apr_split(apr, j, i, c);
         PslRecord o;
         o.x = __ldg(r.x + i); o.y = __ldg(r.y + i); o.u = __ldg(r.u + i); o.v = __ldg(r.v + i);
-        o.e = __ldg(r.e + i); o.wt = __ldg(r.wt + i); o.src = (uint32_t)i; o.q = (int32_t)__ldg(r.q + i);
-        float4 *d = reinterpret_cast<float4 *>(out + i);
+        o.e = __ldg(r.e + i); o.wt = __ldg(r.wt + i); o.src = (uint32_t)j; o.q = (int32_t)__ldg(r.q + i);
+        if (c) {
+            float cs, sn;
+            apr_angle(apr, i, c, cs, sn);
+            apr_rotate(cs, sn, o.x, o.y);
+            apr_rotate(cs, sn, o.u, o.v);
+        }
+        float4 *d = reinterpret_cast<float4 *>(out + j);
         const float4 *sp = reinterpret_cast<const float4 *>(&o);
         d[0] = sp[0]; d[1] = sp[1];
     }
@@ -142,11 +203,12 @@ int psl_sm_count() {
 extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_store_t **out, void *stream_) {
     if (!prm || !rec || !out) return psl_fail(PSL_EINVAL, "psl_build: null argument");
     *out = nullptr;
-    if (prm->apr_copies != 1) return psl_fail(PSL_EINVAL, "psl_build: apr_copies must be 1");
+    if (prm->apr_copies < 1) return psl_fail(PSL_EINVAL, "psl_build: apr_copies must be >= 1");
     if (prm->nx <= 0 || prm->ny <= 0 || prm->n_ebins <= 0) return psl_fail(PSL_EINVAL, "psl_build: bad bin counts");
     const int64_t n_bins = 2ll * prm->n_ebins * prm->nx * prm->ny;
     if (n_bins >= (1ll << 31) - 1) return psl_fail(PSL_EINVAL, "psl_build: too many bins");
-    if (rec->n < 0 || rec->n >= (1ll << 30)) return psl_fail(PSL_EINVAL, "psl_build: record count out of range");
+    if (rec->n < 0 || rec->n >= (1ll << 30) || rec->n * (int64_t)prm->apr_copies >= (1ll << 30))
+        return psl_fail(PSL_EINVAL, "psl_build: record count (times apr_copies) out of range");
     if (!prm->x_edges || !prm->y_edges || !prm->e_edges) return psl_fail(PSL_EINVAL, "psl_build: null edges");
     for (int i = 0; i < prm->nx; ++i)
         if (!(prm->x_edges[i] < prm->x_edges[i + 1])) return psl_fail(PSL_EINVAL, "psl_build: x edges not ascending");
@@ -158,9 +220,10 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         return psl_fail(PSL_EINVAL, "psl_build: null record array");
 
     cudaStream_t st = as_stream(stream_);
-    const uint32_t n = (uint32_t)rec->n;
+    const uint32_t n = (uint32_t)(rec->n * prm->apr_copies);     // records after redistribution
+    const Apr apr{prm->apr_copies, (uint32_t)prm->apr_seed, (uint32_t)(prm->apr_seed >> 32)};
     psl_store *s = new psl_store();
-    s->n_records = rec->n; s->n_bins = n_bins; s->nx = prm->nx; s->ny = prm->ny; s->n_ebins = prm->n_ebins;
+    s->n_records = n; s->n_bins = n_bins; s->nx = prm->nx; s->ny = prm->ny; s->n_ebins = prm->n_ebins;
     s->z_psl = prm->z_psl;
     s->stream = st;
     cudaGetDevice(&s->device);
@@ -203,7 +266,7 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
             break;
         }
         int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_KEY, st, &tk_); k_key<<<grid, 256, edges.size() * sizeof(float), st>>>(*rec, ed, (uint32_t)n_bins, keys[0], passes, hist); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_KEY, st, tk_); }
+        { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_KEY, st, &tk_); k_key<<<grid, 256, edges.size() * sizeof(float), st>>>(*rec, ed, apr, (int64_t)n, (uint32_t)n_bins, keys[0], passes, hist); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_KEY, st, tk_); }
         int alt = 0;
         sort_pairs_u32(keys[0], vals[0], keys[1], vals[1], n, bits, hist, true, scratch, &alt, st);
         // after an odd number of passes the result is in the alternate buffers
@@ -215,7 +278,7 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         {
             void *tk_ = nullptr;
             if (psl_timer_on()) psl_timer_begin(PK_GATHER, st, &tk_);
-            k_pack<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16), 256, 0, st>>>(*rec, n, packed); PSL_NOTE_LAUNCH();
+            k_pack<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16), 256, 0, st>>>(*rec, apr, n, packed); PSL_NOTE_LAUNCH();
             if (tk_) psl_timer_end(PK_GATHER, st, tk_);
         }
         int64_t nvalid = 0;
@@ -388,7 +451,7 @@ extern "C" int psl_build_static(const psl_params_t *prm, const psl_records_t *re
     Edges ed{prm->nx, prm->ny, prm->n_ebins, edges, edges + prm->nx + 1, edges + prm->nx + prm->ny + 2};
     const int sms = psl_sm_count();
     int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-    k_key<<<grid, 256, n_edges * sizeof(float), st>>>(*rec, ed, (uint32_t)n_bins, keys0, passes, hist); PSL_NOTE_LAUNCH();
+    k_key<<<grid, 256, n_edges * sizeof(float), st>>>(*rec, ed, Apr{1, 0u, 0u}, rec->n, (uint32_t)n_bins, keys0, passes, hist); PSL_NOTE_LAUNCH();
     int alt = 0;
     sort_pairs_u32(keys0, vals0, keys1, vals1, n, bits, hist, true, sort_scratch, &alt, st);
     uint32_t *skeys = alt ? keys1 : keys0, *svals = alt ? vals1 : vals0;

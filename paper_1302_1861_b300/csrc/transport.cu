@@ -193,13 +193,6 @@ __device__ __forceinline__ float range_of(const Tables &T, float E) {
     return range_at(T, i, f);
 }
 
-__device__ __forceinline__ float stop_of(const Tables &T, float E) {
-    int i; float f;
-    tab_pos(T, E, i, f);
-    float p = __ldg(&T.el[i].x), q = __ldg(&T.el[i + 1].x);
-    return p + f * (q - p);
-}
-
 // ------------------------------------------------------------- helpers ---
 __device__ __forceinline__ unsigned long long fixed_point(float e, float wt) {
     return (unsigned long long)__float2ll_rn(__fmul_rn(e, wt) * 4294967296.0f);
@@ -557,14 +550,6 @@ __device__ __forceinline__ float energy_of_range(const Tables &T, float r) {
     const float f = x - (float)i;
     const float a = __ldg(T.irng + i), b = __ldg(T.irng + i + 1);
     return __expf(a + f * (b - a));
-}
-
-// energy after a path h (g/cm^2): RK4 on dT/dh = -S(T), k1 = S(t) given
-__device__ __forceinline__ float energy_after(const Tables &T, float t, float h, float k1) {
-    const float k2 = stop_of(T, fmaxf(t - 0.5f * h * k1, 1e-3f));
-    const float k3 = stop_of(T, fmaxf(t - 0.5f * h * k2, 1e-3f));
-    const float k4 = stop_of(T, fmaxf(t - h * k3, 1e-3f));
-    return t - h * (k1 + 2.0f * k2 + 2.0f * k3 + k4) * (1.0f / 6.0f);
 }
 
 __device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, const uint32_t *rk, uint32_t p0,

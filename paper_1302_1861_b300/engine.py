@@ -46,7 +46,8 @@ def upload(w: Workload, device: str = "cuda", records=None) -> DeviceWorkload:
         rec_t = list(records)
     b = w.binning
     xe, ye, ee = (np.ascontiguousarray(a, np.float32) for a in (b.x_edges, b.y_edges, b.e_edges))
-    params = capi.Params(b.nx, b.ny, b.n_ebins, 1, xe.ctypes.data, ye.ctypes.data, ee.ctypes.data, float(w.z_psl))
+    params = capi.Params(b.nx, b.ny, b.n_ebins, int(b.apr_copies), xe.ctypes.data, ye.ctypes.data, ee.ctypes.data,
+                         float(w.z_psl), int(b.apr_seed))
     ph = w.phantom
     nz, ny, nx = ph.shape
     mat_t = torch.from_numpy(np.ascontiguousarray(ph.mat, np.uint8)).to(device)
@@ -83,7 +84,9 @@ def batch_histories(first: int, n: int, n_batches: int, b: int):
 
 def normalisation(n_total_psl: int, n_histories: int, n_incident: int) -> float:
     """Sec. 2.5: D = D_o N^phsp / (N_simulated N_incident); with PSL selection the
-    histories stand for the N_total^psl selected records."""
+    histories stand for the N_total^psl selected records.  With azimuthal
+    redistribution a phase space of N records and K copies stands for K N
+    incident particles (pass n_incident = K N)."""
     return float(n_total_psl) / (float(n_histories) * float(n_incident))
 
 
@@ -113,7 +116,7 @@ def run(dw: DeviceWorkload, n_histories: Optional[int] = None, n_batches: Option
         sigma = torch.empty_like(dose)
         ledger = torch.empty(3, dtype=torch.float64, device=dose.device)
         _, n_total_psl, _ = plan.info()
-        norm = normalisation(n_total_psl, n_h, w.records.n)
+        norm = normalisation(n_total_psl, n_h, w.records.n * int(w.binning.apr_copies))
         capi.dose_readout(tally, dw.phantom, norm, dose, sigma, ledger, stream)
         out.update(dose=dose, sigma=sigma, ledger=ledger, norm=norm)
     return out

@@ -70,6 +70,8 @@ class Binning:
     y_edges: np.ndarray      # float32, ny+1
     e_edges: np.ndarray      # float32, n_ebins+1
     log_ebins: bool
+    apr_copies: int = 1      # azimuthal redistribution: copies per record (Sec. 2.3.1)
+    apr_seed: int = 0        # Philox key of the redistribution angles
 
     @property
     def nx(self):

@@ -7,6 +7,8 @@ counts, start offsets, entry, read number, record, beam, status) and for the
 float32 weight; the rotated / projected float32 state within 2e-5 cm of the
 oracle's float64 value (float32 rounding of ~100 cm coordinates).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -154,3 +156,64 @@ def test_source_strided_batches():
     for b in (0, 9):
         ent, _ = source.history_map(opl, np.arange(b, w.n_histories, 10))
         assert set(np.unique(opl.group[ent])) == set(np.unique(opl.group[opl.count > 0]))
+
+
+# ---------------------------------------------------- redistribution (APR) ---
+def _apr_workload(w, k, seed):
+    w.binning.apr_copies, w.binning.apr_seed = k, seed
+    return dataclasses.replace(w, records=source.apr_expand(w.records, k, seed))
+
+
+@pytest.mark.parametrize("k,n", [(2, 4097), (4, 100_000), (7, 1), (3, 0)])
+def test_apr_store_bit_exact(k, n):
+    """psl_build with K copies per record (Sec. 2.3.1): the rotated records,
+    their PSL ids, order and offsets equal the oracle's bit for bit."""
+    w = inputs.config1(n_records=max(n, 1))
+    if n == 0:
+        w.records = inputs.Records(*(a[:0] for a in w.records.arrays()))
+    we = _apr_workload(w, k, 0xA5A5000012340000 + k)
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    n_records, n_valid, n_bins = store.info()
+    assert n_records == k * n
+    ost = source.psl_build(we.records, w.binning)
+    _check_store(we, store, ost, n_valid, n_bins)
+
+
+def test_apr_full_size_store():
+    """The 1e7-record phase space with 3 copies (3e7 sorted records)."""
+    w = inputs.config2(n_histories=1000)
+    we = _apr_workload(w, 3, 0x5EED)
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    n_records, n_valid, n_bins = store.info()
+    assert n_records == 3 * w.records.n
+    _check_store(we, store, source.psl_build(we.records, w.binning), n_valid, n_bins)
+
+
+def test_apr_source_stage_bit_exact():
+    """Plan and source stage over a redistributed store, every history."""
+    w = inputs.config1()
+    we = _apr_workload(w, 4, 99)
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    ost = source.psl_build(we.records, w.binning)
+    dw, plan, opl = _plan_both(we, store, ost)
+    n_ok = int(_check_trace(we, dw, plan, ost, opl, np.arange(w.n_histories)))
+    assert n_ok > 0.3 * w.n_histories, n_ok
+
+
+def test_apr_rejects_bad_copy_counts():
+    w = inputs.config1(n_records=100)
+    for k in (0, -2, 1 << 24):
+        w.binning.apr_copies = k
+        dw = engine.upload(w)
+        with pytest.raises(capi.PslError):
+            capi.psl_build(dw.params, dw.records)
+    w.binning.apr_copies = 2
+    dw = engine.upload(w)
+    nb = w.binning.n_bins
+    off = torch.empty(nb + 1, dtype=torch.int64, device="cuda")
+    rec = torch.empty(100 * 8, dtype=torch.float32, device="cuda")
+    with pytest.raises(capi.PslError):                 # the allocation-free build takes no copies
+        capi.psl_build_static(dw.params, dw.records, off, rec)
