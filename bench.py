@@ -182,6 +182,7 @@ def main():
     ap.add_argument("--no-imrt", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-apr", action="store_true")
+    ap.add_argument("--no-methods", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -362,6 +363,10 @@ def main():
     apr = None
     if rank == 0 and world == 1 and not args.no_apr:
         apr = apr_build(capi, engine, inputs, torch, flush)
+    methods = None
+    if rank == 0 and world == 1 and not args.no_methods:
+        methods = stream_method_run(capi, engine, torch, flush, w, dw, per_rank)
+        methods["method3_psl_histories_per_s"] = value
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
@@ -381,6 +386,7 @@ def main():
                           "unit": "histories/s"},
                 "imrt_batched_graph": imrt,
                 "apr_build": apr,
+                "methods": methods,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
         print(json.dumps(line))
     if world > 1:
@@ -398,6 +404,39 @@ THREAD_INST_PER_WOODCOCK_STEP = 439.6
 DRAM_BYTES_PER_HISTORY = {"electron": 28.22, "photon": 40.06}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
+
+
+def stream_method_run(capi, engine, torch, flush, w, dw, n, capacity=1 << 20):
+    """Method 2 of the paper (Sec. 2.2) on the same workload: the phase space
+    read as an unsorted stream (history h reads record h mod N), jaw model,
+    on-the-fly type/energy binning in groups of `capacity`, transport and
+    readout; one warm-up run, then one timed run."""
+    tally = capi.psl_tally_create(dw.phantom, 1)
+    nvox = dw.mat_t.numel()
+    dose = torch.empty(nvox, dtype=torch.float64, device="cuda")
+    sigma = torch.empty_like(dose)
+    lg = torch.empty(3, dtype=torch.float64, device="cuda")
+    out = {}
+    for it in range(2):
+        capi.psl_tally_reset(tally)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        batch = capi.psl_stream_bin(dw.records, w.binning.e_edges, dw.beams[0], capi.METHOD_JAW_MODEL, w.z_psl,
+                                    w.sad, dw.phantom, 0, n, w.seed, capacity)
+        e1.record()
+        capi.transport_run(dw.phantom, capi.physics(), batch, tally, 0)
+        capi.dose_readout(tally, dw.phantom, 1.0 / n, dose, sigma, lg)
+        e2.record()
+        torch.cuda.synchronize()
+        groups, kept, _, _ = capi.psl_stream_info(batch)
+        batch.close()
+        out = {"method2_histories_per_s": n / (e0.elapsed_time(e2) / 1e3), "method2_bin_ms": e0.elapsed_time(e1),
+               "method2_total_ms": e0.elapsed_time(e2), "histories": n, "groups": groups, "kept": kept,
+               "capacity": capacity}
+    tally.close()
+    return out
 
 
 def apr_build(capi, engine, inputs, torch, flush, k=4):

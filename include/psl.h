@@ -269,6 +269,60 @@ PSL_API int psl_source_trace(const psl_plan_t *plan, const psl_phantom_t *phanto
 PSL_API int psl_batch_from_particles(const float *state, const int32_t *ptype, const uint64_t *pid, int64_t n,
                              uint64_t seed, psl_batch_t **out, void *stream);
 
+/* Methods 1 and 2 (Sec. 2.1, 2.2): the phase space read as an unsorted
+ * stream and binned on the fly by particle type and energy, without the PSL
+ * position bins.  History h = first + i, 0 <= i < n, reads record h mod N of
+ * the caller's phase space (N = records->n; the stream recycled).
+ *   method 2: a phase space above the collimators; the field's jaw model and
+ *     fluence map decide acceptance and weight (Sec. 2.2, 2.4), as in the PSL
+ *     path.
+ *   method 1: a patient-dependent phase space that already holds the
+ *     collimation: every record is accepted with its own weight.
+ * Accepted particles are rotated into the patient and entered into the
+ * phantom box as in the PSL path (a single field: MU weight 1).  Then the
+ * paper's binning: 2 x n_ebins bins (photons; electrons and positrons; the
+ * energy bin by the interior edges of e_edges, as psl_build), each holding
+ * at most `capacity` particles; a bin that fills is sent to transport as one
+ * group and emptied, and at the end of the stream the partly filled bins are
+ * sent in bin order.  The groups come out in exactly that order: full groups
+ * in the order of the stream position at which they filled, then the partial
+ * ones.  The returned batch holds the accepted particles in group order
+ * (photons from the front, electrons and positrons from the back), particle
+ * id = history id, keyed by `seed`; transport_run transports it and adds the
+ * emitted and missed energy of the stream to the ledger.  Particles that
+ * miss the phantom are counted as emitted and escaped and not kept.
+ * records: device SoA, caller-owned; e_edges: host, n_ebins+1 ascending;
+ * beam: host, its fluence device.  0 <= n < 2^31, capacity >= 1.
+ * Errors: PSL_EINVAL, PSL_ENOMEM, PSL_ECUDA, PSL_ETIMEOUT (sort look-back).
+ * Synchronises stream. */
+#define PSL_METHOD_PATIENT_DEPENDENT 1
+#define PSL_METHOD_JAW_MODEL 2
+PSL_API int psl_stream_bin(const psl_records_t *records, const float *e_edges, int32_t n_ebins,
+                           const psl_beam_t *beam, int32_t method, float z_psl, float sad,
+                           const psl_phantom_t *phantom, int64_t first_history, int64_t n_histories,
+                           uint64_t seed, int64_t capacity, psl_batch_t **out, void *stream);
+
+/* Groups of a batch from psl_stream_bin and the particles it kept (host
+ * outputs); the stream's emitted and missed energy in fixed point (2^-32
+ * MeV per unit weight). */
+PSL_API int psl_stream_info(const psl_batch_t *batch, int64_t *n_groups, int64_t *n_kept,
+                            int64_t *emitted_fp, int64_t *missed_fp);
+
+/* The groups in transport order (device int64 outputs, NULL to skip): bin
+ * (type * n_ebins + energy bin), particle count, and for each kept particle
+ * in group order its history id.  Particles that missed the phantom are not
+ * in any group. */
+PSL_API int psl_stream_read(const psl_batch_t *batch, int64_t *group_bin, int64_t *group_count,
+                            int64_t *history, void *stream);
+
+/* The particles of a batch from psl_batch_from_particles or psl_stream_bin
+ * (device outputs, NULL to skip): photons first, then electrons and
+ * positrons, each in the batch's transport order: state n x 8 float32
+ * (x y z u v w e wt, phantom-local), type, particle id.  n = photons +
+ * charged particles of psl_batch_info.  PSL_EINVAL for a batch from
+ * psl_source_batch (its particles exist only inside transport_run). */
+PSL_API int psl_batch_read(const psl_batch_t *batch, float *state, int32_t *ptype, uint64_t *pid, void *stream);
+
 /* Histories (or caller particles) in a batch, and its photon and charged
  * particle counts (-1 for a batch from psl_source_batch: known only once
  * transported). */
@@ -362,6 +416,14 @@ PSL_API int psl_atomic_peak(int64_t n_cells, int64_t n_updates, double *updates_
 /* Number of kernels this library has launched in this process (all threads);
  * a diagnostic for counting the launches of a timed region. */
 PSL_API int64_t psl_kernel_launches(void);
+
+/* The library takes its stream-ordered scratch (psl_build, psl_plan_create,
+ * psl_stream_bin, batches) from its own device memory pool, one per device,
+ * which keeps freed blocks for the next call.  psl_memory_trim waits for the
+ * device (cudaDeviceSynchronize), then returns pool memory beyond keep_bytes
+ * to the driver; *held_bytes (may be NULL) receives what the pool still
+ * reserves.  Errors: PSL_ECUDA. */
+PSL_API int psl_memory_trim(uint64_t keep_bytes, uint64_t *held_bytes);
 
 /* Text of the calling thread's last error ("" if none). */
 PSL_API const char *psl_last_error(void);

@@ -8,8 +8,11 @@ physics, transport and readout.  Inputs come from the separate seeded
 generator module ``paper_1302_1861_b300.inputs``.
 
 Layout:
-  source.py     PSL build, selection, history counts, reading order, jaw,
-                fluence, MU weights, rotations (Sec. 2.2, 2.3.2, 2.3.3, 2.4)
+  source.py     azimuthal redistribution (Sec. 2.3.1), PSL build, selection,
+                history counts, reading order, jaw, fluence, MU weights,
+                rotations (Sec. 2.2, 2.3.2, 2.3.3, 2.4); Methods 1 and 2 as
+                an unsorted stream (Sec. 2.1, 2.2)
+  stream.c      the on-the-fly type/energy bin fill of Methods 1 and 2
   transport.c   double-precision photon/electron transport and tally
                 (Sec. 2.3.3 "dose counters", Sec. 2.6 cut-offs)
   readout.py    dose, batch uncertainty, normalisation (Sec. 2.3.3, 2.5),

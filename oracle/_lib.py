@@ -1,4 +1,5 @@
-"""ctypes loader of the oracle's C transport (TEST INFRASTRUCTURE).
+"""ctypes loader of the oracle's C code: transport and stream binning
+(TEST INFRASTRUCTURE).
 
 Builds ``oracle/_build/liboracle.so`` with gcc on first use.  Only the tests,
 the package smoke check and the CPU-baseline leg of the benchmark load it.
@@ -15,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "liboracle.so")
-SRC = [os.path.join(HERE, "transport.c")]
+SRC = [os.path.join(HERE, "transport.c"), os.path.join(HERE, "stream.c")]
 
 _lock = threading.Lock()
 _lib = None
@@ -61,6 +62,8 @@ def lib():
             L.ora_sample_kn.argtypes = [d, u64, i64, vp, vp]
             L.ora_sample_moller.restype = None
             L.ora_sample_moller.argtypes = [d, d, u64, i64, vp]
+            L.ora_stream_bin.restype = i64
+            L.ora_stream_bin.argtypes = [i64, vp, i32, i64, vp, vp, vp]
             L.ora_transport.restype = i32
             L.ora_transport.argtypes = ([i64] + [vp] * 6 + [i32, i32, i32, d, d, d, vp, vp, u64, u32,
                                         d, d, d, d] + [vp] * 6 + [i32])

@@ -369,17 +369,13 @@ def mu_ratios(beams) -> np.ndarray:
     return np.array([F32(m / tot) for m in mus], F32)
 
 
-def source(plan: Plan, store: Store, records, beams, phantom, h: np.ndarray,
-           z_psl: float, sad: float) -> SourceOut:
-    h = np.asarray(h, np.int64)
-    entry, use = history_map(plan, h)
-    nrec = plan.nrec[entry]
-    rec = plan.start[entry] + (plan.offset[entry] + use) % nrec
-    beam = plan.field[entry]
-    src = store.perm[rec]
-    x, y, u, v = records.x[src], records.y[src], records.u[src], records.v[src]
-    e, wt0, q = records.e[src], records.wt[src], records.q[src]
-    n = len(h)
+def to_phantom(x, y, u, v, e, wt0, q, beam, beams, phantom, z_psl: float, sad: float, collimate: bool = True):
+    """Sec. 2.2, 2.3.3 and 2.4 for records (float32 arrays) of fields `beam`
+    (index into beams): jaw model and fluence map when `collimate`, MU weight,
+    rotation into the patient and entry into the phantom box.
+
+    Returns (status, wt, pos, dirs, ptype, fixed-point energy per record)."""
+    n = len(x)
     status = np.zeros(n, np.int8)
     wt = np.zeros(n, F32)
     murat = mu_ratios(beams)
@@ -394,24 +390,26 @@ def source(plan: Plan, store: Store, records, beams, phantom, h: np.ndarray,
         if not m.any():
             continue
         zjx, zjy, sadf, zp = F32(b.z_jaw_x), F32(b.z_jaw_y), F32(sad), F32(z_psl)
-        xlo, xhi = (F32(b.x1) * zjx) / sadf, (F32(b.x2) * zjx) / sadf
-        ylo, yhi = (F32(b.y1) * zjy) / sadf, (F32(b.y2) * zjy) / sadf
-        xj = x[m] + u[m] * ((zjx - zp) / w32[m])
-        yj = y[m] + v[m] * ((zjy - zp) / w32[m])
-        acc = (xj >= xlo) & (xj <= xhi) & (yj >= ylo) & (yj <= yhi)
         ww = wt0[m].copy()
-        st = np.where(acc, ST_TRANSPORT, ST_JAW).astype(np.int8)
-        if b.fluence is not None:
-            fny, fnx = b.fluence.shape
-            ti = (sadf - zp) / w32[m]
-            fx = ((x[m] + u[m] * ti) - F32(b.fx0)) / F32(b.fdx)
-            fy = ((y[m] + v[m] * ti) - F32(b.fy0)) / F32(b.fdy)
-            ix, iy = np.floor(fx), np.floor(fy)
-            inside = (ix >= 0) & (ix < fnx) & (iy >= 0) & (iy < fny)
-            st = np.where(acc & ~inside, ST_FLUENCE, st).astype(np.int8)
-            ixc = np.clip(ix, 0, fnx - 1).astype(np.int64)
-            iyc = np.clip(iy, 0, fny - 1).astype(np.int64)
-            ww = ww * b.fluence[iyc, ixc]
+        st = np.full(m.sum(), ST_TRANSPORT, np.int8)
+        if collimate:
+            xlo, xhi = (F32(b.x1) * zjx) / sadf, (F32(b.x2) * zjx) / sadf
+            ylo, yhi = (F32(b.y1) * zjy) / sadf, (F32(b.y2) * zjy) / sadf
+            xj = x[m] + u[m] * ((zjx - zp) / w32[m])
+            yj = y[m] + v[m] * ((zjy - zp) / w32[m])
+            acc = (xj >= xlo) & (xj <= xhi) & (yj >= ylo) & (yj <= yhi)
+            st = np.where(acc, ST_TRANSPORT, ST_JAW).astype(np.int8)
+            if b.fluence is not None:
+                fny, fnx = b.fluence.shape
+                ti = (sadf - zp) / w32[m]
+                fx = ((x[m] + u[m] * ti) - F32(b.fx0)) / F32(b.fdx)
+                fy = ((y[m] + v[m] * ti) - F32(b.fy0)) / F32(b.fdy)
+                ix, iy = np.floor(fx), np.floor(fy)
+                inside = (ix >= 0) & (ix < fnx) & (iy >= 0) & (iy < fny)
+                st = np.where(acc & ~inside, ST_FLUENCE, st).astype(np.int8)
+                ixc = np.clip(ix, 0, fnx - 1).astype(np.int64)
+                iyc = np.clip(iy, 0, fny - 1).astype(np.int64)
+                ww = ww * b.fluence[iyc, ixc]
         ww = ww * murat[i]
         st = np.where((st == ST_TRANSPORT) & (ww == 0), ST_ZERO_WEIGHT, st).astype(np.int8)
         status[m] = st
@@ -448,9 +446,76 @@ def source(plan: Plan, store: Store, records, beams, phantom, h: np.ndarray,
         pos[idx] = pp + t_in[:, None] * dd
         dirs[idx] = dd
     ptype = np.where(q == 0, 0, np.where(q < 0, 1, 2)).astype(np.int32)
+    fp = np.rint(e.astype(np.float64) * wt.astype(np.float64) * 4294967296.0).astype(np.int64)
+    return status, wt, pos, dirs, ptype, fp
+
+
+def source(plan: Plan, store: Store, records, beams, phantom, h: np.ndarray,
+           z_psl: float, sad: float) -> SourceOut:
+    h = np.asarray(h, np.int64)
+    entry, use = history_map(plan, h)
+    nrec = plan.nrec[entry]
+    rec = plan.start[entry] + (plan.offset[entry] + use) % nrec
+    beam = plan.field[entry]
+    src = store.perm[rec]
+    x, y, u, v = records.x[src], records.y[src], records.u[src], records.v[src]
+    e, wt0, q = records.e[src], records.wt[src], records.q[src]
+    status, wt, pos, dirs, ptype, fp = to_phantom(x, y, u, v, e, wt0, q, beam, beams, phantom, z_psl, sad)
     accepted = (status == ST_TRANSPORT) | (status == ST_MISS)
-    e64 = e.astype(np.float64)
-    fp = np.rint(e64 * wt.astype(np.float64) * 4294967296.0).astype(np.int64)
     emitted = int(fp[accepted].sum())
     missed = int(fp[status == ST_MISS].sum())
-    return SourceOut(status, entry, use, rec, beam, ptype, pos, dirs, e64, wt, emitted, missed)
+    return SourceOut(status, entry, use, rec, beam, ptype, pos, dirs, e.astype(np.float64), wt, emitted, missed)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.1, 2.2: Methods 1 and 2, the phase space as an unsorted stream
+# --------------------------------------------------------------------------
+METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
+
+
+@dataclasses.dataclass
+class StreamOut:
+    status: np.ndarray       # int8 [n] per history (ST_*)
+    ptype: np.ndarray
+    pos: np.ndarray
+    dirs: np.ndarray
+    e: np.ndarray
+    wt: np.ndarray
+    key: np.ndarray          # int32 [n] bin (type * n_ebins + energy bin), -1 if not binned
+    emitted: int
+    missed: int
+    group_bin: np.ndarray    # int64 [groups] in the order they are sent to transport
+    group_count: np.ndarray
+    hist: np.ndarray         # int64 history ids of the binned particles in that order
+
+
+def stream_bin(records, e_edges, beam, method: int, phantom, first: int, n: int, capacity: int,
+               z_psl: float, sad: float) -> StreamOut:
+    """Methods 1 and 2: history h = first + i reads record h mod N (the
+    stream, recycled).  Method 2 applies the field's jaw model and fluence
+    map (Sec. 2.2), method 1 takes every record as it is (the phase space
+    already holds the collimation, Sec. 2.1).  The particles that pass, and
+    only those, are binned by type and energy (interior edges, as in the PSL
+    generation) and sent to transport in the paper's on-the-fly order."""
+    h = first + np.arange(n, dtype=np.int64)
+    r = h % records.n if n else h
+    x, y, u, v = records.x[r], records.y[r], records.u[r], records.v[r]
+    e, wt0, q = records.e[r], records.wt[r], records.q[r]
+    status, wt, pos, dirs, ptype, fp = to_phantom(x, y, u, v, e, wt0, q, np.zeros(n, np.int64), [beam], phantom,
+                                                  z_psl, sad, collimate=(method == METHOD_JAW_MODEL))
+    ne = len(e_edges) - 1
+    binned = ((status == ST_TRANSPORT) | (status == ST_MISS)) & (e > 0)
+    eb = np.searchsorted(np.asarray(e_edges, F32)[1:-1], e, side="right")
+    key = np.where(binned, (q != 0).astype(np.int64) * ne + eb, -1).astype(np.int32)
+    gb = np.zeros(max(n, 1), np.int64)
+    gc = np.zeros(max(n, 1), np.int64)
+    order = np.zeros(max(n, 1), np.int64)
+    key_c = np.ascontiguousarray(key)
+    ng = _lib.lib().ora_stream_bin(n, _lib._p(key_c), 2 * ne, int(capacity), _lib._p(gb), _lib._p(gc),
+                                   _lib._p(order))
+    if ng < 0:
+        raise ValueError("ora_stream_bin: bad arguments")
+    nb = int(gc[:ng].sum())
+    return StreamOut(status, ptype, pos, dirs, e.astype(np.float64), wt, key, int(fp[binned].sum()),
+                     int(fp[binned & (status == ST_MISS)].sum()), gb[:ng].copy(), gc[:ng].copy(),
+                     first + order[:nb])

@@ -26,8 +26,10 @@ EXPORTS = (
     "psl_batch_info", "psl_tally_create", "psl_tally_reset", "psl_tally_read", "transport_run",
     "transport_trace", "dose_readout", "psl_store_destroy", "psl_plan_destroy", "psl_batch_destroy",
     "psl_tally_destroy", "psl_last_error", "psl_kernel_launches", "psl_profile", "psl_profile_read",
-    "psl_build_static", "psl_atomic_peak", "psl_run", "psl_autotune",
+    "psl_build_static", "psl_atomic_peak", "psl_run", "psl_autotune", "psl_stream_bin", "psl_stream_info",
+    "psl_stream_read", "psl_batch_read", "psl_memory_trim",
 )
+METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 STATIC_MAX_RECORDS = 1 << 20
 
 vp = ctypes.c_void_p
@@ -110,6 +112,11 @@ def lib():
             "psl_run": [vp, vp, vp, vp, i64, i64, i32, vp],
             "psl_autotune": [vp, vp, vp, vp, i64, vp, vp, vp],
             "psl_profile_read": [i32, vp, vp, vp],
+            "psl_stream_bin": [vp, vp, i32, vp, i32, f32, f32, vp, i64, i64, u64, i64, vp, vp],
+            "psl_stream_info": [vp, vp, vp, vp, vp],
+            "psl_stream_read": [vp, vp, vp, vp, vp],
+            "psl_batch_read": [vp, vp, vp, vp, vp],
+            "psl_memory_trim": [u64, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -280,6 +287,41 @@ def psl_batch_from_particles(state, ptype, pid, seed: int, stream=None) -> Batch
     check(lib().psl_batch_from_particles(ptr(state), ptr(ptype), ptr(pid), int(ptype.shape[0]), int(seed),
                                          ctypes.byref(h), stream_ptr(stream)))
     return Batch(h.value)
+
+
+def psl_stream_bin(records: Records, e_edges, beam: Beam, method: int, z_psl: float, sad: float, phantom: Phantom,
+                   first: int, n: int, seed: int, capacity: int, stream=None) -> Batch:
+    """Methods 1 / 2: the on-the-fly type/energy binning of the phase-space
+    stream (see psl.h); e_edges is a host float32 array."""
+    ee = np.ascontiguousarray(e_edges, np.float32)
+    h = _out_handle()
+    check(lib().psl_stream_bin(ctypes.byref(records), ee.ctypes.data, int(len(ee) - 1), ctypes.byref(beam),
+                               int(method), float(z_psl), float(sad), ctypes.byref(phantom), int(first), int(n),
+                               int(seed), int(capacity), ctypes.byref(h), stream_ptr(stream)))
+    return Batch(h.value)
+
+
+def psl_stream_info(batch: Batch):
+    """(groups, particles kept, emitted fixed point, missed fixed point)."""
+    a, b, c, d = i64(), i64(), i64(), i64()
+    check(lib().psl_stream_info(batch.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def psl_stream_read(batch: Batch, group_bin=None, group_count=None, history=None, stream=None):
+    check(lib().psl_stream_read(batch.h, ptr(group_bin), ptr(group_count), ptr(history), stream_ptr(stream)))
+
+
+def psl_batch_read(batch: Batch, state=None, ptype=None, pid=None, stream=None):
+    check(lib().psl_batch_read(batch.h, ptr(state), ptr(ptype), ptr(pid), stream_ptr(stream)))
+
+
+def memory_trim(keep_bytes: int = 0) -> int:
+    """Return the library pool's memory beyond keep_bytes to the driver;
+    returns the bytes the pool still reserves."""
+    held = u64()
+    check(lib().psl_memory_trim(int(keep_bytes), ctypes.byref(held)))
+    return held.value
 
 
 def psl_tally_create(phantom: Phantom, n_batches: int) -> Tally:

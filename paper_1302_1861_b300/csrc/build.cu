@@ -244,17 +244,17 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
     auto fail = [&](int code, const std::string &m) { rc = psl_fail(code, m); };
     do {
         cudaError_t e;
-        if ((e = cudaMallocAsync((void **)&s->edges, edges.size() * sizeof(float), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if ((e = psl_malloc_async((void **)&s->edges, edges.size() * sizeof(float), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
         if ((e = cudaMemcpyAsync(s->edges, edges.data(), edges.size() * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
-        if ((e = cudaMallocAsync((void **)&s->offsets, (n_bins + 1) * sizeof(int64_t), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if ((e = psl_malloc_async((void **)&s->offsets, (n_bins + 1) * sizeof(int64_t), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
         size_t nn = std::max<uint32_t>(n, 1);
         bool ok = true;
         for (int b = 0; b < 2 && ok; ++b) {
-            ok &= cudaMallocAsync((void **)&keys[b], nn * 4, st) == cudaSuccess;
-            ok &= cudaMallocAsync((void **)&vals[b], nn * 4, st) == cudaSuccess;
+            ok &= psl_malloc_async((void **)&keys[b], nn * 4, st) == cudaSuccess;
+            ok &= psl_malloc_async((void **)&vals[b], nn * 4, st) == cudaSuccess;
         }
-        ok &= cudaMallocAsync(&scratch, sort_pairs_scratch_bytes(n), st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&hist, MAX_PASSES * RADIX * 4 + 16, st) == cudaSuccess;
+        ok &= psl_malloc_async(&scratch, sort_pairs_scratch_bytes(n), st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&hist, MAX_PASSES * RADIX * 4 + 16, st) == cudaSuccess;
         if (!ok) { fail(PSL_ENOMEM, "psl_build: sort buffers"); break; }
         nvalid_d = reinterpret_cast<int64_t *>(hist + MAX_PASSES * RADIX);
         cudaMemsetAsync(hist, 0, MAX_PASSES * RADIX * 4, st);
@@ -262,7 +262,7 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         const int sms = psl_sm_count();
         if (n == 0) {
             cudaMemsetAsync(s->offsets, 0, (n_bins + 1) * sizeof(int64_t), st);
-            cudaMallocAsync((void **)&s->rec, sizeof(PslRecord), st);
+            psl_malloc_async((void **)&s->rec, sizeof(PslRecord), st);
             break;
         }
         int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
@@ -274,7 +274,7 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         int g2 = (int)std::min<int64_t>((int64_t)n / 256 + 1, (int64_t)sms * 8);
         k_offsets<<<g2, 256, 0, st>>>(skeys, n, n_bins, s->offsets); PSL_NOTE_LAUNCH();
         k_count_valid<<<1, 1, 0, st>>>(s->offsets, n_bins, nvalid_d); PSL_NOTE_LAUNCH();
-        if ((e = cudaMallocAsync((void **)&packed, (size_t)n * sizeof(PslRecord), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if ((e = psl_malloc_async((void **)&packed, (size_t)n * sizeof(PslRecord), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
         {
             void *tk_ = nullptr;
             if (psl_timer_on()) psl_timer_begin(PK_GATHER, st, &tk_);
@@ -288,7 +288,7 @@ extern "C" int psl_build(const psl_params_t *prm, const psl_records_t *rec, psl_
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { fail(PSL_ECUDA, cudaGetErrorString(e)); break; }
         if (herr & PSL_DEV_ERR_TIMEOUT) { fail(PSL_ETIMEOUT, "psl_build: look-back wait gave up"); break; }
         s->n_valid = nvalid;
-        if ((e = cudaMallocAsync((void **)&s->rec, std::max<int64_t>(nvalid, 1) * sizeof(PslRecord), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
+        if ((e = psl_malloc_async((void **)&s->rec, std::max<int64_t>(nvalid, 1) * sizeof(PslRecord), st)) != cudaSuccess) { fail(PSL_ENOMEM, cudaGetErrorString(e)); break; }
         if (nvalid > 0) {
             int g3 = (int)std::min<int64_t>((nvalid + 255) / 256, (int64_t)sms * 16);
             { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_GATHER, st, &tk_); k_gather<<<g3, 256, 0, st>>>(packed, svals, nvalid, s->rec); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_GATHER, st, tk_); }

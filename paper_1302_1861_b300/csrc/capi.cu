@@ -23,6 +23,66 @@ int psl_fail(int code, const std::string &msg) {
 
 extern "C" const char *psl_last_error(void) { return g_last_error.c_str(); }
 
+// ------------------------------------------------------------------------
+// Device memory pool of the library: one per device, created on first use,
+// keeping freed blocks (release threshold = unlimited) so that the large
+// stream-ordered scratch of psl_build, psl_plan_create and psl_stream_bin is
+// mapped once, not at every call.  psl_memory_trim hands memory back.
+#include <mutex>
+
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[256] = {};
+
+cudaError_t pool_of_current(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if ((e = cudaMemPoolCreate(&p, &props)) != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        if ((e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pools[dev] = p;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t psl_malloc_async(void **ptr, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t p = nullptr;
+    cudaError_t e = pool_of_current(&p);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(ptr, bytes, p, st);
+}
+
+extern "C" int psl_memory_trim(uint64_t keep_bytes, uint64_t *held_bytes) {
+    cudaMemPool_t p = nullptr;
+    cudaError_t e = pool_of_current(&p);
+    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("psl_memory_trim: ") + cudaGetErrorString(e));
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess)
+        return psl_fail(PSL_ECUDA, std::string("psl_memory_trim: ") + cudaGetErrorString(e));
+    if ((e = cudaMemPoolTrimTo(p, (size_t)keep_bytes)) != cudaSuccess)
+        return psl_fail(PSL_ECUDA, std::string("psl_memory_trim: ") + cudaGetErrorString(e));
+    if (held_bytes) {
+        uint64_t v = 0;
+        if ((e = cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &v)) != cudaSuccess)
+            return psl_fail(PSL_ECUDA, std::string("psl_memory_trim: ") + cudaGetErrorString(e));
+        *held_bytes = v;
+    }
+    return PSL_OK;
+}
+
 extern "C" void psl_physics_default(psl_physics_t *out) {
     if (!out) return;
     out->photon_cut = 0.010f;                        // Sec. 2.6

@@ -208,13 +208,13 @@ struct Pool {   // frees temporaries at scope exit (stream ordered)
     bool ok = true;
     template <class T> T *get(int64_t n) {
         void *p = nullptr;
-        if (cudaMallocAsync(&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), st) != cudaSuccess) { ok = false; return nullptr; }
+        if (psl_malloc_async(&p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), st) != cudaSuccess) { ok = false; return nullptr; }
         ptrs.push_back(p);
         return (T *)p;
     }
     void *raw(size_t bytes) {
         void *p = nullptr;
-        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 16), st) != cudaSuccess) { ok = false; return nullptr; }
+        if (psl_malloc_async(&p, std::max<size_t>(bytes, 16), st) != cudaSuccess) { ok = false; return nullptr; }
         ptrs.push_back(p);
         return p;
     }
@@ -230,6 +230,22 @@ extern "C" void psl_plan_destroy(psl_plan_t *p) {
     for (void *q : ptrs)
         if (q) cudaFreeAsync(q, p->stream);
     delete p;
+}
+
+int psl_beams_dev(const psl_beam_t *beams, int n, float sad, float z_psl, BeamDev **out, cudaStream_t st) {
+    *out = nullptr;
+    psl_beam_t *bd = nullptr;
+    if (psl_malloc_async((void **)&bd, n * sizeof(psl_beam_t), st) != cudaSuccess ||
+        psl_malloc_async((void **)out, n * sizeof(BeamDev), st) != cudaSuccess) {
+        if (bd) cudaFreeAsync(bd, st);
+        if (*out) { cudaFreeAsync(*out, st); *out = nullptr; }
+        return psl_fail(PSL_ENOMEM, "beam table allocation");
+    }
+    cudaMemcpyAsync(bd, beams, n * sizeof(psl_beam_t), cudaMemcpyHostToDevice, st);
+    k_beams<<<1, 32, 0, st>>>(bd, n, sad, z_psl, *out); PSL_NOTE_LAUNCH();
+    cudaFreeAsync(bd, st);
+    PSL_CUDA(cudaGetLastError());
+    return PSL_OK;
 }
 
 extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams, int32_t n_beams, float sad,
@@ -264,7 +280,7 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
         int64_t *cnt = tmp.get<int64_t>(n_beams), *ebase = tmp.get<int64_t>(n_beams + 1);
         int32_t *selpos = tmp.get<int32_t>(nflag);
         void *sscr = tmp.raw(scan_i64_scratch_bytes(std::max<int64_t>(nflag, 1 << 20)));
-        cudaError_t e = cudaMallocAsync((void **)&p->beams, n_beams * sizeof(BeamDev), st);
+        cudaError_t e = psl_malloc_async((void **)&p->beams, n_beams * sizeof(BeamDev), st);
         if (!tmp.ok || e != cudaSuccess) { psl_plan_destroy(p); return psl_fail(PSL_ENOMEM, "psl_plan_create: allocation"); }
         cudaMemcpyAsync(bd, beams, n_beams * sizeof(psl_beam_t), cudaMemcpyHostToDevice, st);
         k_beams<<<1, 32, 0, st>>>(bd, n_beams, sad, store->z_psl, p->beams); PSL_NOTE_LAUNCH();
@@ -279,12 +295,12 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
         if (n_entries <= 0 || n_entries >= (1ll << 32)) { psl_plan_destroy(p); return psl_fail(PSL_EINVAL, "psl_plan_create: no PSL selected (or too many)"); }
         p->n_entries = n_entries;
         bool ok = true;
-        ok &= cudaMallocAsync((void **)&p->e_beam, n_entries * 4, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->e_psl, n_entries * 4, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->e_start, n_entries * 8, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->e_nrec, n_entries * 8, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->e_count, n_entries * 8, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->e_offset, n_entries * 8, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->e_beam, n_entries * 4, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->e_psl, n_entries * 4, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->e_start, n_entries * 8, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->e_nrec, n_entries * 8, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->e_count, n_entries * 8, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->e_offset, n_entries * 8, st) == cudaSuccess;
         int32_t *e_group = tmp.get<int32_t>(n_entries);
         int64_t *C = tmp.get<int64_t>(n_entries + 1), *act = tmp.get<int64_t>(n_entries), *A = tmp.get<int64_t>(n_entries + 1);
         void *sscr2 = tmp.raw(scan_i64_scratch_bytes(n_entries + 1));
@@ -308,12 +324,12 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
         int64_t *ghist = tmp.get<int64_t>(n_te), *lens = tmp.get<int64_t>(n_active), *X2 = tmp.get<int64_t>(n_active + 1);
         int32_t *seg_g = tmp.get<int32_t>(n_active);
         ok = tmp.ok;
-        ok &= cudaMallocAsync((void **)&p->sorted, n_active * 4, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->seg_h, n_active * 8, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->seg_r0, n_active * 8, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->seg_w, n_active * 4, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->group_seg, (n_te + 1) * 8, st) == cudaSuccess;
-        ok &= cudaMallocAsync((void **)&p->group_start, (n_te + 1) * 8, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->sorted, n_active * 4, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->seg_h, n_active * 8, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->seg_r0, n_active * 8, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->seg_w, n_active * 4, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->group_seg, (n_te + 1) * 8, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->group_start, (n_te + 1) * 8, st) == cudaSuccess;
         void *sscr3 = tmp.raw(scan_i64_scratch_bytes(n_active + 1));
         if (!ok || !tmp.ok) { psl_plan_destroy(p); return psl_fail(PSL_ENOMEM, "psl_plan_create: order arrays"); }
         k_compact<<<grid_for(n_entries), 256, 0, st>>>(act, A, p->e_count, n_entries, k0, v0); PSL_NOTE_LAUNCH();

@@ -119,6 +119,10 @@ struct psl_batch {
     int64_t n_photons = 0, n_electrons = 0;
     int consumed = 0;
     cudaStream_t stream = nullptr;
+    // batches from psl_stream_bin: the on-the-fly groups (device arrays)
+    int64_t s_groups = 0, s_binned = 0;
+    int64_t *s_gbin = nullptr, *s_gcount = nullptr, *s_hist = nullptr;
+    unsigned long long s_emitted = 0, s_missed = 0;
 };
 
 struct Workspace;
@@ -240,3 +244,12 @@ __device__ __forceinline__ void queue_push(const Queue &q, const Particle &p, ui
 
 // grid size for a memory-bound kernel: multiple of the SM count
 int psl_sm_count();
+
+// Stream-ordered allocation from the library's device memory pool (freed
+// blocks stay in the pool for the next call; see psl_memory_trim).
+cudaError_t psl_malloc_async(void **ptr, size_t bytes, cudaStream_t st);
+
+// Device copies of beams (host array) with their float32 jaw bounds, MU
+// ratios and rotation matrices; *out is stream-ordered device memory the
+// caller frees with cudaFreeAsync.
+int psl_beams_dev(const psl_beam_t *beams, int n, float sad, float z_psl, BeamDev **out, cudaStream_t st);

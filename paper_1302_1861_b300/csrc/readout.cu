@@ -128,7 +128,7 @@ extern "C" int psl_atomic_peak(int64_t n_cells, int64_t n_updates, double *updat
     if (n_cells <= 0 || n_updates <= 0 || !updates_per_s) return psl_fail(PSL_EINVAL, "psl_atomic_peak: bad argument");
     cudaStream_t st = as_stream(stream_);
     unsigned long long *cells = nullptr;
-    PSL_CUDA(cudaMallocAsync((void **)&cells, n_cells * 8, st));
+    PSL_CUDA(psl_malloc_async((void **)&cells, n_cells * 8, st));
     PSL_CUDA(cudaMemsetAsync(cells, 0, n_cells * 8, st));
     cudaEvent_t a, b;
     cudaEventCreate(&a);

@@ -57,14 +57,28 @@ __global__ void k_from_particles(const float *state, const int32_t *ptype, const
     }
 }
 
+__global__ void k_batch_read(const Particle *p, int64_t cap, int64_t nph, int64_t nel, float *state, int32_t *ptype,
+                             uint64_t *pid) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nph + nel; t += (int64_t)gridDim.x * blockDim.x) {
+        const Particle q = load_particle(p + (t < nph ? t : cap - 1 - (t - nph)));
+        if (state) {
+            state[8 * t] = q.x; state[8 * t + 1] = q.y; state[8 * t + 2] = q.z;
+            state[8 * t + 3] = q.u; state[8 * t + 4] = q.v; state[8 * t + 5] = q.w;
+            state[8 * t + 6] = q.e; state[8 * t + 7] = q.wt;
+        }
+        if (ptype) ptype[t] = (int32_t)q.type;
+        if (pid) pid[t] = ((uint64_t)q.pid_hi << 32) | q.pid_lo;
+    }
+}
+
 }  // namespace
 
 static int alloc_batch(int64_t n, int64_t first, cudaStream_t st, psl_batch **out) {
     psl_batch *b = new psl_batch();
     b->n_histories = n; b->first_history = first; b->cap = std::max<int64_t>(n, 1);
     b->stream = st;
-    cudaError_t e1 = cudaMallocAsync((void **)&b->p, b->cap * sizeof(Particle), st);
-    cudaError_t e2 = cudaMallocAsync((void **)&b->counts, 32, st);
+    cudaError_t e1 = psl_malloc_async((void **)&b->p, b->cap * sizeof(Particle), st);
+    cudaError_t e2 = psl_malloc_async((void **)&b->counts, 32, st);
     if (e1 != cudaSuccess || e2 != cudaSuccess) { psl_batch_destroy(b); return psl_fail(PSL_ENOMEM, "batch allocation"); }
     cudaMemsetAsync(b->counts, 0, 32, st);
     *out = b;
@@ -140,6 +154,16 @@ extern "C" int psl_batch_from_particles(const float *state, const int32_t *ptype
     return PSL_OK;
 }
 
+extern "C" int psl_batch_read(const psl_batch_t *b, float *state, int32_t *ptype, uint64_t *pid, void *stream_) {
+    if (!b || b->lazy) return psl_fail(PSL_EINVAL, "psl_batch_read: null or lazy batch");
+    const int64_t n = b->n_photons + b->n_electrons;
+    if (n <= 0) return PSL_OK;
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+    k_batch_read<<<grid, 256, 0, as_stream(stream_)>>>(b->p, b->cap, b->n_photons, b->n_electrons, state, ptype, pid); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaGetLastError());
+    return PSL_OK;
+}
+
 extern "C" int psl_batch_info(const psl_batch_t *b, int64_t *n_histories, int64_t *n_photons, int64_t *n_electrons) {
     if (!b) return psl_fail(PSL_EINVAL, "psl_batch_info: null batch");
     if (n_histories) *n_histories = b->n_histories;
@@ -152,5 +176,8 @@ extern "C" void psl_batch_destroy(psl_batch_t *b) {
     if (!b) return;
     if (b->p) cudaFreeAsync(b->p, b->stream);
     if (b->counts) cudaFreeAsync(b->counts, b->stream);
+    if (b->s_gbin) cudaFreeAsync(b->s_gbin, b->stream);
+    if (b->s_gcount) cudaFreeAsync(b->s_gcount, b->stream);
+    if (b->s_hist) cudaFreeAsync(b->s_hist, b->stream);
     delete b;
 }

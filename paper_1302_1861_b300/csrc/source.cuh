@@ -74,6 +74,60 @@ __device__ __forceinline__ void divmod_u64(uint64_t a, uint64_t b, uint64_t &q, 
     }
 }
 
+// Sec. 2.2, 2.3.3, 2.4 for one record and field: jaw model and fluence map
+// (when `collimate`), MU weight, rotation into the patient and entry into the
+// phantom box [0, L].  Sets o.ptype, o.status and o.s.
+__device__ __forceinline__ void record_to_phantom(const PslRecord &R, const BeamDev &B, float z_psl, const float L[3],
+                                                  const float origin[3], bool collimate, SrcOut &o) {
+    o.ptype = R.q == 0 ? 0 : (R.q < 0 ? 1 : 2);
+    // jaw model (Sec. 2.2)
+    float w2 = __fsub_rn(__fsub_rn(1.0f, __fmul_rn(R.u, R.u)), __fmul_rn(R.v, R.v));
+    if (!(w2 > 0.0f)) { o.status = PSL_SRC_JAW; return; }
+    const float wz = __fsqrt_rn(w2);
+    const float xj = __fadd_rn(R.x, __fmul_rn(R.u, __fdiv_rn(B.dzx, wz)));
+    const float yj = __fadd_rn(R.y, __fmul_rn(R.v, __fdiv_rn(B.dzy, wz)));
+    if (collimate && !(xj >= B.xlo && xj <= B.xhi && yj >= B.ylo && yj <= B.yhi)) { o.status = PSL_SRC_JAW; return; }
+    // fluence map at the isocentre plane (Sec. 2.2, 2.4)
+    float wt = R.wt;
+    if (collimate && B.fluence) {
+        const float ti = __fdiv_rn(B.diso, wz);
+        const float fx = __fdiv_rn(__fsub_rn(__fadd_rn(R.x, __fmul_rn(R.u, ti)), B.fx0), B.fdx);
+        const float fy = __fdiv_rn(__fsub_rn(__fadd_rn(R.y, __fmul_rn(R.v, ti)), B.fy0), B.fdy);
+        const float ix = floorf(fx), iy = floorf(fy);
+        if (!(ix >= 0.0f && ix < (float)B.fnx && iy >= 0.0f && iy < (float)B.fny)) { o.status = PSL_SRC_FLUENCE; return; }
+        wt = __fmul_rn(wt, __ldg(B.fluence + (int)iy * B.fnx + (int)ix));
+    }
+    wt = __fmul_rn(wt, B.mu_ratio);        // MU weight (Sec. 2.3.3)
+    if (wt == 0.0f) { o.status = PSL_SRC_ZERO_WEIGHT; return; }
+    // rotate about the isocentre into the patient frame, then phantom-local
+    const float pb[3] = {R.x, R.y, z_psl - B.sad};
+    const float db[3] = {R.u, R.v, wz};
+    float p[3], d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = B.r[3 * k] * pb[0] + B.r[3 * k + 1] * pb[1] + B.r[3 * k + 2] * pb[2] + B.iso[k] - origin[k];
+        d[k] = B.r[3 * k] * db[0] + B.r[3 * k + 1] * db[1] + B.r[3 * k + 2] * db[2];
+    }
+    // entry of the full line into the phantom box [0, L]
+    float tin = -INFINITY, tout = INFINITY;
+    bool miss = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (d[k] != 0.0f) {
+            float t0 = (0.0f - p[k]) / d[k], t1 = (L[k] - p[k]) / d[k];
+            tin = fmaxf(tin, fminf(t0, t1));
+            tout = fminf(tout, fmaxf(t0, t1));
+        } else if (p[k] < 0.0f || p[k] > L[k]) {
+            miss = true;
+        }
+    }
+    o.s[6] = R.e; o.s[7] = wt;
+    if (miss || !(tin < tout)) { o.status = PSL_SRC_MISS; return; }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { o.s[k] = p[k] + tin * d[k]; o.s[3 + k] = d[k]; }
+    o.status = PSL_SRC_TRANSPORT;
+}
+
 __device__ __forceinline__ void source_at(const PlanDev &P, const int64_t *gs_sh, int64_t h, int g, int64_t q,
                                           SrcOut &o) {
     const int64_t hl = h - gs_sh[g];
@@ -87,55 +141,7 @@ __device__ __forceinline__ void source_at(const PlanDev &P, const int64_t *gs_sh
     o.entry = entry; o.use = r; o.rec = rec;
     const int b = P.e_beam[entry];
     o.beam = b;
-    const PslRecord R = P.rec[rec];
-    const BeamDev &B = P.beams[b];
-    o.ptype = R.q == 0 ? 0 : (R.q < 0 ? 1 : 2);
-    // jaw model (Sec. 2.2)
-    float w2 = __fsub_rn(__fsub_rn(1.0f, __fmul_rn(R.u, R.u)), __fmul_rn(R.v, R.v));
-    if (!(w2 > 0.0f)) { o.status = PSL_SRC_JAW; return; }
-    const float wz = __fsqrt_rn(w2);
-    const float xj = __fadd_rn(R.x, __fmul_rn(R.u, __fdiv_rn(B.dzx, wz)));
-    const float yj = __fadd_rn(R.y, __fmul_rn(R.v, __fdiv_rn(B.dzy, wz)));
-    if (!(xj >= B.xlo && xj <= B.xhi && yj >= B.ylo && yj <= B.yhi)) { o.status = PSL_SRC_JAW; return; }
-    // fluence map at the isocentre plane (Sec. 2.2, 2.4)
-    float wt = R.wt;
-    if (B.fluence) {
-        const float ti = __fdiv_rn(B.diso, wz);
-        const float fx = __fdiv_rn(__fsub_rn(__fadd_rn(R.x, __fmul_rn(R.u, ti)), B.fx0), B.fdx);
-        const float fy = __fdiv_rn(__fsub_rn(__fadd_rn(R.y, __fmul_rn(R.v, ti)), B.fy0), B.fdy);
-        const float ix = floorf(fx), iy = floorf(fy);
-        if (!(ix >= 0.0f && ix < (float)B.fnx && iy >= 0.0f && iy < (float)B.fny)) { o.status = PSL_SRC_FLUENCE; return; }
-        wt = __fmul_rn(wt, __ldg(B.fluence + (int)iy * B.fnx + (int)ix));
-    }
-    wt = __fmul_rn(wt, B.mu_ratio);        // MU weight (Sec. 2.3.3)
-    if (wt == 0.0f) { o.status = PSL_SRC_ZERO_WEIGHT; return; }
-    // rotate about the isocentre into the patient frame, then phantom-local
-    const float pb[3] = {R.x, R.y, P.z_psl - B.sad};
-    const float db[3] = {R.u, R.v, wz};
-    float p[3], d[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        p[k] = B.r[3 * k] * pb[0] + B.r[3 * k + 1] * pb[1] + B.r[3 * k + 2] * pb[2] + B.iso[k] - P.origin[k];
-        d[k] = B.r[3 * k] * db[0] + B.r[3 * k + 1] * db[1] + B.r[3 * k + 2] * db[2];
-    }
-    // entry of the full line into the phantom box [0, L]
-    float tin = -INFINITY, tout = INFINITY;
-    bool miss = false;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        if (d[k] != 0.0f) {
-            float t0 = (0.0f - p[k]) / d[k], t1 = (P.L[k] - p[k]) / d[k];
-            tin = fmaxf(tin, fminf(t0, t1));
-            tout = fminf(tout, fmaxf(t0, t1));
-        } else if (p[k] < 0.0f || p[k] > P.L[k]) {
-            miss = true;
-        }
-    }
-    o.s[6] = R.e; o.s[7] = wt;
-    if (miss || !(tin < tout)) { o.status = PSL_SRC_MISS; return; }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { o.s[k] = p[k] + tin * d[k]; o.s[3 + k] = d[k]; }
-    o.status = PSL_SRC_TRANSPORT;
+    record_to_phantom(P.rec[rec], P.beams[b], P.z_psl, P.L, P.origin, true, o);
 }
 
 __device__ __forceinline__ void source_one(const PlanDev &P, const int64_t *gs_sh, int64_t h, SrcOut &o) {
