@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-apr", action="store_true")
     ap.add_argument("--no-methods", action="store_true")
+    ap.add_argument("--no-t1pct", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -225,17 +226,18 @@ def main():
     tally = capi.psl_tally_create(dw.phantom, nb)       # device buffers held across steps
 
     def step(dwx, out_dose, plain=False):
-        """psl_build + psl_plan_create + all batches + dose_readout.  Default:
-        all batches in one psl_run call (no host synchronisation); plain:
-        psl_source_batch + transport_run batch by batch."""
+        """psl_build + psl_plan_create + all histories + dose_readout.
+        Default: the whole range in one psl_run call (no host
+        synchronisation); plain: psl_source_batch + transport_run piece by
+        piece (N_b pieces).  Either way every history's deposits go to the
+        tally slice (batch) of its id."""
         store = capi.psl_build(dwx.params, dwx.records)
         plan = capi.psl_plan_create(store, dwx.beams, w.sad, n_plan, w.seed)
         capi.psl_tally_reset(tally)
         if plain:
-            for b in range(nb):
-                f0, cnt, stride = engine.batch_histories(first, per_rank, nb, b)
-                batch = capi.psl_source_batch(plan, dwx.phantom, f0, cnt, stride)
-                capi.transport_run(dwx.phantom, phys, batch, tally, b)
+            for f0, cnt in engine.chunks(first, per_rank, -(-per_rank // nb)):
+                batch = capi.psl_source_batch(plan, dwx.phantom, f0, cnt, 1)
+                capi.transport_run(dwx.phantom, phys, batch, tally, capi.SLICE_BY_HISTORY)
                 batch.close()
         else:
             capi.psl_run(plan, dwx.phantom, phys, tally, first, per_rank)
@@ -308,6 +310,14 @@ def main():
     rel = float((s[sl] / d[sl]).mean())
     n_1pct = per_rank * (rel / 0.01) ** 2
 
+    # time to 1 % at the isocentre, measured: whole plans of N histories, N
+    # from the run's sigma, raised until the criterion holds
+    t1pct = None
+    if rank == 0 and world == 1 and not args.no_t1pct:
+        t1pct = time_to_1pct(capi, torch, w, dw, phys, per_rank * (rel / 0.01) ** 2, sl, (nz, ny, nx))
+        t1pct["extrapolated_histories"] = n_1pct
+        t1pct["extrapolated_seconds"] = n_1pct / (per_rank / t_step)
+
     # e2e: pinned host records/phantom uploaded and results read back inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -378,8 +388,9 @@ def main():
                            "batches": nb, "l2": "inputs > L2 and L2 flushed between steps",
                            "parallelism": f"history-range shards x{world}"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
-                "time_to_1pct": {"histories": n_1pct, "seconds": n_1pct / (per_rank / t_step),
-                                 "isocentre_rel_sigma_at_run": rel, "kind": "extrapolated from the run's sigma"},
+                "time_to_1pct": t1pct if t1pct is not None else
+                {"histories": n_1pct, "seconds": n_1pct / (per_rank / t_step), "isocentre_rel_sigma_at_run": rel,
+                 "kind": "extrapolated from the run's sigma"},
                 "energy_balance": float((lg[1] + lg[2] - lg[0]) / lg[0]),
                 "transport": transport,
                 "modes": {"batched_psl_run": value, "plain_per_batch": per_rank * world / t_plain,
@@ -404,6 +415,44 @@ THREAD_INST_PER_WOODCOCK_STEP = 439.6
 DRAM_BYTES_PER_HISTORY = {"electron": 28.22, "photon": 40.06}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
+
+
+def time_to_1pct(capi, torch, w, dw, phys, n_est, sl, shape):
+    """Wall time of a whole plan (psl_build, psl_plan_create, psl_run of all
+    batches, dose_readout) of N histories whose isocentre uncertainty (mean
+    sigma/D over the 3x3x3 voxels at the isocentre, N_b = 10 batches) is at
+    most 1 %.  N starts 5 % above the estimate and grows until it holds."""
+    from paper_1302_1861_b300 import engine
+    nvox = dw.mat_t.numel()
+    dose = torch.empty(nvox, dtype=torch.float64, device="cuda")
+    sigma = torch.empty_like(dose)
+    lg = torch.empty(3, dtype=torch.float64, device="cuda")
+    n = int(n_est * 1.05)
+    tries = []
+    for _ in range(3):
+        tally = capi.psl_tally_create(dw.phantom, w.n_batches)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        store = capi.psl_build(dw.params, dw.records)
+        plan = capi.psl_plan_create(store, dw.beams, w.sad, n, w.seed)
+        capi.psl_run(plan, dw.phantom, phys, tally, 0, n)
+        _, n_total, _ = plan.info()
+        capi.dose_readout(tally, dw.phantom, engine.normalisation(n_total, n, w.records.n * w.binning.apr_copies),
+                          dose, sigma, lg)
+        e1.record()
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        d = dose.view(*shape).cpu().numpy()
+        s = sigma.view(*shape).cpu().numpy()
+        rel = float((s[sl] / d[sl]).mean())
+        tries.append({"histories": n, "seconds": secs, "isocentre_rel_sigma": rel})
+        tally.close(); plan.close(); store.close()
+        if rel <= 0.01:
+            return {"histories": n, "seconds": secs, "isocentre_rel_sigma": rel, "kind": "measured",
+                    "histories_per_s": n / secs, "tries": tries}
+        n = int(n * (rel / 0.01) ** 2 * 1.02)
+    return {"histories": None, "seconds": None, "kind": "measured: not reached in 3 tries", "tries": tries}
 
 
 def stream_method_run(capi, engine, torch, flush, w, dw, n, capacity=1 << 20):

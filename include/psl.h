@@ -217,7 +217,8 @@ PSL_API int psl_store_read(const psl_store_t *store, int64_t *offsets, int64_t *
  * histories (N = n_histories, N_total = sum of N_j over all entries), so the
  * counts sum to N exactly.  Each entry reads its PSL from a random record
  * offset drawn from Philox(seed; beam, PSL id).  `beams` is a host array.
- * Requires 0 < n_histories < 2^32.  Synchronises stream. */
+ * Requires 0 < n_histories < 2^62 and fewer than 2^32 - 1 histories for
+ * every selected PSL (PSL_EINVAL otherwise).  Synchronises stream. */
 PSL_API int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams, int32_t n_beams, float sad,
                     int64_t n_histories, uint64_t seed, psl_plan_t **out, void *stream);
 
@@ -328,6 +329,15 @@ PSL_API int psl_batch_read(const psl_batch_t *batch, float *state, int32_t *ptyp
  * transported). */
 PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64_t *n_photons, int64_t *n_electrons);
 
+/* Tally slices (batches, Sec. 2.3.3).  A history's deposits all go to one
+ * slice; with PSL_SLICE_BY_HISTORY that slice is the first word of
+ * Philox(key = seed; counter = (0, 4, history id)) times n_batches / 2^32,
+ * so every slice is an independent pseudo-random subset of the histories,
+ * whatever order they are read in, and the batch standard deviation is a
+ * valid uncertainty.  1 <= n_batches <= PSL_MAX_BATCHES. */
+#define PSL_SLICE_BY_HISTORY (-1)
+#define PSL_MAX_BATCHES 1024
+
 /* One int64 tally of nz*ny*nx voxels per batch, plus a 12-slot ledger:
  * 0 emitted, 1 escaped, 2 deposited (fixed point, 2^-32 MeV per unit
  * weight), 3 Compton, 4 photoelectric and 5 pair events, 6 electron steps,
@@ -341,7 +351,9 @@ PSL_API int psl_tally_reset(psl_tally_t *tally, void *stream);
 PSL_API int psl_tally_read(const psl_tally_t *tally, int64_t *tallies, int64_t *ledger, void *stream);
 
 /* Sec. 2.3.3.  Transport every particle of the batch and its secondaries
- * through the phantom and add the deposits to tally slice `batch_index`.
+ * through the phantom and add the deposits to tally slice `batch_index`, or,
+ * with PSL_SLICE_BY_HISTORY, to the slice of each particle's history (for
+ * caller particles: of its particle id).
  * Photons: Woodcock tracking, Klein-Nishina Compton (Kahn), photoelectric,
  * pair.  Electrons/positrons: class-II condensed history, restricted Bethe
  * stopping, hard Moller and bremsstrahlung, Highland multiple scattering.
@@ -355,18 +367,19 @@ PSL_API int transport_run(const psl_phantom_t *phantom, const psl_physics_t *phy
 
 /* transport_run that also adds, per history (or caller particle) i of the
  * batch, its deposited and escaped fixed-point energy and its event count
- * (device arrays of the batch's n_histories, added to). */
+ * (device arrays of the batch's n_histories, added to).  At most 2^22
+ * histories (or particles) per traced batch. */
 PSL_API int transport_trace(const psl_phantom_t *phantom, const psl_physics_t *physics, psl_batch_t *batch,
                     psl_tally_t *tally, int32_t batch_index, int64_t *hist_dep, int64_t *hist_esc,
                     int32_t *hist_events, void *stream);
 
 /* Sec. 2.3.3, all fields of a plan in one call (the batched IMRT launch).
- * Runs histories [first, first+n) of the plan as the tally's N_b batches
- * (batch b takes histories first + b + k N_b, into tally slice b): source
+ * Runs histories [first, first+n) of the plan in reading order, each
+ * history's deposits into its tally slice (PSL_SLICE_BY_HISTORY): source
  * stage and transport of every beam/segment, with no host synchronisation
- * between batches: each pass is followed by 3 secondary generations launched
+ * between passes: each pass is followed by 3 secondary generations launched
  * unchecked, after which the host reads the queue counts once per further
- * generation (usually once per batch).  use_graph = 1 records the whole
+ * generation (usually once per pass).  use_graph = 1 records the whole
  * sequence once as a CUDA graph with a fixed budget of 10 generations per
  * pass (kernels of an empty generation exit at once), keeps it in the tally
  * for this plan, range, phantom and settings, and replays it with a single

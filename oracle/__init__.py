@@ -73,6 +73,24 @@ def transport(ptype, pos, dirs, e, wt, pid, phantom, seed, flags=0, nthreads=0,
     return tally, ledger
 
 
+TAG_BATCH = 4
+
+
+def history_slices(h: np.ndarray, seed: int, n_batches: int) -> np.ndarray:
+    """Batch of every history (Sec. 2.3.3: independent batches): the first
+    word r of Philox(key = seed; counter = (0, TAG_BATCH, history id)) scaled
+    to [0, N_b) as floor(r N_b / 2^32).  A pseudo-random partition: every
+    batch is an independent sample whatever order the histories are read in."""
+    h = np.asarray(h, np.uint64)
+    ctr = np.zeros((len(h), 4), np.uint32)
+    ctr[:, 1] = TAG_BATCH
+    ctr[:, 2] = (h & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    ctr[:, 3] = (h >> np.uint64(32)).astype(np.uint32)
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], np.uint32)
+    r = philox(ctr, key)[:, 0].astype(np.uint64)
+    return ((r * np.uint64(n_batches)) >> np.uint64(32)).astype(np.int64)
+
+
 def run_plan(w, n_histories=None, first=0, n_batches=None, nthreads=0, flags=0,
              store=None, plan=None):
     """Whole path for a workload on the CPU: build, plan, source, transport
@@ -87,10 +105,10 @@ def run_plan(w, n_histories=None, first=0, n_batches=None, nthreads=0, flags=0,
     nz, ny, nx = w.phantom.shape
     tallies = np.zeros((nb, nz, ny, nx), np.int64)
     ledger = np.zeros(8, np.int64)
+    h_all = np.arange(first, first + n_h, dtype=np.int64)
+    sl = history_slices(h_all, w.seed, nb)
     for b in range(nb):
-        # batch b: every nb-th history, so that each batch samples every
-        # energy division (independent batches, Sec. 2.3.3)
-        h = np.arange(first + b, first + n_h, nb, dtype=np.int64)
+        h = h_all[sl == b]                  # batch b: the histories drawn into it
         s = source.source(plan, store, w.records, w.beams, w.phantom, h, w.z_psl, w.sad)
         ledger[L_EMITTED] += s.emitted_fp
         ledger[L_ESCAPED] += s.missed_fp

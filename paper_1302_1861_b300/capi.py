@@ -30,6 +30,7 @@ EXPORTS = (
     "psl_stream_read", "psl_batch_read", "psl_memory_trim",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
+SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
 STATIC_MAX_RECORDS = 1 << 20
 
 vp = ctypes.c_void_p

@@ -148,6 +148,14 @@ __global__ void k_counts(const int64_t *C, int64_t n_entries, uint64_t n_sim, co
     }
 }
 
+__global__ void k_max_count(const int64_t *e_count, int64_t n, unsigned long long *mx) {
+    unsigned long long m = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)e_count[k]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
+}
+
 __global__ void k_compact(const int64_t *act, const int64_t *A, const int64_t *e_count, int64_t n_entries,
                           uint32_t *keys, uint32_t *vals) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_entries; k += (int64_t)gridDim.x * blockDim.x)
@@ -252,7 +260,7 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
                                int64_t n_histories, uint64_t seed, psl_plan_t **out, void *stream_) {
     if (!store || !beams || !out || n_beams <= 0) return psl_fail(PSL_EINVAL, "psl_plan_create: bad argument");
     *out = nullptr;
-    if (n_histories <= 0 || n_histories >= (1ll << 32)) return psl_fail(PSL_EINVAL, "psl_plan_create: n_histories out of range");
+    if (n_histories <= 0 || n_histories >= (1ll << 62)) return psl_fail(PSL_EINVAL, "psl_plan_create: n_histories out of range");
     if (!(sad > 0.f)) return psl_fail(PSL_EINVAL, "psl_plan_create: sad must be > 0");
     double mu_tot = 0;
     for (int i = 0; i < n_beams; ++i) {
@@ -313,9 +321,16 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
                                                       seed, p->e_count, p->e_offset, act); PSL_NOTE_LAUNCH();
         scan_i64(act, A, n_entries, sscr2, st);
         int64_t n_active = 0;
+        unsigned long long *mx = tmp.get<unsigned long long>(1), max_count = 0;
+        if (!tmp.ok) { psl_plan_destroy(p); return psl_fail(PSL_ENOMEM, "psl_plan_create: entry arrays"); }
+        cudaMemsetAsync(mx, 0, 8, st);
+        k_max_count<<<grid_for(n_entries), 256, 0, st>>>(p->e_count, n_entries, mx); PSL_NOTE_LAUNCH();
         cudaMemcpyAsync(&n_active, A + n_entries, 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(&max_count, mx, 8, cudaMemcpyDeviceToHost, st);
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) { psl_plan_destroy(p); return psl_fail(PSL_ECUDA, cudaGetErrorString(e)); }
         if (p->n_total_psl <= 0) { psl_plan_destroy(p); return psl_fail(PSL_EINVAL, "psl_plan_create: selected PSLs hold no records"); }
+        // a PSL's history count keys the entry order sort (32 bits)
+        if (max_count >= 0xFFFFFFFFull) { psl_plan_destroy(p); return psl_fail(PSL_EINVAL, "psl_plan_create: a PSL would get 2^32 or more histories"); }
         p->n_active = n_active;
         // order entries: (group, count descending, entry) via two stable sorts
         uint32_t *k0 = tmp.get<uint32_t>(n_active), *v0 = tmp.get<uint32_t>(n_active);

@@ -140,6 +140,12 @@ struct psl_tally {
 #define TAG_PARTICLE 0u
 #define TAG_OFFSET 1u
 #define TAG_CHILD 2u
+#define TAG_BATCH 4u
+
+// A particle's `root` word: bits 22-31 hold the tally slice (batch) of its
+// history, bits 0-21 the history's index in a traced transport call.
+#define ROOT_SLICE_SHIFT 22
+#define ROOT_INDEX_MASK ((1u << ROOT_SLICE_SHIFT) - 1u)
 
 struct u32x4 { uint32_t a, b, c, d; };
 
@@ -200,6 +206,15 @@ struct Rng {
         return ((float)(r >> 9) + 0.5f) * (1.0f / 8388608.0f);
     }
 };
+
+// Tally slice of history (p0, p1) among nb (Sec. 2.3.3 batches): the first
+// word of Philox(key seed; counter (0, TAG_BATCH, history id)) scaled to
+// [0, nb).  Every batch is an independent pseudo-random subset of the
+// histories, whatever the reading order.
+__device__ __forceinline__ uint32_t history_slice(uint32_t p0, uint32_t p1, const uint32_t *rk, uint32_t nb) {
+    const u32x4 r = philox10_rk(0u, TAG_BATCH, p0, p1, rk);
+    return __umulhi(r.a, nb);
+}
 
 __device__ __forceinline__ void child_id(uint64_t seed, uint32_t p0, uint32_t p1, uint32_t ordinal,
                                          uint32_t &c0, uint32_t &c1) {

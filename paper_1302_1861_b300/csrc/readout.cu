@@ -53,7 +53,7 @@ __global__ void k_ledger_out(const unsigned long long *ledger, const unsigned lo
 }  // namespace
 
 extern "C" int psl_tally_create(const psl_phantom_t *ph, int32_t n_batches, psl_tally_t **out) {
-    if (!ph || !out || n_batches <= 0 || ph->nx <= 0 || ph->ny <= 0 || ph->nz <= 0)
+    if (!ph || !out || n_batches <= 0 || n_batches > PSL_MAX_BATCHES || ph->nx <= 0 || ph->ny <= 0 || ph->nz <= 0)
         return psl_fail(PSL_EINVAL, "psl_tally_create: bad argument");
     *out = nullptr;
     psl_tally *t = new psl_tally();

@@ -70,7 +70,9 @@ struct Args {
     uint32_t k0, k1;          // the seed's two words (Philox key)
     uint32_t rk[20];          // Philox key schedule of the seed
     Tables tab;
-    unsigned long long *tally;
+    unsigned long long *tally;  // slice 0 of the tally; a history's slice is in its root word
+    int64_t nvox;
+    uint32_t n_slices;
     unsigned long long *ledger;
     unsigned long long *hist_dep, *hist_esc;
     int32_t *hist_events;
@@ -201,20 +203,20 @@ __device__ __forceinline__ unsigned long long fixed_point(float e, float wt) {
 __device__ __forceinline__ void deposit(const Args &A, Acc &acc, int64_t iv, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
     if (!q) return;
-    atomicAdd(&A.tally[iv], q);
+    atomicAdd(&A.tally[(int64_t)(root >> ROOT_SLICE_SHIFT) * A.nvox + iv], q);
     acc.dep += q;
     acc.atomics++;
-    if (A.hist_dep) atomicAdd(&A.hist_dep[root], q);
+    if (A.hist_dep) atomicAdd(&A.hist_dep[root & ROOT_INDEX_MASK], q);
 }
 
 __device__ __forceinline__ void escape(const Args &A, Acc &acc, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
     acc.esc += q;
-    if (A.hist_esc) atomicAdd(&A.hist_esc[root], q);
+    if (A.hist_esc) atomicAdd(&A.hist_esc[root & ROOT_INDEX_MASK], q);
 }
 
 __device__ __forceinline__ void count_event(const Args &A, uint32_t root) {
-    if (A.hist_events) atomicAdd(&A.hist_events[root], 1);
+    if (A.hist_events) atomicAdd(&A.hist_events[root & ROOT_INDEX_MASK], 1);
 }
 
 // rotate unit direction by polar cosine c and azimuth phi (renormalised)
@@ -715,13 +717,23 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
     flush_acc(A, acc, 9);
 }
 
+// Slice of every caller particle of a materialised batch: the given one, or
+// (slice < 0) its history's by the particle id.
+__global__ void k_assign_slices(Args A, Particle *p, int64_t nph, int64_t nel, int64_t cap, int32_t slice) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nph + nel; t += (int64_t)gridDim.x * blockDim.x) {
+        Particle *q = p + (t < nph ? t : cap - 1 - (t - nph));
+        const uint32_t sl = slice >= 0 ? (uint32_t)slice : history_slice(q->pid_lo, q->pid_hi, A.rk, A.n_slices);
+        q->root = (sl << ROOT_SLICE_SHIFT) | (q->root & ROOT_INDEX_MASK);
+    }
+}
+
 // ---------------------------------------------------------------- source ---
 // Source stage of a lazy batch (histories first + i * stride): accepted
 // photons are written to the primary buffer, charged primaries go straight to
 // the electron queue.  Each warp locates its first history and its lanes
 // reuse that (group, segment) when it is also theirs.
 __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first, int64_t stride, uint32_t n,
-                                                uint32_t root0, Particle *out, uint32_t *count) {
+                                                uint32_t root0, int32_t slice, Particle *out, uint32_t *count) {
     __shared__ int64_t gs[1025];
     for (int i = threadIdx.x; i <= P.n_groups; i += blockDim.x) gs[i] = P.group_start[i];
     __syncthreads();
@@ -753,7 +765,9 @@ __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first
             c.x = o.s[0]; c.y = o.s[1]; c.z = o.s[2]; c.e = o.s[6];
             c.u = o.s[3]; c.v = o.s[4]; c.w = o.s[5]; c.wt = o.s[7];
             c.pid_lo = (uint32_t)h; c.pid_hi = (uint32_t)((uint64_t)h >> 32);
-            c.type = (uint32_t)o.ptype; c.root = root0 + i;
+            c.type = (uint32_t)o.ptype;
+            const uint32_t sl = slice >= 0 ? (uint32_t)slice : history_slice(c.pid_lo, c.pid_hi, A.rk, A.n_slices);
+            c.root = (sl << ROOT_SLICE_SHIFT) | ((root0 + i) & ROOT_INDEX_MASK);
             if (o.ptype == 0) queue_push(Queue{out, count, n}, c, A.err);
             else queue_push(A.e_out, c, A.err);
         }
@@ -1010,7 +1024,15 @@ struct Runner {
     // launches RUN_GENERATIONS generations with no host check (graph capture).
     int run(const Job &J, int check_from) {
         const bool sync_gens = check_from >= 0;
-        A.tally = tally->t + (size_t)J.slice * tally->nvox;
+        A.tally = tally->t;
+        A.nvox = tally->nvox;
+        A.n_slices = (uint32_t)tally->n_batches;
+        if (!J.lazy && J.nph + J.nel > 0) {
+            // caller particles: their histories' slices go into the root words
+            // (the batch's own buffer: a batch is consumed by its transport)
+            k_assign_slices<<<grid_m, 256, 0, st>>>(A, const_cast<Particle *>(J.p), J.nph, J.nel, J.cap, J.slice);
+            PSL_NOTE_LAUNCH();
+        }
         uint32_t *cP[2] = {w->cnt + 0, w->cnt + 1}, *cE[2] = {w->cnt + 2, w->cnt + 3}, *cS = w->cnt + 4;
         uint32_t *head = w->cnt + 5, *hist = w->cnt + 16, *cursor = w->cnt + 48;
         int pc = 0, ec = 0;
@@ -1060,8 +1082,8 @@ struct Runner {
                 cudaMemsetAsync(w->cnt + 7, 0, 4, st);
                 void *tk = nullptr;
                 tb(PK_SOURCE, &tk);
-                k_source<<<grid_m, 256, 0, st>>>(a2, J.P, J.first + a0 * J.stride, J.stride, cp, (uint32_t)a0, w->Q,
-                                                 w->cnt + 7); PSL_NOTE_LAUNCH();
+                k_source<<<grid_m, 256, 0, st>>>(a2, J.P, J.first + a0 * J.stride, J.stride, cp, (uint32_t)a0, J.slice,
+                                                 w->Q, w->cnt + 7); PSL_NOTE_LAUNCH();
                 te(PK_SOURCE, tk);
                 photon_pass(w->Q, w->cnt + 7, 0, cp);
                 band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
@@ -1138,7 +1160,12 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     int rc = check_transport_args(ph, tally);
     if (rc) return rc;
     if (!batch) return psl_fail(PSL_EINVAL, "transport_run: null batch");
-    if (b < 0 || b >= tally->n_batches) return psl_fail(PSL_EINVAL, "transport_run: batch index out of range");
+    if ((b < 0 && b != PSL_SLICE_BY_HISTORY) || b >= tally->n_batches)
+        return psl_fail(PSL_EINVAL, "transport_run: batch index out of range");
+    if (hist_dep || hist_esc || hist_events) {
+        const int64_t nt = batch->lazy ? batch->n_histories : batch->n_photons + batch->n_electrons;
+        if (nt > (int64_t)ROOT_INDEX_MASK + 1) return psl_fail(PSL_EINVAL, "transport_trace: batch too large to trace");
+    }
     if (batch->consumed) return psl_fail(PSL_EINVAL, "transport_run: batch already transported");
     if (batch->lazy && (batch->phantom.nx != ph->nx || batch->phantom.ny != ph->ny || batch->phantom.nz != ph->nz))
         return psl_fail(PSL_EINVAL, "transport_run: batch was sourced for another phantom");
@@ -1174,20 +1201,15 @@ extern "C" int transport_trace(const psl_phantom_t *ph, const psl_physics_t *phy
 
 static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
                     int64_t first, int64_t n, cudaStream_t st, bool capturing, Runner &R) {
-    const int nb = tally->n_batches;
-    const int64_t per_batch = (n + nb - 1) / nb;
-    int rc = R.prepare(ph, phys, tally, plan->seed, per_batch, st, capturing);
+    // the whole range in reading order; each history's deposits go to the
+    // tally slice of its id (independent batches, Sec. 2.3.3)
+    int rc = R.prepare(ph, phys, tally, plan->seed, n, st, capturing);
     if (rc) return rc;
-    for (int b = 0; b < nb; ++b) {
-        const int64_t cnt = std::max<int64_t>(0, (n - b + nb - 1) / nb);
-        if (!cnt) continue;
-        Job J;
-        J.lazy = true;
-        J.P = make_plan_dev(plan, ph);
-        J.first = first + b; J.stride = nb; J.n = cnt; J.slice = b;
-        if ((rc = R.run(J, capturing ? -1 : UNCHECKED_GENERATIONS))) return rc;
-    }
-    return PSL_OK;
+    Job J;
+    J.lazy = true;
+    J.P = make_plan_dev(plan, ph);
+    J.first = first; J.stride = 1; J.n = n; J.slice = PSL_SLICE_BY_HISTORY;
+    return R.run(J, capturing ? -1 : UNCHECKED_GENERATIONS);
 }
 
 extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
@@ -1210,10 +1232,9 @@ extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const ps
                        (uint64_t)(uintptr_t)ph->mat, ((uint64_t)P.flags << 32) | (uint64_t)tally->grid_mult,
                        (uint64_t)tally->chunk_cap, (uint64_t)plan->seed};
     // workspace and tables are set up outside the capture
-    const int64_t per_batch = (n + tally->n_batches - 1) / tally->n_batches;
     {
         Runner pre;
-        if ((rc = pre.prepare(ph, phys, tally, plan->seed, per_batch, st, false))) return rc;
+        if ((rc = pre.prepare(ph, phys, tally, plan->seed, n, st, false))) return rc;
         PSL_CUDA(cudaStreamSynchronize(st));
     }
     Workspace *w = tally->ws;
@@ -1261,7 +1282,7 @@ extern "C" int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *ph, con
     cudaEventCreate(&b);
     for (int gi : grids) {
         for (int64_t d : depths) {
-            if (d > 2 * ((n_probe + tally->n_batches - 1) / tally->n_batches) && d != depths[0]) continue;
+            if (d > 2 * n_probe && d != depths[0]) continue;
             tally->grid_mult = gi;
             tally->chunk_cap = d;
             cudaEventRecord(a, st);

@@ -1,5 +1,5 @@
 """Run a workload through the C ABI: upload, psl_build, psl_plan_create,
-psl_source_batch + transport_run per batch, dose_readout.
+psl_source_batch + transport_run per piece of the history range, dose_readout.
 
 PyTorch supplies device memory and streams; every computation is a call into
 libpsl_b300.so.
@@ -74,12 +74,10 @@ def shard_histories(rank: int, world: int, per_rank: int):
     return rank * per_rank, per_rank, world * per_rank
 
 
-def batch_histories(first: int, n: int, n_batches: int, b: int):
-    """(first, count, stride) of batch b of the histories [first, first+n):
-    every n_batches-th history, so each batch samples every energy division
-    (independent batches, Sec. 2.3.3)."""
-    cnt = max(0, (n - b + n_batches - 1) // n_batches)
-    return first + b, cnt, n_batches
+def chunks(first: int, n: int, size: int):
+    """Contiguous pieces [f, f + c) of the history range [first, first+n)."""
+    size = max(1, int(size))
+    return [(f, min(size, first + n - f)) for f in range(first, first + n, size)]
 
 
 def normalisation(n_total_psl: int, n_histories: int, n_incident: int) -> float:
@@ -91,7 +89,8 @@ def normalisation(n_total_psl: int, n_histories: int, n_incident: int) -> float:
 
 
 def run(dw: DeviceWorkload, n_histories: Optional[int] = None, n_batches: Optional[int] = None,
-        flags: int = 0, store=None, plan=None, tally=None, readout: bool = True, stream=None):
+        flags: int = 0, store=None, plan=None, tally=None, readout: bool = True, stream=None,
+        batch_size: int = 1 << 24):
     """Whole plan on the GPU.  Returns a dict with the handles and (device) dose."""
     w = dw.w
     n_sim = w.n_histories
@@ -104,10 +103,11 @@ def run(dw: DeviceWorkload, n_histories: Optional[int] = None, n_batches: Option
     if tally is None:
         tally = capi.psl_tally_create(dw.phantom, nb)
     phys = capi.physics(flags)
-    for b in range(nb):
-        f0, cnt, stride = batch_histories(0, n_h, nb, b)
-        batch = capi.psl_source_batch(plan, dw.phantom, f0, cnt, stride, stream)
-        capi.transport_run(dw.phantom, phys, batch, tally, b, stream)
+    # histories in reading order, one psl_source_batch per piece; every
+    # history's deposits go to the tally slice (batch) of its id
+    for f0, cnt in chunks(0, n_h, batch_size):
+        batch = capi.psl_source_batch(plan, dw.phantom, f0, cnt, 1, stream)
+        capi.transport_run(dw.phantom, phys, batch, tally, capi.SLICE_BY_HISTORY, stream)
         batch.close()
     out = dict(store=store, plan=plan, tally=tally)
     if readout:

@@ -217,3 +217,20 @@ def test_apr_rejects_bad_copy_counts():
     rec = torch.empty(100 * 8, dtype=torch.float32, device="cuda")
     with pytest.raises(capi.PslError):                 # the allocation-free build takes no copies
         capi.psl_build_static(dw.params, dw.records, off, rec)
+
+
+def test_plan_beyond_2_32_histories():
+    """A 6e9-history plan (the size that reaches 1 % at the isocentre): the
+    integer plan whole, and the source stage on ranges past 2^32, bit-exact."""
+    w = inputs.config2(n_histories=6_000_000_000)
+    dw, store, ost, n_valid, n_bins = _build_both(w)
+    dw, plan, opl = _plan_both(w, store, ost)
+    for h0 in (0, (1 << 32) - 32, 5_123_456_789, w.n_histories - 64):
+        hs = np.arange(h0, h0 + 64)
+        g = source_trace(dw, plan, int(h0), 64)
+        ent, use = source.history_map(opl, hs, literal_limit=0)
+        assert np.array_equal(g["entry"], ent) and np.array_equal(g["use"], use)
+        rec = opl.start[ent] + (opl.offset[ent] + use) % opl.nrec[ent]
+        assert np.array_equal(g["rec"], rec)
+    with pytest.raises(capi.PslError):              # some PSL would get >= 2^32 histories
+        capi.psl_plan_create(store, dw.beams, w.sad, 1 << 61, w.seed)

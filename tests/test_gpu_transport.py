@@ -188,6 +188,57 @@ def test_determinism_and_batch_split():
     c = engine.run(dw, n_batches=1, readout=False, store=a["store"], plan=a["plan"])
     tc, _ = engine.raw_tallies(dw, c["tally"], 1)
     assert np.array_equal(ta, tc)
+    # the slices do not depend on how the range is cut into source batches
+    d = engine.run(dw, n_batches=3, readout=False, store=a["store"], plan=a["plan"], batch_size=7_777)
+    td, _ = engine.raw_tallies(dw, d["tally"], 3)
+    assert np.array_equal(tb, td)
+
+
+def test_history_slices_follow_the_oracle_partition():
+    """PSL_SLICE_BY_HISTORY: every history's deposits land in the batch the
+    oracle draws for its id (per-history sums from a traced transport)."""
+    w = inputs.config1()
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
+    n, first, nb = 20_000, 3_000, 7
+    batch = capi.psl_source_batch(plan, dw.phantom, first, n)
+    tally = capi.psl_tally_create(dw.phantom, nb)
+    hd = torch.zeros(n, dtype=torch.int64, device="cuda")
+    capi.transport_trace(dw.phantom, capi.physics(), batch, tally, capi.SLICE_BY_HISTORY, hd, None, None)
+    t, _ = engine.raw_tallies(dw, tally, nb)
+    sl = oracle.history_slices(np.arange(first, first + n), w.seed, nb)
+    dep = hd.cpu().numpy()
+    for b in range(nb):
+        assert int(t[b].sum()) == int(dep[sl == b].sum())
+    assert np.all(t.reshape(nb, -1).sum(1) > 0)
+
+
+def test_batch_uncertainty_falls_as_one_over_root_n():
+    """The isocentre batch uncertainty of the 10x10 plan at 1e8 and 4e8
+    histories: sigma/D halves (it would plateau if a batch sampled only a
+    subset of the PSLs)."""
+    w = inputs.config2()
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    nz, ny, nx = w.phantom.shape
+    iso = np.array(w.beams[0].iso) - np.array(w.phantom.origin)
+    ic = (iso / np.array(w.phantom.voxel)).astype(int)[::-1]
+    sl = tuple(slice(c - 2, c + 3) for c in ic)
+    rel = []
+    for n in (100_000_000, 400_000_000):
+        plan = capi.psl_plan_create(store, dw.beams, w.sad, n, w.seed)
+        tally = capi.psl_tally_create(dw.phantom, 10)
+        capi.psl_run(plan, dw.phantom, capi.physics(), tally, 0, n)
+        dose = torch.empty(nx * ny * nz, dtype=torch.float64, device="cuda")
+        sig = torch.empty_like(dose)
+        lg = torch.empty(3, dtype=torch.float64, device="cuda")
+        _, n_total, _ = plan.info()
+        capi.dose_readout(tally, dw.phantom, engine.normalisation(n_total, n, w.records.n), dose, sig, lg)
+        d = dose.view(nz, ny, nx).cpu().numpy()
+        s = sig.view(nz, ny, nx).cpu().numpy()
+        rel.append(float((s[sl] / d[sl]).mean()))
+    assert 1.6 < rel[0] / rel[1] < 2.5, rel
 
 
 def _tallies_of(dw, tally, nb):
@@ -197,8 +248,9 @@ def _tallies_of(dw, tally, nb):
 
 @pytest.mark.parametrize("cfg", [1, 4])
 def test_psl_run_and_graph_match_per_batch_path(cfg):
-    """All batches in one call (no host synchronisation) and as one CUDA-graph
-    launch give the same integer tallies as batch-by-batch transport."""
+    """All histories in one call (no host synchronisation) and as one
+    CUDA-graph launch give the same integer tallies, slice by slice, as
+    psl_source_batch + transport_run piece by piece."""
     w = inputs.config1(n_histories=60_000) if cfg == 1 else inputs.config4(n_records=300_000, n_histories=200_000)
     w.n_batches = 4
     dw = engine.upload(w)
