@@ -28,6 +28,7 @@ EXPORTS = (
     "psl_tally_destroy", "psl_last_error", "psl_kernel_launches", "psl_profile", "psl_profile_read",
     "psl_build_static", "psl_atomic_peak", "psl_run", "psl_autotune", "psl_stream_bin", "psl_stream_info",
     "psl_stream_read", "psl_batch_read", "psl_memory_trim",
+    "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
@@ -85,6 +86,8 @@ def lib():
         L.psl_kernel_launches.argtypes = []
         L.psl_last_error.restype = ctypes.c_char_p
         L.psl_last_error.argtypes = []
+        L.psl_conv3d_packed_size.restype = ctypes.c_int64
+        L.psl_conv3d_packed_size.argtypes = [i32, i32]
         L.psl_physics_default.restype = None
         L.psl_physics_default.argtypes = [vp]
         for name in ("psl_store_destroy", "psl_plan_destroy", "psl_batch_destroy", "psl_tally_destroy"):
@@ -118,6 +121,8 @@ def lib():
             "psl_stream_read": [vp, vp, vp, vp, vp],
             "psl_batch_read": [vp, vp, vp, vp, vp],
             "psl_memory_trim": [u64, vp],
+            "psl_conv3d_pack": [vp, i32, i32, i32, vp, vp],
+            "psl_conv3d": [vp, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -323,6 +328,23 @@ def memory_trim(keep_bytes: int = 0) -> int:
     held = u64()
     check(lib().psl_memory_trim(int(keep_bytes), ctypes.byref(held)))
     return held.value
+
+
+def conv3d_pack(w, ci: int, co: int, mirror: bool = False, stream=None):
+    """FP32 taps (device [27, ci, co]) -> packed BF16 tiles (a device int16 tensor)."""
+    import torch
+    cin, cout = (co, ci) if mirror else (ci, co)
+    n = int(lib().psl_conv3d_packed_size(cin, cout))
+    out = torch.empty(n, dtype=torch.int16, device=w.device)
+    check(lib().psl_conv3d_pack(ptr(w), int(ci), int(co), 1 if mirror else 0, ptr(out), stream_ptr(stream)))
+    return out
+
+
+def conv3d(x, ci: int, wpk, bias, co: int, nx: int, ny: int, nz: int, relu: bool, out=None, out_f32=None,
+           stream=None):
+    """3x3x3 convolution on the tensor cores (see psl_denoise.h); x, out: BF16 bit patterns."""
+    check(lib().psl_conv3d(ptr(x), int(ci), ptr(wpk), ptr(bias), int(co), int(nx), int(ny), int(nz),
+                           1 if relu else 0, ptr(out), ptr(out_f32), stream_ptr(stream)))
 
 
 def psl_tally_create(phantom: Phantom, n_batches: int) -> Tally:

@@ -1,0 +1,259 @@
+// BF16 3D convolution (3x3x3 taps, zero padding 1, channels last) on the
+// tcgen05 tensor cores: the forward pass and, with mirrored and transposed
+// taps, the input gradient, as one implicit GEMM.
+//
+// GEMM view: D[voxel][o] = sum_k A[voxel][k] B[o][k], k = tap * C_in + i,
+// A[v][k] = x[v + offset(tap)][i] (zero outside the volume), B[o][k] =
+// w[tap][i][o].  A CTA owns 128 consecutive voxels (M = 128) and all C_out
+// outputs (N = C_out, 16..128); the FP32 accumulator lives in tensor memory.
+// K runs in steps of 16 (one MMA each), 8 steps per pipeline stage: the 128
+// threads gather the stage's A rows (16-byte vectors: 8 channels of one tap)
+// and copy its pre-packed B tile into shared memory, one thread issues the
+// stage's MMAs and commits them to the stage buffer's mbarrier, and the
+// threads go on to fill the other buffer.  The epilogue reads the
+// accumulator back with tcgen05.ld, adds the bias, applies ReLU and stores
+// BF16 (or FP32).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/psl_denoise.h"
+#include "psl_internal.cuh"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int BM = 128;               // voxels per CTA
+constexpr int SK = 8;                 // K steps (of 16) per stage
+constexpr uint32_t WAIT_LIMIT = 1u << 24;
+
+struct ConvArgs {
+    const __nv_bfloat16 *in;          // [V][ci]
+    const __nv_bfloat16 *wpk;         // packed taps, ksteps x N x 16
+    const float *bias;                // [N] or null
+    __nv_bfloat16 *out;               // [V][N] or null
+    float *out_f32;                   // [V][N] or null
+    int ci, D, H, W, relu, ksteps;
+    uint32_t *err;
+};
+
+// one 16-byte chunk (8 channels of one tap) of voxel (z, y, x)'s A row
+__device__ __forceinline__ uint4 gather_chunk(const ConvArgs &a, int z, int y, int x, bool row_ok, int kc) {
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    const int k0 = kc * 8;
+    const int tap = k0 / a.ci, c0 = k0 - tap * a.ci;
+    if (!row_ok || tap >= 27) return v;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    if (zz < 0 || zz >= a.D || yy < 0 || yy >= a.H || xx < 0 || xx >= a.W) return v;
+    const int64_t nv = ((int64_t)zz * a.H + yy) * a.W + xx;
+    return __ldg(reinterpret_cast<const uint4 *>(a.in + nv * a.ci + c0));
+}
+
+template <int N>
+__global__ void __launch_bounds__(128, 1) k_conv3d(ConvArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int A_STAGE = SK * BM * 32;          // bytes: 8 K steps x 128 rows x 16 BF16
+    constexpr int B_STAGE = SK * N * 32;
+    constexpr uint32_t TCOLS = N < 32 ? 32 : N;
+    uint8_t *sA = smem;                             // [2][A_STAGE]
+    uint8_t *sB = smem + 2 * A_STAGE;               // [2][B_STAGE]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * A_STAGE + 2 * B_STAGE);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+
+    const int t = threadIdx.x, warp = t >> 5;
+    const int64_t V = (int64_t)a.D * a.H * a.W;
+    const int64_t v = (int64_t)blockIdx.x * BM + t;
+    const bool row_ok = v < V;
+    int z = 0, y = 0, x = 0;
+    if (row_ok) {
+        x = (int)(v % a.W);
+        y = (int)((v / a.W) % a.H);
+        z = (int)(v / ((int64_t)a.W * a.H));
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, TCOLS);
+        tc::tmem_relinquish();
+    }
+    if (t == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        tc::mbar_fence_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16(BM, N);
+    const int nst = (a.ksteps + SK - 1) / SK;
+    bool ok = true;
+
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        // the MMAs of stage st - 2 have finished reading this buffer
+        if (st >= 2 && !tc::mbar_wait(&bar[buf], (uint32_t)((st - 2) >> 1) & 1u, WAIT_LIMIT)) ok = false;
+        const int k0 = st * SK, nk = min(SK, a.ksteps - k0);
+        uint8_t *A = sA + buf * A_STAGE, *B = sB + buf * B_STAGE;
+        // A rows: this thread's voxel, core-matrix layout (LBO 128, SBO 256)
+        for (int kk = 0; kk < nk; ++kk) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const uint4 c = gather_chunk(a, z, y, x, row_ok, 2 * (k0 + kk) + j);
+                *reinterpret_cast<uint4 *>(A + kk * (BM * 32) + (t >> 3) * 256 + j * 128 + (t & 7) * 16) = c;
+            }
+        }
+        // B tile: already packed in the same layout, copied as 16-byte chunks
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.wpk) + (size_t)k0 * N * 2;
+        for (int i = t; i < nk * N * 2; i += BM) reinterpret_cast<uint4 *>(B)[i] = __ldg(src + i);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        if (!__syncthreads_and(ok)) { ok = false; break; }       // block-uniform
+        if (t == 0) {
+            tc::fence_after_sync();
+            for (int kk = 0; kk < nk; ++kk) {
+                const uint64_t ad = tc::desc_kmajor(tc::smem_u32(A + kk * (BM * 32)), 128, 256);
+                const uint64_t bd = tc::desc_kmajor(tc::smem_u32(B + kk * (N * 32)), 128, 256);
+                tc::mma_bf16(tmem, ad, bd, idesc, (st > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar[buf]);
+        }
+    }
+    if (ok && !tc::mbar_wait(&bar[(nst - 1) & 1], (uint32_t)((nst - 1) >> 1) & 1u, WAIT_LIMIT)) ok = false;
+    ok = __syncthreads_and(ok) != 0;
+    tc::fence_after_sync();
+    if (!ok) {
+        if (t == 0) atomicOr(a.err, PSL_DEV_ERR_TIMEOUT);
+    } else {
+        // epilogue: warp w holds accumulator rows 32w..32w+31
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float r[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, r);
+            if (row_ok) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    float q = r[i] + (a.bias ? __ldg(a.bias + c0 + i) : 0.0f);
+                    r[i] = a.relu ? fmaxf(q, 0.0f) : q;
+                }
+                if (a.out) {
+                    __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(r[i]);
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.out + v * N + c0);
+                    dst[0] = reinterpret_cast<uint4 *>(h)[0];
+                    dst[1] = reinterpret_cast<uint4 *>(h)[1];
+                }
+                if (a.out_f32) {
+                    float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + v * N + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dst[i] = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+}
+
+// Taps W[27][ci][co] (FP32) -> BF16 B tiles: K step s, 8-row group g of the
+// outputs, K chunk j, row n % 8, element e: k = 16 s + 8 j + e, tap = k / ci.
+// mirror: the input-gradient form, W'[t][o][i] = W[26 - t][i][o] (a
+// convolution from co channels to ci).
+__global__ void k_pack(const float *w, int ci, int co, int mirror, __nv_bfloat16 *out, int ksteps) {
+    const int cin = mirror ? co : ci, cout = mirror ? ci : co;
+    const int64_t total = (int64_t)ksteps * cout * 16;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(q / (cout * 16));
+        const int r = (int)(q % (cout * 16));
+        const int g = r / 128, j = (r % 128) / 64, n8 = (r % 64) / 8, e = r % 8;
+        const int n = g * 8 + n8;
+        const int k = 16 * s + 8 * j + e;
+        const int tap = k / cin, c = k % cin;
+        float val = 0.0f;
+        if (tap < 27) val = mirror ? w[((int64_t)(26 - tap) * ci + n) * co + c] : w[((int64_t)tap * ci + c) * co + n];
+        out[q] = __float2bfloat16_rn(val);
+    }
+}
+
+template <int N>
+int launch(const ConvArgs &a, int64_t V, cudaStream_t st) {
+    const size_t smem = 2 * (size_t)(SK * BM * 32) + 2 * (size_t)(SK * N * 32) + 64;
+    static bool attr = false;
+    if (!attr) {
+        PSL_CUDA(cudaFuncSetAttribute(k_conv3d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    const int grid = (int)((V + BM - 1) / BM);
+    k_conv3d<N><<<grid, 128, smem, st>>>(a); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaGetLastError());
+    return PSL_OK;
+}
+
+}  // namespace
+
+int psl_conv_ksteps(int ci) { return (27 * ci + 15) / 16; }
+
+int psl_conv3d_run(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, const float *bias, int co, int nx,
+                   int ny, int nz, int relu, __nv_bfloat16 *out, float *out_f32, uint32_t *err, cudaStream_t st) {
+    ConvArgs a{in, wpk, bias, out, out_f32, ci, nz, ny, nx, relu, psl_conv_ksteps(ci), err};
+    const int64_t V = (int64_t)nx * ny * nz;
+    if (V == 0) return PSL_OK;
+    switch (co) {
+        case 16: return launch<16>(a, V, st);
+        case 32: return launch<32>(a, V, st);
+        case 64: return launch<64>(a, V, st);
+        case 128: return launch<128>(a, V, st);
+        default: return psl_fail(PSL_EINVAL, "conv3d: C_out must be 16, 32, 64 or 128");
+    }
+}
+
+int psl_conv3d_pack_run(const float *w, int ci, int co, int mirror, __nv_bfloat16 *out, cudaStream_t st) {
+    const int cin = mirror ? co : ci, cout = mirror ? ci : co;
+    const int ks = psl_conv_ksteps(cin);
+    const int64_t total = (int64_t)ks * cout * 16;
+    k_pack<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(w, ci, co, mirror, out, ks); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaGetLastError());
+    return PSL_OK;
+}
+
+static bool conv_shape_ok(int ci, int co) {
+    return ci >= 8 && ci <= 128 && ci % 8 == 0 && (co == 16 || co == 32 || co == 64 || co == 128);
+}
+
+extern "C" int psl_conv3d_pack(const float *w, int32_t ci, int32_t co, int32_t mirror, uint16_t *wpk, void *stream) {
+    if (!w || !wpk) return psl_fail(PSL_EINVAL, "psl_conv3d_pack: null pointer");
+    if (!conv_shape_ok(mirror ? co : ci, mirror ? ci : co))
+        return psl_fail(PSL_EINVAL, "psl_conv3d_pack: channels (C_in multiple of 8 up to 128; C_out 16/32/64/128)");
+    return psl_conv3d_pack_run(w, ci, co, mirror, reinterpret_cast<__nv_bfloat16 *>(wpk), as_stream(stream));
+}
+
+extern "C" int64_t psl_conv3d_packed_size(int32_t ci, int32_t co) { return (int64_t)psl_conv_ksteps(ci) * co * 16; }
+
+extern "C" int psl_conv3d(const uint16_t *in, int32_t ci, const uint16_t *wpk, const float *bias, int32_t co,
+                          int32_t nx, int32_t ny, int32_t nz, int32_t relu, uint16_t *out, float *out_f32,
+                          void *stream) {
+    if (!in || !wpk || (!out && !out_f32)) return psl_fail(PSL_EINVAL, "psl_conv3d: null pointer");
+    if (!conv_shape_ok(ci, co)) return psl_fail(PSL_EINVAL, "psl_conv3d: channels (C_in multiple of 8 up to 128; C_out 16/32/64/128)");
+    if (nx <= 0 || ny <= 0 || nz <= 0 || (int64_t)nx * ny * nz >= (1ll << 31))
+        return psl_fail(PSL_EINVAL, "psl_conv3d: volume size");
+    if (((uintptr_t)in | (uintptr_t)wpk | (uintptr_t)out | (uintptr_t)out_f32) & 15)
+        return psl_fail(PSL_EINVAL, "psl_conv3d: arrays must be 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    uint32_t *err = nullptr;
+    PSL_CUDA(psl_malloc_async((void **)&err, 4, st));
+    cudaMemsetAsync(err, 0, 4, st);
+    int rc = psl_conv3d_run(reinterpret_cast<const __nv_bfloat16 *>(in), ci, reinterpret_cast<const __nv_bfloat16 *>(wpk),
+                            bias, co, nx, ny, nz, relu, reinterpret_cast<__nv_bfloat16 *>(out), out_f32, err, st);
+    uint32_t herr = 0;
+    cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(err, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, cudaGetErrorString(e));
+    if (herr) return psl_fail(PSL_ETIMEOUT, "psl_conv3d: tensor-core completion wait gave up");
+    return PSL_OK;
+}

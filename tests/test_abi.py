@@ -1,5 +1,6 @@
 """The C ABI library builds for sm_103a, loads without a GPU and exports every
-entry point that include/psl.h declares (CPU only, no compute calls)."""
+entry point that include/psl.h and include/psl_denoise.h declare (CPU only,
+no compute calls)."""
 import ctypes
 import os
 import re
@@ -10,8 +11,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared():
-    text = open(os.path.join(ROOT, "include", "psl.h")).read()
-    return sorted(set(re.findall(r"^PSL_API\s+[\w\s\*]*?\b(\w+)\(", text, re.M)))
+    names = set()
+    for h in ("psl.h", "psl_denoise.h"):
+        text = open(os.path.join(ROOT, "include", h)).read()
+        names |= set(re.findall(r"^PSL_API\s+[\w\s\*]*?\b(\w+)\(", text, re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
