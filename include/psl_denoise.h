@@ -45,6 +45,13 @@ PSL_API int psl_conv3d(const uint16_t *in, int32_t ci, const uint16_t *wpk, cons
                        int32_t nx, int32_t ny, int32_t nz, int32_t relu, uint16_t *out, float *out_f32,
                        void *stream);
 
+/* The tap gradient of that convolution, on the tensor cores:
+ *   dw[t, i, o] += sum_v in[v + offset_t, i] gy[v, o]
+ * (FP32 dw [27][ci][co], device, accumulated into: zero it first).  in BF16
+ * [V][ci], gy BF16 [V][co]; shapes as psl_conv3d.  Synchronises stream. */
+PSL_API int psl_conv3d_wgrad(const uint16_t *in, int32_t ci, const uint16_t *gy, int32_t co, int32_t nx, int32_t ny,
+                             int32_t nz, float *dw, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

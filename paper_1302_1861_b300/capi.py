@@ -28,7 +28,7 @@ EXPORTS = (
     "psl_tally_destroy", "psl_last_error", "psl_kernel_launches", "psl_profile", "psl_profile_read",
     "psl_build_static", "psl_atomic_peak", "psl_run", "psl_autotune", "psl_stream_bin", "psl_stream_info",
     "psl_stream_read", "psl_batch_read", "psl_memory_trim",
-    "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d",
+    "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d", "psl_conv3d_wgrad",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
@@ -123,6 +123,7 @@ def lib():
             "psl_memory_trim": [u64, vp],
             "psl_conv3d_pack": [vp, i32, i32, i32, vp, vp],
             "psl_conv3d": [vp, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp],
+            "psl_conv3d_wgrad": [vp, i32, vp, i32, i32, i32, i32, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -345,6 +346,12 @@ def conv3d(x, ci: int, wpk, bias, co: int, nx: int, ny: int, nz: int, relu: bool
     """3x3x3 convolution on the tensor cores (see psl_denoise.h); x, out: BF16 bit patterns."""
     check(lib().psl_conv3d(ptr(x), int(ci), ptr(wpk), ptr(bias), int(co), int(nx), int(ny), int(nz),
                            1 if relu else 0, ptr(out), ptr(out_f32), stream_ptr(stream)))
+
+
+def conv3d_wgrad(x, ci: int, gy, co: int, nx: int, ny: int, nz: int, dw, stream=None):
+    """dw[27, ci, co] (FP32, device) += the tap gradient (see psl_denoise.h)."""
+    check(lib().psl_conv3d_wgrad(ptr(x), int(ci), ptr(gy), int(co), int(nx), int(ny), int(nz), ptr(dw),
+                                 stream_ptr(stream)))
 
 
 def psl_tally_create(phantom: Phantom, n_batches: int) -> Tally:

@@ -159,6 +159,136 @@ __global__ void __launch_bounds__(128, 1) k_conv3d(ConvArgs a) {
     if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
 }
 
+// Weight gradient as a GEMM over voxels: dW[(t, i)][o] = sum_v A[(t,i)][v]
+// B[o][v], A[(t,i)][v] = x[v + offset_t][i], B[o][v] = gy[v][o].  A CTA owns
+// 128 rows (t, i) and one range of voxels (split K); per stage 128 voxels =
+// 8 MMAs of 16.  Both operands are stored voxel-major in HBM, so each thread
+// loads 8 voxels x 8 channels (eight 16-byte vectors) and transposes the 8x8
+// BF16 block in registers into eight K-major rows.  The FP32 partial sums
+// are added into dW with atomics.
+__device__ __forceinline__ void transpose8(const uint4 (&in)[8], uint4 (&out)[8]) {
+    const uint32_t *w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = reinterpret_cast<const uint32_t *>(&in[k]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t sel = (c & 1) ? 0x7632u : 0x5410u;
+        uint32_t o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = __byte_perm(w[2 * q][c >> 1], w[2 * q + 1][c >> 1], sel);
+        out[c] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+struct WgradArgs {
+    const __nv_bfloat16 *x;           // [V][ci]
+    const __nv_bfloat16 *gy;          // [V][N]
+    float *dw;                        // [27 ci][N], added to
+    int ci, D, H, W;
+    int64_t vox_per_cta;
+    uint32_t *err;
+};
+
+template <int N>
+__global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(WgradArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int A_STAGE = SK * BM * 32, B_STAGE = SK * N * 32;
+    constexpr uint32_t TCOLS = N < 32 ? 32 : N;
+    uint8_t *sA = smem, *sB = smem + 2 * A_STAGE;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * A_STAGE + 2 * B_STAGE);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int64_t V = (int64_t)a.D * a.H * a.W;
+    const int rows = 27 * a.ci;
+    const int m0 = blockIdx.x * BM;
+    const int64_t vbeg = (int64_t)blockIdx.y * a.vox_per_cta, vend = min(V, vbeg + a.vox_per_cta);
+    if (warp == 0) { tc::tmem_alloc(tslot, TCOLS); tc::tmem_relinquish(); }
+    if (t == 0) { tc::mbar_init(&bar[0], 1); tc::mbar_init(&bar[1], 1); tc::mbar_fence_init(); }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc::idesc_bf16(BM, N);
+    const int nst = vend > vbeg ? (int)((vend - vbeg + BM - 1) / BM) : 0;
+    bool ok = true;
+    for (int st = 0; st < nst; ++st) {
+        const int buf = st & 1;
+        if (st >= 2 && !tc::mbar_wait(&bar[buf], (uint32_t)((st - 2) >> 1) & 1u, WAIT_LIMIT)) ok = false;
+        uint8_t *A = sA + buf * A_STAGE, *B = sB + buf * B_STAGE;
+        const int64_t vs = vbeg + (int64_t)st * BM;
+        // A: 16 row groups x 16 voxel groups, two 8x8 blocks per thread
+        for (int blk = t; blk < 256; blk += BM) {
+            const int g = blk >> 4, q = blk & 15;
+            const int r0 = m0 + 8 * g;
+            const int tap = r0 / a.ci, i0 = r0 - tap * a.ci;
+            uint4 in[8], out[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                in[k] = make_uint4(0u, 0u, 0u, 0u);
+                const int64_t vv = vs + 8 * q + k;
+                if (r0 < rows && vv < vend) {
+                    const int x = (int)(vv % a.W), y = (int)((vv / a.W) % a.H), z = (int)(vv / ((int64_t)a.W * a.H));
+                    const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+                    if (zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
+                        in[k] = __ldg(reinterpret_cast<const uint4 *>(a.x + (((int64_t)zz * a.H + yy) * a.W + xx) * a.ci + i0));
+                }
+            }
+            transpose8(in, out);
+            uint8_t *dst = A + (q >> 1) * (BM * 32) + g * 256 + (q & 1) * 128;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(dst + c * 16) = out[c];
+        }
+        // B: N/8 row groups x 16 voxel groups
+        for (int blk = t; blk < (N / 8) * 16; blk += BM) {
+            const int g = blk >> 4, q = blk & 15;
+            uint4 in[8], out[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int64_t vv = vs + 8 * q + k;
+                in[k] = vv < vend ? __ldg(reinterpret_cast<const uint4 *>(a.gy + vv * N + 8 * g)) : make_uint4(0u, 0u, 0u, 0u);
+            }
+            transpose8(in, out);
+            uint8_t *dst = B + (q >> 1) * (N * 32) + g * 256 + (q & 1) * 128;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(dst + c * 16) = out[c];
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        if (!__syncthreads_and(ok)) { ok = false; break; }
+        if (t == 0) {
+            tc::fence_after_sync();
+#pragma unroll 1
+            for (int kk = 0; kk < SK; ++kk) {
+                const uint64_t ad = tc::desc_kmajor(tc::smem_u32(A + kk * (BM * 32)), 128, 256);
+                const uint64_t bd = tc::desc_kmajor(tc::smem_u32(B + kk * (N * 32)), 128, 256);
+                tc::mma_bf16(tmem, ad, bd, idesc, (st > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar[buf]);
+        }
+    }
+    if (ok && nst > 0 && !tc::mbar_wait(&bar[(nst - 1) & 1], (uint32_t)((nst - 1) >> 1) & 1u, WAIT_LIMIT)) ok = false;
+    ok = __syncthreads_and(ok) != 0;
+    tc::fence_after_sync();
+    if (!ok) {
+        if (t == 0) atomicOr(a.err, PSL_DEV_ERR_TIMEOUT);
+    } else if (nst > 0) {
+        const int r = m0 + t;                         // this thread's TMEM lane = its row (t, i)
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+            if (r < rows) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) atomicAdd(a.dw + (int64_t)r * N + c0 + i, v[i]);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+}
+
 // Taps W[27][ci][co] (FP32) -> BF16 B tiles: K step s, 8-row group g of the
 // outputs, K chunk j, row n % 8, element e: k = 16 s + 8 j + e, tap = k / ci.
 // mirror: the input-gradient form, W'[t][o][i] = W[26 - t][i][o] (a
@@ -193,9 +323,44 @@ int launch(const ConvArgs &a, int64_t V, cudaStream_t st) {
     return PSL_OK;
 }
 
+template <int N>
+int launch_wgrad(const WgradArgs &a0, int64_t V, cudaStream_t st) {
+    const size_t smem = 2 * (size_t)(SK * BM * 32) + 2 * (size_t)(SK * N * 32) + 64;
+    static bool attr = false;
+    if (!attr) {
+        PSL_CUDA(cudaFuncSetAttribute(k_conv3d_wgrad<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    WgradArgs a = a0;
+    const int mt = (27 * a.ci + BM - 1) / BM;
+    // enough voxel splits to fill the GPU about twice, each a whole number of stages
+    const int64_t want = std::max<int64_t>(1, (int64_t)psl_sm_count() * 2 / mt);
+    int64_t per = (V + want - 1) / want;
+    per = std::max<int64_t>(BM, (per + BM - 1) / BM * BM);
+    a.vox_per_cta = per;
+    const dim3 grid(mt, (unsigned)((V + per - 1) / per));
+    k_conv3d_wgrad<N><<<grid, 128, smem, st>>>(a); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaGetLastError());
+    return PSL_OK;
+}
+
 }  // namespace
 
 int psl_conv_ksteps(int ci) { return (27 * ci + 15) / 16; }
+
+int psl_conv3d_wgrad_run(const __nv_bfloat16 *x, int ci, const __nv_bfloat16 *gy, int co, int nx, int ny, int nz,
+                         float *dw, uint32_t *err, cudaStream_t st) {
+    WgradArgs a{x, gy, dw, ci, nz, ny, nx, 0, err};
+    const int64_t V = (int64_t)nx * ny * nz;
+    if (V == 0) return PSL_OK;
+    switch (co) {
+        case 16: return launch_wgrad<16>(a, V, st);
+        case 32: return launch_wgrad<32>(a, V, st);
+        case 64: return launch_wgrad<64>(a, V, st);
+        case 128: return launch_wgrad<128>(a, V, st);
+        default: return psl_fail(PSL_EINVAL, "conv3d wgrad: C_out must be 16, 32, 64 or 128");
+    }
+}
 
 int psl_conv3d_run(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, const float *bias, int co, int nx,
                    int ny, int nz, int relu, __nv_bfloat16 *out, float *out_f32, uint32_t *err, cudaStream_t st) {
@@ -255,5 +420,28 @@ extern "C" int psl_conv3d(const uint16_t *in, int32_t ci, const uint16_t *wpk, c
     if (rc) return rc;
     if (e != cudaSuccess) return psl_fail(PSL_ECUDA, cudaGetErrorString(e));
     if (herr) return psl_fail(PSL_ETIMEOUT, "psl_conv3d: tensor-core completion wait gave up");
+    return PSL_OK;
+}
+
+extern "C" int psl_conv3d_wgrad(const uint16_t *x, int32_t ci, const uint16_t *gy, int32_t co, int32_t nx,
+                                int32_t ny, int32_t nz, float *dw, void *stream) {
+    if (!x || !gy || !dw) return psl_fail(PSL_EINVAL, "psl_conv3d_wgrad: null pointer");
+    if (!conv_shape_ok(ci, co)) return psl_fail(PSL_EINVAL, "psl_conv3d_wgrad: channels (C_in multiple of 8 up to 128; C_out 16/32/64/128)");
+    if (nx <= 0 || ny <= 0 || nz <= 0 || (int64_t)nx * ny * nz >= (1ll << 31))
+        return psl_fail(PSL_EINVAL, "psl_conv3d_wgrad: volume size");
+    if (((uintptr_t)x | (uintptr_t)gy) & 15) return psl_fail(PSL_EINVAL, "psl_conv3d_wgrad: arrays must be 16-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    uint32_t *err = nullptr;
+    PSL_CUDA(psl_malloc_async((void **)&err, 4, st));
+    cudaMemsetAsync(err, 0, 4, st);
+    int rc = psl_conv3d_wgrad_run(reinterpret_cast<const __nv_bfloat16 *>(x), ci, reinterpret_cast<const __nv_bfloat16 *>(gy),
+                                  co, nx, ny, nz, dw, err, st);
+    uint32_t herr = 0;
+    cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(err, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, cudaGetErrorString(e));
+    if (herr) return psl_fail(PSL_ETIMEOUT, "psl_conv3d_wgrad: tensor-core completion wait gave up");
     return PSL_OK;
 }

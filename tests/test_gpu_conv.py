@@ -77,6 +77,25 @@ def test_mirrored_taps_give_the_input_gradient(ci, co):
     assert np.all(np.abs(of - ref) <= 2e-5 * mag + 1e-6), np.abs(of - ref).max()
 
 
+@pytest.mark.parametrize("shape,ci,co", [((6, 7, 9), 8, 16), ((8, 8, 8), 16, 16), ((5, 6, 11), 16, 32),
+                                         ((4, 9, 6), 32, 64), ((4, 4, 4), 64, 128), ((3, 5, 4), 128, 64),
+                                         ((16, 16, 16), 32, 32)])
+def test_weight_gradient_matches_oracle(shape, ci, co):
+    rng = np.random.default_rng(11 + ci + co)
+    x = rng.normal(size=shape + (ci,)).astype(np.float32)
+    gy = rng.normal(size=shape + (co,)).astype(np.float32)
+    xb, gb = _bf16(x), _bf16(gy)
+    dw = torch.zeros(27 * ci * co, dtype=torch.float32, device="cuda")
+    D, H, W = shape
+    capi.conv3d_wgrad(xb.cuda().view(torch.int16), ci, gb.cuda().view(torch.int16), co, W, H, D, dw)
+    torch.cuda.synchronize()
+    xq, gq = xb.float().numpy().astype(np.float64), gb.float().numpy().astype(np.float64)
+    ref = dn.conv3d_dw(xq, gq)
+    mag = dn.conv3d_dw(np.abs(xq), np.abs(gq))
+    got = dw.cpu().numpy().reshape(27, ci, co)
+    assert np.all(np.abs(got - ref) <= 2e-5 * mag + 1e-6), np.abs(got - ref).max()
+
+
 def test_conv_rejects_bad_shapes():
     x = torch.zeros(64 * 8, dtype=torch.int16, device="cuda")
     w = torch.zeros(27 * 8 * 24, dtype=torch.float32, device="cuda")
