@@ -52,6 +52,47 @@ PSL_API int psl_conv3d(const uint16_t *in, int32_t ci, const uint16_t *wpk, cons
 PSL_API int psl_conv3d_wgrad(const uint16_t *in, int32_t ci, const uint16_t *gy, int32_t co, int32_t nx, int32_t ny,
                              int32_t nz, float *dw, void *stream);
 
+/* The denoiser network.  Input: dose / scale and density (two channels,
+ * padded to 8); output: dose.  Layers (3x3x3 convolution + ReLU, channels):
+ *   e0a 8->16, e0b 16->16  -> skip s0, 2x2x2 average pool
+ *   e1 16->32              -> skip s1, pool
+ *   e2 32->64              -> skip s2, pool
+ *   b3a 64->128, b3b 128->64
+ *   up x2 + s2, d2 64->32; up x2 + s1, d1 32->16; up x2 + s0, d0 16->16
+ *   y = d0 . w_out + b_out + dose / scale;  out = y * scale.
+ * Parameters (FP32, psl_denoiser_param_count() of them, in this order): for
+ * each layer e0a..d0 its taps [27][ci][co] then its biases [co]; then w_out
+ * [16], b_out [1].  psl_denoiser_create draws He-normal taps from `seed`,
+ * zero biases and a zero output layer (the network starts as the identity
+ * on the dose).  Volume sides must be multiples of 8.  All calls synchronise
+ * stream. */
+typedef struct psl_denoiser psl_denoiser_t;
+PSL_API int64_t psl_denoiser_param_count(void);
+PSL_API int psl_denoiser_create(uint64_t seed, psl_denoiser_t **out);
+PSL_API void psl_denoiser_destroy(psl_denoiser_t *d);
+
+/* Device arrays of psl_denoiser_param_count() floats, NULL to skip: `set`
+ * replaces the parameters, `get` receives them, `grad` receives the
+ * accumulated gradients (sums over the psl_denoiser_backward calls since the
+ * last step). */
+PSL_API int psl_denoiser_params(psl_denoiser_t *d, const float *set, float *get, float *grad, void *stream);
+
+/* Denoise: dose and rho are FP32 device volumes [nz][ny][nx] (Gy, g/cm^3);
+ * scale > 0 normalises the dose for the network (e.g. its maximum); out
+ * (FP32, device, same shape) receives the denoised dose. */
+PSL_API int psl_denoiser_forward(psl_denoiser_t *d, const float *dose, const float *rho, int32_t nx, int32_t ny,
+                                 int32_t nz, float scale, float *out, void *stream);
+
+/* One training sample: forward, the mean squared error against target / scale
+ * over the voxels (written to *loss, host, may be NULL) and its gradient,
+ * added to the accumulated gradients. */
+PSL_API int psl_denoiser_backward(psl_denoiser_t *d, const float *dose, const float *rho, const float *target,
+                                  int32_t nx, int32_t ny, int32_t nz, float scale, double *loss, void *stream);
+
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr on the mean
+ * of the accumulated gradients, which are then cleared. */
+PSL_API int psl_denoiser_step(psl_denoiser_t *d, float lr, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,9 @@ EXPORTS = (
     "psl_tally_destroy", "psl_last_error", "psl_kernel_launches", "psl_profile", "psl_profile_read",
     "psl_build_static", "psl_atomic_peak", "psl_run", "psl_autotune", "psl_stream_bin", "psl_stream_info",
     "psl_stream_read", "psl_batch_read", "psl_memory_trim",
-    "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d", "psl_conv3d_wgrad",
+    "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d", "psl_conv3d_wgrad", "psl_denoiser_param_count",
+    "psl_denoiser_create", "psl_denoiser_destroy", "psl_denoiser_params", "psl_denoiser_forward",
+    "psl_denoiser_backward", "psl_denoiser_step",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
@@ -86,6 +88,10 @@ def lib():
         L.psl_kernel_launches.argtypes = []
         L.psl_last_error.restype = ctypes.c_char_p
         L.psl_last_error.argtypes = []
+        L.psl_denoiser_param_count.restype = ctypes.c_int64
+        L.psl_denoiser_param_count.argtypes = []
+        L.psl_denoiser_destroy.restype = None
+        L.psl_denoiser_destroy.argtypes = [vp]
         L.psl_conv3d_packed_size.restype = ctypes.c_int64
         L.psl_conv3d_packed_size.argtypes = [i32, i32]
         L.psl_physics_default.restype = None
@@ -124,6 +130,11 @@ def lib():
             "psl_conv3d_pack": [vp, i32, i32, i32, vp, vp],
             "psl_conv3d": [vp, i32, vp, vp, i32, i32, i32, i32, i32, vp, vp, vp],
             "psl_conv3d_wgrad": [vp, i32, vp, i32, i32, i32, i32, vp, vp],
+            "psl_denoiser_create": [u64, vp],
+            "psl_denoiser_params": [vp, vp, vp, vp, vp],
+            "psl_denoiser_forward": [vp, vp, vp, i32, i32, i32, f32, vp, vp],
+            "psl_denoiser_backward": [vp, vp, vp, vp, i32, i32, i32, f32, vp, vp],
+            "psl_denoiser_step": [vp, f32, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -352,6 +363,37 @@ def conv3d_wgrad(x, ci: int, gy, co: int, nx: int, ny: int, nz: int, dw, stream=
     """dw[27, ci, co] (FP32, device) += the tap gradient (see psl_denoise.h)."""
     check(lib().psl_conv3d_wgrad(ptr(x), int(ci), ptr(gy), int(co), int(nx), int(ny), int(nz), ptr(dw),
                                  stream_ptr(stream)))
+
+
+class Denoiser(Handle):
+    """The dose denoiser network (see psl_denoise.h)."""
+    _destroy = "psl_denoiser_destroy"
+
+    @staticmethod
+    def param_count() -> int:
+        return int(lib().psl_denoiser_param_count())
+
+    @classmethod
+    def create(cls, seed: int = 0) -> "Denoiser":
+        h = _out_handle()
+        check(lib().psl_denoiser_create(int(seed), ctypes.byref(h)))
+        return cls(h.value)
+
+    def params(self, set=None, get=None, grad=None, stream=None):
+        check(lib().psl_denoiser_params(self.h, ptr(set), ptr(get), ptr(grad), stream_ptr(stream)))
+
+    def forward(self, dose, rho, nx: int, ny: int, nz: int, scale: float, out, stream=None):
+        check(lib().psl_denoiser_forward(self.h, ptr(dose), ptr(rho), int(nx), int(ny), int(nz), float(scale),
+                                         ptr(out), stream_ptr(stream)))
+
+    def backward(self, dose, rho, target, nx: int, ny: int, nz: int, scale: float, stream=None) -> float:
+        loss = ctypes.c_double()
+        check(lib().psl_denoiser_backward(self.h, ptr(dose), ptr(rho), ptr(target), int(nx), int(ny), int(nz),
+                                          float(scale), ctypes.byref(loss), stream_ptr(stream)))
+        return loss.value
+
+    def step(self, lr: float, stream=None):
+        check(lib().psl_denoiser_step(self.h, float(lr), stream_ptr(stream)))
 
 
 def psl_tally_create(phantom: Phantom, n_batches: int) -> Tally:
