@@ -430,6 +430,19 @@ PSL_API int psl_atomic_peak(int64_t n_cells, int64_t n_updates, double *updates_
  * a diagnostic for counting the launches of a timed region. */
 PSL_API int64_t psl_kernel_launches(void);
 
+/* Dose comparison by the global gamma index (the paper's Sec. 3 criteria,
+ * e.g. 2 % / 2 mm): the fraction of reference voxels with D_ref >= threshold
+ * * max(ref) whose gamma <= 1.  Gamma at a reference voxel is the minimum
+ * over evaluated points r within max_radius_cm (<= 0: 1.5 dta) of
+ * sqrt(|r - r_ref|^2 / dta^2 + (D_ev(r) - D_ref)^2 / (dose_crit max ref)^2),
+ * D_ev trilinear between voxel centres, on a grid of voxel / upsample
+ * (1..16); points outside the volume are skipped.  ref, ev: device float64
+ * [nz][ny][nx]; voxel sizes in cm; outputs on the host.  FP64 throughout.
+ * Synchronises stream. */
+PSL_API int psl_gamma(const double *ref, const double *ev, int32_t nx, int32_t ny, int32_t nz, float vx, float vy,
+                      float vz, double dose_crit, double dta_cm, double threshold, int32_t upsample,
+                      double max_radius_cm, double *pass_rate, int64_t *n_evaluated, void *stream);
+
 /* The library takes its stream-ordered scratch (psl_build, psl_plan_create,
  * psl_stream_bin, batches) from its own device memory pool, one per device,
  * which keeps freed blocks for the next call.  psl_memory_trim waits for the

@@ -30,7 +30,7 @@ EXPORTS = (
     "psl_stream_read", "psl_batch_read", "psl_memory_trim",
     "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d", "psl_conv3d_wgrad", "psl_denoiser_param_count",
     "psl_denoiser_create", "psl_denoiser_destroy", "psl_denoiser_params", "psl_denoiser_forward",
-    "psl_denoiser_backward", "psl_denoiser_step",
+    "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
@@ -135,6 +135,7 @@ def lib():
             "psl_denoiser_forward": [vp, vp, vp, i32, i32, i32, f32, vp, vp],
             "psl_denoiser_backward": [vp, vp, vp, vp, i32, i32, i32, f32, vp, vp],
             "psl_denoiser_step": [vp, f32, vp],
+            "psl_gamma": [vp, vp, i32, i32, i32, f32, f32, f32, f64, f64, f64, i32, f64, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -363,6 +364,18 @@ def conv3d_wgrad(x, ci: int, gy, co: int, nx: int, ny: int, nz: int, dw, stream=
     """dw[27, ci, co] (FP32, device) += the tap gradient (see psl_denoise.h)."""
     check(lib().psl_conv3d_wgrad(ptr(x), int(ci), ptr(gy), int(co), int(nx), int(ny), int(nz), ptr(dw),
                                  stream_ptr(stream)))
+
+
+def gamma(ref, ev, voxel, dose_crit=0.02, dta_cm=0.2, threshold=0.10, upsample=4, max_radius_cm=0.0,
+          stream=None):
+    """Global gamma pass rate of ev against ref (device float64 [nz, ny, nx]);
+    returns (pass rate, voxels evaluated)."""
+    nz, ny, nx = ref.shape
+    rate, n = ctypes.c_double(), i64()
+    check(lib().psl_gamma(ptr(ref), ptr(ev), nx, ny, nz, float(voxel[0]), float(voxel[1]), float(voxel[2]),
+                          float(dose_crit), float(dta_cm), float(threshold), int(upsample), float(max_radius_cm),
+                          ctypes.byref(rate), ctypes.byref(n), stream_ptr(stream)))
+    return rate.value, n.value
 
 
 class Denoiser(Handle):

@@ -148,3 +148,99 @@ extern "C" int psl_atomic_peak(int64_t n_cells, int64_t n_updates, double *updat
     *updates_per_s = (double)n_updates / (ms * 1e-3);
     return PSL_OK;
 }
+
+// ------------------------------------------------------------------ gamma --
+// Global gamma index (Sec. 3 comparisons; 2 % / 2 mm in the paper's tables):
+// at every reference voxel with D_ref >= threshold * max(ref), the minimum
+// over evaluated points r within the search radius of sqrt(|r - r_ref|^2 /
+// dta^2 + (D_ev(r) - D_ref)^2 / (dose_crit max ref)^2), with D_ev trilinear
+// between voxel centres on a grid of voxel / upsample; points outside the
+// volume are skipped.  FP64 throughout.
+namespace {
+__global__ void k_max(const double *a, int64_t n, unsigned long long *mx) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, a[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    // non-negative doubles order as their bit patterns
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+__device__ __forceinline__ bool trilinear(const double *a, int nx, int ny, int nz, double fz, double fy, double fx,
+                                          double &out) {
+    if (!(fz >= 0.0 && fz <= nz - 1 && fy >= 0.0 && fy <= ny - 1 && fx >= 0.0 && fx <= nx - 1)) return false;
+    int z0 = (int)floor(fz), y0 = (int)floor(fy), x0 = (int)floor(fx);
+    z0 = min(z0, nz - 2 < 0 ? 0 : nz - 2); y0 = min(y0, ny - 2 < 0 ? 0 : ny - 2); x0 = min(x0, nx - 2 < 0 ? 0 : nx - 2);
+    const int z1 = min(z0 + 1, nz - 1), y1 = min(y0 + 1, ny - 1), x1 = min(x0 + 1, nx - 1);
+    const double tz = fz - z0, ty = fy - y0, tx = fx - x0;
+    auto at = [&](int z, int y, int x) { return a[((int64_t)z * ny + y) * nx + x]; };
+    const double c00 = at(z0, y0, x0) * (1 - tx) + at(z0, y0, x1) * tx;
+    const double c01 = at(z0, y1, x0) * (1 - tx) + at(z0, y1, x1) * tx;
+    const double c10 = at(z1, y0, x0) * (1 - tx) + at(z1, y0, x1) * tx;
+    const double c11 = at(z1, y1, x0) * (1 - tx) + at(z1, y1, x1) * tx;
+    out = (c00 * (1 - ty) + c01 * ty) * (1 - tz) + (c10 * (1 - ty) + c11 * ty) * tz;
+    return true;
+}
+
+__global__ void k_gamma(const double *ref, const double *ev, int nx, int ny, int nz, double vx, double vy, double vz,
+                        const unsigned long long *mx, double dose_crit, double dta, double threshold, int upsample,
+                        double rad, unsigned long long *counts) {
+    const double dmax = __longlong_as_double((long long)*mx);
+    const double dd = dose_crit * dmax, thr = threshold * dmax;
+    const int64_t n = (int64_t)nx * ny * nz;
+    const double hz = vz / upsample, hy = vy / upsample, hx = vx / upsample;
+    const int mz = (int)ceil(rad / hz), my = (int)ceil(rad / hy), mxx = (int)ceil(rad / hx);
+    unsigned long long pass = 0, eval = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const double dr = ref[v];
+        if (!(dr >= thr) || dmax <= 0.0) continue;
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+        double best = (ev[v] - dr) / dd;
+        best *= best;
+        for (int iz = -mz; iz <= mz && best > 0.0; ++iz)
+            for (int iy = -my; iy <= my; ++iy)
+                for (int ix = -mxx; ix <= mxx; ++ix) {
+                    const double oz = iz * hz, oy = iy * hy, ox = ix * hx;
+                    const double r2 = oz * oz + oy * oy + ox * ox;
+                    if (r2 == 0.0 || r2 > rad * rad || r2 / (dta * dta) >= best) continue;
+                    double val;
+                    if (!trilinear(ev, nx, ny, nz, z + oz / vz, y + oy / vy, x + ox / vx, val)) continue;
+                    const double t = (val - dr) / dd;
+                    best = fmin(best, r2 / (dta * dta) + t * t);
+                }
+        eval++;
+        if (best <= 1.0) pass++;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        pass += __shfl_xor_sync(0xFFFFFFFFu, pass, o);
+        eval += __shfl_xor_sync(0xFFFFFFFFu, eval, o);
+    }
+    if ((threadIdx.x & 31) == 0) { atomicAdd(counts, pass); atomicAdd(counts + 1, eval); }
+}
+}  // namespace
+
+extern "C" int psl_gamma(const double *ref, const double *ev, int32_t nx, int32_t ny, int32_t nz, float vx, float vy,
+                         float vz, double dose_crit, double dta_cm, double threshold, int32_t upsample,
+                         double max_radius_cm, double *pass_rate, int64_t *n_evaluated, void *stream_) {
+    if (!ref || !ev || nx <= 0 || ny <= 0 || nz <= 0 || !(vx > 0) || !(vy > 0) || !(vz > 0) || !(dose_crit > 0) ||
+        !(dta_cm > 0) || upsample < 1 || upsample > 16)
+        return psl_fail(PSL_EINVAL, "psl_gamma: bad argument");
+    cudaStream_t st = as_stream(stream_);
+    const int64_t n = (int64_t)nx * ny * nz;
+    unsigned long long *buf = nullptr;
+    PSL_CUDA(psl_malloc_async((void **)&buf, 24, st));
+    cudaMemsetAsync(buf, 0, 24, st);
+    const int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)psl_sm_count() * 8);
+    k_max<<<g, 256, 0, st>>>(ref, n, buf); PSL_NOTE_LAUNCH();
+    const double rad = max_radius_cm > 0 ? max_radius_cm : 1.5 * dta_cm;
+    k_gamma<<<g, 256, 0, st>>>(ref, ev, nx, ny, nz, vx, vy, vz, buf, dose_crit, dta_cm, threshold, upsample, rad,
+                               buf + 1); PSL_NOTE_LAUNCH();
+    unsigned long long h[2] = {0, 0};
+    cudaMemcpyAsync(h, buf + 1, 16, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(buf, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, cudaGetErrorString(e));
+    if (pass_rate) *pass_rate = h[1] ? (double)h[0] / (double)h[1] : 0.0;
+    if (n_evaluated) *n_evaluated = (int64_t)h[1];
+    return PSL_OK;
+}
