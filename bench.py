@@ -184,6 +184,7 @@ def main():
     ap.add_argument("--no-apr", action="store_true")
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-t1pct", action="store_true")
+    ap.add_argument("--no-denoise", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -373,6 +374,9 @@ def main():
     apr = None
     if rank == 0 and world == 1 and not args.no_apr:
         apr = apr_build(capi, engine, inputs, torch, flush)
+    denoised = None
+    if rank == 0 and world == 1 and not args.no_denoise:
+        denoised = denoised_run(capi, torch, w, flush, peaks_for_denoise())
     methods = None
     if rank == 0 and world == 1 and not args.no_methods:
         methods = stream_method_run(capi, engine, torch, flush, w, dw, per_rank)
@@ -398,6 +402,7 @@ def main():
                 "imrt_batched_graph": imrt,
                 "apr_build": apr,
                 "methods": methods,
+                "denoised": denoised,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
         print(json.dumps(line))
     if world > 1:
@@ -415,6 +420,76 @@ THREAD_INST_PER_WOODCOCK_STEP = 439.6
 DRAM_BYTES_PER_HISTORY = {"electron": 28.22, "photon": 40.06}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
+
+
+def peaks_for_denoise():
+    peaks, kind = measured_peaks()
+    return peaks, kind
+
+
+def conv_flops(V):
+    """Multiply-add FLOPs of the denoiser's convolutions on a volume of V voxels."""
+    lay = [(0, 8, 16), (0, 16, 16), (1, 16, 32), (2, 32, 64), (3, 64, 128), (3, 128, 64), (2, 64, 32), (1, 32, 16),
+           (0, 16, 16)]
+    return sum(2.0 * (V / 8 ** lev) * 27 * ci * co for lev, ci, co in lay)
+
+
+def denoised_run(capi, torch, w, flush, peaks):
+    """The denoised form on this workload: trained weights (the package's
+    weights/denoiser_psl.npy, trained by `python -m
+    paper_1302_1861_b300.denoiser` on pairs the method generated on other
+    seeded geometries), a plain 2e9-history reference, low-history runs
+    denoised and scored; the tensor-core convolution timed alone on its
+    heaviest shape, and the network's inference on a full 128^3 volume."""
+    from paper_1302_1861_b300 import denoiser as dz
+    path = os.path.join(ROOT, "paper_1302_1861_b300", "weights", "denoiser_psl.npy")
+    if not os.path.exists(path):
+        return {"unavailable": "no trained weights"}
+    den = dz.load(path)
+    runner = dz.DoseRunner(w)
+    ref, _, t_ref = runner.dose(runner.dw, 2_000_000_000, 4242)
+    runs = [dz.evaluate(den, runner, runner.dw, n, ref, seed=77 + i)
+            for i, n in enumerate((3_000_000, 10_000_000, 30_000_000))]
+    # the convolution kernel alone: 64^3 voxels, 64 -> 128 channels (1.2e11 FLOP)
+    V, ci, co = 64 ** 3, 64, 128
+    x = torch.randn(V * ci, device="cuda").to(torch.bfloat16)
+    wt = torch.randn(27 * ci * co, device="cuda") * 0.05
+    wpk = capi.conv3d_pack(wt, ci, co)
+    out = torch.empty(V * co, dtype=torch.bfloat16, device="cuda")
+    ts = []
+    for it in range(6):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        capi.conv3d(x.view(torch.int16), ci, wpk, None, co, 64, 64, 64, True, out.view(torch.int16))
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= 2:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    t_conv = float(np.median(ts))
+    fl = 2.0 * V * 27 * ci * co
+    pk = peaks[0].get("bf16_tflops") if isinstance(peaks[0], dict) else None
+    conv = {"shape": "64^3 x 64->128, 3x3x3", "flop": fl, "ms": 1e3 * t_conv, "tflops": fl / t_conv / 1e12,
+            "peak_tflops": pk, "frac": (fl / t_conv / 1e12 / pk) if pk else None,
+            "peak_kind": f"bf16_tflops ({peaks[1]})", "note": "psl_conv3d call: includes its host synchronisation"}
+    # inference on a full 128^3 volume
+    n = 128
+    dose = torch.rand(n ** 3, device="cuda")
+    rho = torch.ones(n ** 3, device="cuda")
+    o = torch.empty_like(dose)
+    ti = []
+    for it in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        den.forward(dose, rho, n, n, n, 1.0, o)
+        torch.cuda.synchronize()
+        if it >= 2:
+            ti.append(time.perf_counter() - t0)
+    t_inf = float(np.median(ti))
+    den.close()
+    return {"reference_histories": 2_000_000_000, "reference_seconds": t_ref, "runs": runs, "conv_kernel": conv,
+            "inference_128cubed": {"ms": 1e3 * t_inf, "conv_tflops": conv_flops(n ** 3) / t_inf / 1e12}}
 
 
 def time_to_1pct(capi, torch, w, dw, phys, n_est, sl, shape):

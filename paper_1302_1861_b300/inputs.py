@@ -325,6 +325,26 @@ def config4(n_records: int = 40_000_000, n_histories: int = 500_000_000) -> Work
                     ct_phantom(4, (100, 128, 128), 0.25), n_histories)
 
 
+def denoiser_geometry(kind: str, g: int):
+    """Seeded training geometry g for the dose denoiser: ('slab', g) a 64^3 x
+    0.25 cm slab phantom (config-2 recipe, its own slab depths) under a square
+    field of side U(3, 10) cm shifted by up to 1 cm; ('ct', g) a 128^3 x 0.25
+    cm CT-like phantom (config-3 recipe) under a field of side U(8, 30) cm
+    with its own smooth fluence map.  Returns (phantom, beams)."""
+    rng = _rng(100 + g, 7 if kind == "slab" else 8)
+    f32 = lambda v: float(np.float32(v))
+    if kind == "slab":
+        side = rng.uniform(3.0, 10.0)
+        cx, cy = rng.uniform(-1.0, 1.0, 2)
+        beams = [Beam(f32(cx - side / 2), f32(cx + side / 2), f32(cy - side / 2), f32(cy + side / 2),
+                      roi_margin=1.0)]
+        return slab_phantom(1000 + g, 64, 0.25), beams
+    side = rng.uniform(8.0, 30.0)
+    beams = [Beam(f32(-side / 2), f32(side / 2), f32(-side / 2), f32(side / 2), roi_margin=1.0,
+                  fluence=smooth_field(rng), fx0=-20.0, fy0=-20.0, fdx=1.0, fdy=1.0)]
+    return ct_phantom(2000 + g, (128, 128, 128), 0.25), beams
+
+
 def small(config: int = 1, n_records: int = 20_000, n_histories: int = 4_000) -> Workload:
     """A reduced copy of a workload for fast parity tests (same recipe)."""
     if config == 1:
