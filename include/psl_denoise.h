@@ -45,6 +45,15 @@ PSL_API int psl_conv3d(const uint16_t *in, int32_t ci, const uint16_t *wpk, cons
                        int32_t nx, int32_t ny, int32_t nz, int32_t relu, uint16_t *out, float *out_f32,
                        void *stream);
 
+/* Which form psl_conv3d (and the network) uses: 0 (default) the TMA form
+ * wherever the volume allows (nx >= 128, or nx a power of two: the 128
+ * voxels of a CTA are one box of the volume, loaded by the tensor memory
+ * accelerator with its zero fill as the padding, warp-specialised copy /
+ * MMA / epilogue roles over a 4-stage ring), else the gather form; 1 the
+ * gather form everywhere (threads load the A rows; two-stage ring).  Both
+ * give the same result. */
+PSL_API int psl_conv3d_form(int32_t form);
+
 /* The tap gradient of that convolution, on the tensor cores:
  *   dw[t, i, o] += sum_v in[v + offset_t, i] gy[v, o]
  * (FP32 dw [27][ci][co], device, accumulated into: zero it first).  in BF16

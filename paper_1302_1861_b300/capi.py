@@ -30,7 +30,7 @@ EXPORTS = (
     "psl_stream_read", "psl_batch_read", "psl_memory_trim",
     "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d", "psl_conv3d_wgrad", "psl_denoiser_param_count",
     "psl_denoiser_create", "psl_denoiser_destroy", "psl_denoiser_params", "psl_denoiser_forward",
-    "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma",
+    "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma", "psl_conv3d_form",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
@@ -136,6 +136,7 @@ def lib():
             "psl_denoiser_backward": [vp, vp, vp, vp, i32, i32, i32, f32, vp, vp],
             "psl_denoiser_step": [vp, f32, vp],
             "psl_gamma": [vp, vp, i32, i32, i32, f32, f32, f32, f64, f64, f64, i32, f64, vp, vp, vp],
+            "psl_conv3d_form": [i32],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -358,6 +359,11 @@ def conv3d(x, ci: int, wpk, bias, co: int, nx: int, ny: int, nz: int, relu: bool
     """3x3x3 convolution on the tensor cores (see psl_denoise.h); x, out: BF16 bit patterns."""
     check(lib().psl_conv3d(ptr(x), int(ci), ptr(wpk), ptr(bias), int(co), int(nx), int(ny), int(nz),
                            1 if relu else 0, ptr(out), ptr(out_f32), stream_ptr(stream)))
+
+
+def conv3d_form(form: int):
+    """0: TMA form where the volume allows, 1: gather form everywhere."""
+    check(lib().psl_conv3d_form(int(form)))
 
 
 def conv3d_wgrad(x, ci: int, gy, co: int, nx: int, ny: int, nz: int, dw, stream=None):

@@ -13,11 +13,13 @@
 // threads go on to fill the other buffer.  The epilogue reads the
 // accumulator back with tcgen05.ld, adds the bias, applies ReLU and stores
 // BF16 (or FP32).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "../../include/psl_denoise.h"
 #include "psl_internal.cuh"
@@ -289,6 +291,208 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(WgradArgs a) {
     if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
 }
 
+// ------------------------------------------------------ TMA form ---
+// The same implicit GEMM with its operands brought in by the tensor memory
+// accelerator and the work split by warp role.  A CTA's 128 voxels are a
+// box of BX x BY x BZ voxels of the volume; for one K chunk (8 channels of
+// one tap) the A rows are one 4-D TMA box {8 channels, BX, BY, BZ} of the
+// input at the tap's offset, its out-of-volume part filled with zeros by the
+// copy engine (the convolution's padding), landing as 128 rows of 16 bytes
+// (core matrices 128 bytes apart, the two chunks of a K step 2 KB apart).
+// The B tile of a stage is one bulk copy of the packed taps.  Warp 0 issues
+// the copies into a 4-stage ring (full / empty mbarriers), warp 1 issues the
+// MMAs and frees each stage by committing to its empty barrier, warps 2-5
+// read the accumulator back.
+constexpr int TKS = 4;                // K steps per stage
+constexpr int TST = 4;                // stages
+
+struct TmaConvArgs {
+    const __nv_bfloat16 *wpk;
+    const float *bias;
+    __nv_bfloat16 *out;
+    float *out_f32;
+    int ci, D, H, W, relu, ksteps;
+    int bx, by, bz;                   // the CTA's voxel box
+    uint32_t *err;
+};
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+
+template <int N>
+__global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ CUtensorMap map, TmaConvArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int A_ST = TKS * BM * 32, B_ST = TKS * N * 32;
+    constexpr uint32_t TCOLS = N < 32 ? 32 : N;
+    uint8_t *sA = smem, *sB = smem + TST * A_ST;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + TST * (A_ST + B_ST));
+    uint64_t *empty = full + TST, *accum = empty + TST;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accum + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int x0 = blockIdx.x * a.bx, y0 = blockIdx.y * a.by, z0 = blockIdx.z * a.bz;
+    if (warp == 1) { tc::tmem_alloc(tslot, TCOLS); tc::tmem_relinquish(); }
+    if (t == 0) {
+        for (int s = 0; s < TST; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        tc::mbar_init(accum, 1);
+        *abort_flag = 0;
+        tc::mbar_fence_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int nkb = (a.ksteps + TKS - 1) / TKS;
+
+    if (warp == 0 && lane == 0) {                           // producer
+        for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
+            const int s = kb % TST;
+            const uint32_t ph = (uint32_t)(kb / TST) & 1u;
+            if (!tc::mbar_wait(&empty[s], ph ^ 1u, WAIT_LIMIT)) { *abort_flag = 1; atomicOr(a.err, PSL_DEV_ERR_TIMEOUT); break; }
+            const int nks = min(TKS, a.ksteps - kb * TKS);
+            const uint32_t fb = tc::smem_u32(&full[s]);
+            mbar_expect_tx(fb, (uint32_t)(nks * 2 * BM * 16 + nks * N * 32));
+            for (int kk = 0; kk < nks; ++kk) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int k0 = (2 * (kb * TKS + kk) + j) * 8;
+                    const int tap = k0 / a.ci, c0 = k0 - tap * a.ci;
+                    const uint32_t dst = tc::smem_u32(sA + s * A_ST + kk * (BM * 32) + j * (BM * 16));
+                    if (tap < 27)
+                        tma_load_4d(dst, &map, c0, x0 + tap % 3 - 1, y0 + (tap / 3) % 3 - 1, z0 + tap / 9 - 1, fb);
+                    else                                             // K padding: a box wholly outside, all zeros
+                        tma_load_4d(dst, &map, 0, x0, y0, -4 * a.bz - 8, fb);
+                }
+            }
+            bulk_load(tc::smem_u32(sB + s * B_ST), a.wpk + (size_t)kb * TKS * N * 16, (uint32_t)(nks * N * 32), fb);
+        }
+    } else if (warp == 1 && lane == 0) {                    // MMA issuer
+        const uint32_t idesc = tc::idesc_bf16(BM, N);
+        for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
+            const int s = kb % TST;
+            if (!tc::mbar_wait(&full[s], (uint32_t)(kb / TST) & 1u, WAIT_LIMIT)) { *abort_flag = 1; atomicOr(a.err, PSL_DEV_ERR_TIMEOUT); break; }
+            tc::fence_after_sync();
+            const int nks = min(TKS, a.ksteps - kb * TKS);
+            for (int kk = 0; kk < nks; ++kk) {
+                const uint64_t ad = tc::desc_kmajor(tc::smem_u32(sA + s * A_ST + kk * (BM * 32)), BM * 16, 128);
+                const uint64_t bd = tc::desc_kmajor(tc::smem_u32(sB + s * B_ST + kk * (N * 32)), 128, 256);
+                tc::mma_bf16(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(accum);
+    } else if (warp >= 2) {                                  // epilogue
+        const bool ok = tc::mbar_wait(accum, 0u, WAIT_LIMIT) && !*abort_flag;
+        if (!ok && t == 64) { *abort_flag = 1; atomicOr(a.err, PSL_DEV_ERR_TIMEOUT); }
+        tc::fence_after_sync();
+        const int q = warp & 3;                              // TMEM lanes 32q..32q+31
+        const int m = 32 * q + lane;
+        const int xx = x0 + m % a.bx, yy = y0 + (m / a.bx) % a.by, zz = z0 + m / (a.bx * a.by);
+        const bool row_ok = ok && xx < a.W && yy < a.H && zz < a.D;
+        const int64_t v = ((int64_t)zz * a.H + yy) * a.W + xx;
+        if (__any_sync(0xFFFFFFFFu, ok)) {
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float r[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
+                if (row_ok) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float qv = r[i] + (a.bias ? __ldg(a.bias + c0 + i) : 0.0f);
+                        r[i] = a.relu ? fmaxf(qv, 0.0f) : qv;
+                    }
+                    if (a.out) {
+                        __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(r[i]);
+                        uint4 *dst = reinterpret_cast<uint4 *>(a.out + v * N + c0);
+                        dst[0] = reinterpret_cast<uint4 *>(h)[0];
+                        dst[1] = reinterpret_cast<uint4 *>(h)[1];
+                    }
+                    if (a.out_f32) {
+                        float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + v * N + c0);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) dst[i] = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, TCOLS);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// the CTA box of the TMA form, or false when the volume needs the gather form
+bool tma_box(int W, int H, int D, int &bx, int &by, int &bz) {
+    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (W >= BM) { bx = BM; by = 1; bz = 1; return true; }
+    if (!pow2(W)) return false;
+    bx = W;
+    int rest = BM / bx, h = 1;
+    while (h * 2 <= H && h * 2 <= rest) h *= 2;
+    by = h;
+    bz = rest / by;
+    return bz <= 256 && by <= 256 && bx <= 256 && D >= 1;
+}
+
+template <int N>
+int launch_tma(const ConvArgs &c, int bx, int by, int bz, cudaStream_t st) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return psl_fail(PSL_ECUDA, "conv3d: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap map;
+    const cuuint64_t dims[4] = {(cuuint64_t)c.ci, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.D};
+    const cuuint64_t strides[3] = {(cuuint64_t)c.ci * 2, (cuuint64_t)c.ci * 2 * c.W, (cuuint64_t)c.ci * 2 * c.W * c.H};
+    const cuuint32_t box[4] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(c.in), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return psl_fail(PSL_ECUDA, "conv3d: tensor map encoding failed");
+    const size_t smem = (size_t)TST * (TKS * BM * 32 + TKS * N * 32) + 128;
+    static bool attr = false;
+    if (!attr) {
+        PSL_CUDA(cudaFuncSetAttribute(k_conv3d_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    TmaConvArgs a{c.wpk, c.bias, c.out, c.out_f32, c.ci, c.D, c.H, c.W, c.relu, c.ksteps, bx, by, bz, c.err};
+    const dim3 grid((c.W + bx - 1) / bx, (c.H + by - 1) / by, (c.D + bz - 1) / bz);
+    k_conv3d_tma<N><<<grid, 192, smem, st>>>(map, a); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaGetLastError());
+    return PSL_OK;
+}
+
 // Taps W[27][ci][co] (FP32) -> BF16 B tiles: K step s, 8-row group g of the
 // outputs, K chunk j, row n % 8, element e: k = 16 s + 8 j + e, tap = k / ci.
 // mirror: the input-gradient form, W'[t][o][i] = W[26 - t][i][o] (a
@@ -362,11 +566,23 @@ int psl_conv3d_wgrad_run(const __nv_bfloat16 *x, int ci, const __nv_bfloat16 *gy
     }
 }
 
+static int g_conv_form = 0;             // 0: TMA form where the volume allows, 1: gather form only
+
 int psl_conv3d_run(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, const float *bias, int co, int nx,
                    int ny, int nz, int relu, __nv_bfloat16 *out, float *out_f32, uint32_t *err, cudaStream_t st) {
     ConvArgs a{in, wpk, bias, out, out_f32, ci, nz, ny, nx, relu, psl_conv_ksteps(ci), err};
     const int64_t V = (int64_t)nx * ny * nz;
     if (V == 0) return PSL_OK;
+    int bx, by, bz;
+    if (g_conv_form == 0 && tma_box(nx, ny, nz, bx, by, bz)) {
+        switch (co) {
+            case 16: return launch_tma<16>(a, bx, by, bz, st);
+            case 32: return launch_tma<32>(a, bx, by, bz, st);
+            case 64: return launch_tma<64>(a, bx, by, bz, st);
+            case 128: return launch_tma<128>(a, bx, by, bz, st);
+            default: break;
+        }
+    }
     switch (co) {
         case 16: return launch<16>(a, V, st);
         case 32: return launch<32>(a, V, st);
@@ -443,5 +659,11 @@ extern "C" int psl_conv3d_wgrad(const uint16_t *x, int32_t ci, const uint16_t *g
     if (rc) return rc;
     if (e != cudaSuccess) return psl_fail(PSL_ECUDA, cudaGetErrorString(e));
     if (herr) return psl_fail(PSL_ETIMEOUT, "psl_conv3d_wgrad: tensor-core completion wait gave up");
+    return PSL_OK;
+}
+
+extern "C" int psl_conv3d_form(int32_t form) {
+    if (form != 0 && form != 1) return psl_fail(PSL_EINVAL, "psl_conv3d_form: 0 (TMA where possible) or 1 (gather)");
+    g_conv_form = form;
     return PSL_OK;
 }

@@ -44,10 +44,19 @@ def _run(x, w, b, relu, mirror=False):
             xin.float().cpu().numpy().astype(np.float64))
 
 
+@pytest.fixture(params=[0, 1], ids=["tma", "gather"])
+def form(request):
+    capi.conv3d_form(request.param)
+    yield request.param
+    capi.conv3d_form(0)
+
+
 @pytest.mark.parametrize("shape,ci,co", [((5, 7, 9), 8, 16), ((8, 8, 8), 16, 16), ((6, 5, 11), 16, 32),
                                          ((4, 9, 6), 32, 64), ((4, 4, 4), 64, 128), ((3, 5, 4), 128, 64),
-                                         ((2, 3, 23), 128, 128), ((16, 16, 16), 32, 32)])
-def test_conv_forward_matches_oracle(shape, ci, co):
+                                         ((2, 3, 23), 128, 128), ((16, 16, 16), 32, 32), ((3, 5, 64), 16, 16),
+                                         ((6, 4, 32), 64, 32), ((2, 2, 200), 16, 64), ((9, 3, 16), 128, 128),
+                                         ((4, 8, 8), 8, 16)])
+def test_conv_forward_matches_oracle(shape, ci, co, form):
     rng = np.random.default_rng(ci * 1000 + co)
     x = rng.normal(size=shape + (ci,)).astype(np.float32)
     w = rng.normal(0, 0.2, size=(27, ci, co)).astype(np.float32)
@@ -64,11 +73,11 @@ def test_conv_forward_matches_oracle(shape, ci, co):
 
 
 @pytest.mark.parametrize("ci,co", [(16, 16), (16, 32), (32, 64), (64, 128), (128, 64)])
-def test_mirrored_taps_give_the_input_gradient(ci, co):
+def test_mirrored_taps_give_the_input_gradient(ci, co, form):
     """psl_conv3d with the mirrored packing of w, applied to an output
     gradient, is the oracle's input gradient."""
     rng = np.random.default_rng(7 + ci + co)
-    gy = rng.normal(size=(5, 6, 7, co)).astype(np.float32)
+    gy = rng.normal(size=(5, 6, 8, co)).astype(np.float32)
     w = rng.normal(0, 0.2, size=(27, ci, co)).astype(np.float32)
     wq = _bf16(w).float().numpy().astype(np.float64)
     ob, of, gq = _run(gy, w, None, False, mirror=True)
