@@ -313,6 +313,7 @@ struct TmaConvArgs {
     float *out_f32;
     int ci, D, H, W, relu, ksteps;
     int bx, by, bz;                   // the CTA's voxel box
+    int wide;                         // 1: 16-channel boxes (C_in >= 16, 32-byte swizzle); 0: 8-channel boxes
     uint32_t *err;
 };
 
@@ -366,6 +367,13 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ C
             const uint32_t fb = tc::smem_u32(&full[s]);
             mbar_expect_tx(fb, (uint32_t)(nks * 2 * BM * 16 + nks * N * 32));
             for (int kk = 0; kk < nks; ++kk) {
+                if (a.wide) {                                // one 16-channel box per K step
+                    const int k0 = (kb * TKS + kk) * 16;
+                    const int tap = k0 / a.ci, c0 = k0 - tap * a.ci;
+                    tma_load_4d(tc::smem_u32(sA + s * A_ST + kk * (BM * 32)), &map, c0, x0 + tap % 3 - 1,
+                                y0 + (tap / 3) % 3 - 1, z0 + tap / 9 - 1, fb);
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     const int k0 = (2 * (kb * TKS + kk) + j) * 8;
@@ -387,7 +395,8 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ C
             tc::fence_after_sync();
             const int nks = min(TKS, a.ksteps - kb * TKS);
             for (int kk = 0; kk < nks; ++kk) {
-                const uint64_t ad = tc::desc_kmajor(tc::smem_u32(sA + s * A_ST + kk * (BM * 32)), BM * 16, 128);
+                const uint32_t aaddr = tc::smem_u32(sA + s * A_ST + kk * (BM * 32));
+                const uint64_t ad = a.wide ? tc::desc_kmajor_sw32(aaddr, 256) : tc::desc_kmajor(aaddr, BM * 16, 128);
                 const uint64_t bd = tc::desc_kmajor(tc::smem_u32(sB + s * B_ST + kk * (N * 32)), 128, 256);
                 tc::mma_bf16(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
             }
@@ -472,13 +481,16 @@ int launch_tma(const ConvArgs &c, int bx, int by, int bz, cudaStream_t st) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return psl_fail(PSL_ECUDA, "conv3d: cuTensorMapEncodeTiled unavailable");
     CUtensorMap map;
+    // 16-channel boxes fill whole 32-byte L2 sectors (8-channel ones fetch
+    // half of every sector for nothing); they land 32-byte swizzled
+    const int wide = c.ci >= 16 ? 1 : 0;
     const cuuint64_t dims[4] = {(cuuint64_t)c.ci, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.D};
     const cuuint64_t strides[3] = {(cuuint64_t)c.ci * 2, (cuuint64_t)c.ci * 2 * c.W, (cuuint64_t)c.ci * 2 * c.W * c.H};
-    const cuuint32_t box[4] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t box[4] = {wide ? 16u : 8u, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(c.in), dims, strides, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, wide ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return psl_fail(PSL_ECUDA, "conv3d: tensor map encoding failed");
     const size_t smem = (size_t)TST * (TKS * BM * 32 + TKS * N * 32) + 128;
     static bool attr = false;
@@ -486,7 +498,7 @@ int launch_tma(const ConvArgs &c, int bx, int by, int bz, cudaStream_t st) {
         PSL_CUDA(cudaFuncSetAttribute(k_conv3d_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
-    TmaConvArgs a{c.wpk, c.bias, c.out, c.out_f32, c.ci, c.D, c.H, c.W, c.relu, c.ksteps, bx, by, bz, c.err};
+    TmaConvArgs a{c.wpk, c.bias, c.out, c.out_f32, c.ci, c.D, c.H, c.W, c.relu, c.ksteps, bx, by, bz, wide, c.err};
     const dim3 grid((c.W + bx - 1) / bx, (c.H + by - 1) / by, (c.D + bz - 1) / bz);
     k_conv3d_tma<N><<<grid, 192, smem, st>>>(map, a); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());

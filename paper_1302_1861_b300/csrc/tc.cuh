@@ -24,6 +24,22 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr, uint32_t lbo, ui
     return d;                           // base offset 0, swizzle none
 }
 
+// Shared-memory matrix descriptor, K-major operand in the 32-byte swizzled
+// layout: rows of 32 bytes (16 BF16 of K: both K chunks of one MMA side by
+// side, their 16-byte halves exchanged on every other 4-row half of an
+// 8-row group, the pattern the copy engine writes with 32-byte swizzling);
+// `sbo` is the byte distance between 8-row groups.  The start address must
+// be 256-byte aligned (base offset 0).
+__device__ __forceinline__ uint64_t desc_kmajor_sw32(uint32_t saddr, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;            // leading byte offset: unused inside one swizzle atom
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;            // descriptor version
+    d |= (uint64_t)6u << 61;            // layout: 32-byte swizzle
+    return d;
+}
+
 // Instruction descriptor of tcgen05.mma.kind::f16: D FP32, A and B BF16,
 // both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
