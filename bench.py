@@ -415,9 +415,9 @@ def main():
 # / events) and DRAM bytes per history (dram__bytes_read + write).  See
 # profiles/transport_k_electron_k_photon_psl-10x10-slab64.md.  They hold for
 # the kernels they were measured on; re-measure after changing the kernels.
-THREAD_INST_PER_ELECTRON_STEP = 537.1
-THREAD_INST_PER_WOODCOCK_STEP = 439.6
-DRAM_BYTES_PER_HISTORY = {"electron": 28.22, "photon": 40.06}
+THREAD_INST_PER_ELECTRON_STEP = 503.9
+THREAD_INST_PER_WOODCOCK_STEP = 413.4
+DRAM_BYTES_PER_HISTORY = {"electron": 26.52, "photon": 58.76}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
 
@@ -450,8 +450,8 @@ def denoised_run(capi, torch, w, flush, peaks):
     ref, _, t_ref = runner.dose(runner.dw, 2_000_000_000, 4242)
     runs = [dz.evaluate(den, runner, runner.dw, n, ref, seed=77 + i)
             for i, n in enumerate((3_000_000, 10_000_000, 30_000_000))]
-    # the convolution kernel alone: 64^3 voxels, 64 -> 128 channels (1.2e11 FLOP)
-    V, ci, co = 64 ** 3, 64, 128
+    # the convolution kernel alone: 128^3 voxels, 128 -> 128 channels (1.9e12 FLOP)
+    V, ci, co = 128 ** 3, 128, 128
     x = torch.randn(V * ci, device="cuda").to(torch.bfloat16)
     wt = torch.randn(27 * ci * co, device="cuda") * 0.05
     wpk = capi.conv3d_pack(wt, ci, co)
@@ -462,7 +462,7 @@ def denoised_run(capi, torch, w, flush, peaks):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        capi.conv3d(x.view(torch.int16), ci, wpk, None, co, 64, 64, 64, True, out.view(torch.int16))
+        capi.conv3d(x.view(torch.int16), ci, wpk, None, co, 128, 128, 128, True, out.view(torch.int16))
         e1.record()
         torch.cuda.synchronize()
         if it >= 2:
@@ -470,7 +470,7 @@ def denoised_run(capi, torch, w, flush, peaks):
     t_conv = float(np.median(ts))
     fl = 2.0 * V * 27 * ci * co
     pk = peaks[0].get("bf16_tflops") if isinstance(peaks[0], dict) else None
-    conv = {"shape": "64^3 x 64->128, 3x3x3", "flop": fl, "ms": 1e3 * t_conv, "tflops": fl / t_conv / 1e12,
+    conv = {"shape": "128^3 x 128->128, 3x3x3", "flop": fl, "ms": 1e3 * t_conv, "tflops": fl / t_conv / 1e12,
             "peak_tflops": pk, "frac": (fl / t_conv / 1e12 / pk) if pk else None,
             "peak_kind": f"bf16_tflops ({peaks[1]})", "note": "psl_conv3d call: includes its host synchronisation"}
     # inference on a full 128^3 volume

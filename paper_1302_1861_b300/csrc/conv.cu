@@ -299,12 +299,17 @@ __global__ void __launch_bounds__(128, 1) k_conv3d_wgrad(WgradArgs a) {
 // input at the tap's offset, its out-of-volume part filled with zeros by the
 // copy engine (the convolution's padding), landing as 128 rows of 16 bytes
 // (core matrices 128 bytes apart, the two chunks of a K step 2 KB apart).
-// The B tile of a stage is one bulk copy of the packed taps.  Warp 0 issues
+// A CTA owns 2 x 128 voxels (two MMA tiles, two accumulators) so that each
+// B stage serves both.  The B tile of a stage is one bulk copy of the packed
+// taps.  Warp 0 issues
 // the copies into a 4-stage ring (full / empty mbarriers), warp 1 issues the
 // MMAs and frees each stage by committing to its empty barrier, warps 2-5
 // read the accumulator back.
 constexpr int TKS = 4;                // K steps per stage
 constexpr int TST = 4;                // stages
+// 128-voxel MMA tiles per CTA, sharing every B stage: two for wide outputs
+// (the B traffic dominates), one for narrow ones (more CTAs per SM)
+__host__ __device__ constexpr int tiles_for(int n) { return n >= 64 ? 2 : 1; }
 
 struct TmaConvArgs {
     const __nv_bfloat16 *wpk;
@@ -335,9 +340,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 
 template <int N>
 __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ CUtensorMap map, TmaConvArgs a) {
+    constexpr int TT = tiles_for(N);
     extern __shared__ __align__(1024) uint8_t smem[];
-    constexpr int A_ST = TKS * BM * 32, B_ST = TKS * N * 32;
-    constexpr uint32_t TCOLS = N < 32 ? 32 : N;
+    constexpr int A_ST = TKS * TT * BM * 32, B_ST = TKS * N * 32;
+    constexpr uint32_t TCOLS = TT * N < 32 ? 32 : TT * N;
     uint8_t *sA = smem, *sB = smem + TST * A_ST;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + TST * (A_ST + B_ST));
     uint64_t *empty = full + TST, *accum = empty + TST;
@@ -365,12 +371,12 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ C
             if (!tc::mbar_wait(&empty[s], ph ^ 1u, WAIT_LIMIT)) { *abort_flag = 1; atomicOr(a.err, PSL_DEV_ERR_TIMEOUT); break; }
             const int nks = min(TKS, a.ksteps - kb * TKS);
             const uint32_t fb = tc::smem_u32(&full[s]);
-            mbar_expect_tx(fb, (uint32_t)(nks * 2 * BM * 16 + nks * N * 32));
+            mbar_expect_tx(fb, (uint32_t)(nks * TT * BM * 32 + nks * N * 32));
             for (int kk = 0; kk < nks; ++kk) {
                 if (a.wide) {                                // one 16-channel box per K step
                     const int k0 = (kb * TKS + kk) * 16;
                     const int tap = k0 / a.ci, c0 = k0 - tap * a.ci;
-                    tma_load_4d(tc::smem_u32(sA + s * A_ST + kk * (BM * 32)), &map, c0, x0 + tap % 3 - 1,
+                    tma_load_4d(tc::smem_u32(sA + s * A_ST + kk * (TT * BM * 32)), &map, c0, x0 + tap % 3 - 1,
                                 y0 + (tap / 3) % 3 - 1, z0 + tap / 9 - 1, fb);
                     continue;
                 }
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ C
                 for (int j = 0; j < 2; ++j) {
                     const int k0 = (2 * (kb * TKS + kk) + j) * 8;
                     const int tap = k0 / a.ci, c0 = k0 - tap * a.ci;
-                    const uint32_t dst = tc::smem_u32(sA + s * A_ST + kk * (BM * 32) + j * (BM * 16));
+                    const uint32_t dst = tc::smem_u32(sA + s * A_ST + kk * (TT * BM * 32) + j * (TT * BM * 16));
                     if (tap < 27)
                         tma_load_4d(dst, &map, c0, x0 + tap % 3 - 1, y0 + (tap / 3) % 3 - 1, z0 + tap / 9 - 1, fb);
                     else                                             // K padding: a box wholly outside, all zeros
@@ -395,10 +401,15 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ C
             tc::fence_after_sync();
             const int nks = min(TKS, a.ksteps - kb * TKS);
             for (int kk = 0; kk < nks; ++kk) {
-                const uint32_t aaddr = tc::smem_u32(sA + s * A_ST + kk * (BM * 32));
-                const uint64_t ad = a.wide ? tc::desc_kmajor_sw32(aaddr, 256) : tc::desc_kmajor(aaddr, BM * 16, 128);
                 const uint64_t bd = tc::desc_kmajor(tc::smem_u32(sB + s * B_ST + kk * (N * 32)), 128, 256);
-                tc::mma_bf16(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+#pragma unroll
+                for (int tt = 0; tt < TT; ++tt) {
+                    // tile tt: rows 128 tt .. 128 tt + 127 of the stage's boxes
+                    const uint32_t base = tc::smem_u32(sA + s * A_ST + kk * (TT * BM * 32));
+                    const uint64_t ad = a.wide ? tc::desc_kmajor_sw32(base + tt * (BM * 32), 256)
+                                               : tc::desc_kmajor(base + tt * (BM * 16), TT * BM * 16, 128);
+                    tc::mma_bf16(tmem + (uint32_t)(tt * N), ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                }
             }
             tc::mma_commit(&empty[s]);
         }
@@ -408,15 +419,15 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ C
         if (!ok && t == 64) { *abort_flag = 1; atomicOr(a.err, PSL_DEV_ERR_TIMEOUT); }
         tc::fence_after_sync();
         const int q = warp & 3;                              // TMEM lanes 32q..32q+31
-        const int m = 32 * q + lane;
-        const int xx = x0 + m % a.bx, yy = y0 + (m / a.bx) % a.by, zz = z0 + m / (a.bx * a.by);
-        const bool row_ok = ok && xx < a.W && yy < a.H && zz < a.D;
-        const int64_t v = ((int64_t)zz * a.H + yy) * a.W + xx;
-        if (__any_sync(0xFFFFFFFFu, ok)) {
+        for (int tt = 0; tt < TT && __any_sync(0xFFFFFFFFu, ok); ++tt) {
+            const int m = tt * BM + 32 * q + lane;
+            const int xx = x0 + m % a.bx, yy = y0 + (m / a.bx) % a.by, zz = z0 + m / (a.bx * a.by);
+            const bool row_ok = ok && xx < a.W && yy < a.H && zz < a.D;
+            const int64_t v = ((int64_t)zz * a.H + yy) * a.W + xx;
 #pragma unroll
             for (int c0 = 0; c0 < N; c0 += 16) {
                 float r[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, r);
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(tt * N + c0), r);
                 if (row_ok) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
@@ -464,12 +475,14 @@ EncodeTiledFn encode_fn() {
 }
 
 // the CTA box of the TMA form, or false when the volume needs the gather form
-bool tma_box(int W, int H, int D, int &bx, int &by, int &bz) {
+bool tma_box(int W, int H, int D, int tt, int &bx, int &by, int &bz) {
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-    if (W >= BM) { bx = BM; by = 1; bz = 1; return true; }
-    if (!pow2(W)) return false;
-    bx = W;
-    int rest = BM / bx, h = 1;
+    const int vox = tt * BM;                      // voxels of one CTA
+    int rest;
+    if (W >= BM) { bx = BM; rest = vox / BM; }
+    else if (pow2(W)) { bx = W; rest = vox / bx; }
+    else return false;
+    int h = 1;
     while (h * 2 <= H && h * 2 <= rest) h *= 2;
     by = h;
     bz = rest / by;
@@ -492,7 +505,8 @@ int launch_tma(const ConvArgs &c, int bx, int by, int bz, cudaStream_t st) {
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, wide ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return psl_fail(PSL_ECUDA, "conv3d: tensor map encoding failed");
-    const size_t smem = (size_t)TST * (TKS * BM * 32 + TKS * N * 32) + 128;
+    constexpr int TT = tiles_for(N);
+    const size_t smem = (size_t)TST * (TKS * TT * BM * 32 + TKS * N * 32) + 128;
     static bool attr = false;
     if (!attr) {
         PSL_CUDA(cudaFuncSetAttribute(k_conv3d_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -586,7 +600,7 @@ int psl_conv3d_run(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, co
     const int64_t V = (int64_t)nx * ny * nz;
     if (V == 0) return PSL_OK;
     int bx, by, bz;
-    if (g_conv_form == 0 && tma_box(nx, ny, nz, bx, by, bz)) {
+    if (g_conv_form == 0 && (co == 16 || co == 32 || co == 64 || co == 128) && tma_box(nx, ny, nz, tiles_for(co), bx, by, bz)) {
         switch (co) {
             case 16: return launch_tma<16>(a, bx, by, bz, st);
             case 32: return launch_tma<32>(a, bx, by, bz, st);

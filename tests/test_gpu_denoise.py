@@ -120,12 +120,19 @@ def test_fresh_network_is_the_identity_and_training_reduces_the_loss():
     d.forward(dg, rg, n, n, n, 1.0, out)
     # zero output layer: out = dose, up to the BF16 rounding of the input
     assert np.allclose(out.cpu().numpy(), dose, rtol=2 ** -8, atol=1e-6)
+    # training from a non-trivial output layer (from the identity start only
+    # the output layer has a gradient and Adam's first steps follow the signs
+    # of near-zero values, which depend on the order of FP32 atomics)
+    p = torch.empty(capi.Denoiser.param_count(), device="cuda")
+    d.params(get=p)
+    p[-17:-1] = 0.1
+    d.params(set=p)
     losses = []
-    for it in range(60):
+    for it in range(40):
         losses.append(d.backward(dg, rg, tg, n, n, n, 1.0))
         d.step(2e-3)
-    # (measured: 0.0061 -> 0.0042 in 60 steps of 2e-3 from the identity start)
-    assert losses[-1] < 0.8 * losses[0], (losses[0], losses[-1])
+    # (measured: 0.33 -> 0.0065 after 10 steps, 0.0064 after 40)
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
     assert all(np.isfinite(losses))
     d.close()
 
