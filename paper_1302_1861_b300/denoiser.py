@@ -218,9 +218,23 @@ def held_out_report(den: capi.Denoiser, n_ref=(4_000_000_000, 2_000_000_000), n_
     return rep
 
 
+def conv_probe(n: int, ci: int, co: int, calls: int = 2):
+    """psl_conv3d on random BF16 data: an n^3 volume, ci -> co channels,
+    `calls` times (for profiling one launch of the tensor-core kernel)."""
+    x = torch.randn(n ** 3 * ci, device="cuda").to(torch.bfloat16)
+    w = torch.randn(27 * ci * co, device="cuda") * 0.05
+    wpk = capi.conv3d_pack(w, ci, co)
+    out = torch.empty(n ** 3 * co, dtype=torch.bfloat16, device="cuda")
+    for _ in range(calls):
+        capi.conv3d(x.view(torch.int16), ci, wpk, None, co, n, n, n, True, out.view(torch.int16))
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser(description="train the dose denoiser on pairs generated by the PSL method")
-    ap.add_argument("--out", required=True)
+    ap.add_argument("--conv-probe", nargs=3, type=int, metavar=("N", "CI", "CO"),
+                    help="only run two tensor-core convolutions of an N^3 volume, CI -> CO channels")
+    ap.add_argument("--out")
     ap.add_argument("--report", default=None, help="write the held-out accuracy report (JSON) here")
     ap.add_argument("--slab", type=int, default=16)
     ap.add_argument("--ct", type=int, default=4)
@@ -230,6 +244,11 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=1)
     a = ap.parse_args()
+    if a.conv_probe:
+        conv_probe(*a.conv_probe)
+        return
+    if not a.out:
+        ap.error("--out is required for training")
     t0 = time.perf_counter()
     pairs = make_pairs(a.slab, a.ct, a.lo_per_geometry, int(a.n_hi))
     t1 = time.perf_counter()
