@@ -346,8 +346,10 @@ PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64
 PSL_API int psl_tally_create(const psl_phantom_t *phantom, int32_t n_batches, psl_tally_t **out);
 PSL_API int psl_tally_reset(psl_tally_t *tally, void *stream);
 
-/* Copy raw tallies (device int64 [n_batches * nvox]) and ledger (device int64
- * [12]) out; NULL to skip. */
+/* Copy raw tallies (device int64 [n_batches][nvox]: batch b's voxels at
+ * b * nvox) and ledger (device int64 [12]) out; NULL to skip.  (Inside the
+ * tally the batches of a voxel are adjacent, so that a deposit's cache line
+ * serves all batches; this call lays them out batch by batch.) */
 PSL_API int psl_tally_read(const psl_tally_t *tally, int64_t *tallies, int64_t *ledger, void *stream);
 
 /* Sec. 2.3.3.  Transport every particle of the batch and its secondaries

@@ -70,7 +70,7 @@ struct Args {
     uint32_t k0, k1;          // the seed's two words (Philox key)
     uint32_t rk[20];          // Philox key schedule of the seed
     Tables tab;
-    unsigned long long *tally;  // slice 0 of the tally; a history's slice is in its root word
+    unsigned long long *tally;  // [voxel][slice] (a history's slice is in its root word)
     int64_t nvox;
     uint32_t n_slices;
     unsigned long long *ledger;
@@ -203,7 +203,7 @@ __device__ __forceinline__ unsigned long long fixed_point(float e, float wt) {
 __device__ __forceinline__ void deposit(const Args &A, Acc &acc, int64_t iv, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
     if (!q) return;
-    atomicAdd(&A.tally[(int64_t)(root >> ROOT_SLICE_SHIFT) * A.nvox + iv], q);
+    atomicAdd(&A.tally[iv * A.n_slices + (root >> ROOT_SLICE_SHIFT)], q);
     acc.dep += q;
     acc.atomics++;
     if (A.hist_dep) atomicAdd(&A.hist_dep[root & ROOT_INDEX_MASK], q);
