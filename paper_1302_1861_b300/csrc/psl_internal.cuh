@@ -205,6 +205,18 @@ struct Rng {
         ++draw;
         return ((float)(r >> 9) + 0.5f) * (1.0f / 8388608.0f);
     }
+    // compute the block of an aligned draw index ahead of its draws, at one
+    // program point for every lane; take() then reads words of that block
+    // (at most 4 takes per fill; next() continues correctly afterwards)
+    __device__ __forceinline__ void fill(const uint32_t *rk, uint32_t p0, uint32_t p1) {
+        blk = philox10_rk(draw >> 2, TAG_PARTICLE, p0, p1, rk);
+    }
+    __device__ __forceinline__ float take() {
+        uint32_t w = draw & 3u;
+        uint32_t r = w == 0 ? blk.a : (w == 1 ? blk.b : (w == 2 ? blk.c : blk.d));
+        ++draw;
+        return ((float)(r >> 9) + 0.5f) * (1.0f / 8388608.0f);
+    }
 };
 
 // Tally slice of history (p0, p1) among nb (Sec. 2.3.3 batches): the first

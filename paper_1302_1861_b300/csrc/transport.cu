@@ -39,6 +39,15 @@ constexpr float F_TWO_PI = 6.28318530717958647692f;
 constexpr int MAX_E_STEPS = 100000;
 constexpr int MAX_GEN = 64;
 constexpr unsigned FULL = 0xFFFFFFFFu;
+#ifndef PSL_BAND_DESC
+#define PSL_BAND_DESC 1
+#endif
+#ifndef PSL_G_DEFER
+#define PSL_G_DEFER 24                 // lanes with a pending real photon interaction before a warp runs them
+#endif
+#ifndef PSL_E_DEFER
+#define PSL_E_DEFER 4                  // lanes with a pending hard event before a warp runs them
+#endif
 #ifndef PSL_TRANSPORT_MIN_BLOCKS
 #define PSL_TRANSPORT_MIN_BLOCKS 4     // resident 256-thread blocks per SM (register cap 64)
 #endif
@@ -412,6 +421,7 @@ struct Photon {
     float mumax, inv_mumax;
     int ti;
     float tf;
+    uint32_t chan;             // channel of a drawn real interaction: 0 Compton, 1 photoelectric, 2 pair
 };
 
 __device__ __forceinline__ void photon_energy(const Args &A, Photon &g) {
@@ -420,8 +430,18 @@ __device__ __forceinline__ void photon_energy(const Args &A, Photon &g) {
     g.inv_mumax = __frcp_rn(g.mumax);
 }
 
-// one Woodcock step (+ interaction); returns false when the photon ends
-__device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g) {
+// One Woodcock step.  Returns G_END when the photon leaves the phantom,
+// G_ON after a virtual interaction, G_REAL when a real interaction was drawn
+// (its channel in g.chan; photon_interact() runs it and the caller may
+// defer it).
+enum { G_END = 0, G_ON = 1, G_REAL = 2 };
+
+__device__ __forceinline__ int64_t photon_voxel(const Args &A, const Photon &g) {
+    const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
+    return ((int64_t)fz * A.ny + (int64_t)fy) * A.nx + (int64_t)fx;
+}
+
+__device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
     acc.wsteps++;
     g.rng.align();                                                // Woodcock step: step, virtual, channel
     const float s = -__logf(g.rng.next(A.rk, g.p0, g.p1)) * g.inv_mumax;
@@ -429,7 +449,7 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
     const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
     if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)A.nx && fy < (float)A.ny && fz < (float)A.nz)) {
         escape(A, acc, g.e, g.wt, g.root);
-        return false;
+        return G_END;
     }
     const int64_t iv = ((int64_t)fz * A.ny + (int64_t)fy) * A.nx + (int64_t)fx;
     const float mr = __ldg(A.mrho + iv);
@@ -438,12 +458,19 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
     const float mc = rho * c.x, mpe = rho * c.y, mpp = rho * c.z;
     const float mu = mc + mpe + mpp;
     if (mu > g.mumax) atomicOr(A.err, 8u);
-    if (g.rng.next(A.rk, g.p0, g.p1) * g.mumax >= mu) return true;           // virtual interaction
+    if (g.rng.next(A.rk, g.p0, g.p1) * g.mumax >= mu) return G_ON;          // virtual interaction
     count_event(A, g.root);
     const float r = g.rng.next(A.rk, g.p0, g.p1) * mu;
+    g.chan = r < mc ? 0u : (r < mc + mpe ? 1u : 2u);
+    return G_REAL;
+}
+
+// the real interaction drawn by the last step; returns false when the photon ends
+__device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon &g) {
+    const int64_t iv = photon_voxel(A, g);
     g.rng.align();                                                // the interaction's draws
     const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
-    if (r < mc) {                                                 // Compton (Kahn's method)
+    if (g.chan == 0u) {                                           // Compton (Kahn's method)
         acc.compton++;
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         const float k = g.e * (1.0f / F_ME), ik = __frcp_rn(k);
@@ -475,7 +502,7 @@ __device__ __forceinline__ bool photon_event(const Args &A, Acc &acc, Photon &g)
         if (g.e < A.pcut) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         photon_energy(A, g);
         return true;
-    } else if (r < mc + mpe) {                                    // photoelectric
+    } else if (g.chan == 1u) {                                    // photoelectric
         acc.photo++;
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         emit_charged(A, acc, g.rng, 1, g.e, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
@@ -500,7 +527,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
     Photon g;
     Feed F;
     F.init(sm, src, n, head, A.err);
-    bool alive = false, done = false;
+    bool alive = false, done = false, real = false;
     for (;;) {
         const unsigned need = __ballot_sync(FULL, !alive && !done);
         if (need) {
@@ -519,8 +546,20 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
                 }
             }
         }
-        if (!__any_sync(FULL, alive)) break;
-        if (alive) alive = photon_event(A, acc, g);
+        const unsigned live = __ballot_sync(FULL, alive);
+        if (!live) break;
+        // Real interactions wait until enough lanes have one (or every live
+        // lane waits), so that the interaction code runs with most lanes
+        // active; the other lanes keep taking Woodcock steps meanwhile.
+        const unsigned rm = __ballot_sync(FULL, real);
+        if (rm && (__popc(rm) >= PSL_G_DEFER || rm == live)) {
+            if (real) { alive = photon_interact(A, acc, g); real = false; }
+        }
+        if (alive && !real) {
+            const int r = photon_step(A, acc, g);
+            alive = r != G_END;
+            real = r == G_REAL;
+        }
     }
     flush_acc(A, acc, 8);
 }
@@ -579,18 +618,23 @@ __device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &
     }
 }
 
-// one condensed-history step (+ hard event); returns false when the electron ends
-__device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron &s) {
+// One condensed-history step.  Returns E_END when the electron ends,
+// E_HARD when the step ends at a hard event (electron_hard() runs it; the
+// caller may defer it), E_ON otherwise.
+enum { E_END = 0, E_ON = 1, E_HARD = 2 };
+
+__device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &s) {
     const int64_t iv = ((int64_t)s.iz * A.ny + s.iy) * A.nx + s.ix;
     if (s.t <= A.ecut || ++s.steps > MAX_E_STEPS) {
         if (s.steps > MAX_E_STEPS) atomicOr(A.err, PSL_DEV_ERR_STEPS);
         electron_end(A, acc, s, iv);
-        return false;
+        return E_END;
     }
     acc.steps++;
     count_event(A, s.root);
-    s.rng.align();                                                // the step's draws
-    if (s.nlam < 0.0f) s.nlam = -__logf(s.rng.next(A.rk, s.p0, s.p1));   // a new mean free path count
+    s.rng.align();                                                // the step's draws (at most 3)
+    s.rng.fill(A.rk, s.p0, s.p1);
+    if (s.nlam < 0.0f) s.nlam = -__logf(s.rng.take());           // a new mean free path count
     const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
     const float rho = fabsf(__ldg(A.mrho + iv));
     int ti; float tf;
@@ -631,9 +675,9 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
     s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
     s.nlam -= step * sig;
     if (!(A.flags & PSL_PHYS_NO_MSC) && step > 0.0f) {
-        const float l2 = -2.0f * __logf(s.rng.next(A.rk, s.p0, s.p1));
+        const float l2 = -2.0f * __logf(s.rng.take());
         const float th = th0 * (l2 * rsqrtf(l2));
-        const float phi = F_TWO_PI * s.rng.next(A.rk, s.p0, s.p1);
+        const float phi = F_TWO_PI * s.rng.take();
         rotate_dir(s.u, s.v, s.w, __cosf(th), phi);
     }
     if (which == 1) {
@@ -643,9 +687,17 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
         else { s.z = (float)(cross > 0 ? s.iz + 1 : s.iz) * A.vz; s.iz += cross; out = s.iz < 0 || s.iz >= A.nz; }
         if (out) {
             escape(A, acc, s.t + (s.pos ? 2.0f * F_ME : 0.0f), s.wt, s.root);
-            return false;
+            return E_END;
         }
-    } else if (which == 0) {
+    }
+    return which == 0 ? E_HARD : E_ON;
+}
+
+// the hard event (Moller delta ray or bremsstrahlung photon) that ended the
+// last step; the electron stays in the voxel of that step
+__device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron &s) {
+    const int64_t iv = ((int64_t)s.iz * A.ny + s.iy) * A.nx + s.ix;
+    {
         int tj; float tg;
         tab_pos(A.tab, s.t, tj, tg);
         const float4 e2 = lerp4(A.tab.el, tj, tg);
@@ -673,7 +725,6 @@ __device__ __forceinline__ bool electron_event(const Args &A, Acc &acc, Electron
         }
         s.nlam = -1.0f;                                           // drawn at the next step
     }
-    return true;
 }
 
 __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
@@ -685,7 +736,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
     const unsigned lt = (1u << lane) - 1u;
     Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     Electron s;
-    bool alive = false, done = false;
+    bool alive = false, done = false, hard = false;
     for (;;) {
         const unsigned need = __ballot_sync(FULL, !alive && !done);
         if (need) {
@@ -711,8 +762,20 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                 }
             }
         }
-        if (!__any_sync(FULL, alive)) break;
-        if (alive) alive = electron_event(A, acc, s);
+        const unsigned live = __ballot_sync(FULL, alive);
+        if (!live) break;
+        // Hard events wait until enough lanes have one (or every live lane
+        // waits), so that the long hard-event code runs with most lanes
+        // active; the other lanes keep stepping meanwhile.
+        const unsigned hm = __ballot_sync(FULL, hard);
+        if (hm && (__popc(hm) >= PSL_E_DEFER || hm == live)) {
+            if (hard) { electron_hard(A, acc, s); hard = false; }
+        }
+        if (alive && !hard) {
+            const int r = electron_step(A, acc, s);
+            alive = r != E_END;
+            hard = r == E_HARD;
+        }
     }
     flush_acc(A, acc, 9);
 }
@@ -799,14 +862,21 @@ __global__ void __launch_bounds__(256) k_band_count(Args A, const Particle *a, u
 
 __global__ void k_band_scan(uint32_t *hist, uint32_t *cursor, uint32_t *out_count) {
     const int t = threadIdx.x;                  // one warp
-    uint32_t v = hist[t], x = v;
+#if PSL_BAND_DESC
+    // highest band first: the longest-lived electrons start first and the
+    // short ones fill the lanes at the end of the pass
+    const int b = NBANDS - 1 - t;
+#else
+    const int b = t;
+#endif
+    uint32_t v = hist[b], x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(FULL, x, o);
         if (t >= o) x += y;
     }
-    cursor[t] = x - v;
-    hist[t] = 0;
+    cursor[b] = x - v;
+    hist[b] = 0;
     if (t == 31) *out_count = x;
 }
 
