@@ -282,20 +282,21 @@ def _literal_group(plan: Plan, g: int):
     return plan._literal[g]
 
 
-def _group_lookup(plan: Plan, g: int, hl: int):
-    """(entry, use) of the hl-th history of group g: the round is the largest
-    r with sum_e min(count_e, r) <= hl."""
+def _group_lookup(plan: Plan, g: int, hl: np.ndarray):
+    """(entry, use) of the hl-th histories of group g: the round is the
+    largest r with F(r) = sum_e min(count_e, r) <= hl, and the history is
+    the (hl - F(r))-th entry visited in that round (the visiting order puts
+    the entries that still have histories first).  F is tabulated for every
+    round r = 0 .. max count and searched for all hl at once."""
     o = plan.group_order[g]
     c = plan.count[o]
-    lo, hi = 0, int(c.max())
-    while hi - lo > 1:
-        mid = (lo + hi) // 2
-        if int(np.minimum(c, mid).sum()) <= hl:
-            lo = mid
-        else:
-            hi = mid
-    p = hl - int(np.minimum(c, lo).sum())
-    return int(o[p]), lo
+    cs = np.sort(c)
+    r = np.arange(int(c.max()) + 1, dtype=np.int64)
+    k = np.searchsorted(cs, r, side="left")          # entries with count < r
+    below = np.concatenate([[0], np.cumsum(cs)])
+    F = below[k] + r * (len(cs) - k)
+    rnd = np.searchsorted(F, hl, side="right") - 1
+    return o[hl - F[rnd]].astype(np.int64), rnd
 
 
 def history_map(plan: Plan, h: np.ndarray, literal_limit: int = 4_000_000):
@@ -312,9 +313,7 @@ def history_map(plan: Plan, h: np.ndarray, literal_limit: int = 4_000_000):
             ent, k = _literal_group(plan, int(gg))
             entry[m], use[m] = ent[hl], k[hl]
         else:
-            r = [_group_lookup(plan, int(gg), int(x)) for x in hl]
-            entry[m] = [a for a, _ in r]
-            use[m] = [b for _, b in r]
+            entry[m], use[m] = _group_lookup(plan, int(gg), hl)
     return entry, use
 
 
