@@ -342,7 +342,9 @@ PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64
  * 0 emitted, 1 escaped, 2 deposited (fixed point, 2^-32 MeV per unit
  * weight), 3 Compton, 4 photoelectric and 5 pair events, 6 electron steps,
  * 7 errors, 8 tally atomics issued by photon passes, 9 by electron passes,
- * 10 Woodcock (photon) steps, 11 reserved. */
+ * 10 Woodcock (photon) steps, 11 reserved.  The phantom must have fewer
+ * than 2^31 voxels (PSL_EINVAL otherwise): transport indexes voxels in
+ * 32 bits. */
 PSL_API int psl_tally_create(const psl_phantom_t *phantom, int32_t n_batches, psl_tally_t **out);
 PSL_API int psl_tally_reset(psl_tally_t *tally, void *stream);
 

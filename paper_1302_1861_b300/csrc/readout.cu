@@ -64,6 +64,8 @@ __global__ void k_ledger_out(const unsigned long long *ledger, const unsigned lo
 extern "C" int psl_tally_create(const psl_phantom_t *ph, int32_t n_batches, psl_tally_t **out) {
     if (!ph || !out || n_batches <= 0 || n_batches > PSL_MAX_BATCHES || ph->nx <= 0 || ph->ny <= 0 || ph->nz <= 0)
         return psl_fail(PSL_EINVAL, "psl_tally_create: bad argument");
+    if ((int64_t)ph->nx * ph->ny * ph->nz >= (int64_t)1 << 31)
+        return psl_fail(PSL_EINVAL, "psl_tally_create: the phantom must have fewer than 2^31 voxels");
     *out = nullptr;
     psl_tally *t = new psl_tally();
     t->nx = ph->nx; t->ny = ph->ny; t->nz = ph->nz; t->n_batches = n_batches;

@@ -35,7 +35,6 @@ constexpr int NT = 2048;                  // table nodes
 constexpr double T_LO = 1.0e-3, T_HI = 30.0;
 constexpr int NBANDS = 32;
 constexpr float F_ME = 0.51099895f;
-constexpr float F_TWO_PI = 6.28318530717958647692f;
 constexpr int MAX_E_STEPS = 100000;
 constexpr int MAX_GEN = 64;
 constexpr unsigned FULL = 0xFFFFFFFFu;
@@ -57,7 +56,6 @@ struct Tables {
     const float4 *el;          // S_restricted (MeV cm^2/g), sigma_moller, sigma_brem (cm^2/g), 0
     const float2 *rng;         // CSDA range R (g/cm^2) and dR/dlnT * dlnT at each node
     const float *irng;         // ln T at uniform steps of ln R (inverse range)
-    const float *mumax;        // majorant (1/cm), phantom dependent
     float lnE0, inv_dln;
     float lnR0, inv_dlnR;      // grid of the inverse range table
 };
@@ -73,6 +71,7 @@ struct Args {
     const uint8_t *mat;
     const float *rho;
     const float *mrho;        // rho, negated for bone (one load per lookup)
+    const int *rmax;          // largest density of each material (float bits), phantom dependent
     float pcut, ecut, wcc, wcb;
     uint32_t flags;
     uint64_t seed;
@@ -166,14 +165,6 @@ __global__ void k_rho_max(const uint8_t *mat, const float *rho, int64_t n, int *
     if (threadIdx.x < 2) atomicMax(&out[threadIdx.x], m[threadIdx.x]);
 }
 
-__global__ void k_majorant(const float4 *ph0, const float4 *ph1, const int *rmax, float *mumax) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= NT) return;
-    float r0 = __int_as_float(rmax[0]), r1 = __int_as_float(rmax[1]);
-    // 1e-6 relative head-room over the interpolated material coefficients
-    mumax[i] = fmaxf(r0 * ph0[i].w, r1 * ph1[i].w) * 1.000001f;
-}
-
 __device__ __forceinline__ void tab_pos(const Tables &T, float E, int &i, float &f) {
     float x = (__logf(E) - T.lnE0) * T.inv_dln;
     x = fminf(fmaxf(x, 0.0f), (float)(NT - 1) - 1e-3f);
@@ -184,11 +175,6 @@ __device__ __forceinline__ void tab_pos(const Tables &T, float E, int &i, float 
 __device__ __forceinline__ float4 lerp4(const float4 *a, int i, float f) {
     float4 p = __ldg(a + i), q = __ldg(a + i + 1);
     return make_float4(p.x + f * (q.x - p.x), p.y + f * (q.y - p.y), p.z + f * (q.z - p.z), p.w + f * (q.w - p.w));
-}
-
-__device__ __forceinline__ float lerp1(const float *a, int i, float f) {
-    float p = __ldg(a + i), q = __ldg(a + i + 1);
-    return p + f * (q - p);
 }
 
 // R(E): cubic Hermite in ln E with the exact node derivatives dR/dlnE = E/S
@@ -209,10 +195,10 @@ __device__ __forceinline__ unsigned long long fixed_point(float e, float wt) {
     return (unsigned long long)__float2ll_rn(__fmul_rn(e, wt) * 4294967296.0f);
 }
 
-__device__ __forceinline__ void deposit(const Args &A, Acc &acc, int64_t iv, float e, float wt, uint32_t root) {
+__device__ __forceinline__ void deposit(const Args &A, Acc &acc, uint32_t iv, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
     if (!q) return;
-    atomicAdd(&A.tally[iv * A.n_slices + (root >> ROOT_SLICE_SHIFT)], q);
+    atomicAdd(&A.tally[(uint64_t)iv * A.n_slices + (root >> ROOT_SLICE_SHIFT)], q);
     acc.dep += q;
     acc.atomics++;
     if (A.hist_dep) atomicAdd(&A.hist_dep[root & ROOT_INDEX_MASK], q);
@@ -228,15 +214,24 @@ __device__ __forceinline__ void count_event(const Args &A, uint32_t root) {
     if (A.hist_events) atomicAdd(&A.hist_events[root & ROOT_INDEX_MASK], 1);
 }
 
-// rotate unit direction by polar cosine c and azimuth phi (renormalised)
-__device__ __forceinline__ void rotate_dir(float &u, float &v, float &w, float c, float phi) {
-    float st = sqrtf(fmaxf(0.0f, 1.0f - c * c)), sp, cp;
-    __sincosf(phi, &sp, &cp);
+// Angles are evaluated so that FP32 keeps their small parts: the sine of a
+// polar angle comes from a form without cancellation (never sqrt(1 - c^2)
+// near c = 1), the azimuth 2 pi xi through sincospif, logarithms of
+// uniforms through logf (a uniform near 1 has a small logarithm that the
+// fast intrinsic only gets to an absolute error), and 1 - w^2 of a
+// direction as u^2 + v^2.  Trajectories then follow the FP64 ones longer.
+__device__ __forceinline__ float ln_uniform(float xi) { return logf(xi); }
+__device__ __forceinline__ void sincos_2pi(float xi, float *s, float *c) { sincospif(2.0f * xi, s, c); }
+
+// rotate unit direction by the polar angle (cosine c, sine st >= 0) and the
+// azimuth (sine sp, cosine cp); renormalised
+__device__ __forceinline__ void rotate_dir(float &u, float &v, float &w, float c, float st, float sp, float cp) {
     float nu, nv, nw;
     if (fabsf(w) > 0.99999f) {
         nu = st * cp; nv = st * sp; nw = w > 0.0f ? c : -c;
     } else {
-        const float it = rsqrtf(1.0f - w * w), t = (1.0f - w * w) * it;
+        const float s2 = u * u + v * v;                           // 1 - w^2 without cancellation
+        const float it = rsqrtf(s2), t = s2 * it;
         nu = u * c + st * (u * w * cp - v * sp) * it;
         nv = v * c + st * (v * w * cp + u * sp) * it;
         nw = w * c - st * cp * t;
@@ -258,9 +253,10 @@ __device__ __forceinline__ void push_particle(const Queue &q, const Args &A, uin
 __device__ __forceinline__ void annihilate(const Args &A, Rng &rng, float x, float y, float z, float wt, uint32_t p0, uint32_t p1,
                            uint32_t &nchild, uint32_t root) {
     rng.align();
-    float cth = 2.0f * rng.next(A.rk, p0, p1) - 1.0f, phi = F_TWO_PI * rng.next(A.rk, p0, p1);
-    float sth = sqrtf(fmaxf(0.0f, 1.0f - cth * cth)), sp, cp;
-    __sincosf(phi, &sp, &cp);
+    const float xi = rng.next(A.rk, p0, p1);
+    float cth = 2.0f * xi - 1.0f, sp, cp;
+    float sth = 2.0f * sqrtf(fmaxf(0.0f, xi * (1.0f - xi)));     // sqrt(1 - cth^2)
+    sincos_2pi(rng.next(A.rk, p0, p1), &sp, &cp);
     float a0 = sth * cp, a1 = sth * sp, a2 = cth;
     push_particle(A.p_out, A, 0, x, y, z, a0, a1, a2, F_ME, wt, p0, p1, nchild, root);
     push_particle(A.p_out, A, 0, x, y, z, -a0, -a1, -a2, F_ME, wt, p0, p1, nchild, root);
@@ -268,7 +264,7 @@ __device__ __forceinline__ void annihilate(const Args &A, Rng &rng, float x, flo
 
 // a charged secondary: queued for transport, or deposited in place
 __device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, uint32_t type, float T, float x, float y, float z,
-                             float u, float v, float w, float wt, int64_t iv, uint32_t p0, uint32_t p1, uint32_t &nchild,
+                             float u, float v, float w, float wt, uint32_t iv, uint32_t p0, uint32_t p1, uint32_t &nchild,
                              uint32_t root) {
     if (T > A.ecut && !(A.flags & PSL_PHYS_LOCAL_SECONDARIES)) {
         push_particle(A.e_out, A, type, x, y, z, u, v, w, T, wt, p0, p1, nchild, root);
@@ -424,9 +420,19 @@ struct Photon {
     uint32_t chan;             // channel of a drawn real interaction: 0 Compton, 1 photoelectric, 2 pair
 };
 
+// Table position and Woodcock majorant at the photon's energy: the largest
+// attenuation coefficient any voxel can have, max over the materials of
+// (largest density of the material) x (its coefficients), summed without
+// contraction in the order photon_step sums a voxel's, so that no voxel's
+// coefficient exceeds it (rounding is monotone) and none is given headroom.
+__device__ __forceinline__ float mu_of(float rho, const float4 &c) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(rho, c.x), __fmul_rn(rho, c.y)), __fmul_rn(rho, c.z));
+}
+
 __device__ __forceinline__ void photon_energy(const Args &A, Photon &g) {
     tab_pos(A.tab, g.e, g.ti, g.tf);
-    g.mumax = lerp1(A.tab.mumax, g.ti, g.tf);
+    const float r0 = __int_as_float(__ldg(A.rmax)), r1 = __int_as_float(__ldg(A.rmax + 1));
+    g.mumax = fmaxf(mu_of(r0, lerp4(A.tab.ph0, g.ti, g.tf)), mu_of(r1, lerp4(A.tab.ph1, g.ti, g.tf)));
     g.inv_mumax = __frcp_rn(g.mumax);
 }
 
@@ -436,27 +442,27 @@ __device__ __forceinline__ void photon_energy(const Args &A, Photon &g) {
 // defer it).
 enum { G_END = 0, G_ON = 1, G_REAL = 2 };
 
-__device__ __forceinline__ int64_t photon_voxel(const Args &A, const Photon &g) {
+__device__ __forceinline__ uint32_t photon_voxel(const Args &A, const Photon &g) {
     const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
-    return ((int64_t)fz * A.ny + (int64_t)fy) * A.nx + (int64_t)fx;
+    return ((uint32_t)fz * (uint32_t)A.ny + (uint32_t)fy) * (uint32_t)A.nx + (uint32_t)fx;
 }
 
 __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
     acc.wsteps++;
     g.rng.align();                                                // Woodcock step: step, virtual, channel
-    const float s = -__logf(g.rng.next(A.rk, g.p0, g.p1)) * g.inv_mumax;
+    const float s = -ln_uniform(g.rng.next(A.rk, g.p0, g.p1)) * g.inv_mumax;
     g.x += s * g.u; g.y += s * g.v; g.z += s * g.w;
     const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
     if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)A.nx && fy < (float)A.ny && fz < (float)A.nz)) {
         escape(A, acc, g.e, g.wt, g.root);
         return G_END;
     }
-    const int64_t iv = ((int64_t)fz * A.ny + (int64_t)fy) * A.nx + (int64_t)fx;
+    const uint32_t iv = ((uint32_t)fz * (uint32_t)A.ny + (uint32_t)fy) * (uint32_t)A.nx + (uint32_t)fx;
     const float mr = __ldg(A.mrho + iv);
     const float rho = fabsf(mr);
     const float4 c = lerp4(mr < 0.0f ? A.tab.ph1 : A.tab.ph0, g.ti, g.tf);
-    const float mc = rho * c.x, mpe = rho * c.y, mpp = rho * c.z;
-    const float mu = mc + mpe + mpp;
+    const float mc = __fmul_rn(rho, c.x), mpe = __fmul_rn(rho, c.y), mpp = __fmul_rn(rho, c.z);
+    const float mu = __fadd_rn(__fadd_rn(mc, mpe), mpp);          // = mu_of(rho, c)
     if (mu > g.mumax) atomicOr(A.err, 8u);
     if (g.rng.next(A.rk, g.p0, g.p1) * g.mumax >= mu) return G_ON;          // virtual interaction
     count_event(A, g.root);
@@ -467,7 +473,7 @@ __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
 
 // the real interaction drawn by the last step; returns false when the photon ends
 __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon &g) {
-    const int64_t iv = photon_voxel(A, g);
+    const uint32_t iv = photon_voxel(A, g);
     g.rng.align();                                                // the interaction's draws
     const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
     if (g.chan == 0u) {                                           // Compton (Kahn's method)
@@ -489,10 +495,13 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
                 if (r3 <= 0.5f * (cc * cc + ix)) break;
             }
         }
-        const float cth = fminf(1.0f, fmaxf(-1.0f, 1.0f - (x - 1.0f) * ik));
-        const float ep = g.e * ix, phi = F_TWO_PI * g.rng.next(A.rk, g.p0, g.p1);
+        const float dc = fminf(2.0f, fmaxf(0.0f, (x - 1.0f) * ik));   // 1 - cos(theta)
+        const float cth = 1.0f - dc, sth = sqrtf(dc * (2.0f - dc));
+        const float ep = g.e * ix;
+        float sp, cp;
+        sincos_2pi(g.rng.next(A.rk, g.p0, g.p1), &sp, &cp);
         float nu = g.u, nv = g.v, nw = g.w;
-        rotate_dir(nu, nv, nw, cth, phi);
+        rotate_dir(nu, nv, nw, cth, sth, sp, cp);
         const float te = g.e - ep;
         float du = g.e * g.u - ep * nu, dv = g.e * g.v - ep * nv, dw = g.e * g.w - ep * nw;
         const float nn2 = du * du + dv * dv + dw * dw;
@@ -567,6 +576,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
 // ----------------------------------------------------------- electrons ---
 struct Electron {
     float x, y, z, u, v, w, t, wt, nlam;
+    float r;                   // CSDA range at t (g/cm^2), carried from step to step
     int ix, iy, iz;
     uint32_t p0, p1, root, nchild;
     int steps;
@@ -583,14 +593,27 @@ __device__ __forceinline__ float highland(float T, float s, float rho) {
     return __fdividef(13.6f, bcp) * (t * rsqrtf(t)) * f;
 }
 
-// energy whose CSDA range is r (g/cm^2): the inverse range table
+// energy whose CSDA range is r (g/cm^2): ln T from the inverse range table,
+// then one Newton step on the forward (Hermite) range, so that the range of
+// the result is r to float precision (a step of zero length keeps T)
 __device__ __forceinline__ float energy_of_range(const Tables &T, float r) {
     float x = (__logf(r) - T.lnR0) * T.inv_dlnR;
     x = fminf(fmaxf(x, 0.0f), (float)(NT - 1) - 1e-3f);
     const int i = (int)x;
     const float f = x - (float)i;
     const float a = __ldg(T.irng + i), b = __ldg(T.irng + i + 1);
-    return __expf(a + f * (b - a));
+    const float lt0 = a + f * (b - a);
+    // forward table position of ln T0 and the Hermite range with its slope
+    float xf = (lt0 - T.lnE0) * T.inv_dln;
+    xf = fminf(fmaxf(xf, 0.0f), (float)(NT - 1) - 1e-3f);
+    const int j = (int)xf;
+    const float g = xf - (float)j;
+    const float2 p = __ldg(T.rng + j), q = __ldg(T.rng + j + 1);
+    const float g2 = g * g, g3 = g2 * g;
+    const float rg = (2.f * g3 - 3.f * g2 + 1.f) * p.x + (g3 - 2.f * g2 + g) * p.y + (3.f * g2 - 2.f * g3) * q.x + (g3 - g2) * q.y;
+    const float dr = (6.f * g2 - 6.f * g) * p.x + (3.f * g2 - 4.f * g + 1.f) * p.y + (6.f * g - 6.f * g2) * q.x + (3.f * g2 - 2.f * g) * q.y;
+    const float g1 = dr > 0.0f ? g + __fdividef(r - rg, dr) : g;
+    return expf(T.lnE0 + ((float)j + g1) * __frcp_rn(T.inv_dln));
 }
 
 __device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, const uint32_t *rk, uint32_t p0,
@@ -610,7 +633,7 @@ __device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, con
     return ec;
 }
 
-__device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &s, int64_t iv) {
+__device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &s, uint32_t iv) {
     deposit(A, acc, iv, s.t, s.wt, s.root);
     if (s.pos) {
         if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) deposit(A, acc, iv, 2.0f * F_ME, s.wt, s.root);
@@ -624,7 +647,7 @@ __device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &
 enum { E_END = 0, E_ON = 1, E_HARD = 2 };
 
 __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &s) {
-    const int64_t iv = ((int64_t)s.iz * A.ny + s.iy) * A.nx + s.ix;
+    const uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
     if (s.t <= A.ecut || ++s.steps > MAX_E_STEPS) {
         if (s.steps > MAX_E_STEPS) atomicOr(A.err, PSL_DEV_ERR_STEPS);
         electron_end(A, acc, s, iv);
@@ -634,7 +657,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
     count_event(A, s.root);
     s.rng.align();                                                // the step's draws (at most 3)
     s.rng.fill(A.rk, s.p0, s.p1);
-    if (s.nlam < 0.0f) s.nlam = -__logf(s.rng.take());           // a new mean free path count
+    if (s.nlam < 0.0f) s.nlam = -ln_uniform(s.rng.take());       // a new mean free path count
     const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
     const float rho = fabsf(__ldg(A.mrho + iv));
     int ti; float tf;
@@ -660,25 +683,32 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
         }
     }
     const float tlim = fmaxf(0.9f * s.t, A.ecut);
-    const float r_t = range_at(A.tab, ti, tf);
-    const float s_max = (r_t - range_of(A.tab, tlim)) * __frcp_rn(rho);
+    const float rlim = range_of(A.tab, tlim);
+    const float s_max = (s.r - rlim) * __frcp_rn(rho);
     int which;
     float step;
     if (s_hard <= s_bound && s_hard <= s_max) { which = 0; step = s_hard; }
     else if (s_bound <= s_max) { which = 1; step = s_bound; }
     else { which = 2; step = s_max; }
-    // energy at the end of the step: the 10 % limit exactly, else from the range
-    float tend = which == 2 ? tlim : fmaxf(energy_of_range(A.tab, r_t - rho * step), tlim);
+    // energy at the end of the step: the 10 % limit exactly, else from the
+    // range left; the range itself is carried, not recomputed from the energy
+    float tend, rend;
+    if (which == 2) { tend = tlim; rend = rlim; }
+    else { rend = s.r - rho * step; tend = fmaxf(energy_of_range(A.tab, rend), tlim); }
     const float th0 = highland(s.t, step, rho);
     deposit(A, acc, iv, s.t - tend, s.wt, s.root);
     s.t = tend;
+    s.r = rend;
     s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
     s.nlam -= step * sig;
     if (!(A.flags & PSL_PHYS_NO_MSC) && step > 0.0f) {
-        const float l2 = -2.0f * __logf(s.rng.take());
+        const float l2 = -2.0f * ln_uniform(s.rng.take());
         const float th = th0 * (l2 * rsqrtf(l2));
-        const float phi = F_TWO_PI * s.rng.take();
-        rotate_dir(s.u, s.v, s.w, __cosf(th), phi);
+        float st, ct, sp, cp;
+        sincosf(th, &st, &ct);
+        st = fabsf(st);
+        sincos_2pi(s.rng.take(), &sp, &cp);
+        rotate_dir(s.u, s.v, s.w, ct, st, sp, cp);
     }
     if (which == 1) {
         int out = 0;
@@ -696,7 +726,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
 // the hard event (Moller delta ray or bremsstrahlung photon) that ended the
 // last step; the electron stays in the voxel of that step
 __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron &s) {
-    const int64_t iv = ((int64_t)s.iz * A.ny + s.iy) * A.nx + s.ix;
+    const uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
     {
         int tj; float tg;
         tab_pos(A.tab, s.t, tj, tg);
@@ -708,12 +738,17 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
             if (r < sm) {                                         // hard Moller
                 const float eps = sample_moller(s.t, A.wcc, s.rng, A.rk, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
+                // polar cosines of the two electrons from momentum balance;
+                // their sines from the same balance without cancellation
                 const float cp = sqrtf(tp * (s.t + 2.0f * F_ME) / (s.t * (tp + 2.0f * F_ME)));
                 const float cd = sqrtf(W * (s.t + 2.0f * F_ME) / (s.t * (W + 2.0f * F_ME)));
-                const float phi = F_TWO_PI * s.rng.next(A.rk, s.p0, s.p1);
+                const float sp_ = sqrtf(2.0f * F_ME * W / (s.t * (tp + 2.0f * F_ME)));
+                const float sd_ = sqrtf(2.0f * F_ME * tp / (s.t * (W + 2.0f * F_ME)));
+                float sph, cph;
+                sincos_2pi(s.rng.next(A.rk, s.p0, s.p1), &sph, &cph);
                 float du = s.u, dv = s.v, dw = s.w;
-                rotate_dir(du, dv, dw, cd, phi + 3.14159265358979f);
-                rotate_dir(s.u, s.v, s.w, cp, phi);
+                rotate_dir(du, dv, dw, cd, sd_, -sph, -cph);              // azimuth phi + pi
+                rotate_dir(s.u, s.v, s.w, cp, sp_, sph, cph);
                 emit_charged(A, acc, s.rng, 1, W, s.x, s.y, s.z, du, dv, dw, s.wt, iv, s.p0, s.p1, s.nchild, s.root);
                 s.t = tp;
             } else {                                              // hard bremsstrahlung
@@ -722,6 +757,7 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
                 else push_particle(A.p_out, A, 0, s.x, s.y, s.z, s.u, s.v, s.w, kph, s.wt, s.p0, s.p1, s.nchild, s.root);
                 s.t -= kph;
             }
+            s.r = range_of(A.tab, s.t);
         }
         s.nlam = -1.0f;                                           // drawn at the next step
     }
@@ -756,6 +792,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
                     s.rng.draw = 0;
                     s.nlam = -1.0f;                               // drawn at the first step
+                    s.r = range_of(A.tab, s.t);
                     alive = true;
                 } else {
                     done = true;
@@ -969,7 +1006,6 @@ struct Workspace {
     Particle *P[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr}, *S = nullptr, *Q = nullptr;
     uint32_t *cnt = nullptr;           // [0..1] P counts, [2..3] E counts, [4] S count, [5..6] heads,
                                        // [7] primary photons, [9] err, [16..47] band hist, [48..79] cursors
-    float *mumax = nullptr;
     int *rmax = nullptr;
     float *mrho = nullptr;             // packed material/density of the phantom
     int64_t nvox = 0;
@@ -986,7 +1022,6 @@ void workspace_free(Workspace *w) {
     if (w->S) cudaFree(w->S);
     if (w->Q) cudaFree(w->Q);
     if (w->cnt) cudaFree(w->cnt);
-    if (w->mumax) cudaFree(w->mumax);
     if (w->rmax) cudaFree(w->rmax);
     if (w->mrho) cudaFree(w->mrho);
     if (w->host) cudaFreeHost(w->host);
@@ -1012,7 +1047,6 @@ static int workspace_ensure(psl_tally *t, int64_t chunk) {
     PSL_CUDA(cudaMalloc((void **)&w->Q, (size_t)base * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->cnt, 128 * sizeof(uint32_t)));
     PSL_CUDA(cudaMemset(w->cnt, 0, 128 * sizeof(uint32_t)));
-    PSL_CUDA(cudaMalloc((void **)&w->mumax, NT * sizeof(float)));
     PSL_CUDA(cudaMalloc((void **)&w->rmax, 2 * sizeof(int)));
     PSL_CUDA(cudaMalloc((void **)&w->mrho, t->nvox * sizeof(float)));
     w->nvox = t->nvox;
@@ -1061,7 +1095,6 @@ struct Runner {
         const int64_t nvox = t->nvox;
         cudaMemsetAsync(w->rmax, 0, 2 * sizeof(int), st);
         k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax, w->mrho); PSL_NOTE_LAUNCH();
-        k_majorant<<<(NT + 255) / 256, 256, 0, st>>>(tc.ph0, tc.ph1, w->rmax, w->mumax); PSL_NOTE_LAUNCH();
         A.nx = ph->nx; A.ny = ph->ny; A.nz = ph->nz;
         A.vx = ph->vx; A.vy = ph->vy; A.vz = ph->vz;
         A.ivx = 1.0f / ph->vx; A.ivy = 1.0f / ph->vy; A.ivz = 1.0f / ph->vz;
@@ -1073,7 +1106,7 @@ struct Runner {
             A.rk[2 * r] = A.k0 + (uint32_t)r * 0x9E3779B9u;
             A.rk[2 * r + 1] = A.k1 + (uint32_t)r * 0xBB67AE85u;
         }
-        A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.rng = tc.rng; A.tab.mumax = w->mumax;
+        A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.rng = tc.rng; A.rmax = w->rmax;
         A.tab.irng = tc.irng; A.tab.lnR0 = tc.igrid[0]; A.tab.inv_dlnR = tc.igrid[1];
         A.tab.lnE0 = (float)log(T_LO);
         A.tab.inv_dln = (float)((NT - 1) / (log(T_HI) - log(T_LO)));
