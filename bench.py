@@ -415,9 +415,9 @@ def main():
 # / events) and DRAM bytes per history (dram__bytes_read + write).  See
 # profiles/transport_k_electron_k_photon_psl-10x10-slab64.md.  They hold for
 # the kernels they were measured on; re-measure after changing the kernels.
-THREAD_INST_PER_ELECTRON_STEP = 540.5
-THREAD_INST_PER_WOODCOCK_STEP = 487.8
-DRAM_BYTES_PER_HISTORY = {"electron": 28.23, "photon": 59.52}
+THREAD_INST_PER_ELECTRON_STEP = 582.2
+THREAD_INST_PER_WOODCOCK_STEP = 523.4
+DRAM_BYTES_PER_HISTORY = {"electron": 28.22, "photon": 60.14}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
 
