@@ -214,6 +214,17 @@ __device__ __forceinline__ void count_event(const Args &A, uint32_t root) {
     if (A.hist_events) atomicAdd(&A.hist_events[root & ROOT_INDEX_MASK], 1);
 }
 
+// An event's random draws: the particle's draw counter is loaded at the
+// start of the event and stored back at its end; the Philox block lives only
+// inside the event (every event starts its draws on a fresh block), so no
+// register holds it between events.
+struct EventRng {
+    uint32_t &saved;
+    Rng r;
+    __device__ __forceinline__ explicit EventRng(uint32_t &d) : saved(d) { r.draw = d; }
+    __device__ __forceinline__ ~EventRng() { saved = r.draw; }
+};
+
 // Angles are evaluated so that FP32 keeps their small parts: the sine of a
 // polar angle comes from a form without cancellation (never sqrt(1 - c^2)
 // near c = 1), the azimuth 2 pi xi through sincospif, logarithms of
@@ -413,7 +424,7 @@ struct Feed {
 struct Photon {
     float x, y, z, u, v, w, e, wt;
     uint32_t p0, p1, root, nchild;
-    Rng rng;
+    uint32_t draw;             // draws taken from the particle's Philox stream
     float mumax, inv_mumax;
     int ti;
     float tf;
@@ -449,8 +460,10 @@ __device__ __forceinline__ uint32_t photon_voxel(const Args &A, const Photon &g)
 
 __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
     acc.wsteps++;
-    g.rng.align();                                                // Woodcock step: step, virtual, channel
-    const float s = -ln_uniform(g.rng.next(A.rk, g.p0, g.p1)) * g.inv_mumax;
+    EventRng ev(g.draw);
+    Rng &rng = ev.r;
+    rng.align();                                                // Woodcock step: step, virtual, channel
+    const float s = -ln_uniform(rng.next(A.rk, g.p0, g.p1)) * g.inv_mumax;
     g.x += s * g.u; g.y += s * g.v; g.z += s * g.w;
     const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
     if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)A.nx && fy < (float)A.ny && fz < (float)A.nz)) {
@@ -464,9 +477,9 @@ __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
     const float mc = __fmul_rn(rho, c.x), mpe = __fmul_rn(rho, c.y), mpp = __fmul_rn(rho, c.z);
     const float mu = __fadd_rn(__fadd_rn(mc, mpe), mpp);          // = mu_of(rho, c)
     if (mu > g.mumax) atomicOr(A.err, 8u);
-    if (g.rng.next(A.rk, g.p0, g.p1) * g.mumax >= mu) return G_ON;          // virtual interaction
+    if (rng.next(A.rk, g.p0, g.p1) * g.mumax >= mu) return G_ON;          // virtual interaction
     count_event(A, g.root);
-    const float r = g.rng.next(A.rk, g.p0, g.p1) * mu;
+    const float r = rng.next(A.rk, g.p0, g.p1) * mu;
     g.chan = r < mc ? 0u : (r < mc + mpe ? 1u : 2u);
     return G_REAL;
 }
@@ -474,7 +487,9 @@ __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
 // the real interaction drawn by the last step; returns false when the photon ends
 __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon &g) {
     const uint32_t iv = photon_voxel(A, g);
-    g.rng.align();                                                // the interaction's draws
+    EventRng ev(g.draw);
+    Rng &rng = ev.r;
+    rng.align();                                                // the interaction's draws
     const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
     if (g.chan == 0u) {                                           // Compton (Kahn's method)
         acc.compton++;
@@ -483,7 +498,7 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
         const float p_first = __fdividef(1.0f + 2.0f * k, 9.0f + 2.0f * k);
         float x = 1.0f, ix = 1.0f;
         for (int it = 0; it < 1000; ++it) {
-            const float r1 = g.rng.next(A.rk, g.p0, g.p1), r2 = g.rng.next(A.rk, g.p0, g.p1), r3 = g.rng.next(A.rk, g.p0, g.p1);
+            const float r1 = rng.next(A.rk, g.p0, g.p1), r2 = rng.next(A.rk, g.p0, g.p1), r3 = rng.next(A.rk, g.p0, g.p1);
             if (r1 <= p_first) {
                 x = 1.0f + 2.0f * k * r2;
                 ix = __frcp_rn(x);
@@ -499,14 +514,14 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
         const float cth = 1.0f - dc, sth = sqrtf(dc * (2.0f - dc));
         const float ep = g.e * ix;
         float sp, cp;
-        sincos_2pi(g.rng.next(A.rk, g.p0, g.p1), &sp, &cp);
+        sincos_2pi(rng.next(A.rk, g.p0, g.p1), &sp, &cp);
         float nu = g.u, nv = g.v, nw = g.w;
         rotate_dir(nu, nv, nw, cth, sth, sp, cp);
         const float te = g.e - ep;
         float du = g.e * g.u - ep * nu, dv = g.e * g.v - ep * nv, dw = g.e * g.w - ep * nw;
         const float nn2 = du * du + dv * dv + dw * dw;
         if (nn2 > 0.0f) { const float in = rsqrtf(nn2); du *= in; dv *= in; dw *= in; } else { du = g.u; dv = g.v; dw = g.w; }
-        emit_charged(A, acc, g.rng, 1, te, g.x, g.y, g.z, du, dv, dw, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+        emit_charged(A, acc, rng, 1, te, g.x, g.y, g.z, du, dv, dw, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
         g.e = ep; g.u = nu; g.v = nv; g.w = nw;
         if (g.e < A.pcut) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         photon_energy(A, g);
@@ -514,15 +529,15 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
     } else if (g.chan == 1u) {                                    // photoelectric
         acc.photo++;
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
-        emit_charged(A, acc, g.rng, 1, g.e, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+        emit_charged(A, acc, rng, 1, g.e, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
         return false;
     }
     acc.pair++;                                                    // pair production
     if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
-    const float avail = g.e - 2.0f * F_ME, eps = g.rng.next(A.rk, g.p0, g.p1);
+    const float avail = g.e - 2.0f * F_ME, eps = rng.next(A.rk, g.p0, g.p1);
     const float t1 = eps * avail, t2 = avail - t1;
-    emit_charged(A, acc, g.rng, 1, t1, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
-    emit_charged(A, acc, g.rng, 2, t2, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+    emit_charged(A, acc, rng, 1, t1, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+    emit_charged(A, acc, rng, 2, t2, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
     return false;
 }
 
@@ -549,7 +564,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
                 } else {
                     g.x = p.x; g.y = p.y; g.z = p.z; g.u = p.u; g.v = p.v; g.w = p.w; g.e = p.e; g.wt = p.wt;
                     g.p0 = p.pid_lo; g.p1 = p.pid_hi; g.root = p.root; g.nchild = 0;
-                    g.rng.draw = 0;
+                    g.draw = 0;
                     photon_energy(A, g);
                     alive = true;
                 }
@@ -581,7 +596,7 @@ struct Electron {
     uint32_t p0, p1, root, nchild;
     int steps;
     bool pos;
-    Rng rng;
+    uint32_t draw;             // draws taken from the particle's Philox stream
 };
 
 __device__ __forceinline__ float highland(float T, float s, float rho) {
@@ -636,8 +651,12 @@ __device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, con
 __device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &s, uint32_t iv) {
     deposit(A, acc, iv, s.t, s.wt, s.root);
     if (s.pos) {
-        if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) deposit(A, acc, iv, 2.0f * F_ME, s.wt, s.root);
-        else annihilate(A, s.rng, s.x, s.y, s.z, s.wt, s.p0, s.p1, s.nchild, s.root);
+        if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) {
+            deposit(A, acc, iv, 2.0f * F_ME, s.wt, s.root);
+        } else {
+            EventRng ev(s.draw);
+            annihilate(A, ev.r, s.x, s.y, s.z, s.wt, s.p0, s.p1, s.nchild, s.root);
+        }
     }
 }
 
@@ -655,9 +674,11 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
     }
     acc.steps++;
     count_event(A, s.root);
-    s.rng.align();                                                // the step's draws (at most 3)
-    s.rng.fill(A.rk, s.p0, s.p1);
-    if (s.nlam < 0.0f) s.nlam = -ln_uniform(s.rng.take());       // a new mean free path count
+    EventRng ev(s.draw);
+    Rng &rng = ev.r;
+    rng.align();                                                  // the step's draws (at most 3)
+    rng.fill(A.rk, s.p0, s.p1);
+    if (s.nlam < 0.0f) s.nlam = -ln_uniform(rng.take());       // a new mean free path count
     const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
     const float rho = fabsf(__ldg(A.mrho + iv));
     int ti; float tf;
@@ -702,12 +723,12 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
     s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
     s.nlam -= step * sig;
     if (!(A.flags & PSL_PHYS_NO_MSC) && step > 0.0f) {
-        const float l2 = -2.0f * ln_uniform(s.rng.take());
+        const float l2 = -2.0f * ln_uniform(rng.take());
         const float th = th0 * (l2 * rsqrtf(l2));
         float st, ct, sp, cp;
         sincosf(th, &st, &ct);
         st = fabsf(st);
-        sincos_2pi(s.rng.take(), &sp, &cp);
+        sincos_2pi(rng.take(), &sp, &cp);
         rotate_dir(s.u, s.v, s.w, ct, st, sp, cp);
     }
     if (which == 1) {
@@ -727,16 +748,18 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
 // last step; the electron stays in the voxel of that step
 __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron &s) {
     const uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
+    EventRng ev(s.draw);
+    Rng &rng = ev.r;
     {
         int tj; float tg;
         tab_pos(A.tab, s.t, tj, tg);
         const float4 e2 = lerp4(A.tab.el, tj, tg);
         const float sm = s.t > 2.0f * A.wcc ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
-        s.rng.align();                                            // the hard event's draws
-        const float r = s.rng.next(A.rk, s.p0, s.p1) * (sm + sb);
+        rng.align();                                            // the hard event's draws
+        const float r = rng.next(A.rk, s.p0, s.p1) * (sm + sb);
         if (sm + sb > 0.0f) {
             if (r < sm) {                                         // hard Moller
-                const float eps = sample_moller(s.t, A.wcc, s.rng, A.rk, s.p0, s.p1, A.err);
+                const float eps = sample_moller(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
                 // polar cosines of the two electrons from momentum balance;
                 // their sines from the same balance without cancellation
@@ -745,14 +768,14 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
                 const float sp_ = sqrtf(2.0f * F_ME * W / (s.t * (tp + 2.0f * F_ME)));
                 const float sd_ = sqrtf(2.0f * F_ME * tp / (s.t * (W + 2.0f * F_ME)));
                 float sph, cph;
-                sincos_2pi(s.rng.next(A.rk, s.p0, s.p1), &sph, &cph);
+                sincos_2pi(rng.next(A.rk, s.p0, s.p1), &sph, &cph);
                 float du = s.u, dv = s.v, dw = s.w;
                 rotate_dir(du, dv, dw, cd, sd_, -sph, -cph);              // azimuth phi + pi
                 rotate_dir(s.u, s.v, s.w, cp, sp_, sph, cph);
-                emit_charged(A, acc, s.rng, 1, W, s.x, s.y, s.z, du, dv, dw, s.wt, iv, s.p0, s.p1, s.nchild, s.root);
+                emit_charged(A, acc, rng, 1, W, s.x, s.y, s.z, du, dv, dw, s.wt, iv, s.p0, s.p1, s.nchild, s.root);
                 s.t = tp;
             } else {                                              // hard bremsstrahlung
-                const float kph = A.wcb * expf(s.rng.next(A.rk, s.p0, s.p1) * logf(s.t / A.wcb));
+                const float kph = A.wcb * expf(rng.next(A.rk, s.p0, s.p1) * logf(s.t / A.wcb));
                 if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) deposit(A, acc, iv, kph, s.wt, s.root);
                 else push_particle(A.p_out, A, 0, s.x, s.y, s.z, s.u, s.v, s.w, kph, s.wt, s.p0, s.p1, s.nchild, s.root);
                 s.t -= kph;
@@ -790,7 +813,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     s.ix = min(max((int)floorf(s.x * A.ivx), 0), A.nx - 1);
                     s.iy = min(max((int)floorf(s.y * A.ivy), 0), A.ny - 1);
                     s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
-                    s.rng.draw = 0;
+                    s.draw = 0;
                     s.nlam = -1.0f;                               // drawn at the first step
                     s.r = range_of(A.tab, s.t);
                     alive = true;
