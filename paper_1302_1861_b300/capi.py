@@ -30,10 +30,11 @@ EXPORTS = (
     "psl_stream_read", "psl_batch_read", "psl_memory_trim",
     "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d", "psl_conv3d_wgrad", "psl_denoiser_param_count",
     "psl_denoiser_create", "psl_denoiser_destroy", "psl_denoiser_params", "psl_denoiser_forward",
-    "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma", "psl_conv3d_form",
+    "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma", "psl_conv3d_form", "psl_tally_set_order",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
+ORDER_AUTO, ORDER_READING, ORDER_BATCH = 0, 1, 2
 STATIC_MAX_RECORDS = 1 << 20
 
 vp = ctypes.c_void_p
@@ -419,6 +420,10 @@ def psl_tally_create(phantom: Phantom, n_batches: int) -> Tally:
     h = _out_handle()
     check(lib().psl_tally_create(ctypes.byref(phantom), int(n_batches), ctypes.byref(h)))
     return Tally(h.value)
+
+
+def psl_tally_set_order(tally: Tally, order: int):
+    check(lib().psl_tally_set_order(tally.h, int(order)))
 
 
 def psl_tally_reset(tally: Tally, stream=None):

@@ -131,7 +131,8 @@ struct psl_tally {
     int64_t nvox = 0;
     int32_t grid_mult = 4;            // persistent transport grid: blocks per SM
     int64_t chunk_cap = 1 << 24;      // primaries per transport pass (queue depth)
-    unsigned long long *t = nullptr;  // [nvox][n_batches] (voxel-major)
+    int32_t order = 0;                // psl_run history order: 0 auto, 1 reading order, 2 batch by batch
+    unsigned long long *t = nullptr;  // [n_batches][nvox] (a batch's slice contiguous)
     unsigned long long *ledger = nullptr;  // [8]
     Workspace *ws = nullptr;
 };

@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(256) k_readout(const unsigned long long *t, in
     unsigned long long local = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
         long long sum = 0;
-        for (int b = 0; b < nb; ++b) sum += (long long)t[(size_t)v * nb + b];
+        for (int b = 0; b < nb; ++b) sum += (long long)t[(size_t)b * nvox + v];
         local += (unsigned long long)sum;
         const double r = (double)rho[v];
         const double c = r > 0.0 ? scale / r : 0.0;     // Gy per fixed-point unit
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_readout(const unsigned long long *t, in
                 const double mean = tot / nb;
                 double var = 0.0;
                 for (int b = 0; b < nb; ++b) {
-                    const double d = (double)(long long)t[(size_t)v * nb + b] - mean;
+                    const double d = (double)(long long)t[(size_t)b * nvox + v] - mean;
                     var += d * d;
                 }
                 s = c * sqrt((double)nb / (nb - 1.0) * var);
@@ -41,15 +41,6 @@ __global__ void __launch_bounds__(256) k_readout(const unsigned long long *t, in
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(dep, local);
-}
-
-// the public layout [batch][voxel] from the internal [voxel][batch]
-__global__ void k_tally_out(const unsigned long long *t, int64_t nvox, int nb, int64_t *out) {
-    const int64_t n = nvox * nb;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = q / nvox, v = q - b * nvox;
-        out[q] = (int64_t)t[v * nb + b];
-    }
 }
 
 __global__ void k_ledger_out(const unsigned long long *ledger, const unsigned long long *dep, double *out) {
@@ -80,6 +71,12 @@ extern "C" int psl_tally_create(const psl_phantom_t *ph, int32_t n_batches, psl_
     return PSL_OK;
 }
 
+extern "C" int psl_tally_set_order(psl_tally_t *t, int32_t order) {
+    if (!t || order < PSL_ORDER_AUTO || order > PSL_ORDER_BATCH) return psl_fail(PSL_EINVAL, "psl_tally_set_order: bad argument");
+    t->order = order;
+    return PSL_OK;
+}
+
 extern "C" int psl_tally_reset(psl_tally_t *t, void *stream_) {
     if (!t) return psl_fail(PSL_EINVAL, "psl_tally_reset: null tally");
     cudaStream_t st = as_stream(stream_);
@@ -91,12 +88,7 @@ extern "C" int psl_tally_reset(psl_tally_t *t, void *stream_) {
 extern "C" int psl_tally_read(const psl_tally_t *t, int64_t *tallies, int64_t *ledger, void *stream_) {
     if (!t) return psl_fail(PSL_EINVAL, "psl_tally_read: null tally");
     cudaStream_t st = as_stream(stream_);
-    if (tallies) {
-        const int64_t n = t->nvox * t->n_batches;
-        k_tally_out<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)), 256, 0, st>>>(t->t, t->nvox, t->n_batches, tallies);
-        PSL_NOTE_LAUNCH();
-        PSL_CUDA(cudaGetLastError());
-    }
+    if (tallies) PSL_CUDA(cudaMemcpyAsync(tallies, t->t, (size_t)t->n_batches * t->nvox * 8, cudaMemcpyDeviceToDevice, st));
     if (ledger) PSL_CUDA(cudaMemcpyAsync(ledger, t->ledger, 12 * 8, cudaMemcpyDeviceToDevice, st));
     return PSL_OK;
 }

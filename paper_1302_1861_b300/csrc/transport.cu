@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -28,6 +29,7 @@
 #include "physics.cuh"
 #include "psl_internal.cuh"
 #include "source.cuh"
+#include "sort.cuh"
 
 namespace {
 
@@ -78,7 +80,7 @@ struct Args {
     uint32_t k0, k1;          // the seed's two words (Philox key)
     uint32_t rk[20];          // Philox key schedule of the seed
     Tables tab;
-    unsigned long long *tally;  // [voxel][slice] (a history's slice is in its root word)
+    unsigned long long *tally;  // [slice][voxel] (a history's slice is in its root word)
     int64_t nvox;
     uint32_t n_slices;
     unsigned long long *ledger;
@@ -198,7 +200,7 @@ __device__ __forceinline__ unsigned long long fixed_point(float e, float wt) {
 __device__ __forceinline__ void deposit(const Args &A, Acc &acc, uint32_t iv, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
     if (!q) return;
-    atomicAdd(&A.tally[(uint64_t)iv * A.n_slices + (root >> ROOT_SLICE_SHIFT)], q);
+    atomicAdd(&A.tally[(uint64_t)(root >> ROOT_SLICE_SHIFT) * (uint64_t)A.nvox + iv], q);
     acc.dep += q;
     acc.atomics++;
     if (A.hist_dep) atomicAdd(&A.hist_dep[root & ROOT_INDEX_MASK], q);
@@ -855,18 +857,56 @@ __global__ void k_assign_slices(Args A, Particle *p, int64_t nph, int64_t nel, i
 // photons are written to the primary buffer, charged primaries go straight to
 // the electron queue.  Each warp locates its first history and its lanes
 // reuse that (group, segment) when it is also theirs.
+// Batch of every history of a window [first, first + n): the key of the
+// stable sort that partitions the window batch by batch.
+__global__ void __launch_bounds__(256) k_slice_keys(Args A, int64_t first, uint32_t n, uint32_t nb, uint32_t *keys) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t h = (uint64_t)(first + i);
+        keys[i] = history_slice((uint32_t)h, (uint32_t)(h >> 32), A.rk, nb);
+    }
+}
+
+__global__ void k_or_err(const uint32_t *src, uint32_t *err) {
+    if (*src) atomicOr(err, *src);
+}
+
+// off[b] = first position of batch b in the sorted keys (off[nb] = n)
+__global__ void k_slice_bounds(const uint32_t *keys, uint32_t n, uint32_t nb, uint32_t *off) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = n;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (keys[mid] < b) lo = mid + 1; else hi = mid;
+        }
+        off[b] = lo;
+    }
+}
+
+// Histories first + i * stride, i < n; or, with a list, the histories
+// first + list[list_off[slice] + root0 + i] of one batch of a window whose
+// offsets were sorted by batch (at most n of them: more is an overflow).
 __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first, int64_t stride, uint32_t n,
-                                                uint32_t root0, int32_t slice, Particle *out, uint32_t *count) {
+                                                uint32_t root0, int32_t slice, Particle *out, uint32_t *count,
+                                                const uint32_t *list, const uint32_t *list_off) {
     __shared__ int64_t gs[1025];
     for (int i = threadIdx.x; i <= P.n_groups; i += blockDim.x) gs[i] = P.group_start[i];
     __syncthreads();
+    const uint32_t cap = n;
+    uint32_t lbase = 0;
+    if (list) {
+        lbase = list_off[slice] + root0;
+        const uint32_t total = list_off[slice + 1] - list_off[slice];
+        const uint32_t left = total > root0 ? total - root0 : 0u;
+        if (left > n && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, PSL_DEV_ERR_QUEUE);
+        n = min(n, left);
+    }
     Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int lane = threadIdx.x & 31;
     const uint32_t gstride = gridDim.x * blockDim.x;
     const uint32_t n_round = (n + 31u) & ~31u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += gstride) {
         const bool ok = i < n;
-        const int64_t h = first + (int64_t)i * stride;
+        const int64_t h = list ? (ok ? first + (int64_t)__ldg(list + lbase + i) : first) : first + (int64_t)i * stride;
         int g = -1;
         int64_t q = -1;
         if (lane == 0 && ok) locate(P, gs, h, g, q);
@@ -891,7 +931,7 @@ __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first
             c.type = (uint32_t)o.ptype;
             const uint32_t sl = slice >= 0 ? (uint32_t)slice : history_slice(c.pid_lo, c.pid_hi, A.rk, A.n_slices);
             c.root = (sl << ROOT_SLICE_SHIFT) | ((root0 + i) & ROOT_INDEX_MASK);
-            if (o.ptype == 0) queue_push(Queue{out, count, n}, c, A.err);
+            if (o.ptype == 0) queue_push(Queue{out, count, cap}, c, A.err);
             else queue_push(A.e_out, c, A.err);
         }
     }
@@ -1033,6 +1073,11 @@ struct Workspace {
     float *mrho = nullptr;             // packed material/density of the phantom
     int64_t nvox = 0;
     uint32_t *host = nullptr;          // pinned: counts read back
+    // batch-by-batch order (psl_run): a window's batch keys and history
+    // offsets, sorted by batch, the sort's scratch and the batch bounds
+    int64_t bm_cap = 0;
+    uint32_t *bm_keys[2] = {nullptr, nullptr}, *bm_vals[2] = {nullptr, nullptr}, *bm_off = nullptr;
+    void *bm_scratch = nullptr;
     // cached CUDA graph of one psl_run call
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_key[8] = {0};
@@ -1048,7 +1093,48 @@ void workspace_free(Workspace *w) {
     if (w->rmax) cudaFree(w->rmax);
     if (w->mrho) cudaFree(w->mrho);
     if (w->host) cudaFreeHost(w->host);
+    for (int k = 0; k < 2; ++k) { if (w->bm_keys[k]) cudaFree(w->bm_keys[k]); if (w->bm_vals[k]) cudaFree(w->bm_vals[k]); }
+    if (w->bm_off) cudaFree(w->bm_off);
+    if (w->bm_scratch) cudaFree(w->bm_scratch);
     delete w;
+}
+
+// Batch-by-batch order (PSL_ORDER_BATCH): histories per window, so that a
+// batch of a window (binomial, mean W / nb) stays within one transport pass
+// of `chunk` primaries by 8 standard deviations: W / nb = (sqrt(chunk + 16) - 4)^2.
+static int64_t batch_window(int64_t chunk, int nb) {
+    const double r = std::sqrt((double)chunk + 16.0) - 4.0;
+    return std::min<int64_t>(std::max<int64_t>(1, (int64_t)(r * r)) * nb, (int64_t)1 << 28);
+}
+
+static bool use_batch_order(const psl_tally *t) {
+    if (t->n_batches < 2 || t->order == PSL_ORDER_READING) return false;
+    if (t->order == PSL_ORDER_BATCH) return true;
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    return (double)t->nvox * (double)t->n_batches * 8.0 > 0.5 * (double)l2;
+}
+
+static int batch_order_ensure(psl_tally *t, int64_t W) {
+    Workspace *w = t->ws;
+    if (w->bm_cap >= W) return PSL_OK;
+    for (int k = 0; k < 2; ++k) {
+        if (w->bm_keys[k]) cudaFree(w->bm_keys[k]);
+        if (w->bm_vals[k]) cudaFree(w->bm_vals[k]);
+        w->bm_keys[k] = w->bm_vals[k] = nullptr;
+    }
+    if (w->bm_off) cudaFree(w->bm_off);
+    if (w->bm_scratch) cudaFree(w->bm_scratch);
+    w->bm_off = nullptr; w->bm_scratch = nullptr; w->bm_cap = 0;
+    for (int k = 0; k < 2; ++k) {
+        PSL_CUDA(cudaMalloc((void **)&w->bm_keys[k], (size_t)W * 4));
+        PSL_CUDA(cudaMalloc((void **)&w->bm_vals[k], (size_t)W * 4));
+    }
+    PSL_CUDA(cudaMalloc((void **)&w->bm_off, (PSL_MAX_BATCHES + 1) * 4));
+    PSL_CUDA(cudaMalloc((void **)&w->bm_scratch, sort_pairs_scratch_bytes((uint32_t)W)));
+    w->bm_cap = W;
+    return PSL_OK;
 }
 
 static int workspace_ensure(psl_tally *t, int64_t chunk) {
@@ -1086,6 +1172,7 @@ struct Job {
     bool lazy = false;
     PlanDev P{};
     int64_t first = 0, stride = 1, n = 0;            // lazy
+    const uint32_t *list = nullptr, *list_off = nullptr;  // lazy, one batch of a sorted window (slice = the batch)
     const Particle *p = nullptr;                     // materialised
     int64_t nph = 0, nel = 0, cap = 0;
     int32_t slice = 0;
@@ -1208,8 +1295,9 @@ struct Runner {
                 cudaMemsetAsync(w->cnt + 7, 0, 4, st);
                 void *tk = nullptr;
                 tb(PK_SOURCE, &tk);
-                k_source<<<grid_m, 256, 0, st>>>(a2, J.P, J.first + a0 * J.stride, J.stride, cp, (uint32_t)a0, J.slice,
-                                                 w->Q, w->cnt + 7); PSL_NOTE_LAUNCH();
+                k_source<<<grid_m, 256, 0, st>>>(a2, J.P, J.list ? J.first : J.first + a0 * J.stride, J.stride, cp,
+                                                 (uint32_t)a0, J.slice, w->Q, w->cnt + 7, J.list, J.list_off);
+                PSL_NOTE_LAUNCH();
                 te(PK_SOURCE, tk);
                 photon_pass(w->Q, w->cnt + 7, 0, cp);
                 band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
@@ -1325,17 +1413,53 @@ extern "C" int transport_trace(const psl_phantom_t *ph, const psl_physics_t *phy
 // most batches finish within them, so a batch usually costs one host check.
 #define UNCHECKED_GENERATIONS 3
 
+// Windows of the batch-by-batch order for a range of n histories (0: the
+// range runs in reading order).
+static int64_t batch_order_window(const psl_tally *tally, int64_t n) {
+    if (!use_batch_order(tally)) return 0;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, tally->chunk_cap));
+    return std::min<int64_t>(batch_window(chunk, tally->n_batches), n);
+}
+
 static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
                     int64_t first, int64_t n, cudaStream_t st, bool capturing, Runner &R) {
-    // the whole range in reading order; each history's deposits go to the
-    // tally slice of its id (independent batches, Sec. 2.3.3)
+    // each history's deposits go to the tally slice of its id (independent
+    // batches, Sec. 2.3.3); the range runs in reading order, or window by
+    // window and, inside a window, batch by batch (the dose is the same)
     int rc = R.prepare(ph, phys, tally, plan->seed, n, st, capturing);
     if (rc) return rc;
     Job J;
     J.lazy = true;
     J.P = make_plan_dev(plan, ph);
     J.first = first; J.stride = 1; J.n = n; J.slice = PSL_SLICE_BY_HISTORY;
-    return R.run(J, capturing ? -1 : UNCHECKED_GENERATIONS);
+    const int check = capturing ? -1 : UNCHECKED_GENERATIONS;
+    const int64_t W = batch_order_window(tally, n);
+    if (W <= 0) return R.run(J, check);
+    if (!capturing && (rc = batch_order_ensure(tally, W))) return rc;   // (a capture is set up beforehand)
+    Workspace *w = tally->ws;
+    if (w->bm_cap < W) return psl_fail(PSL_EINVAL, "psl_run: batch-order buffers not set up");
+    const uint32_t nb = (uint32_t)tally->n_batches;
+    const int bits = 32 - __builtin_clz(nb - 1);
+    for (int64_t w0 = 0; w0 < n; w0 += W) {
+        const uint32_t wn = (uint32_t)std::min<int64_t>(W, n - w0);
+        k_slice_keys<<<R.grid_m, 256, 0, st>>>(R.A, first + w0, wn, nb, w->bm_keys[0]); PSL_NOTE_LAUNCH();
+        int alt = 0;
+        if (sort_pairs_u32(w->bm_keys[0], w->bm_vals[0], w->bm_keys[1], w->bm_vals[1], wn, bits, nullptr, true,
+                           w->bm_scratch, &alt, st))
+            return psl_fail(PSL_EINVAL, "psl_run: batch sort");
+        k_or_err<<<1, 1, 0, st>>>(sort_err_word(w->bm_scratch), R.A.err); PSL_NOTE_LAUNCH();
+        k_slice_bounds<<<1, 256, 0, st>>>(w->bm_keys[alt], wn, nb, w->bm_off); PSL_NOTE_LAUNCH();
+        for (uint32_t b = 0; b < nb; ++b) {
+            Job Jb = J;
+            Jb.first = first + w0;
+            Jb.n = std::min<int64_t>(R.chunk, wn);     // one pass; k_source flags a batch larger than it
+            Jb.slice = (int32_t)b;
+            Jb.list = w->bm_vals[alt];
+            Jb.list_off = w->bm_off;
+            if ((rc = R.run(Jb, check))) return rc;
+        }
+    }
+    return PSL_OK;
 }
 
 extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
@@ -1356,11 +1480,13 @@ extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const ps
     if (phys) P = *phys;
     uint64_t key[8] = {(uint64_t)(uintptr_t)plan, (uint64_t)first, (uint64_t)n, (uint64_t)(uintptr_t)ph->rho,
                        (uint64_t)(uintptr_t)ph->mat, ((uint64_t)P.flags << 32) | (uint64_t)tally->grid_mult,
-                       (uint64_t)tally->chunk_cap, (uint64_t)plan->seed};
+                       (uint64_t)tally->chunk_cap ^ ((uint64_t)tally->order << 60), (uint64_t)plan->seed};
     // workspace and tables are set up outside the capture
     {
         Runner pre;
         if ((rc = pre.prepare(ph, phys, tally, plan->seed, n, st, false))) return rc;
+        const int64_t W = batch_order_window(tally, n);
+        if (W > 0 && (rc = batch_order_ensure(tally, W))) return rc;
         PSL_CUDA(cudaStreamSynchronize(st));
     }
     Workspace *w = tally->ws;

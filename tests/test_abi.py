@@ -49,3 +49,4 @@ def test_invalid_arguments_fail_cleanly_without_gpu():
     assert L.psl_build(ctypes.byref(prm), ctypes.byref(rec), ctypes.byref(h), None) == capi.PSL_EINVAL
     assert b"bad bin counts" in L.psl_last_error()
     assert L.psl_plan_create(None, None, 0, 100.0, 10, 1, ctypes.byref(h), None) == capi.PSL_EINVAL
+    assert L.psl_tally_set_order(None, capi.ORDER_BATCH) == capi.PSL_EINVAL
