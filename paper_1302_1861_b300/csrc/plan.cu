@@ -229,12 +229,27 @@ struct Pool {   // frees temporaries at scope exit (stream ordered)
     ~Pool() { for (void *p : ptrs) cudaFreeAsync(p, st); }
 };
 
+// the source stage's packed copies of the visiting order and its segments
+__global__ void k_pack_order(const uint32_t *sorted, int64_t n, const int64_t *e_start, const int64_t *e_nrec,
+                             const int64_t *e_offset, const int32_t *e_beam, const int64_t *seg_h,
+                             const int64_t *seg_r0, const int32_t *seg_w, EntryDev *ent, SegDev *seg) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = sorted[t];
+        EntryDev e;
+        e.start = e_start[k]; e.nrec = e_nrec[k]; e.offset = e_offset[k]; e.beam = e_beam[k]; e.entry = k;
+        ent[t] = e;
+        SegDev g;
+        g.h = seg_h[t]; g.r0 = seg_r0[t]; g.w = seg_w[t]; g.pad = 0;
+        seg[t] = g;
+    }
+}
+
 }  // namespace
 
 extern "C" void psl_plan_destroy(psl_plan_t *p) {
     if (!p) return;
     void *ptrs[] = {p->beams, p->e_beam, p->e_psl, p->e_start, p->e_nrec, p->e_count, p->e_offset,
-                    p->group_start, p->group_seg, p->sorted, p->seg_h, p->seg_r0, p->seg_w};
+                    p->group_start, p->group_seg, p->sorted, p->seg_h, p->seg_r0, p->seg_w, p->ent, p->seg};
     for (void *q : ptrs)
         if (q) cudaFreeAsync(q, p->stream);
     delete p;
@@ -343,6 +358,8 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
         ok &= psl_malloc_async((void **)&p->seg_h, n_active * 8, st) == cudaSuccess;
         ok &= psl_malloc_async((void **)&p->seg_r0, n_active * 8, st) == cudaSuccess;
         ok &= psl_malloc_async((void **)&p->seg_w, n_active * 4, st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->ent, n_active * sizeof(EntryDev), st) == cudaSuccess;
+        ok &= psl_malloc_async((void **)&p->seg, n_active * sizeof(SegDev), st) == cudaSuccess;
         ok &= psl_malloc_async((void **)&p->group_seg, (n_te + 1) * 8, st) == cudaSuccess;
         ok &= psl_malloc_async((void **)&p->group_start, (n_te + 1) * 8, st) == cudaSuccess;
         void *sscr3 = tmp.raw(scan_i64_scratch_bytes(n_active + 1));
@@ -365,6 +382,9 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
         scan_i64(lens, X2, n_active, sscr3, st);
         k_seg_h<<<grid_for(n_active), 256, 0, st>>>(X2, p->group_seg, seg_g, n_active, p->seg_h); PSL_NOTE_LAUNCH();
         k_group_start<<<(n_te + 256) / 256, 256, 0, st>>>(X2, p->group_seg, n_te, p->group_start); PSL_NOTE_LAUNCH();
+        k_pack_order<<<grid_for(n_active), 256, 0, st>>>(p->sorted, n_active, p->e_start, p->e_nrec, p->e_offset,
+                                                         p->e_beam, p->seg_h, p->seg_r0, p->seg_w, p->ent, p->seg);
+        PSL_NOTE_LAUNCH();
         uint32_t herr = 0;
         cudaMemcpyAsync(&herr, sort_err_word(sort_scr), 4, cudaMemcpyDeviceToHost, st);
         if ((e = cudaGetLastError()) != cudaSuccess) rc = psl_fail(PSL_ECUDA, cudaGetErrorString(e));

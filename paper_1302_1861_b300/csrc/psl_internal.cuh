@@ -82,6 +82,23 @@ struct BeamDev {
     float sad;
 };
 
+// One entry of a plan's reading order in visiting position, packed so that
+// the source stage reads it with one 32-byte load: the PSL's first sorted
+// record, its record count, the entry's random start offset (Sec. 2.3.3),
+// its beam and the entry's index in the entry list.
+struct __align__(16) EntryDev {
+    int64_t start, nrec, offset;
+    int32_t beam;
+    uint32_t entry;
+};
+
+// One segment of a group's reading order (rounds of constant width): its
+// group-local first history, first round and active entries.
+struct __align__(16) SegDev {
+    int64_t h, r0;
+    int32_t w, pad;
+};
+
 struct psl_plan {
     const psl_store *store = nullptr;
     int32_t n_beams = 0;
@@ -101,6 +118,8 @@ struct psl_plan {
     int64_t *seg_h = nullptr;        // [n_active] group-local first history of segment
     int64_t *seg_r0 = nullptr;       // first round of segment
     int32_t *seg_w = nullptr;        // active entries in the segment's rounds
+    EntryDev *ent = nullptr;         // [n_active] entry data in visiting order (sorted[])
+    SegDev *seg = nullptr;           // [n_active] seg_h, seg_r0, seg_w packed
     int64_t n_active = 0;
     cudaStream_t stream = nullptr;
 };

@@ -18,13 +18,13 @@ namespace {
 __global__ void __launch_bounds__(256) k_source_trace(PlanDev P, int64_t first, int64_t n, int64_t stride, int64_t *entry, int64_t *use,
                                                       int64_t *rec, int32_t *beam, int8_t *status, float *state,
                                                       int32_t *ptype) {
-    __shared__ int64_t gs[1025];
-    for (int i = threadIdx.x; i <= P.n_groups; i += blockDim.x) gs[i] = P.group_start[i];
+    __shared__ PlanShared S;
+    plan_shared_load(P, S);
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         SrcOut o;
         for (int k = 0; k < 8; ++k) o.s[k] = 0.f;
-        source_one(P, gs, first + i * stride, o);
+        source_one(P, S, first + i * stride, o);
         if (entry) entry[i] = o.entry;
         if (use) use[i] = o.use;
         if (rec) rec[i] = o.rec;

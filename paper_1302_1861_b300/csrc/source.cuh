@@ -11,11 +11,9 @@
 #include "psl_internal.cuh"
 
 struct PlanDev {
-    const int64_t *group_start, *group_seg, *seg_h, *seg_r0;
-    const int32_t *seg_w;
-    const uint32_t *sorted;
-    const int64_t *e_start, *e_nrec, *e_offset;
-    const int32_t *e_beam;
+    const int64_t *group_start, *group_seg;
+    const SegDev *seg;               // segments, packed
+    const EntryDev *ent;             // entries in visiting order, packed
     const BeamDev *beams;
     const PslRecord *rec;
     int n_groups;
@@ -31,35 +29,49 @@ struct SrcOut {
     float s[8];                    // x y z u v w e wt (phantom-local)
 };
 
-__device__ __forceinline__ int64_t upper_bound_i64(const int64_t *a, int64_t lo, int64_t hi, int64_t v) {
-    // first index in [lo, hi) with a[i] > v
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (a[mid] <= v) lo = mid + 1; else hi = mid;
+// A block's copy of the group bounds (at most 1024 groups: energy
+// divisions x types): first history and first segment of each group.
+struct PlanShared {
+    int64_t gs[1025], gseg[1025];
+};
+
+__device__ __forceinline__ void plan_shared_load(const PlanDev &P, PlanShared &S) {
+    for (int i = threadIdx.x; i <= P.n_groups; i += blockDim.x) {
+        S.gs[i] = P.group_start[i];
+        S.gseg[i] = P.group_seg[i];
     }
-    return lo;
 }
 
 // group g and segment q of history h (the last segment whose first history
 // is <= h's group-local index)
-__device__ __forceinline__ void locate(const PlanDev &P, const int64_t *gs_sh, int64_t h, int &g, int64_t &q) {
+__device__ __forceinline__ void locate(const PlanDev &P, const PlanShared &S, int64_t h, int &g, int64_t &q) {
     int lo = 0, hi = P.n_groups;            // last g with group_start[g] <= h
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
-        if (gs_sh[mid] <= h) lo = mid; else hi = mid;
+        if (S.gs[mid] <= h) lo = mid; else hi = mid;
     }
     g = lo;
-    q = upper_bound_i64(P.seg_h, P.group_seg[g], P.group_seg[g + 1], h - gs_sh[g]) - 1;
+    const int64_t hl = h - S.gs[g];
+    int64_t a = S.gseg[g], b = S.gseg[g + 1];  // first segment in [a, b) whose first history is > hl
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (P.seg[mid].h <= hl) a = mid + 1; else b = mid;
+    }
+    q = a - 1;
 }
 
 // locate with a guess (g, q), e.g. a neighbouring history's: kept if it is
-// exactly what locate() would return, otherwise searched
-__device__ __forceinline__ void locate_hinted(const PlanDev &P, const int64_t *gs_sh, int64_t h, int &g, int64_t &q) {
-    if (g >= 0 && gs_sh[g] <= h && h < gs_sh[g + 1]) {
-        const int64_t hl = h - gs_sh[g];
-        if (P.seg_h[q] <= hl && (q + 1 == P.group_seg[g + 1] || P.seg_h[q + 1] > hl)) return;
+// exactly what locate() would return, moved to the next segment if that one
+// holds h, otherwise searched
+__device__ __forceinline__ void locate_hinted(const PlanDev &P, const PlanShared &S, int64_t h, int &g, int64_t &q) {
+    if (g >= 0 && S.gs[g] <= h && h < S.gs[g + 1]) {
+        const int64_t hl = h - S.gs[g], end = S.gseg[g + 1];
+        if (P.seg[q].h <= hl) {
+            if (q + 1 == end || P.seg[q + 1].h > hl) return;
+            if (q + 2 == end || P.seg[q + 2].h > hl) { ++q; return; }
+        }
     }
-    locate(P, gs_sh, h, g, q);
+    locate(P, S, h, g, q);
 }
 
 // a / b and a % b for non-negative a and 0 < b; 32-bit arithmetic when both fit
@@ -128,34 +140,32 @@ __device__ __forceinline__ void record_to_phantom(const PslRecord &R, const Beam
     o.status = PSL_SRC_TRANSPORT;
 }
 
-__device__ __forceinline__ void source_at(const PlanDev &P, const int64_t *gs_sh, int64_t h, int g, int64_t q,
+__device__ __forceinline__ void source_at(const PlanDev &P, const PlanShared &S, int64_t h, int g, int64_t q,
                                           SrcOut &o) {
-    const int64_t hl = h - gs_sh[g];
+    const int64_t hl = h - S.gs[g];
+    const SegDev sg = P.seg[q];
     uint64_t rq, pidx, rr, rw;
-    divmod_u64((uint64_t)(hl - P.seg_h[q]), (uint64_t)P.seg_w[q], rq, pidx);
-    const int64_t r = P.seg_r0[q] + (int64_t)rq;
-    const int64_t entry = P.sorted[P.group_seg[g] + pidx];
-    const int64_t nrec = P.e_nrec[entry];
-    divmod_u64((uint64_t)(P.e_offset[entry] + r), (uint64_t)nrec, rw, rr);
-    const int64_t rec = P.e_start[entry] + (int64_t)rr;
-    o.entry = entry; o.use = r; o.rec = rec;
-    const int b = P.e_beam[entry];
-    o.beam = b;
-    record_to_phantom(P.rec[rec], P.beams[b], P.z_psl, P.L, P.origin, true, o);
+    divmod_u64((uint64_t)(hl - sg.h), (uint64_t)sg.w, rq, pidx);
+    const int64_t r = sg.r0 + (int64_t)rq;
+    const EntryDev E = P.ent[S.gseg[g] + (int64_t)pidx];
+    divmod_u64((uint64_t)(E.offset + r), (uint64_t)E.nrec, rw, rr);
+    const int64_t rec = E.start + (int64_t)rr;
+    o.entry = E.entry; o.use = r; o.rec = rec;
+    o.beam = E.beam;
+    record_to_phantom(P.rec[rec], P.beams[E.beam], P.z_psl, P.L, P.origin, true, o);
 }
 
-__device__ __forceinline__ void source_one(const PlanDev &P, const int64_t *gs_sh, int64_t h, SrcOut &o) {
+__device__ __forceinline__ void source_one(const PlanDev &P, const PlanShared &S, int64_t h, SrcOut &o) {
     int g;
     int64_t q;
-    locate(P, gs_sh, h, g, q);
-    source_at(P, gs_sh, h, g, q, o);
+    locate(P, S, h, g, q);
+    source_at(P, S, h, g, q, o);
 }
 
 inline PlanDev make_plan_dev(const psl_plan *p, const psl_phantom_t *ph) {
     PlanDev P;
-    P.group_start = p->group_start; P.group_seg = p->group_seg; P.seg_h = p->seg_h; P.seg_r0 = p->seg_r0;
-    P.seg_w = p->seg_w; P.sorted = p->sorted; P.e_start = p->e_start; P.e_nrec = p->e_nrec;
-    P.e_offset = p->e_offset; P.e_beam = p->e_beam; P.beams = p->beams; P.rec = p->store->rec;
+    P.group_start = p->group_start; P.group_seg = p->group_seg; P.seg = p->seg; P.ent = p->ent;
+    P.beams = p->beams; P.rec = p->store->rec;
     P.n_groups = p->n_groups; P.z_psl = p->store->z_psl;
     P.L[0] = ph->nx * ph->vx; P.L[1] = ph->ny * ph->vy; P.L[2] = ph->nz * ph->vz;
     for (int k = 0; k < 3; ++k) P.origin[k] = ph->origin[k];

@@ -888,8 +888,8 @@ __global__ void k_slice_bounds(const uint32_t *keys, uint32_t n, uint32_t nb, ui
 __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first, int64_t stride, uint32_t n,
                                                 uint32_t root0, int32_t slice, Particle *out, uint32_t *count,
                                                 const uint32_t *list, const uint32_t *list_off) {
-    __shared__ int64_t gs[1025];
-    for (int i = threadIdx.x; i <= P.n_groups; i += blockDim.x) gs[i] = P.group_start[i];
+    __shared__ PlanShared S;
+    plan_shared_load(P, S);
     __syncthreads();
     const uint32_t cap = n;
     uint32_t lbase = 0;
@@ -902,21 +902,29 @@ __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first
     }
     Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int lane = threadIdx.x & 31;
-    const uint32_t gstride = gridDim.x * blockDim.x;
-    const uint32_t n_round = (n + 31u) & ~31u;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += gstride) {
-        const bool ok = i < n;
+    // each warp takes a contiguous run of histories, 32 at a time, and each
+    // lane carries its (group, segment) to the next 32: consecutive histories
+    // stay in a segment or step to the next, so the searches are rare
+    const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t per = ((n + n_warps - 1) / n_warps + 31u) & ~31u;
+    const uint32_t i0 = min(n, (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per);
+    const uint32_t i1 = min(n, i0 + per);
+    int g = -1;
+    int64_t q = -1;
+    for (uint32_t ib = i0; ib < i1; ib += 32) {
+        const uint32_t i = ib + lane;
+        const bool ok = i < i1;
         const int64_t h = list ? (ok ? first + (int64_t)__ldg(list + lbase + i) : first) : first + (int64_t)i * stride;
-        int g = -1;
-        int64_t q = -1;
-        if (lane == 0 && ok) locate(P, gs, h, g, q);
-        g = __shfl_sync(FULL, g, 0);
-        q = __shfl_sync(FULL, q, 0);
+        if (ib == i0) {
+            if (lane == 0 && ok) locate(P, S, h, g, q);
+            g = __shfl_sync(FULL, g, 0);
+            q = __shfl_sync(FULL, q, 0);
+        }
         SrcOut o;
         o.status = -1;
         if (ok) {
-            locate_hinted(P, gs, h, g, q);
-            source_at(P, gs, h, g, q, o);
+            locate_hinted(P, S, h, g, q);
+            source_at(P, S, h, g, q, o);
         }
         if (o.status == PSL_SRC_TRANSPORT || o.status == PSL_SRC_MISS) {
             const unsigned long long e = fixed_point(o.s[6], o.s[7]);
