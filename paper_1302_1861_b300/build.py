@@ -29,7 +29,7 @@ def sources():
 
 def deps():
     return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
-        [os.path.join(HERE, "..", "include", "psl.h")]
+        [os.path.join(HERE, "..", "include", "psl.h"), os.path.join(HERE, "..", "include", "psl_denoise.h")]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

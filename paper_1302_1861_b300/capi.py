@@ -31,6 +31,7 @@ EXPORTS = (
     "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d", "psl_conv3d_wgrad", "psl_denoiser_param_count",
     "psl_denoiser_create", "psl_denoiser_destroy", "psl_denoiser_params", "psl_denoiser_forward",
     "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma", "psl_conv3d_form", "psl_tally_set_order",
+    "psl_kth_smallest",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
@@ -138,6 +139,8 @@ def lib():
             "psl_denoiser_step": [vp, f32, vp],
             "psl_gamma": [vp, vp, i32, i32, i32, f32, f32, f32, f64, f64, f64, i32, f64, vp, vp, vp],
             "psl_conv3d_form": [i32],
+            "psl_tally_set_order": [vp, i32],
+            "psl_kth_smallest": [vp, i64, i64, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -420,6 +423,13 @@ def psl_tally_create(phantom: Phantom, n_batches: int) -> Tally:
     h = _out_handle()
     check(lib().psl_tally_create(ctypes.byref(phantom), int(n_batches), ctypes.byref(h)))
     return Tally(h.value)
+
+
+def kth_smallest(x, k: int, stream=None) -> float:
+    """The k-th smallest (0-based) of the values of a float32 device tensor."""
+    v = f32()
+    check(lib().psl_kth_smallest(ptr(x), int(x.numel()), int(k), ctypes.byref(v), stream_ptr(stream)))
+    return v.value
 
 
 def psl_tally_set_order(tally: Tally, order: int):

@@ -19,6 +19,7 @@
 
 #include "../../include/psl_denoise.h"
 #include "psl_internal.cuh"
+#include "sort.cuh"
 
 int psl_conv_ksteps(int ci);
 int psl_conv3d_run(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, const float *bias, int co, int nx,
@@ -440,4 +441,53 @@ extern "C" int psl_denoiser_step(psl_denoiser_t *d, float lr, void *stream) {
     int rc = repack(d, st);
     if (rc) return rc;
     return finish(d, st, "psl_denoiser_step");
+}
+
+// ------------------------------------------------------------ k-th value --
+namespace {
+// order-preserving map of a float's bits to an unsigned key (negatives below
+// positives, larger magnitude negatives lower)
+__global__ void k_float_keys(const float *x, uint32_t n, uint32_t *keys) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t b = __float_as_uint(x[i]);
+        keys[i] = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    }
+}
+__global__ void k_key_value(const uint32_t *keys, uint32_t k, float *out) {
+    const uint32_t b = keys[k];
+    *out = __uint_as_float((b & 0x80000000u) ? (b & 0x7FFFFFFFu) : ~b);
+}
+}  // namespace
+
+extern "C" int psl_kth_smallest(const float *x, int64_t n, int64_t k, float *out, void *stream_) {
+    if (!x || !out || n < 1 || n >= ((int64_t)1 << 32) || k < 0 || k >= n)
+        return psl_fail(PSL_EINVAL, "psl_kth_smallest: bad argument");
+    cudaStream_t st = as_stream(stream_);
+    const uint32_t m = (uint32_t)n;
+    uint32_t *buf = nullptr;
+    void *scratch = nullptr;
+    float *dv = nullptr;
+    if (psl_malloc_async((void **)&buf, (size_t)m * 16, st) != cudaSuccess ||
+        psl_malloc_async(&scratch, sort_pairs_scratch_bytes(m), st) != cudaSuccess ||
+        psl_malloc_async((void **)&dv, 4, st) != cudaSuccess) {
+        if (buf) cudaFreeAsync(buf, st);
+        if (scratch) cudaFreeAsync(scratch, st);
+        return psl_fail(PSL_ENOMEM, "psl_kth_smallest: scratch");
+    }
+    uint32_t *k0 = buf, *v0 = buf + m, *k1 = buf + 2 * (size_t)m, *v1 = buf + 3 * (size_t)m;
+    const int grid = (int)std::min<uint32_t>((m + 255) / 256, (uint32_t)psl_sm_count() * 8);
+    k_float_keys<<<grid, 256, 0, st>>>(x, m, k0); PSL_NOTE_LAUNCH();
+    int alt = 0;
+    sort_pairs_u32(k0, v0, k1, v1, m, 32, nullptr, true, scratch, &alt, st);
+    k_key_value<<<1, 1, 0, st>>>(alt ? k1 : k0, (uint32_t)k, dv); PSL_NOTE_LAUNCH();
+    uint32_t herr = 0;
+    cudaMemcpyAsync(out, dv, 4, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&herr, sort_err_word(scratch), 4, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(buf, st);
+    cudaFreeAsync(scratch, st);
+    cudaFreeAsync(dv, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("psl_kth_smallest: ") + cudaGetErrorString(e));
+    if (herr) return psl_fail(PSL_ETIMEOUT, "psl_kth_smallest: sort look-back timed out");
+    return PSL_OK;
 }

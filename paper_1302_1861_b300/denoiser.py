@@ -46,11 +46,12 @@ def body(dose: torch.Tensor, rho: torch.Tensor) -> torch.Tensor:
 
 
 def dose_scale(dose: torch.Tensor) -> float:
-    """Normalisation of a dose for the network: its 99.9th percentile
-    (robust against single noisy voxels)."""
-    flat = dose.reshape(-1).float()
+    """Normalisation of a dose for the network: its 99.9th percentile, the
+    k-th smallest value with k = max(1, floor(0.999 n)) counted from 1
+    (robust against single noisy voxels), found on the device."""
+    flat = dose.reshape(-1).float().contiguous()
     k = max(1, int(0.999 * flat.numel()))
-    v = float(torch.kthvalue(flat.cpu(), k).values)
+    v = capi.kth_smallest(flat, k - 1)
     return v if v > 0 else 1.0
 
 

@@ -145,3 +145,18 @@ def test_denoiser_rejects_bad_volumes():
     with pytest.raises(capi.PslError):
         d.step(1e-3)                                           # nothing accumulated
     d.close()
+
+
+def test_kth_smallest_is_exact():
+    """psl_kth_smallest (the denoiser's dose scale) against a CPU sort:
+    random values with repeats, negatives and zeros, several k, n = 1."""
+    rng = np.random.default_rng(3)
+    for n in (1, 1000, 262_145):
+        x = rng.normal(0, 1, n).astype(np.float32) * rng.integers(0, 3, n).astype(np.float32)
+        x[: n // 7] = np.round(x[: n // 7], 1)
+        xs = np.sort(x)
+        xt = torch.from_numpy(x).cuda()
+        for k in sorted({0, n // 2, max(0, int(0.999 * n) - 1), n - 1}):
+            assert capi.kth_smallest(xt, k) == xs[k]
+    with pytest.raises(capi.PslError):
+        capi.kth_smallest(torch.zeros(4, device="cuda"), 4)
