@@ -89,6 +89,7 @@ struct Args {
     uint32_t *err;
     Queue e_out, p_out;
     float band_ln0, band_scale;
+    uint32_t *band_hist;      // band counts of the electrons queued for the next regrouping
 };
 
 // ----------------------------------------------------------- tables ------
@@ -275,11 +276,29 @@ __device__ __forceinline__ void annihilate(const Args &A, Rng &rng, float x, flo
     push_particle(A.p_out, A, 0, x, y, z, -a0, -a1, -a2, F_ME, wt, p0, p1, nchild, root);
 }
 
+// energy band of an electron (32 log bands above the cut-off)
+__device__ __forceinline__ int band_of(const Args &A, float e) {
+    int b = (int)((__logf(e) - A.band_ln0) * A.band_scale);
+    return min(max(b, 0), NBANDS - 1);
+}
+
+// Every kernel that queues electrons counts them by band in a block-shared
+// histogram (bh) and adds it to the queue's band histogram when it ends, so
+// the regrouping before the electron pass needs no counting pass of its own.
+__device__ __forceinline__ void band_hist_init(uint32_t *bh) {
+    if (threadIdx.x < NBANDS) bh[threadIdx.x] = 0;
+}
+__device__ __forceinline__ void band_hist_flush(const Args &A, const uint32_t *bh) {
+    __syncthreads();
+    if (threadIdx.x < NBANDS && bh[threadIdx.x]) atomicAdd(&A.band_hist[threadIdx.x], bh[threadIdx.x]);
+}
+
 // a charged secondary: queued for transport, or deposited in place
-__device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, uint32_t type, float T, float x, float y, float z,
-                             float u, float v, float w, float wt, uint32_t iv, uint32_t p0, uint32_t p1, uint32_t &nchild,
-                             uint32_t root) {
+__device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, uint32_t *bh, uint32_t type, float T,
+                             float x, float y, float z, float u, float v, float w, float wt, uint32_t iv, uint32_t p0,
+                             uint32_t p1, uint32_t &nchild, uint32_t root) {
     if (T > A.ecut && !(A.flags & PSL_PHYS_LOCAL_SECONDARIES)) {
+        atomicAdd(&bh[band_of(A, T)], 1u);
         push_particle(A.e_out, A, type, x, y, z, u, v, w, T, wt, p0, p1, nchild, root);
         return;
     }
@@ -487,7 +506,7 @@ __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
 }
 
 // the real interaction drawn by the last step; returns false when the photon ends
-__device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon &g) {
+__device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon &g, uint32_t *bh) {
     const uint32_t iv = photon_voxel(A, g);
     EventRng ev(g.draw);
     Rng &rng = ev.r;
@@ -523,7 +542,7 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
         float du = g.e * g.u - ep * nu, dv = g.e * g.v - ep * nv, dw = g.e * g.w - ep * nw;
         const float nn2 = du * du + dv * dv + dw * dw;
         if (nn2 > 0.0f) { const float in = rsqrtf(nn2); du *= in; dv *= in; dw *= in; } else { du = g.u; dv = g.v; dw = g.w; }
-        emit_charged(A, acc, rng, 1, te, g.x, g.y, g.z, du, dv, dw, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+        emit_charged(A, acc, rng, bh, 1, te, g.x, g.y, g.z, du, dv, dw, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
         g.e = ep; g.u = nu; g.v = nv; g.w = nw;
         if (g.e < A.pcut) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         photon_energy(A, g);
@@ -531,21 +550,24 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
     } else if (g.chan == 1u) {                                    // photoelectric
         acc.photo++;
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
-        emit_charged(A, acc, rng, 1, g.e, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+        emit_charged(A, acc, rng, bh, 1, g.e, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
         return false;
     }
     acc.pair++;                                                    // pair production
     if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
     const float avail = g.e - 2.0f * F_ME, eps = rng.next(A.rk, g.p0, g.p1);
     const float t1 = eps * avail, t2 = avail - t1;
-    emit_charged(A, acc, rng, 1, t1, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
-    emit_charged(A, acc, rng, 2, t2, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+    emit_charged(A, acc, rng, bh, 1, t1, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
+    emit_charged(A, acc, rng, bh, 2, t2, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
     return false;
 }
 
 __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
                                                 uint32_t cap, uint32_t *head) {
     __shared__ FeedSmem sm;
+    __shared__ uint32_t bh[NBANDS];
+    band_hist_init(bh);
+    __syncthreads();
     const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -579,7 +601,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
         // active; the other lanes keep taking Woodcock steps meanwhile.
         const unsigned rm = __ballot_sync(FULL, real);
         if (rm && (__popc(rm) >= PSL_G_DEFER || rm == live)) {
-            if (real) { alive = photon_interact(A, acc, g); real = false; }
+            if (real) { alive = photon_interact(A, acc, g, bh); real = false; }
         }
         if (alive && !real) {
             const int r = photon_step(A, acc, g);
@@ -588,6 +610,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
         }
     }
     flush_acc(A, acc, 8);
+    band_hist_flush(A, bh);
 }
 
 // ----------------------------------------------------------- electrons ---
@@ -748,7 +771,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
 
 // the hard event (Moller delta ray or bremsstrahlung photon) that ended the
 // last step; the electron stays in the voxel of that step
-__device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron &s) {
+__device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron &s, uint32_t *bh) {
     const uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
     EventRng ev(s.draw);
     Rng &rng = ev.r;
@@ -774,7 +797,7 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
                 float du = s.u, dv = s.v, dw = s.w;
                 rotate_dir(du, dv, dw, cd, sd_, -sph, -cph);              // azimuth phi + pi
                 rotate_dir(s.u, s.v, s.w, cp, sp_, sph, cph);
-                emit_charged(A, acc, rng, 1, W, s.x, s.y, s.z, du, dv, dw, s.wt, iv, s.p0, s.p1, s.nchild, s.root);
+                emit_charged(A, acc, rng, bh, 1, W, s.x, s.y, s.z, du, dv, dw, s.wt, iv, s.p0, s.p1, s.nchild, s.root);
                 s.t = tp;
             } else {                                              // hard bremsstrahlung
                 const float kph = A.wcb * expf(rng.next(A.rk, s.p0, s.p1) * logf(s.t / A.wcb));
@@ -792,6 +815,9 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                                                   uint32_t *head) {
     // electrons live for several steps and their queue reads hit L1, so
     // refills load directly (a staged feed measured 2 % slower here)
+    __shared__ uint32_t bh[NBANDS];
+    band_hist_init(bh);
+    __syncthreads();
     const uint32_t n = min(*n_ptr, cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -831,7 +857,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
         // active; the other lanes keep stepping meanwhile.
         const unsigned hm = __ballot_sync(FULL, hard);
         if (hm && (__popc(hm) >= PSL_E_DEFER || hm == live)) {
-            if (hard) { electron_hard(A, acc, s); hard = false; }
+            if (hard) { electron_hard(A, acc, s, bh); hard = false; }
         }
         if (alive && !hard) {
             const int r = electron_step(A, acc, s);
@@ -840,6 +866,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
         }
     }
     flush_acc(A, acc, 9);
+    band_hist_flush(A, bh);
 }
 
 // Slice of every caller particle of a materialised batch: the given one, or
@@ -889,7 +916,9 @@ __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first
                                                 uint32_t root0, int32_t slice, Particle *out, uint32_t *count,
                                                 const uint32_t *list, const uint32_t *list_off) {
     __shared__ PlanShared S;
+    __shared__ uint32_t bh[NBANDS];
     plan_shared_load(P, S);
+    band_hist_init(bh);
     __syncthreads();
     const uint32_t cap = n;
     uint32_t lbase = 0;
@@ -939,19 +968,19 @@ __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first
             c.type = (uint32_t)o.ptype;
             const uint32_t sl = slice >= 0 ? (uint32_t)slice : history_slice(c.pid_lo, c.pid_hi, A.rk, A.n_slices);
             c.root = (sl << ROOT_SLICE_SHIFT) | ((root0 + i) & ROOT_INDEX_MASK);
-            if (o.ptype == 0) queue_push(Queue{out, count, cap}, c, A.err);
-            else queue_push(A.e_out, c, A.err);
+            if (o.ptype == 0) {
+                queue_push(Queue{out, count, cap}, c, A.err);
+            } else {
+                atomicAdd(&bh[band_of(A, c.e)], 1u);
+                queue_push(A.e_out, c, A.err);
+            }
         }
     }
     flush_acc(A, acc, 8);
+    band_hist_flush(A, bh);
 }
 
 // ------------------------------------------------------------ band sort ---
-__device__ __forceinline__ int band_of(const Args &A, float e) {
-    int b = (int)((__logf(e) - A.band_ln0) * A.band_scale);
-    return min(max(b, 0), NBANDS - 1);
-}
-
 __device__ __forceinline__ const Particle *pick(const Particle *a, uint32_t na, const Particle *b, uint32_t i) {
     return i < na ? a + i : b + (i - na);
 }
@@ -1107,6 +1136,18 @@ void workspace_free(Workspace *w) {
     delete w;
 }
 
+// Resident 256-thread blocks of the source kernel per SM: its grid is one
+// wave, since each warp takes an equal contiguous run of histories.
+static int source_blocks_per_sm() {
+    static int nb = 0;
+    if (!nb) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_source, 256, 0) != cudaSuccess || v < 1) v = 4;
+        nb = v;
+    }
+    return nb;
+}
+
 // Batch-by-batch order (PSL_ORDER_BATCH): histories per window, so that a
 // batch of a window (binomial, mean W / nb) stays within one transport pass
 // of `chunk` primaries by 8 standard deviations: W / nb = (sqrt(chunk + 16) - 4)^2.
@@ -1192,7 +1233,7 @@ struct Runner {
     Workspace *w = nullptr;
     Args A{};
     bool timing = false;
-    int grid_t = 0, grid_m = 0;
+    int grid_t = 0, grid_m = 0, grid_src = 0;
     int64_t chunk = 0;
 
     int prepare(const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally *t, uint64_t seed, int64_t need,
@@ -1231,12 +1272,14 @@ struct Runner {
         A.ledger = t->ledger;
         A.hist_dep = nullptr; A.hist_esc = nullptr; A.hist_events = nullptr;
         A.err = w->cnt + 9;
+        A.band_hist = w->cnt + 16;
         A.band_ln0 = logf(P.electron_cut);
         A.band_scale = (float)(NBANDS / log(20.0 / P.electron_cut));
         cudaMemsetAsync(w->cnt, 0, 128 * sizeof(uint32_t), st);
         timing = psl_timer_on() && !capturing;
         grid_t = psl_sm_count() * t->grid_mult;
         grid_m = psl_sm_count() * 8;
+        grid_src = psl_sm_count() * source_blocks_per_sm();
         return PSL_OK;
     }
 
@@ -1266,7 +1309,9 @@ struct Runner {
         auto band_sort = [&](const Particle *a, uint32_t na, const Particle *bq, const uint32_t *nb, uint32_t capb) {
             void *tk = nullptr;
             tb(PK_BAND, &tk);
-            k_band_count<<<gm(), 256, 0, st>>>(A, a, na, bq, nb, capb, hist); PSL_NOTE_LAUNCH();
+            // the queue's electrons were counted by the kernels that queued
+            // them; only caller electrons (a materialised batch) are counted here
+            if (na) { k_band_count<<<gm(), 256, 0, st>>>(A, a, na, bq, nb, 0u, hist); PSL_NOTE_LAUNCH(); }
             k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
             k_band_scatter<<<gm(), 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH();
             te(PK_BAND, tk);
@@ -1303,7 +1348,7 @@ struct Runner {
                 cudaMemsetAsync(w->cnt + 7, 0, 4, st);
                 void *tk = nullptr;
                 tb(PK_SOURCE, &tk);
-                k_source<<<grid_m, 256, 0, st>>>(a2, J.P, J.list ? J.first : J.first + a0 * J.stride, J.stride, cp,
+                k_source<<<grid_src, 256, 0, st>>>(a2, J.P, J.list ? J.first : J.first + a0 * J.stride, J.stride, cp,
                                                  (uint32_t)a0, J.slice, w->Q, w->cnt + 7, J.list, J.list_off);
                 PSL_NOTE_LAUNCH();
                 te(PK_SOURCE, tk);
