@@ -494,7 +494,9 @@ __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
     const uint32_t iv = ((uint32_t)fz * (uint32_t)A.ny + (uint32_t)fy) * (uint32_t)A.nx + (uint32_t)fx;
     const float mr = __ldg(A.mrho + iv);
     const float rho = fabsf(mr);
-    const float4 c = lerp4(mr < 0.0f ? A.tab.ph1 : A.tab.ph0, g.ti, g.tf);
+    // both materials' rows are loaded with the density, not after it
+    const float4 c0 = lerp4(A.tab.ph0, g.ti, g.tf), c1 = lerp4(A.tab.ph1, g.ti, g.tf);
+    const float4 c = mr < 0.0f ? c1 : c0;
     const float mc = __fmul_rn(rho, c.x), mpe = __fmul_rn(rho, c.y), mpp = __fmul_rn(rho, c.z);
     const float mu = __fadd_rn(__fadd_rn(mc, mpe), mpp);          // = mu_of(rho, c)
     if (mu > g.mumax) atomicOr(A.err, 8u);
