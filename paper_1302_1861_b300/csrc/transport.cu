@@ -43,6 +43,9 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #ifndef PSL_BAND_DESC
 #define PSL_BAND_DESC 1
 #endif
+#ifndef SRC_RUN
+#define SRC_RUN 256u                   // consecutive histories a warp of the source stage takes at a time
+#endif
 #ifndef PSL_G_DEFER
 #define PSL_G_DEFER 24                 // lanes with a pending real photon interaction before a warp runs them
 #endif
@@ -933,16 +936,18 @@ __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first
     }
     Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int lane = threadIdx.x & 31;
-    // each warp takes a contiguous run of histories, 32 at a time, and each
-    // lane carries its (group, segment) to the next 32: consecutive histories
-    // stay in a segment or step to the next, so the searches are rare
+    // each warp takes runs of SRC_RUN consecutive histories, 32 at a time,
+    // and each lane carries its (group, segment) to the next 32: consecutive
+    // histories stay in a segment or step to the next, so the searches are
+    // rare; the runs are dealt out in turn, so that all warps read nearby
+    // records of the reading order at the same time
     const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
-    const uint32_t per = ((n + n_warps - 1) / n_warps + 31u) & ~31u;
-    const uint32_t i0 = min(n, (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * per);
-    const uint32_t i1 = min(n, i0 + per);
+    const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t n_runs = (n + SRC_RUN - 1) / SRC_RUN;
     int g = -1;
     int64_t q = -1;
-    for (uint32_t ib = i0; ib < i1; ib += 32) {
+    for (uint32_t run = gw; run < n_runs; run += n_warps)
+    for (uint32_t ib = run * SRC_RUN, i1 = min(n, ib + SRC_RUN), i0 = ib; ib < i1; ib += 32) {
         const uint32_t i = ib + lane;
         const bool ok = i < i1;
         const int64_t h = list ? (ok ? first + (int64_t)__ldg(list + lbase + i) : first) : first + (int64_t)i * stride;
