@@ -412,12 +412,14 @@ def main():
 # Per-event figures of the transport kernels measured with ncu on the 1e7-
 # history case of this workload (all launches of one run; the counts scale
 # with histories): thread instructions per event (smsp__thread_inst_executed
-# / events) and DRAM bytes per history (dram__bytes_read + write).  See
-# profiles/transport_k_electron_k_photon_psl-10x10-slab64.md.  They hold for
-# the kernels they were measured on; re-measure after changing the kernels.
-THREAD_INST_PER_ELECTRON_STEP = 582.2
-THREAD_INST_PER_WOODCOCK_STEP = 523.4
-DRAM_BYTES_PER_HISTORY = {"electron": 28.22, "photon": 60.14}
+# / events) and DRAM bytes per history (dram__bytes_read + write), from
+#   ncu --metrics smsp__thread_inst_executed.sum,dram__bytes_read.sum,...
+#       -k regex:"k_electron|k_photon" python bench.py --histories 10000000 ...
+# They hold for the kernels they were measured on; re-measure after changing
+# the kernels.
+THREAD_INST_PER_ELECTRON_STEP = 584.4
+THREAD_INST_PER_WOODCOCK_STEP = 529.6
+DRAM_BYTES_PER_HISTORY = {"electron": 28.28, "photon": 58.97}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
 
