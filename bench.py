@@ -16,7 +16,7 @@ stream), `cpu_baseline` (the oracle on a bounded sample on the host cores),
 `time_to_1pct` (histories and seconds for 1 % isocentre uncertainty,
 extrapolated from the measured standard error), `clocks`, `gpu_launches`.
 
-`--impl reference` times the CPU oracle (the reference arm of this build).
+`--impl reference` times the CPU oracle as the reference arm, on the same workload.
 """
 from __future__ import annotations
 

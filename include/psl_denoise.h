@@ -3,7 +3,8 @@
  * Carlo dose: a small BF16 3D convolutional encoder-decoder that maps a
  * low-history dose plus density to the high-history dose.  The paper has no
  * such step; it is trained on dose pairs the PSL method itself produces, and
- * the plain Monte Carlo run to 1 % uncertainty is its fallback and judge.
+ * the plain Monte Carlo run to 1 % uncertainty is its fallback and the reference
+ * its accuracy is measured against.
  *
  * Conventions as in psl.h: return 0 (PSL_OK) or a negative PSL_E* code with
  * the text in psl_last_error(); device pointers are caller-owned; `stream` is
