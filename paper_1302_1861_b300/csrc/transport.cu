@@ -1290,11 +1290,59 @@ struct Runner {
         return PSL_OK;
     }
 
-    // One batch.  check_from: the first generation after which the host reads
-    // the queue counts (and stops when they are empty); a negative value
-    // launches RUN_GENERATIONS generations with no host check (graph capture).
-    int run(const Job &J, int check_from) {
-        const bool sync_gens = check_from >= 0;
+    // Queues carried from chunk to chunk (and job to job) of one call: after
+    // a chunk's electron pass its secondaries (photons in P[pc ^ 1],
+    // electrons in E[ec ^ 1]) are not transported generation by generation
+    // at once but join the next chunk's passes; drain() finishes them after
+    // the last chunk.  Particles carry their own random streams and tally
+    // slices, so the order changes nothing in the result.
+    int pc = 0, ec = 0, gen_now = 0;
+    bool begun = false, carried = false;
+
+    uint32_t *cP(int k) { return w->cnt + k; }
+    uint32_t *cE(int k) { return w->cnt + 2 + k; }
+
+    void tb(int k, void **tok) { if (timing) psl_timer_begin(k, st, tok); }
+    void te(int k, void *tok) { if (tok) psl_timer_end(k, st, tok); }
+    // generations after the first two are small: a smaller grid starts faster
+    int gm() const { return gen_now >= 2 ? psl_sm_count() : grid_m; }
+    int gt() const { return gen_now >= 2 ? psl_sm_count() : grid_t; }
+
+    void band_sort(const Particle *a, uint32_t na) {
+        uint32_t *hist = w->cnt + 16, *cursor = w->cnt + 48, *cS = w->cnt + 4;
+        void *tk = nullptr;
+        tb(PK_BAND, &tk);
+        // the queue's electrons were counted by the kernels that queued them;
+        // only caller electrons (a materialised batch) are counted here
+        if (na) { k_band_count<<<gm(), 256, 0, st>>>(A, a, na, w->E[ec], cE(ec), 0u, hist); PSL_NOTE_LAUNCH(); }
+        k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
+        k_band_scatter<<<gm(), 256, 0, st>>>(A, a, na, w->E[ec], cE(ec), w->cap_e, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH();
+        te(PK_BAND, tk);
+    }
+    void photon_pass(const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
+        Args a2 = A;
+        a2.e_out = Queue{w->E[ec], cE(ec), w->cap_e};
+        a2.p_out = Queue{w->P[pc ^ 1], cP(pc ^ 1), w->cap_p};
+        cudaMemsetAsync(w->cnt + 5, 0, 4, st);
+        void *tk = nullptr;
+        tb(PK_PHOTON, &tk);
+        k_photon<<<gt(), 256, 0, st>>>(a2, src, nptr, nfix, cap, w->cnt + 5); PSL_NOTE_LAUNCH();
+        te(PK_PHOTON, tk);
+    }
+    void electron_pass() {
+        Args a2 = A;
+        a2.e_out = Queue{w->E[ec ^ 1], cE(ec ^ 1), w->cap_e};
+        a2.p_out = Queue{w->P[pc ^ 1], cP(pc ^ 1), w->cap_p};
+        cudaMemsetAsync(w->cnt + 6, 0, 4, st);
+        void *tk = nullptr;
+        tb(PK_ELECTRON, &tk);
+        k_electron<<<gt(), 256, 0, st>>>(a2, w->S, w->cnt + 4, w->cap_s, w->cnt + 6); PSL_NOTE_LAUNCH();
+        te(PK_ELECTRON, tk);
+    }
+
+    // One job, chunk by chunk: its primaries (source stage or caller
+    // particles) and the secondaries carried from the chunk before.
+    int run(const Job &J) {
         A.tally = tally->t;
         A.nvox = tally->nvox;
         A.n_slices = (uint32_t)tally->n_batches;
@@ -1304,54 +1352,26 @@ struct Runner {
             k_assign_slices<<<grid_m, 256, 0, st>>>(A, const_cast<Particle *>(J.p), J.nph, J.nel, J.cap, J.slice);
             PSL_NOTE_LAUNCH();
         }
-        uint32_t *cP[2] = {w->cnt + 0, w->cnt + 1}, *cE[2] = {w->cnt + 2, w->cnt + 3}, *cS = w->cnt + 4;
-        uint32_t *head = w->cnt + 5, *hist = w->cnt + 16, *cursor = w->cnt + 48;
-        int pc = 0, ec = 0;
-        auto tb = [&](int k, void **tok) { if (timing) psl_timer_begin(k, st, tok); };
-        auto te = [&](int k, void *tok) { if (tok) psl_timer_end(k, st, tok); };
-        // generations after the first two are small: a smaller grid starts faster
-        int gen_now = 0;
-        auto gm = [&]() { return gen_now >= 2 ? psl_sm_count() : grid_m; };
-        auto gt = [&]() { return gen_now >= 2 ? psl_sm_count() : grid_t; };
-        auto band_sort = [&](const Particle *a, uint32_t na, const Particle *bq, const uint32_t *nb, uint32_t capb) {
-            void *tk = nullptr;
-            tb(PK_BAND, &tk);
-            // the queue's electrons were counted by the kernels that queued
-            // them; only caller electrons (a materialised batch) are counted here
-            if (na) { k_band_count<<<gm(), 256, 0, st>>>(A, a, na, bq, nb, 0u, hist); PSL_NOTE_LAUNCH(); }
-            k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
-            k_band_scatter<<<gm(), 256, 0, st>>>(A, a, na, bq, nb, capb, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH();
-            te(PK_BAND, tk);
-        };
-        auto photon_pass = [&](const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
-            Args a2 = A;
-            a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
-            a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
-            cudaMemsetAsync(head, 0, 4, st);
-            void *tk = nullptr;
-            tb(PK_PHOTON, &tk);
-            k_photon<<<gt(), 256, 0, st>>>(a2, src, nptr, nfix, cap, head); PSL_NOTE_LAUNCH();
-            te(PK_PHOTON, tk);
-        };
-        auto electron_pass = [&]() {
-            Args a2 = A;
-            a2.e_out = Queue{w->E[ec ^ 1], cE[ec ^ 1], w->cap_e};
-            a2.p_out = Queue{w->P[pc ^ 1], cP[pc ^ 1], w->cap_p};
-            cudaMemsetAsync(head + 1, 0, 4, st);
-            void *tk = nullptr;
-            tb(PK_ELECTRON, &tk);
-            k_electron<<<gt(), 256, 0, st>>>(a2, w->S, cS, w->cap_s, head + 1); PSL_NOTE_LAUNCH();
-            te(PK_ELECTRON, tk);
-        };
+        if (!begun) {
+            cudaMemsetAsync(w->cnt, 0, 5 * sizeof(uint32_t), st);
+            pc = 0; ec = 0;
+            begun = true;
+        }
         const int64_t total = J.lazy ? J.n : std::max(J.nph, J.nel);
         for (int64_t a0 = 0; a0 < total; a0 += chunk) {
-            pc = 0; ec = 0;
             gen_now = 0;
-            cudaMemsetAsync(w->cnt, 0, 5 * sizeof(uint32_t), st);
+            if (carried) {
+                // the last chunk's outputs are this chunk's inputs
+                pc ^= 1; ec ^= 1;
+                cudaMemsetAsync(cP(pc ^ 1), 0, 4, st);
+                cudaMemsetAsync(cE(ec ^ 1), 0, 4, st);
+            }
+            const Particle *ca = nullptr;
+            uint32_t na = 0;
             if (J.lazy) {
                 const uint32_t cp = (uint32_t)std::min<int64_t>(J.n - a0, chunk);
                 Args a2 = A;
-                a2.e_out = Queue{w->E[ec], cE[ec], w->cap_e};
+                a2.e_out = Queue{w->E[ec], cE(ec), w->cap_e};
                 cudaMemsetAsync(w->cnt + 7, 0, 4, st);
                 void *tk = nullptr;
                 tb(PK_SOURCE, &tk);
@@ -1360,41 +1380,55 @@ struct Runner {
                 PSL_NOTE_LAUNCH();
                 te(PK_SOURCE, tk);
                 photon_pass(w->Q, w->cnt + 7, 0, cp);
-                band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
             } else {
                 const uint32_t cp = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(J.nph - a0, chunk));
-                const uint32_t ce = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(J.nel - a0, chunk));
+                na = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(J.nel - a0, chunk));
+                ca = J.p + (J.cap - a0 - na);
                 if (cp) photon_pass(J.p + a0, nullptr, cp, cp);
-                band_sort(J.p + (J.cap - a0 - ce), ce, w->E[ec], cE[ec], w->cap_e);
             }
+            if (carried) photon_pass(w->P[pc], cP(pc), 0, w->cap_p);
+            band_sort(ca, na);
             electron_pass();
-            for (int gen = 0;; ++gen) {
-                if (sync_gens && gen >= check_from) {
-                    cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-                    cudaError_t e = cudaStreamSynchronize(st);
-                    if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport: ") + cudaGetErrorString(e));
-                    if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport: particle queue overflow");
-                    if (w->host[pc ^ 1] == 0 && w->host[2 + (ec ^ 1)] == 0) break;
-                    if (gen >= MAX_GEN) return psl_fail(PSL_EOVERFLOW, "transport: too many secondary generations");
-                } else if (!sync_gens && gen >= RUN_GENERATIONS) {
-                    break;
-                }
-                // next generation: swap current/next, clear the new "next"
-                gen_now = gen + 1;
-                pc ^= 1; ec ^= 1;
-                cudaMemsetAsync(cP[pc ^ 1], 0, 4, st);
-                cudaMemsetAsync(cE[ec ^ 1], 0, 4, st);
-                photon_pass(w->P[pc], cP[pc], 0, w->cap_p);
-                band_sort(nullptr, 0, w->E[ec], cE[ec], w->cap_e);
-                electron_pass();
-            }
-            if (!sync_gens) {
-                // the last generation's output must be empty (checked by finish())
-                cudaMemcpyAsync(w->cnt + 10, cP[pc ^ 1], 4, cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(w->cnt + 11, cE[ec ^ 1], 4, cudaMemcpyDeviceToDevice, st);
-                k_accumulate_leftover<<<1, 1, 0, st>>>(w->cnt); PSL_NOTE_LAUNCH();
-            }
+            carried = true;
         }
+        return PSL_OK;
+    }
+
+    // The generations left after the last chunk.  check_from: the first
+    // generation after which the host reads the queue counts (and stops when
+    // they are empty); a negative value launches RUN_GENERATIONS generations
+    // with no host check (graph capture) and leaves the count of undone
+    // particles for finish().
+    int drain(int check_from) {
+        if (!carried) return PSL_OK;
+        const bool sync_gens = check_from >= 0;
+        for (int gen = 0;; ++gen) {
+            if (sync_gens && gen >= check_from) {
+                cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+                cudaError_t e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport: ") + cudaGetErrorString(e));
+                if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport: particle queue overflow");
+                if (w->host[pc ^ 1] == 0 && w->host[2 + (ec ^ 1)] == 0) break;
+                if (gen >= MAX_GEN) return psl_fail(PSL_EOVERFLOW, "transport: too many secondary generations");
+            } else if (!sync_gens && gen >= RUN_GENERATIONS) {
+                break;
+            }
+            // next generation: swap current/next, clear the new "next"
+            gen_now = gen + 1;
+            pc ^= 1; ec ^= 1;
+            cudaMemsetAsync(cP(pc ^ 1), 0, 4, st);
+            cudaMemsetAsync(cE(ec ^ 1), 0, 4, st);
+            photon_pass(w->P[pc], cP(pc), 0, w->cap_p);
+            band_sort(nullptr, 0);
+            electron_pass();
+        }
+        if (!sync_gens) {
+            // the last generation's output must be empty (checked by finish())
+            cudaMemcpyAsync(w->cnt + 10, cP(pc ^ 1), 4, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(w->cnt + 11, cE(ec ^ 1), 4, cudaMemcpyDeviceToDevice, st);
+            k_accumulate_leftover<<<1, 1, 0, st>>>(w->cnt); PSL_NOTE_LAUNCH();
+        }
+        carried = false;
         return PSL_OK;
     }
 
@@ -1452,7 +1486,8 @@ static int transport_impl(const psl_phantom_t *ph, const psl_physics_t *phys, ps
     R.A.hist_events = hist_events;
     batch->consumed = 1;
     if (!batch->lazy) { k_ledger_add<<<1, 1, 0, st>>>(tally->ledger, (const unsigned long long *)(batch->counts + 2)); PSL_NOTE_LAUNCH(); }
-    if ((rc = R.run(job_of(batch, b), 0))) return rc;
+    if ((rc = R.run(job_of(batch, b)))) return rc;
+    if ((rc = R.drain(0))) return rc;
     return R.finish();
 }
 
@@ -1494,7 +1529,10 @@ static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_p
     J.first = first; J.stride = 1; J.n = n; J.slice = PSL_SLICE_BY_HISTORY;
     const int check = capturing ? -1 : UNCHECKED_GENERATIONS;
     const int64_t W = batch_order_window(tally, n);
-    if (W <= 0) return R.run(J, check);
+    if (W <= 0) {
+        if ((rc = R.run(J))) return rc;
+        return R.drain(check);
+    }
     if (!capturing && (rc = batch_order_ensure(tally, W))) return rc;   // (a capture is set up beforehand)
     Workspace *w = tally->ws;
     if (w->bm_cap < W) return psl_fail(PSL_EINVAL, "psl_run: batch-order buffers not set up");
@@ -1516,10 +1554,10 @@ static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_p
             Jb.slice = (int32_t)b;
             Jb.list = w->bm_vals[alt];
             Jb.list_off = w->bm_off;
-            if ((rc = R.run(Jb, check))) return rc;
+            if ((rc = R.run(Jb))) return rc;
         }
     }
-    return PSL_OK;
+    return R.drain(check);
 }
 
 extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
