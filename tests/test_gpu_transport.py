@@ -155,6 +155,16 @@ def test_event_parity_config2_sampled():
     assert rate >= 0.95
 
 
+@pytest.mark.parametrize("cfg", [3, 4])
+def test_event_parity_full_size_ct_plans_sampled(cfg):
+    """Full-size CT plans (30x30 field with jaws and fluence, 4e7 records,
+    1e9 histories; IMRT plan of 218 segments, 5e8 histories): per-history
+    parity on a range deep inside each plan."""
+    w = inputs.config3() if cfg == 3 else inputs.config4()
+    rate, _ = _event_parity(w, 3000, first=w.n_histories * 3 // 5)
+    assert rate >= 0.95
+
+
 def test_dose_parity_config1():
     w = inputs.config1()
     dw = engine.upload(w)
