@@ -399,15 +399,17 @@ PSL_API int transport_trace(const psl_phantom_t *phantom, const psl_physics_t *p
  * Runs histories [first, first+n) of the plan in reading order (or window by
  * window, batch by batch: see psl_tally_set_order), each
  * history's deposits into its tally slice (PSL_SLICE_BY_HISTORY): source
- * stage and transport of every beam/segment, with no host synchronisation
- * between passes: each pass is followed by 3 secondary generations launched
- * unchecked, after which the host reads the queue counts once per further
- * generation (usually once per pass).  use_graph = 1 records the whole
- * sequence once as a CUDA graph with a fixed budget of 10 generations per
- * pass (kernels of an empty generation exit at once), keeps it in the tally
- * for this plan, range, phantom and settings, and replays it with a single
- * launch on `stream`; the first such call sets up outside the capture.  Synchronises stream at the end; PSL_EOVERFLOW if a
- * queue overflowed or secondaries were left after the budget. */
+ * stage and transport of every beam/segment, in chunks of the queue depth,
+ * each chunk's secondaries joining the next chunk's passes, with no host
+ * synchronisation until the last chunk; its secondaries are then drained
+ * generation by generation: 3 generations launched unchecked, after which
+ * the host reads the queue counts once per further generation.  use_graph = 1
+ * records the whole sequence once as a CUDA graph with a fixed budget of 10
+ * drain generations (kernels of an empty generation exit at once), keeps it
+ * in the tally for this plan, range, phantom and settings, and replays it
+ * with a single launch on `stream`; the first such call sets up outside the
+ * capture.  Synchronises stream at the end; PSL_EOVERFLOW if a queue
+ * overflowed or secondaries were left after the budget. */
 PSL_API int psl_run(const psl_plan_t *plan, const psl_phantom_t *phantom, const psl_physics_t *physics,
                     psl_tally_t *tally, int64_t first, int64_t n, int32_t use_graph, void *stream);
 
