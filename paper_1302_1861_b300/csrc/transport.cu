@@ -128,29 +128,47 @@ __global__ void k_range_intervals(double *iv, double wcc, double wcb) {
     iv[i] = h * acc;
 }
 
-__global__ void k_range_table(double *iv, float2 *rt, float *irt, float *igrid, double wcc, double wcb) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One block: the running sum of the interval ranges in order (one thread),
+// then the node values and the inverse table (all threads).  The inverse
+// node j takes the same pair of forward nodes as a walk along the nodes
+// would (ln R is increasing), found by binary search.
+__global__ void __launch_bounds__(1024) k_range_table(double *iv, float2 *rt, float *irt, float *igrid, double wcc,
+                                                      double wcb) {
+    __shared__ double liv[NT];
     const double l0 = log(T_LO), dl = (log(T_HI) - log(T_LO)) / (NT - 1);
-    double R = 0.0;
-    for (int i = 0; i < NT; ++i) {
-        R += iv[i];
-        iv[i] = R;                                   // keep the cumulative range for the inverse
-        const double T = exp(l0 + dl * i);
-        rt[i] = make_float2((float)R, (float)(T * dl / el_stop_restricted(T, wcc, wcb)));
+    if (threadIdx.x == 0) {
+        double R = 0.0;
+        for (int i = 0; i < NT; ++i) {
+            R += iv[i];
+            iv[i] = R;                               // keep the cumulative range for the inverse
+        }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) {
+        const double R = iv[i], T = exp(l0 + dl * i);
+        rt[i] = make_float2((float)R, (float)(T * dl / el_stop_restricted(T, wcc, wcb)));
+        liv[i] = i > 0 ? log(R) : 0.0;
+    }
+    __syncthreads();
     // inverse: ln T at NT uniform points of ln R over [R_1, R_{NT-1}], by
     // interpolating ln T linearly in ln R between the forward nodes
-    const double a = log(iv[1]), b = log(iv[NT - 1]), dr = (b - a) / (NT - 1);
-    int i = 1;
-    for (int j = 0; j < NT; ++j) {
+    const double a = liv[1], b = liv[NT - 1], dr = (b - a) / (NT - 1);
+    for (int j = threadIdx.x; j < NT; j += blockDim.x) {
         const double lr = a + dr * j;
-        while (i < NT - 2 && log(iv[i + 1]) < lr) ++i;
-        const double r0 = log(iv[i]), r1 = log(iv[i + 1]);
+        int lo = 2, hi = NT;                         // first k >= 2 with ln R_k >= lr
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (liv[mid] < lr) lo = mid + 1; else hi = mid;
+        }
+        const int i = min(max(lo - 1, 1), NT - 2);
+        const double r0 = liv[i], r1 = liv[i + 1];
         const double f = (lr - r0) / (r1 - r0);
         irt[j] = (float)(l0 + dl * (i + f));
     }
-    igrid[0] = (float)a;
-    igrid[1] = (float)(1.0 / dr);
+    if (threadIdx.x == 0) {
+        igrid[0] = (float)a;
+        igrid[1] = (float)(1.0 / dr);
+    }
 }
 
 __global__ void k_rho_max(const uint8_t *mat, const float *rho, int64_t n, int *out, float *mrho) {
@@ -1093,7 +1111,7 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
     PSL_CUDA(cudaMalloc((void **)&ig, 2 * sizeof(float)));
     PSL_CUDA(cudaMalloc((void **)&t.irng, NT * sizeof(float)));
     k_range_intervals<<<(NT + 127) / 128, 128, 0, st>>>(iv, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
-    k_range_table<<<1, 32, 0, st>>>(iv, t.rng, t.irng, ig, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    k_range_table<<<1, 1024, 0, st>>>(iv, t.rng, t.irng, ig, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaMemcpyAsync(t.igrid, ig, 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
     PSL_CUDA(cudaStreamSynchronize(st));
     cudaFree(iv);
