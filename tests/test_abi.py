@@ -50,3 +50,8 @@ def test_invalid_arguments_fail_cleanly_without_gpu():
     assert b"bad bin counts" in L.psl_last_error()
     assert L.psl_plan_create(None, None, 0, 100.0, 10, 1, ctypes.byref(h), None) == capi.PSL_EINVAL
     assert L.psl_tally_set_order(None, capi.ORDER_BATCH) == capi.PSL_EINVAL
+    # a tally of 2^33 voxels is refused before any device work (voxels are indexed in 32 bits)
+    big = capi.Phantom(2048, 2048, 2048, 0.1, 0.1, 0.1, (capi.f32 * 3)(0, 0, 0), None, None)
+    assert L.psl_tally_create(ctypes.byref(big), 10, ctypes.byref(h)) == capi.PSL_EINVAL
+    assert b"2^31" in L.psl_last_error()
+    assert L.psl_kth_smallest(None, 10, 0, None, None) == capi.PSL_EINVAL
