@@ -265,7 +265,7 @@ def main():
     ap.add_argument("--ct", type=int, default=12)
     ap.add_argument("--lo-per-geometry", type=int, default=10)
     ap.add_argument("--n-hi", type=float, default=2e9)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=80)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=1)
     a = ap.parse_args()
