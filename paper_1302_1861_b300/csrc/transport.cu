@@ -713,83 +713,89 @@ __device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &
 // caller may defer it), E_ON otherwise.
 enum { E_END = 0, E_ON = 1, E_HARD = 2 };
 
+// An electron whose step ends below the cut-off (not at a hard event) ends in
+// that same call, in the voxel the step ended in, so that its lane takes the
+// next electron at once instead of idling through one more pass of the loop;
+// the deposits and draws are those of ending at the start of the next step.
 __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &s) {
-    const uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
-    if (s.t <= A.ecut || ++s.steps > MAX_E_STEPS) {
-        if (s.steps > MAX_E_STEPS) atomicOr(A.err, PSL_DEV_ERR_STEPS);
-        electron_end(A, acc, s, iv);
-        return E_END;
-    }
-    acc.steps++;
-    count_event(A, s.root);
-    EventRng ev(s.draw);
-    Rng &rng = ev.r;
-    rng.align();                                                  // the step's draws (at most 3)
-    rng.fill(A.rk, s.p0, s.p1);
-    if (s.nlam < 0.0f) s.nlam = -ln_uniform(rng.take());       // a new mean free path count
-    const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
-    const float rho = fabsf(__ldg(A.mrho + iv));
-    int ti; float tf;
-    tab_pos(A.tab, s.t, ti, tf);
-    const float4 el = lerp4(A.tab.el, ti, tf);
-    // hard cross sections vanish below their thresholds (guard the interpolation)
-    const float sig = hard_on ? rho * ((s.t > 2.0f * A.wcc ? el.y : 0.0f) + (s.t > A.wcb ? el.z : 0.0f)) : 0.0f;
-    const float s_hard = sig > 0.0f ? __fdividef(s.nlam, sig) : INFINITY;
-    // distance to the voxel boundary
-    float s_bound = INFINITY;
-    int axis = -1, cross = 0;
-    {
-        const float d[3] = {s.u, s.v, s.w}, p[3] = {s.x, s.y, s.z}, vv[3] = {A.vx, A.vy, A.vz};
-        const int ii[3] = {s.ix, s.iy, s.iz};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float t;
-            if (d[k] > 0.0f) t = __fdividef((float)(ii[k] + 1) * vv[k] - p[k], d[k]);
-            else if (d[k] < 0.0f) t = __fdividef((float)ii[k] * vv[k] - p[k], d[k]);
-            else continue;
-            t = fmaxf(t, 0.0f);
-            if (t < s_bound) { s_bound = t; axis = k; cross = d[k] > 0.0f ? 1 : -1; }
+    uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
+    if (!(s.t <= A.ecut) && ++s.steps <= MAX_E_STEPS) {
+        acc.steps++;
+        count_event(A, s.root);
+        EventRng ev(s.draw);
+        Rng &rng = ev.r;
+        rng.align();                                                  // the step's draws (at most 3)
+        rng.fill(A.rk, s.p0, s.p1);
+        if (s.nlam < 0.0f) s.nlam = -ln_uniform(rng.take());       // a new mean free path count
+        const bool hard_on = !(A.flags & PSL_PHYS_NO_HARD);
+        const float rho = fabsf(__ldg(A.mrho + iv));
+        int ti; float tf;
+        tab_pos(A.tab, s.t, ti, tf);
+        const float4 el = lerp4(A.tab.el, ti, tf);
+        // hard cross sections vanish below their thresholds (guard the interpolation)
+        const float sig = hard_on ? rho * ((s.t > 2.0f * A.wcc ? el.y : 0.0f) + (s.t > A.wcb ? el.z : 0.0f)) : 0.0f;
+        const float s_hard = sig > 0.0f ? __fdividef(s.nlam, sig) : INFINITY;
+        // distance to the voxel boundary
+        float s_bound = INFINITY;
+        int axis = -1, cross = 0;
+        {
+            const float d[3] = {s.u, s.v, s.w}, p[3] = {s.x, s.y, s.z}, vv[3] = {A.vx, A.vy, A.vz};
+            const int ii[3] = {s.ix, s.iy, s.iz};
+    #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float t;
+                if (d[k] > 0.0f) t = __fdividef((float)(ii[k] + 1) * vv[k] - p[k], d[k]);
+                else if (d[k] < 0.0f) t = __fdividef((float)ii[k] * vv[k] - p[k], d[k]);
+                else continue;
+                t = fmaxf(t, 0.0f);
+                if (t < s_bound) { s_bound = t; axis = k; cross = d[k] > 0.0f ? 1 : -1; }
+            }
         }
-    }
-    const float tlim = fmaxf(0.9f * s.t, A.ecut);
-    const float rlim = range_of(A.tab, tlim);
-    const float s_max = (s.r - rlim) * __frcp_rn(rho);
-    int which;
-    float step;
-    if (s_hard <= s_bound && s_hard <= s_max) { which = 0; step = s_hard; }
-    else if (s_bound <= s_max) { which = 1; step = s_bound; }
-    else { which = 2; step = s_max; }
-    // energy at the end of the step: the 10 % limit exactly, else from the
-    // range left; the range itself is carried, not recomputed from the energy
-    float tend, rend;
-    if (which == 2) { tend = tlim; rend = rlim; }
-    else { rend = s.r - rho * step; tend = fmaxf(energy_of_range(A.tab, rend), tlim); }
-    const float th0 = highland(s.t, step, rho);
-    deposit(A, acc, iv, s.t - tend, s.wt, s.root);
-    s.t = tend;
-    s.r = rend;
-    s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
-    s.nlam -= step * sig;
-    if (!(A.flags & PSL_PHYS_NO_MSC) && step > 0.0f) {
-        const float l2 = -2.0f * ln_uniform(rng.take());
-        const float th = th0 * (l2 * rsqrtf(l2));
-        float st, ct, sp, cp;
-        sincosf(th, &st, &ct);
-        st = fabsf(st);
-        sincos_2pi(rng.take(), &sp, &cp);
-        rotate_dir(s.u, s.v, s.w, ct, st, sp, cp);
-    }
-    if (which == 1) {
-        int out = 0;
-        if (axis == 0) { s.x = (float)(cross > 0 ? s.ix + 1 : s.ix) * A.vx; s.ix += cross; out = s.ix < 0 || s.ix >= A.nx; }
-        else if (axis == 1) { s.y = (float)(cross > 0 ? s.iy + 1 : s.iy) * A.vy; s.iy += cross; out = s.iy < 0 || s.iy >= A.ny; }
-        else { s.z = (float)(cross > 0 ? s.iz + 1 : s.iz) * A.vz; s.iz += cross; out = s.iz < 0 || s.iz >= A.nz; }
-        if (out) {
-            escape(A, acc, s.t + (s.pos ? 2.0f * F_ME : 0.0f), s.wt, s.root);
-            return E_END;
+        const float tlim = fmaxf(0.9f * s.t, A.ecut);
+        const float rlim = range_of(A.tab, tlim);
+        const float s_max = (s.r - rlim) * __frcp_rn(rho);
+        int which;
+        float step;
+        if (s_hard <= s_bound && s_hard <= s_max) { which = 0; step = s_hard; }
+        else if (s_bound <= s_max) { which = 1; step = s_bound; }
+        else { which = 2; step = s_max; }
+        // energy at the end of the step: the 10 % limit exactly, else from the
+        // range left; the range itself is carried, not recomputed from the energy
+        float tend, rend;
+        if (which == 2) { tend = tlim; rend = rlim; }
+        else { rend = s.r - rho * step; tend = fmaxf(energy_of_range(A.tab, rend), tlim); }
+        const float th0 = highland(s.t, step, rho);
+        deposit(A, acc, iv, s.t - tend, s.wt, s.root);
+        s.t = tend;
+        s.r = rend;
+        s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
+        s.nlam -= step * sig;
+        if (!(A.flags & PSL_PHYS_NO_MSC) && step > 0.0f) {
+            const float l2 = -2.0f * ln_uniform(rng.take());
+            const float th = th0 * (l2 * rsqrtf(l2));
+            float st, ct, sp, cp;
+            sincosf(th, &st, &ct);
+            st = fabsf(st);
+            sincos_2pi(rng.take(), &sp, &cp);
+            rotate_dir(s.u, s.v, s.w, ct, st, sp, cp);
         }
-    }
-    return which == 0 ? E_HARD : E_ON;
+        if (which == 1) {
+            int out = 0;
+            if (axis == 0) { s.x = (float)(cross > 0 ? s.ix + 1 : s.ix) * A.vx; s.ix += cross; out = s.ix < 0 || s.ix >= A.nx; }
+            else if (axis == 1) { s.y = (float)(cross > 0 ? s.iy + 1 : s.iy) * A.vy; s.iy += cross; out = s.iy < 0 || s.iy >= A.ny; }
+            else { s.z = (float)(cross > 0 ? s.iz + 1 : s.iz) * A.vz; s.iz += cross; out = s.iz < 0 || s.iz >= A.nz; }
+            if (out) {
+                escape(A, acc, s.t + (s.pos ? 2.0f * F_ME : 0.0f), s.wt, s.root);
+                return E_END;
+            }
+        }
+        if (which == 0) return E_HARD;
+        if (!(s.t <= A.ecut)) return E_ON;
+        iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
+    }                                                         // the step's draws are committed here
+    if (s.steps > MAX_E_STEPS) atomicOr(A.err, PSL_DEV_ERR_STEPS);
+    electron_end(A, acc, s, iv);
+    return E_END;
 }
 
 // the hard event (Moller delta ray or bremsstrahlung photon) that ended the
@@ -848,6 +854,14 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
     Electron s;
     bool alive = false, done = false, hard = false;
     for (;;) {
+        // Hard events wait until enough lanes have one (or every live lane
+        // waits), so that the long hard-event code runs with most lanes
+        // active; the other lanes keep stepping meanwhile.
+        const unsigned hm = __ballot_sync(FULL, hard), live0 = __ballot_sync(FULL, alive);
+        if (hm && (__popc(hm) >= PSL_E_DEFER || hm == live0)) {
+            if (hard) { electron_hard(A, acc, s, bh); hard = false; }
+        }
+        // lanes whose electron ended (in this pass's step or before) take the next
         const unsigned need = __ballot_sync(FULL, !alive && !done);
         if (need) {
             const int leader = __ffs(need) - 1;
@@ -873,15 +887,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                 }
             }
         }
-        const unsigned live = __ballot_sync(FULL, alive);
-        if (!live) break;
-        // Hard events wait until enough lanes have one (or every live lane
-        // waits), so that the long hard-event code runs with most lanes
-        // active; the other lanes keep stepping meanwhile.
-        const unsigned hm = __ballot_sync(FULL, hard);
-        if (hm && (__popc(hm) >= PSL_E_DEFER || hm == live)) {
-            if (hard) { electron_hard(A, acc, s, bh); hard = false; }
-        }
+        if (!__ballot_sync(FULL, alive)) break;
         if (alive && !hard) {
             const int r = electron_step(A, acc, s);
             alive = r != E_END;
