@@ -46,6 +46,12 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #ifndef SRC_RUN
 #define SRC_RUN 256u                   // consecutive histories a warp of the source stage takes at a time
 #endif
+#ifndef SRC_ILP
+#define SRC_ILP 1                      // histories a lane of the source stage looks up at once (2-4 need
+#endif                                 // 80-126 registers; the lost occupancy cost more than they gained)
+#ifndef SRC_MIN_BLOCKS
+#define SRC_MIN_BLOCKS 4               // resident 256-thread source blocks per SM (register cap 64)
+#endif
 #ifndef PSL_G_DEFER
 #define PSL_G_DEFER 24                 // lanes with a pending real photon interaction before a warp runs them
 #endif
@@ -941,7 +947,7 @@ __global__ void k_slice_bounds(const uint32_t *keys, uint32_t n, uint32_t nb, ui
 // Histories first + i * stride, i < n; or, with a list, the histories
 // first + list[list_off[slice] + root0 + i] of one batch of a window whose
 // offsets were sorted by batch (at most n of them: more is an overflow).
-__global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first, int64_t stride, uint32_t n,
+__global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev P, int64_t first, int64_t stride, uint32_t n,
                                                 uint32_t root0, int32_t slice, Particle *out, uint32_t *count,
                                                 const uint32_t *list, const uint32_t *list_off) {
     __shared__ PlanShared S;
@@ -971,39 +977,69 @@ __global__ void __launch_bounds__(256) k_source(Args A, PlanDev P, int64_t first
     int g = -1;
     int64_t q = -1;
     for (uint32_t run = gw; run < n_runs; run += n_warps)
-    for (uint32_t ib = run * SRC_RUN, i1 = min(n, ib + SRC_RUN), i0 = ib; ib < i1; ib += 32) {
-        const uint32_t i = ib + lane;
-        const bool ok = i < i1;
-        const int64_t h = list ? (ok ? first + (int64_t)__ldg(list + lbase + i) : first) : first + (int64_t)i * stride;
-        if (ib == i0) {
-            if (lane == 0 && ok) locate(P, S, h, g, q);
-            g = __shfl_sync(FULL, g, 0);
-            q = __shfl_sync(FULL, q, 0);
+    for (uint32_t ib = run * SRC_RUN, i1 = min(n, ib + SRC_RUN), i0 = ib; ib < i1; ib += 32u * SRC_ILP) {
+        // SRC_ILP histories per lane, 32 apart: their plan lookups and
+        // record reads are issued together, so that their latencies overlap
+        bool ok[SRC_ILP];
+        int64_t h[SRC_ILP], use[SRC_ILP], qk[SRC_ILP];
+        int gk[SRC_ILP];
+#pragma unroll
+        for (int k = 0; k < SRC_ILP; ++k) {
+            const uint32_t i = ib + 32u * k + lane;
+            ok[k] = i < i1;
+            h[k] = list ? (ok[k] ? first + (int64_t)__ldg(list + lbase + i) : first) : first + (int64_t)i * stride;
+            if (k == 0 && ib == i0) {
+                if (lane == 0 && ok[0]) locate(P, S, h[0], g, q);
+                g = __shfl_sync(FULL, g, 0);
+                q = __shfl_sync(FULL, q, 0);
+            }
+            if (ok[k]) locate_hinted(P, S, h[k], g, q);
+            gk[k] = g; qk[k] = q;
         }
-        SrcOut o;
-        o.status = -1;
-        if (ok) {
-            locate_hinted(P, S, h, g, q);
-            source_at(P, S, h, g, q, o);
+        // the segment -> entry -> record chain of the plan lookup, as source_at
+        EntryDev E[SRC_ILP];
+#pragma unroll
+        for (int k = 0; k < SRC_ILP; ++k) {
+            if (!ok[k]) continue;
+            const SegDev sg = P.seg[qk[k]];
+            uint64_t rq, pidx;
+            divmod_u64((uint64_t)(h[k] - S.gs[gk[k]] - sg.h), (uint64_t)sg.w, rq, pidx);
+            use[k] = sg.r0 + (int64_t)rq;
+            E[k] = P.ent[S.gseg[gk[k]] + (int64_t)pidx];
         }
-        if (o.status == PSL_SRC_TRANSPORT || o.status == PSL_SRC_MISS) {
-            const unsigned long long e = fixed_point(o.s[6], o.s[7]);
-            acc.emitted += e;
-            if (o.status == PSL_SRC_MISS) acc.esc += e;
+        PslRecord R[SRC_ILP];
+#pragma unroll
+        for (int k = 0; k < SRC_ILP; ++k) {
+            if (!ok[k]) continue;
+            uint64_t rw, rr;
+            divmod_u64((uint64_t)(E[k].offset + use[k]), (uint64_t)E[k].nrec, rw, rr);
+            R[k] = P.rec[E[k].start + (int64_t)rr];
         }
-        if (o.status == PSL_SRC_TRANSPORT) {
-            Particle c;
-            c.x = o.s[0]; c.y = o.s[1]; c.z = o.s[2]; c.e = o.s[6];
-            c.u = o.s[3]; c.v = o.s[4]; c.w = o.s[5]; c.wt = o.s[7];
-            c.pid_lo = (uint32_t)h; c.pid_hi = (uint32_t)((uint64_t)h >> 32);
-            c.type = (uint32_t)o.ptype;
-            const uint32_t sl = slice >= 0 ? (uint32_t)slice : history_slice(c.pid_lo, c.pid_hi, A.rk, A.n_slices);
-            c.root = (sl << ROOT_SLICE_SHIFT) | ((root0 + i) & ROOT_INDEX_MASK);
-            if (o.ptype == 0) {
-                queue_push(Queue{out, count, cap}, c, A.err);
-            } else {
-                atomicAdd(&bh[band_of(A, c.e)], 1u);
-                queue_push(A.e_out, c, A.err);
+#pragma unroll
+        for (int k = 0; k < SRC_ILP; ++k) {
+            const uint32_t i = ib + 32u * k + lane;
+            SrcOut o;
+            o.status = -1;
+            if (ok[k]) record_to_phantom(R[k], P.beams[E[k].beam], P.z_psl, P.L, P.origin, true, o);
+            if (o.status == PSL_SRC_TRANSPORT || o.status == PSL_SRC_MISS) {
+                const unsigned long long e = fixed_point(o.s[6], o.s[7]);
+                acc.emitted += e;
+                if (o.status == PSL_SRC_MISS) acc.esc += e;
+            }
+            if (o.status == PSL_SRC_TRANSPORT) {
+                Particle c;
+                c.x = o.s[0]; c.y = o.s[1]; c.z = o.s[2]; c.e = o.s[6];
+                c.u = o.s[3]; c.v = o.s[4]; c.w = o.s[5]; c.wt = o.s[7];
+                c.pid_lo = (uint32_t)h[k]; c.pid_hi = (uint32_t)((uint64_t)h[k] >> 32);
+                c.type = (uint32_t)o.ptype;
+                const uint32_t sl = slice >= 0 ? (uint32_t)slice : history_slice(c.pid_lo, c.pid_hi, A.rk, A.n_slices);
+                c.root = (sl << ROOT_SLICE_SHIFT) | ((root0 + i) & ROOT_INDEX_MASK);
+                if (o.ptype == 0) {
+                    queue_push(Queue{out, count, cap}, c, A.err);
+                } else {
+                    atomicAdd(&bh[band_of(A, c.e)], 1u);
+                    queue_push(A.e_out, c, A.err);
+                }
             }
         }
     }
