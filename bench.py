@@ -50,7 +50,7 @@ def measured_peaks():
 class ClockSampler:
     """SM clocks and throttle reasons sampled during the timed region: NVML
     polled every 10 ms from a thread (the device found by its UUID), else
-    nvidia-smi at its 200 ms interval.  Read-only queries."""
+    nvidia-smi at its 200 ms interval.  Read-only queries; nothing is set."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -62,39 +62,57 @@ class ClockSampler:
         self.nvml = None
         self.lines = []
         self.samples = []          # (sm MHz, max sm MHz, reason names)
+        self.nvml_error = None
         self.done = threading.Event()
 
     def _nvml_handle(self):
-        import pynvml
+        """NVML (read-only queries, through ctypes on the driver's
+        libnvidia-ml) and the handle of CUDA device `index`: by its UUID,
+        else the only device NVML sees."""
+        import ctypes
         import torch
-        pynvml.nvmlInit()
-        uuid = str(torch.cuda.get_device_properties(self.index).uuid)
-        if not uuid.startswith("GPU-"):
-            uuid = "GPU-" + uuid
-        return pynvml, pynvml.nvmlDeviceGetHandleByUUID(uuid)
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        u = str(getattr(torch.cuda.get_device_properties(self.index), "uuid", ""))
+        for cand in ([u, "GPU-" + u] if u else []):
+            if lib.nvmlDeviceGetHandleByUUID(ctypes.c_char_p(cand.encode()), ctypes.byref(h)) == 0:
+                return lib, h
+        n = ctypes.c_uint()
+        if lib.nvmlDeviceGetCount_v2(ctypes.byref(n)) == 0 and n.value == 1 and \
+                lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(0), ctypes.byref(h)) == 0:
+            return lib, h
+        raise RuntimeError(f"no NVML device for CUDA device {self.index} (uuid {u})")
 
     def start(self):
         try:
-            nv, h = self._nvml_handle()
-            bits = [nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
-                    nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap]
-            smax = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
-            self.nvml = nv
+            import ctypes
+            lib, h = self._nvml_handle()
+            NVML_CLOCK_SM = 1
+            # clock event reason bits of nvml.h: sw power cap 0x4, hw slowdown
+            # 0x8, sw thermal 0x20, hw thermal 0x40
+            bits = [0x8, 0x40, 0x20, 0x4]
+            v = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, NVML_CLOCK_SM, ctypes.byref(v)) != 0:
+                raise RuntimeError("nvmlDeviceGetMaxClockInfo failed")
+            smax = float(v.value)
+            self.nvml = lib
 
             def poll():
+                c, r = ctypes.c_uint(), ctypes.c_ulonglong()
                 while not self.done.is_set():
-                    try:
-                        sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
-                        r = int(nv.nvmlDeviceGetCurrentClocksEventReasons(h))
-                        self.samples.append((sm, smax, [n for n, b in zip(self.NAMES, bits) if r & b]))
-                    except Exception:
-                        pass
+                    if lib.nvmlDeviceGetClockInfo(h, NVML_CLOCK_SM, ctypes.byref(c)) == 0 and \
+                            lib.nvmlDeviceGetCurrentClocksThrottleReasons(h, ctypes.byref(r)) == 0:
+                        self.samples.append((float(c.value), smax,
+                                             [n for n, b in zip(self.NAMES, bits) if r.value & b]))
                     self.done.wait(0.01)
             self.th = threading.Thread(target=poll, daemon=True)
             self.th.start()
             return
-        except Exception:
+        except Exception as e:            # noqa: BLE001 - fall back to nvidia-smi
             self.nvml = None
+            self.nvml_error = str(e)[:200]
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -112,10 +130,7 @@ class ClockSampler:
         if self.nvml is not None:
             self.done.set()
             self.th.join(timeout=5)
-            try:
-                self.nvml.nvmlShutdown()
-            except Exception:
-                pass
+            self.nvml.nvmlShutdown()
             src = "nvml, 10 ms"
         elif self.proc:
             self.proc.terminate()
@@ -134,12 +149,15 @@ class ClockSampler:
                     continue
             src = "nvidia-smi, 200 ms"
         else:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "nvml_error": self.nvml_error}
         sm = [x[0] for x in self.samples]
         smax = [x[1] for x in self.samples]
         reasons = sorted({n for x in self.samples for n in x[2]})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "sm_min_mhz": min(sm) if sm else None, "reasons": reasons, "samples": len(sm), "source": src}
+        out = {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+               "sm_min_mhz": min(sm) if sm else None, "reasons": reasons, "samples": len(sm), "source": src}
+        if self.nvml_error:
+            out["nvml_error"] = self.nvml_error
+        return out
 
 
 # --------------------------------------------------------------------------
@@ -487,9 +505,9 @@ def main():
 #       -k regex:"k_electron|k_photon" python bench.py --histories 10000000 ...
 # They hold for the kernels they were measured on; re-measure after changing
 # the kernels.
-THREAD_INST_PER_ELECTRON_STEP = 584.4
-THREAD_INST_PER_WOODCOCK_STEP = 529.6
-DRAM_BYTES_PER_HISTORY = {"electron": 28.28, "photon": 58.97}
+THREAD_INST_PER_ELECTRON_STEP = 587.4
+THREAD_INST_PER_WOODCOCK_STEP = 529.5
+DRAM_BYTES_PER_HISTORY = {"electron": 28.28, "photon": 58.89}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
 
