@@ -430,6 +430,12 @@ PSL_API int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *phantom, c
 PSL_API int dose_readout(const psl_tally_t *tally, const psl_phantom_t *phantom, double norm, double *dose,
                  double *sigma, double *ledger, void *stream);
 
+/* Destroy functions free what the handle owns (NULL is ignored).  A tally's
+ * transport workspace (its particle queues, ~30 x 48 B per primary of a
+ * pass: 26 GB at the default 2^24 primaries per pass) is not freed but kept
+ * for the next tally created on the same device (at most one is kept), since
+ * mapping it again costs ~14 ms; psl_tally_destroy first waits for the
+ * device.  psl_memory_trim frees it. */
 PSL_API void psl_store_destroy(psl_store_t *store);
 PSL_API void psl_plan_destroy(psl_plan_t *plan);
 PSL_API void psl_batch_destroy(psl_batch_t *batch);
@@ -470,10 +476,11 @@ PSL_API int psl_gamma(const double *ref, const double *ev, int32_t nx, int32_t n
 
 /* The library takes its stream-ordered scratch (psl_build, psl_plan_create,
  * psl_stream_bin, batches) from its own device memory pool, one per device,
- * which keeps freed blocks for the next call.  psl_memory_trim waits for the
- * device (cudaDeviceSynchronize), then returns pool memory beyond keep_bytes
- * to the driver; *held_bytes (may be NULL) receives what the pool still
- * reserves.  Errors: PSL_ECUDA. */
+ * which keeps freed blocks for the next call.  psl_memory_trim frees the
+ * transport workspace kept from a destroyed tally on the current device,
+ * waits for the device (cudaDeviceSynchronize), then returns pool memory
+ * beyond keep_bytes to the driver; *held_bytes (may be NULL) receives what
+ * the pool still reserves.  Errors: PSL_ECUDA. */
 PSL_API int psl_memory_trim(uint64_t keep_bytes, uint64_t *held_bytes);
 
 /* Text of the calling thread's last error ("" if none). */

@@ -66,7 +66,10 @@ cudaError_t psl_malloc_async(void **ptr, size_t bytes, cudaStream_t st) {
     return cudaMallocFromPoolAsync(ptr, bytes, p, st);
 }
 
+void workspace_cache_trim();
+
 extern "C" int psl_memory_trim(uint64_t keep_bytes, uint64_t *held_bytes) {
+    workspace_cache_trim();
     cudaMemPool_t p = nullptr;
     cudaError_t e = pool_of_current(&p);
     if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("psl_memory_trim: ") + cudaGetErrorString(e));

@@ -9,7 +9,7 @@
 
 #include "psl_internal.cuh"
 
-void workspace_free(Workspace *w);
+void workspace_release(Workspace *w);
 
 namespace {
 
@@ -114,7 +114,7 @@ extern "C" void psl_tally_destroy(psl_tally_t *t) {
     if (!t) return;
     if (t->t) cudaFree(t->t);
     if (t->ledger) cudaFree(t->ledger);
-    if (t->ws) workspace_free(t->ws);
+    if (t->ws) workspace_release(t->ws);            // kept for the next tally
     delete t;
 }
 

@@ -1168,6 +1168,7 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
 }  // namespace
 
 struct Workspace {
+    int device = 0;                    // the device its buffers live on
     int64_t chunk = 0;                 // primaries per pass the buffers are sized for
     uint32_t cap_p = 0, cap_e = 0, cap_s = 0;
     Particle *P[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr}, *S = nullptr, *Q = nullptr;
@@ -1201,6 +1202,59 @@ void workspace_free(Workspace *w) {
     if (w->bm_off) cudaFree(w->bm_off);
     if (w->bm_scratch) cudaFree(w->bm_scratch);
     delete w;
+}
+
+// The workspace of a destroyed tally, kept for the next tally on the same
+// device: its particle queues hold ~30 x chunk particles (26 GB at the
+// default chunk of 2^24) and mapping them afresh cost ~14 ms per tally.  At
+// most WS_CACHE_MAX are kept; psl_memory_trim frees them.
+namespace {
+constexpr size_t WS_CACHE_MAX = 1;
+std::mutex g_ws_mu;
+std::vector<Workspace *> g_ws_cache;
+}  // namespace
+
+// A destroyed tally's workspace: into the cache (after the device is idle,
+// as cudaFree would wait too), or freed when the cache is full.
+void workspace_release(Workspace *w) {
+    if (!w) return;
+    cudaDeviceSynchronize();
+    if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }
+    std::memset(w->graph_key, 0, sizeof(w->graph_key));
+    Workspace *drop = w;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        if (g_ws_cache.size() < WS_CACHE_MAX) { g_ws_cache.push_back(w); drop = nullptr; }
+    }
+    workspace_free(drop);
+}
+
+// Free the cached workspaces of the current device (psl_memory_trim).
+void workspace_cache_trim() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<Workspace *> out;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        for (size_t i = 0; i < g_ws_cache.size();) {
+            if (g_ws_cache[i]->device == dev) { out.push_back(g_ws_cache[i]); g_ws_cache.erase(g_ws_cache.begin() + i); }
+            else ++i;
+        }
+    }
+    for (Workspace *w : out) workspace_free(w);
+}
+
+// A cached workspace of this device with room for `chunk` primaries, or null.
+static Workspace *workspace_take(int dev, int64_t chunk) {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    for (size_t i = 0; i < g_ws_cache.size(); ++i) {
+        Workspace *w = g_ws_cache[i];
+        if (w->device == dev && w->chunk >= chunk) {
+            g_ws_cache.erase(g_ws_cache.begin() + i);
+            return w;
+        }
+    }
+    return nullptr;
 }
 
 // Resident 256-thread blocks of the source kernel per SM: its grid is one
@@ -1257,8 +1311,21 @@ static int workspace_ensure(psl_tally *t, int64_t chunk) {
     Workspace *w = t->ws;
     if (w && w->chunk >= chunk) return PSL_OK;
     if (w) { cudaDeviceSynchronize(); workspace_free(w); t->ws = nullptr; }
+    int dev = 0;
+    PSL_CUDA(cudaGetDevice(&dev));
+    if ((w = workspace_take(dev, chunk))) {
+        t->ws = w;
+        if (w->nvox < t->nvox) {                     // the phantom's packed densities need more room
+            PSL_CUDA(cudaFree(w->mrho));
+            w->mrho = nullptr;
+            PSL_CUDA(cudaMalloc((void **)&w->mrho, t->nvox * sizeof(float)));
+            w->nvox = t->nvox;
+        }
+        return PSL_OK;
+    }
     w = new Workspace();
     t->ws = w;
+    w->device = dev;
     w->chunk = chunk;
     const int64_t base = std::max<int64_t>(chunk, 4096);
     w->cap_p = (uint32_t)std::min<int64_t>(3 * base, 0xF0000000ll);
