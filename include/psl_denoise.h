@@ -104,11 +104,13 @@ PSL_API int psl_denoiser_backward(psl_denoiser_t *d, const float *dose, const fl
 PSL_API int psl_denoiser_step(psl_denoiser_t *d, float lr, void *stream);
 
 /* The k-th smallest (0-based, 0 <= k < n) of n FP32 values in device memory,
- * exactly (the values' order-preserving bit patterns sorted by the library's
- * radix sort), written to *out (host).  The denoiser normalises a dose by
- * its 99.9th percentile: k = floor(0.999 n) - 1.  NaN inputs order above
- * +inf.  Uses stream-ordered scratch of ~32 bytes per value; synchronises
- * stream.  PSL_EINVAL for n < 1, n >= 2^32, k out of range or null pointers. */
+ * exactly, written to *out (host): radix selection on the values'
+ * order-preserving bit patterns (three histogram passes over the values fix
+ * 11, 11 and 10 bits of the answer).  The denoiser normalises a dose by its
+ * 99.9th percentile: k = floor(0.999 n) - 1.  -0 orders below +0; NaNs with
+ * the sign bit clear order above +inf, those with it set below -inf.  Uses
+ * 8 KB of stream-ordered scratch; synchronises stream.  PSL_EINVAL for
+ * n < 1, n >= 2^32, k out of range or null pointers. */
 PSL_API int psl_kth_smallest(const float *x, int64_t n, int64_t k, float *out, void *stream);
 
 #ifdef __cplusplus

@@ -447,15 +447,70 @@ extern "C" int psl_denoiser_step(psl_denoiser_t *d, float lr, void *stream) {
 namespace {
 // order-preserving map of a float's bits to an unsigned key (negatives below
 // positives, larger magnitude negatives lower)
-__global__ void k_float_keys(const float *x, uint32_t n, uint32_t *keys) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t b = __float_as_uint(x[i]);
-        keys[i] = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-    }
+// k-th smallest by radix selection on the values' order-preserving bit
+// patterns (sign flipped for non-negatives, all bits for negatives): three
+// passes fix 11, 11 and 10 bits of the answer, each a histogram of the
+// values that share the bits fixed so far, then a search for the bin that
+// holds the k-th.  State: [0] the bits fixed so far, [1] k among the values
+// that share them.
+__device__ __forceinline__ uint32_t float_key(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
-__global__ void k_key_value(const uint32_t *keys, uint32_t k, float *out) {
-    const uint32_t b = keys[k];
-    *out = __uint_as_float((b & 0x80000000u) ? (b & 0x7FFFFFFFu) : ~b);
+constexpr int SEL_BINS = 2048;
+
+__global__ void __launch_bounds__(256) k_select_hist(const float *x, uint32_t n, int shift, uint32_t field,
+                                                     uint32_t prefix_mask, const uint32_t *state, uint32_t *hist) {
+    __shared__ uint32_t h[SEL_BINS];
+    for (int i = threadIdx.x; i < SEL_BINS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint32_t prefix = state[0];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t key = float_key(__ldg(x + i));
+        if ((key & prefix_mask) == prefix) atomicAdd(&h[(key >> shift) & field], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SEL_BINS; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// one block of 1024 threads: the bin holding the k-th value, by a block scan
+// of the histogram (two bins per thread); the histogram is cleared for the
+// next pass
+__global__ void __launch_bounds__(1024) k_select_pick(uint32_t *hist, int shift, uint32_t *state) {
+    __shared__ uint32_t warp_sum[32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const uint32_t a = hist[2 * t], b = hist[2 * t + 1];
+    uint32_t x = a + b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t v = warp_sum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            if (lane >= o) v += y;
+        }
+        warp_sum[lane] = v;                          // inclusive sums of the warps
+    }
+    __syncthreads();
+    const uint32_t below = x - (a + b) + (wid ? warp_sum[wid - 1] : 0u);   // values in bins < 2t
+    const uint32_t k = state[1];
+    __syncthreads();                                 // every thread has read state[1]
+    if (k >= below && k < below + a) { state[0] |= (uint32_t)(2 * t) << shift; state[1] = k - below; }
+    else if (k >= below + a && k < below + a + b) { state[0] |= (uint32_t)(2 * t + 1) << shift; state[1] = k - below - a; }
+    hist[2 * t] = 0;
+    hist[2 * t + 1] = 0;
+}
+
+__global__ void k_select_value(const uint32_t *state, float *out) {
+    const uint32_t key = state[0];
+    *out = __uint_as_float((key & 0x80000000u) ? (key & 0x7FFFFFFFu) : ~key);
 }
 }  // namespace
 
@@ -464,30 +519,25 @@ extern "C" int psl_kth_smallest(const float *x, int64_t n, int64_t k, float *out
         return psl_fail(PSL_EINVAL, "psl_kth_smallest: bad argument");
     cudaStream_t st = as_stream(stream_);
     const uint32_t m = (uint32_t)n;
-    uint32_t *buf = nullptr;
-    void *scratch = nullptr;
-    float *dv = nullptr;
-    if (psl_malloc_async((void **)&buf, (size_t)m * 16, st) != cudaSuccess ||
-        psl_malloc_async(&scratch, sort_pairs_scratch_bytes(m), st) != cudaSuccess ||
-        psl_malloc_async((void **)&dv, 4, st) != cudaSuccess) {
-        if (buf) cudaFreeAsync(buf, st);
-        if (scratch) cudaFreeAsync(scratch, st);
+    uint32_t *buf = nullptr;                         // [SEL_BINS] histogram, [2] state, value
+    if (psl_malloc_async((void **)&buf, (SEL_BINS + 4) * sizeof(uint32_t), st) != cudaSuccess)
         return psl_fail(PSL_ENOMEM, "psl_kth_smallest: scratch");
+    uint32_t *hist = buf, *state = buf + SEL_BINS;
+    float *dv = reinterpret_cast<float *>(buf + SEL_BINS + 2);
+    const uint32_t init[2] = {0u, (uint32_t)k};
+    cudaMemsetAsync(hist, 0, SEL_BINS * sizeof(uint32_t), st);
+    cudaMemcpyAsync(state, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    const int grid = (int)std::min<uint32_t>((m + 255) / 256, (uint32_t)psl_sm_count() * 4);
+    const int shifts[3] = {21, 10, 0};
+    const uint32_t fields[3] = {0x7FFu, 0x7FFu, 0x3FFu}, masks[3] = {0u, 0xFFE00000u, 0xFFFFFC00u};
+    for (int p = 0; p < 3; ++p) {
+        k_select_hist<<<grid, 256, 0, st>>>(x, m, shifts[p], fields[p], masks[p], state, hist); PSL_NOTE_LAUNCH();
+        k_select_pick<<<1, 1024, 0, st>>>(hist, shifts[p], state); PSL_NOTE_LAUNCH();
     }
-    uint32_t *k0 = buf, *v0 = buf + m, *k1 = buf + 2 * (size_t)m, *v1 = buf + 3 * (size_t)m;
-    const int grid = (int)std::min<uint32_t>((m + 255) / 256, (uint32_t)psl_sm_count() * 8);
-    k_float_keys<<<grid, 256, 0, st>>>(x, m, k0); PSL_NOTE_LAUNCH();
-    int alt = 0;
-    sort_pairs_u32(k0, v0, k1, v1, m, 32, nullptr, true, scratch, &alt, st);
-    k_key_value<<<1, 1, 0, st>>>(alt ? k1 : k0, (uint32_t)k, dv); PSL_NOTE_LAUNCH();
-    uint32_t herr = 0;
+    k_select_value<<<1, 1, 0, st>>>(state, dv); PSL_NOTE_LAUNCH();
     cudaMemcpyAsync(out, dv, 4, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(&herr, sort_err_word(scratch), 4, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(buf, st);
-    cudaFreeAsync(scratch, st);
-    cudaFreeAsync(dv, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("psl_kth_smallest: ") + cudaGetErrorString(e));
-    if (herr) return psl_fail(PSL_ETIMEOUT, "psl_kth_smallest: sort look-back timed out");
     return PSL_OK;
 }

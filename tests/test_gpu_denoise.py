@@ -149,7 +149,8 @@ def test_denoiser_rejects_bad_volumes():
 
 def test_kth_smallest_is_exact():
     """psl_kth_smallest (the denoiser's dose scale) against a CPU sort:
-    random values with repeats, negatives and zeros, several k, n = 1."""
+    random values with repeats, negatives and zeros, several k, n = 1, a
+    dose-like 128^3 volume with +inf, all-equal values."""
     rng = np.random.default_rng(3)
     for n in (1, 1000, 262_145):
         x = rng.normal(0, 1, n).astype(np.float32) * rng.integers(0, 3, n).astype(np.float32)
@@ -158,5 +159,16 @@ def test_kth_smallest_is_exact():
         xt = torch.from_numpy(x).cuda()
         for k in sorted({0, n // 2, max(0, int(0.999 * n) - 1), n - 1}):
             assert capi.kth_smallest(xt, k) == xs[k]
+    # a dose-like 128^3 volume (mostly air zeros, an exponential tail, +inf),
+    # and values that are all equal
+    x = rng.exponential(1.0, 128 ** 3).astype(np.float32)
+    x[rng.random(x.size) < 0.6] = 0.0
+    x[5] = np.inf
+    xs = np.sort(x)
+    xt = torch.from_numpy(x).cuda()
+    for k in (0, x.size // 2, int(0.999 * x.size) - 1, x.size - 2, x.size - 1):
+        assert capi.kth_smallest(xt, k) == xs[k]
+    same = torch.full((4097,), 2.5, device="cuda")
+    assert capi.kth_smallest(same, 0) == 2.5 and capi.kth_smallest(same, 4096) == 2.5
     with pytest.raises(capi.PslError):
         capi.kth_smallest(torch.zeros(4, device="cuda"), 4)
