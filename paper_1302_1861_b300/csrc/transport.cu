@@ -1218,7 +1218,11 @@ std::vector<Workspace *> g_ws_cache;
 // as cudaFree would wait too), or freed when the cache is full.
 void workspace_release(Workspace *w) {
     if (!w) return;
-    cudaDeviceSynchronize();
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != w->device) cudaSetDevice(w->device);
+    cudaDeviceSynchronize();                         // the device the queues live on
+    if (cur != w->device) cudaSetDevice(cur);
     if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }
     std::memset(w->graph_key, 0, sizeof(w->graph_key));
     Workspace *drop = w;
