@@ -7,7 +7,9 @@ closed form (Sec. 2.3.3 selection and counts, Sec. 2.5 readout):
   conserved, and the voxel's tally matches the oracle's;
 * a phantom every history misses: nothing is deposited, everything emitted
   is escaped, on both sides;
-* one history at each end of a plan, and an empty caller batch.
+* one history at each end of a plan, and an empty caller batch;
+* a transport workspace kept from a destroyed tally (for a smaller phantom)
+  gives the same tally as a fresh one.
 """
 import dataclasses
 
@@ -100,3 +102,31 @@ def test_empty_caller_batch():
     capi.transport_run(dw.phantom, capi.physics(), batch, tally, 0)
     t, lg = engine.raw_tallies(dw, tally, 1)
     assert int(t.sum()) == 0 and int(lg[0]) == 0 and int(lg[2]) == 0
+
+
+def test_kept_workspace_gives_the_same_tally():
+    """A destroyed tally's transport workspace is kept and taken by the next
+    tally: here a 32^3 phantom's (so the 64^3 run after it must grow the
+    packed-density buffer).  The result equals a run on a fresh workspace,
+    bit for bit."""
+    capi.memory_trim()                                   # nothing kept from earlier tests
+    small = inputs.config1(n_records=20_000, n_histories=300_000)
+    big = inputs.config2(n_records=200_000, n_histories=200_000)
+
+    def run(w):
+        dw = engine.upload(w)
+        store = capi.psl_build(dw.params, dw.records)
+        plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
+        tally = capi.psl_tally_create(dw.phantom, 2)
+        capi.psl_run(plan, dw.phantom, capi.physics(), tally, 0, w.n_histories)
+        out = engine.raw_tallies(dw, tally, 2)
+        tally.close()
+        return out
+
+    run(small)                                           # its workspace (room for 300,000 primaries) is kept
+    t_kept, l_kept = run(big)                            # ... and taken here
+    capi.memory_trim()
+    t_fresh, l_fresh = run(big)                          # a new workspace
+    assert t_kept.sum() > 0
+    assert np.array_equal(t_kept, t_fresh)
+    assert np.array_equal(l_kept[:11], l_fresh[:11])
