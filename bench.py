@@ -452,6 +452,7 @@ def main():
     name, (ms_tot, nl) = max(prof.items(), key=lambda kv: kv[1][0])
     per_launch_s = ms_tot / 1e3 / max(nl, 1)
     roof = roofline_for(name, per_launch_s, nl, args.steps, w, per_rank, peaks, pk_kind, counts)
+    rooflines = rooflines_per_step(prof, args.steps, w, per_rank, peaks, counts)
     ms_e = prof["electron"][0] / args.steps / 1e3
     ms_p = prof["photon"][0] / args.steps / 1e3
     transport = {"electron_steps": int(counts[6]), "woodcock_steps": int(counts[10]),
@@ -484,7 +485,7 @@ def main():
                            "phantom": "64^3 x 0.25 cm water + lung/bone slabs", "histories_per_gpu": per_rank,
                            "batches": nb, "l2": "inputs > L2 and L2 flushed between steps",
                            "parallelism": f"history-range shards x{world}"},
-                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
+                "e2e": e2e, "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
                 "time_to_1pct": t1pct if t1pct is not None else
                 {"histories": n_1pct, "seconds": n_1pct / (per_rank / t_step), "isocentre_rel_sigma_at_run": rel,
                  "kind": "extrapolated from the run's sigma"},
@@ -732,6 +733,38 @@ def imrt_run(capi, engine, inputs, torch):
             "energy_balance": float((lgh[1] + lgh[2] - lgh[0]) / lgh[0])}
 
 
+def rooflines_per_step(prof, steps, w, per_rank, peaks, counts):
+    """Every timed kernel class against its own bound, from its device time
+    per step: algorithmic bytes per step over that time for the HBM-bound
+    ones (the onesweep class also holds the plan's small sorts, whose bytes
+    are left out; the band sort's bytes depend on the electron count, which
+    the ledger does not hold), events per second against the issue speed of
+    light for the transport kernels."""
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    n = w.records.n
+    n_bins = 2 * w.binning.n_ebins * w.binning.nx * w.binning.ny
+    passes = -(-int(np.ceil(np.log2(n_bins + 1))) // 8)     # 8-bit digits of the PSL id (+ sentinel)
+    nvox = int(np.prod(w.phantom.shape))
+    # gather class: k_pack (25 B read, 32 B written) + k_gather (4 B permutation,
+    # 32 B record read, 32 B written) per record
+    bytes_per_step = {"key": n * 17.0, "onesweep": passes * n * 16.0, "gather": n * 125.0,
+                      "source": per_rank * 80.0, "readout": nvox * (w.n_batches * 8.0 + 16.0)}
+    out = {}
+    for k, (ms_k, n_k) in prof.items():
+        if not n_k:
+            continue
+        t = ms_k / 1e3 / max(steps, 1)
+        if k in bytes_per_step:
+            a = bytes_per_step[k] / t / 1e9
+            out[k] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm}
+        elif k in ("electron", "photon"):
+            ev, ipe = (counts[6], THREAD_INST_PER_ELECTRON_STEP) if k == "electron" else \
+                (counts[10], THREAD_INST_PER_WOODCOCK_STEP)
+            a, pk = ev / t / 1e9, THREAD_INST_PEAK / ipe / 1e9
+            out[k] = {"bound": "alu", "achieved": a, "peak": pk, "unit": "Gevents/s", "frac": a / pk}
+    return out
+
+
 def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kind, counts):
     """Algorithmic bytes (HBM-bound kernels) or operations per launch over the
     measured launch duration."""
@@ -744,9 +777,12 @@ def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kin
         elif name == "key":
             byts = n * (13.0 + 4.0)                  # read x, y, e, q; write the PSL id
         elif name == "gather":
-            byts = n * (4.0 + 25.0 + 32.0)           # permutation, SoA record, sorted record
+            byts = n * 125.0 / 2.0                   # k_pack + k_gather (see rooflines_per_step), per launch
         elif name == "source":
             byts = per_rank / per_step * (32.0 + 48.0)
+        elif name == "readout":
+            nvox = int(np.prod(w.phantom.shape))
+            byts = nvox * (w.n_batches * 8.0 + 16.0)  # the batch tallies read, dose and sigma written
         else:
             byts = 0.0
         ach = byts / per_launch_s / 1e9
