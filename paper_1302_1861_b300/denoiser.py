@@ -99,7 +99,7 @@ def _crops(shape, rng, count):
     return out
 
 
-def make_pairs(n_slab: int = 16, n_ct: int = 12, lo_per_geometry: int = 10, n_hi: int = 2_000_000_000,
+def make_pairs(n_slab: int = 16, n_ct: int = 16, lo_per_geometry: int = 10, n_hi: int = 2_000_000_000,
                n_lo=(1_000_000, 10_000_000), n_hi_ct: int = 4_000_000_000, n_lo_ct=(30_000_000, 300_000_000),
                lo_per_ct: int = 8, crops_per_ct: int = 4, seed: int = 7, log=print) -> List[Pair]:
     """Training pairs from seeded slab (64^3, whole volume) and CT (128^3,
@@ -262,10 +262,10 @@ def main():
     ap.add_argument("--out")
     ap.add_argument("--report", default=None, help="write the held-out accuracy report (JSON) here")
     ap.add_argument("--slab", type=int, default=16)
-    ap.add_argument("--ct", type=int, default=12)
+    ap.add_argument("--ct", type=int, default=16)
     ap.add_argument("--lo-per-geometry", type=int, default=10)
     ap.add_argument("--n-hi", type=float, default=2e9)
-    ap.add_argument("--epochs", type=int, default=80)
+    ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=1)
     a = ap.parse_args()
