@@ -134,10 +134,18 @@ def make_pairs(n_slab: int = 16, n_ct: int = 16, lo_per_geometry: int = 10, n_hi
     return pairs
 
 
+class TrainingStalled(RuntimeError):
+    """The loss stopped falling in the first epochs: the ReLUs of the
+    decoder died and the network is stuck at the identity on the dose."""
+
+
 def train(den: capi.Denoiser, pairs: List[Pair], epochs: int = 30, lr: float = 2e-3, batch: int = 4, seed: int = 0,
-          log=print) -> List[float]:
+          log=print, stall_epoch: int = 3) -> List[float]:
     """Adam on the mean squared error (in units of each pair's scale), a
-    cosine learning-rate decay to lr / 20; returns the mean loss per epoch."""
+    cosine learning-rate decay to lr / 20; returns the mean loss per epoch.
+    Raises TrainingStalled when the loss of epoch `stall_epoch` is above 0.9
+    of the first epoch's (healthy runs fall ~7x by epoch 5; a run on 24 CT
+    geometries stayed at the identity from its first epoch)."""
     rng = np.random.default_rng(seed)
     hist = []
     steps = epochs * ((len(pairs) + batch - 1) // batch)
@@ -156,6 +164,8 @@ def train(den: capi.Denoiser, pairs: List[Pair], epochs: int = 30, lr: float = 2
         hist.append(tot / len(pairs))
         if log and (ep % 5 == 0 or ep == epochs - 1):
             log(f"epoch {ep}: loss {hist[-1]:.3e}")
+        if ep == stall_epoch and hist[-1] > 0.9 * hist[0]:
+            raise TrainingStalled(f"loss {hist[0]:.3e} -> {hist[-1]:.3e} after {ep} epochs")
     return hist
 
 
@@ -277,8 +287,17 @@ def main():
     t0 = time.perf_counter()
     pairs = make_pairs(a.slab, a.ct, a.lo_per_geometry, int(a.n_hi))
     t1 = time.perf_counter()
-    den = capi.Denoiser.create(a.seed)
-    hist = train(den, pairs, a.epochs, a.lr)
+    # a stalled start (dead ReLUs) is restarted from the next seed's weights
+    for attempt in range(3):
+        den = capi.Denoiser.create(a.seed + attempt)
+        try:
+            hist = train(den, pairs, a.epochs, a.lr)
+            break
+        except TrainingStalled as e:
+            print(f"seed {a.seed + attempt}: {e}; restarting from seed {a.seed + attempt + 1}", flush=True)
+            den.close()
+    else:
+        raise SystemExit("training stalled from three initial weight sets")
     t2 = time.perf_counter()
     save(den, a.out)
     summary = {"pairs": len(pairs), "pair_seconds": t1 - t0, "train_seconds": t2 - t1, "loss": hist}
