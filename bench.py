@@ -182,6 +182,8 @@ def run_reference(args, rank, world):
     t_setup = time.perf_counter() - t0
     n_s = args.ref_sample
     rng = np.random.default_rng(7)
+    # every host core (a launcher's OMP_NUM_THREADS=1 is meant for the GPU ranks)
+    cores = os.cpu_count()
 
     def step(k):
         h0 = int(rng.integers(0, w.n_histories - n_s))
@@ -189,7 +191,7 @@ def run_reference(args, rank, world):
         s = source.source(pl, st, w.records, w.beams, w.phantom, np.arange(h0, h0 + n_s), w.z_psl, w.sad)
         m = s.status == source.ST_TRANSPORT
         oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
-                         np.arange(h0, h0 + n_s)[m].astype(np.uint64), w.phantom, w.seed)
+                         np.arange(h0, h0 + n_s)[m].astype(np.uint64), w.phantom, w.seed, nthreads=cores)
         return time.perf_counter() - t
 
     for k in range(args.warmup):
@@ -197,8 +199,7 @@ def run_reference(args, rank, world):
     times = [step(k) for k in range(args.steps)]
     t_h = float(np.mean(times)) / n_s
     value = w.n_histories / (t_setup + t_h * w.n_histories)
-    cores = os.cpu_count()
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": 1,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * (t_setup + t_h * w.n_histories), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
