@@ -228,7 +228,7 @@ def cpu_baseline(n_sample=40_000):
     s = source.source(pl, st, w.records, w.beams, w.phantom, hs, w.z_psl, w.sad)
     m = s.status == source.ST_TRANSPORT
     oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
-                     hs[m].astype(np.uint64), w.phantom, w.seed)
+                     hs[m].astype(np.uint64), w.phantom, w.seed, nthreads=os.cpu_count())
     t_h = (time.perf_counter() - t1) / n_sample
     value = w.n_histories / (t_setup + t_h * w.n_histories)
     return {"value": value, "unit": "histories/s", "cores": os.cpu_count(), "kind": "oracle",
