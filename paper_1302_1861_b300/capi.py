@@ -341,8 +341,9 @@ def psl_batch_read(batch: Batch, state=None, ptype=None, pid=None, stream=None):
 
 
 def memory_trim(keep_bytes: int = 0) -> int:
-    """Return the library pool's memory beyond keep_bytes to the driver;
-    returns the bytes the pool still reserves."""
+    """Free the transport workspace kept from a destroyed tally, then return
+    the library pool's memory beyond keep_bytes to the driver; returns the
+    bytes the pool still reserves."""
     held = u64()
     check(lib().psl_memory_trim(int(keep_bytes), ctypes.byref(held)))
     return held.value
