@@ -231,9 +231,19 @@ def cpu_baseline(n_sample=40_000):
                      hs[m].astype(np.uint64), w.phantom, w.seed, nthreads=os.cpu_count())
     t_h = (time.perf_counter() - t1) / n_sample
     value = w.n_histories / (t_setup + t_h * w.n_histories)
+    # the same on one thread, a quarter of the sample
+    hs1 = hs[: n_sample // 4]
+    t1 = time.perf_counter()
+    s = source.source(pl, st, w.records, w.beams, w.phantom, hs1, w.z_psl, w.sad)
+    m = s.status == source.ST_TRANSPORT
+    oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
+                     hs1[m].astype(np.uint64), w.phantom, w.seed, nthreads=1)
+    t_h1 = (time.perf_counter() - t1) / len(hs1)
     return {"value": value, "unit": "histories/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"psl_build+plan of all {w.records.n} records ({t_setup:.2f} s) + {n_sample} histories "
-                      f"from history {h0} ({t_h * n_sample:.2f} s), scaled to {w.n_histories} histories"}
+                      f"from history {h0} ({t_h * n_sample:.2f} s), scaled to {w.n_histories} histories",
+            "one_thread": {"value": w.n_histories / (t_setup + t_h1 * w.n_histories), "unit": "histories/s",
+                           "sample": f"the same setup + {len(hs1)} histories on 1 thread ({t_h1 * len(hs1):.2f} s)"}}
 
 
 # --------------------------------------------------------------------------
