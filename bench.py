@@ -1,27 +1,34 @@
 #!/usr/bin/env python
 """Benchmark of the PSL Monte Carlo dose path on one B300 (or N, one rank per GPU).
 
-Workload (the 10x10 cm^2 configuration): 1e7 phase-space records (2 types x
-32 log-energy x 12 x 12 1-cm PSL bins), a 64^3 x 0.25 cm water phantom with a
-lung and a bone slab, 1e8 histories in 10 batches.  One step is the whole path
-on that input: psl_build (sort the phase space into PSLs), psl_plan_create,
-psl_run over all 1e8 histories (each history's deposits into its batch) and
-dose_readout.  The metric is histories per second (whole job, all ranks);
-inputs (250 MB of records) are resident in HBM and larger than L2, and L2 is
-also flushed between steps.
+Headline workload (the 30x30 cm^2 configuration, the largest that runs on
+one GPU): a patient-independent phase space of 4e7 records over 40 x 40 cm
+(2 types x 32 log-energy x 40 x 40 1-cm PSL bins = 102,400 PSLs), 30x30 cm
+jaws with a 40x40 fluence map, a 128^3 x 0.25 cm CT-like phantom, 1e9
+histories in 10 batches.  One step is the whole path on that input:
+psl_build (sort the phase space into PSLs), psl_plan_create, psl_run over
+the rank's histories (each history's deposits into its batch), with N > 1
+ranks the int64 sum of every rank's tally, and dose_readout.  The metric is
+histories per second (whole job, all ranks); the inputs (1 GB of records)
+are resident in HBM and larger than L2, and L2 is also flushed between
+steps.
 
 Extra keys: `e2e` (the same step through the C ABI from pinned host buffers,
 with the records/phantom uploaded and dose/sigma/ledger read back inside the
 timed region), `modes` (the plain form, psl_source_batch + transport_run
 batch by batch), `roofline` (dominant kernel, timed live with CUDA events on
-its stream), `cpu_baseline` (the oracle on a bounded sample on the host
-cores), `time_to_1pct` (a whole plan timed from psl_build to dose_readout,
-its histories raised until the isocentre uncertainty is <= 1 %),
-`imrt_batched_graph` (the IMRT plan in one CUDA-graph launch, and its time to
-1 % measured the same way), `methods`, `apr_build`, `denoised`, `transport`,
-`clocks`, `gpu_launches`.
+its stream), `cpu_baseline` (the oracle on a bounded stratified sample on
+the host cores), `time_to_1pct` (a whole plan timed from psl_build to
+dose_readout, its histories raised until the isocentre uncertainty is
+<= 1 %), `workload_10x10` (the 10x10 slab workload: histories/s and its
+measured time to 1 %), `imrt_batched_graph` (the IMRT plan autotuned and in
+one CUDA-graph launch, and its time to 1 % measured the same way),
+`methods`, `apr_build`, `denoised`, `transport`, `tally_memory`, `clocks`,
+`gpu_launches`.
 
-`--impl reference` times the CPU oracle as the reference arm, on the same workload.
+`--impl reference` times the CPU oracle as the reference arm, on the same
+workload and the same sample size.  `--conv N CI CO` only times the
+denoiser's convolution kernel (for profiling).
 """
 from __future__ import annotations
 
@@ -166,84 +173,326 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
-def run_reference(args, rank, world):
-    """The CPU oracle as the reference arm: each step transports a bounded
-    sample of the workload's histories on the host cores."""
-    if rank != 0:
-        return
-    import oracle
+def oracle_setup(w):
+    """The oracle's PSL build and plan of the whole phase space (timed)."""
     from oracle import source
-    from paper_1302_1861_b300 import inputs
-
-    w = inputs.config2()
     t0 = time.perf_counter()
     st = source.psl_build(w.records, w.binning)
     pl = source.make_plan(st, w.beams, w.n_histories, w.seed, w.z_psl, w.sad)
-    t_setup = time.perf_counter() - t0
+    return st, pl, time.perf_counter() - t0
+
+
+def oracle_sample_seconds(w, st, pl, n_sample, nthreads, offset=0):
+    """Seconds the oracle takes for `n_sample` histories of the plan: 20
+    runs of n_sample / 20 consecutive histories, one in each twentieth of
+    the reading order (it is energy major, so every stratum is sampled),
+    shifted by `offset` within its stratum; source stage and transport."""
+    import oracle
+    from oracle import source
+    k = 20
+    per = max(1, n_sample // k)
+    stride = w.n_histories // k
+    tot = 0.0
+    for j in range(k):
+        h0 = j * stride + (offset % max(1, stride - per))
+        hs = np.arange(h0, h0 + per)
+        t = time.perf_counter()
+        s = source.source(pl, st, w.records, w.beams, w.phantom, hs, w.z_psl, w.sad)
+        m = s.status == source.ST_TRANSPORT
+        oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
+                         hs[m].astype(np.uint64), w.phantom, w.seed, nthreads=nthreads)
+        tot += time.perf_counter() - t
+    return tot, per * k
+
+
+def headline_workload():
+    from paper_1302_1861_b300 import inputs
+    return inputs.config3()
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm, on the headline workload: the
+    oracle's PSL build and plan of all records once, then each step a
+    bounded stratified sample of the plan's histories on every host core,
+    the whole-plan time scaled from the setup and the per-history time."""
+    if rank != 0:
+        return
+    w = headline_workload()
+    st, pl, t_setup = oracle_setup(w)
     n_s = args.ref_sample
     rng = np.random.default_rng(7)
     # every host core (a launcher's OMP_NUM_THREADS=1 is meant for the GPU ranks)
     cores = os.cpu_count()
 
-    def step(k):
-        h0 = int(rng.integers(0, w.n_histories - n_s))
-        t = time.perf_counter()
-        s = source.source(pl, st, w.records, w.beams, w.phantom, np.arange(h0, h0 + n_s), w.z_psl, w.sad)
-        m = s.status == source.ST_TRANSPORT
-        oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
-                         np.arange(h0, h0 + n_s)[m].astype(np.uint64), w.phantom, w.seed, nthreads=cores)
-        return time.perf_counter() - t
+    def step():
+        secs, n = oracle_sample_seconds(w, st, pl, n_s, cores, int(rng.integers(0, 1 << 30)))
+        return secs / n
 
-    for k in range(args.warmup):
-        step(k)
-    times = [step(k) for k in range(args.steps)]
-    t_h = float(np.mean(times)) / n_s
+    for _ in range(args.warmup):
+        step()
+    t_h = float(np.mean([step() for _ in range(args.steps)]))
     value = w.n_histories / (t_setup + t_h * w.n_histories)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * (t_setup + t_h * w.n_histories), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "records": w.records.n, "histories": w.n_histories,
-                       "phantom": "64^3 x 0.25 cm slab", "batches": w.n_batches},
+            "config": workload_config(w, w.n_histories, world),
             "cpu_baseline": {"value": value, "unit": "histories/s", "cores": cores, "kind": "oracle",
-                             "sample": f"psl_build+plan on all {w.records.n} records ({t_setup:.2f} s) + "
-                                       f"{args.steps} x {n_s} histories at random offsets, scaled to 1e8"},
+                             "sample": f"psl_build+plan of all {w.records.n} records ({t_setup:.2f} s) + per step "
+                                       f"{n_s} histories in 20 strata of the reading order "
+                                       f"({t_h * n_s:.2f} s), scaled to {w.n_histories} histories"},
             "e2e": {"value": value, "unit": "histories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def cpu_baseline(n_sample=40_000):
-    """The oracle as it stands on a bounded sample of the same workload."""
-    import oracle
-    from oracle import source
-    from paper_1302_1861_b300 import inputs
-    w = inputs.config2()
-    t0 = time.perf_counter()
-    st = source.psl_build(w.records, w.binning)
-    pl = source.make_plan(st, w.beams, w.n_histories, w.seed, w.z_psl, w.sad)
-    t_setup = time.perf_counter() - t0
-    h0 = 50_000_000
-    hs = np.arange(h0, h0 + n_sample)
-    t1 = time.perf_counter()
-    s = source.source(pl, st, w.records, w.beams, w.phantom, hs, w.z_psl, w.sad)
-    m = s.status == source.ST_TRANSPORT
-    oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
-                     hs[m].astype(np.uint64), w.phantom, w.seed, nthreads=os.cpu_count())
-    t_h = (time.perf_counter() - t1) / n_sample
+def cpu_baseline(w, n_sample):
+    """The oracle as it stands on a bounded sample of the headline workload:
+    the same setup and the same stratified sample size as the reference arm,
+    on every host core, and a quarter of it on one thread."""
+    st, pl, t_setup = oracle_setup(w)
+    cores = os.cpu_count()
+    secs, n = oracle_sample_seconds(w, st, pl, n_sample, cores)
+    t_h = secs / n
     value = w.n_histories / (t_setup + t_h * w.n_histories)
-    # the same on one thread, a quarter of the sample
-    hs1 = hs[: n_sample // 4]
-    t1 = time.perf_counter()
-    s = source.source(pl, st, w.records, w.beams, w.phantom, hs1, w.z_psl, w.sad)
-    m = s.status == source.ST_TRANSPORT
-    oracle.transport(s.ptype[m], s.pos[m], s.dir[m], s.e[m], s.wt[m].astype(float),
-                     hs1[m].astype(np.uint64), w.phantom, w.seed, nthreads=1)
-    t_h1 = (time.perf_counter() - t1) / len(hs1)
-    return {"value": value, "unit": "histories/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"psl_build+plan of all {w.records.n} records ({t_setup:.2f} s) + {n_sample} histories "
-                      f"from history {h0} ({t_h * n_sample:.2f} s), scaled to {w.n_histories} histories",
+    secs1, n1 = oracle_sample_seconds(w, st, pl, n_sample // 4, 1)
+    t_h1 = secs1 / n1
+    return {"value": value, "unit": "histories/s", "cores": cores, "kind": "oracle",
+            "sample": f"psl_build+plan of all {w.records.n} records ({t_setup:.2f} s) + {n} histories in 20 strata "
+                      f"of the reading order ({secs:.2f} s), scaled to {w.n_histories} histories",
             "one_thread": {"value": w.n_histories / (t_setup + t_h1 * w.n_histories), "unit": "histories/s",
-                           "sample": f"the same setup + {len(hs1)} histories on 1 thread ({t_h1 * len(hs1):.2f} s)"}}
+                           "sample": f"the same setup + {n1} histories on 1 thread ({secs1:.2f} s)"}}
+
+
+def workload_config(w, per_rank, world):
+    phantoms = {"psl-10x10-slab64": "64^3 x 0.25 cm water + lung/bone slabs",
+                "psl-30x30-ct128": "128^3 x 0.25 cm CT-like (air, lung, soft tissue, bone ellipsoids)"}
+    return {"workload": w.name, "records": w.records.n, "psl_bins": w.binning.n_bins,
+            "field": "30x30 cm jaws + 40x40 fluence map" if w.index == 3 else "10x10 cm jaws",
+            "phantom": phantoms.get(w.name, str(w.phantom.shape)), "histories_per_gpu": per_rank,
+            "batches": w.n_batches, "l2": "inputs > L2 and L2 flushed between steps",
+            "parallelism": f"history-range shards x{world}"}
+
+
+class Ctx:
+    """What the measurement helpers share: the torch / library modules, the
+    run's ranks and the L2 flush buffer."""
+
+    def __init__(self, torch, dist, capi, engine, inputs, rank, world, local, args):
+        self.torch, self.dist, self.capi, self.engine, self.inputs = torch, dist, capi, engine, inputs
+        self.rank, self.world, self.local, self.args = rank, world, local, args
+        self.flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+        self.torch.cuda.synchronize()
+
+    def max_over_ranks(self, v):
+        if self.world > 1:
+            tt = self.torch.tensor([v], device="cuda", dtype=self.torch.float64)
+            self.dist.all_reduce(tt, op=self.dist.ReduceOp.MAX)
+            v = float(tt.item())
+        return v
+
+
+def make_step(c, w, tally, first, per_rank, n_plan):
+    """psl_build + psl_plan_create + the rank's histories + (N > 1: the
+    int64 sum of every rank's tally) + dose_readout.  Default: the rank's
+    whole range in one psl_run call; plain: psl_source_batch +
+    transport_run piece by piece (N_b pieces).  Every history's deposits go
+    to the tally slice (batch) of its id."""
+    capi, engine = c.capi, c.engine
+    phys = capi.physics()
+
+    def step(dwx, out, plain=False):
+        store = capi.psl_build(dwx.params, dwx.records)
+        plan = capi.psl_plan_create(store, dwx.beams, w.sad, n_plan, w.seed)
+        capi.psl_tally_reset(tally)
+        if plain:
+            for f0, cnt in engine.chunks(first, per_rank, -(-per_rank // w.n_batches)):
+                batch = capi.psl_source_batch(plan, dwx.phantom, f0, cnt, 1)
+                capi.transport_run(dwx.phantom, phys, batch, tally, capi.SLICE_BY_HISTORY)
+                batch.close()
+        else:
+            capi.psl_run(plan, dwx.phantom, phys, tally, first, per_rank)
+        if c.world > 1:
+            engine.reduce_tallies(tally)                # one dose from all ranks' histories
+        norm = engine.normalisation(plan, per_rank * c.world)
+        capi.dose_readout(tally, dwx.phantom, norm, out[0], out[1], out[2])
+        return store, plan
+    return step
+
+
+def timed_steps(c, step, dw, out, steps, plain=False):
+    """Device time of `steps` steps (CUDA events on the launching stream,
+    barrier + synchronize on both sides, L2 flushed before each)."""
+    torch = c.torch
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(steps):
+        c.flush.fill_(1.0)
+        c.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(dw, out, plain)
+        e1.record(stream)
+        c.barrier()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return times
+
+
+def isocentre_slice(w):
+    iso = np.array(w.beams[0].iso) - np.array(w.phantom.origin)
+    ic = (iso / np.array(w.phantom.voxel)).astype(int)[::-1]
+    return tuple(slice(k - 1, k + 2) for k in ic)
+
+
+def e2e_run(c, w, step, out, steps, warmup):
+    """End to end through the C ABI: every step uploads its records and
+    phantom from pinned host memory and reads back dose, sigma and ledger,
+    all inside the timed region.  Double-buffered: step k+1's inputs go up
+    on a copy stream while step k computes (the copy engine runs beside the
+    kernels), as a service taking plan after plan would stream them."""
+    torch, engine = c.torch, c.engine
+    stream = torch.cuda.current_stream()
+    nvox = int(np.prod(w.phantom.shape))
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.records.arrays()]
+    host_mat = torch.from_numpy(np.ascontiguousarray(w.phantom.mat)).pin_memory()
+    host_rho = torch.from_numpy(np.ascontiguousarray(w.phantom.rho)).pin_memory()
+    dws = [engine.upload(w, records=[torch.empty_like(h, device="cuda") for h in host]) for _ in range(2)]
+    out_h = torch.empty(2 * nvox + 3, dtype=torch.float64).pin_memory()
+    bi = sum(h.numel() * h.element_size() for h in host) + host_mat.numel() + host_rho.numel() * 4
+    bo = out_h.numel() * 8
+    cstream = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_free = [torch.cuda.Event() for _ in range(2)]
+    for e in ev_free:
+        e.record(stream)
+
+    def upload(slot):
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(ev_free[slot])            # the step that used this buffer is done
+            for hh, dd in zip(host, dws[slot].rec_t):
+                dd.copy_(hh, non_blocking=True)
+            dws[slot].mat_t.copy_(host_mat, non_blocking=True)
+            dws[slot].rho_t.copy_(host_rho, non_blocking=True)
+            ev_in[slot].record(cstream)
+
+    def run(k_steps):
+        upload(0)
+        for k in range(k_steps):
+            slot = k & 1
+            if k + 1 < k_steps:
+                upload(slot ^ 1)
+            stream.wait_event(ev_in[slot])
+            c.flush.fill_(1.0)
+            step(dws[slot], out)
+            ev_free[slot].record(stream)
+            out_h[:nvox].copy_(out[0], non_blocking=True)
+            out_h[nvox:2 * nvox].copy_(out[1], non_blocking=True)
+            out_h[2 * nvox:].copy_(out[2], non_blocking=True)
+        torch.cuda.synchronize()
+
+    run(warmup)
+    c.barrier()
+    t0 = time.perf_counter()
+    run(steps)
+    te = c.max_over_ranks((time.perf_counter() - t0) / steps)
+    del dws
+    return te, int(bi), int(bo)
+
+
+def measure(c, w, steps, warmup, with_e2e, with_t1pct, with_plain, profile=False):
+    """The workload's step timed on this rank's history shard, and what
+    goes with it: plain per-batch form, e2e, time to 1 %, counters."""
+    torch, capi, engine = c.torch, c.capi, c.engine
+    per_rank = w.n_histories if c.args.histories is None else c.args.histories
+    # weak scaling: rank r transports histories [r*N, (r+1)*N) of a plan of world*N histories
+    first, per_rank, n_plan = engine.shard_histories(c.rank, c.world, per_rank)
+    dw = engine.upload(w)
+    nz, ny, nx = w.phantom.shape
+    nvox = nx * ny * nz
+    out = (torch.empty(nvox, dtype=torch.float64, device="cuda"),
+           torch.empty(nvox, dtype=torch.float64, device="cuda"),
+           torch.empty(3, dtype=torch.float64, device="cuda"))
+    tally = capi.psl_tally_create(dw.phantom, w.n_batches)       # device buffers held across steps
+    step = make_step(c, w, tally, first, per_rank, n_plan)
+    for _ in range(warmup):
+        step(dw, out)
+    c.barrier()
+    clocks = ClockSampler(c.local) if profile else None
+    if profile:
+        capi.profile(True)
+        n_launch0 = capi.kernel_launches()
+        clocks.start()
+    times = timed_steps(c, step, dw, out, steps)
+    r = {"w": w, "per_rank": per_rank, "dw": dw, "tally": tally, "out": out}
+    if profile:
+        r["clocks"] = clocks.stop()
+        r["launches"] = capi.kernel_launches() - n_launch0
+        r["prof"] = capi.profile_read()
+        capi.profile(False)
+    t_step = c.max_over_ranks(float(np.mean(times)))
+    r["t_step"] = t_step
+    r["value"] = per_rank * c.world / t_step
+    lg = out[2].cpu().numpy()
+    raw = torch.empty(12, dtype=torch.int64, device="cuda")
+    capi.psl_tally_read(tally, None, raw)
+    r["counts"] = raw.cpu().numpy()            # event and atomic counters of the last step (all ranks)
+    r["energy_balance"] = float((lg[1] + lg[2] - lg[0]) / lg[0])
+    r["ledger_mev"] = [float(x) for x in lg]
+    d = out[0].view(nz, ny, nx).cpu().numpy()
+    s = out[1].view(nz, ny, nx).cpu().numpy()
+    sl = isocentre_slice(w)
+    rel = float((s[sl] / d[sl]).mean())
+    r["iso_rel"] = rel
+    n_1pct = per_rank * c.world * (rel / 0.01) ** 2
+    if with_plain:
+        pt = timed_steps(c, step, dw, out, 2, plain=True)
+        r["plain"] = per_rank * c.world / c.max_over_ranks(float(np.mean(pt[1:])))
+    if with_t1pct and c.rank == 0 and c.world == 1:
+        t1 = time_to_1pct(capi, torch, w, dw, capi.physics(), n_1pct, sl, (nz, ny, nx))
+        t1["extrapolated_histories"] = n_1pct
+        t1["extrapolated_seconds"] = n_1pct / (per_rank / t_step)
+        r["t1pct"] = t1
+    else:
+        r["t1pct"] = {"histories": n_1pct, "seconds": n_1pct / r["value"], "isocentre_rel_sigma_at_run": rel,
+                      "kind": "extrapolated from the run's sigma"}
+    if with_e2e:
+        te, bi, bo = e2e_run(c, w, step, out, steps, warmup)
+        r["e2e"] = {"value": per_rank * c.world / te, "unit": "histories/s", "h2d_bytes_per_step": bi,
+                    "d2h_bytes_per_step": bo,
+                    "note": "every step uploads its records and phantom from pinned host memory and reads back "
+                            "dose, sigma and ledger; step k+1's upload runs on a copy stream during step k (two "
+                            "device buffers); the first upload and the last read-back are inside the timed region"}
+    return r
+
+
+def conv_only(args):
+    """Only the tensor-core convolution of the denoiser on an n^3 volume,
+    ci -> co channels (random BF16 data): two calls, then the median of
+    four timed calls (for profiling one launch of its kernel)."""
+    import torch
+    from paper_1302_1861_b300 import capi
+    n, ci, co = args.conv
+    x = torch.randn(n ** 3 * ci, device="cuda").to(torch.bfloat16)
+    wt = torch.randn(27 * ci * co, device="cuda") * 0.05
+    wpk = capi.conv3d_pack(wt, ci, co)
+    out = torch.empty(n ** 3 * co, dtype=torch.bfloat16, device="cuda")
+    ts = []
+    for it in range(2 + args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        capi.conv3d(x.view(torch.int16), ci, wpk, None, co, n, n, n, True, out.view(torch.int16))
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= 2:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    t = float(np.median(ts)) if ts else float("nan")
+    fl = 2.0 * n ** 3 * 27 * ci * co
+    print(json.dumps({"conv": f"{n}^3 x {ci}->{co}", "ms": 1e3 * t, "tflops": fl / t / 1e12}))
 
 
 # --------------------------------------------------------------------------
@@ -254,7 +503,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--histories", type=int, default=None, help="override histories per rank (profiling only)")
-    ap.add_argument("--ref-sample", type=int, default=20_000)
+    ap.add_argument("--workload", default="ct", choices=["ct", "slab"],
+                    help="headline workload (slab: the 10x10 one, for profiling only)")
+    ap.add_argument("--ref-sample", type=int, default=40_000)
+    ap.add_argument("--conv", nargs=3, type=int, metavar=("N", "CI", "CO"),
+                    help="only time the denoiser's tensor-core convolution (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-imrt", action="store_true")
@@ -263,6 +516,7 @@ def main():
     ap.add_argument("--no-methods", action="store_true")
     ap.add_argument("--no-t1pct", action="store_true")
     ap.add_argument("--no-denoise", action="store_true")
+    ap.add_argument("--no-slab", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -271,6 +525,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.conv:
+        conv_only(args)
         return
 
     import torch
@@ -281,188 +538,23 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    c = Ctx(torch, dist, capi, engine, inputs, rank, world, local, args)
 
+    w = headline_workload() if args.workload == "ct" else inputs.config2()
     # cpu baseline before any heavy GPU work (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(w, args.ref_sample)
 
-    w = inputs.config2()
-    per_rank = w.n_histories if args.histories is None else args.histories
-    # weak scaling: rank r transports histories [r*N, (r+1)*N) of a plan of world*N histories
-    first, per_rank, n_plan = engine.shard_histories(rank, world, per_rank)
-    nb = w.n_batches
-    dw = engine.upload(w)
-    stream = torch.cuda.current_stream()
-    nz, ny, nx = w.phantom.shape
-    nvox = nx * ny * nz
-    dose = torch.empty(nvox, dtype=torch.float64, device="cuda")
-    sigma = torch.empty_like(dose)
-    ledger = torch.empty(3, dtype=torch.float64, device="cuda")
-    phys = capi.physics()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    tally = capi.psl_tally_create(dw.phantom, nb)       # device buffers held across steps
-
-    def step(dwx, out_dose, plain=False):
-        """psl_build + psl_plan_create + all histories + dose_readout.
-        Default: the whole range in one psl_run call (no host
-        synchronisation); plain: psl_source_batch + transport_run piece by
-        piece (N_b pieces).  Either way every history's deposits go to the
-        tally slice (batch) of its id."""
-        store = capi.psl_build(dwx.params, dwx.records)
-        plan = capi.psl_plan_create(store, dwx.beams, w.sad, n_plan, w.seed)
-        capi.psl_tally_reset(tally)
-        if plain:
-            for f0, cnt in engine.chunks(first, per_rank, -(-per_rank // nb)):
-                batch = capi.psl_source_batch(plan, dwx.phantom, f0, cnt, 1)
-                capi.transport_run(dwx.phantom, phys, batch, tally, capi.SLICE_BY_HISTORY)
-                batch.close()
-        else:
-            capi.psl_run(plan, dwx.phantom, phys, tally, first, per_rank)
-        _, n_total, _ = plan.info()
-        norm = engine.normalisation(n_total, per_rank, w.records.n * w.binning.apr_copies)
-        capi.dose_readout(tally, dwx.phantom, norm, out_dose[0], out_dose[1], out_dose[2])
-        return store, plan, tally
-
-    for _ in range(args.warmup):
-        step(dw, (dose, sigma, ledger))
-    torch.cuda.synchronize()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    times = []
-    capi.profile(True)
-    n_launch0 = capi.kernel_launches()
-    clocks.start()
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(dw, (dose, sigma, ledger))
-        e1.record(stream)
-        barrier()
-        times.append(e0.elapsed_time(e1) / 1e3)
-    clk = clocks.stop()
-    launches = capi.kernel_launches() - n_launch0
-    prof = capi.profile_read()
-    capi.profile(False)
-
-    t_step = float(np.mean(times))
-    if world > 1:
-        tt = torch.tensor([t_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = per_rank * world / t_step
-
-    # the plain form (batch by batch, host checks per generation), for comparison
-    plain_times = []
-    for _ in range(0 if args.no_plain else 2):
-        flush.fill_(1.0)
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(dw, (dose, sigma, ledger), plain=True)
-        e1.record(stream)
-        barrier()
-        plain_times.append(e0.elapsed_time(e1) / 1e3)
-    t_plain = float(np.mean(plain_times[1:])) if plain_times else float("nan")
-
-    # ledger and isocentre uncertainty of the last step
-    lg = ledger.cpu().numpy()
-    raw = torch.empty(12, dtype=torch.int64, device="cuda")
-    capi.psl_tally_read(tally, None, raw)
-    counts = raw.cpu().numpy()            # event and atomic counters of the last step
-    atom_peak = capi.atomic_peak(nvox, 1 << 30)
-    d = dose.view(nz, ny, nx).cpu().numpy()
-    s = sigma.view(nz, ny, nx).cpu().numpy()
-    iso = np.array(w.beams[0].iso) - np.array(w.phantom.origin)
-    ic = (iso / np.array(w.phantom.voxel)).astype(int)[::-1]
-    sl = tuple(slice(c - 1, c + 2) for c in ic)
-    rel = float((s[sl] / d[sl]).mean())
-    n_1pct = per_rank * (rel / 0.01) ** 2
-
-    # time to 1 % at the isocentre, measured: whole plans of N histories, N
-    # from the run's sigma, raised until the criterion holds
-    t1pct = None
-    if rank == 0 and world == 1 and not args.no_t1pct:
-        t1pct = time_to_1pct(capi, torch, w, dw, phys, per_rank * (rel / 0.01) ** 2, sl, (nz, ny, nx))
-        t1pct["extrapolated_histories"] = n_1pct
-        t1pct["extrapolated_seconds"] = n_1pct / (per_rank / t_step)
-
-    # e2e: pinned host records/phantom uploaded and results read back inside
-    # the timed region, every step.  Double-buffered: step k+1's inputs go up
-    # on a copy stream while step k computes (the copy engine runs beside the
-    # kernels), as a service taking plan after plan would stream them.
-    e2e = None
-    if not args.no_e2e:
-        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.records.arrays()]
-        host_mat = torch.from_numpy(np.ascontiguousarray(w.phantom.mat)).pin_memory()
-        host_rho = torch.from_numpy(np.ascontiguousarray(w.phantom.rho)).pin_memory()
-        dws = []
-        for _ in range(2):
-            dev = [torch.empty_like(h, device="cuda") for h in host]
-            dws.append(engine.upload(w, records=dev))
-        out_h = torch.empty(2 * nvox + 3, dtype=torch.float64).pin_memory()
-        bi = sum(h.numel() * h.element_size() for h in host) + host_mat.numel() + host_rho.numel() * 4
-        bo = out_h.numel() * 8
-        cstream = torch.cuda.Stream()
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_free = [torch.cuda.Event() for _ in range(2)]
-        for e in ev_free:
-            e.record(stream)
-
-        def upload(slot):
-            with torch.cuda.stream(cstream):
-                cstream.wait_event(ev_free[slot])            # the step that used this buffer is done
-                for hh, dd in zip(host, dws[slot].rec_t):
-                    dd.copy_(hh, non_blocking=True)
-                dws[slot].mat_t.copy_(host_mat, non_blocking=True)
-                dws[slot].rho_t.copy_(host_rho, non_blocking=True)
-                ev_in[slot].record(cstream)
-
-        def run(k_steps):
-            upload(0)
-            for k in range(k_steps):
-                slot = k & 1
-                if k + 1 < k_steps:
-                    upload(slot ^ 1)
-                stream.wait_event(ev_in[slot])
-                flush.fill_(1.0)
-                step(dws[slot], (dose, sigma, ledger))
-                ev_free[slot].record(stream)
-                out_h[:nvox].copy_(dose, non_blocking=True)
-                out_h[nvox:2 * nvox].copy_(sigma, non_blocking=True)
-                out_h[2 * nvox:].copy_(ledger, non_blocking=True)
-            torch.cuda.synchronize()
-
-        run(args.warmup)
-        barrier()
-        t0 = time.perf_counter()
-        run(args.steps)
-        te = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": per_rank * world / te, "unit": "histories/s", "h2d_bytes_per_step": int(bi),
-               "d2h_bytes_per_step": int(bo),
-               "note": "every step uploads its records and phantom from pinned host memory and reads back dose, "
-                       "sigma and ledger; step k+1's upload runs on a copy stream during step k (two device "
-                       "buffers); the first upload and the last read-back are inside the timed region"}
+    h = measure(c, w, args.steps, args.warmup, not args.no_e2e, not args.no_t1pct, not args.no_plain, profile=True)
+    prof, counts, per_rank, t_step = h["prof"], h["counts"], h["per_rank"], h["t_step"]
+    atom_peak = capi.atomic_peak(int(np.prod(w.phantom.shape)), 1 << 30)
 
     # roofline of the dominant kernel (largest device time in the timed region)
     peaks, pk_kind = measured_peaks()
     name, (ms_tot, nl) = max(prof.items(), key=lambda kv: kv[1][0])
     per_launch_s = ms_tot / 1e3 / max(nl, 1)
-    roof = roofline_for(name, per_launch_s, nl, args.steps, w, per_rank, peaks, pk_kind, counts)
+    roof = roofline_for(name, per_launch_s, nl, args.steps, w, per_rank, peaks, pk_kind, counts, atom_peak)
     rooflines = rooflines_per_step(prof, args.steps, w, per_rank, peaks, counts)
     ms_e = prof["electron"][0] / args.steps / 1e3
     ms_p = prof["photon"][0] / args.steps / 1e3
@@ -471,39 +563,58 @@ def main():
                  "tally_atomics": {"photon": int(counts[8]), "electron": int(counts[9])},
                  "atomics_per_s": {"photon": counts[8] / ms_p, "electron": counts[9] / ms_e},
                  "atomic_peak_per_s": atom_peak, "atomic_peak_kind": "measured: psl_atomic_peak, int64 adds into "
-                                                                    f"{nvox} cells"}
+                                                                    f"{int(np.prod(w.phantom.shape))} cells"}
+    n_counters, ws_bytes, qdepth, bps = capi.psl_tally_info(h["tally"])
+    h["tally"].close()
+    del h["dw"]
 
+    # the 10x10 workload: its own steps and measured time to 1 %
+    slab = None
+    if rank == 0 and world == 1 and not args.no_slab and args.workload == "ct":
+        s2 = measure(c, inputs.config2(), max(3, args.steps // 2), args.warmup, False, not args.no_t1pct,
+                     False)
+        s2["tally"].close()
+        slab = {"workload": s2["w"].name, "value": s2["value"], "unit": "histories/s",
+                "ms_per_step": 1e3 * s2["t_step"], "time_to_1pct": s2["t1pct"],
+                "energy_balance": s2["energy_balance"]}
+        del s2
     imrt = None
     if rank == 0 and world == 1 and not args.no_imrt:
-        imrt = imrt_run(capi, engine, inputs, torch)
+        imrt = imrt_run(capi, engine, inputs, torch, w.records if w.index == 3 else None)
     apr = None
     if rank == 0 and world == 1 and not args.no_apr:
-        apr = apr_build(capi, engine, inputs, torch, flush)
+        apr = apr_build(capi, engine, inputs, torch, c.flush)
     denoised = None
     if rank == 0 and world == 1 and not args.no_denoise:
-        denoised = denoised_run(capi, torch, w, flush, peaks_for_denoise())
+        measured_1pct = {w.name: h["t1pct"] if h["t1pct"].get("kind") == "measured" else None}
+        if slab and slab["time_to_1pct"].get("kind") == "measured":
+            measured_1pct["psl-10x10-slab64"] = slab["time_to_1pct"]
+        denoised = denoised_run(capi, torch, c.flush, peaks_for_denoise(), measured_1pct)
     methods = None
     if rank == 0 and world == 1 and not args.no_methods:
-        methods = stream_method_run(capi, engine, torch, flush, w, dw, per_rank)
-        methods["method3_psl_histories_per_s"] = value
+        w2 = inputs.config2()
+        methods = stream_method_run(capi, engine, torch, c.flush, w2, engine.upload(w2), w2.n_histories)
+        if slab:
+            methods["method3_psl_histories_per_s"] = slab["value"]
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "histories/s", "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC, "value": h["value"], "unit": "histories/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic (seeded 6 MV-like phase space, slab phantom)",
-                "config": {"workload": w.name, "records": w.records.n, "psl_bins": w.binning.n_bins,
-                           "phantom": "64^3 x 0.25 cm water + lung/bone slabs", "histories_per_gpu": per_rank,
-                           "batches": nb, "l2": "inputs > L2 and L2 flushed between steps",
-                           "parallelism": f"history-range shards x{world}"},
-                "e2e": e2e, "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": int(launches),
-                "time_to_1pct": t1pct if t1pct is not None else
-                {"histories": n_1pct, "seconds": n_1pct / (per_rank / t_step), "isocentre_rel_sigma_at_run": rel,
-                 "kind": "extrapolated from the run's sigma"},
-                "energy_balance": float((lg[1] + lg[2] - lg[0]) / lg[0]),
+                "data": "synthetic (seeded 6 MV-like phase space, CT-like phantom)",
+                "config": workload_config(w, per_rank, world),
+                "e2e": h.get("e2e"), "roofline": roof, "rooflines": rooflines, "cpu_baseline": cpu,
+                "clocks": h["clocks"], "gpu_launches": int(h["launches"]),
+                "time_to_1pct": h["t1pct"],
+                "energy_balance": h["energy_balance"],
+                "ledger_mev": {"emitted": h["ledger_mev"][0], "escaped": h["ledger_mev"][1],
+                               "deposited": h["ledger_mev"][2],
+                               "note": "one dose of all ranks' histories (int64 tallies summed over ranks)"},
                 "transport": transport,
-                "modes": {"batched_psl_run": value, "plain_per_batch": per_rank * world / t_plain,
-                          "unit": "histories/s"},
+                "tally_memory": {"counters": n_counters, "workspace_bytes": ws_bytes, "queue_depth": qdepth,
+                                 "blocks_per_sm": bps},
+                "modes": {"batched_psl_run": h["value"], "plain_per_batch": h.get("plain"), "unit": "histories/s"},
+                "workload_10x10": slab,
                 "imrt_batched_graph": imrt,
                 "apr_build": apr,
                 "methods": methods,
@@ -541,21 +652,22 @@ def conv_flops(V):
     return sum(2.0 * (V / 8 ** lev) * 27 * ci * co for lev, ci, co in lay)
 
 
-def denoised_run(capi, torch, w, flush, peaks):
+def denoised_run(capi, torch, flush, peaks, measured_1pct=None):
     """The denoised form: trained weights (the package's
     weights/denoiser_psl.npy, trained by `python -m
     paper_1302_1861_b300.denoiser` on pairs the method generated on other
-    seeded geometries); on this workload (10x10 slab) and on the 30x30 CT
-    workload, a plain 4e9-history reference, low-history runs denoised and
-    scored in the body, and the plain run to 1 % extrapolated from the
-    reference; the tensor-core convolution timed alone on its heaviest
+    seeded geometries); on the 10x10 slab and the 30x30 CT workloads, a
+    plain 4e9-history reference, low-history runs denoised and scored in the
+    body, beside the plain run to 1 % (measured on whole plans by the
+    headline and 10x10 legs when given, else extrapolated from the
+    reference); the tensor-core convolution timed alone on its heaviest
     shape, and the network's inference on a full 128^3 volume."""
     from paper_1302_1861_b300 import denoiser as dz
     path = os.path.join(ROOT, "paper_1302_1861_b300", "weights", "denoiser_psl.npy")
     if not os.path.exists(path):
         return {"unavailable": "no trained weights"}
     den = dz.load(path)
-    held_out = dz.held_out_report(den, log=None)
+    held_out = dz.held_out_report(den, log=None, plain_1pct=measured_1pct)
     # the convolution kernel alone: 128^3 voxels, 128 -> 128 channels (1.9e12 FLOP)
     V, ci, co = 128 ** 3, 128, 128
     x = torch.randn(V * ci, device="cuda").to(torch.bfloat16)
@@ -619,7 +731,7 @@ def time_to_1pct(capi, torch, w, dw, phys, n_est, sl, shape):
         plan = capi.psl_plan_create(store, dw.beams, w.sad, n, w.seed)
         capi.psl_run(plan, dw.phantom, phys, tally, 0, n)
         _, n_total, _ = plan.info()
-        capi.dose_readout(tally, dw.phantom, engine.normalisation(n_total, n, w.records.n * w.binning.apr_copies),
+        capi.dose_readout(tally, dw.phantom, engine.normalisation(plan, n),
                           dose, sigma, lg)
         e1.record()
         torch.cuda.synchronize()
@@ -695,17 +807,21 @@ def apr_build(capi, engine, inputs, torch, flush, k=4):
             "ms": 1e3 * t, "sorted_records_per_s": n_records / t}
 
 
-def imrt_run(capi, engine, inputs, torch):
+def imrt_run(capi, engine, inputs, torch, records=None):
     """The batched IMRT plan (7 gantry angles x 10-60 segments, per-segment
     fluence, 4e7-record phase space, 128x128x100 CT-like phantom, 5e8
-    histories) as one CUDA-graph launch of psl_run: capture once, then time
-    the replays."""
-    w = inputs.config4()
+    histories) as one CUDA-graph launch of psl_run: the persistent grid and
+    queue depth picked by psl_autotune on 2e7 probe histories of the plan,
+    then capture once and time the replays."""
+    w = inputs.config4(records=records)
     dw = engine.upload(w)
     store = capi.psl_build(dw.params, dw.records)
     plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
     tally = capi.psl_tally_create(dw.phantom, w.n_batches)
     phys = capi.physics()
+    t0 = time.perf_counter()
+    tuned_grid, tuned_depth = capi.psl_autotune(plan, dw.phantom, phys, tally, 20_000_000)
+    t_tune = time.perf_counter() - t0
     capi.psl_run(plan, dw.phantom, phys, tally, 0, w.n_histories, use_graph=True)     # capture + first run
     times = []
     for _ in range(2):
@@ -723,7 +839,7 @@ def imrt_run(capi, engine, inputs, torch):
     sigma = torch.empty_like(dose)
     lg = torch.empty(3, dtype=torch.float64, device="cuda")
     n_entries, n_total, _ = plan.info()
-    capi.dose_readout(tally, dw.phantom, engine.normalisation(n_total, w.n_histories, w.records.n * w.binning.apr_copies), dose, sigma, lg)
+    capi.dose_readout(tally, dw.phantom, engine.normalisation(plan, w.n_histories), dose, sigma, lg)
     d = dose.view(nz, ny, nx).cpu().numpy()
     sg = sigma.view(nz, ny, nx).cpu().numpy()
     ic = ((np.array(w.beams[0].iso) - np.array(w.phantom.origin)) / np.array(w.phantom.voxel)).astype(int)[::-1]
@@ -739,6 +855,8 @@ def imrt_run(capi, engine, inputs, torch):
     t1 = time_to_1pct(capi, torch, w, dw, phys, n1, sl, (nz, ny, nx))
     return {"workload": w.name, "segments": len(w.beams), "psl_entries": n_entries, "histories": w.n_histories,
             "seconds_per_plan": t, "histories_per_s": rate, "launch": "one CUDA graph (psl_run, use_graph=1)",
+            "autotuned": {"blocks_per_sm": tuned_grid, "queue_depth": tuned_depth, "probe_histories": 20_000_000,
+                          "seconds": t_tune},
             "isocentre_rel_sigma": rel, "time_to_1pct_s": n1 / rate, "time_to_1pct_s_kind": "extrapolated",
             "time_to_1pct_measured": t1,
             "energy_balance": float((lgh[1] + lgh[2] - lgh[0]) / lgh[0])}
@@ -776,7 +894,7 @@ def rooflines_per_step(prof, steps, w, per_rank, peaks, counts):
     return out
 
 
-def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kind, counts):
+def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kind, counts, atom_peak=None):
     """Algorithmic bytes (HBM-bound kernels) or operations per launch over the
     measured launch duration."""
     hbm = float(peaks.get("hbm_gbs", 6400.0))
@@ -808,8 +926,16 @@ def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kin
     ach = events / per_step / per_launch_s / 1e9
     peak = THREAD_INST_PEAK / ipe / 1e9 if ipe else None
     traffic = DRAM_BYTES_PER_HISTORY.get(name, 0.0) * per_rank / per_step
+    # the tally's bound: the kernel's int64 atomics per second against the
+    # measured int64 atomic peak (psl_atomic_peak)
+    at = counts[9] if name == "electron" else counts[8]
+    atomic = None
+    if atom_peak:
+        a_rate = at / per_step / per_launch_s
+        atomic = {"achieved": a_rate, "peak": atom_peak, "unit": "int64 atomics/s", "frac": a_rate / atom_peak}
     return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gevents/s",
             "frac": ach / peak if peak else None, "traffic": traffic, "per_launch_ms": per_launch_s * 1e3,
+            "atomic_bound": atomic,
             "launches": launches, "events": "electron steps" if name == "electron" else "Woodcock steps",
             "events_per_launch": events / per_step,
             "peak_kind": "derived: 148 SMs x 4 issue/clk x 32 lanes x 2.032 GHz / %.1f thread instructions "

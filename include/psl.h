@@ -179,8 +179,11 @@ PSL_API int psl_build(const psl_params_t *params, const psl_records_t *records, 
  * inside another runtime's memory pool, under a fixed device-memory budget, or
  * in a process that must not call cudaMalloc after start-up.  The paper has
  * no counterpart; it is the same PSL sort written into caller arrays.
- * Scratch lives in one fixed device array of about 17 MB that every GPU that
- * loads this library holds until the process exits.  Limits: at most
+ * Scratch lives in one fixed device array of about 17 MB, part of the
+ * library's device code: a CUDA context commits it when it loads that code
+ * (with lazy module loading, at the first psl_build_static call in the
+ * context) and holds it until the context ends, so a caller under a fixed
+ * device-memory budget should make its first call at start-up.  Limits: at most
  * PSL_STATIC_MAX_RECORDS records, apr_copies = 1 (no redistribution) and
  * PSL_STATIC_MAX_EDGES bin edges
  * (nx+1 + ny+1 + n_ebins+1); larger inputs return PSL_EINVAL with the limit
@@ -188,8 +191,10 @@ PSL_API int psl_build(const psl_params_t *params, const psl_records_t *records, 
  * int64 and sorted [n x 8] float32 (16-byte aligned) in the psl_store_read
  * record layout (the
  * first *n_valid rows are written); *n_valid (host) receives the records
- * kept.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * kept.  The first call in each CUDA context looks up the array's device
+ * address there (cudaGetSymbolAddress; a context created again after
+ * cudaDeviceReset gets a lookup of its own), so make that first call before
+ * any stream capture.
  * All calls share the array: calls that overlap on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  Calls no
  * cudaMalloc, cudaFree or allocating library routine.  Synchronises stream. */
@@ -366,6 +371,35 @@ PSL_API int psl_tally_reset(psl_tally_t *tally, void *stream);
 #define PSL_ORDER_BATCH 2
 PSL_API int psl_tally_set_order(psl_tally_t *tally, int32_t order);
 
+/* Device addresses of the tally's own counters (outputs, NULL to skip):
+ * int64 [n_batches][nvox] (the psl_tally_read layout) and the int64 [12]
+ * ledger.  Owned by the tally, valid until psl_tally_destroy.  They are for
+ * combining tallies of one plan run in pieces by several processes (Sec.
+ * 2.3.3: a job split over GPUs): after every rank's transport has completed,
+ * an element-wise integer SUM of both arrays across the ranks (for example
+ * an NCCL all-reduce in place) leaves on every rank the tally of the whole
+ * history range, bit for bit, since the counters are integers and each
+ * history is run on one rank only; dose_readout then reads it as usual.  The
+ * caller orders its own work on these arrays with the library's streams. */
+PSL_API int psl_tally_buffers(psl_tally_t *tally, int64_t **tallies, int64_t **ledger);
+
+/* Sizes of a tally (host outputs, NULL to skip): its int64 counters
+ * (n_batches x voxels, the array of psl_tally_buffers); the device bytes of its transport workspace (0 until the first
+ * transport call sizes it: particle queues of 32 x 48 bytes per primary of
+ * a pass, i.e. 1536 bytes x the queue depth when a call runs at least that
+ * many histories, else x the call's histories; plus 4 bytes per voxel and
+ * the batch-order buffers); the queue depth (primaries per transport pass)
+ * and the persistent grid (256-thread blocks per SM) later calls use. */
+PSL_API int psl_tally_info(const psl_tally_t *tally, int64_t *n_counters, int64_t *workspace_bytes,
+                           int64_t *queue_depth, int32_t *blocks_per_sm);
+
+/* Set the queue depth (primaries per transport pass, 2^12 <= depth <= 2^26;
+ * default 2^24) of later transport calls on the tally: the bound on its
+ * transport workspace (1536 bytes per primary of a pass), for callers that
+ * share the device.  A workspace sized for a larger depth is kept until the
+ * tally is destroyed.  PSL_EINVAL outside the range. */
+PSL_API int psl_tally_set_queue_depth(psl_tally_t *tally, int64_t depth);
+
 /* Copy raw tallies (device int64 [n_batches][nvox]: batch b's voxels at
  * b * nvox, the layout the tally keeps, so that one batch's slice is
  * contiguous for the batch-by-batch order) and ledger (device int64 [12])
@@ -429,6 +463,22 @@ PSL_API int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *phantom, c
  * ledger: device float64 [3]; any may be NULL. */
 PSL_API int dose_readout(const psl_tally_t *tally, const psl_phantom_t *phantom, double norm, double *dose,
                  double *sigma, double *ledger, void *stream);
+
+/* Sec. 2.5: the normalisation factor of dose_readout,
+ *   norm = calibration * N_total^psl / (n_histories * N_incident),
+ * the paper's D = D_o N_total^phsp / (N_simulated N_incident) with the
+ * records of the PSLs the plan selected (N_total^psl, psl_plan_info) in place
+ * of the whole phase space, since the simulated histories are drawn from
+ * them only.  n_histories: the histories whose deposits the tally holds (all
+ * ranks of a split job together).  n_incident: the particles incident on the
+ * accelerator that the phase space stands for; 0 takes the plan's store
+ * records (input records x redistribution copies), the reading for a
+ * synthetic phase space that is its own incident set.  calibration: the
+ * absolute dose calibration factor (> 0; 1 for none).  Host output *norm.
+ * PSL_EINVAL for a null plan or output, n_histories <= 0, n_incident < 0 or
+ * calibration <= 0.  No device work. */
+PSL_API int psl_dose_normalisation(const psl_plan_t *plan, int64_t n_histories, int64_t n_incident,
+                                   double calibration, double *norm);
 
 /* Destroy functions free what the handle owns (NULL is ignored).  A tally's
  * transport workspace (its particle queues, ~30 x 48 B per primary of a

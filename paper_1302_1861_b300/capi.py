@@ -31,7 +31,8 @@ EXPORTS = (
     "psl_conv3d_packed_size", "psl_conv3d_pack", "psl_conv3d", "psl_conv3d_wgrad", "psl_denoiser_param_count",
     "psl_denoiser_create", "psl_denoiser_destroy", "psl_denoiser_params", "psl_denoiser_forward",
     "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma", "psl_conv3d_form", "psl_tally_set_order",
-    "psl_kth_smallest",
+    "psl_kth_smallest", "psl_tally_buffers", "psl_tally_info", "psl_tally_set_queue_depth",
+    "psl_dose_normalisation",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
@@ -141,6 +142,10 @@ def lib():
             "psl_conv3d_form": [i32],
             "psl_tally_set_order": [vp, i32],
             "psl_kth_smallest": [vp, i64, i64, vp, vp],
+            "psl_tally_buffers": [vp, vp, vp],
+            "psl_tally_info": [vp, vp, vp, vp, vp],
+            "psl_tally_set_queue_depth": [vp, i64],
+            "psl_dose_normalisation": [vp, i64, i64, f64, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -340,6 +345,13 @@ def psl_batch_read(batch: Batch, state=None, ptype=None, pid=None, stream=None):
     check(lib().psl_batch_read(batch.h, ptr(state), ptr(ptype), ptr(pid), stream_ptr(stream)))
 
 
+def memory_held() -> int:
+    """Bytes the library's device memory pool reserves on the current device
+    (psl_memory_trim asked to keep all of it; a transport workspace kept from
+    a destroyed tally is still freed)."""
+    return memory_trim(keep_bytes=(1 << 64) - 1)
+
+
 def memory_trim(keep_bytes: int = 0) -> int:
     """Free the transport workspace kept from a destroyed tally, then return
     the library pool's memory beyond keep_bytes to the driver; returns the
@@ -435,6 +447,32 @@ def kth_smallest(x, k: int, stream=None) -> float:
 
 def psl_tally_set_order(tally: Tally, order: int):
     check(lib().psl_tally_set_order(tally.h, int(order)))
+
+
+def psl_tally_buffers(tally: Tally):
+    """Device addresses of the tally's int64 counters [n_batches][nvox] and ledger [12]."""
+    t, g = vp(), vp()
+    check(lib().psl_tally_buffers(tally.h, ctypes.byref(t), ctypes.byref(g)))
+    return t.value, g.value
+
+
+def psl_tally_info(tally: Tally):
+    """(int64 counters, transport workspace bytes, queue depth, blocks per SM)."""
+    a, b, c, d = i64(), i64(), i64(), i32()
+    check(lib().psl_tally_info(tally.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def psl_tally_set_queue_depth(tally: Tally, depth: int):
+    check(lib().psl_tally_set_queue_depth(tally.h, int(depth)))
+
+
+def dose_normalisation(plan: Plan, n_histories: int, n_incident: int = 0, calibration: float = 1.0) -> float:
+    """Sec. 2.5 normalisation computed by the library (psl_dose_normalisation)."""
+    v = f64()
+    check(lib().psl_dose_normalisation(plan.h, int(n_histories), int(n_incident), float(calibration),
+                                       ctypes.byref(v)))
+    return v.value
 
 
 def psl_tally_reset(tally: Tally, stream=None):

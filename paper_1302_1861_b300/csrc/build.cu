@@ -358,7 +358,7 @@ namespace {
 constexpr size_t ST_MAX_N = PSL_STATIC_MAX_RECORDS;
 constexpr size_t ST_ROUND = 64;                                   // 256 bytes in 4-byte words
 constexpr size_t st_round(size_t w) { return (w + ST_ROUND - 1) / ST_ROUND * ST_ROUND; }
-constexpr size_t ST_TILES = (ST_MAX_N + 4095) / 4096;
+constexpr size_t ST_TILES = (ST_MAX_N + SORT_TILE - 1) / SORT_TILE;
 // word offsets of the regions
 constexpr size_t ST_KEYS0 = 0;
 constexpr size_t ST_KEYS1 = ST_KEYS0 + ST_MAX_N;
@@ -367,30 +367,74 @@ constexpr size_t ST_VALS1 = ST_VALS0 + ST_MAX_N;
 constexpr size_t ST_HIST = ST_VALS1 + ST_MAX_N;                  // digit histograms + kept count (int64)
 constexpr size_t ST_EDGES = ST_HIST + st_round(MAX_PASSES * RADIX + 4);
 constexpr size_t ST_SORT = ST_EDGES + st_round(PSL_STATIC_MAX_EDGES);
-constexpr size_t ST_SORT_WORDS = st_round(2 * SORT_MAX_PASSES * RADIX + 4 + ST_TILES * RADIX);
+constexpr size_t ST_SORT_WORDS = st_round(SORT_HEAD_WORDS + ST_TILES * 256);
 constexpr size_t ST_WORDS = ST_SORT + ST_SORT_WORDS;
+// sort_pairs_u32 writes SORT_HEAD_WORDS words, then a look-back table of 256
+// words per tile of SORT_TILE keys: the region must hold both at the limit
+static_assert(ST_SORT_WORDS >= SORT_HEAD_WORDS + ((ST_MAX_N + SORT_TILE - 1) / SORT_TILE) * 256,
+              "static sort scratch too small for sort_pairs_u32");
 
 // Held by every device that loads the library, until the process exits.
 static __device__ __align__(256) uint32_t g_build_scratch[ST_WORDS];
 
-std::mutex g_static_mu;
-uint32_t *g_static_addr[256] = {nullptr};
+// Device address of g_build_scratch in the current CUDA context.  Host code
+// cannot use the symbol itself as an address: it is looked up with
+// cudaGetSymbolAddress once per context (keyed by the driver's unique
+// context id, so a context torn down and created again - cudaDeviceReset -
+// gets its own lookup instead of a stale address).
+typedef int (*ctx_get_current_fn)(void **);                     // cuCtxGetCurrent
+typedef int (*ctx_get_id_fn)(void *, unsigned long long *);       // cuCtxGetId (driver API 12.0)
 
-// Device address of g_build_scratch on the current device (looked up once per
-// device; host code cannot use the symbol itself as an address).
+struct StaticSlot {
+    unsigned long long ctx_id = 0;
+    uint32_t *addr = nullptr;
+};
+std::mutex g_static_mu;
+StaticSlot g_static_slots[64];
+
+int current_context_id(unsigned long long *id) {
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_current = (ctx_get_current_fn)f1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess)
+            get_id = (ctx_get_id_fn)f2;
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return psl_fail(PSL_ECUDA, "psl_build_static: driver context queries unavailable");
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return psl_fail(PSL_ECUDA, "psl_build_static: no current CUDA context");
+    if (get_id(ctx, id) != 0) return psl_fail(PSL_ECUDA, "psl_build_static: cuCtxGetId failed");
+    return PSL_OK;
+}
+
 int static_scratch(uint32_t **out) {
     int dev = 0;
     PSL_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return psl_fail(PSL_EINVAL, "psl_build_static: device index out of range");
+    PSL_CUDA(cudaFree(nullptr));                 // make the device's primary context current
+    unsigned long long id = 0;
+    int rc = current_context_id(&id);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_build_scratch);
-        if (e != cudaSuccess)
-            return psl_fail(PSL_ECUDA, std::string("psl_build_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_static_addr[dev] = (uint32_t *)p;
+    StaticSlot *free_slot = nullptr;
+    for (auto &s : g_static_slots) {
+        if (s.addr && s.ctx_id == id) { *out = s.addr; return PSL_OK; }
+        if (!s.addr && !free_slot) free_slot = &s;
     }
-    *out = g_static_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_build_scratch);
+    if (e != cudaSuccess)
+        return psl_fail(PSL_ECUDA, std::string("psl_build_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    if (!free_slot) free_slot = &g_static_slots[id % 64];      // more contexts than slots: reuse one
+    free_slot->ctx_id = id;
+    free_slot->addr = (uint32_t *)p;
+    *out = free_slot->addr;
     return PSL_OK;
 }
 

@@ -288,6 +288,7 @@ extern "C" int psl_plan_create(const psl_store_t *store, const psl_beam_t *beams
     cudaStream_t st = as_stream(stream_);
     psl_plan *p = new psl_plan();
     p->store = store; p->n_beams = n_beams; p->sad = sad; p->n_histories = n_histories; p->seed = seed;
+    p->n_incident = store->n_records;
     p->stream = st;
     const int nx = store->nx, ny = store->ny, ne = store->n_ebins;
     const int64_t npos = (int64_t)nx * ny;

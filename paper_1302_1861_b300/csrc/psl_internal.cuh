@@ -104,6 +104,7 @@ struct psl_plan {
     int32_t n_beams = 0;
     float sad = 100.f;
     int64_t n_histories = 0, n_entries = 0, n_total_psl = 0;
+    int64_t n_incident = 0;          // the store's records (input records x redistribution copies)
     uint64_t seed = 0;
     int32_t n_groups = 0;
     BeamDev *beams = nullptr;        // [n_beams]

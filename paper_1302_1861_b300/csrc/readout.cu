@@ -10,6 +10,7 @@
 #include "psl_internal.cuh"
 
 void workspace_release(Workspace *w);
+int64_t workspace_bytes_of(const Workspace *w);
 
 namespace {
 
@@ -90,6 +91,43 @@ extern "C" int psl_tally_read(const psl_tally_t *t, int64_t *tallies, int64_t *l
     cudaStream_t st = as_stream(stream_);
     if (tallies) PSL_CUDA(cudaMemcpyAsync(tallies, t->t, (size_t)t->n_batches * t->nvox * 8, cudaMemcpyDeviceToDevice, st));
     if (ledger) PSL_CUDA(cudaMemcpyAsync(ledger, t->ledger, 12 * 8, cudaMemcpyDeviceToDevice, st));
+    return PSL_OK;
+}
+
+extern "C" int psl_tally_buffers(psl_tally_t *t, int64_t **tallies, int64_t **ledger) {
+    if (!t) return psl_fail(PSL_EINVAL, "psl_tally_buffers: null tally");
+    if (tallies) *tallies = reinterpret_cast<int64_t *>(t->t);
+    if (ledger) *ledger = reinterpret_cast<int64_t *>(t->ledger);
+    return PSL_OK;
+}
+
+extern "C" int psl_tally_set_queue_depth(psl_tally_t *t, int64_t depth) {
+    if (!t || depth < ((int64_t)1 << 12) || depth > ((int64_t)1 << 26))
+        return psl_fail(PSL_EINVAL, "psl_tally_set_queue_depth: depth outside [2^12, 2^26]");
+    t->chunk_cap = depth;
+    return PSL_OK;
+}
+
+extern "C" int psl_tally_info(const psl_tally_t *t, int64_t *n_counters, int64_t *workspace_bytes,
+                              int64_t *queue_depth, int32_t *blocks_per_sm) {
+    if (!t) return psl_fail(PSL_EINVAL, "psl_tally_info: null tally");
+    if (n_counters) *n_counters = (int64_t)t->n_batches * t->nvox;
+    if (workspace_bytes) *workspace_bytes = workspace_bytes_of(t->ws);
+    if (queue_depth) *queue_depth = t->chunk_cap;
+    if (blocks_per_sm) *blocks_per_sm = t->grid_mult;
+    return PSL_OK;
+}
+
+// Sec. 2.5: D = D_o N_total^phsp / (N_simulated N_incident).  With PSL
+// selection the simulated histories stand for the N_total^psl records of the
+// selected PSLs, so N_total^psl takes the place of the phase space's total.
+extern "C" int psl_dose_normalisation(const psl_plan_t *plan, int64_t n_histories, int64_t n_incident,
+                                      double calibration, double *norm) {
+    if (!plan || !norm || n_histories <= 0 || n_incident < 0 || !(calibration > 0.0))
+        return psl_fail(PSL_EINVAL, "psl_dose_normalisation: bad argument");
+    const int64_t inc = n_incident > 0 ? n_incident : plan->n_incident;
+    if (inc <= 0) return psl_fail(PSL_EINVAL, "psl_dose_normalisation: no incident particle count");
+    *norm = calibration * (double)plan->n_total_psl / ((double)n_histories * (double)inc);
     return PSL_OK;
 }
 

@@ -25,6 +25,8 @@ constexpr int RADIX = 256;
 constexpr int SORT_THREADS = 256;     // 8 warps
 constexpr int SORT_ITEMS = 16;        // keys per thread
 constexpr int TILE = SORT_THREADS * SORT_ITEMS;
+static_assert(TILE == SORT_TILE, "sort.cuh states the onesweep tile size");
+static_assert(RADIX == 256, "sort.cuh sizes the look-back table with 256 digits");
 constexpr uint32_t LB_AGG = 1u << 30;
 constexpr uint32_t LB_INC = 2u << 30;
 constexpr uint32_t LB_MASK = (1u << 30) - 1u;
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(256) k_digit_hist(const uint32_t *__restrict__
 
 size_t sort_pairs_scratch_bytes(uint32_t n) {
     uint32_t n_tiles = std::max<uint32_t>((n + TILE - 1) / TILE, 1);
-    return (size_t)(2 * SORT_MAX_PASSES * RADIX + 4 + (size_t)n_tiles * RADIX) * 4 + (size_t)std::max<uint32_t>(n, 1) * 16;
+    return (size_t)(SORT_HEAD_WORDS + (size_t)n_tiles * RADIX) * 4 + (size_t)std::max<uint32_t>(n, 1) * 16;
 }
 
 int sort_pairs_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint32_t n, int bits,
@@ -199,7 +201,8 @@ int sort_pairs_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t 
     uint32_t *scratch = (uint32_t *)scratch_v;
     uint32_t *hist = scratch, *doffs = scratch + SORT_MAX_PASSES * RADIX, *err = doffs + SORT_MAX_PASSES * RADIX;
     uint32_t *tile_ctr = err + 1, *lookback = err + 4;
-    cudaMemsetAsync(scratch, 0, (2 * SORT_MAX_PASSES * RADIX + 4) * 4, st);
+    static_assert(2 * SORT_MAX_PASSES * RADIX + 4 == SORT_HEAD_WORDS, "look-back table offset");
+    cudaMemsetAsync(scratch, 0, SORT_HEAD_WORDS * 4, st);
     if (hist_in) cudaMemcpyAsync(hist, hist_in, passes * RADIX * 4, cudaMemcpyDeviceToDevice, st);
     else { k_digit_hist<<<std::min<uint32_t>((n + 255) / 256, 1184), 256, 0, st>>>(keys, n, passes, hist); PSL_NOTE_LAUNCH(); }
     k_digit_offsets<<<1, RADIX, 0, st>>>(hist, doffs, passes); PSL_NOTE_LAUNCH();

@@ -4,6 +4,12 @@
 #include <stdint.h>
 
 #define SORT_MAX_PASSES 4
+// Keys one onesweep block ranks (its tile): 256 threads x 16 keys.  The
+// look-back table of sort_pairs_u32 holds 256 words per tile.
+#define SORT_TILE 4096
+// 32-bit words of sort_pairs_u32's scratch before the look-back table:
+// digit histograms and offsets, the error word, the tile counter.
+#define SORT_HEAD_WORDS (2 * SORT_MAX_PASSES * 256 + 4)
 
 // Scratch needed by sort_pairs_u32 for n keys (bytes).
 size_t sort_pairs_scratch_bytes(uint32_t n);

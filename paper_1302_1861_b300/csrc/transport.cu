@@ -1204,6 +1204,18 @@ void workspace_free(Workspace *w) {
     delete w;
 }
 
+// Device bytes a workspace holds: the particle queues (photons 2 x cap_p,
+// electrons 2 x cap_e, the regrouped electrons cap_s, the primary photons
+// one chunk), the packed densities and the batch-order buffers.
+int64_t workspace_bytes_of(const Workspace *w) {
+    if (!w) return 0;
+    const int64_t base = std::max<int64_t>(w->chunk, 4096);
+    int64_t b = (2 * (int64_t)w->cap_p + 2 * (int64_t)w->cap_e + (int64_t)w->cap_s + base) * (int64_t)sizeof(Particle);
+    b += 128 * 4 + 2 * 4 + w->nvox * 4;
+    if (w->bm_cap) b += 16 * w->bm_cap + (PSL_MAX_BATCHES + 1) * 4 + (int64_t)sort_pairs_scratch_bytes((uint32_t)w->bm_cap);
+    return b;
+}
+
 // The workspace of a destroyed tally, kept for the next tally on the same
 // device: its particle queues hold ~30 x chunk particles (26 GB at the
 // default chunk of 2^24) and mapping them afresh cost ~14 ms per tally.  At

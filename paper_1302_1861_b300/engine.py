@@ -80,12 +80,57 @@ def chunks(first: int, n: int, size: int):
     return [(f, min(size, first + n - f)) for f in range(first, first + n, size)]
 
 
-def normalisation(n_total_psl: int, n_histories: int, n_incident: int) -> float:
-    """Sec. 2.5: D = D_o N^phsp / (N_simulated N_incident); with PSL selection the
-    histories stand for the N_total^psl selected records.  With azimuthal
-    redistribution a phase space of N records and K copies stands for K N
-    incident particles (pass n_incident = K N)."""
-    return float(n_total_psl) / (float(n_histories) * float(n_incident))
+def normalisation(plan, n_histories: int, n_incident: int = 0, calibration: float = 1.0) -> float:
+    """Sec. 2.5 normalisation, computed by the library (psl_dose_normalisation):
+    N_total^psl / (N_simulated N_incident) x calibration.  n_incident = 0 takes
+    the store's records x redistribution copies (a synthetic phase space is
+    its own incident set)."""
+    return capi.dose_normalisation(plan, n_histories, n_incident, calibration)
+
+
+class _DeviceInt64:
+    """A library-owned device int64 array seen by torch without a copy."""
+
+    def __init__(self, addr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<i8", "data": (int(addr), False),
+                                         "version": 3, "strides": None}
+
+
+def tally_views(tally):
+    """Torch views (no copy) of a tally's int64 counters [n_batches * nvox]
+    and its 12-slot ledger, on the current CUDA device."""
+    n, _, _, _ = capi.psl_tally_info(tally)
+    t_addr, l_addr = capi.psl_tally_buffers(tally)
+    t = torch.as_tensor(_DeviceInt64(t_addr, n), device="cuda")
+    lg = torch.as_tensor(_DeviceInt64(l_addr, 12), device="cuda")
+    return t, lg
+
+
+def sum_over_ranks(counters, ledger, group=None) -> None:
+    """Element-wise int64 SUM of a tally's counters and ledger over the
+    ranks of `group`, in place (torch.distributed): device tensors on NCCL
+    directly, otherwise through host copies (gloo); host tensors directly."""
+    import torch.distributed as dist
+    if counters.is_cuda and dist.get_backend(group) != "nccl":
+        th, lh = counters.cpu(), ledger.cpu()
+        dist.all_reduce(th, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(lh, op=dist.ReduceOp.SUM, group=group)
+        counters.copy_(th)
+        ledger.copy_(lh)
+        return
+    dist.all_reduce(counters, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(ledger, op=dist.ReduceOp.SUM, group=group)
+
+
+def reduce_tallies(tally, group=None) -> None:
+    """Sec. 2.3.3 (a job split over GPUs): sum every rank's tally and ledger
+    into every rank's, in place, on the tally's own device arrays.  Each
+    history runs on one rank and the counters are integers, so the sum is
+    the tally of the whole range bit for bit; dose_readout follows on it.
+    Call it after the rank's transport calls (psl_run and transport_run
+    synchronise their stream before returning)."""
+    t, lg = tally_views(tally)
+    sum_over_ranks(t, lg, group)
 
 
 def run(dw: DeviceWorkload, n_histories: Optional[int] = None, n_batches: Optional[int] = None,
@@ -115,8 +160,7 @@ def run(dw: DeviceWorkload, n_histories: Optional[int] = None, n_batches: Option
         dose = torch.empty(nvox, dtype=torch.float64, device=dw.mat_t.device)
         sigma = torch.empty_like(dose)
         ledger = torch.empty(3, dtype=torch.float64, device=dose.device)
-        _, n_total_psl, _ = plan.info()
-        norm = normalisation(n_total_psl, n_h, w.records.n * int(w.binning.apr_copies))
+        norm = normalisation(plan, n_h)
         capi.dose_readout(tally, dw.phantom, norm, dose, sigma, ledger, stream)
         out.update(dose=dose, sigma=sigma, ledger=ledger, norm=norm)
     return out

@@ -292,10 +292,11 @@ def config2(n_records: int = 10_000_000, n_histories: int = 100_000_000) -> Work
                     slab_phantom(2, 64, 0.25), n_histories)
 
 
-def config3(n_records: int = 40_000_000, n_histories: int = 1_000_000_000) -> Workload:
+def config3(n_records: int = 40_000_000, n_histories: int = 1_000_000_000, records=None) -> Workload:
     """30x30 cm2 jaws over a 40x40 cm patient-independent phase space with a
-    40x40 fluence map; 128^3 x 0.25 cm CT-like phantom; 1e9 histories."""
-    rec = make_records(3, n_records, half=20.0)
+    40x40 fluence map; 128^3 x 0.25 cm CT-like phantom; 1e9 histories.
+    `records` may pass the phase space already made (the same seeded one)."""
+    rec = make_records(3, n_records, half=20.0) if records is None else records
     binning = make_binning(20.0, 1.0, 32, log_ebins=True)
     flu = smooth_field(_rng(3, 4))
     beams = [Beam(-15.0, 15.0, -15.0, 15.0, roi_margin=1.0, fluence=flu,
@@ -304,11 +305,12 @@ def config3(n_records: int = 40_000_000, n_histories: int = 1_000_000_000) -> Wo
                     ct_phantom(3, (128, 128, 128), 0.25), n_histories)
 
 
-def config4(n_records: int = 40_000_000, n_histories: int = 500_000_000) -> Workload:
+def config4(n_records: int = 40_000_000, n_histories: int = 500_000_000, records=None) -> Workload:
     """Batched IMRT plan on the config-3 phase space: 7 gantry angles x
     10-60 square segments (2-20 cm), per-segment 40x40 fluence, MU in
-    [0.5, 2]; 128x128x100 x 0.25 cm CT-like phantom; 5e8 histories."""
-    rec = make_records(3, n_records, half=20.0)
+    [0.5, 2]; 128x128x100 x 0.25 cm CT-like phantom; 5e8 histories.
+    `records` may pass the config-3 phase space already made."""
+    rec = make_records(3, n_records, half=20.0) if records is None else records
     binning = make_binning(20.0, 1.0, 32, log_ebins=True)
     rng = _rng(4, 5)
     beams = []

@@ -244,7 +244,7 @@ def test_batch_uncertainty_falls_as_one_over_root_n():
         sig = torch.empty_like(dose)
         lg = torch.empty(3, dtype=torch.float64, device="cuda")
         _, n_total, _ = plan.info()
-        capi.dose_readout(tally, dw.phantom, engine.normalisation(n_total, n, w.records.n), dose, sig, lg)
+        capi.dose_readout(tally, dw.phantom, engine.normalisation(plan, n), dose, sig, lg)
         d = dose.view(nz, ny, nx).cpu().numpy()
         s = sig.view(nz, ny, nx).cpu().numpy()
         rel.append(float((s[sl] / d[sl]).mean()))

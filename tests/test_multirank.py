@@ -1,8 +1,10 @@
 """History-range sharding across ranks (world size 2, gloo, CPU).
 
 Each rank computes the tally of its own history range of one plan with the
-oracle; an int64 all-reduce over gloo must give exactly the tally of the
-whole range computed in one process.  This is the multi-GPU contract of the
+oracle; the product's int64 rank reduce (engine.sum_over_ranks, the step
+engine.reduce_tallies runs on a tally's device arrays) over gloo must give
+exactly the tally of the whole range computed in one process.  The same
+reduce on the CUDA path's tallies is tests/test_gpu_multirank.py.  This is the multi-GPU contract of the
 path: independent histories, random streams keyed by history id, integer
 tallies, so any shard count gives bitwise-identical dose.
 """
@@ -48,11 +50,11 @@ def _worker(rank, world, port, out_path):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1302_1861_b300 import engine
     t, lg = _shard_tally(rank, world)
     tt = torch.from_numpy(np.ascontiguousarray(t.ravel()))
     tl = torch.from_numpy(np.ascontiguousarray(lg))
-    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-    dist.all_reduce(tl, op=dist.ReduceOp.SUM)
+    engine.sum_over_ranks(tt, tl)           # the product's rank reduce, on host tensors here
     if rank == 0:
         np.save(out_path, np.concatenate([tt.numpy(), tl.numpy()]))
     dist.barrier()
