@@ -36,7 +36,8 @@ F_FIRST_INTERACTION = 2
 F_NO_MSC = 4
 F_NO_HARD = 8
 
-L_EMITTED, L_ESCAPED, L_DEPOSITED, L_COMPTON, L_PHOTO, L_PAIR, L_ESTEPS, L_ERRORS = range(8)
+L_EMITTED, L_ESCAPED, L_DEPOSITED, L_COMPTON, L_PHOTO, L_PAIR, L_ESTEPS, L_ERRORS, L_HARD_COLL, L_HARD_BREM = range(10)
+L_N = 10
 
 
 def transport(ptype, pos, dirs, e, wt, pid, phantom, seed, flags=0, nthreads=0,
@@ -56,7 +57,7 @@ def transport(ptype, pos, dirs, e, wt, pid, phantom, seed, flags=0, nthreads=0,
     mat = np.ascontiguousarray(phantom.mat, np.uint8)
     rho = np.ascontiguousarray(phantom.rho, np.float32)
     tally = np.zeros(nx * ny * nz, np.int64)
-    ledger = np.zeros(8, np.int64)
+    ledger = np.zeros(L_N, np.int64)
     hd = he = hv = hp = None
     if per_history:
         hd, he = np.zeros(n, np.int64), np.zeros(n, np.int64)
@@ -104,7 +105,7 @@ def run_plan(w, n_histories=None, first=0, n_batches=None, nthreads=0, flags=0,
         plan = source.make_plan(store, w.beams, n_sim, w.seed, w.z_psl, w.sad)
     nz, ny, nx = w.phantom.shape
     tallies = np.zeros((nb, nz, ny, nx), np.int64)
-    ledger = np.zeros(8, np.int64)
+    ledger = np.zeros(L_N, np.int64)
     h_all = np.arange(first, first + n_h, dtype=np.int64)
     sl = history_slices(h_all, w.seed, nb)
     for b in range(nb):

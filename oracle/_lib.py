@@ -47,15 +47,26 @@ def lib():
                 getattr(L, name).argtypes = [d]
             L.ora_mu_rho.restype = d
             L.ora_mu_rho.argtypes = [d, i32, i32]
-            for name in ("ora_col_stopping", "ora_moller_dcs", "ora_moller_sigma", "ora_brem_sigma"):
+            for name in ("ora_col_stopping", "ora_moller_dcs", "ora_moller_sigma", "ora_brem_sigma",
+                         "ora_bhabha_dcs", "ora_bhabha_sigma", "ora_pos_col_stopping"):
                 getattr(L, name).restype = d
                 getattr(L, name).argtypes = [d, d]
-            L.ora_restricted_stopping.restype = d
-            L.ora_restricted_stopping.argtypes = [d, d, d]
-            L.ora_range.restype = d
-            L.ora_range.argtypes = [d, d, d]
-            L.ora_range_inv.restype = d
-            L.ora_range_inv.argtypes = [d, d, d]
+            for name in ("ora_restricted_stopping", "ora_restricted_stopping_pos", "ora_range", "ora_range_inv",
+                         "ora_range_pos", "ora_range_inv_pos", "ora_highland"):
+                getattr(L, name).restype = d
+                getattr(L, name).argtypes = [d, d, d]
+            L.ora_sample_bhabha.restype = None
+            L.ora_sample_bhabha.argtypes = [d, d, u64, i64, vp]
+            L.ora_sample_msc.restype = None
+            L.ora_sample_msc.argtypes = [d, u64, i64, vp, vp]
+            L.ora_sample_brem.restype = None
+            L.ora_sample_brem.argtypes = [d, d, u64, i64, vp]
+            L.ora_sample_pair.restype = None
+            L.ora_sample_pair.argtypes = [d, u64, i64, vp, vp]
+            L.ora_sample_annihilation.restype = None
+            L.ora_sample_annihilation.argtypes = [u64, i64, vp, vp]
+            L.ora_rotate.restype = None
+            L.ora_rotate.argtypes = [i64, vp, vp, vp, vp]
             L.ora_philox.restype = None
             L.ora_philox.argtypes = [i64, vp, vp, vp]
             L.ora_sample_kn.restype = None

@@ -14,9 +14,11 @@
  * physics here is the stated synthetic model of the workload definition:
  * Woodcock photon tracking with Klein-Nishina Compton (Kahn's sampling),
  * Z^4/E^3 photoelectric and a threshold pair fit; class-II condensed-history
- * electrons with the restricted Bethe (Moller) collision stopping power,
- * hard Moller delta rays and hard bremsstrahlung above fixed thresholds and
- * Gaussian (Highland) multiple scattering.  All constants are stated below.
+ * electrons and positrons with the restricted Bethe collision stopping power
+ * (Moller form for electrons, Bhabha form for positrons), hard Moller (e-)
+ * or Bhabha (e+) delta rays and hard bremsstrahlung above fixed thresholds
+ * and Gaussian (Highland) multiple scattering.  All constants are stated
+ * below.
  * Parity of these constants against the paper is unpinned (the paper has
  * none); the tests pin the formulas against closed forms instead.
  *
@@ -63,7 +65,10 @@ static const double MAT_ZEFF[2] = {7.42, 13.8};
 #define F_NO_HARD 8u            /* electrons: no hard delta rays or bremsstrahlung */
 
 /* ledger slots */
-enum { L_EMITTED = 0, L_ESCAPED, L_DEPOSITED, L_COMPTON, L_PHOTO, L_PAIR, L_ESTEPS, L_ERRORS, L_N };
+enum { L_EMITTED = 0, L_ESCAPED, L_DEPOSITED, L_COMPTON, L_PHOTO, L_PAIR, L_ESTEPS, L_ERRORS,
+       L_HARD_COLL,    /* hard Moller / Bhabha collisions */
+       L_HARD_BREM,    /* hard bremsstrahlung events */
+       L_N };
 
 /* ------------------------------- Philox ---------------------------------- */
 static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
@@ -187,9 +192,70 @@ double ora_restricted_stopping(double T, double wcc, double wcb) {
     return ora_col_stopping(T, wcc) + ora_rad_stopping(T) * fmin(wcb, T) / T;
 }
 
+/* ---------------------------- positron physics --------------------------- */
+/* Bhabha coefficients of a positron of kinetic energy T: with y = 1/(tau+2),
+ * B1 = 2 - y^2, B2 = (1-2y)(3+y^2), B4 = (1-2y)^3, B3 = B4 + (1-2y)^2. */
+static void bhabha_b(double T, double b[4]) {
+    double y = 1.0 / (T / ME + 2.0), x = 1.0 - 2.0 * y;
+    b[0] = 2.0 - y * y;
+    b[1] = x * (3.0 + y * y);
+    b[3] = x * x * x;
+    b[2] = b[3] + x * x;
+}
+
+/* Bhabha differential cross section per unit energy W given to the atomic
+ * electron (0 < W <= T: the two particles are distinguishable), cm^2/(g MeV):
+ * 2 pi r_e^2 m c^2 (N_A Z/A) / T^2 [1/(beta^2 e^2) - B1/e + B2 - B3 e + B4 e^2],
+ * e = W/T. */
+double ora_bhabha_dcs(double T, double W) {
+    double b2 = beta2_of(T), e = W / T, b[4];
+    bhabha_b(T, b);
+    double K = 2.0 * PI_D * RE * RE * ME * NAV * MAT_ZA[0];
+    return K / (T * T) * (1.0 / (b2 * e * e) - b[0] / e + b[1] - b[2] * e + b[3] * e * e);
+}
+
+/* hard Bhabha cross section (W from wcc to T), cm^2/g: the integral of the
+ * bracket over e in [ec, 1] */
+double ora_bhabha_sigma(double T, double wcc) {
+    if (T <= wcc) return 0.0;
+    double b2 = beta2_of(T), ec = wcc / T, b[4];
+    bhabha_b(T, b);
+    double K = 2.0 * PI_D * RE * RE * ME * NAV * MAT_ZA[0];
+    return K / T * ((1.0 / ec - 1.0) / b2 - b[0] * log(1.0 / ec) + b[1] * (1.0 - ec)
+                    - b[2] * 0.5 * (1.0 - ec * ec) + b[3] * (1.0 - ec * ec * ec) / 3.0);
+}
+
+/* Restricted collision stopping power of a positron (Bhabha, no density
+ * effect), MeV cm^2/g, for energy transfers below `cut`; cut >= T gives the
+ * unrestricted value.  With d = min(cut, T)/mc^2 and y = 1/(tau+2):
+ * K/beta^2 [ln(2 (tau+2) / (I/mc^2)^2) + F+], F+ = ln(tau d) - (beta^2/tau)
+ * [tau + 2d - 3 d^2 y/2 - (d - d^3/3) y^2 - (d^2/2 - tau d^3/3 + d^4/4) y^3]. */
+double ora_pos_col_stopping(double T, double cut) {
+    double tau = T / ME, b2 = beta2_of(T), d = fmin(cut, T) / ME, y = 1.0 / (tau + 2.0);
+    double iom = I_WATER / ME;
+    double F = log(tau * d) - (b2 / tau) * (tau + 2.0 * d - 1.5 * d * d * y - (d - d * d * d / 3.0) * y * y
+                                             - (0.5 * d * d - tau * d * d * d / 3.0 + 0.25 * d * d * d * d) * y * y * y);
+    double K = 2.0 * PI_D * RE * RE * ME * NAV * MAT_ZA[0] / b2;
+    return K * (log(2.0 * (tau + 2.0) / (iom * iom)) + F);
+}
+
+double ora_restricted_stopping_pos(double T, double wcc, double wcb) {
+    return ora_pos_col_stopping(T, wcc) + ora_rad_stopping(T) * fmin(wcb, T) / T;
+}
+
+/* restricted stopping power of a species (0 electron, 1 positron) */
+static double restricted_stopping(int pos, double T, double wcc, double wcb) {
+    return pos ? ora_restricted_stopping_pos(T, wcc, wcb) : ora_restricted_stopping(T, wcc, wcb);
+}
+
+/* hard collision (delta-ray) cross section of a species, cm^2/g */
+static double hard_collision_sigma(int pos, double T, double wcc) {
+    return pos ? ora_bhabha_sigma(T, wcc) : ora_moller_sigma(T, wcc);
+}
+
 /* ----------------------- CSDA range with restricted S --------------------- */
 static double gl_x[16], gl_w[16];
-static double rt_T[N_RANGE], rt_R[N_RANGE];
+static double rt_T[N_RANGE], rt_R[2][N_RANGE];    /* [species][node]: 0 electron, 1 positron */
 static double rt_wcc = -1.0, rt_wcb = -1.0;
 
 static void gauss_legendre16(void) {
@@ -210,9 +276,9 @@ static void gauss_legendre16(void) {
     }
 }
 
-static double int_inv_s(double a, double b, double wcc, double wcb) {
+static double int_inv_s(int pos, double a, double b, double wcc, double wcb) {
     double m = 0.5 * (a + b), h = 0.5 * (b - a), s = 0.0;
-    for (int i = 0; i < 16; ++i) s += gl_w[i] / ora_restricted_stopping(m + h * gl_x[i], wcc, wcb);
+    for (int i = 0; i < 16; ++i) s += gl_w[i] / restricted_stopping(pos, m + h * gl_x[i], wcc, wcb);
     return s * h;
 }
 
@@ -221,29 +287,32 @@ static void range_setup(double wcc, double wcb) {
     gauss_legendre16();
     double lr = log(T_RANGE_HI / T_RANGE_LO);
     for (int i = 0; i < N_RANGE; ++i) rt_T[i] = T_RANGE_LO * exp(lr * i / (N_RANGE - 1));
-    rt_R[0] = 0.0;
-    for (int i = 1; i < N_RANGE; ++i) rt_R[i] = rt_R[i - 1] + int_inv_s(rt_T[i - 1], rt_T[i], wcc, wcb);
+    for (int p = 0; p < 2; ++p) {
+        rt_R[p][0] = 0.0;
+        for (int i = 1; i < N_RANGE; ++i) rt_R[p][i] = rt_R[p][i - 1] + int_inv_s(p, rt_T[i - 1], rt_T[i], wcc, wcb);
+    }
     rt_wcc = wcc; rt_wcb = wcb;
 }
 
-/* R(T) = integral from T_RANGE_LO to T of dT'/S_restricted, g/cm^2 */
-static double range_of(double T, double wcc, double wcb) {
+/* R(T) = integral from T_RANGE_LO to T of dT'/S_restricted of the species, g/cm^2 */
+static double range_of(int pos, double T, double wcc, double wcb) {
     int lo = 0, hi = N_RANGE - 1;
     if (T <= rt_T[0]) return 0.0;
     while (hi - lo > 1) { int mid = (lo + hi) / 2; if (rt_T[mid] <= T) lo = mid; else hi = mid; }
-    return rt_R[lo] + int_inv_s(rt_T[lo], T, wcc, wcb);
+    return rt_R[pos][lo] + int_inv_s(pos, rt_T[lo], T, wcc, wcb);
 }
 
 /* inverse of range_of by Newton's method (dR/dT = 1/S) */
-static double range_inv(double r, double wcc, double wcb) {
+static double range_inv(int pos, double r, double wcc, double wcb) {
     if (r <= 0.0) return T_RANGE_LO;
+    const double *R = rt_R[pos];
     int lo = 0, hi = N_RANGE - 1;
-    while (hi - lo > 1) { int mid = (lo + hi) / 2; if (rt_R[mid] <= r) lo = mid; else hi = mid; }
+    while (hi - lo > 1) { int mid = (lo + hi) / 2; if (R[mid] <= r) lo = mid; else hi = mid; }
     double a = rt_T[lo], b = rt_T[hi];
-    double T = a + (b - a) * (r - rt_R[lo]) / (rt_R[hi] - rt_R[lo]);
+    double T = a + (b - a) * (r - R[lo]) / (R[hi] - R[lo]);
     for (int it = 0; it < 60; ++it) {
-        double f = range_of(T, wcc, wcb) - r;
-        double Tn = T - f * ora_restricted_stopping(T, wcc, wcb);
+        double f = range_of(pos, T, wcc, wcb) - r;
+        double Tn = T - f * restricted_stopping(pos, T, wcc, wcb);
         if (Tn < a) Tn = a;
         if (Tn > b) Tn = b;
         if (fabs(Tn - T) <= 1e-15 * T) { T = Tn; break; }
@@ -252,8 +321,10 @@ static double range_inv(double r, double wcc, double wcb) {
     return T;
 }
 
-double ora_range(double T, double wcc, double wcb) { range_setup(wcc, wcb); return range_of(T, wcc, wcb); }
-double ora_range_inv(double r, double wcc, double wcb) { range_setup(wcc, wcb); return range_inv(r, wcc, wcb); }
+double ora_range(double T, double wcc, double wcb) { range_setup(wcc, wcb); return range_of(0, T, wcc, wcb); }
+double ora_range_inv(double r, double wcc, double wcb) { range_setup(wcc, wcb); return range_inv(0, r, wcc, wcb); }
+double ora_range_pos(double T, double wcc, double wcb) { range_setup(wcc, wcb); return range_of(1, T, wcc, wcb); }
+double ora_range_inv_pos(double r, double wcc, double wcb) { range_setup(wcc, wcb); return range_inv(1, r, wcc, wcb); }
 
 /* ------------------------------- sampling -------------------------------- */
 /* Kahn's rejection method for the Klein-Nishina distribution.  Returns
@@ -310,20 +381,131 @@ void ora_sample_moller(double T, double wcc, uint64_t seed, int64_t n, double *e
     }
 }
 
-/* rotate unit direction d by polar cosine c and azimuth phi */
+/* Bhabha energy-transfer fraction e in [wcc/T, 1] (the atomic electron
+ * gets e T).  The cross section is (1/e^2) h(e) with
+ * h(e) = 1 - beta^2 e (B1 - e (B2 - e (B3 - e B4))), and 0 < h <= 1 on
+ * (0, 1] (checked by the tests), so e is proposed from the density 1/e^2 on
+ * [ec, 1] and accepted with probability h(e). */
+static double sample_bhabha(double T, double wcc, stream_t *s) {
+    double ec = wcc / T, b2 = beta2_of(T), b[4];
+    bhabha_b(T, b);
+    for (;;) {
+        double r1 = uniform(s), r2 = uniform(s);
+        double e = ec / (1.0 - r1 * (1.0 - ec));
+        double h = 1.0 - b2 * e * (b[0] - e * (b[1] - e * (b[2] - e * b[3])));
+        if (r2 <= h) return e;
+    }
+}
+
+void ora_sample_bhabha(double T, double wcc, uint64_t seed, int64_t n, double *eps_out) {
+    for (int64_t i = 0; i < n; ++i) {
+        stream_t s = {seed, (uint64_t)i, 0};
+        eps_out[i] = sample_bhabha(T, wcc, &s);
+    }
+}
+
+/* Highland's characteristic multiple-scattering angle (radians) of a step of
+ * s cm at density rho: theta0 = 13.6 MeV / (beta c p) sqrt(t) (1 + 0.038 ln t),
+ * t = s rho / X0 (the water radiation length scaled by density), with
+ * beta c p = T (T + 2 m c^2) / (T + m c^2); 0 where the bracket is not positive. */
+double ora_highland(double T, double s, double rho) {
+    double x0 = X0_WATER / rho, t = s / x0;
+    if (t <= 0.0) return 0.0;
+    double bcp = T * (T + 2.0 * ME) / (T + ME);
+    double f = 1.0 + 0.038 * log(t);
+    if (f <= 0.0) return 0.0;
+    return 13.6 / bcp * sqrt(t) * f;
+}
+
+/* The multiple-scattering deflection of a step: polar angle theta =
+ * theta0 sqrt(-2 ln u) (the space angle of a two-dimensional Gaussian of
+ * width theta0 per projected plane: Rayleigh distributed), azimuth 2 pi u'. */
+static void sample_msc(double th0, stream_t *s, double *theta, double *phi) {
+    *theta = th0 * sqrt(-2.0 * log(uniform(s)));
+    *phi = 2.0 * PI_D * uniform(s);
+}
+
+void ora_sample_msc(double th0, uint64_t seed, int64_t n, double *theta_out, double *phi_out) {
+    for (int64_t i = 0; i < n; ++i) {
+        stream_t s = {seed, (uint64_t)i, 0};
+        sample_msc(th0, &s, theta_out + i, phi_out + i);
+    }
+}
+
+/* Energy of a hard bremsstrahlung photon: the 1/k spectrum on [wcb, T],
+ * k = wcb (T/wcb)^u. */
+static double sample_brem_photon(double T, double wcb, stream_t *s) {
+    return wcb * exp(uniform(s) * log(T / wcb));
+}
+
+void ora_sample_brem(double T, double wcb, uint64_t seed, int64_t n, double *k_out) {
+    for (int64_t i = 0; i < n; ++i) {
+        stream_t s = {seed, (uint64_t)i, 0};
+        k_out[i] = sample_brem_photon(T, wcb, &s);
+    }
+}
+
+/* Pair production: the kinetic energy E - 2 m c^2 split uniformly between
+ * the electron (t1) and the positron (t2). */
+static void sample_pair_split(double E, stream_t *s, double *t1, double *t2) {
+    double avail = E - 2.0 * ME;
+    *t1 = uniform(s) * avail;
+    *t2 = avail - *t1;
+}
+
+void ora_sample_pair(double E, uint64_t seed, int64_t n, double *t1_out, double *t2_out) {
+    for (int64_t i = 0; i < n; ++i) {
+        stream_t s = {seed, (uint64_t)i, 0};
+        sample_pair_split(E, &s, t1_out + i, t2_out + i);
+    }
+}
+
+/* Annihilation at rest: the first photon's direction uniform on the sphere
+ * (cos theta = 2u - 1, azimuth 2 pi u'); the second goes the opposite way. */
+static void sample_annihilation(stream_t *s, double a[3]) {
+    double cth = 2.0 * uniform(s) - 1.0, phi = 2.0 * PI_D * uniform(s);
+    double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+    a[0] = sth * cos(phi); a[1] = sth * sin(phi); a[2] = cth;
+}
+
+void ora_sample_annihilation(uint64_t seed, int64_t n, double *d1_out, double *d2_out) {
+    for (int64_t i = 0; i < n; ++i) {
+        stream_t s = {seed, (uint64_t)i, 0};
+        double a[3];
+        sample_annihilation(&s, a);
+        for (int k = 0; k < 3; ++k) { d1_out[3 * i + k] = a[k]; d2_out[3 * i + k] = -a[k]; }
+    }
+}
+
+/* Rotate unit direction d by polar cosine c and azimuth phi.  The azimuth
+ * is measured from the plane through d and the z axis:
+ *   d' = c d + sin(theta) (cos(phi) e1 + sin(phi) e2),
+ *   e1 = (u w, v w, -t) / t,  e2 = (-v, u, 0) / t,  t = sqrt(u^2 + v^2),
+ * an orthonormal pair perpendicular to d, so d.d' = c exactly.  Only a
+ * direction on the z axis itself (t^2 <= 1e-30) takes the fixed pair
+ * e1 = (1, 0, 0), e2 = (0, 1, 0). */
 static void rotate_dir(double d[3], double c, double phi) {
     double st = sqrt(fmax(0.0, 1.0 - c * c)), cp = cos(phi), sp = sin(phi);
     double u = d[0], v = d[1], w = d[2], nu, nv, nw;
-    if (fabs(w) > 0.99999) {
+    double t2 = u * u + v * v;
+    if (t2 <= 1e-30) {
         nu = st * cp; nv = st * sp; nw = (w > 0 ? c : -c);
     } else {
-        double t = sqrt(1.0 - w * w);
+        double t = sqrt(t2);
         nu = u * c + st * (u * w * cp - v * sp) / t;
         nv = v * c + st * (v * w * cp + u * sp) / t;
         nw = w * c - st * cp * t;
     }
     double n = sqrt(nu * nu + nv * nv + nw * nw);
     d[0] = nu / n; d[1] = nv / n; d[2] = nw / n;
+}
+
+void ora_rotate(int64_t n, const double *d_in, const double *c, const double *phi, double *d_out) {
+    for (int64_t i = 0; i < n; ++i) {
+        double d[3] = {d_in[3 * i], d_in[3 * i + 1], d_in[3 * i + 2]};
+        rotate_dir(d, c[i], phi[i]);
+        for (int k = 0; k < 3; ++k) d_out[3 * i + k] = d[k];
+    }
 }
 
 /* ------------------------------- transport ------------------------------- */
@@ -384,9 +566,8 @@ static double mu_max_of(const ctx_t *c, double E) {
 static void annihilate(const ctx_t *c, stream_t *s, uint32_t *nchild, uint64_t pid, const double p[3],
                        double wt, pstack_t *st) {
     align_stream(s);
-    double cth = 2.0 * uniform(s) - 1.0, phi = 2.0 * PI_D * uniform(s);
-    double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
-    double a[3] = {sth * cos(phi), sth * sin(phi), cth};
+    double a[3];
+    sample_annihilation(s, a);
     for (int k = 0; k < 2; ++k) {
         part_t g = {0, {p[0], p[1], p[2]}, {k ? -a[0] : a[0], k ? -a[1] : a[1], k ? -a[2] : a[2]}, ME, wt,
                     child_pid(c->seed, pid, (*nchild)++)};
@@ -454,22 +635,13 @@ static void photon(const ctx_t *c, acc_t *a, part_t *g, pstack_t *st) {
         } else {                                           /* pair */
             a->ledger[L_PAIR]++;
             if (c->flags & F_FIRST_INTERACTION) { deposit(c, a, iv, E, wt); return; }
-            double avail = E - 2.0 * ME, eps = uniform(&s);
-            double T1 = eps * avail, T2 = avail - T1;
+            double T1, T2;
+            sample_pair_split(E, &s, &T1, &T2);
             emit_charged(c, a, 1, T1, p, d, wt, iv, g->pid, &nchild, &s, st);
             emit_charged(c, a, 2, T2, p, d, wt, iv, g->pid, &nchild, &s, st);
             return;
         }
     }
-}
-
-static double highland(double T, double s, double rho) {
-    double x0 = X0_WATER / rho, t = s / x0;
-    if (t <= 0.0) return 0.0;
-    double bcp = T * (T + 2.0 * ME) / (T + ME);
-    double f = 1.0 + 0.038 * log(t);
-    if (f <= 0.0) return 0.0;
-    return 13.6 / bcp * sqrt(t) * f;
 }
 
 static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
@@ -486,7 +658,7 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
     }
     int hard_on = !(c->flags & F_NO_HARD);
     double nlam = -1.0;             /* mean free paths to the next hard event; < 0: draw at the next step */
-    double R = range_of(T, c->wcc, c->wcb);
+    double R = range_of(pos, T, c->wcc, c->wcb);
     int steps = 0;
     for (;;) {
         int64_t iv = ((int64_t)ix[2] * c->ny + ix[1]) * c->nx + ix[0];
@@ -504,7 +676,7 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
         align_stream(&s);                                  /* the step's draws */
         if (nlam < 0.0) nlam = -log(uniform(&s));          /* a new mean free path count */
         double rho = c->rho[iv];
-        double sig = hard_on ? rho * (ora_moller_sigma(T, c->wcc) + ora_brem_sigma(T, c->wcb)) : 0.0;
+        double sig = hard_on ? rho * (hard_collision_sigma(pos, T, c->wcc) + ora_brem_sigma(T, c->wcb)) : 0.0;
         double s_hard = sig > 0.0 ? nlam / sig : INFINITY;
         /* distance to the voxel boundary */
         double s_bound = INFINITY;
@@ -518,7 +690,7 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
             if (t < s_bound) { s_bound = t; axis = k; cross = d[k] > 0 ? 1 : -1; }
         }
         double Tlim = fmax(0.9 * T, c->ecut);
-        double Rlim = range_of(Tlim, c->wcc, c->wcb);
+        double Rlim = range_of(pos, Tlim, c->wcc, c->wcb);
         double s_max = (R - Rlim) / rho;
         int which;                                          /* 0 hard, 1 boundary, 2 energy-loss limit */
         double step;
@@ -527,16 +699,16 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
         else { which = 2; step = s_max; }
         double Tend, Rend;
         if (which == 2) { Tend = Tlim; Rend = Rlim; }
-        else { Rend = R - rho * step; Tend = range_inv(Rend, c->wcc, c->wcb); if (Tend < Tlim) Tend = Tlim; }
-        double th0 = highland(T, step, rho);
+        else { Rend = R - rho * step; Tend = range_inv(pos, Rend, c->wcc, c->wcb); if (Tend < Tlim) Tend = Tlim; }
+        double th0 = ora_highland(T, step, rho);
         deposit(c, a, iv, T - Tend, wt);
         a->path += step;
         T = Tend; R = Rend;
         for (int k = 0; k < 3; ++k) p[k] += step * d[k];
         nlam -= step * sig;
         if (!(c->flags & F_NO_MSC) && step > 0.0) {
-            double th = th0 * sqrt(-2.0 * log(uniform(&s)));
-            double phi = 2.0 * PI_D * uniform(&s);
+            double th, phi;
+            sample_msc(th0, &s, &th, &phi);
             rotate_dir(d, cos(th), phi);
         }
         if (which == 1) {
@@ -548,12 +720,14 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
                 return;
             }
         } else if (which == 0) {
-            double sm = ora_moller_sigma(T, c->wcc), sb = ora_brem_sigma(T, c->wcb);
+            double sm = hard_collision_sigma(pos, T, c->wcc), sb = ora_brem_sigma(T, c->wcb);
             align_stream(&s);                              /* the hard event's draws */
             double r = uniform(&s) * (sm + sb);
             if (sm + sb > 0.0) {
-                if (r < sm) {                                /* hard Moller */
-                    double eps = sample_moller(T, c->wcc, &s), W = eps * T, Tp = T - W;
+                if (r < sm) {                                /* hard Moller (e-) or Bhabha (e+) */
+                    a->ledger[L_HARD_COLL]++;
+                    double eps = pos ? sample_bhabha(T, c->wcc, &s) : sample_moller(T, c->wcc, &s);
+                    double W = eps * T, Tp = T - W;           /* W to the atomic electron */
                     double cp = sqrt(Tp * (T + 2.0 * ME) / (T * (Tp + 2.0 * ME)));
                     double cd = sqrt(W * (T + 2.0 * ME) / (T * (W + 2.0 * ME)));
                     double phi = 2.0 * PI_D * uniform(&s);
@@ -563,7 +737,8 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
                     emit_charged(c, a, 1, W, p, dd, wt, iv, e->pid, &nchild, &s, st);
                     T = Tp;
                 } else {                                     /* hard bremsstrahlung */
-                    double kph = c->wcb * exp(uniform(&s) * log(T / c->wcb));
+                    a->ledger[L_HARD_BREM]++;
+                    double kph = sample_brem_photon(T, c->wcb, &s);
                     if (c->flags & F_LOCAL_SECONDARIES) deposit(c, a, iv, kph, wt);
                     else {
                         part_t g = {0, {p[0], p[1], p[2]}, {d[0], d[1], d[2]}, kph, wt, child_pid(c->seed, e->pid, nchild++)};
@@ -571,7 +746,7 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
                     }
                     T -= kph;
                 }
-                R = range_of(T, c->wcc, c->wcb);
+                R = range_of(pos, T, c->wcc, c->wcb);
             }
             nlam = -1.0;                                   /* drawn at the next step */
         }
@@ -580,8 +755,9 @@ static void electron(const ctx_t *c, acc_t *a, part_t *e, pstack_t *st) {
 
 /*
  * Transport n primaries (phantom-local coordinates, cm) and add their dose to
- * `tally` (int64 fixed point, 2^-32 MeV per unit weight).  ledger[8] is added
- * to (escaped, deposited, interaction and step counts, errors); the emitted
+ * `tally` (int64 fixed point, 2^-32 MeV per unit weight).  ledger[10] is added
+ * to (escaped, deposited, interaction and step counts, errors, hard
+ * collision and hard bremsstrahlung events); the emitted
  * slot belongs to the source stage.  Per-primary sums over the whole
  * secondary tree (deposited and escaped fixed point, events, electron path
  * length in cm) are optional outputs.

@@ -153,3 +153,96 @@ def test_range_is_integral_of_inverse_stopping(T):
     num, _ = integrate.quad(f, 1e-3, T, epsrel=1e-13, limit=400, points=pts or None)
     assert abs(L.ora_range(T, 0.2, 0.2) / num - 1) < 1e-9
     assert abs(L.ora_range_inv(L.ora_range(T, 0.2, 0.2), 0.2, 0.2) / T - 1) < 1e-12
+
+
+# ----------------------------------------------------------- positrons -----
+def icru37_positron_collision_stopping(T, I=75e-6, za=ZA_WATER):
+    """Unrestricted positron collision stopping power, ICRU Report 37 form
+    (its F+ function), no density effect, MeV cm^2/g."""
+    tau = T / ME
+    b2 = 1 - 1 / (1 + tau) ** 2
+    Fp = 2 * math.log(2) - (b2 / 12) * (23 + 14 / (tau + 2) + 10 / (tau + 2) ** 2 + 4 / (tau + 2) ** 3)
+    return (2 * math.pi * RE * RE * ME * NA * za / b2) * (math.log(tau * tau * (tau + 2) / (2 * (I / ME) ** 2)) + Fp)
+
+
+def bhabha_dcs_by_hand(T, W):
+    """Bhabha cross section per unit energy transfer from its textbook form
+    dsigma/deps = 2 pi r_e^2 m c^2 / (beta^2 T) [1/eps^2 - beta^2 (B1/eps - B2
+    + B3 eps - B4 eps^2)], gamma = 1 + T/mc^2, y = 1/(gamma + 1), per unit
+    mass of water (N_A Z/A), divided by T for per unit W."""
+    gam = 1 + T / ME
+    b2 = 1 - 1 / gam ** 2
+    y = 1 / (gam + 1)
+    B1 = 2 - y * y
+    B2 = (1 - 2 * y) * (3 + y * y)
+    B4 = (1 - 2 * y) ** 3
+    B3 = B4 + (1 - 2 * y) ** 2
+    e = W / T
+    per_eps = 2 * math.pi * RE * RE * ME / (b2 * T) * (1 / e ** 2 - b2 * (B1 / e - B2 + B3 * e - B4 * e * e))
+    return per_eps * NA * ZA_WATER / T
+
+
+@pytest.mark.parametrize("T", [0.05, 0.2, 1.0, 3.0, 10.0])
+def test_unrestricted_positron_stopping_is_icru37(T):
+    assert abs(L.ora_pos_col_stopping(T, T) / icru37_positron_collision_stopping(T) - 1) < 1e-12
+    # above ~1 MeV positrons lose a little less than electrons (ICRU 37)
+    if T >= 1.0:
+        assert L.ora_pos_col_stopping(T, T) < L.ora_col_stopping(T, T)
+
+
+@pytest.mark.parametrize("T,W", [(0.5, 0.21), (1.0, 0.3), (1.0, 0.99), (6.0, 0.2), (6.0, 5.5)])
+def test_bhabha_dcs_matches_textbook_form(T, W):
+    assert L.ora_bhabha_dcs(T, W) == pytest.approx(bhabha_dcs_by_hand(T, W), rel=1e-12)
+
+
+@pytest.mark.parametrize("T", [0.3, 1.0, 2.5, 6.0])
+def test_restricted_positron_stopping_plus_hard_losses_is_unrestricted(T):
+    """L+(T; T) - L+(T; W_c) = integral over W_c..T of W dsigma_Bhabha/dW:
+    links the restricted stopping power to the hard cross section."""
+    wc = 0.2
+    hard, _ = integrate.quad(lambda W: W * L.ora_bhabha_dcs(T, W), wc, T, epsrel=1e-11)
+    assert abs((L.ora_pos_col_stopping(T, T) - L.ora_pos_col_stopping(T, wc)) / hard - 1) < 1e-8
+
+
+@pytest.mark.parametrize("T", [0.25, 1.0, 3.0, 6.0])
+def test_bhabha_total_is_integral_of_dcs(T):
+    num, _ = integrate.quad(lambda W: L.ora_bhabha_dcs(T, W), 0.2, T, epsrel=1e-11)
+    assert abs(L.ora_bhabha_sigma(T, 0.2) / num - 1) < 1e-9
+    assert L.ora_bhabha_sigma(0.19, 0.2) == 0.0
+    # a positron can hand its whole energy to the electron: its hard events
+    # start at W_c, below the Moller threshold 2 W_c
+    assert L.ora_bhabha_sigma(0.3, 0.2) > 0.0 and L.ora_moller_sigma(0.3, 0.2) == 0.0
+
+
+def test_bhabha_rejection_bound():
+    """The sampler proposes from 1/eps^2 and keeps eps with probability
+    eps^2 dsigma/deps / (its Rutherford factor), which must lie in (0, 1]."""
+    for T in np.geomspace(0.2, 30.0, 60):
+        for e in np.linspace(0.2 / T, 1.0, 200):
+            h = bhabha_dcs_by_hand(T, e * T) * (e * T) ** 2 / (2 * math.pi * RE * RE * ME / (1 - 1 / (1 + T / ME) ** 2)
+                                                               * NA * ZA_WATER) / T * T
+            assert 0.0 < h <= 1.0 + 1e-12, (T, e, h)
+
+
+@pytest.mark.parametrize("T", [0.5, 2.0, 6.0])
+def test_bhabha_sampler_chi2(T):
+    n = 400_000
+    eps = np.zeros(n)
+    L.ora_sample_bhabha(T, 0.2, 9, n, _lib._p(eps))
+    ec = 0.2 / T
+    assert eps.min() >= ec and eps.max() <= 1.0
+    edges = np.geomspace(ec, 1.0, 31)
+    obs, _ = np.histogram(eps, edges)
+    p = np.array([integrate.quad(lambda e: L.ora_bhabha_dcs(T, e * T), a, b)[0] for a, b in zip(edges[:-1], edges[1:])])
+    p /= p.sum()
+    chi2 = ((obs - n * p) ** 2 / (n * p)).sum()
+    assert stats.chi2.sf(chi2, len(p) - 1) > 1e-3
+
+
+@pytest.mark.parametrize("T", [0.3, 1.0, 4.0, 12.0])
+def test_positron_range_is_integral_of_inverse_stopping(T):
+    f = lambda t: 1.0 / L.ora_restricted_stopping_pos(t, 0.2, 0.2)
+    pts = [p for p in (0.2,) if p < T]
+    num, _ = integrate.quad(f, 1e-3, T, epsrel=1e-13, limit=400, points=pts or None)
+    assert abs(L.ora_range_pos(T, 0.2, 0.2) / num - 1) < 1e-9
+    assert abs(L.ora_range_inv_pos(L.ora_range_pos(T, 0.2, 0.2), 0.2, 0.2) / T - 1) < 1e-12

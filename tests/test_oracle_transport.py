@@ -100,6 +100,55 @@ def test_csda_range_of_straight_electron(T0, rho):
     assert abs((lg[oracle.L_DEPOSITED] - n * T0 * 2.0 ** 32) / (n * T0 * 2.0 ** 32)) < 1e-9
 
 
+@pytest.mark.parametrize("T0,rho", [(2.0, 1.0), (5.0, 1.85)])
+def test_csda_range_of_straight_positron(T0, rho):
+    """A positron with hard events and scattering off travels the CSDA range
+    of its own (Bhabha) restricted stopping power, then annihilates at rest:
+    with secondaries kept local its 2 m c^2 is deposited where it stops."""
+    nz = 200
+    ph = _column(nz, 0.05, rho=np.full((nz, 1, 1), rho, np.float32))
+    n = 4
+    t, lg, h = oracle.transport(*_pencil(n, 2, T0, ph), ph, seed=3,
+                                flags=oracle.F_NO_MSC | oracle.F_NO_HARD | oracle.F_LOCAL_SECONDARIES,
+                                per_history=True)
+    f = lambda T: 1.0 / (rho * L.ora_restricted_stopping_pos(T, oracle.WCC, oracle.WCB))
+    csda, _ = integrate.quad(f, oracle.ECUT, T0, epsrel=1e-12, points=[0.2], limit=200)
+    assert np.allclose(h["path"], csda, rtol=1e-6)
+    # the electron's range differs: the species' own tables are used
+    fe = lambda T: 1.0 / (rho * L.ora_restricted_stopping(T, oracle.WCC, oracle.WCB))
+    assert abs(integrate.quad(fe, oracle.ECUT, T0, points=[0.2, 0.4], limit=200)[0] / csda - 1) > 1e-3
+    e_all = n * (T0 + 2 * oracle.ME) * 2.0 ** 32
+    assert abs((lg[oracle.L_DEPOSITED] - e_all) / e_all) < 1e-9
+
+
+@pytest.mark.parametrize("ptype", [1, 2])
+def test_hard_collision_rate_on_a_thin_slab(ptype):
+    """Electrons collide hard at the Moller rate, positrons at the Bhabha
+    rate: 3 MeV particles crossing 0.5 mm of water (scatter-free, hard
+    bremsstrahlung off by W_cb above the energy) make, to first order, the
+    integral of sigma(T) / S(T) dT over the energy they lose on the way."""
+    T0, n, dz = 3.0, 400_000, 0.05
+    ph = _column(1, dz)
+    wcb = 10.0
+    _, lg = oracle.transport(*_pencil(n, ptype, T0, ph), ph, seed=8,
+                             flags=oracle.F_NO_MSC | oracle.F_LOCAL_SECONDARIES, wcb=wcb)
+    pos = ptype == 2
+    S = (lambda T: L.ora_restricted_stopping_pos(T, oracle.WCC, wcb)) if pos else \
+        (lambda T: L.ora_restricted_stopping(T, oracle.WCC, wcb))
+    R = L.ora_range_pos if pos else L.ora_range
+    Rinv = L.ora_range_inv_pos if pos else L.ora_range_inv
+    t_exit = Rinv(R(T0, oracle.WCC, wcb) - dz, oracle.WCC, wcb)
+    sig = L.ora_bhabha_sigma if pos else L.ora_moller_sigma
+    other = L.ora_moller_sigma if pos else L.ora_bhabha_sigma
+    expect = n * integrate.quad(lambda T: sig(T, oracle.WCC) / S(T), t_exit, T0)[0]
+    wrong = n * integrate.quad(lambda T: other(T, oracle.WCC) / S(T), t_exit, T0)[0]
+    got = lg[oracle.L_HARD_COLL]
+    assert lg[oracle.L_HARD_BREM] == 0
+    # first order: a second hard event on the same track is rare (~1 %)
+    assert abs(got - expect) < 5 * math.sqrt(expect) + 0.02 * expect
+    assert abs(got - wrong) > 10 * math.sqrt(expect)
+
+
 def test_energy_deposited_only_along_track():
     ph = inputs.water_phantom(21, 0.5)
     ph.origin = (0.0, 0.0, 0.0)
