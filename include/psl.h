@@ -347,7 +347,8 @@ PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64
  * 0 emitted, 1 escaped, 2 deposited (fixed point, 2^-32 MeV per unit
  * weight), 3 Compton, 4 photoelectric and 5 pair events, 6 electron steps,
  * 7 errors, 8 tally atomics issued by photon passes, 9 by electron passes,
- * 10 Woodcock (photon) steps, 11 reserved.  The phantom must have fewer
+ * 10 Woodcock (photon) steps, 11 hard Moller (e-) and Bhabha (e+) collisions.
+ * The phantom must have fewer
  * than 2^31 voxels (PSL_EINVAL otherwise): transport indexes voxels in
  * 32 bits. */
 PSL_API int psl_tally_create(const psl_phantom_t *phantom, int32_t n_batches, psl_tally_t **out);
@@ -400,6 +401,22 @@ PSL_API int psl_tally_info(const psl_tally_t *tally, int64_t *n_counters, int64_
  * tally is destroyed.  PSL_EINVAL outside the range. */
 PSL_API int psl_tally_set_queue_depth(psl_tally_t *tally, int64_t depth);
 
+/* Sec. 2.2, 2.3.3, 2.4: a record of the production source stage.  Later
+ * psl_run and transport_run calls on the tally write, for every history h
+ * in [first, first + n) that they source, at index h - first (device
+ * arrays, caller-owned, NULL to skip): the plan entry, its read number k,
+ * the sorted record index, the status (PSL_SRC_*), the particle type (0
+ * photon, 1 electron, 2 positron) and, for PSL_SRC_TRANSPORT only, the state
+ * (8 float32: x y z u v w e wt, phantom-local) - the same quantities
+ * psl_source_trace computes, here from the source kernel that feeds
+ * transport (reading order or batch by batch).  n = 0 turns the record
+ * off.  The arrays must stay valid while it is on.  A CUDA graph of
+ * psl_run is captured again when the record changes.  For tests and
+ * diagnostics; it costs nothing when off.  PSL_EINVAL for first < 0 or
+ * n < 0. */
+PSL_API int psl_tally_trace_source(psl_tally_t *tally, int64_t first, int64_t n, int64_t *entry, int64_t *use,
+                                   int64_t *rec, int8_t *status, float *state, int32_t *ptype);
+
 /* Copy raw tallies (device int64 [n_batches][nvox]: batch b's voxels at
  * b * nvox, the layout the tally keeps, so that one batch's slice is
  * contiguous for the batch-by-batch order) and ledger (device int64 [12])
@@ -412,7 +429,10 @@ PSL_API int psl_tally_read(const psl_tally_t *tally, int64_t *tallies, int64_t *
  * caller particles: of its particle id).
  * Photons: Woodcock tracking, Klein-Nishina Compton (Kahn), photoelectric,
  * pair.  Electrons/positrons: class-II condensed history, restricted Bethe
- * stopping, hard Moller and bremsstrahlung, Highland multiple scattering.
+ * stopping (Moller form for electrons, Bhabha form for positrons), hard
+ * Moller (e-) or Bhabha (e+) collisions and bremsstrahlung, Highland
+ * multiple scattering; a positron that stops annihilates into two 0.511 MeV
+ * photons.
  * Electrons are grouped by energy band before each transport pass so that a
  * warp steps one band.  Deposits are rounded to int64 in units of 2^-32
  * MeV and added atomically.  The batch is consumed (transport it once).
@@ -506,6 +526,29 @@ PSL_API int psl_profile_read(int32_t kernel, double *total_ms, int64_t *launches
  * land), used as the peak of the transport kernels' tally roofline.
  * Allocates and frees the cells on `stream`; synchronises it. */
 PSL_API int psl_atomic_peak(int64_t n_cells, int64_t n_updates, double *updates_per_s, void *stream);
+
+/* Failure-detection hooks for tests (process-wide; psl_debug_waits(0, 0, 0)
+ * restores the defaults).  Every device-side wait of the library is bounded
+ * and gives up with an error status instead of hanging: the onesweep sort's
+ * look-back (psl_build, psl_build_static, psl_stream_bin, psl_plan_create)
+ * returns PSL_ETIMEOUT, the photon pass's staged queue feed (an mbarrier
+ * wait) makes transport_run / psl_run return PSL_ETIMEOUT with the tally
+ * incomplete.  polls > 0 sets how many times such a wait polls before it
+ * gives up (default: about a second's worth).  flags make a wait wait on
+ * something that never comes, so that the limit runs out:
+ *   PSL_DEBUG_LOOKBACK_STALL  a sort tile never sees its predecessors'
+ *                             counts (every tile but the first gives up; the
+ *                             sort's output is then wrong but in bounds);
+ *   PSL_DEBUG_FEED_STALL      the second chunk a photon warp claims is never
+ *                             copied, so its mbarrier never completes (no
+ *                             copy is left in flight when the warp stops).
+ * queue_cap > 0 caps every particle queue of later transport calls at that
+ * many particles, so that secondaries overflow it (PSL_EOVERFLOW, tally
+ * incomplete).  Nothing here faults or hangs the device.  PSL_EINVAL for
+ * negative values or unknown flags. */
+#define PSL_DEBUG_LOOKBACK_STALL 1u
+#define PSL_DEBUG_FEED_STALL 2u
+PSL_API int psl_debug_waits(int64_t polls, uint32_t flags, int64_t queue_cap);
 
 /* Number of kernels this library has launched in this process (all threads);
  * a diagnostic for counting the launches of a timed region. */

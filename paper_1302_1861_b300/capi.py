@@ -32,12 +32,13 @@ EXPORTS = (
     "psl_denoiser_create", "psl_denoiser_destroy", "psl_denoiser_params", "psl_denoiser_forward",
     "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma", "psl_conv3d_form", "psl_tally_set_order",
     "psl_kth_smallest", "psl_tally_buffers", "psl_tally_info", "psl_tally_set_queue_depth",
-    "psl_dose_normalisation",
+    "psl_dose_normalisation", "psl_tally_trace_source", "psl_debug_waits",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
 ORDER_AUTO, ORDER_READING, ORDER_BATCH = 0, 1, 2
 STATIC_MAX_RECORDS = 1 << 20
+DEBUG_LOOKBACK_STALL, DEBUG_FEED_STALL = 1, 2
 
 vp = ctypes.c_void_p
 f32, i32, i64, u32, u64, f64 = (ctypes.c_float, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
@@ -146,6 +147,8 @@ def lib():
             "psl_tally_info": [vp, vp, vp, vp, vp],
             "psl_tally_set_queue_depth": [vp, i64],
             "psl_dose_normalisation": [vp, i64, i64, f64, vp],
+            "psl_tally_trace_source": [vp, i64, i64, vp, vp, vp, vp, vp, vp],
+            "psl_debug_waits": [i64, u32, i64],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -461,6 +464,19 @@ def psl_tally_info(tally: Tally):
     a, b, c, d = i64(), i64(), i64(), i32()
     check(lib().psl_tally_info(tally.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
     return a.value, b.value, c.value, d.value
+
+
+def psl_tally_trace_source(tally: Tally, first: int, n: int, entry=None, use=None, rec=None, status=None,
+                           state=None, ptype=None):
+    """Record the production source stage's decisions for histories [first, first+n) (n = 0: off)."""
+    check(lib().psl_tally_trace_source(tally.h, int(first), int(n), ptr(entry), ptr(use), ptr(rec), ptr(status),
+                                       ptr(state), ptr(ptype)))
+
+
+def debug_waits(polls: int = 0, flags: int = 0, queue_cap: int = 0):
+    """Failure-detection hooks (tests): polls of a bounded device wait, stalls
+    that make a wait run out, a cap on the particle queues; all 0 restores."""
+    check(lib().psl_debug_waits(int(polls), int(flags), int(queue_cap)))
 
 
 def psl_tally_set_queue_depth(tally: Tally, depth: int):

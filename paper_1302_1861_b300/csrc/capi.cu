@@ -24,6 +24,32 @@ int psl_fail(int code, const std::string &msg) {
 extern "C" const char *psl_last_error(void) { return g_last_error.c_str(); }
 
 // ------------------------------------------------------------------------
+// Failure-detection hooks (psl_debug_waits): the polls a bounded device
+// wait makes before it gives up, and the stalls and queue cap that let a
+// test make a wait run out or a queue overflow without faulting the GPU.
+namespace {
+std::atomic<long long> g_dbg_polls{0};
+std::atomic<unsigned> g_dbg_flags{0};
+std::atomic<long long> g_dbg_queue_cap{0};
+}  // namespace
+
+long long psl_wait_polls(long long dflt) {
+    const long long v = g_dbg_polls.load(std::memory_order_relaxed);
+    return v > 0 ? v : dflt;
+}
+unsigned psl_debug_flags() { return g_dbg_flags.load(std::memory_order_relaxed); }
+long long psl_debug_queue_cap() { return g_dbg_queue_cap.load(std::memory_order_relaxed); }
+
+extern "C" int psl_debug_waits(int64_t polls, uint32_t flags, int64_t queue_cap) {
+    if (polls < 0 || queue_cap < 0 || (flags & ~(uint32_t)(PSL_DEBUG_LOOKBACK_STALL | PSL_DEBUG_FEED_STALL)))
+        return psl_fail(PSL_EINVAL, "psl_debug_waits: bad argument");
+    g_dbg_polls.store(polls, std::memory_order_relaxed);
+    g_dbg_flags.store(flags, std::memory_order_relaxed);
+    g_dbg_queue_cap.store(queue_cap, std::memory_order_relaxed);
+    return PSL_OK;
+}
+
+// ------------------------------------------------------------------------
 // Device memory pool of the library: one per device, created on first use,
 // keeping freed blocks (release threshold = unlimited) so that the large
 // stream-ordered scratch of psl_build, psl_plan_create and psl_stream_bin is

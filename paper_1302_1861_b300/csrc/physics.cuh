@@ -5,12 +5,13 @@
 //   Compton       N_A (Z/A) sigma_KN(E), Klein-Nishina total cross section
 //   photoelectric C_PE (Z/A) Zeff^3 / E^3            (Z^4 / (A E^3) per atom)
 //   pair          C_PP (Z/A) Zeff (1 - 2 m c^2 / E)^3,  E > 2 m c^2
-// Electrons (water-like electron density for every medium, density scaled):
-//   restricted collision stopping power (Moller, energy transfers below
-//   W_cc, mean excitation energy 75 eV, no density effect), radiative
-//   stopping (T + m) T / (X0 (T + 2 MeV)) with a 1/k spectrum, of which the
-//   part below W_cb is continuous; hard Moller and bremsstrahlung cross
-//   sections above W_cc and W_cb.
+// Electrons and positrons (water-like electron density for every medium,
+// density scaled): restricted collision stopping power (energy transfers
+// below W_cc, mean excitation energy 75 eV, no density effect; Moller form
+// for electrons, Bhabha form for positrons), radiative stopping
+// (T + m) T / (X0 (T + 2 MeV)) with a 1/k spectrum, of which the part below
+// W_cb is continuous; hard Moller (e-) or Bhabha (e+) and bremsstrahlung
+// cross sections above W_cc and W_cb.
 #pragma once
 
 #define PH_ME 0.51099895
@@ -67,4 +68,48 @@ __device__ inline double el_brem_sigma(double T, double wcb) { return T <= wcb ?
 
 __device__ inline double el_stop_restricted(double T, double wcc, double wcb) {
     return el_col_restricted(T, wcc) + el_rad(T) * fmin(wcb, T) / T;
+}
+
+// Positrons.  Bhabha scattering on an atomic electron that takes the energy
+// W = x T, x in (0, 1] (the two are distinguishable): per unit x,
+//   2 pi r_e^2 m c^2 n / T * (1/(beta^2 x^2) - B1/x + B2 - B3 x + B4 x^2),
+// y = 1/(tau + 2), B1 = 2 - y^2, B2 = (1 - 2y)(3 + y^2), B4 = (1 - 2y)^3,
+// B3 = B4 + (1 - 2y)^2.
+struct BhabhaB { double b1, b2, b3, b4; };
+
+__host__ __device__ inline BhabhaB bhabha_coeffs(double T) {
+    const double y = 1.0 / (T / PH_ME + 2.0), q = 1.0 - 2.0 * y, q2 = q * q;
+    BhabhaB c;
+    c.b1 = 2.0 - y * y;
+    c.b2 = q * (3.0 + y * y);
+    c.b4 = q2 * q;
+    c.b3 = c.b4 + q2;
+    return c;
+}
+
+// hard Bhabha cross section (W from wcc to T), cm^2/g
+__device__ inline double pos_bhabha_sigma(double T, double wcc) {
+    if (T <= wcc) return 0.0;
+    const BhabhaB c = bhabha_coeffs(T);
+    const double x0 = wcc / T, b2 = el_beta2(T);
+    const double k = 2.0 * PH_PI * PH_RE * PH_RE * PH_ME * PH_NA * PH_ZA_WATER / T;
+    const double poly = (1.0 - x0) * (c.b2 - 0.5 * c.b3 * (1.0 + x0) + c.b4 * (1.0 + x0 + x0 * x0) / 3.0);
+    return k * ((1.0 - x0) / (b2 * x0) - c.b1 * log(1.0 / x0) + poly);
+}
+
+// restricted collision stopping power of a positron (transfers below cut)
+__device__ inline double pos_col_restricted(double T, double cut) {
+    const double tau = T / PH_ME, b2 = el_beta2(T), d = fmin(cut, T) / PH_ME, y = 1.0 / (tau + 2.0);
+    const double iom = PH_I_WATER / PH_ME, d2 = d * d, d3 = d2 * d;
+    const double brk = tau + 2.0 * d - 1.5 * d2 * y - (d - d3 / 3.0) * y * y - (0.5 * d2 - tau * d3 / 3.0 + 0.25 * d2 * d2) * y * y * y;
+    return el_K(T) * (log(2.0 * (tau + 2.0) / (iom * iom)) + log(tau * d) - b2 / tau * brk);
+}
+
+__device__ inline double pos_stop_restricted(double T, double wcc, double wcb) {
+    return pos_col_restricted(T, wcc) + el_rad(T) * fmin(wcb, T) / T;
+}
+
+// restricted stopping power of species sp (0 electron, 1 positron)
+__device__ inline double stop_restricted(int sp, double T, double wcc, double wcb) {
+    return sp ? pos_stop_restricted(T, wcc, wcb) : el_stop_restricted(T, wcc, wcb);
 }

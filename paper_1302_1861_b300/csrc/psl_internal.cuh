@@ -25,6 +25,12 @@ int psl_fail(int code, const std::string &msg);
 // opt-in event timing of the main kernels (psl_profile)
 enum { PK_KEY = 0, PK_ONESWEEP, PK_GATHER, PK_SOURCE, PK_PHOTON, PK_ELECTRON, PK_BAND, PK_READOUT };
 bool psl_timer_on();
+
+// failure-detection hooks (psl_debug_waits): polls of a bounded wait (dflt
+// unless a test set a limit), the stall flags and a cap on queue capacity
+long long psl_wait_polls(long long dflt);
+unsigned psl_debug_flags();
+long long psl_debug_queue_cap();
 void psl_timer_begin(int k, cudaStream_t st, void **tok);
 void psl_timer_end(int k, cudaStream_t st, void *tok);
 
@@ -146,6 +152,16 @@ struct psl_batch {
 };
 
 struct Workspace;
+// Per-history record of what the production source stage decided, for the
+// histories [first, first + n) of later transport calls on a tally.
+struct SrcTraceDev {
+    int64_t first = 0, n = 0;        // n = 0: off
+    int64_t *entry = nullptr, *use = nullptr, *rec = nullptr;
+    int8_t *status = nullptr;
+    float *state = nullptr;          // n x 8 (transported histories only)
+    int32_t *ptype = nullptr;
+};
+
 struct psl_tally {
     int32_t nx = 0, ny = 0, nz = 0, n_batches = 0;
     int64_t nvox = 0;
@@ -153,8 +169,9 @@ struct psl_tally {
     int64_t chunk_cap = 1 << 24;      // primaries per transport pass (queue depth)
     int32_t order = 0;                // psl_run history order: 0 auto, 1 reading order, 2 batch by batch
     unsigned long long *t = nullptr;  // [n_batches][nvox] (a batch's slice contiguous)
-    unsigned long long *ledger = nullptr;  // [8]
+    unsigned long long *ledger = nullptr;  // [16]: 12 reported slots, then scratch
     Workspace *ws = nullptr;
+    SrcTraceDev trace;                // psl_tally_trace_source
 };
 
 // ----------------------------------------------------------------- Philox --

@@ -101,6 +101,18 @@ extern "C" int psl_tally_buffers(psl_tally_t *t, int64_t **tallies, int64_t **le
     return PSL_OK;
 }
 
+extern "C" int psl_tally_trace_source(psl_tally_t *t, int64_t first, int64_t n, int64_t *entry, int64_t *use,
+                                      int64_t *rec, int8_t *status, float *state, int32_t *ptype) {
+    if (!t || first < 0 || n < 0) return psl_fail(PSL_EINVAL, "psl_tally_trace_source: bad argument");
+    SrcTraceDev T;
+    if (n > 0) {
+        T.first = first; T.n = n;
+        T.entry = entry; T.use = use; T.rec = rec; T.status = status; T.state = state; T.ptype = ptype;
+    }
+    t->trace = T;
+    return PSL_OK;
+}
+
 extern "C" int psl_tally_set_queue_depth(psl_tally_t *t, int64_t depth) {
     if (!t || depth < ((int64_t)1 << 12) || depth > ((int64_t)1 << 26))
         return psl_fail(PSL_EINVAL, "psl_tally_set_queue_depth: depth outside [2^12, 2^26]");

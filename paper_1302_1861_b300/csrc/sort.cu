@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(const uint32_t *__res
                                                           uint32_t *__restrict__ keys_out,
                                                           uint32_t *__restrict__ vals_out, uint32_t n, int shift,
                                                           const uint32_t *__restrict__ digit_offs,
-                                                          uint32_t *lookback, uint32_t *tile_counter, uint32_t *err) {
+                                                          uint32_t *lookback, uint32_t *tile_counter, uint32_t *err,
+                                                          long long spin_limit, bool stall) {
     __shared__ uint32_t s_keys[TILE];
     __shared__ uint32_t s_vals[TILE];
     __shared__ uint32_t whist[SORT_THREADS / 32][RADIX];   // per-warp digit counts, then warp prefixes
@@ -120,9 +121,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_onesweep(const uint32_t *__res
             long long spins = 0;
             while (t >= 0) {
                 uint32_t v = lb[(size_t)t * RADIX + d];
-                uint32_t st = v & ~LB_MASK;
+                uint32_t st = stall ? 0u : (v & ~LB_MASK);      // (stall: a test's flag nothing sets)
                 if (st == 0) {
-                    if (++spins > SPIN_LIMIT) { atomicOr(err, PSL_DEV_ERR_TIMEOUT); break; }
+                    if (++spins > spin_limit) { atomicOr(err, PSL_DEV_ERR_TIMEOUT); break; }
                     continue;
                 }
                 excl += v & LB_MASK;
@@ -212,7 +213,8 @@ int sort_pairs_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t 
         cudaMemsetAsync(tile_ctr, 0, 4, st);
         cudaMemsetAsync(lookback, 0, (size_t)n_tiles * RADIX * 4, st);
         { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_ONESWEEP, st, &tk_); k_onesweep<<<n_tiles, SORT_THREADS, 0, st>>>(kb[cur], (p == 0 && vals_identity) ? nullptr : vb[cur], kb[cur ^ 1],
-                                                     vb[cur ^ 1], n, 8 * p, doffs + p * RADIX, lookback, tile_ctr, err); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_ONESWEEP, st, tk_); }
+                                                     vb[cur ^ 1], n, 8 * p, doffs + p * RADIX, lookback, tile_ctr, err,
+                                                     psl_wait_polls(SPIN_LIMIT), (psl_debug_flags() & PSL_DEBUG_LOOKBACK_STALL) != 0); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_ONESWEEP, st, tk_); }
         cur ^= 1;
     }
     *result_in_alt = cur;

@@ -62,18 +62,21 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #define PSL_TRANSPORT_MIN_BLOCKS 4     // resident 256-thread blocks per SM (register cap 64)
 #endif
 
+// Charged-particle tables hold the electron's NT nodes, then the positron's
+// (species offset NT): the species of a particle selects its rows.
 struct Tables {
     const float4 *ph0, *ph1;   // material 0/1: mu_c, mu_pe, mu_pp, mu_total (cm^2/g)
-    const float4 *el;          // S_restricted (MeV cm^2/g), sigma_moller, sigma_brem (cm^2/g), 0
-    const float2 *rng;         // CSDA range R (g/cm^2) and dR/dlnT * dlnT at each node
-    const float *irng;         // ln T at uniform steps of ln R (inverse range)
+    const float4 *el;          // [2][NT] S_restricted (MeV cm^2/g), sigma_moller or sigma_bhabha, sigma_brem (cm^2/g), 0
+    const float2 *rng;         // [2][NT] CSDA range R (g/cm^2) and dR/dlnT * dlnT at each node
+    const float *irng;         // [2][NT] ln T at uniform steps of ln R (inverse range)
     float lnE0, inv_dln;
-    float lnR0, inv_dlnR;      // grid of the inverse range table
+    float lnR0[2], inv_dlnR[2];  // grid of each species' inverse range table
 };
 
 struct Acc {
     unsigned long long dep, esc, emitted;                      // fixed-point energy
     uint32_t compton, photo, pair, steps, atomics, wsteps;     // per-thread event counts
+    uint32_t hard;                                             // hard Moller / Bhabha collisions
 };
 
 struct Args {
@@ -99,6 +102,8 @@ struct Args {
     Queue e_out, p_out;
     float band_ln0, band_scale;
     uint32_t *band_hist;      // band counts of the electrons queued for the next regrouping
+    uint32_t wait_polls;      // polls of a bounded wait before it gives up
+    uint32_t dbg;             // failure-detection stalls (PSL_DEBUG_*)
 };
 
 // ----------------------------------------------------------- tables ------
@@ -114,14 +119,17 @@ __global__ void k_tables(float4 *ph0, float4 *ph1, float4 *el, double wcc, doubl
     ph1[i] = make_float4((float)mc, (float)mpe, (float)mpp, (float)(mc + mpe + mpp));
     el[i] = make_float4((float)el_stop_restricted(E, wcc, wcb), (float)el_moller_sigma(E, wcc),
                         (float)el_brem_sigma(E, wcb), 0.f);
+    el[NT + i] = make_float4((float)pos_stop_restricted(E, wcc, wcb), (float)pos_bhabha_sigma(E, wcc),
+                             (float)el_brem_sigma(E, wcb), 0.f);
 }
 
 // CSDA range with the restricted stopping power: R_i = integral from T_0 to
 // T_i of dT/S, each interval by 8-point Gauss-Legendre in double (one thread
 // per interval), then a running sum
 __global__ void k_range_intervals(double *iv, double wcc, double wcb) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, sp = blockIdx.y;   // species: 0 e-, 1 e+
     if (i >= NT) return;
+    iv += sp * NT;
     const double x8[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
     const double w8[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
     const double l0 = log(T_LO), dl = (log(T_HI) - log(T_LO)) / (NT - 1);
@@ -130,7 +138,7 @@ __global__ void k_range_intervals(double *iv, double wcc, double wcb) {
     const double m = 0.5 * (T + Tp), h = 0.5 * (T - Tp);
     double acc = 0.0;
     for (int k = 0; k < 4; ++k)
-        acc += w8[k] * (1.0 / el_stop_restricted(m - h * x8[k], wcc, wcb) + 1.0 / el_stop_restricted(m + h * x8[k], wcc, wcb));
+        acc += w8[k] * (1.0 / stop_restricted(sp, m - h * x8[k], wcc, wcb) + 1.0 / stop_restricted(sp, m + h * x8[k], wcc, wcb));
     iv[i] = h * acc;
 }
 
@@ -141,6 +149,8 @@ __global__ void k_range_intervals(double *iv, double wcc, double wcb) {
 __global__ void __launch_bounds__(1024) k_range_table(double *iv, float2 *rt, float *irt, float *igrid, double wcc,
                                                       double wcb) {
     __shared__ double liv[NT];
+    const int sp = blockIdx.x;                       // one block per species
+    iv += sp * NT; rt += sp * NT; irt += sp * NT; igrid += 2 * sp;
     const double l0 = log(T_LO), dl = (log(T_HI) - log(T_LO)) / (NT - 1);
     if (threadIdx.x == 0) {
         double R = 0.0;
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(1024) k_range_table(double *iv, float2 *rt, fl
     __syncthreads();
     for (int i = threadIdx.x; i < NT; i += blockDim.x) {
         const double R = iv[i], T = exp(l0 + dl * i);
-        rt[i] = make_float2((float)R, (float)(T * dl / el_stop_restricted(T, wcc, wcb)));
+        rt[i] = make_float2((float)R, (float)(T * dl / stop_restricted(sp, T, wcc, wcb)));
         liv[i] = i > 0 ? log(R) : 0.0;
     }
     __syncthreads();
@@ -208,16 +218,18 @@ __device__ __forceinline__ float4 lerp4(const float4 *a, int i, float f) {
 }
 
 // R(E): cubic Hermite in ln E with the exact node derivatives dR/dlnE = E/S
+// (i: node index including the species offset)
 __device__ __forceinline__ float range_at(const Tables &T, int i, float f) {
     const float2 a = __ldg(T.rng + i), b = __ldg(T.rng + i + 1);
     const float f2 = f * f, f3 = f2 * f;
     return (2.f * f3 - 3.f * f2 + 1.f) * a.x + (f3 - 2.f * f2 + f) * a.y + (3.f * f2 - 2.f * f3) * b.x + (f3 - f2) * b.y;
 }
 
-__device__ __forceinline__ float range_of(const Tables &T, float E) {
+// sp: the species offset (0 electron, NT positron)
+__device__ __forceinline__ float range_of(const Tables &T, float E, int sp) {
     int i; float f;
     tab_pos(T, E, i, f);
-    return range_at(T, i, f);
+    return range_at(T, i + sp, f);
 }
 
 // ------------------------------------------------------------- helpers ---
@@ -265,13 +277,15 @@ __device__ __forceinline__ float ln_uniform(float xi) { return logf(xi); }
 __device__ __forceinline__ void sincos_2pi(float xi, float *s, float *c) { sincospif(2.0f * xi, s, c); }
 
 // rotate unit direction by the polar angle (cosine c, sine st >= 0) and the
-// azimuth (sine sp, cosine cp); renormalised
+// azimuth (sine sp, cosine cp), the azimuth measured from the plane through
+// the direction and the z axis (exact for every direction off the axis;
+// only one on the axis itself takes the x-y pair); renormalised
 __device__ __forceinline__ void rotate_dir(float &u, float &v, float &w, float c, float st, float sp, float cp) {
     float nu, nv, nw;
-    if (fabsf(w) > 0.99999f) {
+    const float s2 = u * u + v * v;                               // 1 - w^2 without cancellation
+    if (s2 <= 1e-30f) {
         nu = st * cp; nv = st * sp; nw = w > 0.0f ? c : -c;
     } else {
-        const float s2 = u * u + v * v;                           // 1 - w^2 without cancellation
         const float it = rsqrtf(s2), t = s2 * it;
         nu = u * c + st * (u * w * cp - v * sp) * it;
         nv = v * c + st * (v * w * cp + u * sp) * it;
@@ -338,12 +352,14 @@ __device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, 
 
 // ledger slots: 0 emitted, 1 escaped, 2 deposited (fixed point), 3 Compton,
 // 4 photoelectric, 5 pair, 6 electron steps, 7 errors, 8 tally atomics of
-// photon passes, 9 tally atomics of electron passes, 10 Woodcock steps
+// photon passes, 9 tally atomics of electron passes, 10 Woodcock steps,
+// 11 hard Moller / Bhabha collisions
 __device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int atomics_slot) {
-    unsigned long long v[9] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps, a.atomics, a.wsteps, a.emitted};
+    unsigned long long v[10] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps, a.atomics, a.wsteps, a.emitted,
+                                a.hard};
     // (the 32-bit event counts widen here)
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 0; k < 10; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
     }
@@ -357,6 +373,7 @@ __device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int atomics_slo
         if (v[6]) atomicAdd(&A.ledger[atomics_slot], v[6]);
         if (v[7]) atomicAdd(&A.ledger[10], v[7]);
         if (v[8]) atomicAdd(&A.ledger[0], v[8]);
+        if (v[9]) atomicAdd(&A.ledger[11], v[9]);
     }
 }
 
@@ -392,7 +409,8 @@ struct Feed {
         return &sm.buf[threadIdx.x >> 5][b][i];
     }
 
-    __device__ __forceinline__ void init(FeedSmem &sm, const Particle *src, uint32_t n, uint32_t *head, uint32_t *err) {
+    __device__ __forceinline__ void init(FeedSmem &sm, const Particle *src, uint32_t n, uint32_t *head, uint32_t *err,
+                                         uint32_t polls, bool stall) {
         st = 0;
         if ((threadIdx.x & 31) == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar_addr(sm, 0)) : "memory");
@@ -401,17 +419,19 @@ struct Feed {
         }
         __syncwarp();
         set_cnt(0, claim(sm, 0, src, n, head));
-        set_cnt(1, claim(sm, 1, src, n, head));
-        if (cnt(0)) wait(sm, 0, err);
+        // (stall: a failure-detection test; the second chunk's copy is never
+        // issued, so its mbarrier never completes and the wait runs out)
+        set_cnt(1, claim(sm, 1, src, n, head, stall));
+        if (cnt(0)) wait(sm, 0, err, polls);
     }
     // claim the next chunk into buffer b; returns its particle count
     __device__ __forceinline__ static uint32_t claim(FeedSmem &sm, uint32_t b, const Particle *src, uint32_t n,
-                                                     uint32_t *head) {
+                                                     uint32_t *head, bool no_copy = false) {
         uint32_t base = 0;
         if ((threadIdx.x & 31) == 0) base = atomicAdd(head, (uint32_t)FEED_CHUNK);
         base = __shfl_sync(FULL, base, 0);
         const uint32_t c = base < n ? min(n - base, (uint32_t)FEED_CHUNK) : 0u;
-        if (c && (threadIdx.x & 31) == 0) {
+        if (c && !no_copy && (threadIdx.x & 31) == 0) {
             const uint32_t bytes = c * (uint32_t)sizeof(Particle);
             const uint32_t mb = bar_addr(sm, b);
             const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slot(sm, b, 0));
@@ -422,11 +442,11 @@ struct Feed {
         }
         return c;
     }
-    // wait (bounded) until buffer b's copy has landed
-    __device__ __forceinline__ void wait(FeedSmem &sm, uint32_t b, uint32_t *err) {
+    // wait (bounded: `polls` tries) until buffer b's copy has landed
+    __device__ __forceinline__ void wait(FeedSmem &sm, uint32_t b, uint32_t *err, uint32_t polls) {
         const uint32_t mb = bar_addr(sm, b), par = (st >> (19u + b)) & 1u;
         uint32_t ok = 0;
-        for (uint32_t it = 0; it < FEED_SPIN && !ok; ++it)
+        for (uint32_t it = 0; it < polls && !ok; ++it)
             asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
                          : "=r"(ok) : "r"(mb), "r"(par) : "memory");
         st ^= 1u << (19u + b);
@@ -439,10 +459,11 @@ struct Feed {
     // true and fills p for a lane in `need` that got one; a lane in `need`
     // that got none finds the queue exhausted.
     __device__ __forceinline__ bool take(FeedSmem &sm, unsigned need, unsigned lt, bool mine, Particle &p,
-                                         const Particle *src, uint32_t n, uint32_t *head, uint32_t *err) {
+                                         const Particle *src, uint32_t n, uint32_t *head, uint32_t *err,
+                                         uint32_t polls) {
         const uint32_t k = __popc(need), rank = __popc(need & lt);
         const uint32_t c = cur(), nx = c ^ 1u, avail = cnt(c) - pos();
-        if (k >= avail && cnt(nx)) wait(sm, nx, err);
+        if (k >= avail && cnt(nx)) wait(sm, nx, err, polls);
         const uint32_t cn = cnt(nx);                    // after a failed wait this is 0
         bool got = false;
         if (mine) {
@@ -600,17 +621,17 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
     const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     Photon g;
     Feed F;
-    F.init(sm, src, n, head, A.err);
+    F.init(sm, src, n, head, A.err, A.wait_polls, (A.dbg & PSL_DEBUG_FEED_STALL) != 0);
     bool alive = false, done = false, real = false;
     for (;;) {
         const unsigned need = __ballot_sync(FULL, !alive && !done);
         if (need) {
             Particle p;
             const bool mine = !alive && !done;
-            const bool got = F.take(sm, need, lt, mine, p, src, n, head, A.err);
+            const bool got = F.take(sm, need, lt, mine, p, src, n, head, A.err, A.wait_polls);
             if (mine) {
                 if (!got) {
                     done = true;
@@ -665,11 +686,13 @@ __device__ __forceinline__ float highland(float T, float s, float rho) {
 // energy whose CSDA range is r (g/cm^2): ln T from the inverse range table,
 // then one Newton step on the forward (Hermite) range, so that the range of
 // the result is r to float precision (a step of zero length keeps T)
-__device__ __forceinline__ float energy_of_range(const Tables &T, float r) {
-    float x = (__logf(r) - T.lnR0) * T.inv_dlnR;
+// (pos: the particle is a positron; its tables start at offset NT)
+__device__ __forceinline__ float energy_of_range(const Tables &T, float r, bool pos) {
+    const int sp = pos ? NT : 0;
+    float x = (__logf(r) - T.lnR0[pos]) * T.inv_dlnR[pos];
     x = fminf(fmaxf(x, 0.0f), (float)(NT - 1) - 1e-3f);
-    const int i = (int)x;
-    const float f = x - (float)i;
+    const int i = (int)x + sp;
+    const float f = x - (float)(i - sp);
     const float a = __ldg(T.irng + i), b = __ldg(T.irng + i + 1);
     const float lt0 = a + f * (b - a);
     // forward table position of ln T0 and the Hermite range with its slope
@@ -677,7 +700,7 @@ __device__ __forceinline__ float energy_of_range(const Tables &T, float r) {
     xf = fminf(fmaxf(xf, 0.0f), (float)(NT - 1) - 1e-3f);
     const int j = (int)xf;
     const float g = xf - (float)j;
-    const float2 p = __ldg(T.rng + j), q = __ldg(T.rng + j + 1);
+    const float2 p = __ldg(T.rng + j + sp), q = __ldg(T.rng + j + sp + 1);
     const float g2 = g * g, g3 = g2 * g;
     const float rg = (2.f * g3 - 3.f * g2 + 1.f) * p.x + (g3 - 2.f * g2 + g) * p.y + (3.f * g2 - 2.f * g3) * q.x + (g3 - g2) * q.y;
     const float dr = (6.f * g2 - 6.f * g) * p.x + (3.f * g2 - 4.f * g + 1.f) * p.y + (6.f * g - 6.f * g2) * q.x + (3.f * g2 - 2.f * g) * q.y;
@@ -700,6 +723,25 @@ __device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, con
     }
     atomicOr(err, PSL_DEV_ERR_STEPS);
     return ec;
+}
+
+// Bhabha energy-transfer fraction x in [wcc/T, 1]: x proposed from the
+// density 1/x^2 on [x0, 1] and kept with probability
+// h(x) = 1 - beta^2 x (B1 - x (B2 - x (B3 - x B4))), which lies in (0, 1].
+__device__ __forceinline__ float sample_bhabha(float T, float wcc, Rng &rng, const uint32_t *rk, uint32_t p0,
+                                               uint32_t p1, uint32_t *err) {
+    const float y = 1.0f / (T * (1.0f / F_ME) + 2.0f), q = 1.0f - 2.0f * y, q2 = q * q;
+    const float b1 = 2.0f - y * y, b2 = q * (3.0f + y * y), b4 = q2 * q, b3 = b4 + q2;
+    const float gm = T * (1.0f / F_ME) + 1.0f, beta2 = 1.0f - 1.0f / (gm * gm);
+    const float x0 = wcc / T;
+    for (int it = 0; it < 1000; ++it) {
+        const float r1 = rng.next(rk, p0, p1), r2 = rng.next(rk, p0, p1);
+        const float x = x0 / (1.0f - r1 * (1.0f - x0));
+        const float h = 1.0f - beta2 * x * (b1 - x * (b2 - x * (b3 - x * b4)));
+        if (r2 <= h) return x;
+    }
+    atomicOr(err, PSL_DEV_ERR_STEPS);
+    return x0;
 }
 
 __device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &s, uint32_t iv) {
@@ -737,9 +779,12 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
         const float rho = fabsf(__ldg(A.mrho + iv));
         int ti; float tf;
         tab_pos(A.tab, s.t, ti, tf);
-        const float4 el = lerp4(A.tab.el, ti, tf);
-        // hard cross sections vanish below their thresholds (guard the interpolation)
-        const float sig = hard_on ? rho * ((s.t > 2.0f * A.wcc ? el.y : 0.0f) + (s.t > A.wcb ? el.z : 0.0f)) : 0.0f;
+        const int sp = s.pos ? NT : 0;
+        const float4 el = lerp4(A.tab.el + sp, ti, tf);
+        // hard cross sections vanish below their thresholds (guard the
+        // interpolation): Moller above 2 W_cc, Bhabha above W_cc
+        const float wth = s.pos ? A.wcc : 2.0f * A.wcc;
+        const float sig = hard_on ? rho * ((s.t > wth ? el.y : 0.0f) + (s.t > A.wcb ? el.z : 0.0f)) : 0.0f;
         const float s_hard = sig > 0.0f ? __fdividef(s.nlam, sig) : INFINITY;
         // distance to the voxel boundary
         float s_bound = INFINITY;
@@ -758,7 +803,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
             }
         }
         const float tlim = fmaxf(0.9f * s.t, A.ecut);
-        const float rlim = range_of(A.tab, tlim);
+        const float rlim = range_of(A.tab, tlim, sp);
         const float s_max = (s.r - rlim) * __frcp_rn(rho);
         int which;
         float step;
@@ -769,7 +814,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
         // range left; the range itself is carried, not recomputed from the energy
         float tend, rend;
         if (which == 2) { tend = tlim; rend = rlim; }
-        else { rend = s.r - rho * step; tend = fmaxf(energy_of_range(A.tab, rend), tlim); }
+        else { rend = s.r - rho * step; tend = fmaxf(energy_of_range(A.tab, rend, s.pos), tlim); }
         const float th0 = highland(s.t, step, rho);
         deposit(A, acc, iv, s.t - tend, s.wt, s.root);
         s.t = tend;
@@ -813,13 +858,16 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
     {
         int tj; float tg;
         tab_pos(A.tab, s.t, tj, tg);
-        const float4 e2 = lerp4(A.tab.el, tj, tg);
-        const float sm = s.t > 2.0f * A.wcc ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
+        const int sp = s.pos ? NT : 0;
+        const float4 e2 = lerp4(A.tab.el + sp, tj, tg);
+        const float sm = s.t > (s.pos ? A.wcc : 2.0f * A.wcc) ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
         rng.align();                                            // the hard event's draws
         const float r = rng.next(A.rk, s.p0, s.p1) * (sm + sb);
         if (sm + sb > 0.0f) {
-            if (r < sm) {                                         // hard Moller
-                const float eps = sample_moller(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err);
+            if (r < sm) {                                         // hard Moller (e-) or Bhabha (e+)
+                acc.hard++;
+                const float eps = s.pos ? sample_bhabha(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err)
+                                        : sample_moller(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
                 // polar cosines of the two electrons from momentum balance;
                 // their sines from the same balance without cancellation
@@ -840,7 +888,7 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
                 else push_particle(A.p_out, A, 0, s.x, s.y, s.z, s.u, s.v, s.w, kph, s.wt, s.p0, s.p1, s.nchild, s.root);
                 s.t -= kph;
             }
-            s.r = range_of(A.tab, s.t);
+            s.r = range_of(A.tab, s.t, sp);
         }
         s.nlam = -1.0f;                                           // drawn at the next step
     }
@@ -856,7 +904,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
     const uint32_t n = min(*n_ptr, cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     Electron s;
     bool alive = false, done = false, hard = false;
     for (;;) {
@@ -886,7 +934,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
                     s.draw = 0;
                     s.nlam = -1.0f;                               // drawn at the first step
-                    s.r = range_of(A.tab, s.t);
+                    s.r = range_of(A.tab, s.t, s.pos ? NT : 0);
                     alive = true;
                 } else {
                     done = true;
@@ -947,9 +995,12 @@ __global__ void k_slice_bounds(const uint32_t *keys, uint32_t n, uint32_t nb, ui
 // Histories first + i * stride, i < n; or, with a list, the histories
 // first + list[list_off[slice] + root0 + i] of one batch of a window whose
 // offsets were sorted by batch (at most n of them: more is an overflow).
+// TRACE: the instance launched while a tally records the source stage
+// (psl_tally_trace_source); the production instance compiles without it.
+template <bool TRACE>
 __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev P, int64_t first, int64_t stride, uint32_t n,
                                                 uint32_t root0, int32_t slice, Particle *out, uint32_t *count,
-                                                const uint32_t *list, const uint32_t *list_off) {
+                                                const uint32_t *list, const uint32_t *list_off, SrcTraceDev T) {
     __shared__ PlanShared S;
     __shared__ uint32_t bh[NBANDS];
     plan_shared_load(P, S);
@@ -959,12 +1010,15 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
     uint32_t lbase = 0;
     if (list) {
         lbase = list_off[slice] + root0;
-        const uint32_t total = list_off[slice + 1] - list_off[slice];
+        // (bounds from a sort whose look-back gave up may be out of order:
+        // then the batch is skipped, and the error word already says why)
+        const uint32_t o0 = list_off[slice], o1 = list_off[slice + 1];
+        const uint32_t total = o1 >= o0 ? o1 - o0 : 0u;
         const uint32_t left = total > root0 ? total - root0 : 0u;
         if (left > n && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, PSL_DEV_ERR_QUEUE);
         n = min(n, left);
     }
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int lane = threadIdx.x & 31;
     // each warp takes runs of SRC_RUN consecutive histories, 32 at a time,
     // and each lane carries its (group, segment) to the next 32: consecutive
@@ -1008,12 +1062,14 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
             E[k] = P.ent[S.gseg[gk[k]] + (int64_t)pidx];
         }
         PslRecord R[SRC_ILP];
+        int64_t ri[SRC_ILP];
 #pragma unroll
         for (int k = 0; k < SRC_ILP; ++k) {
             if (!ok[k]) continue;
             uint64_t rw, rr;
             divmod_u64((uint64_t)(E[k].offset + use[k]), (uint64_t)E[k].nrec, rw, rr);
-            R[k] = P.rec[E[k].start + (int64_t)rr];
+            ri[k] = E[k].start + (int64_t)rr;
+            R[k] = P.rec[ri[k]];
         }
 #pragma unroll
         for (int k = 0; k < SRC_ILP; ++k) {
@@ -1021,6 +1077,18 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
             SrcOut o;
             o.status = -1;
             if (ok[k]) record_to_phantom(R[k], P.beams[E[k].beam], P.z_psl, P.L, P.origin, true, o);
+            if (TRACE && ok[k]) {                                   // traced call (tests)
+                const int64_t t = h[k] - T.first;
+                if (t >= 0 && t < T.n) {
+                    if (T.entry) T.entry[t] = E[k].entry;
+                    if (T.use) T.use[t] = use[k];
+                    if (T.rec) T.rec[t] = ri[k];
+                    if (T.status) T.status[t] = (int8_t)o.status;
+                    if (T.ptype) T.ptype[t] = o.ptype;
+                    if (T.state && o.status == PSL_SRC_TRANSPORT)
+                        for (int c = 0; c < 8; ++c) T.state[8 * t + c] = o.s[c];
+                }
+            }
             if (o.status == PSL_SRC_TRANSPORT || o.status == PSL_SRC_MISS) {
                 const unsigned long long e = fixed_point(o.s[6], o.s[7]);
                 acc.emitted += e;
@@ -1129,7 +1197,7 @@ struct TableCache {
     float4 *ph0 = nullptr, *ph1 = nullptr, *el = nullptr;
     float2 *rng = nullptr;
     float *irng = nullptr;
-    float igrid[2] = {0.f, 0.f};
+    float igrid[4] = {0.f, 0.f, 0.f, 0.f};   // per species: ln R0, 1 / d ln R
 };
 std::mutex g_tab_mu;
 std::vector<TableCache> g_tabs;
@@ -1144,17 +1212,17 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
     t.device = dev; t.wcc = wcc; t.wcb = wcb;
     PSL_CUDA(cudaMalloc((void **)&t.ph0, NT * sizeof(float4)));
     PSL_CUDA(cudaMalloc((void **)&t.ph1, NT * sizeof(float4)));
-    PSL_CUDA(cudaMalloc((void **)&t.el, NT * sizeof(float4)));
-    PSL_CUDA(cudaMalloc((void **)&t.rng, NT * sizeof(float2)));
+    PSL_CUDA(cudaMalloc((void **)&t.el, 2 * NT * sizeof(float4)));
+    PSL_CUDA(cudaMalloc((void **)&t.rng, 2 * NT * sizeof(float2)));
     k_tables<<<(NT + 255) / 256, 256, 0, st>>>(t.ph0, t.ph1, t.el, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
     double *iv = nullptr;
     float *ig = nullptr;
-    PSL_CUDA(cudaMalloc((void **)&iv, NT * sizeof(double)));
-    PSL_CUDA(cudaMalloc((void **)&ig, 2 * sizeof(float)));
-    PSL_CUDA(cudaMalloc((void **)&t.irng, NT * sizeof(float)));
-    k_range_intervals<<<(NT + 127) / 128, 128, 0, st>>>(iv, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
-    k_range_table<<<1, 1024, 0, st>>>(iv, t.rng, t.irng, ig, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
-    PSL_CUDA(cudaMemcpyAsync(t.igrid, ig, 2 * sizeof(float), cudaMemcpyDeviceToHost, st));
+    PSL_CUDA(cudaMalloc((void **)&iv, 2 * NT * sizeof(double)));
+    PSL_CUDA(cudaMalloc((void **)&ig, 4 * sizeof(float)));
+    PSL_CUDA(cudaMalloc((void **)&t.irng, 2 * NT * sizeof(float)));
+    k_range_intervals<<<dim3((NT + 127) / 128, 2), 128, 0, st>>>(iv, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    k_range_table<<<2, 1024, 0, st>>>(iv, t.rng, t.irng, ig, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaMemcpyAsync(t.igrid, ig, 4 * sizeof(float), cudaMemcpyDeviceToHost, st));
     PSL_CUDA(cudaStreamSynchronize(st));
     cudaFree(iv);
     cudaFree(ig);
@@ -1185,7 +1253,7 @@ struct Workspace {
     void *bm_scratch = nullptr;
     // cached CUDA graph of one psl_run call
     cudaGraphExec_t graph = nullptr;
-    uint64_t graph_key[8] = {0};
+    uint64_t graph_key[11] = {0};
 };
 
 void workspace_free(Workspace *w) {
@@ -1279,7 +1347,7 @@ static int source_blocks_per_sm() {
     static int nb = 0;
     if (!nb) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_source, 256, 0) != cudaSuccess || v < 1) v = 4;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_source<false>, 256, 0) != cudaSuccess || v < 1) v = 4;
         nb = v;
     }
     return nb;
@@ -1385,6 +1453,7 @@ struct Runner {
     bool timing = false;
     int grid_t = 0, grid_m = 0, grid_src = 0;
     int64_t chunk = 0;
+    uint32_t cap_p = 0, cap_e = 0, cap_s = 0;   // queue capacities in use (a test may cap them)
 
     int prepare(const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally *t, uint64_t seed, int64_t need,
                 cudaStream_t stream, bool capturing) {
@@ -1401,6 +1470,14 @@ struct Runner {
         chunk = std::max<int64_t>(1, std::min<int64_t>(need, t->chunk_cap));
         if ((rc = workspace_ensure(t, chunk))) return rc;
         w = t->ws;
+        {
+            const long long qc = psl_debug_queue_cap();       // failure-detection tests only
+            cap_p = qc > 0 ? (uint32_t)std::min<long long>(w->cap_p, qc) : w->cap_p;
+            cap_e = qc > 0 ? (uint32_t)std::min<long long>(w->cap_e, qc) : w->cap_e;
+            cap_s = qc > 0 ? (uint32_t)std::min<long long>(w->cap_s, qc) : w->cap_s;
+        }
+        A.wait_polls = (uint32_t)std::min<long long>(psl_wait_polls(FEED_SPIN), 0xFFFFFFFFll);
+        A.dbg = psl_debug_flags();
         const int64_t nvox = t->nvox;
         cudaMemsetAsync(w->rmax, 0, 2 * sizeof(int), st);
         k_rho_max<<<(int)std::min<int64_t>((nvox + 255) / 256, psl_sm_count() * 4), 256, 0, st>>>(ph->mat, ph->rho, nvox, w->rmax, w->mrho); PSL_NOTE_LAUNCH();
@@ -1416,7 +1493,8 @@ struct Runner {
             A.rk[2 * r + 1] = A.k1 + (uint32_t)r * 0xBB67AE85u;
         }
         A.tab.ph0 = tc.ph0; A.tab.ph1 = tc.ph1; A.tab.el = tc.el; A.tab.rng = tc.rng; A.rmax = w->rmax;
-        A.tab.irng = tc.irng; A.tab.lnR0 = tc.igrid[0]; A.tab.inv_dlnR = tc.igrid[1];
+        A.tab.irng = tc.irng;
+        for (int k = 0; k < 2; ++k) { A.tab.lnR0[k] = tc.igrid[2 * k]; A.tab.inv_dlnR[k] = tc.igrid[2 * k + 1]; }
         A.tab.lnE0 = (float)log(T_LO);
         A.tab.inv_dln = (float)((NT - 1) / (log(T_HI) - log(T_LO)));
         A.ledger = t->ledger;
@@ -1459,13 +1537,13 @@ struct Runner {
         // only caller electrons (a materialised batch) are counted here
         if (na) { k_band_count<<<gm(), 256, 0, st>>>(A, a, na, w->E[ec], cE(ec), 0u, hist); PSL_NOTE_LAUNCH(); }
         k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
-        k_band_scatter<<<gm(), 256, 0, st>>>(A, a, na, w->E[ec], cE(ec), w->cap_e, cursor, w->S, w->cap_s); PSL_NOTE_LAUNCH();
+        k_band_scatter<<<gm(), 256, 0, st>>>(A, a, na, w->E[ec], cE(ec), cap_e, cursor, w->S, cap_s); PSL_NOTE_LAUNCH();
         te(PK_BAND, tk);
     }
     void photon_pass(const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
         Args a2 = A;
-        a2.e_out = Queue{w->E[ec], cE(ec), w->cap_e};
-        a2.p_out = Queue{w->P[pc ^ 1], cP(pc ^ 1), w->cap_p};
+        a2.e_out = Queue{w->E[ec], cE(ec), cap_e};
+        a2.p_out = Queue{w->P[pc ^ 1], cP(pc ^ 1), cap_p};
         cudaMemsetAsync(w->cnt + 5, 0, 4, st);
         void *tk = nullptr;
         tb(PK_PHOTON, &tk);
@@ -1474,12 +1552,12 @@ struct Runner {
     }
     void electron_pass() {
         Args a2 = A;
-        a2.e_out = Queue{w->E[ec ^ 1], cE(ec ^ 1), w->cap_e};
-        a2.p_out = Queue{w->P[pc ^ 1], cP(pc ^ 1), w->cap_p};
+        a2.e_out = Queue{w->E[ec ^ 1], cE(ec ^ 1), cap_e};
+        a2.p_out = Queue{w->P[pc ^ 1], cP(pc ^ 1), cap_p};
         cudaMemsetAsync(w->cnt + 6, 0, 4, st);
         void *tk = nullptr;
         tb(PK_ELECTRON, &tk);
-        k_electron<<<gt(), 256, 0, st>>>(a2, w->S, w->cnt + 4, w->cap_s, w->cnt + 6); PSL_NOTE_LAUNCH();
+        k_electron<<<gt(), 256, 0, st>>>(a2, w->S, w->cnt + 4, cap_s, w->cnt + 6); PSL_NOTE_LAUNCH();
         te(PK_ELECTRON, tk);
     }
 
@@ -1514,12 +1592,14 @@ struct Runner {
             if (J.lazy) {
                 const uint32_t cp = (uint32_t)std::min<int64_t>(J.n - a0, chunk);
                 Args a2 = A;
-                a2.e_out = Queue{w->E[ec], cE(ec), w->cap_e};
+                a2.e_out = Queue{w->E[ec], cE(ec), cap_e};
                 cudaMemsetAsync(w->cnt + 7, 0, 4, st);
                 void *tk = nullptr;
                 tb(PK_SOURCE, &tk);
-                k_source<<<grid_src, 256, 0, st>>>(a2, J.P, J.list ? J.first : J.first + a0 * J.stride, J.stride, cp,
-                                                 (uint32_t)a0, J.slice, w->Q, w->cnt + 7, J.list, J.list_off);
+                auto *ks = tally->trace.n ? k_source<true> : k_source<false>;
+                ks<<<grid_src, 256, 0, st>>>(a2, J.P, J.list ? J.first : J.first + a0 * J.stride, J.stride, cp,
+                                             (uint32_t)a0, J.slice, w->Q, w->cnt + 7, J.list, J.list_off,
+                                             tally->trace);
                 PSL_NOTE_LAUNCH();
                 te(PK_SOURCE, tk);
                 photon_pass(w->Q, w->cnt + 7, 0, cp);
@@ -1529,7 +1609,7 @@ struct Runner {
                 ca = J.p + (J.cap - a0 - na);
                 if (cp) photon_pass(J.p + a0, nullptr, cp, cp);
             }
-            if (carried) photon_pass(w->P[pc], cP(pc), 0, w->cap_p);
+            if (carried) photon_pass(w->P[pc], cP(pc), 0, cap_p);
             band_sort(ca, na);
             electron_pass();
             carried = true;
@@ -1542,7 +1622,17 @@ struct Runner {
     // they are empty); a negative value launches RUN_GENERATIONS generations
     // with no host check (graph capture) and leaves the count of undone
     // particles for finish().
+    // the device's error word: a queue that overflowed or a bounded wait that
+    // gave up leaves the tally incomplete
+    static int device_errors(uint32_t e) {
+        if (e & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport: particle queue overflow (tally incomplete)");
+        if (e & PSL_DEV_ERR_TIMEOUT)
+            return psl_fail(PSL_ETIMEOUT, "transport: a bounded device wait gave up (tally incomplete)");
+        return PSL_OK;
+    }
+
     int drain(int check_from) {
+        int rc_err = PSL_OK;
         if (!carried) return PSL_OK;
         const bool sync_gens = check_from >= 0;
         for (int gen = 0;; ++gen) {
@@ -1550,7 +1640,7 @@ struct Runner {
                 cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
                 cudaError_t e = cudaStreamSynchronize(st);
                 if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport: ") + cudaGetErrorString(e));
-                if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport: particle queue overflow");
+                if ((rc_err = device_errors(w->host[9]))) return rc_err;
                 if (w->host[pc ^ 1] == 0 && w->host[2 + (ec ^ 1)] == 0) break;
                 if (gen >= MAX_GEN) return psl_fail(PSL_EOVERFLOW, "transport: too many secondary generations");
             } else if (!sync_gens && gen >= RUN_GENERATIONS) {
@@ -1561,7 +1651,7 @@ struct Runner {
             pc ^= 1; ec ^= 1;
             cudaMemsetAsync(cP(pc ^ 1), 0, 4, st);
             cudaMemsetAsync(cE(ec ^ 1), 0, 4, st);
-            photon_pass(w->P[pc], cP(pc), 0, w->cap_p);
+            photon_pass(w->P[pc], cP(pc), 0, cap_p);
             band_sort(nullptr, 0);
             electron_pass();
         }
@@ -1580,7 +1670,8 @@ struct Runner {
         cudaMemcpyAsync(w->host, w->cnt, 16 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("transport: ") + cudaGetErrorString(e));
-        if (w->host[9] & PSL_DEV_ERR_QUEUE) return psl_fail(PSL_EOVERFLOW, "transport: particle queue overflow");
+        int rc_err = device_errors(w->host[9]);
+        if (rc_err) return rc_err;
         if (w->host[12]) return psl_fail(PSL_EOVERFLOW, "transport: secondaries left after the generation budget");
         return PSL_OK;
     }
@@ -1719,9 +1810,15 @@ extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const ps
     psl_physics_t P;
     psl_physics_default(&P);
     if (phys) P = *phys;
-    uint64_t key[8] = {(uint64_t)(uintptr_t)plan, (uint64_t)first, (uint64_t)n, (uint64_t)(uintptr_t)ph->rho,
-                       (uint64_t)(uintptr_t)ph->mat, ((uint64_t)P.flags << 32) | (uint64_t)tally->grid_mult,
-                       (uint64_t)tally->chunk_cap ^ ((uint64_t)tally->order << 60), (uint64_t)plan->seed};
+    const SrcTraceDev &T = tally->trace;
+    uint64_t key[11] = {(uint64_t)(uintptr_t)plan, (uint64_t)first, (uint64_t)n, (uint64_t)(uintptr_t)ph->rho,
+                        (uint64_t)(uintptr_t)ph->mat, ((uint64_t)P.flags << 32) | (uint64_t)tally->grid_mult,
+                        (uint64_t)tally->chunk_cap ^ ((uint64_t)tally->order << 60), (uint64_t)plan->seed,
+                        (uint64_t)T.first ^ ((uint64_t)T.n << 1), (uint64_t)(uintptr_t)T.entry ^ (uint64_t)(uintptr_t)T.use ^
+                            (uint64_t)(uintptr_t)T.rec ^ (uint64_t)(uintptr_t)T.status ^ (uint64_t)(uintptr_t)T.state ^
+                            (uint64_t)(uintptr_t)T.ptype,
+                        (uint64_t)psl_debug_flags() ^ ((uint64_t)psl_debug_queue_cap() << 8) ^
+                            ((uint64_t)psl_wait_polls(0) << 40)};
     // workspace and tables are set up outside the capture
     {
         Runner pre;

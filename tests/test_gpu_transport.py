@@ -95,6 +95,50 @@ def test_csda_range_and_track(T0, rho):
     assert abs(int(lg[2]) - n * np.float32(T0) * FP) < 1e-6 * n * T0 * FP
 
 
+@pytest.mark.parametrize("T0,rho", [(2.0, 1.0), (5.0, 1.85)])
+def test_csda_range_and_track_positron(T0, rho):
+    """Straight positron, no hard events: its own (Bhabha) range table; the
+    dose profile follows the oracle's, and the 2 m c^2 of the annihilation
+    at rest is deposited where it stops (secondaries local)."""
+    nz = 200
+    w = _column_workload(nz, 0.05, rho=np.full((nz, 1, 1), rho, np.float32))
+    dw = engine.upload(w)
+    n = 8
+    flags = capi.PHYS_NO_MSC | capi.PHYS_NO_HARD | capi.PHYS_LOCAL_SECONDARIES
+    t, lg = transport_particles(dw, *_pencil(n, 2, T0), seed=3, flags=flags)
+    to, lo, ho = oracle.transport(*_pencil(n, 2, T0), w.phantom, seed=3, flags=flags, per_history=True)
+    prof = t[:, 0, 0].astype(float)
+    assert np.abs(prof - to[:, 0, 0]).sum() < 1e-4 * prof.sum() + 4
+    e_all = n * (np.float32(T0) + 2 * np.float32(oracle.ME)) * FP
+    assert abs(int(lg[2]) - e_all) < 1e-6 * e_all
+
+
+@pytest.mark.parametrize("ptype", [1, 2])
+def test_hard_collision_counts_match_oracle(ptype):
+    """Hard Moller (electrons) and Bhabha (positrons) collisions of 3 MeV
+    particles crossing 0.5 mm of water on the same random streams: the
+    GPU's count (ledger slot 11) equals the oracle's up to the rare
+    histories a float32 rounding flips, and the two species differ."""
+    w = _column_workload(1, 0.05)
+    dw = engine.upload(w)
+    n = 400_000
+    phys_flags = capi.PHYS_NO_MSC | capi.PHYS_LOCAL_SECONDARIES
+    # W_cb above the energy: no hard bremsstrahlung
+    st = np.concatenate([np.tile([0.5, 0.5, 0.0, 0.0, 0.0, 1.0], (n, 1)), np.full((n, 1), 3.0), np.ones((n, 1))],
+                        1).astype(np.float32)
+    batch = capi.psl_batch_from_particles(torch.from_numpy(st).cuda(),
+                                          torch.full((n,), ptype, dtype=torch.int32).cuda(),
+                                          torch.arange(n, dtype=torch.int64).cuda(), 8)
+    tally = capi.psl_tally_create(dw.phantom, 1)
+    capi.transport_run(dw.phantom, capi.physics(phys_flags, wcb=10.0), batch, tally, 0)
+    _, lg = engine.raw_tallies(dw, tally, 1)
+    _, lo = oracle.transport(*_pencil(n, ptype, 3.0), w.phantom, seed=8, flags=phys_flags, wcb=10.0)
+    g, o = int(lg[11]), int(lo[oracle.L_HARD_COLL])
+    assert o > 5000
+    assert abs(g - o) <= 0.002 * o + 5, (g, o)
+    tally.close()
+
+
 def test_energy_ledger_heterogeneous_with_pairs():
     w = _column_workload(32, 0.5, nxy=32, vxy=0.5)
     w.phantom = inputs.slab_phantom(2, 32, 0.5)
