@@ -348,7 +348,9 @@ PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64
  * weight), 3 Compton, 4 photoelectric and 5 pair events, 6 electron steps,
  * 7 errors, 8 tally atomics issued by photon passes, 9 by electron passes,
  * 10 Woodcock (photon) steps, 11 hard Moller (e-) and Bhabha (e+) collisions.
- * The phantom must have fewer
+ * Slot 2 is the sum of the tally's counters: psl_tally_read and dose_readout
+ * take it from them (in the array of psl_tally_buffers it holds the value
+ * the last of those calls took).  The phantom must have fewer
  * than 2^31 voxels (PSL_EINVAL otherwise): transport indexes voxels in
  * 32 bits. */
 PSL_API int psl_tally_create(const psl_phantom_t *phantom, int32_t n_batches, psl_tally_t **out);
@@ -539,9 +541,11 @@ PSL_API int psl_atomic_peak(int64_t n_cells, int64_t n_updates, double *updates_
  *   PSL_DEBUG_LOOKBACK_STALL  a sort tile never sees its predecessors'
  *                             counts (every tile but the first gives up; the
  *                             sort's output is then wrong but in bounds);
- *   PSL_DEBUG_FEED_STALL      the second chunk a photon warp claims is never
- *                             copied, so its mbarrier never completes (no
- *                             copy is left in flight when the warp stops).
+ *   PSL_DEBUG_FEED_STALL      no chunk a photon warp claims into its second
+ *                             buffer is ever copied, so that buffer's
+ *                             mbarrier never completes (no copy is left in
+ *                             flight when the warp stops; a pass needs more
+ *                             photons than one chunk per warp for it).
  * queue_cap > 0 caps every particle queue of later transport calls at that
  * many particles, so that secondaries overflow it (PSL_EOVERFLOW, tally
  * incomplete).  Nothing here faults or hangs the device.  PSL_EINVAL for

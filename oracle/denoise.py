@@ -17,6 +17,12 @@ float64, with numpy array operations as the only primitives:
 * the network: a 4-level encoder-decoder (16/32/64/128 channels) with
   additive skips and a residual output, its mean-squared-error loss and
   backward pass, and the Adam update.
+
+The network is defined with BF16 activations (FP32 accumulation):
+forward() and loss_and_grads() take `bf16=True` to round every stored
+activation and activation gradient to BF16 (8 significant bits, round to
+nearest even) at the points where that definition stores them, in float64
+arithmetic otherwise; `bf16=False` is the exact float64 network.
 """
 from __future__ import annotations
 
@@ -90,6 +96,18 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even): the value is first
+    rounded to float32, whose upper 16 bits BF16 keeps."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _ident(x):
+    return x
+
+
 # ------------------------------------------------------------------ network --
 # Layers of the encoder-decoder: (name, C_in, C_out).  The input has two
 # channels (dose / scale, density) padded with zeros to 8.
@@ -111,32 +129,40 @@ def init_params(seed: int) -> dict:
     return p
 
 
-def forward(p: dict, x: np.ndarray, keep: bool = False):
+def forward(p: dict, x: np.ndarray, keep: bool = False, bf16: bool = False):
     """x [D,H,W,8] (channel 0 = scaled dose) -> predicted scaled dose [D,H,W]
-    (and the activations when keep)."""
+    (and the activations when keep).  bf16: every stored activation (layer
+    outputs after bias and ReLU, pooled and upsampled-plus-skip tensors) is
+    rounded to BF16; the output layer stays in full precision."""
+    q = round_bf16 if bf16 else _ident
     a = {}
-    h = relu(conv3d(x, p["e0a.w"], p["e0a.b"])); a["e0a"] = h
-    s0 = relu(conv3d(h, p["e0b.w"], p["e0b.b"])); a["e0b"] = s0
-    h = avgpool2(s0); a["p0"] = h
-    s1 = relu(conv3d(h, p["e1.w"], p["e1.b"])); a["e1"] = s1
-    h = avgpool2(s1); a["p1"] = h
-    s2 = relu(conv3d(h, p["e2.w"], p["e2.b"])); a["e2"] = s2
-    h = avgpool2(s2); a["p2"] = h
-    h = relu(conv3d(h, p["b3a.w"], p["b3a.b"])); a["b3a"] = h
-    h = relu(conv3d(h, p["b3b.w"], p["b3b.b"])); a["b3b"] = h
-    h = upsample2(h) + s2; a["u2"] = h
-    h = relu(conv3d(h, p["d2.w"], p["d2.b"])); a["d2"] = h
-    h = upsample2(h) + s1; a["u1"] = h
-    h = relu(conv3d(h, p["d1.w"], p["d1.b"])); a["d1"] = h
-    h = upsample2(h) + s0; a["u0"] = h
-    h = relu(conv3d(h, p["d0.w"], p["d0.b"])); a["d0"] = h
+    h = q(relu(conv3d(x, p["e0a.w"], p["e0a.b"]))); a["e0a"] = h
+    s0 = q(relu(conv3d(h, p["e0b.w"], p["e0b.b"]))); a["e0b"] = s0
+    h = q(avgpool2(s0)); a["p0"] = h
+    s1 = q(relu(conv3d(h, p["e1.w"], p["e1.b"]))); a["e1"] = s1
+    h = q(avgpool2(s1)); a["p1"] = h
+    s2 = q(relu(conv3d(h, p["e2.w"], p["e2.b"]))); a["e2"] = s2
+    h = q(avgpool2(s2)); a["p2"] = h
+    h = q(relu(conv3d(h, p["b3a.w"], p["b3a.b"]))); a["b3a"] = h
+    h = q(relu(conv3d(h, p["b3b.w"], p["b3b.b"]))); a["b3b"] = h
+    h = q(upsample2(h) + s2); a["u2"] = h
+    h = q(relu(conv3d(h, p["d2.w"], p["d2.b"]))); a["d2"] = h
+    h = q(upsample2(h) + s1); a["u1"] = h
+    h = q(relu(conv3d(h, p["d1.w"], p["d1.b"]))); a["d1"] = h
+    h = q(upsample2(h) + s0); a["u0"] = h
+    h = q(relu(conv3d(h, p["d0.w"], p["d0.b"]))); a["d0"] = h
     y = h @ p["out.w"] + p["out.b"][0] + x[..., 0]
     return (y, a) if keep else y
 
 
-def loss_and_grads(p: dict, x: np.ndarray, target: np.ndarray):
-    """Mean squared error over the voxels and its gradient for every parameter."""
-    y, a = forward(p, x, keep=True)
+def loss_and_grads(p: dict, x: np.ndarray, target: np.ndarray, bf16: bool = False):
+    """Mean squared error over the voxels and its gradient for every
+    parameter.  bf16: the forward pass as forward(bf16=True), and every
+    stored activation gradient (the output layer's, each layer's input
+    gradient, pooled and skip-summed gradients) rounded to BF16; parameter
+    gradients are accumulated in full precision."""
+    q = round_bf16 if bf16 else _ident
+    y, a = forward(p, x, keep=True, bf16=bf16)
     n = y.size
     r = y - target
     loss = float((r * r).mean())
@@ -144,30 +170,30 @@ def loss_and_grads(p: dict, x: np.ndarray, target: np.ndarray):
     g = {}
     g["out.w"] = (a["d0"].reshape(-1, 16).T @ gy.reshape(-1))
     g["out.b"] = np.array([gy.sum()])
-    gh = gy[..., None] * p["out.w"]
+    gh = q(gy[..., None] * p["out.w"] * (a["d0"] > 0))
 
     def conv_back(name, x_in, gh_out):
         gz = gh_out * (a[name] > 0)
         g[name + ".w"] = conv3d_dw(x_in, gz)
         g[name + ".b"] = gz.reshape(-1, gz.shape[-1]).sum(0)
-        return conv3d_dx(gz, p[name + ".w"])
+        return q(conv3d_dx(gz, p[name + ".w"]))
 
     gu0 = conv_back("d0", a["u0"], gh)
     gs0 = gu0.copy()
-    gd1 = upsample2_grad(gu0)
+    gd1 = q(upsample2_grad(gu0))
     gu1 = conv_back("d1", a["u1"], gd1)
     gs1 = gu1.copy()
-    gd2 = upsample2_grad(gu1)
+    gd2 = q(upsample2_grad(gu1))
     gu2 = conv_back("d2", a["u2"], gd2)
     gs2 = gu2.copy()
-    gb3b = upsample2_grad(gu2)
+    gb3b = q(upsample2_grad(gu2))
     gb3a = conv_back("b3b", a["b3a"], gb3b)
     gp2 = conv_back("b3a", a["p2"], gb3a)
-    gs2 = gs2 + avgpool2_grad(gp2)
+    gs2 = q(gs2 + avgpool2_grad(gp2))
     gp1 = conv_back("e2", a["p1"], gs2)
-    gs1 = gs1 + avgpool2_grad(gp1)
+    gs1 = q(gs1 + avgpool2_grad(gp1))
     gp0 = conv_back("e1", a["p0"], gs1)
-    gs0 = gs0 + avgpool2_grad(gp0)
+    gs0 = q(gs0 + avgpool2_grad(gp0))
     ge0a = conv_back("e0b", a["e0a"], gs0)
     gz = ge0a * (a["e0a"] > 0)
     g["e0a.w"] = conv3d_dw(x, gz)

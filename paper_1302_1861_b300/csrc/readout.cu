@@ -44,11 +44,25 @@ __global__ void __launch_bounds__(256) k_readout(const unsigned long long *t, in
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(dep, local);
 }
 
-__global__ void k_ledger_out(const unsigned long long *ledger, const unsigned long long *dep, double *out) {
+// ledger slot 2 (deposited) is the sum of the tally: set from the sum the
+// readout took (the transport kernels do not count it separately)
+__global__ void k_ledger_out(unsigned long long *ledger, const unsigned long long *dep, double *out) {
+    ledger[2] = dep[0];
+    if (!out) return;
     const double s = 1.0 / 4294967296.0;
     out[0] = (double)(long long)ledger[0] * s;
     out[1] = (double)(long long)ledger[1] * s;
     out[2] = (double)(long long)dep[0] * s;
+}
+
+// sum of every counter of the tally (two's complement, as the ledger keeps it)
+__global__ void __launch_bounds__(256) k_tally_sum(const unsigned long long *t, int64_t n, unsigned long long *out) {
+    unsigned long long local = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        local += t[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xFFFFFFFFu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(out, local);
 }
 
 }  // namespace
@@ -90,7 +104,14 @@ extern "C" int psl_tally_read(const psl_tally_t *t, int64_t *tallies, int64_t *l
     if (!t) return psl_fail(PSL_EINVAL, "psl_tally_read: null tally");
     cudaStream_t st = as_stream(stream_);
     if (tallies) PSL_CUDA(cudaMemcpyAsync(tallies, t->t, (size_t)t->n_batches * t->nvox * 8, cudaMemcpyDeviceToDevice, st));
-    if (ledger) PSL_CUDA(cudaMemcpyAsync(ledger, t->ledger, 12 * 8, cudaMemcpyDeviceToDevice, st));
+    if (ledger) {
+        // slot 2 (deposited) is the sum of the tally
+        PSL_CUDA(cudaMemsetAsync(t->ledger + 2, 0, 8, st));
+        const int64_t n = (int64_t)t->n_batches * t->nvox;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)psl_sm_count() * 8));
+        k_tally_sum<<<grid, 256, 0, st>>>(t->t, n, t->ledger + 2); PSL_NOTE_LAUNCH();
+        PSL_CUDA(cudaMemcpyAsync(ledger, t->ledger, 12 * 8, cudaMemcpyDeviceToDevice, st));
+    }
     return PSL_OK;
 }
 
@@ -155,7 +176,7 @@ extern "C" int dose_readout(const psl_tally_t *t, const psl_phantom_t *ph, doubl
     PSL_CUDA(cudaMemsetAsync(dep, 0, 8, st));
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((t->nvox + 255) / 256, (int64_t)psl_sm_count() * 8));
     { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_READOUT, st, &tk_); k_readout<<<grid, 256, 0, st>>>(t->t, t->nvox, t->n_batches, ph->rho, scale, dose, sigma, dep); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_READOUT, st, tk_); }
-    if (ledger) { k_ledger_out<<<1, 1, 0, st>>>(t->ledger, dep, ledger); PSL_NOTE_LAUNCH(); }
+    k_ledger_out<<<1, 1, 0, st>>>(t->ledger, dep, ledger); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());
     return PSL_OK;
 }

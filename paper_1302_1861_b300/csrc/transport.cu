@@ -73,11 +73,16 @@ struct Tables {
     float lnR0[2], inv_dlnR[2];  // grid of each species' inverse range table
 };
 
+// A kernel's ledger counts: the frequent ones (steps, tally atomics) in two
+// registers of every thread, the rare ones (escaped energy, interactions,
+// hard collisions) added to a block-shared copy of the ledger, so that the
+// transport kernels keep few registers for bookkeeping.  The deposited total
+// is not counted at all: it is the sum of the tally, taken when it is read.
 struct Acc {
-    unsigned long long dep, esc, emitted;                      // fixed-point energy
-    uint32_t compton, photo, pair, steps, atomics, wsteps;     // per-thread event counts
-    uint32_t hard;                                             // hard Moller / Bhabha collisions
+    unsigned long long *s;     // the block's ledger [NLEDGER] (shared memory)
+    uint32_t steps, atomics;
 };
+constexpr int NLEDGER = 12;
 
 struct Args {
     int nx, ny, nz;
@@ -241,14 +246,13 @@ __device__ __forceinline__ void deposit(const Args &A, Acc &acc, uint32_t iv, fl
     unsigned long long q = fixed_point(e, wt);
     if (!q) return;
     atomicAdd(&A.tally[(uint64_t)(root >> ROOT_SLICE_SHIFT) * (uint64_t)A.nvox + iv], q);
-    acc.dep += q;
     acc.atomics++;
     if (A.hist_dep) atomicAdd(&A.hist_dep[root & ROOT_INDEX_MASK], q);
 }
 
 __device__ __forceinline__ void escape(const Args &A, Acc &acc, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
-    acc.esc += q;
+    if (q) atomicAdd(&acc.s[1], q);
     if (A.hist_esc) atomicAdd(&A.hist_esc[root & ROOT_INDEX_MASK], q);
 }
 
@@ -350,31 +354,29 @@ __device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, 
     }
 }
 
-// ledger slots: 0 emitted, 1 escaped, 2 deposited (fixed point), 3 Compton,
-// 4 photoelectric, 5 pair, 6 electron steps, 7 errors, 8 tally atomics of
-// photon passes, 9 tally atomics of electron passes, 10 Woodcock steps,
-// 11 hard Moller / Bhabha collisions
-__device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int atomics_slot) {
-    unsigned long long v[10] = {a.dep, a.esc, a.compton, a.photo, a.pair, a.steps, a.atomics, a.wsteps, a.emitted,
-                                a.hard};
-    // (the 32-bit event counts widen here)
+// ledger slots: 0 emitted, 1 escaped, 2 deposited (fixed point; taken from
+// the tally when it is read), 3 Compton, 4 photoelectric, 5 pair, 6 electron
+// steps, 7 errors, 8 tally atomics of photon passes, 9 tally atomics of
+// electron passes, 10 Woodcock steps, 11 hard Moller / Bhabha collisions
+__device__ __forceinline__ void acc_init(unsigned long long *s) {
+    if (threadIdx.x < NLEDGER) s[threadIdx.x] = 0ull;
+}
+
+// End of a kernel: every thread's step and atomic counts into the block's
+// ledger (steps_slot, atomics_slot), then the block's ledger into the tally's.
+__device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int steps_slot, int atomics_slot) {
+    uint32_t v0 = a.steps, v1 = a.atomics;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(FULL, v0, o);
+        v1 += __shfl_xor_sync(FULL, v1, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (v[0]) atomicAdd(&A.ledger[2], v[0]);
-        if (v[1]) atomicAdd(&A.ledger[1], v[1]);
-        if (v[2]) atomicAdd(&A.ledger[3], v[2]);
-        if (v[3]) atomicAdd(&A.ledger[4], v[3]);
-        if (v[4]) atomicAdd(&A.ledger[5], v[4]);
-        if (v[5]) atomicAdd(&A.ledger[6], v[5]);
-        if (v[6]) atomicAdd(&A.ledger[atomics_slot], v[6]);
-        if (v[7]) atomicAdd(&A.ledger[10], v[7]);
-        if (v[8]) atomicAdd(&A.ledger[0], v[8]);
-        if (v[9]) atomicAdd(&A.ledger[11], v[9]);
+        if (v0) atomicAdd(&a.s[steps_slot], (unsigned long long)v0);
+        if (v1) atomicAdd(&a.s[atomics_slot], (unsigned long long)v1);
     }
+    __syncthreads();
+    if (threadIdx.x < NLEDGER && a.s[threadIdx.x]) atomicAdd(&A.ledger[threadIdx.x], a.s[threadIdx.x]);
 }
 
 // ------------------------------------------------------------ warp feed ---
@@ -419,7 +421,7 @@ struct Feed {
         }
         __syncwarp();
         set_cnt(0, claim(sm, 0, src, n, head));
-        // (stall: a failure-detection test; the second chunk's copy is never
+        // (stall: a failure-detection test; no copy into buffer 1 is ever
         // issued, so its mbarrier never completes and the wait runs out)
         set_cnt(1, claim(sm, 1, src, n, head, stall));
         if (cnt(0)) wait(sm, 0, err, polls);
@@ -460,7 +462,7 @@ struct Feed {
     // that got none finds the queue exhausted.
     __device__ __forceinline__ bool take(FeedSmem &sm, unsigned need, unsigned lt, bool mine, Particle &p,
                                          const Particle *src, uint32_t n, uint32_t *head, uint32_t *err,
-                                         uint32_t polls) {
+                                         uint32_t polls, bool stall) {
         const uint32_t k = __popc(need), rank = __popc(need & lt);
         const uint32_t c = cur(), nx = c ^ 1u, avail = cnt(c) - pos();
         if (k >= avail && cnt(nx)) wait(sm, nx, err, polls);
@@ -481,7 +483,7 @@ struct Feed {
             __syncwarp();                               // every lane has read it
             const uint32_t np = min(k - avail, cn);
             st = (st & ~((63u << 12) | (1u << 18))) | (np << 12) | (nx << 18);
-            set_cnt(c, cn ? claim(sm, c, src, n, head) : 0u);   // a short chunk means the queue is exhausted
+            set_cnt(c, cn ? claim(sm, c, src, n, head, stall && c == 1u) : 0u);   // a short chunk: queue exhausted
         } else {
             st += k << 12;
         }
@@ -528,7 +530,7 @@ __device__ __forceinline__ uint32_t photon_voxel(const Args &A, const Photon &g)
 }
 
 __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
-    acc.wsteps++;
+    acc.steps++;
     EventRng ev(g.draw);
     Rng &rng = ev.r;
     rng.align();                                                // Woodcock step: step, virtual, channel
@@ -563,7 +565,7 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
     rng.align();                                                // the interaction's draws
     const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
     if (g.chan == 0u) {                                           // Compton (Kahn's method)
-        acc.compton++;
+        atomicAdd(&acc.s[3], 1ull);
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         const float k = g.e * (1.0f / F_ME), ik = __frcp_rn(k);
         const float p_first = __fdividef(1.0f + 2.0f * k, 9.0f + 2.0f * k);
@@ -598,12 +600,12 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
         photon_energy(A, g);
         return true;
     } else if (g.chan == 1u) {                                    // photoelectric
-        acc.photo++;
+        atomicAdd(&acc.s[4], 1ull);
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         emit_charged(A, acc, rng, bh, 1, g.e, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
         return false;
     }
-    acc.pair++;                                                    // pair production
+    atomicAdd(&acc.s[5], 1ull);                                    // pair production
     if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
     const float avail = g.e - 2.0f * F_ME, eps = rng.next(A.rk, g.p0, g.p1);
     const float t1 = eps * avail, t2 = avail - t1;
@@ -616,12 +618,14 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
                                                 uint32_t cap, uint32_t *head) {
     __shared__ FeedSmem sm;
     __shared__ uint32_t bh[NBANDS];
+    __shared__ unsigned long long sled[NLEDGER];
     band_hist_init(bh);
+    acc_init(sled);
     __syncthreads();
     const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {sled, 0u, 0u};
     Photon g;
     Feed F;
     F.init(sm, src, n, head, A.err, A.wait_polls, (A.dbg & PSL_DEBUG_FEED_STALL) != 0);
@@ -631,7 +635,8 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
         if (need) {
             Particle p;
             const bool mine = !alive && !done;
-            const bool got = F.take(sm, need, lt, mine, p, src, n, head, A.err, A.wait_polls);
+            const bool got = F.take(sm, need, lt, mine, p, src, n, head, A.err, A.wait_polls,
+                                    (A.dbg & PSL_DEBUG_FEED_STALL) != 0);
             if (mine) {
                 if (!got) {
                     done = true;
@@ -659,7 +664,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
             real = r == G_REAL;
         }
     }
-    flush_acc(A, acc, 8);
+    flush_acc(A, acc, 10, 8);
     band_hist_flush(A, bh);
 }
 
@@ -865,7 +870,7 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
         const float r = rng.next(A.rk, s.p0, s.p1) * (sm + sb);
         if (sm + sb > 0.0f) {
             if (r < sm) {                                         // hard Moller (e-) or Bhabha (e+)
-                acc.hard++;
+                atomicAdd(&acc.s[11], 1ull);
                 const float eps = s.pos ? sample_bhabha(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err)
                                         : sample_moller(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
@@ -899,12 +904,14 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
     // electrons live for several steps and their queue reads hit L1, so
     // refills load directly (a staged feed measured 2 % slower here)
     __shared__ uint32_t bh[NBANDS];
+    __shared__ unsigned long long sled[NLEDGER];
     band_hist_init(bh);
+    acc_init(sled);
     __syncthreads();
     const uint32_t n = min(*n_ptr, cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {sled, 0u, 0u};
     Electron s;
     bool alive = false, done = false, hard = false;
     for (;;) {
@@ -948,7 +955,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
             hard = r == E_HARD;
         }
     }
-    flush_acc(A, acc, 9);
+    flush_acc(A, acc, 6, 9);
     band_hist_flush(A, bh);
 }
 
@@ -1003,8 +1010,10 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
                                                 const uint32_t *list, const uint32_t *list_off, SrcTraceDev T) {
     __shared__ PlanShared S;
     __shared__ uint32_t bh[NBANDS];
+    __shared__ unsigned long long sled[NLEDGER];
     plan_shared_load(P, S);
     band_hist_init(bh);
+    acc_init(sled);
     __syncthreads();
     const uint32_t cap = n;
     uint32_t lbase = 0;
@@ -1018,7 +1027,8 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
         if (left > n && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, PSL_DEV_ERR_QUEUE);
         n = min(n, left);
     }
-    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc acc = {sled, 0u, 0u};
+    unsigned long long emitted = 0, missed = 0;      // this thread's fixed-point energy
     const int lane = threadIdx.x & 31;
     // each warp takes runs of SRC_RUN consecutive histories, 32 at a time,
     // and each lane carries its (group, segment) to the next 32: consecutive
@@ -1091,8 +1101,8 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
             }
             if (o.status == PSL_SRC_TRANSPORT || o.status == PSL_SRC_MISS) {
                 const unsigned long long e = fixed_point(o.s[6], o.s[7]);
-                acc.emitted += e;
-                if (o.status == PSL_SRC_MISS) acc.esc += e;
+                emitted += e;
+                if (o.status == PSL_SRC_MISS) missed += e;
             }
             if (o.status == PSL_SRC_TRANSPORT) {
                 Particle c;
@@ -1111,7 +1121,16 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
             }
         }
     }
-    flush_acc(A, acc, 8);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        emitted += __shfl_xor_sync(FULL, emitted, o);
+        missed += __shfl_xor_sync(FULL, missed, o);
+    }
+    if (lane == 0) {
+        if (emitted) atomicAdd(&sled[0], emitted);
+        if (missed) atomicAdd(&sled[1], missed);
+    }
+    flush_acc(A, acc, 6, 8);
     band_hist_flush(A, bh);
 }
 

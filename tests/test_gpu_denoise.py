@@ -1,10 +1,20 @@
-"""GPU parity of the denoiser network against the float64 oracle.
+"""GPU parity of the denoiser network against the oracle, element by element.
 
-The GPU keeps activations and gradients in BF16 (8 significant bits) through
-nine convolution layers, so the bar is on whole tensors: the output within
-3 % of the oracle's in relative L2 norm, every parameter group's gradient
-within 10 % in relative L2 norm (cosine > 0.99), and one Adam step equal, to
-FP32 rounding, to the oracle's update computed from the GPU's own gradients.
+The network stores activations and activation gradients in BF16 (8
+significant bits) with FP32 accumulation; the oracle follows the same
+definition (oracle.denoise with bf16=True rounds at the same storage
+points) in float64 otherwise.  What is left between the two: the order of
+the FP32 sums (relative 1e-6) and, where that moves a value across a BF16
+rounding boundary, a one-ulp (2^-8 relative) flip that later layers carry.
+Bars, element by element (ulp = 2^-8):
+* forward output: every voxel within 2^-6 of the output's largest
+  magnitude, and 99.9 % within 4 ulps of its own value (+ 2^-10 of that
+  largest magnitude);
+* every parameter gradient: 99 % of the elements within 4 ulps of their own
+  value + 2^-8 of the group's largest magnitude, every element within 2^-4
+  of it;
+* the loss within 0.5 %, and one Adam step equal, to FP32 rounding, to the
+  oracle's update computed from the GPU's own gradients.
 """
 import numpy as np
 import pytest
@@ -63,10 +73,6 @@ def _oracle_input(dose, rho, scale):
     return x
 
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 def test_network_forward_backward_and_adam_match_the_oracle():
     n, scale = 16, 1.3
     p, dose, rho, target = _case(3, n)
@@ -83,19 +89,25 @@ def test_network_forward_backward_and_adam_match_the_oracle():
     out = torch.empty_like(dg)
     d.forward(dg, rg, n, n, n, scale, out)
     x = _oracle_input(dose, rho, scale)
-    y_ref = dn.forward(pq, x) * scale
-    assert _rel(out.cpu().numpy(), y_ref) < 0.03
+    y_ref = dn.forward(pq, x, bf16=True) * scale
+    y = out.cpu().numpy().astype(np.float64)
+    big = np.abs(y_ref).max()
+    err = np.abs(y - y_ref)
+    assert err.max() <= 2 ** -6 * big, err.max() / big
+    assert np.mean(err <= 4 * 2 ** -8 * np.abs(y_ref) + 2 ** -10 * big) >= 0.999
     # gradients of one sample
     loss = d.backward(dg, rg, tg, n, n, n, scale)
-    loss_ref, g_ref = dn.loss_and_grads(pq, x, target / scale)
-    assert abs(loss - loss_ref) <= 0.05 * loss_ref
+    loss_ref, g_ref = dn.loss_and_grads(pq, x, target / scale, bf16=True)
+    assert abs(loss - loss_ref) <= 0.005 * loss_ref, (loss, loss_ref)
     grad = torch.empty(npar, dtype=torch.float32, device="cuda")
     d.params(grad=grad)
     g = _unflatten(grad.cpu().numpy().astype(np.float64))
     for k in g_ref:
         a, b = g[k].reshape(-1), g_ref[k].reshape(-1)
-        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
-        assert _rel(a, b) < 0.10 and cos > 0.99, (k, _rel(a, b), cos)
+        gbig = np.abs(b).max()
+        e = np.abs(a - b)
+        frac = float(np.mean(e <= 4 * 2 ** -8 * np.abs(b) + 2 ** -8 * gbig))
+        assert frac >= 0.99 and e.max() <= 2 ** -4 * gbig, (k, frac, e.max() / gbig)
     # one Adam step = the oracle's update from the GPU's own gradients
     before = torch.empty(npar, dtype=torch.float32, device="cuda")
     d.params(get=before)

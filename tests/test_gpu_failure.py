@@ -52,7 +52,8 @@ def test_lookback_wait_gives_up_with_timeout():
 
 
 def test_photon_feed_wait_gives_up_with_timeout():
-    w = inputs.config1()
+    # enough photons for every warp of the pass to claim a second chunk
+    w = inputs.config1(n_histories=2_000_000)
     dw = engine.upload(w)
     store = capi.psl_build(dw.params, dw.records)
     plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)

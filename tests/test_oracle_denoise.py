@@ -107,3 +107,34 @@ def test_adam_first_step_moves_by_lr_against_the_gradient_sign():
     m, v = {}, {}
     dn.adam_step(p, g, m, v, 1, 0.01)
     assert np.allclose(p["a"], [1.0 - 0.01, -2.0 + 0.01, 0.5 - 0.01], atol=1e-6)
+
+
+def test_round_bf16_hand_values_and_ties():
+    """BF16 keeps 8 significant bits: the spacing above 1 is 2^-7; ties go
+    to the even neighbour."""
+    from oracle import denoise as dn
+    x = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 3 * 2 ** -9, 1 + 2 ** -9, -2.0 - 2 ** -6 - 2 ** -8,
+                  0.0, 3.5e38])
+    # the largest finite BF16 value is (2 - 2^-7) 2^127 = 3.39e38: 3.5e38 rounds to infinity
+    want = np.array([1.0, 1.0, 1 + 2 ** -6, 1 + 2 ** -7, 1.0, -2.0 - 2 ** -6, 0.0, np.inf])
+    got = dn.round_bf16(x)
+    assert np.array_equal(got, want)
+    assert dn.round_bf16(np.array([(2 - 2 ** -7) * 2.0 ** 127]))[0] == (2 - 2 ** -7) * 2.0 ** 127
+    r = np.random.default_rng(0).normal(0, 10, 10000)
+    q = dn.round_bf16(r)
+    assert np.all(np.abs(q - r) <= 2 ** -8 * np.abs(r))       # half a unit in the 8th bit
+    assert np.array_equal(dn.round_bf16(q), q)                # idempotent
+
+
+def test_bf16_network_stays_close_to_the_exact_one():
+    """The BF16 storage points move the output by a few units in the 8th
+    significant bit, not more (the same parameters, a 16^3 volume)."""
+    from oracle import denoise as dn
+    rng = np.random.default_rng(1)
+    p = dn.init_params(2)
+    p["out.w"] = rng.normal(0, 0.3, 16)
+    x = np.zeros((16, 16, 16, 8))
+    x[..., 0] = rng.random((16, 16, 16))
+    x[..., 1] = 1.0
+    y, yq = dn.forward(p, x), dn.forward(p, x, bf16=True)
+    assert 0 < np.abs(y - yq).max() <= 0.02 * np.abs(y).max()
