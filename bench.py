@@ -815,10 +815,20 @@ def imrt_run(capi, engine, inputs, torch, records=None):
     then capture once and time the replays."""
     w = inputs.config4(records=records)
     dw = engine.upload(w)
+    phys = capi.physics()
+    # PSL bin size first (the store is rebuilt per candidate), then the
+    # persistent grid and queue depth on the chosen store
+    cells = [0.5, 1.0, 2.0]
+    t0 = time.perf_counter()
+    cell, cell_secs = capi.psl_autotune_bins(dw.params, dw.records, dw.beams, w.sad, dw.phantom, phys,
+                                             w.n_histories, w.seed, w.n_batches, cells, 20_000_000)
+    t_bins = time.perf_counter() - t0
+    if cell != 1.0:
+        w.binning = inputs.make_binning(20.0, cell, 32, log_ebins=True)
+        dw = engine.upload(w, records=dw.rec_t)
     store = capi.psl_build(dw.params, dw.records)
     plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
     tally = capi.psl_tally_create(dw.phantom, w.n_batches)
-    phys = capi.physics()
     t0 = time.perf_counter()
     tuned_grid, tuned_depth = capi.psl_autotune(plan, dw.phantom, phys, tally, 20_000_000)
     t_tune = time.perf_counter() - t0
@@ -840,6 +850,18 @@ def imrt_run(capi, engine, inputs, torch, records=None):
     lg = torch.empty(3, dtype=torch.float64, device="cuda")
     n_entries, n_total, _ = plan.info()
     capi.dose_readout(tally, dw.phantom, engine.normalisation(plan, w.n_histories), dose, sigma, lg)
+    # the whole per-plan sequence (tally reset, run, readout) as one graph launch
+    norm = engine.normalisation(plan, w.n_histories)
+    capi.psl_plan_replay(plan, dw.phantom, phys, tally, 0, w.n_histories, norm, dose, sigma, lg)   # capture
+    t_whole = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        capi.psl_plan_replay(plan, dw.phantom, phys, tally, 0, w.n_histories, norm, dose, sigma, lg)
+        e1.record()
+        torch.cuda.synchronize()
+        t_whole.append(e0.elapsed_time(e1) / 1e3)
     d = dose.view(nz, ny, nx).cpu().numpy()
     sg = sigma.view(nz, ny, nx).cpu().numpy()
     ic = ((np.array(w.beams[0].iso) - np.array(w.phantom.origin)) / np.array(w.phantom.voxel)).astype(int)[::-1]
@@ -856,7 +878,11 @@ def imrt_run(capi, engine, inputs, torch, records=None):
     return {"workload": w.name, "segments": len(w.beams), "psl_entries": n_entries, "histories": w.n_histories,
             "seconds_per_plan": t, "histories_per_s": rate, "launch": "one CUDA graph (psl_run, use_graph=1)",
             "autotuned": {"blocks_per_sm": tuned_grid, "queue_depth": tuned_depth, "probe_histories": 20_000_000,
-                          "seconds": t_tune},
+                          "seconds": t_tune, "psl_cell_cm": cell,
+                          "psl_cell_estimates_s": dict(zip(map(str, cells), map(float, cell_secs))),
+                          "psl_cell_seconds": t_bins},
+            "whole_plan_graph_s": float(np.mean(t_whole)),
+            "whole_plan_graph": "psl_plan_replay: tally reset + all segments + dose readout in one CUDA graph launch",
             "isocentre_rel_sigma": rel, "time_to_1pct_s": n1 / rate, "time_to_1pct_s_kind": "extrapolated",
             "time_to_1pct_measured": t1,
             "energy_balance": float((lgh[1] + lgh[2] - lgh[0]) / lgh[0])}

@@ -478,6 +478,35 @@ PSL_API int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *phantom, c
                          psl_tally_t *tally, int64_t n_probe, int32_t *blocks_per_sm, int64_t *queue_depth,
                          void *stream);
 
+/* Sec. 2.3.3 and 2.5: the whole dose computation of a plan that is run
+ * again and again (a service recomputing one plan, a denoiser's training
+ * runs) as one CUDA graph launch: the tally is cleared, histories
+ * [first, first+n) of the plan are run as psl_run runs them, and the dose is
+ * read out with dose_readout's arguments (norm, dose, sigma, ledger: device,
+ * NULL to skip).  The graph is recorded by the first call for this plan,
+ * range, phantom, settings and outputs (outside any other capture) and kept
+ * in the tally; later calls replay it in one launch.  Synchronises stream;
+ * errors as psl_run. */
+PSL_API int psl_plan_replay(const psl_plan_t *plan, const psl_phantom_t *phantom, const psl_physics_t *physics,
+                            psl_tally_t *tally, int64_t first, int64_t n, double norm, double *dose, double *sigma,
+                            double *ledger, void *stream);
+
+/* Sec. 2.3.2, 2.3.3 ("the size of the PSL bins ... benchmarking"): autotune
+ * the PSL position-bin size for a plan.  For every candidate cell size
+ * cell_cm[k] (> 0, cm) the store is built from the records with square
+ * cells over the extent of params' x and y edges (rounded to a whole number
+ * of cells; energy bins as given), the plan of n_histories created, and
+ * n_probe of its histories run on a tally of n_batches (once to warm up,
+ * once timed).  plan_seconds[k] (host, may be NULL) receives the estimate
+ * plan creation + probe time x n_histories / n_probe; *best_cell (host, may
+ * be NULL) the fastest size.  The dose does not depend on the cell size
+ * (every selected PSL's records are sampled in proportion), only the time
+ * does.  Synchronises stream. */
+PSL_API int psl_autotune_bins(const psl_params_t *params, const psl_records_t *records, const psl_beam_t *beams,
+                              int32_t n_beams, float sad, const psl_phantom_t *phantom, const psl_physics_t *physics,
+                              int64_t n_histories, uint64_t seed, int32_t n_batches, const float *cell_cm,
+                              int32_t n_cells, int64_t n_probe, float *best_cell, double *plan_seconds, void *stream);
+
 /* Sec. 2.3.3 and 2.5.  dose[v] = norm * sum_b T_bv * 2^-32 MeV * 1.602176634e-13
  * J/MeV / (rho_v * voxel volume * 1e-3 kg), sigma[v] = the standard error of
  * the mean of the N_b batch estimates, ledger[0..2] = emitted, escaped,

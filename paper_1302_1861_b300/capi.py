@@ -32,7 +32,8 @@ EXPORTS = (
     "psl_denoiser_create", "psl_denoiser_destroy", "psl_denoiser_params", "psl_denoiser_forward",
     "psl_denoiser_backward", "psl_denoiser_step", "psl_gamma", "psl_conv3d_form", "psl_tally_set_order",
     "psl_kth_smallest", "psl_tally_buffers", "psl_tally_info", "psl_tally_set_queue_depth",
-    "psl_dose_normalisation", "psl_tally_trace_source", "psl_debug_waits",
+    "psl_dose_normalisation", "psl_tally_trace_source", "psl_debug_waits", "psl_plan_replay",
+    "psl_autotune_bins",
 )
 METHOD_PATIENT_DEPENDENT, METHOD_JAW_MODEL = 1, 2
 SLICE_BY_HISTORY, MAX_BATCHES = -1, 1024
@@ -149,6 +150,8 @@ def lib():
             "psl_dose_normalisation": [vp, i64, i64, f64, vp],
             "psl_tally_trace_source": [vp, i64, i64, vp, vp, vp, vp, vp, vp],
             "psl_debug_waits": [i64, u32, i64],
+            "psl_plan_replay": [vp, vp, vp, vp, i64, i64, f64, vp, vp, vp, vp],
+            "psl_autotune_bins": [vp, vp, vp, i32, f32, vp, vp, i64, u64, i32, vp, i32, i64, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -519,6 +522,27 @@ def psl_run(plan: Plan, phantom: Phantom, phys: Physics, tally: Tally, first: in
             stream=None):
     check(lib().psl_run(plan.h, ctypes.byref(phantom), ctypes.byref(phys), tally.h, int(first), int(n),
                         1 if use_graph else 0, stream_ptr(stream)))
+
+
+def psl_plan_replay(plan: Plan, phantom: Phantom, phys: Physics, tally: Tally, first: int, n: int, norm: float,
+                    dose=None, sigma=None, ledger=None, stream=None):
+    """Tally reset + psl_run + dose_readout recorded once as a CUDA graph, then replayed."""
+    check(lib().psl_plan_replay(plan.h, ctypes.byref(phantom), ctypes.byref(phys), tally.h, int(first), int(n),
+                                float(norm), ptr(dose), ptr(sigma), ptr(ledger), stream_ptr(stream)))
+
+
+def psl_autotune_bins(params: Params, records: Records, beams: Sequence[Beam], sad: float, phantom: Phantom,
+                      phys: Physics, n_histories: int, seed: int, n_batches: int, cells, n_probe: int, stream=None):
+    """PSL position-bin size autotuner: returns (best cell size, estimated seconds per candidate)."""
+    arr = (Beam * len(beams))(*beams)
+    c = np.ascontiguousarray(cells, np.float32)
+    out = np.zeros(len(c))
+    best = f32()
+    check(lib().psl_autotune_bins(ctypes.byref(params), ctypes.byref(records), arr, len(beams), float(sad),
+                                  ctypes.byref(phantom), ctypes.byref(phys), int(n_histories), int(seed),
+                                  int(n_batches), c.ctypes.data, len(c), int(n_probe), ctypes.byref(best),
+                                  out.ctypes.data, stream_ptr(stream)))
+    return best.value, out
 
 
 def psl_autotune(plan: Plan, phantom: Phantom, phys: Physics, tally: Tally, n_probe: int, stream=None):

@@ -175,7 +175,11 @@ extern "C" int dose_readout(const psl_tally_t *t, const psl_phantom_t *ph, doubl
     unsigned long long *dep = t->ledger + 12;         // scratch slot for the deposited sum
     PSL_CUDA(cudaMemsetAsync(dep, 0, 8, st));
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>((t->nvox + 255) / 256, (int64_t)psl_sm_count() * 8));
-    { void *tk_ = nullptr; if (psl_timer_on()) psl_timer_begin(PK_READOUT, st, &tk_); k_readout<<<grid, 256, 0, st>>>(t->t, t->nvox, t->n_batches, ph->rho, scale, dose, sigma, dep); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_READOUT, st, tk_); }
+    // (no timer events inside a stream capture: psl_plan_replay records this call into its graph)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    const bool timed = psl_timer_on() && cap == cudaStreamCaptureStatusNone;
+    { void *tk_ = nullptr; if (timed) psl_timer_begin(PK_READOUT, st, &tk_); k_readout<<<grid, 256, 0, st>>>(t->t, t->nvox, t->n_batches, ph->rho, scale, dose, sigma, dep); PSL_NOTE_LAUNCH(); if (tk_) psl_timer_end(PK_READOUT, st, tk_); }
     k_ledger_out<<<1, 1, 0, st>>>(t->ledger, dep, ledger); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());
     return PSL_OK;

@@ -58,6 +58,9 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #ifndef PSL_E_DEFER
 #define PSL_E_DEFER 4                  // lanes with a pending hard event before a warp runs them
 #endif
+#ifndef PSL_DEP_COMBINE
+#define PSL_DEP_COMBINE 0              // 1: an electron sums its consecutive deposits into one voxel in
+#endif                                 //    registers and adds them with one atomic when it leaves the voxel
 #ifndef PSL_TRANSPORT_MIN_BLOCKS
 #define PSL_TRANSPORT_MIN_BLOCKS 4     // resident 256-thread blocks per SM (register cap 64)
 #endif
@@ -73,16 +76,18 @@ struct Tables {
     float lnR0[2], inv_dlnR[2];  // grid of each species' inverse range table
 };
 
-// A kernel's ledger counts: the frequent ones (steps, tally atomics) in two
-// registers of every thread, the rare ones (escaped energy, interactions,
-// hard collisions) added to a block-shared copy of the ledger, so that the
-// transport kernels keep few registers for bookkeeping.  The deposited total
-// is not counted at all: it is the sum of the tally, taken when it is read.
+// A thread's ledger counts, in few registers: steps and tally atomics, the
+// escaped energy, and the event counts packed 21 bits each into one word
+// (photon kernel: Compton, photoelectric, pair; electron kernel: hard
+// collisions in the first field); a thread handles far fewer than 2^21
+// events of a kind in one launch.  The deposited total is not counted: it is
+// the sum of the tally, taken when the tally is read.
 struct Acc {
-    unsigned long long *s;     // the block's ledger [NLEDGER] (shared memory)
     uint32_t steps, atomics;
+    unsigned long long esc, ev;
 };
 constexpr int NLEDGER = 12;
+constexpr unsigned long long EV_COMPTON = 1ull, EV_PHOTO = 1ull << 21, EV_PAIR = 1ull << 42, EV_HARD = 1ull;
 
 struct Args {
     int nx, ny, nz;
@@ -252,7 +257,7 @@ __device__ __forceinline__ void deposit(const Args &A, Acc &acc, uint32_t iv, fl
 
 __device__ __forceinline__ void escape(const Args &A, Acc &acc, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
-    if (q) atomicAdd(&acc.s[1], q);
+    acc.esc += q;
     if (A.hist_esc) atomicAdd(&A.hist_esc[root & ROOT_INDEX_MASK], q);
 }
 
@@ -362,21 +367,30 @@ __device__ __forceinline__ void acc_init(unsigned long long *s) {
     if (threadIdx.x < NLEDGER) s[threadIdx.x] = 0ull;
 }
 
-// End of a kernel: every thread's step and atomic counts into the block's
-// ledger (steps_slot, atomics_slot), then the block's ledger into the tally's.
-__device__ __forceinline__ void flush_acc(const Args &A, Acc &a, int steps_slot, int atomics_slot) {
-    uint32_t v0 = a.steps, v1 = a.atomics;
+// End of a kernel: every thread's counts into the block's ledger s (shared
+// memory; steps, tally atomics and the packed events into their slots: ev_slot
+// holds the first packed field's slot, or -1), then the block's ledger into
+// the tally's.
+__device__ __forceinline__ void flush_acc(const Args &A, const Acc &a, unsigned long long *s, int steps_slot,
+                                          int atomics_slot, int ev_slot) {
+    unsigned long long v[6] = {a.steps, a.atomics, a.esc, a.ev & 0x1FFFFFull, (a.ev >> 21) & 0x1FFFFFull, a.ev >> 42};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v0 += __shfl_xor_sync(FULL, v0, o);
-        v1 += __shfl_xor_sync(FULL, v1, o);
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (v0) atomicAdd(&a.s[steps_slot], (unsigned long long)v0);
-        if (v1) atomicAdd(&a.s[atomics_slot], (unsigned long long)v1);
+        if (v[0]) atomicAdd(&s[steps_slot], v[0]);
+        if (v[1]) atomicAdd(&s[atomics_slot], v[1]);
+        if (v[2]) atomicAdd(&s[1], v[2]);
+        if (ev_slot >= 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (v[3 + k] && ev_slot + k < NLEDGER) atomicAdd(&s[ev_slot + k], v[3 + k]);
+        }
     }
     __syncthreads();
-    if (threadIdx.x < NLEDGER && a.s[threadIdx.x]) atomicAdd(&A.ledger[threadIdx.x], a.s[threadIdx.x]);
+    if (threadIdx.x < NLEDGER && s[threadIdx.x]) atomicAdd(&A.ledger[threadIdx.x], s[threadIdx.x]);
 }
 
 // ------------------------------------------------------------ warp feed ---
@@ -565,7 +579,7 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
     rng.align();                                                // the interaction's draws
     const bool first = A.flags & PSL_PHYS_FIRST_INTERACTION;
     if (g.chan == 0u) {                                           // Compton (Kahn's method)
-        atomicAdd(&acc.s[3], 1ull);
+        acc.ev += EV_COMPTON;
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         const float k = g.e * (1.0f / F_ME), ik = __frcp_rn(k);
         const float p_first = __fdividef(1.0f + 2.0f * k, 9.0f + 2.0f * k);
@@ -600,12 +614,12 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
         photon_energy(A, g);
         return true;
     } else if (g.chan == 1u) {                                    // photoelectric
-        atomicAdd(&acc.s[4], 1ull);
+        acc.ev += EV_PHOTO;
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
         emit_charged(A, acc, rng, bh, 1, g.e, g.x, g.y, g.z, g.u, g.v, g.w, g.wt, iv, g.p0, g.p1, g.nchild, g.root);
         return false;
     }
-    atomicAdd(&acc.s[5], 1ull);                                    // pair production
+    acc.ev += EV_PAIR;                                             // pair production
     if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
     const float avail = g.e - 2.0f * F_ME, eps = rng.next(A.rk, g.p0, g.p1);
     const float t1 = eps * avail, t2 = avail - t1;
@@ -625,7 +639,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
     const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {sled, 0u, 0u};
+    Acc acc = {0u, 0u, 0ull, 0ull};
     Photon g;
     Feed F;
     F.init(sm, src, n, head, A.err, A.wait_polls, (A.dbg & PSL_DEBUG_FEED_STALL) != 0);
@@ -664,7 +678,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
             real = r == G_REAL;
         }
     }
-    flush_acc(A, acc, 10, 8);
+    flush_acc(A, acc, sled, 10, 8, 3);
     band_hist_flush(A, bh);
 }
 
@@ -677,7 +691,42 @@ struct Electron {
     int steps;
     bool pos;
     uint32_t draw;             // draws taken from the particle's Philox stream
+#if PSL_DEP_COMBINE
+    uint32_t piv;              // voxel of the deposits summed in pq (not yet added to the tally)
+    unsigned long long pq;
+#endif
 };
+
+// The per-step deposit of an electron.  With PSL_DEP_COMBINE the deposits
+// of consecutive steps in one voxel are summed in registers (the integer
+// sum is the same) and added with one atomic when the voxel changes or the
+// electron ends (electron_flush).
+__device__ __forceinline__ void electron_deposit(const Args &A, Acc &acc, Electron &s, uint32_t iv, float e) {
+#if PSL_DEP_COMBINE
+    const unsigned long long q = fixed_point(e, s.wt);
+    if (!q) return;
+    if (A.hist_dep) atomicAdd(&A.hist_dep[s.root & ROOT_INDEX_MASK], q);
+    if (iv == s.piv) { s.pq += q; return; }
+    if (s.pq) {
+        atomicAdd(&A.tally[(uint64_t)(s.root >> ROOT_SLICE_SHIFT) * (uint64_t)A.nvox + s.piv], s.pq);
+        acc.atomics++;
+    }
+    s.piv = iv;
+    s.pq = q;
+#else
+    deposit(A, acc, iv, e, s.wt, s.root);
+#endif
+}
+
+__device__ __forceinline__ void electron_flush(const Args &A, Acc &acc, Electron &s) {
+#if PSL_DEP_COMBINE
+    if (s.pq) {
+        atomicAdd(&A.tally[(uint64_t)(s.root >> ROOT_SLICE_SHIFT) * (uint64_t)A.nvox + s.piv], s.pq);
+        acc.atomics++;
+        s.pq = 0;
+    }
+#endif
+}
 
 __device__ __forceinline__ float highland(float T, float s, float rho) {
     const float t = s * rho * (1.0f / 36.08f);
@@ -821,7 +870,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
         if (which == 2) { tend = tlim; rend = rlim; }
         else { rend = s.r - rho * step; tend = fmaxf(energy_of_range(A.tab, rend, s.pos), tlim); }
         const float th0 = highland(s.t, step, rho);
-        deposit(A, acc, iv, s.t - tend, s.wt, s.root);
+        electron_deposit(A, acc, s, iv, s.t - tend);
         s.t = tend;
         s.r = rend;
         s.x += step * s.u; s.y += step * s.v; s.z += step * s.w;
@@ -841,6 +890,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
             else if (axis == 1) { s.y = (float)(cross > 0 ? s.iy + 1 : s.iy) * A.vy; s.iy += cross; out = s.iy < 0 || s.iy >= A.ny; }
             else { s.z = (float)(cross > 0 ? s.iz + 1 : s.iz) * A.vz; s.iz += cross; out = s.iz < 0 || s.iz >= A.nz; }
             if (out) {
+                electron_flush(A, acc, s);
                 escape(A, acc, s.t + (s.pos ? 2.0f * F_ME : 0.0f), s.wt, s.root);
                 return E_END;
             }
@@ -850,6 +900,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
         iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
     }                                                         // the step's draws are committed here
     if (s.steps > MAX_E_STEPS) atomicOr(A.err, PSL_DEV_ERR_STEPS);
+    electron_flush(A, acc, s);
     electron_end(A, acc, s, iv);
     return E_END;
 }
@@ -870,7 +921,7 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
         const float r = rng.next(A.rk, s.p0, s.p1) * (sm + sb);
         if (sm + sb > 0.0f) {
             if (r < sm) {                                         // hard Moller (e-) or Bhabha (e+)
-                atomicAdd(&acc.s[11], 1ull);
+                acc.ev += EV_HARD;
                 const float eps = s.pos ? sample_bhabha(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err)
                                         : sample_moller(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
@@ -911,7 +962,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
     const uint32_t n = min(*n_ptr, cap);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {sled, 0u, 0u};
+    Acc acc = {0u, 0u, 0ull, 0ull};
     Electron s;
     bool alive = false, done = false, hard = false;
     for (;;) {
@@ -940,6 +991,9 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     s.iy = min(max((int)floorf(s.y * A.ivy), 0), A.ny - 1);
                     s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
                     s.draw = 0;
+#if PSL_DEP_COMBINE
+                    s.piv = 0xFFFFFFFFu; s.pq = 0ull;
+#endif
                     s.nlam = -1.0f;                               // drawn at the first step
                     s.r = range_of(A.tab, s.t, s.pos ? NT : 0);
                     alive = true;
@@ -955,7 +1009,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
             hard = r == E_HARD;
         }
     }
-    flush_acc(A, acc, 6, 9);
+    flush_acc(A, acc, sled, 6, 9, 11);
     band_hist_flush(A, bh);
 }
 
@@ -1027,7 +1081,7 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
         if (left > n && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, PSL_DEV_ERR_QUEUE);
         n = min(n, left);
     }
-    Acc acc = {sled, 0u, 0u};
+    Acc acc = {0u, 0u, 0ull, 0ull};
     unsigned long long emitted = 0, missed = 0;      // this thread's fixed-point energy
     const int lane = threadIdx.x & 31;
     // each warp takes runs of SRC_RUN consecutive histories, 32 at a time,
@@ -1130,7 +1184,7 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
         if (emitted) atomicAdd(&sled[0], emitted);
         if (missed) atomicAdd(&sled[1], missed);
     }
-    flush_acc(A, acc, 6, 8);
+    flush_acc(A, acc, sled, 6, 8, -1);
     band_hist_flush(A, bh);
 }
 
@@ -1273,11 +1327,15 @@ struct Workspace {
     // cached CUDA graph of one psl_run call
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_key[11] = {0};
+    // cached CUDA graph of one psl_plan_replay call (reset, run, readout)
+    cudaGraphExec_t plan_graph = nullptr;
+    uint64_t plan_key[16] = {0};
 };
 
 void workspace_free(Workspace *w) {
     if (!w) return;
     if (w->graph) cudaGraphExecDestroy(w->graph);
+    if (w->plan_graph) cudaGraphExecDestroy(w->plan_graph);
     for (int k = 0; k < 2; ++k) { if (w->P[k]) cudaFree(w->P[k]); if (w->E[k]) cudaFree(w->E[k]); }
     if (w->S) cudaFree(w->S);
     if (w->Q) cudaFree(w->Q);
@@ -1324,6 +1382,8 @@ void workspace_release(Workspace *w) {
     if (cur != w->device) cudaSetDevice(cur);
     if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }
     std::memset(w->graph_key, 0, sizeof(w->graph_key));
+    if (w->plan_graph) { cudaGraphExecDestroy(w->plan_graph); w->plan_graph = nullptr; }
+    std::memset(w->plan_key, 0, sizeof(w->plan_key));
     Workspace *drop = w;
     {
         std::lock_guard<std::mutex> lk(g_ws_mu);
@@ -1813,31 +1873,51 @@ static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_p
     return R.drain(check);
 }
 
-extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
-                       int64_t first, int64_t n, int32_t use_graph, void *stream_) {
-    int rc = check_transport_args(ph, tally);
-    if (rc) return rc;
-    if (!plan || first < 0 || n <= 0 || first + n > plan->n_histories)
-        return psl_fail(PSL_EINVAL, "psl_run: bad plan or history range");
-    if (plan->n_groups > 1024) return psl_fail(PSL_EINVAL, "psl_run: too many energy divisions");
-    cudaStream_t st = as_stream(stream_);
-    Runner R;
-    if (!use_graph) {
-        if ((rc = run_body(plan, ph, phys, tally, first, n, st, false, R))) return rc;
-        return R.finish();
-    }
+static inline uint32_t __float_as_uint_host(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+// Key of a captured graph: everything the recorded launches depend on.
+static void run_key(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, const psl_tally_t *tally,
+                    int64_t first, int64_t n, uint64_t key[11]) {
     psl_physics_t P;
     psl_physics_default(&P);
     if (phys) P = *phys;
     const SrcTraceDev &T = tally->trace;
-    uint64_t key[11] = {(uint64_t)(uintptr_t)plan, (uint64_t)first, (uint64_t)n, (uint64_t)(uintptr_t)ph->rho,
-                        (uint64_t)(uintptr_t)ph->mat, ((uint64_t)P.flags << 32) | (uint64_t)tally->grid_mult,
-                        (uint64_t)tally->chunk_cap ^ ((uint64_t)tally->order << 60), (uint64_t)plan->seed,
-                        (uint64_t)T.first ^ ((uint64_t)T.n << 1), (uint64_t)(uintptr_t)T.entry ^ (uint64_t)(uintptr_t)T.use ^
-                            (uint64_t)(uintptr_t)T.rec ^ (uint64_t)(uintptr_t)T.status ^ (uint64_t)(uintptr_t)T.state ^
-                            (uint64_t)(uintptr_t)T.ptype,
-                        (uint64_t)psl_debug_flags() ^ ((uint64_t)psl_debug_queue_cap() << 8) ^
-                            ((uint64_t)psl_wait_polls(0) << 40)};
+    const uint64_t k[11] = {(uint64_t)(uintptr_t)plan, (uint64_t)first, (uint64_t)n, (uint64_t)(uintptr_t)ph->rho,
+                            (uint64_t)(uintptr_t)ph->mat, ((uint64_t)P.flags << 32) | (uint64_t)tally->grid_mult,
+                            (uint64_t)tally->chunk_cap ^ ((uint64_t)tally->order << 60), (uint64_t)plan->seed,
+                            (uint64_t)T.first ^ ((uint64_t)T.n << 1), (uint64_t)(uintptr_t)T.entry ^ (uint64_t)(uintptr_t)T.use ^
+                                (uint64_t)(uintptr_t)T.rec ^ (uint64_t)(uintptr_t)T.status ^ (uint64_t)(uintptr_t)T.state ^
+                                (uint64_t)(uintptr_t)T.ptype,
+                            (uint64_t)psl_debug_flags() ^ ((uint64_t)psl_debug_queue_cap() << 8) ^
+                                ((uint64_t)psl_wait_polls(0) << 40) ^ ((uint64_t)__float_as_uint_host(P.wcc) << 20) ^
+                                (uint64_t)__float_as_uint_host(P.photon_cut) ^ ((uint64_t)__float_as_uint_host(P.electron_cut) << 32) ^
+                                ((uint64_t)__float_as_uint_host(P.wcb) << 12)};
+    memcpy(key, k, sizeof(k));
+}
+
+// The readout a psl_plan_replay graph ends with.
+struct ReadoutArgs {
+    double norm;
+    double *dose, *sigma, *ledger;
+};
+
+// Record (once per key) and replay a graph of psl_run's body; with `ro`,
+// the graph also resets the tally first and reads the dose out last.
+static int graph_run(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
+                     int64_t first, int64_t n, const ReadoutArgs *ro, cudaStream_t st) {
+    int rc;
+    uint64_t key[16] = {0};
+    run_key(plan, ph, phys, tally, first, n, key);
+    if (ro) {
+        uint64_t nb;
+        memcpy(&nb, &ro->norm, 8);
+        key[11] = nb; key[12] = (uint64_t)(uintptr_t)ro->dose; key[13] = (uint64_t)(uintptr_t)ro->sigma;
+        key[14] = (uint64_t)(uintptr_t)ro->ledger; key[15] = (uint64_t)(uintptr_t)ph->rho;
+    }
     // workspace and tables are set up outside the capture
     {
         Runner pre;
@@ -1847,29 +1927,66 @@ extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const ps
         PSL_CUDA(cudaStreamSynchronize(st));
     }
     Workspace *w = tally->ws;
-    if (!w->graph || memcmp(w->graph_key, key, sizeof(key)) != 0) {
-        if (w->graph) { cudaGraphExecDestroy(w->graph); w->graph = nullptr; }
+    cudaGraphExec_t &gx = ro ? w->plan_graph : w->graph;
+    uint64_t *gk = ro ? w->plan_key : w->graph_key;
+    const size_t kbytes = ro ? sizeof(w->plan_key) : sizeof(w->graph_key);
+    if (!gx || memcmp(gk, key, kbytes) != 0) {
+        if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
         cudaStream_t cs;
         PSL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             Runner C;
-            rc = run_body(plan, ph, phys, tally, first, n, cs, true, C);
+            rc = ro ? psl_tally_reset(tally, cs) : PSL_OK;
+            if (!rc) rc = run_body(plan, ph, phys, tally, first, n, cs, true, C);
+            if (!rc && ro) rc = dose_readout(tally, ph, ro->norm, ro->dose, ro->sigma, ro->ledger, cs);
             e = cudaStreamEndCapture(cs, &g);
         }
         cudaStreamDestroy(cs);
         if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-        if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("psl_run: capture: ") + cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&w->graph, g, 0);
+        if (e != cudaSuccess) return psl_fail(PSL_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&gx, g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) { w->graph = nullptr; return psl_fail(PSL_ECUDA, std::string("psl_run: instantiate: ") + cudaGetErrorString(e)); }
-        memcpy(w->graph_key, key, sizeof(key));
+        if (e != cudaSuccess) { gx = nullptr; return psl_fail(PSL_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
+        memcpy(gk, key, kbytes);
     }
-    PSL_CUDA(cudaGraphLaunch(w->graph, st));
+    PSL_CUDA(cudaGraphLaunch(gx, st));
     PSL_NOTE_LAUNCH();
+    Runner R;
     R.st = st; R.w = w; R.tally = tally;
     return R.finish();
+}
+
+static int check_run_args(const psl_plan_t *plan, const psl_phantom_t *ph, psl_tally_t *tally, int64_t first,
+                          int64_t n, const char *who) {
+    int rc = check_transport_args(ph, tally);
+    if (rc) return rc;
+    if (!plan || first < 0 || n <= 0 || first + n > plan->n_histories)
+        return psl_fail(PSL_EINVAL, std::string(who) + ": bad plan or history range");
+    if (plan->n_groups > 1024) return psl_fail(PSL_EINVAL, std::string(who) + ": too many energy divisions");
+    return PSL_OK;
+}
+
+extern "C" int psl_run(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
+                       int64_t first, int64_t n, int32_t use_graph, void *stream_) {
+    int rc = check_run_args(plan, ph, tally, first, n, "psl_run");
+    if (rc) return rc;
+    cudaStream_t st = as_stream(stream_);
+    if (use_graph) return graph_run(plan, ph, phys, tally, first, n, nullptr, st);
+    Runner R;
+    if ((rc = run_body(plan, ph, phys, tally, first, n, st, false, R))) return rc;
+    return R.finish();
+}
+
+extern "C" int psl_plan_replay(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys,
+                               psl_tally_t *tally, int64_t first, int64_t n, double norm, double *dose, double *sigma,
+                               double *ledger, void *stream_) {
+    int rc = check_run_args(plan, ph, tally, first, n, "psl_plan_replay");
+    if (rc) return rc;
+    if (!ph->rho) return psl_fail(PSL_EINVAL, "psl_plan_replay: null density");
+    ReadoutArgs ro{norm, dose, sigma, ledger};
+    return graph_run(plan, ph, phys, tally, first, n, &ro, as_stream(stream_));
 }
 
 // ---------------------------------------------------------------- tuning --
@@ -1915,5 +2032,69 @@ extern "C" int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *ph, con
     if ((rc = psl_tally_reset(tally, stream_))) return rc;
     if (blocks_per_sm) *blocks_per_sm = bg;
     if (queue_depth) *queue_depth = bd;
+    return PSL_OK;
+}
+
+// Autotuner for the PSL position-bin size (the paper leaves it to
+// benchmarking): for every candidate cell size, the store is built with
+// square cells over the same extent, the plan created and n_probe histories
+// run (once to warm up, once timed); the estimate is the plan creation plus
+// the probe's time scaled to the plan's histories.
+extern "C" int psl_autotune_bins(const psl_params_t *params, const psl_records_t *records, const psl_beam_t *beams,
+                                 int32_t n_beams, float sad, const psl_phantom_t *ph, const psl_physics_t *phys,
+                                 int64_t n_histories, uint64_t seed, int32_t n_batches, const float *cell_cm,
+                                 int32_t n_cells, int64_t n_probe, float *best_cell, double *plan_seconds,
+                                 void *stream_) {
+    if (!params || !records || !beams || n_beams <= 0 || !ph || !cell_cm || n_cells <= 0 || n_probe <= 0 ||
+        n_histories <= 0 || !params->x_edges || !params->y_edges || params->nx <= 0 || params->ny <= 0)
+        return psl_fail(PSL_EINVAL, "psl_autotune_bins: bad argument");
+    for (int k = 0; k < n_cells; ++k)
+        if (!(cell_cm[k] > 0.f)) return psl_fail(PSL_EINVAL, "psl_autotune_bins: cell sizes must be > 0");
+    cudaStream_t st = as_stream(stream_);
+    const double x0 = params->x_edges[0], x1 = params->x_edges[params->nx];
+    const double y0 = params->y_edges[0], y1 = params->y_edges[params->ny];
+    const int64_t probe = std::min<int64_t>(n_probe, n_histories);
+    psl_tally_t *tally = nullptr;
+    int rc = psl_tally_create(ph, n_batches, &tally);
+    if (rc) return rc;
+    cudaEvent_t a, b, c;
+    cudaEventCreate(&a); cudaEventCreate(&b); cudaEventCreate(&c);
+    double best = 1e300;
+    float best_c = cell_cm[0];
+    for (int k = 0; k < n_cells && !rc; ++k) {
+        const int nx = (int)std::max<long long>(1, std::llround((x1 - x0) / cell_cm[k]));
+        const int ny = (int)std::max<long long>(1, std::llround((y1 - y0) / cell_cm[k]));
+        std::vector<float> xe(nx + 1), ye(ny + 1);
+        for (int i = 0; i <= nx; ++i) xe[i] = (float)(x0 + (x1 - x0) * i / nx);
+        for (int i = 0; i <= ny; ++i) ye[i] = (float)(y0 + (y1 - y0) * i / ny);
+        psl_params_t pc = *params;
+        pc.nx = nx; pc.ny = ny; pc.x_edges = xe.data(); pc.y_edges = ye.data();
+        psl_store_t *store = nullptr;
+        psl_plan_t *plan = nullptr;
+        if ((rc = psl_build(&pc, records, &store, stream_))) break;
+        float ms_plan = 0.f, ms_run = 0.f;
+        cudaEventRecord(a, st);
+        rc = psl_plan_create(store, beams, n_beams, sad, n_histories, seed, &plan, stream_);
+        cudaEventRecord(b, st);
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            if (rep == 1) cudaEventRecord(b, st);
+            if (!(rc = psl_tally_reset(tally, stream_))) rc = psl_run(plan, ph, phys, tally, 0, probe, 0, stream_);
+            if (rep == 0 && !rc) { cudaEventSynchronize(b); cudaEventElapsedTime(&ms_plan, a, b); }
+        }
+        cudaEventRecord(c, st);
+        if (!rc) {
+            cudaEventSynchronize(c);
+            cudaEventElapsedTime(&ms_run, b, c);
+            const double est = 1e-3 * ((double)ms_plan + (double)ms_run * (double)n_histories / (double)probe);
+            if (plan_seconds) plan_seconds[k] = est;
+            if (est < best) { best = est; best_c = cell_cm[k]; }
+        }
+        psl_plan_destroy(plan);
+        psl_store_destroy(store);
+    }
+    cudaEventDestroy(a); cudaEventDestroy(b); cudaEventDestroy(c);
+    psl_tally_destroy(tally);
+    if (rc) return rc;
+    if (best_cell) *best_cell = best_c;
     return PSL_OK;
 }

@@ -392,3 +392,43 @@ def test_batch_order_windows_on_the_full_imrt_plan():
         tally.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1][:11], out[1][1][:11])
+
+
+def test_plan_replay_graph_equals_run_and_readout():
+    """psl_plan_replay (tally reset + psl_run + dose_readout recorded as one
+    CUDA graph) gives, on every replay, the dose, sigma and ledger of the
+    same calls made one by one."""
+    w = inputs.config4(n_records=300_000, n_histories=300_000)
+    w.n_batches = 5
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
+    phys = capi.physics()
+    nvox = dw.mat_t.numel()
+    norm = engine.normalisation(plan, w.n_histories)
+    ref = [torch.empty(nvox, dtype=torch.float64, device="cuda") for _ in range(2)] + \
+        [torch.empty(3, dtype=torch.float64, device="cuda")]
+    t1 = capi.psl_tally_create(dw.phantom, w.n_batches)
+    capi.psl_run(plan, dw.phantom, phys, t1, 0, w.n_histories)
+    capi.dose_readout(t1, dw.phantom, norm, *ref)
+    t2 = capi.psl_tally_create(dw.phantom, w.n_batches)
+    out = [torch.full_like(ref[0], -1.0), torch.full_like(ref[1], -1.0), torch.full_like(ref[2], -1.0)]
+    for _ in range(3):                                     # record, then two replays
+        for o in out:
+            o.fill_(-1.0)
+        capi.psl_plan_replay(plan, dw.phantom, phys, t2, 0, w.n_histories, norm, *out)
+        for a, b in zip(out, ref):
+            assert torch.equal(a, b)
+    assert float(ref[0].sum()) > 0
+
+
+def test_bin_size_autotuner_picks_a_candidate():
+    w = inputs.config2(n_records=1_000_000, n_histories=2_000_000)
+    dw = engine.upload(w)
+    cells = [0.5, 1.0, 2.0]
+    best, secs = capi.psl_autotune_bins(dw.params, dw.records, dw.beams, w.sad, dw.phantom, capi.physics(),
+                                        w.n_histories, w.seed, 10, cells, 400_000)
+    assert best in cells and np.all(secs > 0) and secs[cells.index(best)] == secs.min()
+    with pytest.raises(capi.PslError):
+        capi.psl_autotune_bins(dw.params, dw.records, dw.beams, w.sad, dw.phantom, capi.physics(),
+                               w.n_histories, w.seed, 10, [0.0], 1000)
