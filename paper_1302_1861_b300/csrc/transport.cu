@@ -628,11 +628,50 @@ __device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon 
     return false;
 }
 
+// Parking slots (PSL_PHOTON_SLOTS): one per lane in shared memory, holding
+// a photon whose Woodcock step drew a real interaction (PENDING) or one set
+// aside to make room for such a photon (READY).  A lane whose photon draws a
+// real interaction parks it and steps another photon (from its slot or the
+// feed) instead of idling; the parked interactions run together once enough
+// lanes have one (or every live lane is blocked), so that the interaction
+// code runs with most lanes active while stepping keeps the lanes busy.
+// Every photon keeps its own random stream, so the order changes nothing.
+// A slot is 19 words (the 18 of Photon and a pad: an odd stride keeps the
+// 32 slots of a warp free of bank conflicts).
+#ifndef PSL_PHOTON_SLOTS
+#define PSL_PHOTON_SLOTS 1
+#endif
+enum { SLOT_EMPTY = 0, SLOT_READY = 1, SLOT_PENDING = 2 };
+constexpr int SLOT_WORDS = 19;
+
+__device__ __forceinline__ void slot_store(uint32_t *s, const Photon &g) {
+    s[0] = __float_as_uint(g.x); s[1] = __float_as_uint(g.y); s[2] = __float_as_uint(g.z);
+    s[3] = __float_as_uint(g.u); s[4] = __float_as_uint(g.v); s[5] = __float_as_uint(g.w);
+    s[6] = __float_as_uint(g.e); s[7] = __float_as_uint(g.wt);
+    s[8] = g.p0; s[9] = g.p1; s[10] = g.root; s[11] = g.nchild; s[12] = g.draw;
+    s[13] = __float_as_uint(g.mumax); s[14] = __float_as_uint(g.inv_mumax); s[15] = (uint32_t)g.ti;
+    s[16] = __float_as_uint(g.tf); s[17] = g.chan;
+}
+
+__device__ __forceinline__ void slot_load(const uint32_t *s, Photon &g) {
+    g.x = __uint_as_float(s[0]); g.y = __uint_as_float(s[1]); g.z = __uint_as_float(s[2]);
+    g.u = __uint_as_float(s[3]); g.v = __uint_as_float(s[4]); g.w = __uint_as_float(s[5]);
+    g.e = __uint_as_float(s[6]); g.wt = __uint_as_float(s[7]);
+    g.p0 = s[8]; g.p1 = s[9]; g.root = s[10]; g.nchild = s[11]; g.draw = s[12];
+    g.mumax = __uint_as_float(s[13]); g.inv_mumax = __uint_as_float(s[14]); g.ti = (int)s[15];
+    g.tf = __uint_as_float(s[16]); g.chan = s[17];
+}
+
 __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
                                                 uint32_t cap, uint32_t *head) {
     __shared__ FeedSmem sm;
     __shared__ uint32_t bh[NBANDS];
     __shared__ unsigned long long sled[NLEDGER];
+#if PSL_PHOTON_SLOTS
+    __shared__ uint32_t slots[FEED_WARPS * 32][SLOT_WORDS];
+    uint32_t *my = slots[threadIdx.x];
+    uint32_t slot = SLOT_EMPTY;
+#endif
     band_hist_init(bh);
     acc_init(sled);
     __syncthreads();
@@ -645,6 +684,9 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
     F.init(sm, src, n, head, A.err, A.wait_polls, (A.dbg & PSL_DEBUG_FEED_STALL) != 0);
     bool alive = false, done = false, real = false;
     for (;;) {
+#if PSL_PHOTON_SLOTS
+        if (!alive && slot == SLOT_READY) { slot_load(my, g); slot = SLOT_EMPTY; alive = true; }
+#endif
         const unsigned need = __ballot_sync(FULL, !alive && !done);
         if (need) {
             Particle p;
@@ -664,6 +706,42 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
             }
         }
         const unsigned live = __ballot_sync(FULL, alive);
+#if PSL_PHOTON_SLOTS
+        const unsigned pend = __ballot_sync(FULL, slot == SLOT_PENDING);
+        if (!live && !pend) break;
+        // the parked interactions run when enough lanes have one, or when
+        // every live lane is blocked (its photon has an interaction too)
+        const unsigned stuck = __ballot_sync(FULL, alive && real);
+        if (pend && (__popc(pend) >= PSL_G_DEFER || stuck == live)) {
+            if (slot == SLOT_PENDING) {
+                Photon q;
+                slot_load(my, q);
+                if (alive) { slot_store(my, g); slot = real ? SLOT_PENDING : SLOT_READY; }
+                else slot = SLOT_EMPTY;
+                g = q;
+                alive = photon_interact(A, acc, g, bh);
+                real = false;
+            }
+        }
+        if (alive && !real) {
+            const int r = photon_step(A, acc, g);
+            if (r == G_END) {
+                alive = false;
+            } else if (r == G_REAL) {
+                if (slot == SLOT_EMPTY) {                     // park it, take other work
+                    slot_store(my, g); slot = SLOT_PENDING; alive = false;
+                } else if (slot == SLOT_READY) {              // swap with the set-aside photon
+                    Photon q;
+                    slot_load(my, q);
+                    slot_store(my, g);
+                    slot = SLOT_PENDING;
+                    g = q;
+                } else {
+                    real = true;                              // blocked until the parked one has run
+                }
+            }
+        }
+#else
         if (!live) break;
         // Real interactions wait until enough lanes have one (or every live
         // lane waits), so that the interaction code runs with most lanes
@@ -677,6 +755,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A
             alive = r != G_END;
             real = r == G_REAL;
         }
+#endif
     }
     flush_acc(A, acc, sled, 10, 8, 3);
     band_hist_flush(A, bh);
@@ -689,7 +768,7 @@ struct Electron {
     int ix, iy, iz;
     uint32_t p0, p1, root, nchild;
     int steps;
-    bool pos;
+    int sp;                    // species: 0 electron, NT positron (the offset of its table rows)
     uint32_t draw;             // draws taken from the particle's Philox stream
 #if PSL_DEP_COMBINE
     uint32_t piv;              // voxel of the deposits summed in pq (not yet added to the tally)
@@ -740,10 +819,10 @@ __device__ __forceinline__ float highland(float T, float s, float rho) {
 // energy whose CSDA range is r (g/cm^2): ln T from the inverse range table,
 // then one Newton step on the forward (Hermite) range, so that the range of
 // the result is r to float precision (a step of zero length keeps T)
-// (pos: the particle is a positron; its tables start at offset NT)
-__device__ __forceinline__ float energy_of_range(const Tables &T, float r, bool pos) {
-    const int sp = pos ? NT : 0;
-    float x = (__logf(r) - T.lnR0[pos]) * T.inv_dlnR[pos];
+// (sp: the species' table offset, 0 for electrons and NT for positrons)
+__device__ __forceinline__ float energy_of_range(const Tables &T, float r, int sp) {
+    const int k = sp / NT;
+    float x = (__logf(r) - T.lnR0[k]) * T.inv_dlnR[k];
     x = fminf(fmaxf(x, 0.0f), (float)(NT - 1) - 1e-3f);
     const int i = (int)x + sp;
     const float f = x - (float)(i - sp);
@@ -800,7 +879,7 @@ __device__ __forceinline__ float sample_bhabha(float T, float wcc, Rng &rng, con
 
 __device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &s, uint32_t iv) {
     deposit(A, acc, iv, s.t, s.wt, s.root);
-    if (s.pos) {
+    if (s.sp) {
         if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) {
             deposit(A, acc, iv, 2.0f * F_ME, s.wt, s.root);
         } else {
@@ -833,11 +912,11 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
         const float rho = fabsf(__ldg(A.mrho + iv));
         int ti; float tf;
         tab_pos(A.tab, s.t, ti, tf);
-        const int sp = s.pos ? NT : 0;
+        const int sp = s.sp;
         const float4 el = lerp4(A.tab.el + sp, ti, tf);
         // hard cross sections vanish below their thresholds (guard the
         // interpolation): Moller above 2 W_cc, Bhabha above W_cc
-        const float wth = s.pos ? A.wcc : 2.0f * A.wcc;
+        const float wth = sp ? A.wcc : 2.0f * A.wcc;
         const float sig = hard_on ? rho * ((s.t > wth ? el.y : 0.0f) + (s.t > A.wcb ? el.z : 0.0f)) : 0.0f;
         const float s_hard = sig > 0.0f ? __fdividef(s.nlam, sig) : INFINITY;
         // distance to the voxel boundary
@@ -868,7 +947,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
         // range left; the range itself is carried, not recomputed from the energy
         float tend, rend;
         if (which == 2) { tend = tlim; rend = rlim; }
-        else { rend = s.r - rho * step; tend = fmaxf(energy_of_range(A.tab, rend, s.pos), tlim); }
+        else { rend = s.r - rho * step; tend = fmaxf(energy_of_range(A.tab, rend, sp), tlim); }
         const float th0 = highland(s.t, step, rho);
         electron_deposit(A, acc, s, iv, s.t - tend);
         s.t = tend;
@@ -891,7 +970,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
             else { s.z = (float)(cross > 0 ? s.iz + 1 : s.iz) * A.vz; s.iz += cross; out = s.iz < 0 || s.iz >= A.nz; }
             if (out) {
                 electron_flush(A, acc, s);
-                escape(A, acc, s.t + (s.pos ? 2.0f * F_ME : 0.0f), s.wt, s.root);
+                escape(A, acc, s.t + (s.sp ? 2.0f * F_ME : 0.0f), s.wt, s.root);
                 return E_END;
             }
         }
@@ -914,15 +993,15 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
     {
         int tj; float tg;
         tab_pos(A.tab, s.t, tj, tg);
-        const int sp = s.pos ? NT : 0;
+        const int sp = s.sp;
         const float4 e2 = lerp4(A.tab.el + sp, tj, tg);
-        const float sm = s.t > (s.pos ? A.wcc : 2.0f * A.wcc) ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
+        const float sm = s.t > (sp ? A.wcc : 2.0f * A.wcc) ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
         rng.align();                                            // the hard event's draws
         const float r = rng.next(A.rk, s.p0, s.p1) * (sm + sb);
         if (sm + sb > 0.0f) {
             if (r < sm) {                                         // hard Moller (e-) or Bhabha (e+)
                 acc.ev += EV_HARD;
-                const float eps = s.pos ? sample_bhabha(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err)
+                const float eps = sp ? sample_bhabha(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err)
                                         : sample_moller(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
                 // polar cosines of the two electrons from momentum balance;
@@ -986,7 +1065,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     const Particle p = load_particle(src + idx);
                     s.x = p.x; s.y = p.y; s.z = p.z; s.u = p.u; s.v = p.v; s.w = p.w; s.t = p.e; s.wt = p.wt;
                     s.p0 = p.pid_lo; s.p1 = p.pid_hi; s.root = p.root; s.nchild = 0; s.steps = 0;
-                    s.pos = p.type == 2;
+                    s.sp = p.type == 2 ? NT : 0;
                     s.ix = min(max((int)floorf(s.x * A.ivx), 0), A.nx - 1);
                     s.iy = min(max((int)floorf(s.y * A.ivy), 0), A.ny - 1);
                     s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
@@ -995,7 +1074,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     s.piv = 0xFFFFFFFFu; s.pq = 0ull;
 #endif
                     s.nlam = -1.0f;                               // drawn at the first step
-                    s.r = range_of(A.tab, s.t, s.pos ? NT : 0);
+                    s.r = range_of(A.tab, s.t, s.sp);
                     alive = true;
                 } else {
                     done = true;
