@@ -348,7 +348,7 @@ __device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, 
                              float x, float y, float z, float u, float v, float w, float wt, uint32_t iv, uint32_t p0,
                              uint32_t p1, uint32_t &nchild, uint32_t root) {
     if (T > A.ecut && !(A.flags & PSL_PHYS_LOCAL_SECONDARIES)) {
-        atomicAdd(&bh[band_of(A, T)], 1u);
+        if (type == 1) atomicAdd(&bh[band_of(A, T)], 1u);     // (positrons leave the band sort)
         push_particle(A.e_out, A, type, x, y, z, u, v, w, T, wt, p0, p1, nchild, root);
         return;
     }
@@ -768,7 +768,6 @@ struct Electron {
     int ix, iy, iz;
     uint32_t p0, p1, root, nchild;
     int steps;
-    int sp;                    // species: 0 electron, NT positron (the offset of its table rows)
     uint32_t draw;             // draws taken from the particle's Philox stream
 #if PSL_DEP_COMBINE
     uint32_t piv;              // voxel of the deposits summed in pq (not yet added to the tally)
@@ -877,9 +876,10 @@ __device__ __forceinline__ float sample_bhabha(float T, float wcc, Rng &rng, con
     return x0;
 }
 
+template <bool POS>
 __device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &s, uint32_t iv) {
     deposit(A, acc, iv, s.t, s.wt, s.root);
-    if (s.sp) {
+    if (POS) {
         if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) {
             deposit(A, acc, iv, 2.0f * F_ME, s.wt, s.root);
         } else {
@@ -898,6 +898,7 @@ enum { E_END = 0, E_ON = 1, E_HARD = 2 };
 // that same call, in the voxel the step ended in, so that its lane takes the
 // next electron at once instead of idling through one more pass of the loop;
 // the deposits and draws are those of ending at the start of the next step.
+template <bool POS>
 __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &s) {
     uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
     if (!(s.t <= A.ecut) && ++s.steps <= MAX_E_STEPS) {
@@ -912,7 +913,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
         const float rho = fabsf(__ldg(A.mrho + iv));
         int ti; float tf;
         tab_pos(A.tab, s.t, ti, tf);
-        const int sp = s.sp;
+        constexpr int sp = POS ? NT : 0;                           // the species' table rows
         const float4 el = lerp4(A.tab.el + sp, ti, tf);
         // hard cross sections vanish below their thresholds (guard the
         // interpolation): Moller above 2 W_cc, Bhabha above W_cc
@@ -970,7 +971,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
             else { s.z = (float)(cross > 0 ? s.iz + 1 : s.iz) * A.vz; s.iz += cross; out = s.iz < 0 || s.iz >= A.nz; }
             if (out) {
                 electron_flush(A, acc, s);
-                escape(A, acc, s.t + (s.sp ? 2.0f * F_ME : 0.0f), s.wt, s.root);
+                escape(A, acc, s.t + (POS ? 2.0f * F_ME : 0.0f), s.wt, s.root);
                 return E_END;
             }
         }
@@ -980,12 +981,13 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
     }                                                         // the step's draws are committed here
     if (s.steps > MAX_E_STEPS) atomicOr(A.err, PSL_DEV_ERR_STEPS);
     electron_flush(A, acc, s);
-    electron_end(A, acc, s, iv);
+    electron_end<POS>(A, acc, s, iv);
     return E_END;
 }
 
 // the hard event (Moller delta ray or bremsstrahlung photon) that ended the
 // last step; the electron stays in the voxel of that step
+template <bool POS>
 __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron &s, uint32_t *bh) {
     const uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
     EventRng ev(s.draw);
@@ -993,7 +995,7 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
     {
         int tj; float tg;
         tab_pos(A.tab, s.t, tj, tg);
-        const int sp = s.sp;
+        constexpr int sp = POS ? NT : 0;
         const float4 e2 = lerp4(A.tab.el + sp, tj, tg);
         const float sm = s.t > (sp ? A.wcc : 2.0f * A.wcc) ? e2.y : 0.0f, sb = s.t > A.wcb ? e2.z : 0.0f;
         rng.align();                                            // the hard event's draws
@@ -1001,7 +1003,7 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
         if (sm + sb > 0.0f) {
             if (r < sm) {                                         // hard Moller (e-) or Bhabha (e+)
                 acc.ev += EV_HARD;
-                const float eps = sp ? sample_bhabha(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err)
+                const float eps = POS ? sample_bhabha(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err)
                                         : sample_moller(s.t, A.wcc, rng, A.rk, s.p0, s.p1, A.err);
                 const float W = eps * s.t, tp = s.t - W;
                 // polar cosines of the two electrons from momentum balance;
@@ -1029,6 +1031,10 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
     }
 }
 
+// POS: the positron instance (its own tables and Bhabha collisions), run on
+// the positron queue; the electron instance compiles without the positron
+// branches (a runtime species cost the electron pass 5 %).
+template <bool POS>
 __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
                                                   uint32_t *head) {
     // electrons live for several steps and their queue reads hit L1, so
@@ -1050,7 +1056,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
         // active; the other lanes keep stepping meanwhile.
         const unsigned hm = __ballot_sync(FULL, hard), live0 = __ballot_sync(FULL, alive);
         if (hm && (__popc(hm) >= PSL_E_DEFER || hm == live0)) {
-            if (hard) { electron_hard(A, acc, s, bh); hard = false; }
+            if (hard) { electron_hard<POS>(A, acc, s, bh); hard = false; }
         }
         // lanes whose electron ended (in this pass's step or before) take the next
         const unsigned need = __ballot_sync(FULL, !alive && !done);
@@ -1065,7 +1071,6 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     const Particle p = load_particle(src + idx);
                     s.x = p.x; s.y = p.y; s.z = p.z; s.u = p.u; s.v = p.v; s.w = p.w; s.t = p.e; s.wt = p.wt;
                     s.p0 = p.pid_lo; s.p1 = p.pid_hi; s.root = p.root; s.nchild = 0; s.steps = 0;
-                    s.sp = p.type == 2 ? NT : 0;
                     s.ix = min(max((int)floorf(s.x * A.ivx), 0), A.nx - 1);
                     s.iy = min(max((int)floorf(s.y * A.ivy), 0), A.ny - 1);
                     s.iz = min(max((int)floorf(s.z * A.ivz), 0), A.nz - 1);
@@ -1074,7 +1079,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
                     s.piv = 0xFFFFFFFFu; s.pq = 0ull;
 #endif
                     s.nlam = -1.0f;                               // drawn at the first step
-                    s.r = range_of(A.tab, s.t, s.sp);
+                    s.r = range_of(A.tab, s.t, POS ? NT : 0);
                     alive = true;
                 } else {
                     done = true;
@@ -1083,7 +1088,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
         }
         if (!__ballot_sync(FULL, alive)) break;
         if (alive && !hard) {
-            const int r = electron_step(A, acc, s);
+            const int r = electron_step<POS>(A, acc, s);
             alive = r != E_END;
             hard = r == E_HARD;
         }
@@ -1248,7 +1253,7 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
                 if (o.ptype == 0) {
                     queue_push(Queue{out, count, cap}, c, A.err);
                 } else {
-                    atomicAdd(&bh[band_of(A, c.e)], 1u);
+                    if (o.ptype == 1) atomicAdd(&bh[band_of(A, c.e)], 1u);
                     queue_push(A.e_out, c, A.err);
                 }
             }
@@ -1278,8 +1283,10 @@ __global__ void __launch_bounds__(256) k_band_count(Args A, const Particle *a, u
     if (threadIdx.x < NBANDS) h[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t n = na + min(*nb_ptr, capb);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        atomicAdd(&h[band_of(A, __ldg(&pick(a, na, b, i)->e))], 1u);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Particle *q = pick(a, na, b, i);
+        if (__ldg(&q->type) != 2u) atomicAdd(&h[band_of(A, __ldg(&q->e))], 1u);
+    }
     __syncthreads();
     if (threadIdx.x < NBANDS && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
 }
@@ -1304,9 +1311,11 @@ __global__ void k_band_scan(uint32_t *hist, uint32_t *cursor, uint32_t *out_coun
     if (t == 31) *out_count = x;
 }
 
+// Electrons go to dst in band order; positrons to the positron queue (their
+// own pass, k_electron<true>).
 __global__ void __launch_bounds__(256) k_band_scatter(Args A, const Particle *a, uint32_t na, const Particle *b,
                                                       const uint32_t *nb_ptr, uint32_t capb, uint32_t *cursor,
-                                                      Particle *dst, uint32_t capd) {
+                                                      Particle *dst, uint32_t capd, Queue pos_q) {
     __shared__ uint32_t h[NBANDS], base[NBANDS];
     const uint32_t n = na + min(*nb_ptr, capb);
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -1317,15 +1326,20 @@ __global__ void __launch_bounds__(256) k_band_scatter(Args A, const Particle *a,
         Particle p;
         int bnd = 0;
         uint32_t local = 0;
-        if (i < n) {
+        const bool have = i < n;
+        bool positron = false;
+        if (have) {
             p = load_particle(pick(a, na, b, i));
+            positron = p.type == 2u;
             bnd = band_of(A, p.e);
-            local = atomicAdd(&h[bnd], 1u);
+            if (!positron) local = atomicAdd(&h[bnd], 1u);
         }
         __syncthreads();
         if (threadIdx.x < NBANDS && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]);
         __syncthreads();
-        if (i < n) {
+        if (have && positron) {
+            queue_push(pos_q, p, A.err);
+        } else if (have) {
             uint32_t d = base[bnd] + local;
             if (d < capd) store_particle(dst + d, p);
             else atomicOr(A.err, PSL_DEV_ERR_QUEUE);
@@ -1390,10 +1404,11 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
 struct Workspace {
     int device = 0;                    // the device its buffers live on
     int64_t chunk = 0;                 // primaries per pass the buffers are sized for
-    uint32_t cap_p = 0, cap_e = 0, cap_s = 0;
-    Particle *P[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr}, *S = nullptr, *Q = nullptr;
+    uint32_t cap_p = 0, cap_e = 0, cap_s = 0, cap_q = 0;
+    Particle *P[2] = {nullptr, nullptr}, *E[2] = {nullptr, nullptr}, *S = nullptr, *Q = nullptr, *Pos = nullptr;
     uint32_t *cnt = nullptr;           // [0..1] P counts, [2..3] E counts, [4] S count, [5..6] heads,
-                                       // [7] primary photons, [9] err, [16..47] band hist, [48..79] cursors
+                                       // [7] primary photons, [9] err, [16..47] band hist, [48..79] cursors,
+                                       // [80] positron count, [81] positron head
     int *rmax = nullptr;
     float *mrho = nullptr;             // packed material/density of the phantom
     int64_t nvox = 0;
@@ -1418,6 +1433,7 @@ void workspace_free(Workspace *w) {
     for (int k = 0; k < 2; ++k) { if (w->P[k]) cudaFree(w->P[k]); if (w->E[k]) cudaFree(w->E[k]); }
     if (w->S) cudaFree(w->S);
     if (w->Q) cudaFree(w->Q);
+    if (w->Pos) cudaFree(w->Pos);
     if (w->cnt) cudaFree(w->cnt);
     if (w->rmax) cudaFree(w->rmax);
     if (w->mrho) cudaFree(w->mrho);
@@ -1434,7 +1450,8 @@ void workspace_free(Workspace *w) {
 int64_t workspace_bytes_of(const Workspace *w) {
     if (!w) return 0;
     const int64_t base = std::max<int64_t>(w->chunk, 4096);
-    int64_t b = (2 * (int64_t)w->cap_p + 2 * (int64_t)w->cap_e + (int64_t)w->cap_s + base) * (int64_t)sizeof(Particle);
+    int64_t b = (2 * (int64_t)w->cap_p + 2 * (int64_t)w->cap_e + (int64_t)w->cap_s + (int64_t)w->cap_q + base) *
+                (int64_t)sizeof(Particle);
     b += 128 * 4 + 2 * 4 + w->nvox * 4;
     if (w->bm_cap) b += 16 * w->bm_cap + (PSL_MAX_BATCHES + 1) * 4 + (int64_t)sort_pairs_scratch_bytes((uint32_t)w->bm_cap);
     return b;
@@ -1573,12 +1590,14 @@ static int workspace_ensure(psl_tally *t, int64_t chunk) {
     w->cap_p = (uint32_t)std::min<int64_t>(3 * base, 0xF0000000ll);
     w->cap_e = (uint32_t)std::min<int64_t>(8 * base, 0xF0000000ll);
     w->cap_s = w->cap_e + (uint32_t)base;
+    w->cap_q = (uint32_t)std::min<int64_t>(base, 0xF0000000ll);   // positrons of a generation (pairs are rare)
     PSL_CUDA(cudaMalloc((void **)&w->P[0], (size_t)w->cap_p * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->P[1], (size_t)w->cap_p * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->E[0], (size_t)w->cap_e * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->E[1], (size_t)w->cap_e * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->S, (size_t)w->cap_s * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->Q, (size_t)base * sizeof(Particle)));
+    PSL_CUDA(cudaMalloc((void **)&w->Pos, (size_t)w->cap_q * sizeof(Particle)));
     PSL_CUDA(cudaMalloc((void **)&w->cnt, 128 * sizeof(uint32_t)));
     PSL_CUDA(cudaMemset(w->cnt, 0, 128 * sizeof(uint32_t)));
     PSL_CUDA(cudaMalloc((void **)&w->rmax, 2 * sizeof(int)));
@@ -1611,7 +1630,7 @@ struct Runner {
     bool timing = false;
     int grid_t = 0, grid_m = 0, grid_src = 0;
     int64_t chunk = 0;
-    uint32_t cap_p = 0, cap_e = 0, cap_s = 0;   // queue capacities in use (a test may cap them)
+    uint32_t cap_p = 0, cap_e = 0, cap_s = 0, cap_q = 0;   // queue capacities in use (a test may cap them)
 
     int prepare(const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally *t, uint64_t seed, int64_t need,
                 cudaStream_t stream, bool capturing) {
@@ -1633,6 +1652,7 @@ struct Runner {
             cap_p = qc > 0 ? (uint32_t)std::min<long long>(w->cap_p, qc) : w->cap_p;
             cap_e = qc > 0 ? (uint32_t)std::min<long long>(w->cap_e, qc) : w->cap_e;
             cap_s = qc > 0 ? (uint32_t)std::min<long long>(w->cap_s, qc) : w->cap_s;
+            cap_q = qc > 0 ? (uint32_t)std::min<long long>(w->cap_q, qc) : w->cap_q;
         }
         A.wait_polls = (uint32_t)std::min<long long>(psl_wait_polls(FEED_SPIN), 0xFFFFFFFFll);
         A.dbg = psl_debug_flags();
@@ -1695,7 +1715,9 @@ struct Runner {
         // only caller electrons (a materialised batch) are counted here
         if (na) { k_band_count<<<gm(), 256, 0, st>>>(A, a, na, w->E[ec], cE(ec), 0u, hist); PSL_NOTE_LAUNCH(); }
         k_band_scan<<<1, 32, 0, st>>>(hist, cursor, cS); PSL_NOTE_LAUNCH();
-        k_band_scatter<<<gm(), 256, 0, st>>>(A, a, na, w->E[ec], cE(ec), cap_e, cursor, w->S, cap_s); PSL_NOTE_LAUNCH();
+        cudaMemsetAsync(w->cnt + 80, 0, 4, st);                 // positrons go to their own queue
+        k_band_scatter<<<gm(), 256, 0, st>>>(A, a, na, w->E[ec], cE(ec), cap_e, cursor, w->S, cap_s,
+                                             Queue{w->Pos, w->cnt + 80, cap_q}); PSL_NOTE_LAUNCH();
         te(PK_BAND, tk);
     }
     void photon_pass(const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
@@ -1715,7 +1737,10 @@ struct Runner {
         cudaMemsetAsync(w->cnt + 6, 0, 4, st);
         void *tk = nullptr;
         tb(PK_ELECTRON, &tk);
-        k_electron<<<gt(), 256, 0, st>>>(a2, w->S, w->cnt + 4, cap_s, w->cnt + 6); PSL_NOTE_LAUNCH();
+        k_electron<false><<<gt(), 256, 0, st>>>(a2, w->S, w->cnt + 4, cap_s, w->cnt + 6); PSL_NOTE_LAUNCH();
+        // the positrons of the same generation (few: one block per SM)
+        cudaMemsetAsync(w->cnt + 81, 0, 4, st);
+        k_electron<true><<<psl_sm_count(), 256, 0, st>>>(a2, w->Pos, w->cnt + 80, cap_q, w->cnt + 81); PSL_NOTE_LAUNCH();
         te(PK_ELECTRON, tk);
     }
 
