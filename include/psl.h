@@ -335,11 +335,14 @@ PSL_API int psl_batch_read(const psl_batch_t *batch, float *state, int32_t *ptyp
 PSL_API int psl_batch_info(const psl_batch_t *batch, int64_t *n_histories, int64_t *n_photons, int64_t *n_electrons);
 
 /* Tally slices (batches, Sec. 2.3.3).  A history's deposits all go to one
- * slice; with PSL_SLICE_BY_HISTORY that slice is the first word of
- * Philox(key = seed; counter = (0, 4, history id)) times n_batches / 2^32,
- * so every slice is an independent pseudo-random subset of the histories,
- * whatever order they are read in, and the batch standard deviation is a
- * valid uncertainty.  1 <= n_batches <= PSL_MAX_BATCHES. */
+ * slice; with PSL_SLICE_BY_HISTORY the history ids are cut into blocks of
+ * PSL_BATCH_BLOCK consecutive ids and block B = id / PSL_BATCH_BLOCK goes to
+ * slice floor(r n_batches / 2^32), r the first word of Philox(key = seed;
+ * counter = (0, 4, B)), so every slice is an independent pseudo-random
+ * subset of blocks of the reading order, whatever order they are read in,
+ * and the batch standard deviation is a valid uncertainty.
+ * 1 <= n_batches <= PSL_MAX_BATCHES. */
+#define PSL_BATCH_BLOCK 256
 #define PSL_SLICE_BY_HISTORY (-1)
 #define PSL_MAX_BATCHES 1024
 
@@ -359,16 +362,17 @@ PSL_API int psl_tally_reset(psl_tally_t *tally, void *stream);
 /* Order in which psl_run visits its history range (the dose is the same
  * bit for bit in every order: integer counters, per-history streams).
  * PSL_ORDER_READING: the range in reading order, every pass depositing into
- * all n_batches slices.  PSL_ORDER_BATCH: windows of the range are
- * partitioned by each history's batch (a stable sort of the batch indices)
- * and run batch by batch, so a pass deposits into one slice; this keeps the
+ * all n_batches slices.  PSL_ORDER_BATCH: windows of the range's batch
+ * blocks are partitioned by batch (a stable sort of the blocks' batch
+ * indices) and run batch by batch, so a pass deposits into one slice; this keeps the
  * hot part of a tally larger than about half the L2 cache resident (the
  * 30x30 CT and IMRT tallies of 128^3 and 128x128x100 voxels x 10 batches are
  * 168 and 131 MB).  PSL_ORDER_AUTO (the default): batch by batch when the
  * tally (voxels x n_batches x 8 bytes) exceeds half the device's L2 and
- * n_batches > 1.  The batch order holds, per tally, 32 bytes per history of
- * a window (at most 2^28 histories: ~n_batches x the queue depth), allocated
- * by the first psl_run that uses it.  Returns PSL_EINVAL for other values. */
+ * n_batches > 1.  The batch order holds, per tally, 16 bytes per batch
+ * block of a window (at most 2^24 blocks: ~n_batches x the queue depth /
+ * PSL_BATCH_BLOCK) and the sort's scratch, allocated by the first psl_run
+ * that uses it.  Returns PSL_EINVAL for other values. */
 #define PSL_ORDER_AUTO 0
 #define PSL_ORDER_READING 1
 #define PSL_ORDER_BATCH 2

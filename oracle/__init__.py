@@ -75,14 +75,17 @@ def transport(ptype, pos, dirs, e, wt, pid, phantom, seed, flags=0, nthreads=0,
 
 
 TAG_BATCH = 4
+BATCH_BLOCK = 256            # consecutive history ids that share a batch
 
 
 def history_slices(h: np.ndarray, seed: int, n_batches: int) -> np.ndarray:
-    """Batch of every history (Sec. 2.3.3: independent batches): the first
-    word r of Philox(key = seed; counter = (0, TAG_BATCH, history id)) scaled
-    to [0, N_b) as floor(r N_b / 2^32).  A pseudo-random partition: every
-    batch is an independent sample whatever order the histories are read in."""
-    h = np.asarray(h, np.uint64)
+    """Batch of every history (Sec. 2.3.3: independent batches).  The ids
+    are cut into blocks of BATCH_BLOCK consecutive histories; block
+    B = h // BATCH_BLOCK goes to batch floor(r N_b / 2^32), r the first word of
+    Philox(key = seed; counter = (0, TAG_BATCH, B)).  A pseudo-random
+    partition of the reading order into blocks: every batch is an independent
+    sample of blocks, whatever order they are read in."""
+    h = np.asarray(h, np.uint64) // np.uint64(BATCH_BLOCK)
     ctr = np.zeros((len(h), 4), np.uint32)
     ctr[:, 1] = TAG_BATCH
     ctr[:, 2] = (h & np.uint64(0xFFFFFFFF)).astype(np.uint32)

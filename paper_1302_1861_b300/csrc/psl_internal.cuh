@@ -261,9 +261,21 @@ struct Rng {
 // word of Philox(key seed; counter (0, TAG_BATCH, history id)) scaled to
 // [0, nb).  Every batch is an independent pseudo-random subset of the
 // histories, whatever the reading order.
-__device__ __forceinline__ uint32_t history_slice(uint32_t p0, uint32_t p1, const uint32_t *rk, uint32_t nb) {
-    const u32x4 r = philox10_rk(0u, TAG_BATCH, p0, p1, rk);
+// Batches are drawn per block of BATCH_BLOCK consecutive history ids: block
+// B = h >> BATCH_BLOCK_SHIFT goes to batch floor(r N_b / 2^32), r the first
+// word of Philox(key = seed; counter = (0, TAG_BATCH, B)).
+#define BATCH_BLOCK_SHIFT 8
+#define BATCH_BLOCK (1 << BATCH_BLOCK_SHIFT)
+static_assert(BATCH_BLOCK == PSL_BATCH_BLOCK, "psl.h states the batch block");
+
+__device__ __forceinline__ uint32_t block_slice(uint64_t blk, const uint32_t *rk, uint32_t nb) {
+    const u32x4 r = philox10_rk(0u, TAG_BATCH, (uint32_t)blk, (uint32_t)(blk >> 32), rk);
     return __umulhi(r.a, nb);
+}
+
+// the batch of history (or caller particle) id p1:p0
+__device__ __forceinline__ uint32_t history_slice(uint32_t p0, uint32_t p1, const uint32_t *rk, uint32_t nb) {
+    return block_slice((((uint64_t)p1 << 32) | p0) >> BATCH_BLOCK_SHIFT, rk, nb);
 }
 
 __device__ __forceinline__ void child_id(uint64_t seed, uint32_t p0, uint32_t p1, uint32_t ordinal,

@@ -1031,23 +1031,15 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
     }
 }
 
-// POS: the positron instance (its own tables and Bhabha collisions), run on
-// the positron queue; the electron instance compiles without the positron
-// branches (a runtime species cost the electron pass 5 %).
+// One species' queue: each lane steps one particle and takes the next
+// when it ends (POS: positrons, with their own tables and Bhabha
+// collisions; the electron loop compiles without the positron branches - a
+// runtime species cost the electron pass 5 %).
 template <bool POS>
-__global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
-                                                  uint32_t *head) {
-    // electrons live for several steps and their queue reads hit L1, so
-    // refills load directly (a staged feed measured 2 % slower here)
-    __shared__ uint32_t bh[NBANDS];
-    __shared__ unsigned long long sled[NLEDGER];
-    band_hist_init(bh);
-    acc_init(sled);
-    __syncthreads();
-    const uint32_t n = min(*n_ptr, cap);
+__device__ __forceinline__ void electron_loop(const Args &A, Acc &acc, const Particle *src, uint32_t n,
+                                              uint32_t *head, uint32_t *bh) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    Acc acc = {0u, 0u, 0ull, 0ull};
     Electron s;
     bool alive = false, done = false, hard = false;
     for (;;) {
@@ -1058,7 +1050,7 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
         if (hm && (__popc(hm) >= PSL_E_DEFER || hm == live0)) {
             if (hard) { electron_hard<POS>(A, acc, s, bh); hard = false; }
         }
-        // lanes whose electron ended (in this pass's step or before) take the next
+        // lanes whose particle ended (in this pass's step or before) take the next
         const unsigned need = __ballot_sync(FULL, !alive && !done);
         if (need) {
             const int leader = __ffs(need) - 1;
@@ -1093,6 +1085,23 @@ __global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args
             hard = r == E_HARD;
         }
     }
+}
+
+// The electron pass: the band-ordered electrons, then (as each warp runs out
+// of electrons) the generation's positrons from their own queue.
+__global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
+                                                  uint32_t *head, const Particle *psrc, const uint32_t *pn_ptr,
+                                                  uint32_t pcap, uint32_t *phead) {
+    // electrons live for several steps and their queue reads hit L1, so
+    // refills load directly (a staged feed measured 2 % slower here)
+    __shared__ uint32_t bh[NBANDS];
+    __shared__ unsigned long long sled[NLEDGER];
+    band_hist_init(bh);
+    acc_init(sled);
+    __syncthreads();
+    Acc acc = {0u, 0u, 0ull, 0ull};
+    electron_loop<false>(A, acc, src, min(*n_ptr, cap), head, bh);
+    electron_loop<true>(A, acc, psrc, min(*pn_ptr, pcap), phead, bh);
     flush_acc(A, acc, sled, 6, 9, 11);
     band_hist_flush(A, bh);
 }
@@ -1114,11 +1123,9 @@ __global__ void k_assign_slices(Args A, Particle *p, int64_t nph, int64_t nel, i
 // reuse that (group, segment) when it is also theirs.
 // Batch of every history of a window [first, first + n): the key of the
 // stable sort that partitions the window batch by batch.
-__global__ void __launch_bounds__(256) k_slice_keys(Args A, int64_t first, uint32_t n, uint32_t nb, uint32_t *keys) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint64_t h = (uint64_t)(first + i);
-        keys[i] = history_slice((uint32_t)h, (uint32_t)(h >> 32), A.rk, nb);
-    }
+__global__ void __launch_bounds__(256) k_slice_keys(Args A, int64_t first_block, uint32_t n, uint32_t nb, uint32_t *keys) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        keys[i] = block_slice((uint64_t)(first_block + i), A.rk, nb);
 }
 
 __global__ void k_or_err(const uint32_t *src, uint32_t *err) {
@@ -1137,12 +1144,14 @@ __global__ void k_slice_bounds(const uint32_t *keys, uint32_t n, uint32_t nb, ui
     }
 }
 
-// Histories first + i * stride, i < n; or, with a list, the histories
-// first + list[list_off[slice] + root0 + i] of one batch of a window whose
-// offsets were sorted by batch (at most n of them: more is an overflow).
+// Histories first + i * stride, i < n; or (LIST, the batch-by-batch
+// order) the histories of one batch of the window [first, first + stride):
+// the blocks list[list_off[slice] ...] (offsets from the window's first
+// batch block, sorted by batch), each block's BATCH_BLOCK consecutive ids
+// clipped to the window (at most n histories: more is an overflow).
 // TRACE: the instance launched while a tally records the source stage
-// (psl_tally_trace_source); the production instance compiles without it.
-template <bool TRACE>
+// (psl_tally_trace_source); the production instances compile without it.
+template <bool TRACE, bool LIST>
 __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev P, int64_t first, int64_t stride, uint32_t n,
                                                 uint32_t root0, int32_t slice, Particle *out, uint32_t *count,
                                                 const uint32_t *list, const uint32_t *list_off, SrcTraceDev T) {
@@ -1154,17 +1163,21 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
     acc_init(sled);
     __syncthreads();
     const uint32_t cap = n;
-    uint32_t lbase = 0;
-    if (list) {
-        lbase = list_off[slice] + root0;
+    // list mode (one batch of a window, PSL_ORDER_BATCH): the batch's blocks of
+    // BATCH_BLOCK consecutive histories, as offsets from the window's first
+    // block (first >> BATCH_BLOCK_SHIFT); the window is [first, first + stride)
+    uint32_t lbase = 0, n_runs;
+    if (LIST) {
         // (bounds from a sort whose look-back gave up may be out of order:
         // then the batch is skipped, and the error word already says why)
         const uint32_t o0 = list_off[slice], o1 = list_off[slice + 1];
-        const uint32_t total = o1 >= o0 ? o1 - o0 : 0u;
-        const uint32_t left = total > root0 ? total - root0 : 0u;
-        if (left > n && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, PSL_DEV_ERR_QUEUE);
-        n = min(n, left);
+        n_runs = o1 >= o0 ? o1 - o0 : 0u;
+        lbase = o0;
+        if ((uint64_t)n_runs * BATCH_BLOCK > n && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, PSL_DEV_ERR_QUEUE);
+    } else {
+        n_runs = (n + SRC_RUN - 1) / SRC_RUN;
     }
+    static_assert(SRC_RUN == BATCH_BLOCK, "a run of the source stage is a batch block");
     Acc acc = {0u, 0u, 0ull, 0ull};
     unsigned long long emitted = 0, missed = 0;      // this thread's fixed-point energy
     const int lane = threadIdx.x & 31;
@@ -1175,11 +1188,25 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
     // records of the reading order at the same time
     const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
     const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const uint32_t n_runs = (n + SRC_RUN - 1) / SRC_RUN;
     int g = -1;
     int64_t q = -1;
-    for (uint32_t run = gw; run < n_runs; run += n_warps)
-    for (uint32_t ib = run * SRC_RUN, i1 = min(n, ib + SRC_RUN), i0 = ib; ib < i1; ib += 32u * SRC_ILP) {
+    for (uint32_t run = gw; run < n_runs; run += n_warps) {
+    // the run's histories: hbase + j, 0 <= j < len (call index ib0 + j)
+    int64_t hbase;
+    uint32_t len, ib0;
+    if (LIST) {
+        const int64_t blk = (first >> BATCH_BLOCK_SHIFT) + (int64_t)__ldg(list + lbase + run);
+        const int64_t lo = max(blk << BATCH_BLOCK_SHIFT, first);
+        const int64_t hi = min((blk + 1) << BATCH_BLOCK_SHIFT, first + stride);
+        hbase = lo;
+        len = hi > lo ? (uint32_t)(hi - lo) : 0u;
+        ib0 = 0;
+    } else {
+        ib0 = run * SRC_RUN;
+        hbase = first + (int64_t)ib0 * stride;
+        len = min(n - ib0, (uint32_t)SRC_RUN);
+    }
+    for (uint32_t jb = 0; jb < len; jb += 32u * SRC_ILP) {
         // SRC_ILP histories per lane, 32 apart: their plan lookups and
         // record reads are issued together, so that their latencies overlap
         bool ok[SRC_ILP];
@@ -1187,10 +1214,10 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
         int gk[SRC_ILP];
 #pragma unroll
         for (int k = 0; k < SRC_ILP; ++k) {
-            const uint32_t i = ib + 32u * k + lane;
-            ok[k] = i < i1;
-            h[k] = list ? (ok[k] ? first + (int64_t)__ldg(list + lbase + i) : first) : first + (int64_t)i * stride;
-            if (k == 0 && ib == i0) {
+            const uint32_t j = jb + 32u * k + lane;
+            ok[k] = j < len;
+            h[k] = hbase + (int64_t)(ok[k] ? j : 0u) * (LIST ? 1 : stride);
+            if (k == 0 && jb == 0) {
                 if (lane == 0 && ok[0]) locate(P, S, h[0], g, q);
                 g = __shfl_sync(FULL, g, 0);
                 q = __shfl_sync(FULL, q, 0);
@@ -1221,7 +1248,7 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
         }
 #pragma unroll
         for (int k = 0; k < SRC_ILP; ++k) {
-            const uint32_t i = ib + 32u * k + lane;
+            const uint32_t i = LIST ? 0u : ib0 + jb + 32u * k + lane;   // index in the call (traced transport)
             SrcOut o;
             o.status = -1;
             if (ok[k]) record_to_phantom(R[k], P.beams[E[k].beam], P.z_psl, P.L, P.origin, true, o);
@@ -1258,6 +1285,7 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
                 }
             }
         }
+    }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1522,18 +1550,19 @@ static int source_blocks_per_sm() {
     static int nb = 0;
     if (!nb) {
         int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_source<false>, 256, 0) != cudaSuccess || v < 1) v = 4;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_source<false, false>, 256, 0) != cudaSuccess || v < 1) v = 4;
         nb = v;
     }
     return nb;
 }
 
-// Batch-by-batch order (PSL_ORDER_BATCH): histories per window, so that a
-// batch of a window (binomial, mean W / nb) stays within one transport pass
-// of `chunk` primaries by 8 standard deviations: W / nb = (sqrt(chunk + 16) - 4)^2.
+// Batch-by-batch order (PSL_ORDER_BATCH): batch blocks per window, so that
+// the blocks of one batch of a window (binomial, mean Wb / nb) hold at most
+// one transport pass of `chunk` primaries by 8 standard deviations:
+// x = Wb / nb with x + 8 sqrt(x) = chunk / BATCH_BLOCK.
 static int64_t batch_window(int64_t chunk, int nb) {
-    const double r = std::sqrt((double)chunk + 16.0) - 4.0;
-    return std::min<int64_t>(std::max<int64_t>(1, (int64_t)(r * r)) * nb, (int64_t)1 << 28);
+    const double r = std::sqrt((double)chunk / BATCH_BLOCK + 16.0) - 4.0;
+    return std::min<int64_t>(std::max<int64_t>(1, (int64_t)(r * r * nb)), (int64_t)1 << 24);
 }
 
 static bool use_batch_order(const psl_tally *t) {
@@ -1737,10 +1766,9 @@ struct Runner {
         cudaMemsetAsync(w->cnt + 6, 0, 4, st);
         void *tk = nullptr;
         tb(PK_ELECTRON, &tk);
-        k_electron<false><<<gt(), 256, 0, st>>>(a2, w->S, w->cnt + 4, cap_s, w->cnt + 6); PSL_NOTE_LAUNCH();
-        // the positrons of the same generation (few: one block per SM)
         cudaMemsetAsync(w->cnt + 81, 0, 4, st);
-        k_electron<true><<<psl_sm_count(), 256, 0, st>>>(a2, w->Pos, w->cnt + 80, cap_q, w->cnt + 81); PSL_NOTE_LAUNCH();
+        k_electron<<<gt(), 256, 0, st>>>(a2, w->S, w->cnt + 4, cap_s, w->cnt + 6, w->Pos, w->cnt + 80, cap_q,
+                                         w->cnt + 81); PSL_NOTE_LAUNCH();
         te(PK_ELECTRON, tk);
     }
 
@@ -1779,7 +1807,8 @@ struct Runner {
                 cudaMemsetAsync(w->cnt + 7, 0, 4, st);
                 void *tk = nullptr;
                 tb(PK_SOURCE, &tk);
-                auto *ks = tally->trace.n ? k_source<true> : k_source<false>;
+                auto *ks = J.list ? (tally->trace.n ? k_source<true, true> : k_source<false, true>)
+                                  : (tally->trace.n ? k_source<true, false> : k_source<false, false>);
                 ks<<<grid_src, 256, 0, st>>>(a2, J.P, J.list ? J.first : J.first + a0 * J.stride, J.stride, cp,
                                              (uint32_t)a0, J.slice, w->Q, w->cnt + 7, J.list, J.list_off,
                                              tally->trace);
@@ -1925,12 +1954,12 @@ extern "C" int transport_trace(const psl_phantom_t *ph, const psl_physics_t *phy
 // most batches finish within them, so a batch usually costs one host check.
 #define UNCHECKED_GENERATIONS 3
 
-// Windows of the batch-by-batch order for a range of n histories (0: the
-// range runs in reading order).
+// Batch blocks per window of the batch-by-batch order for a range of n
+// histories (0: the range runs in reading order).
 static int64_t batch_order_window(const psl_tally *tally, int64_t n) {
     if (!use_batch_order(tally)) return 0;
     const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, tally->chunk_cap));
-    return std::min<int64_t>(batch_window(chunk, tally->n_batches), n);
+    return std::min<int64_t>(batch_window(chunk, tally->n_batches), n / BATCH_BLOCK + 2);
 }
 
 static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_physics_t *phys, psl_tally_t *tally,
@@ -1955,19 +1984,26 @@ static int run_body(const psl_plan_t *plan, const psl_phantom_t *ph, const psl_p
     if (w->bm_cap < W) return psl_fail(PSL_EINVAL, "psl_run: batch-order buffers not set up");
     const uint32_t nb = (uint32_t)tally->n_batches;
     const int bits = 32 - __builtin_clz(nb - 1);
-    for (int64_t w0 = 0; w0 < n; w0 += W) {
-        const uint32_t wn = (uint32_t)std::min<int64_t>(W, n - w0);
-        k_slice_keys<<<R.grid_m, 256, 0, st>>>(R.A, first + w0, wn, nb, w->bm_keys[0]); PSL_NOTE_LAUNCH();
+    // windows of W batch blocks (B = h >> BATCH_BLOCK_SHIFT) over the range's
+    // blocks; in a window the blocks are sorted by batch (a stable radix pass)
+    // and each batch's blocks run as one pass, clipped to the range
+    const int64_t B0 = first >> BATCH_BLOCK_SHIFT, B1 = (first + n - 1) >> BATCH_BLOCK_SHIFT;
+    for (int64_t b0 = B0; b0 <= B1; b0 += W) {
+        const uint32_t wb = (uint32_t)std::min<int64_t>(W, B1 - b0 + 1);
+        const int64_t h_lo = std::max<int64_t>(first, b0 << BATCH_BLOCK_SHIFT);
+        const int64_t h_hi = std::min<int64_t>(first + n, (b0 + wb) << BATCH_BLOCK_SHIFT);
+        k_slice_keys<<<R.grid_m, 256, 0, st>>>(R.A, b0, wb, nb, w->bm_keys[0]); PSL_NOTE_LAUNCH();
         int alt = 0;
-        if (sort_pairs_u32(w->bm_keys[0], w->bm_vals[0], w->bm_keys[1], w->bm_vals[1], wn, bits, nullptr, true,
+        if (sort_pairs_u32(w->bm_keys[0], w->bm_vals[0], w->bm_keys[1], w->bm_vals[1], wb, bits, nullptr, true,
                            w->bm_scratch, &alt, st))
             return psl_fail(PSL_EINVAL, "psl_run: batch sort");
         k_or_err<<<1, 1, 0, st>>>(sort_err_word(w->bm_scratch), R.A.err); PSL_NOTE_LAUNCH();
-        k_slice_bounds<<<1, 256, 0, st>>>(w->bm_keys[alt], wn, nb, w->bm_off); PSL_NOTE_LAUNCH();
+        k_slice_bounds<<<1, 256, 0, st>>>(w->bm_keys[alt], wb, nb, w->bm_off); PSL_NOTE_LAUNCH();
         for (uint32_t b = 0; b < nb; ++b) {
             Job Jb = J;
-            Jb.first = first + w0;
-            Jb.n = std::min<int64_t>(R.chunk, wn);     // one pass; k_source flags a batch larger than it
+            Jb.first = h_lo;                            // the window [h_lo, h_hi)
+            Jb.stride = h_hi - h_lo;
+            Jb.n = std::min<int64_t>(R.chunk, h_hi - h_lo);   // one pass; k_source flags a batch larger than it
             Jb.slice = (int32_t)b;
             Jb.list = w->bm_vals[alt];
             Jb.list_off = w->bm_off;
