@@ -959,7 +959,9 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
             const float l2 = -2.0f * ln_uniform(rng.take());
             const float th = th0 * (l2 * rsqrtf(l2));
             float st, ct, sp, cp;
-            sincosf(th, &st, &ct);
+            // (sin and cos of theta through sincospif of theta / pi: the same
+            // accuracy with no large-argument reduction path)
+            sincospif(th * 0.318309886183790671f, &st, &ct);
             st = fabsf(st);
             sincos_2pi(rng.take(), &sp, &cp);
             rotate_dir(s.u, s.v, s.w, ct, st, sp, cp);
@@ -1173,7 +1175,11 @@ __global__ void __launch_bounds__(256, SRC_MIN_BLOCKS) k_source(Args A, PlanDev 
         const uint32_t o0 = list_off[slice], o1 = list_off[slice + 1];
         n_runs = o1 >= o0 ? o1 - o0 : 0u;
         lbase = o0;
-        if ((uint64_t)n_runs * BATCH_BLOCK > n && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(A.err, PSL_DEV_ERR_QUEUE);
+        // every block but the window's first and last is whole: more of them
+        // than the pass holds is an overflow (the primary queue's own check
+        // catches the rest)
+        if (n_runs > 2u && (uint64_t)(n_runs - 2u) * BATCH_BLOCK > n && blockIdx.x == 0 && threadIdx.x == 0)
+            atomicOr(A.err, PSL_DEV_ERR_QUEUE);
     } else {
         n_runs = (n + SRC_RUN - 1) / SRC_RUN;
     }
