@@ -471,8 +471,9 @@ def measure(c, w, steps, warmup, with_e2e, with_t1pct, with_plain, profile=False
 
 def conv_only(args):
     """Only the tensor-core convolution of the denoiser on an n^3 volume,
-    ci -> co channels (random BF16 data): two calls, then the median of
-    four timed calls (for profiling one launch of its kernel)."""
+    ci -> co channels (random BF16 data): two calls, then `steps` calls
+    timed on the device with the library's events (for profiling one launch
+    of its kernel)."""
     import torch
     from paper_1302_1861_b300 import capi
     n, ci, co = args.conv
@@ -480,19 +481,16 @@ def conv_only(args):
     wt = torch.randn(27 * ci * co, device="cuda") * 0.05
     wpk = capi.conv3d_pack(wt, ci, co)
     out = torch.empty(n ** 3 * co, dtype=torch.bfloat16, device="cuda")
-    ts = []
-    for it in range(2 + args.steps):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+    for it in range(2):                                   # warm-up
         capi.conv3d(x.view(torch.int16), ci, wpk, None, co, n, n, n, True, out.view(torch.int16))
-        e1.record()
-        torch.cuda.synchronize()
-        if it >= 2:
-            ts.append(e0.elapsed_time(e1) / 1e3)
-    t = float(np.median(ts)) if ts else float("nan")
+    capi.profile(True)
+    for it in range(max(args.steps, 1)):
+        capi.conv3d(x.view(torch.int16), ci, wpk, None, co, n, n, n, True, out.view(torch.int16))
+    ms, cnt = capi.profile_read()["conv3d"]
+    capi.profile(False)
+    t = ms / 1e3 / max(cnt, 1)
     fl = 2.0 * n ** 3 * 27 * ci * co
-    print(json.dumps({"conv": f"{n}^3 x {ci}->{co}", "ms": 1e3 * t, "tflops": fl / t / 1e12}))
+    print(json.dumps({"conv": f"{n}^3 x {ci}->{co}", "ms": 1e3 * t, "tflops": fl / t / 1e12, "launches": cnt}))
 
 
 # --------------------------------------------------------------------------
@@ -674,23 +672,22 @@ def denoised_run(capi, torch, flush, peaks, measured_1pct=None):
     wt = torch.randn(27 * ci * co, device="cuda") * 0.05
     wpk = capi.conv3d_pack(wt, ci, co)
     out = torch.empty(V * co, dtype=torch.bfloat16, device="cuda")
-    ts = []
-    for it in range(6):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+    for it in range(2):                                   # warm-up
         capi.conv3d(x.view(torch.int16), ci, wpk, None, co, 128, 128, 128, True, out.view(torch.int16))
-        e1.record()
-        torch.cuda.synchronize()
-        if it >= 2:
-            ts.append(e0.elapsed_time(e1) / 1e3)
-    t_conv = float(np.median(ts))
+    capi.profile(True)
+    for it in range(4):
+        flush.fill_(1.0)
+        capi.conv3d(x.view(torch.int16), ci, wpk, None, co, 128, 128, 128, True, out.view(torch.int16))
+    ms_conv, n_conv = capi.profile_read()["conv3d"]
+    capi.profile(False)
+    t_conv = ms_conv / 1e3 / max(n_conv, 1)
     fl = 2.0 * V * 27 * ci * co
     pk = peaks[0].get("bf16_tflops") if isinstance(peaks[0], dict) else None
     conv = {"shape": "128^3 x 128->128, 3x3x3", "flop": fl, "ms": 1e3 * t_conv, "tflops": fl / t_conv / 1e12,
             "peak_tflops": pk, "frac": (fl / t_conv / 1e12 / pk) if pk else None,
-            "peak_kind": f"bf16_tflops ({peaks[1]})", "note": "psl_conv3d call: includes its host synchronisation"}
+            "peak_kind": f"bf16_tflops ({peaks[1]}, burst: the kernel is timed alone)",
+            "note": "device time of the kernel launch (the library's CUDA events on its stream), L2 flushed "
+                    "before each of 4 launches"}
     # inference on a full 128^3 volume
     n = 128
     dose = torch.rand(n ** 3, device="cuda")

@@ -550,9 +550,10 @@ PSL_API void psl_tally_destroy(psl_tally_t *tally);
  * each kernel is launched on.  psl_profile(1) clears the totals and starts
  * recording, psl_profile(0) stops; psl_profile_read returns, for kernel
  * index 0 <= k < PSL_NK (key, onesweep, gather, source, photon, electron,
- * band_sort, readout), the summed device time in ms, the launches timed and
- * the kernel's name (static string).  Reading waits for the recorded events. */
-#define PSL_NK 8
+ * band_sort, readout, conv3d: the denoiser's convolutions), the summed
+ * device time in ms, the launches timed and the kernel's name (static
+ * string).  Reading waits for the recorded events. */
+#define PSL_NK 9
 PSL_API int psl_profile(int enable);
 PSL_API int psl_profile_read(int32_t kernel, double *total_ms, int64_t *launches, const char **name);
 

@@ -185,7 +185,7 @@ def kernel_launches() -> int:
     return int(lib().psl_kernel_launches())
 
 
-PSL_NK = 8
+PSL_NK = 9
 
 
 def atomic_peak(n_cells: int, n_updates: int = 1 << 30, stream=None) -> float:

@@ -128,7 +128,8 @@ extern "C" void psl_physics_default(psl_physics_t *out) {
 #include <vector>
 
 namespace {
-const char *K_NAMES[PSL_NK] = {"key", "onesweep", "gather", "source", "photon", "electron", "band_sort", "readout"};
+const char *K_NAMES[PSL_NK] = {"key", "onesweep", "gather", "source", "photon", "electron", "band_sort", "readout",
+                               "conv3d"};
 struct TimerState {
     std::mutex mu;
     bool on = false;

@@ -598,8 +598,24 @@ int psl_conv3d_wgrad_run(const __nv_bfloat16 *x, int ci, const __nv_bfloat16 *gy
 
 static int g_conv_form = 0;             // 0: TMA form where the volume allows, 1: gather form only
 
+static int conv3d_dispatch(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, const float *bias, int co,
+                           int nx, int ny, int nz, int relu, __nv_bfloat16 *out, float *out_f32, uint32_t *err,
+                           cudaStream_t st);
+
+// the convolution, timed (device time, CUDA events on its stream) while the
+// library's profiler is on
 int psl_conv3d_run(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, const float *bias, int co, int nx,
                    int ny, int nz, int relu, __nv_bfloat16 *out, float *out_f32, uint32_t *err, cudaStream_t st) {
+    void *tk = nullptr;
+    if (psl_timer_on()) psl_timer_begin(PK_CONV, st, &tk);
+    const int rc = conv3d_dispatch(in, ci, wpk, bias, co, nx, ny, nz, relu, out, out_f32, err, st);
+    if (tk) psl_timer_end(PK_CONV, st, tk);
+    return rc;
+}
+
+static int conv3d_dispatch(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, const float *bias, int co,
+                           int nx, int ny, int nz, int relu, __nv_bfloat16 *out, float *out_f32, uint32_t *err,
+                           cudaStream_t st) {
     ConvArgs a{in, wpk, bias, out, out_f32, ci, nz, ny, nx, relu, psl_conv_ksteps(ci), err};
     const int64_t V = (int64_t)nx * ny * nz;
     if (V == 0) return PSL_OK;

@@ -23,7 +23,7 @@ int psl_fail(int code, const std::string &msg);
 #define PSL_CHECK_LAUNCH(name) PSL_CUDA(cudaGetLastError())
 
 // opt-in event timing of the main kernels (psl_profile)
-enum { PK_KEY = 0, PK_ONESWEEP, PK_GATHER, PK_SOURCE, PK_PHOTON, PK_ELECTRON, PK_BAND, PK_READOUT };
+enum { PK_KEY = 0, PK_ONESWEEP, PK_GATHER, PK_SOURCE, PK_PHOTON, PK_ELECTRON, PK_BAND, PK_READOUT, PK_CONV };
 bool psl_timer_on();
 
 // failure-detection hooks (psl_debug_waits): polls of a bounded wait (dflt
