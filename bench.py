@@ -623,17 +623,20 @@ def main():
         dist.destroy_process_group()
 
 
-# Per-event figures of the transport kernels measured with ncu on the 1e7-
-# history case of this workload (all launches of one run; the counts scale
-# with histories): thread instructions per event (smsp__thread_inst_executed
-# / events) and DRAM bytes per history (dram__bytes_read + write), from
-#   ncu --metrics smsp__thread_inst_executed.sum,dram__bytes_read.sum,...
-#       -k regex:"k_electron|k_photon" python bench.py --histories 10000000 ...
+# Per-event figures of the transport kernels, measured with ncu on one step
+# of the headline workload (every k_photon / k_electron launch of the step,
+# smsp__thread_inst_executed.sum over the step's Woodcock / electron steps;
+# dram__bytes_read.sum + dram__bytes_write.sum per history, also for the
+# source kernel):
+#   ncu --metrics smsp__thread_inst_executed.sum,smsp__inst_executed.sum,gpu__time_duration.sum
+#       -k regex:"k_electron|k_photon" python bench.py --steps 1 --warmup 0 --no-...
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       -k regex:"k_electron|k_photon|k_source" (the same command)
 # They hold for the kernels they were measured on; re-measure after changing
 # the kernels.
-THREAD_INST_PER_ELECTRON_STEP = 587.4
-THREAD_INST_PER_WOODCOCK_STEP = 529.5
-DRAM_BYTES_PER_HISTORY = {"electron": 28.28, "photon": 58.89}
+THREAD_INST_PER_ELECTRON_STEP = 606.6
+THREAD_INST_PER_WOODCOCK_STEP = 414.9
+DRAM_BYTES_PER_HISTORY = {"electron": 23.2, "photon": 57.2, "source": 71.4}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
 
@@ -938,8 +941,9 @@ def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kin
         else:
             byts = 0.0
         ach = byts / per_launch_s / 1e9
+        traffic = DRAM_BYTES_PER_HISTORY[name] * per_rank / per_step if name in DRAM_BYTES_PER_HISTORY else None
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "peak_kind": pk_kind, "launches": launches}
+                "traffic": traffic, "peak_kind": pk_kind, "launches": launches}
     # transport: events per second against the instruction-issue speed of light
     per_step = max(launches // max(steps, 1), 1)
     if name == "electron":
@@ -963,7 +967,8 @@ def roofline_for(name, per_launch_s, launches, steps, w, per_rank, peaks, pk_kin
             "events_per_launch": events / per_step,
             "peak_kind": "derived: 148 SMs x 4 issue/clk x 32 lanes x 2.032 GHz / %.1f thread instructions "
                          "per event (ncu)" % ipe,
-            "traffic_kind": "ncu dram bytes on the 1e7-history case scaled to the launch's histories"}
+            "traffic_kind": "ncu dram bytes of all the kernel's launches in one step of this workload, "
+                            "per history, times the histories per launch"}
 
 
 if __name__ == "__main__":

@@ -61,6 +61,9 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #ifndef PSL_DEP_COMBINE
 #define PSL_DEP_COMBINE 0              // 1: an electron sums its consecutive deposits into one voxel in
 #endif                                 //    registers and adds them with one atomic when it leaves the voxel
+#ifndef PSL_PHOTON_MIN_BLOCKS
+#define PSL_PHOTON_MIN_BLOCKS 4        // resident 256-thread photon blocks per SM (register cap 64)
+#endif
 #ifndef PSL_TRANSPORT_MIN_BLOCKS
 #define PSL_TRANSPORT_MIN_BLOCKS 4     // resident 256-thread blocks per SM (register cap 64)
 #endif
@@ -662,7 +665,7 @@ __device__ __forceinline__ void slot_load(const uint32_t *s, Photon &g) {
     g.tf = __uint_as_float(s[16]); g.chan = s[17];
 }
 
-__global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
+__global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
                                                 uint32_t cap, uint32_t *head) {
     __shared__ FeedSmem sm;
     __shared__ uint32_t bh[NBANDS];
@@ -1762,7 +1765,9 @@ struct Runner {
         cudaMemsetAsync(w->cnt + 5, 0, 4, st);
         void *tk = nullptr;
         tb(PK_PHOTON, &tk);
-        k_photon<<<gt(), 256, 0, st>>>(a2, src, nptr, nfix, cap, w->cnt + 5); PSL_NOTE_LAUNCH();
+        // (a persistent grid: no more blocks than stay resident)
+        const int gp = gen_now >= 2 ? psl_sm_count() : psl_sm_count() * std::min(tally->grid_mult, PSL_PHOTON_MIN_BLOCKS);
+        k_photon<<<gp, 256, 0, st>>>(a2, src, nptr, nfix, cap, w->cnt + 5); PSL_NOTE_LAUNCH();
         te(PK_PHOTON, tk);
     }
     void electron_pass() {
