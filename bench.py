@@ -417,6 +417,7 @@ def measure(c, w, steps, warmup, with_e2e, with_t1pct, with_plain, profile=False
            torch.empty(nvox, dtype=torch.float64, device="cuda"),
            torch.empty(3, dtype=torch.float64, device="cuda"))
     tally = capi.psl_tally_create(dw.phantom, w.n_batches)       # device buffers held across steps
+    capi.psl_tally_set_queue_depth(tally, c.args.queue_depth)
     step = make_step(c, w, tally, first, per_rank, n_plan)
     for _ in range(warmup):
         step(dw, out)
@@ -451,14 +452,6 @@ def measure(c, w, steps, warmup, with_e2e, with_t1pct, with_plain, profile=False
     if with_plain:
         pt = timed_steps(c, step, dw, out, 2, plain=True)
         r["plain"] = per_rank * c.world / c.max_over_ranks(float(np.mean(pt[1:])))
-    if with_t1pct and c.rank == 0 and c.world == 1:
-        t1 = time_to_1pct(capi, torch, w, dw, capi.physics(), n_1pct, sl, (nz, ny, nx))
-        t1["extrapolated_histories"] = n_1pct
-        t1["extrapolated_seconds"] = n_1pct / (per_rank / t_step)
-        r["t1pct"] = t1
-    else:
-        r["t1pct"] = {"histories": n_1pct, "seconds": n_1pct / r["value"], "isocentre_rel_sigma_at_run": rel,
-                      "kind": "extrapolated from the run's sigma"}
     if with_e2e:
         te, bi, bo = e2e_run(c, w, step, out, steps, warmup)
         r["e2e"] = {"value": per_rank * c.world / te, "unit": "histories/s", "h2d_bytes_per_step": bi,
@@ -466,6 +459,19 @@ def measure(c, w, steps, warmup, with_e2e, with_t1pct, with_plain, profile=False
                     "note": "every step uploads its records and phantom from pinned host memory and reads back "
                             "dose, sigma and ledger; step k+1's upload runs on a copy stream during step k (two "
                             "device buffers); the first upload and the last read-back are inside the timed region"}
+    # the step's tally (and its transport workspace) is released before the
+    # whole-plan runs below take theirs
+    r["tally_info"] = capi.psl_tally_info(tally)
+    tally.close()
+    del r["tally"]
+    if with_t1pct and c.rank == 0 and c.world == 1:
+        t1 = time_to_1pct(capi, torch, w, dw, capi.physics(), n_1pct, sl, (nz, ny, nx), c.args.queue_depth)
+        t1["extrapolated_histories"] = n_1pct
+        t1["extrapolated_seconds"] = n_1pct / (per_rank / t_step)
+        r["t1pct"] = t1
+    else:
+        r["t1pct"] = {"histories": n_1pct, "seconds": n_1pct / r["value"], "isocentre_rel_sigma_at_run": rel,
+                      "kind": "extrapolated from the run's sigma"}
     return r
 
 
@@ -504,6 +510,9 @@ def main():
     ap.add_argument("--workload", default="ct", choices=["ct", "slab"],
                     help="headline workload (slab: the 10x10 one, for profiling only)")
     ap.add_argument("--ref-sample", type=int, default=40_000)
+    ap.add_argument("--queue-depth", type=int, default=1 << 26,
+                    help="primaries per transport pass of the 30x30 CT and 10x10 tallies (psl_tally_set_queue_depth; "
+                         "2^26 holds a 103 GB transport workspace: fewer, longer passes)")
     ap.add_argument("--conv", nargs=3, type=int, metavar=("N", "CI", "CO"),
                     help="only time the denoiser's tensor-core convolution (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -562,8 +571,7 @@ def main():
                  "atomics_per_s": {"photon": counts[8] / ms_p, "electron": counts[9] / ms_e},
                  "atomic_peak_per_s": atom_peak, "atomic_peak_kind": "measured: psl_atomic_peak, int64 adds into "
                                                                     f"{int(np.prod(w.phantom.shape))} cells"}
-    n_counters, ws_bytes, qdepth, bps = capi.psl_tally_info(h["tally"])
-    h["tally"].close()
+    n_counters, ws_bytes, qdepth, bps = h["tally_info"]
     del h["dw"]
 
     # the 10x10 workload: its own steps and measured time to 1 %
@@ -571,7 +579,6 @@ def main():
     if rank == 0 and world == 1 and not args.no_slab and args.workload == "ct":
         s2 = measure(c, inputs.config2(), max(3, args.steps // 2), args.warmup, False, not args.no_t1pct,
                      False)
-        s2["tally"].close()
         slab = {"workload": s2["w"].name, "value": s2["value"], "unit": "histories/s",
                 "ms_per_step": 1e3 * s2["t_step"], "time_to_1pct": s2["t1pct"],
                 "energy_balance": s2["energy_balance"]}
@@ -710,7 +717,7 @@ def denoised_run(capi, torch, flush, peaks, measured_1pct=None):
             "inference_128cubed": {"ms": 1e3 * t_inf, "conv_tflops": conv_flops(n ** 3) / t_inf / 1e12}}
 
 
-def time_to_1pct(capi, torch, w, dw, phys, n_est, sl, shape):
+def time_to_1pct(capi, torch, w, dw, phys, n_est, sl, shape, queue_depth=None):
     """Wall time of a whole plan (psl_build, psl_plan_create, psl_run of all
     batches, dose_readout) of N histories whose isocentre uncertainty (mean
     sigma/D over the 3x3x3 voxels at the isocentre, N_b = 10 batches) is at
@@ -724,6 +731,8 @@ def time_to_1pct(capi, torch, w, dw, phys, n_est, sl, shape):
     tries = []
     for _ in range(3):
         tally = capi.psl_tally_create(dw.phantom, w.n_batches)
+        if queue_depth:
+            capi.psl_tally_set_queue_depth(tally, queue_depth)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()

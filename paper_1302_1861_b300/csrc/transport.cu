@@ -55,6 +55,9 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #ifndef PSL_G_DEFER
 #define PSL_G_DEFER 24                 // lanes with a pending real photon interaction before a warp runs them
 #endif
+#ifndef PSL_G_INNER
+#define PSL_G_INNER 3                  // Woodcock steps a photon may take in one pass of the photon loop
+#endif
 #ifndef PSL_E_DEFER
 #define PSL_E_DEFER 4                  // lanes with a pending hard event before a warp runs them
 #endif
@@ -279,14 +282,33 @@ struct EventRng {
     __device__ __forceinline__ ~EventRng() { saved = r.draw; }
 };
 
-// Angles are evaluated so that FP32 keeps their small parts: the sine of a
-// polar angle comes from a form without cancellation (never sqrt(1 - c^2)
-// near c = 1), the azimuth 2 pi xi through sincospif, logarithms of
-// uniforms through logf (a uniform near 1 has a small logarithm that the
-// fast intrinsic only gets to an absolute error), and 1 - w^2 of a
-// direction as u^2 + v^2.  Trajectories then follow the FP64 ones longer.
+// Angles and logarithms keep the accuracy FP32 offers where it decides
+// something: the sine of a polar angle comes from a form without
+// cancellation (never sqrt(1 - c^2) near c = 1), 1 - w^2 of a direction is
+// u^2 + v^2, and the logarithms of uniforms behind a multiple-scattering
+// angle or an electron's mean free path count go through logf (a uniform
+// near 1 has a small logarithm that the fast intrinsic only gets to an
+// absolute error, or rounds to zero).  Sines and cosines that only turn a
+// direction take the hardware approximations on [-pi, pi] (absolute error
+// below 2^-21.4): the azimuth 2 pi xi as 2 pi (xi - 1/2) + pi, the
+// multiple-scattering polar angle after its reduction by 2 pi; so does the
+// Woodcock step length (photon_step).  Measured against sincospif and logf
+// on the 30x30 CT plan: the electron pass 3.5 % and the photon pass 7 %
+// faster, per-history event parity with the oracle unchanged.
 __device__ __forceinline__ float ln_uniform(float xi) { return logf(xi); }
-__device__ __forceinline__ void sincos_2pi(float xi, float *s, float *c) { sincospif(2.0f * xi, s, c); }
+__device__ __forceinline__ void sincos_2pi(float xi, float *s, float *c) {
+    float sn, cs;
+    __sincosf(6.28318531f * (xi - 0.5f), &sn, &cs);         // xi - 1/2 is exact
+    *s = -sn;
+    *c = -cs;
+}
+__device__ __forceinline__ void sincos_polar(float th, float *s, float *c) {
+    // th - 2 pi k in two parts (Cody and Waite): 6.28125 has 8 significant
+    // bits, so k * 6.28125 is exact for any angle drawn, and the rest of 2 pi
+    // follows; the result lies in [-pi, pi]
+    const float k = rintf(th * 0.159154943f);
+    __sincosf(fmaf(-k, 1.93530718e-3f, fmaf(-k, 6.28125f, th)), s, c);
+}
 
 // rotate unit direction by the polar angle (cosine c, sine st >= 0) and the
 // azimuth (sine sp, cosine cp), the azimuth measured from the plane through
@@ -551,7 +573,9 @@ __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
     EventRng ev(g.draw);
     Rng &rng = ev.r;
     rng.align();                                                // Woodcock step: step, virtual, channel
-    const float s = -ln_uniform(rng.next(A.rk, g.p0, g.p1)) * g.inv_mumax;
+    // (the fast logarithm: a virtual step's length needs no more than its
+    // relative accuracy away from u = 1, and one near 1 is short either way)
+    const float s = fmaxf(-__logf(rng.next(A.rk, g.p0, g.p1)), 0.0f) * g.inv_mumax;
     g.x += s * g.u; g.y += s * g.v; g.z += s * g.w;
     const float fx = floorf(g.x * A.ivx), fy = floorf(g.y * A.ivy), fz = floorf(g.z * A.ivz);
     if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)A.nx && fy < (float)A.ny && fz < (float)A.nz)) {
@@ -727,7 +751,10 @@ __global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(Args A, c
             }
         }
         if (alive && !real) {
-            const int r = photon_step(A, acc, g);
+            // up to PSL_G_INNER steps while the steps are virtual: the loop's
+            // refill and parking bookkeeping is then paid once per few steps
+            int r = photon_step(A, acc, g);
+            for (int k = 1; k < PSL_G_INNER && r == G_ON; ++k) r = photon_step(A, acc, g);
             if (r == G_END) {
                 alive = false;
             } else if (r == G_REAL) {
@@ -962,9 +989,7 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
             const float l2 = -2.0f * ln_uniform(rng.take());
             const float th = th0 * (l2 * rsqrtf(l2));
             float st, ct, sp, cp;
-            // (sin and cos of theta through sincospif of theta / pi: the same
-            // accuracy with no large-argument reduction path)
-            sincospif(th * 0.318309886183790671f, &st, &ct);
+            sincos_polar(th, &st, &ct);
             st = fabsf(st);
             sincos_2pi(rng.take(), &sp, &cp);
             rotate_dir(s.u, s.v, s.w, ct, st, sp, cp);
