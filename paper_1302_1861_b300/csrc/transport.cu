@@ -428,6 +428,14 @@ __device__ __forceinline__ void flush_acc(const Args &A, const Acc &a, unsigned 
 #define FEED_WARPS 8                     // 256-thread blocks
 #define FEED_SPIN (1u << 22)
 
+// The particles a feed hands out: queue 1's n1 particles, then queue 2's n2,
+// as one index space in which queue 2 starts at n1 rounded up to a chunk
+// (claims are whole chunks, so none straddles the two queues)
+struct FeedSrc {
+    const Particle *p1, *p2;
+    uint32_t n1, n1p, n2;
+};
+
 struct FeedSmem {
     Particle buf[FEED_WARPS][2][FEED_CHUNK];
     unsigned long long bar[FEED_WARPS][2];
@@ -450,7 +458,7 @@ struct Feed {
         return &sm.buf[threadIdx.x >> 5][b][i];
     }
 
-    __device__ __forceinline__ void init(FeedSmem &sm, const Particle *src, uint32_t n, uint32_t *head, uint32_t *err,
+    __device__ __forceinline__ void init(FeedSmem &sm, const FeedSrc &src, uint32_t *head, uint32_t *err,
                                          uint32_t polls, bool stall) {
         st = 0;
         if ((threadIdx.x & 31) == 0) {
@@ -459,19 +467,23 @@ struct Feed {
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         __syncwarp();
-        set_cnt(0, claim(sm, 0, src, n, head));
+        set_cnt(0, claim(sm, 0, src, head));
         // (stall: a failure-detection test; no copy into buffer 1 is ever
         // issued, so its mbarrier never completes and the wait runs out)
-        set_cnt(1, claim(sm, 1, src, n, head, stall));
+        set_cnt(1, claim(sm, 1, src, head, stall));
         if (cnt(0)) wait(sm, 0, err, polls);
     }
     // claim the next chunk into buffer b; returns its particle count
-    __device__ __forceinline__ static uint32_t claim(FeedSmem &sm, uint32_t b, const Particle *src, uint32_t n,
+    __device__ __forceinline__ static uint32_t claim(FeedSmem &sm, uint32_t b, const FeedSrc &fs,
                                                      uint32_t *head, bool no_copy = false) {
         uint32_t base = 0;
         if ((threadIdx.x & 31) == 0) base = atomicAdd(head, (uint32_t)FEED_CHUNK);
         base = __shfl_sync(FULL, base, 0);
-        const uint32_t c = base < n ? min(n - base, (uint32_t)FEED_CHUNK) : 0u;
+        // (base is a multiple of the chunk, so base < n1p means base < n1)
+        const bool first = base < fs.n1p;
+        const uint32_t j = first ? base : base - fs.n1p, n = first ? fs.n1 : fs.n2;
+        const Particle *src = first ? fs.p1 : fs.p2;
+        const uint32_t c = j < n ? min(n - j, (uint32_t)FEED_CHUNK) : 0u;
         if (c && !no_copy && (threadIdx.x & 31) == 0) {
             const uint32_t bytes = c * (uint32_t)sizeof(Particle);
             const uint32_t mb = bar_addr(sm, b);
@@ -479,7 +491,7 @@ struct Feed {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mb), "r"(bytes) : "memory");
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         :: "r"(dst), "l"(src + base), "r"(bytes), "r"(mb) : "memory");
+                         :: "r"(dst), "l"(src + j), "r"(bytes), "r"(mb) : "memory");
         }
         return c;
     }
@@ -500,7 +512,7 @@ struct Feed {
     // true and fills p for a lane in `need` that got one; a lane in `need`
     // that got none finds the queue exhausted.
     __device__ __forceinline__ bool take(FeedSmem &sm, unsigned need, unsigned lt, bool mine, Particle &p,
-                                         const Particle *src, uint32_t n, uint32_t *head, uint32_t *err,
+                                         const FeedSrc &src, uint32_t *head, uint32_t *err,
                                          uint32_t polls, bool stall) {
         const uint32_t k = __popc(need), rank = __popc(need & lt);
         const uint32_t c = cur(), nx = c ^ 1u, avail = cnt(c) - pos();
@@ -522,7 +534,7 @@ struct Feed {
             __syncwarp();                               // every lane has read it
             const uint32_t np = min(k - avail, cn);
             st = (st & ~((63u << 12) | (1u << 18))) | (np << 12) | (nx << 18);
-            set_cnt(c, cn ? claim(sm, c, src, n, head, stall && c == 1u) : 0u);   // a short chunk: queue exhausted
+            set_cnt(c, cn ? claim(sm, c, src, head, stall && c == 1u) : 0u);   // a short chunk: queue exhausted
         } else {
             st += k << 12;
         }
@@ -690,7 +702,8 @@ __device__ __forceinline__ void slot_load(const uint32_t *s, Photon &g) {
 }
 
 __global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
-                                                uint32_t cap, uint32_t *head) {
+                                                uint32_t cap, uint32_t *head, const Particle *src2,
+                                                const uint32_t *n2_ptr, uint32_t cap2) {
     __shared__ FeedSmem sm;
     __shared__ uint32_t bh[NBANDS];
     __shared__ unsigned long long sled[NLEDGER];
@@ -702,13 +715,20 @@ __global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(Args A, c
     band_hist_init(bh);
     acc_init(sled);
     __syncthreads();
-    const uint32_t n = n_ptr ? min(*n_ptr, cap) : n_fixed;
+    // the photons of the pass: the primaries (or a first queue), then the
+    // secondaries carried over from the previous chunk (src2, may be null)
+    FeedSrc fs;
+    fs.p1 = src;
+    fs.n1 = n_ptr ? min(*n_ptr, cap) : n_fixed;
+    fs.n1p = (fs.n1 + FEED_CHUNK - 1) / FEED_CHUNK * FEED_CHUNK;
+    fs.p2 = src2;
+    fs.n2 = src2 ? min(*n2_ptr, cap2) : 0u;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     Acc acc = {0u, 0u, 0ull, 0ull};
     Photon g;
     Feed F;
-    F.init(sm, src, n, head, A.err, A.wait_polls, (A.dbg & PSL_DEBUG_FEED_STALL) != 0);
+    F.init(sm, fs, head, A.err, A.wait_polls, (A.dbg & PSL_DEBUG_FEED_STALL) != 0);
     bool alive = false, done = false, real = false;
     for (;;) {
 #if PSL_PHOTON_SLOTS
@@ -718,7 +738,7 @@ __global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(Args A, c
         if (need) {
             Particle p;
             const bool mine = !alive && !done;
-            const bool got = F.take(sm, need, lt, mine, p, src, n, head, A.err, A.wait_polls,
+            const bool got = F.take(sm, need, lt, mine, p, fs, head, A.err, A.wait_polls,
                                     (A.dbg & PSL_DEBUG_FEED_STALL) != 0);
             if (mine) {
                 if (!got) {
@@ -959,9 +979,8 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
     #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 float t;
-                if (d[k] > 0.0f) t = __fdividef((float)(ii[k] + 1) * vv[k] - p[k], d[k]);
-                else if (d[k] < 0.0f) t = __fdividef((float)ii[k] * vv[k] - p[k], d[k]);
-                else continue;
+                if (d[k] == 0.0f) continue;                // (the far face: ii + 1 moving up, ii moving down)
+                t = __fdividef((float)(ii[k] + (d[k] > 0.0f)) * vv[k] - p[k], d[k]);
                 t = fmaxf(t, 0.0f);
                 if (t < s_bound) { s_bound = t; axis = k; cross = d[k] > 0.0f ? 1 : -1; }
             }
@@ -1783,7 +1802,10 @@ struct Runner {
                                              Queue{w->Pos, w->cnt + 80, cap_q}); PSL_NOTE_LAUNCH();
         te(PK_BAND, tk);
     }
-    void photon_pass(const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap) {
+    // one photon pass over src (its count at nptr, else nfix) and, when src2
+    // is given, the photons of src2 (its count at n2ptr) after them
+    void photon_pass(const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap,
+                     const Particle *src2 = nullptr, const uint32_t *n2ptr = nullptr, uint32_t cap2 = 0) {
         Args a2 = A;
         a2.e_out = Queue{w->E[ec], cE(ec), cap_e};
         a2.p_out = Queue{w->P[pc ^ 1], cP(pc ^ 1), cap_p};
@@ -1792,7 +1814,7 @@ struct Runner {
         tb(PK_PHOTON, &tk);
         // (a persistent grid: no more blocks than stay resident)
         const int gp = gen_now >= 2 ? psl_sm_count() : psl_sm_count() * std::min(tally->grid_mult, PSL_PHOTON_MIN_BLOCKS);
-        k_photon<<<gp, 256, 0, st>>>(a2, src, nptr, nfix, cap, w->cnt + 5); PSL_NOTE_LAUNCH();
+        k_photon<<<gp, 256, 0, st>>>(a2, src, nptr, nfix, cap, w->cnt + 5, src2, n2ptr, cap2); PSL_NOTE_LAUNCH();
         te(PK_PHOTON, tk);
     }
     void electron_pass() {
@@ -1850,14 +1872,17 @@ struct Runner {
                                              tally->trace);
                 PSL_NOTE_LAUNCH();
                 te(PK_SOURCE, tk);
-                photon_pass(w->Q, w->cnt + 7, 0, cp);
+                // the chunk's primaries and the carried photons in one pass
+                if (carried) photon_pass(w->Q, w->cnt + 7, 0, cp, w->P[pc], cP(pc), cap_p);
+                else photon_pass(w->Q, w->cnt + 7, 0, cp);
             } else {
                 const uint32_t cp = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(J.nph - a0, chunk));
                 na = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(J.nel - a0, chunk));
                 ca = J.p + (J.cap - a0 - na);
-                if (cp) photon_pass(J.p + a0, nullptr, cp, cp);
+                if (cp && carried) photon_pass(J.p + a0, nullptr, cp, cp, w->P[pc], cP(pc), cap_p);
+                else if (cp) photon_pass(J.p + a0, nullptr, cp, cp);
+                else if (carried) photon_pass(w->P[pc], cP(pc), 0, cap_p);
             }
-            if (carried) photon_pass(w->P[pc], cP(pc), 0, cap_p);
             band_sort(ca, na);
             electron_pass();
             carried = true;
