@@ -483,6 +483,7 @@ def conv_only(args):
     import torch
     from paper_1302_1861_b300 import capi
     n, ci, co = args.conv
+    capi.conv3d_form(args.conv_form)
     x = torch.randn(n ** 3 * ci, device="cuda").to(torch.bfloat16)
     wt = torch.randn(27 * ci * co, device="cuda") * 0.05
     wpk = capi.conv3d_pack(wt, ci, co)
@@ -496,7 +497,8 @@ def conv_only(args):
     capi.profile(False)
     t = ms / 1e3 / max(cnt, 1)
     fl = 2.0 * n ** 3 * 27 * ci * co
-    print(json.dumps({"conv": f"{n}^3 x {ci}->{co}", "ms": 1e3 * t, "tflops": fl / t / 1e12, "launches": cnt}))
+    print(json.dumps({"conv": f"{n}^3 x {ci}->{co}", "form": args.conv_form, "ms": 1e3 * t, "tflops": fl / t / 1e12,
+                      "launches": cnt}))
 
 
 # --------------------------------------------------------------------------
@@ -515,6 +517,8 @@ def main():
                          "2^26 holds a 103 GB transport workspace: fewer, longer passes)")
     ap.add_argument("--conv", nargs=3, type=int, metavar=("N", "CI", "CO"),
                     help="only time the denoiser's tensor-core convolution (profiling)")
+    ap.add_argument("--conv-form", type=int, default=0, choices=[0, 1, 2],
+                    help="psl_conv3d_form for --conv: 0 halo/TMA (default), 1 gather, 2 per-tap TMA")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-imrt", action="store_true")

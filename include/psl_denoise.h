@@ -46,13 +46,17 @@ PSL_API int psl_conv3d(const uint16_t *in, int32_t ci, const uint16_t *wpk, cons
                        int32_t nx, int32_t ny, int32_t nz, int32_t relu, uint16_t *out, float *out_f32,
                        void *stream);
 
-/* Which form psl_conv3d (and the network) uses: 0 (default) the TMA form
- * wherever the volume allows (nx >= 128, or nx a power of two: the 128
- * voxels of a CTA are one box of the volume, loaded by the tensor memory
- * accelerator with its zero fill as the padding, warp-specialised copy /
- * MMA / epilogue roles over a 4-stage ring), else the gather form; 1 the
- * gather form everywhere (threads load the A rows; two-stage ring).  Both
- * give the same result. */
+/* Which form psl_conv3d (and the network) uses: 0 (default) the halo form
+ * where nx is a multiple of 128 and ci of 16 (a CTA's tiles are rows of 128
+ * voxels; per 16-channel chunk and tap plane one input plane with its
+ * one-voxel border is loaded by the tensor memory accelerator and the 9 taps
+ * of the plane read shifted views of it), else the per-tap TMA form where
+ * the volume allows (nx >= 128, or nx a power of two: the 128 voxels of a
+ * CTA are one box of the volume, one shifted box per tap; warp-specialised
+ * copy / MMA / epilogue roles, the copy engine's zero fill as the padding),
+ * else the gather form; 1 the gather form everywhere (threads load the A
+ * rows; two-stage ring); 2 as 0 without the halo form.  All give the same
+ * result (the same products, summed in FP32 in the tensor core's order). */
 PSL_API int psl_conv3d_form(int32_t form);
 
 /* The tap gradient of that convolution, on the tensor cores:

@@ -461,6 +461,147 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ C
     if (warp == 1) tc::tmem_dealloc(tmem, TCOLS);
 }
 
+// ------------------------------------------------------ halo form ---
+// For volumes whose rows hold whole 128-voxel tiles (W a multiple of 128)
+// and C_in a multiple of 16: a CTA's TT tiles are TT consecutive rows
+// (y0 .. y0 + TT - 1) of 128 voxels at one z.  For each 16-channel chunk c
+// of the input and each plane dz of the taps, one pipeline stage brings in
+// the input plane z0 + dz over the rows y0 - 1 .. y0 + TT and the columns
+// x0 - 1 .. x0 + 128 (two TMA boxes of 8 channels; the copy engine's zero
+// fill is the padding) and the 9 taps of that plane and chunk (9 packed K
+// steps, bulk copies).  The plane lands as rows of 16 bytes, so the A
+// operand of tap (dy, dx) for tile tt is a view of it: 128 rows starting at
+// row (tt + dy + 1) * 130 + dx + 1 (the no-swizzle K-major layout, 8-row
+// groups 128 bytes apart, the two 8-channel halves HALF bytes apart).  One
+// plane serves 9 x TT MMAs, where the per-tap form loads a shifted box for
+// every tap: a third of the input traffic from L2.  Warp roles and the
+// completion handshakes are those of the TMA form.
+constexpr int HX = BM + 2;                       // plane row: x0 - 1 .. x0 + 128
+constexpr int HST = 2;                           // stages
+
+__host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+template <int N> struct Halo {
+    static constexpr int TT = tiles_for(N);
+    static constexpr int HY = TT + 2;            // plane rows: y0 - 1 .. y0 + TT
+    static constexpr int HALF = round128(HY * HX * 16);      // one 8-channel half of a plane
+    static constexpr int A_ST = 2 * HALF;
+    static constexpr int B_ST = 9 * N * 32;      // 9 packed K steps
+    static constexpr int ST = round128(A_ST + B_ST);
+    static constexpr size_t SMEM = (size_t)HST * ST + 128;
+};
+
+struct HaloConvArgs {
+    const __nv_bfloat16 *wpk;
+    const float *bias;
+    __nv_bfloat16 *out;
+    float *out_f32;
+    int ci, D, H, W, relu;
+    uint32_t *err;
+};
+
+template <int N>
+__global__ void __launch_bounds__(192, 1) k_conv3d_halo(const __grid_constant__ CUtensorMap map, HaloConvArgs a) {
+    using G = Halo<N>;
+    constexpr int TT = G::TT;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr uint32_t TCOLS = TT * N < 32 ? 32 : TT * N;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + HST * G::ST);
+    uint64_t *empty = full + HST, *accum = empty + HST;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(accum + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int x0 = blockIdx.x * BM, y0 = blockIdx.y * TT, z0 = blockIdx.z;
+    if (warp == 1) { tc::tmem_alloc(tslot, TCOLS); tc::tmem_relinquish(); }
+    if (t == 0) {
+        for (int s = 0; s < HST; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        tc::mbar_init(accum, 1);
+        *abort_flag = 0;
+        tc::mbar_fence_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int nch = a.ci / 16;                       // 16-channel chunks
+    const int nit = 3 * nch;                         // stages: (chunk, plane)
+
+    if (warp == 0 && lane == 0) {                           // producer
+        for (int it = 0; it < nit && !*abort_flag; ++it) {
+            const int s = it % HST, c = it / 3, dz = it % 3;
+            const uint32_t ph = (uint32_t)(it / HST) & 1u;
+            if (!tc::mbar_wait(&empty[s], ph ^ 1u, WAIT_LIMIT)) { *abort_flag = 1; atomicOr(a.err, PSL_DEV_ERR_TIMEOUT); break; }
+            uint8_t *st = smem + s * G::ST;
+            const uint32_t fb = tc::smem_u32(&full[s]);
+            mbar_expect_tx(fb, (uint32_t)(2 * G::HY * HX * 16 + G::B_ST));       // the bytes the copies bring
+            tma_load_4d(tc::smem_u32(st), &map, 16 * c, x0 - 1, y0 - 1, z0 + dz - 1, fb);
+            tma_load_4d(tc::smem_u32(st + G::HALF), &map, 16 * c + 8, x0 - 1, y0 - 1, z0 + dz - 1, fb);
+            // tap (dz, j): packed K step tap * nch + c
+            for (int j = 0; j < 9; ++j)
+                bulk_load(tc::smem_u32(st + G::A_ST + j * N * 32), a.wpk + (size_t)((dz * 9 + j) * nch + c) * N * 16,
+                          (uint32_t)(N * 32), fb);
+        }
+    } else if (warp == 1 && lane == 0) {                    // MMA issuer
+        const uint32_t idesc = tc::idesc_bf16(BM, N);
+        for (int it = 0; it < nit && !*abort_flag; ++it) {
+            const int s = it % HST;
+            if (!tc::mbar_wait(&full[s], (uint32_t)(it / HST) & 1u, WAIT_LIMIT)) { *abort_flag = 1; atomicOr(a.err, PSL_DEV_ERR_TIMEOUT); break; }
+            tc::fence_after_sync();
+            const uint32_t base = tc::smem_u32(smem + s * G::ST);
+            for (int j = 0; j < 9; ++j) {
+                const int dy = j / 3 - 1, dx = j % 3 - 1;
+                const uint64_t bd = tc::desc_kmajor(base + G::A_ST + j * (N * 32), 128, 256);
+#pragma unroll
+                for (int tt = 0; tt < TT; ++tt) {
+                    const int row = (tt + dy + 1) * HX + dx + 1;
+                    const uint64_t ad = tc::desc_kmajor(base + row * 16, G::HALF, 128);
+                    tc::mma_bf16(tmem + (uint32_t)(tt * N), ad, bd, idesc, (it > 0 || j > 0) ? 1u : 0u);
+                }
+            }
+            tc::mma_commit(&empty[s]);
+        }
+        tc::mma_commit(accum);
+    } else if (warp >= 2) {                                  // epilogue
+        const bool ok = tc::mbar_wait(accum, 0u, WAIT_LIMIT) && !*abort_flag;
+        if (!ok && t == 64) { *abort_flag = 1; atomicOr(a.err, PSL_DEV_ERR_TIMEOUT); }
+        tc::fence_after_sync();
+        const int q = warp & 3;                              // TMEM lanes 32q..32q+31
+        for (int tt = 0; tt < TT && __any_sync(0xFFFFFFFFu, ok); ++tt) {
+            const int xx = x0 + 32 * q + lane, yy = y0 + tt;
+            const bool row_ok = ok && xx < a.W && yy < a.H;
+            const int64_t v = ((int64_t)z0 * a.H + yy) * a.W + xx;
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float r[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(tt * N + c0), r);
+                if (row_ok) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float qv = r[i] + (a.bias ? __ldg(a.bias + c0 + i) : 0.0f);
+                        r[i] = a.relu ? fmaxf(qv, 0.0f) : qv;
+                    }
+                    if (a.out) {
+                        __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(r[i]);
+                        uint4 *dst = reinterpret_cast<uint4 *>(a.out + v * N + c0);
+                        dst[0] = reinterpret_cast<uint4 *>(h)[0];
+                        dst[1] = reinterpret_cast<uint4 *>(h)[1];
+                    }
+                    if (a.out_f32) {
+                        float4 *dst = reinterpret_cast<float4 *>(a.out_f32 + v * N + c0);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) dst[i] = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, TCOLS);
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -519,6 +660,32 @@ int launch_tma(const ConvArgs &c, int bx, int by, int bz, cudaStream_t st) {
     TmaConvArgs a{c.wpk, c.bias, c.out, c.out_f32, c.ci, c.D, c.H, c.W, c.relu, c.ksteps, bx, by, bz, wide, c.err};
     const dim3 grid((c.W + bx - 1) / bx, (c.H + by - 1) / by, (c.D + bz - 1) / bz);
     k_conv3d_tma<N><<<grid, 192, smem, st>>>(map, a); PSL_NOTE_LAUNCH();
+    PSL_CUDA(cudaGetLastError());
+    return PSL_OK;
+}
+
+template <int N>
+int launch_halo(const ConvArgs &c, cudaStream_t st) {
+    using G = Halo<N>;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return psl_fail(PSL_ECUDA, "conv3d: cuTensorMapEncodeTiled unavailable");
+    CUtensorMap map;
+    const cuuint64_t dims[4] = {(cuuint64_t)c.ci, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.D};
+    const cuuint64_t strides[3] = {(cuuint64_t)c.ci * 2, (cuuint64_t)c.ci * 2 * c.W, (cuuint64_t)c.ci * 2 * c.W * c.H};
+    const cuuint32_t box[4] = {8u, (cuuint32_t)HX, (cuuint32_t)G::HY, 1u};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(c.in), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return psl_fail(PSL_ECUDA, "conv3d: tensor map encoding failed");
+    static bool attr = false;
+    if (!attr) {
+        PSL_CUDA(cudaFuncSetAttribute(k_conv3d_halo<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM));
+        attr = true;
+    }
+    HaloConvArgs a{c.wpk, c.bias, c.out, c.out_f32, c.ci, c.D, c.H, c.W, c.relu, c.err};
+    const dim3 grid((c.W + BM - 1) / BM, (c.H + G::TT - 1) / G::TT, c.D);
+    k_conv3d_halo<N><<<grid, 192, G::SMEM, st>>>(map, a); PSL_NOTE_LAUNCH();
     PSL_CUDA(cudaGetLastError());
     return PSL_OK;
 }
@@ -596,7 +763,7 @@ int psl_conv3d_wgrad_run(const __nv_bfloat16 *x, int ci, const __nv_bfloat16 *gy
     }
 }
 
-static int g_conv_form = 0;             // 0: TMA form where the volume allows, 1: gather form only
+static int g_conv_form = 0;             // 0: halo, else per-tap TMA, else gather; 1: gather only; 2: no halo
 
 static int conv3d_dispatch(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 *wpk, const float *bias, int co,
                            int nx, int ny, int nz, int relu, __nv_bfloat16 *out, float *out_f32, uint32_t *err,
@@ -620,7 +787,16 @@ static int conv3d_dispatch(const __nv_bfloat16 *in, int ci, const __nv_bfloat16 
     const int64_t V = (int64_t)nx * ny * nz;
     if (V == 0) return PSL_OK;
     int bx, by, bz;
-    if (g_conv_form == 0 && (co == 16 || co == 32 || co == 64 || co == 128) && tma_box(nx, ny, nz, tiles_for(co), bx, by, bz)) {
+    if (g_conv_form == 0 && nx % BM == 0 && ci % 16 == 0 && nz <= 65535 && ny <= 65535) {
+        switch (co) {
+            case 16: return launch_halo<16>(a, st);
+            case 32: return launch_halo<32>(a, st);
+            case 64: return launch_halo<64>(a, st);
+            case 128: return launch_halo<128>(a, st);
+            default: break;
+        }
+    }
+    if (g_conv_form != 1 && (co == 16 || co == 32 || co == 64 || co == 128) && tma_box(nx, ny, nz, tiles_for(co), bx, by, bz)) {
         switch (co) {
             case 16: return launch_tma<16>(a, bx, by, bz, st);
             case 32: return launch_tma<32>(a, bx, by, bz, st);
@@ -709,7 +885,8 @@ extern "C" int psl_conv3d_wgrad(const uint16_t *x, int32_t ci, const uint16_t *g
 }
 
 extern "C" int psl_conv3d_form(int32_t form) {
-    if (form != 0 && form != 1) return psl_fail(PSL_EINVAL, "psl_conv3d_form: 0 (TMA where possible) or 1 (gather)");
+    if (form < 0 || form > 2)
+        return psl_fail(PSL_EINVAL, "psl_conv3d_form: 0 (halo or TMA where possible), 1 (gather) or 2 (per-tap TMA)");
     g_conv_form = form;
     return PSL_OK;
 }

@@ -4,8 +4,9 @@ Both sides take the same BF16-rounded inputs and taps.  Bar: the FP32
 output within 2e-5 x (sum over k of |a_k b_k|) + 1e-6 of the oracle (FP32
 accumulation of up to 27 x 128 products); the BF16 output within one BF16
 rounding (2^-8 relative) of that.  Shapes cover every C_out (16, 32, 64,
-128), the 8-channel input layer, several pipeline stages and volumes whose
-voxel count is not a multiple of the 128-voxel tile.
+128), the 8-channel input layer, several pipeline stages, volumes whose
+voxel count is not a multiple of the 128-voxel tile, and rows of 128 and 256
+voxels (the halo form), each in every form of the kernel.
 """
 import numpy as np
 import pytest
@@ -44,7 +45,7 @@ def _run(x, w, b, relu, mirror=False):
             xin.float().cpu().numpy().astype(np.float64))
 
 
-@pytest.fixture(params=[0, 1], ids=["tma", "gather"])
+@pytest.fixture(params=[0, 1, 2], ids=["default", "gather", "per-tap-tma"])
 def form(request):
     capi.conv3d_form(request.param)
     yield request.param
@@ -55,7 +56,10 @@ def form(request):
                                          ((4, 9, 6), 32, 64), ((4, 4, 4), 64, 128), ((3, 5, 4), 128, 64),
                                          ((2, 3, 23), 128, 128), ((16, 16, 16), 32, 32), ((3, 5, 64), 16, 16),
                                          ((6, 4, 32), 64, 32), ((2, 2, 200), 16, 64), ((9, 3, 16), 128, 128),
-                                         ((4, 8, 8), 8, 16)])
+                                         ((4, 8, 8), 8, 16),
+                                         # rows of 128 voxels: the halo form (form 0) where C_in % 16 == 0
+                                         ((3, 5, 128), 16, 16), ((2, 3, 128), 128, 128), ((3, 3, 256), 32, 64),
+                                         ((2, 5, 128), 64, 32), ((2, 2, 128), 16, 128), ((2, 3, 128), 8, 16)])
 def test_conv_forward_matches_oracle(shape, ci, co, form):
     rng = np.random.default_rng(ci * 1000 + co)
     x = rng.normal(size=shape + (ci,)).astype(np.float32)
@@ -72,12 +76,14 @@ def test_conv_forward_matches_oracle(shape, ci, co, form):
         assert np.all(np.abs(ob - of) <= 2.0 ** -8 * np.abs(of) + 1e-30)
 
 
-@pytest.mark.parametrize("ci,co", [(16, 16), (16, 32), (32, 64), (64, 128), (128, 64)])
-def test_mirrored_taps_give_the_input_gradient(ci, co, form):
+@pytest.mark.parametrize("ci,co,vol", [(16, 16, (5, 6, 8)), (16, 32, (5, 6, 8)), (32, 64, (5, 6, 8)),
+                                       (64, 128, (5, 6, 8)), (128, 64, (5, 6, 8)), (32, 64, (2, 3, 128)),
+                                       (128, 16, (2, 2, 128))])
+def test_mirrored_taps_give_the_input_gradient(ci, co, vol, form):
     """psl_conv3d with the mirrored packing of w, applied to an output
     gradient, is the oracle's input gradient."""
     rng = np.random.default_rng(7 + ci + co)
-    gy = rng.normal(size=(5, 6, 8, co)).astype(np.float32)
+    gy = rng.normal(size=vol + (co,)).astype(np.float32)
     w = rng.normal(0, 0.2, size=(27, ci, co)).astype(np.float32)
     wq = _bf16(w).float().numpy().astype(np.float64)
     ob, of, gq = _run(gy, w, None, False, mirror=True)
