@@ -887,7 +887,7 @@ def imrt_run(capi, engine, inputs, torch, records=None):
     tally.close(); plan.close(); store.close()
     # measured: a whole plan of N histories (psl_build to dose_readout, no
     # graph), N from the sigma above, raised until the criterion holds
-    t1 = time_to_1pct(capi, torch, w, dw, phys, n1, sl, (nz, ny, nx))
+    t1 = time_to_1pct(capi, torch, w, dw, phys, n1, sl, (nz, ny, nx), tuned_depth)
     return {"workload": w.name, "segments": len(w.beams), "psl_entries": n_entries, "histories": w.n_histories,
             "seconds_per_plan": t, "histories_per_s": rate, "launch": "one CUDA graph (psl_run, use_graph=1)",
             "autotuned": {"blocks_per_sm": tuned_grid, "queue_depth": tuned_depth, "probe_histories": 20_000_000,

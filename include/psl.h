@@ -392,8 +392,8 @@ PSL_API int psl_tally_buffers(psl_tally_t *tally, int64_t **tallies, int64_t **l
 
 /* Sizes of a tally (host outputs, NULL to skip): its int64 counters
  * (n_batches x voxels, the array of psl_tally_buffers); the device bytes of its transport workspace (0 until the first
- * transport call sizes it: particle queues of 32 x 48 bytes per primary of
- * a pass, i.e. 1536 bytes x the queue depth when a call runs at least that
+ * transport call sizes it: particle queues of 33 x 48 bytes per primary of
+ * a pass, i.e. 1584 bytes x the queue depth when a call runs at least that
  * many histories, else x the call's histories; plus 4 bytes per voxel and
  * the batch-order buffers); the queue depth (primaries per transport pass)
  * and the persistent grid (256-thread blocks per SM) later calls use. */
@@ -402,7 +402,7 @@ PSL_API int psl_tally_info(const psl_tally_t *tally, int64_t *n_counters, int64_
 
 /* Set the queue depth (primaries per transport pass, 2^12 <= depth <= 2^26;
  * default 2^24) of later transport calls on the tally: the bound on its
- * transport workspace (1536 bytes per primary of a pass), for callers that
+ * transport workspace (1584 bytes per primary of a pass), for callers that
  * share the device.  A workspace sized for a larger depth is kept until the
  * tally is destroyed.  PSL_EINVAL outside the range. */
 PSL_API int psl_tally_set_queue_depth(psl_tally_t *tally, int64_t depth);
@@ -473,10 +473,13 @@ PSL_API int transport_trace(const psl_phantom_t *phantom, const psl_physics_t *p
 PSL_API int psl_run(const psl_plan_t *plan, const psl_phantom_t *phantom, const psl_physics_t *physics,
                     psl_tally_t *tally, int64_t first, int64_t n, int32_t use_graph, void *stream);
 
-/* Autotuner for psl_run: times n_probe histories of the plan with each
+/* Autotuner for psl_run: times the plan's first histories with each
  * candidate persistent-grid size (2, 3, 4, 6 blocks of 256 threads per SM)
- * and queue depth (2^21 ... 2^24 primaries per transport pass), keeps the
- * fastest in the tally (used by later transport calls on it), clears the
+ * and queue depth (2^21 ... 2^26 primaries per transport pass; depths above
+ * the plan's histories, or whose workspace would take more than 80 % of the
+ * free device memory, are skipped), each on max(n_probe, 2 x depth)
+ * histories (capped at the plan's), keeps the fastest in histories per
+ * second in the tally (used by later transport calls on it), clears the
  * tally, and returns the choice (host outputs, may be NULL). */
 PSL_API int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *phantom, const psl_physics_t *physics,
                          psl_tally_t *tally, int64_t n_probe, int32_t *blocks_per_sm, int64_t *queue_depth,

@@ -1525,6 +1525,10 @@ void workspace_free(Workspace *w) {
     delete w;
 }
 
+// Queue bytes per primary of a pass: photons 2 x 3, electrons 2 x 8, the
+// regrouped electrons 9, the primary photons 1 and the positrons 1 particles
+constexpr int64_t WORKSPACE_BYTES_PER_PRIMARY = 33 * (int64_t)sizeof(Particle);
+
 // Device bytes a workspace holds: the particle queues (photons 2 x cap_p,
 // electrons 2 x cap_e, the regrouped electrons cap_s, the primary photons
 // one chunk), the packed densities and the batch-order buffers.
@@ -2200,8 +2204,17 @@ extern "C" int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *ph, con
     n_probe = std::min<int64_t>(n_probe, plan->n_histories);
     cudaStream_t st = as_stream(stream_);
     const int grids[] = {2, 3, 4, 6};
-    const int64_t depths[] = {1 << 21, 1 << 22, 1 << 23, 1 << 24};
-    float best = 1e30f;
+    const int64_t depths[] = {1 << 21, 1 << 22, 1 << 23, 1 << 24, 1 << 25, 1 << 26};
+    // A pass ends with a tail in which lanes run out of particles, so a
+    // depth is timed on at least two passes of its own (a probe shorter than
+    // a pass would hide the tail that a deeper queue pays less often), and
+    // the candidates compare histories per second.  Depths whose workspace
+    // would take more than 80 % of the free device memory (or exceed the
+    // plan's histories) are not tried.
+    size_t free_b = 0, total_b = 0;
+    PSL_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const int64_t held = workspace_bytes_of(tally->ws);
+    double best = 0.0;
     int bg = tally->grid_mult;
     int64_t bd = tally->chunk_cap;
     cudaEvent_t a, b;
@@ -2209,19 +2222,23 @@ extern "C" int psl_autotune(const psl_plan_t *plan, const psl_phantom_t *ph, con
     cudaEventCreate(&b);
     for (int gi : grids) {
         for (int64_t d : depths) {
-            if (d > 2 * n_probe && d != depths[0]) continue;
+            if (d != depths[0] && (d > plan->n_histories ||
+                                   (double)d * WORKSPACE_BYTES_PER_PRIMARY > 0.8 * (double)(free_b + held)))
+                continue;
+            const int64_t np = std::min<int64_t>(plan->n_histories, std::max<int64_t>(n_probe, 2 * d));
             tally->grid_mult = gi;
             tally->chunk_cap = d;
             cudaEventRecord(a, st);
             Runner R;
-            rc = run_body(plan, ph, phys, tally, 0, n_probe, st, false, R);
+            rc = run_body(plan, ph, phys, tally, 0, np, st, false, R);
             if (!rc) rc = R.finish();
             cudaEventRecord(b, st);
             if (rc) break;
             cudaEventSynchronize(b);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a, b);
-            if (ms < best) { best = ms; bg = gi; bd = d; }
+            const double rate = (double)np / std::max(ms, 1e-3f);
+            if (rate > best) { best = rate; bg = gi; bd = d; }
         }
         if (rc) break;
     }
