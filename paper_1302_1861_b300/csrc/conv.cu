@@ -476,12 +476,21 @@ __global__ void __launch_bounds__(192, 1) k_conv3d_tma(const __grid_constant__ C
 // plane serves 9 x TT MMAs, where the per-tap form loads a shifted box for
 // every tap: a third of the input traffic from L2.  Warp roles and the
 // completion handshakes are those of the TMA form.
+#ifndef PSL_HALO_TILES_WIDE
+#define PSL_HALO_TILES_WIDE 4                    // 128-voxel rows per CTA for C_out = 128 (all 512 TMEM columns)
+#endif
+#ifndef PSL_HALO_TILES_64
+#define PSL_HALO_TILES_64 2                      // the same for C_out = 64
+#endif
+#ifndef PSL_HALO_STAGES
+#define PSL_HALO_STAGES 2
+#endif
 constexpr int HX = BM + 2;                       // plane row: x0 - 1 .. x0 + 128
-constexpr int HST = 2;                           // stages
+constexpr int HST = PSL_HALO_STAGES;             // stages
 
 __host__ __device__ constexpr int round128(int b) { return (b + 127) / 128 * 128; }
 template <int N> struct Halo {
-    static constexpr int TT = tiles_for(N);
+    static constexpr int TT = N == 128 ? PSL_HALO_TILES_WIDE : (N == 64 ? PSL_HALO_TILES_64 : tiles_for(N));
     static constexpr int HY = TT + 2;            // plane rows: y0 - 1 .. y0 + TT
     static constexpr int HALF = round128(HY * HX * 16);      // one 8-channel half of a plane
     static constexpr int A_ST = 2 * HALF;

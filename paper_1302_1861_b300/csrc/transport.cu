@@ -79,6 +79,7 @@ struct Tables {
     const float2 *rng;         // [2][NT] CSDA range R (g/cm^2) and dR/dlnT * dlnT at each node
     const float *irng;         // [2][NT] ln T at uniform steps of ln R (inverse range)
     float lnE0, inv_dln;
+    float dln;                 // 1 / inv_dln, rounded to float (the node spacing in ln E)
     float lnR0[2], inv_dlnR[2];  // grid of each species' inverse range table
 };
 
@@ -120,6 +121,13 @@ struct Args {
     uint32_t *band_hist;      // band counts of the electrons queued for the next regrouping
     uint32_t wait_polls;      // polls of a bounded wait before it gives up
     uint32_t dbg;             // failure-detection stalls (PSL_DEBUG_*)
+};
+
+// The transport kernels' arguments with a compile-time switch for the
+// per-history record of transport_trace (tests): the production instances
+// (TR = false) compile without its checks and atomics.
+template <bool TR> struct ArgsT : Args {
+    static constexpr bool trace = TR;
 };
 
 // ----------------------------------------------------------- tables ------
@@ -253,22 +261,25 @@ __device__ __forceinline__ unsigned long long fixed_point(float e, float wt) {
     return (unsigned long long)__float2ll_rn(__fmul_rn(e, wt) * 4294967296.0f);
 }
 
-__device__ __forceinline__ void deposit(const Args &A, Acc &acc, uint32_t iv, float e, float wt, uint32_t root) {
+template <class AT>
+__device__ __forceinline__ void deposit(const AT &A, Acc &acc, uint32_t iv, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
     if (!q) return;
     atomicAdd(&A.tally[(uint64_t)(root >> ROOT_SLICE_SHIFT) * (uint64_t)A.nvox + iv], q);
     acc.atomics++;
-    if (A.hist_dep) atomicAdd(&A.hist_dep[root & ROOT_INDEX_MASK], q);
+    if (AT::trace && A.hist_dep) atomicAdd(&A.hist_dep[root & ROOT_INDEX_MASK], q);
 }
 
-__device__ __forceinline__ void escape(const Args &A, Acc &acc, float e, float wt, uint32_t root) {
+template <class AT>
+__device__ __forceinline__ void escape(const AT &A, Acc &acc, float e, float wt, uint32_t root) {
     unsigned long long q = fixed_point(e, wt);
     acc.esc += q;
-    if (A.hist_esc) atomicAdd(&A.hist_esc[root & ROOT_INDEX_MASK], q);
+    if (AT::trace && A.hist_esc) atomicAdd(&A.hist_esc[root & ROOT_INDEX_MASK], q);
 }
 
-__device__ __forceinline__ void count_event(const Args &A, uint32_t root) {
-    if (A.hist_events) atomicAdd(&A.hist_events[root & ROOT_INDEX_MASK], 1);
+template <class AT>
+__device__ __forceinline__ void count_event(const AT &A, uint32_t root) {
+    if (AT::trace && A.hist_events) atomicAdd(&A.hist_events[root & ROOT_INDEX_MASK], 1);
 }
 
 // An event's random draws: the particle's draw counter is loaded at the
@@ -369,7 +380,8 @@ __device__ __forceinline__ void band_hist_flush(const Args &A, const uint32_t *b
 }
 
 // a charged secondary: queued for transport, or deposited in place
-__device__ __forceinline__ void emit_charged(const Args &A, Acc &acc, Rng &rng, uint32_t *bh, uint32_t type, float T,
+template <class AT>
+__device__ __forceinline__ void emit_charged(const AT &A, Acc &acc, Rng &rng, uint32_t *bh, uint32_t type, float T,
                              float x, float y, float z, float u, float v, float w, float wt, uint32_t iv, uint32_t p0,
                              uint32_t p1, uint32_t &nchild, uint32_t root) {
     if (T > A.ecut && !(A.flags & PSL_PHYS_LOCAL_SECONDARIES)) {
@@ -580,7 +592,8 @@ __device__ __forceinline__ uint32_t photon_voxel(const Args &A, const Photon &g)
     return ((uint32_t)fz * (uint32_t)A.ny + (uint32_t)fy) * (uint32_t)A.nx + (uint32_t)fx;
 }
 
-__device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
+template <class AT>
+__device__ __forceinline__ int photon_step(const AT &A, Acc &acc, Photon &g) {
     acc.steps++;
     EventRng ev(g.draw);
     Rng &rng = ev.r;
@@ -611,7 +624,8 @@ __device__ __forceinline__ int photon_step(const Args &A, Acc &acc, Photon &g) {
 }
 
 // the real interaction drawn by the last step; returns false when the photon ends
-__device__ __forceinline__ bool photon_interact(const Args &A, Acc &acc, Photon &g, uint32_t *bh) {
+template <class AT>
+__device__ __forceinline__ bool photon_interact(const AT &A, Acc &acc, Photon &g, uint32_t *bh) {
     const uint32_t iv = photon_voxel(A, g);
     EventRng ev(g.draw);
     Rng &rng = ev.r;
@@ -701,7 +715,8 @@ __device__ __forceinline__ void slot_load(const uint32_t *s, Photon &g) {
     g.tf = __uint_as_float(s[16]); g.chan = s[17];
 }
 
-__global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
+template <bool TR>
+__global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(ArgsT<TR> A, const Particle *src, const uint32_t *n_ptr, uint32_t n_fixed,
                                                 uint32_t cap, uint32_t *head, const Particle *src2,
                                                 const uint32_t *n2_ptr, uint32_t cap2) {
     __shared__ FeedSmem sm;
@@ -829,7 +844,8 @@ struct Electron {
 // of consecutive steps in one voxel are summed in registers (the integer
 // sum is the same) and added with one atomic when the voxel changes or the
 // electron ends (electron_flush).
-__device__ __forceinline__ void electron_deposit(const Args &A, Acc &acc, Electron &s, uint32_t iv, float e) {
+template <class AT>
+__device__ __forceinline__ void electron_deposit(const AT &A, Acc &acc, Electron &s, uint32_t iv, float e) {
 #if PSL_DEP_COMBINE
     const unsigned long long q = fixed_point(e, s.wt);
     if (!q) return;
@@ -846,7 +862,8 @@ __device__ __forceinline__ void electron_deposit(const Args &A, Acc &acc, Electr
 #endif
 }
 
-__device__ __forceinline__ void electron_flush(const Args &A, Acc &acc, Electron &s) {
+template <class AT>
+__device__ __forceinline__ void electron_flush(const AT &A, Acc &acc, Electron &s) {
 #if PSL_DEP_COMBINE
     if (s.pq) {
         atomicAdd(&A.tally[(uint64_t)(s.root >> ROOT_SLICE_SHIFT) * (uint64_t)A.nvox + s.piv], s.pq);
@@ -887,7 +904,7 @@ __device__ __forceinline__ float energy_of_range(const Tables &T, float r, int s
     const float rg = (2.f * g3 - 3.f * g2 + 1.f) * p.x + (g3 - 2.f * g2 + g) * p.y + (3.f * g2 - 2.f * g3) * q.x + (g3 - g2) * q.y;
     const float dr = (6.f * g2 - 6.f * g) * p.x + (3.f * g2 - 4.f * g + 1.f) * p.y + (6.f * g - 6.f * g2) * q.x + (3.f * g2 - 2.f * g) * q.y;
     const float g1 = dr > 0.0f ? g + __fdividef(r - rg, dr) : g;
-    return expf(T.lnE0 + ((float)j + g1) * __frcp_rn(T.inv_dln));
+    return expf(T.lnE0 + ((float)j + g1) * T.dln);
 }
 
 __device__ __forceinline__ float sample_moller(float T, float wcc, Rng &rng, const uint32_t *rk, uint32_t p0,
@@ -926,8 +943,8 @@ __device__ __forceinline__ float sample_bhabha(float T, float wcc, Rng &rng, con
     return x0;
 }
 
-template <bool POS>
-__device__ __forceinline__ void electron_end(const Args &A, Acc &acc, Electron &s, uint32_t iv) {
+template <bool POS, class AT>
+__device__ __forceinline__ void electron_end(const AT &A, Acc &acc, Electron &s, uint32_t iv) {
     deposit(A, acc, iv, s.t, s.wt, s.root);
     if (POS) {
         if (A.flags & PSL_PHYS_LOCAL_SECONDARIES) {
@@ -948,8 +965,8 @@ enum { E_END = 0, E_ON = 1, E_HARD = 2 };
 // that same call, in the voxel the step ended in, so that its lane takes the
 // next electron at once instead of idling through one more pass of the loop;
 // the deposits and draws are those of ending at the start of the next step.
-template <bool POS>
-__device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &s) {
+template <bool POS, class AT>
+__device__ __forceinline__ int electron_step(const AT &A, Acc &acc, Electron &s) {
     uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
     if (!(s.t <= A.ecut) && ++s.steps <= MAX_E_STEPS) {
         acc.steps++;
@@ -1036,8 +1053,8 @@ __device__ __forceinline__ int electron_step(const Args &A, Acc &acc, Electron &
 
 // the hard event (Moller delta ray or bremsstrahlung photon) that ended the
 // last step; the electron stays in the voxel of that step
-template <bool POS>
-__device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron &s, uint32_t *bh) {
+template <bool POS, class AT>
+__device__ __forceinline__ void electron_hard(const AT &A, Acc &acc, Electron &s, uint32_t *bh) {
     const uint32_t iv = ((uint32_t)s.iz * (uint32_t)A.ny + (uint32_t)s.iy) * (uint32_t)A.nx + (uint32_t)s.ix;
     EventRng ev(s.draw);
     Rng &rng = ev.r;
@@ -1084,8 +1101,8 @@ __device__ __forceinline__ void electron_hard(const Args &A, Acc &acc, Electron 
 // when it ends (POS: positrons, with their own tables and Bhabha
 // collisions; the electron loop compiles without the positron branches - a
 // runtime species cost the electron pass 5 %).
-template <bool POS>
-__device__ __forceinline__ void electron_loop(const Args &A, Acc &acc, const Particle *src, uint32_t n,
+template <bool POS, class AT>
+__device__ __forceinline__ void electron_loop(const AT &A, Acc &acc, const Particle *src, uint32_t n,
                                               uint32_t *head, uint32_t *bh) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -1138,7 +1155,8 @@ __device__ __forceinline__ void electron_loop(const Args &A, Acc &acc, const Par
 
 // The electron pass: the band-ordered electrons, then (as each warp runs out
 // of electrons) the generation's positrons from their own queue.
-__global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(Args A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
+template <bool TR>
+__global__ void __launch_bounds__(256, PSL_TRANSPORT_MIN_BLOCKS) k_electron(ArgsT<TR> A, const Particle *src, const uint32_t *n_ptr, uint32_t cap,
                                                   uint32_t *head, const Particle *psrc, const uint32_t *pn_ptr,
                                                   uint32_t pcap, uint32_t *phead) {
     // electrons live for several steps and their queue reads hit L1, so
@@ -1761,6 +1779,7 @@ struct Runner {
         for (int k = 0; k < 2; ++k) { A.tab.lnR0[k] = tc.igrid[2 * k]; A.tab.inv_dlnR[k] = tc.igrid[2 * k + 1]; }
         A.tab.lnE0 = (float)log(T_LO);
         A.tab.inv_dln = (float)((NT - 1) / (log(T_HI) - log(T_LO)));
+        A.tab.dln = 1.0f / A.tab.inv_dln;          // (the correctly rounded reciprocal, as __frcp_rn)
         A.ledger = t->ledger;
         A.hist_dep = nullptr; A.hist_esc = nullptr; A.hist_events = nullptr;
         A.err = w->cnt + 9;
@@ -1806,6 +1825,13 @@ struct Runner {
                                              Queue{w->Pos, w->cnt + 80, cap_q}); PSL_NOTE_LAUNCH();
         te(PK_BAND, tk);
     }
+    // the per-history record of transport_trace is on (the kernels' traced instances)
+    bool traced() const { return A.hist_dep || A.hist_esc || A.hist_events; }
+    template <bool TR> static ArgsT<TR> as_traced(const Args &a) {
+        ArgsT<TR> t;
+        static_cast<Args &>(t) = a;
+        return t;
+    }
     // one photon pass over src (its count at nptr, else nfix) and, when src2
     // is given, the photons of src2 (its count at n2ptr) after them
     void photon_pass(const Particle *src, const uint32_t *nptr, uint32_t nfix, uint32_t cap,
@@ -1818,7 +1844,9 @@ struct Runner {
         tb(PK_PHOTON, &tk);
         // (a persistent grid: no more blocks than stay resident)
         const int gp = gen_now >= 2 ? psl_sm_count() : psl_sm_count() * std::min(tally->grid_mult, PSL_PHOTON_MIN_BLOCKS);
-        k_photon<<<gp, 256, 0, st>>>(a2, src, nptr, nfix, cap, w->cnt + 5, src2, n2ptr, cap2); PSL_NOTE_LAUNCH();
+        if (traced()) k_photon<true><<<gp, 256, 0, st>>>(as_traced<true>(a2), src, nptr, nfix, cap, w->cnt + 5, src2, n2ptr, cap2);
+        else k_photon<false><<<gp, 256, 0, st>>>(as_traced<false>(a2), src, nptr, nfix, cap, w->cnt + 5, src2, n2ptr, cap2);
+        PSL_NOTE_LAUNCH();
         te(PK_PHOTON, tk);
     }
     void electron_pass() {
@@ -1829,8 +1857,13 @@ struct Runner {
         void *tk = nullptr;
         tb(PK_ELECTRON, &tk);
         cudaMemsetAsync(w->cnt + 81, 0, 4, st);
-        k_electron<<<gt(), 256, 0, st>>>(a2, w->S, w->cnt + 4, cap_s, w->cnt + 6, w->Pos, w->cnt + 80, cap_q,
-                                         w->cnt + 81); PSL_NOTE_LAUNCH();
+        if (traced())
+            k_electron<true><<<gt(), 256, 0, st>>>(as_traced<true>(a2), w->S, w->cnt + 4, cap_s, w->cnt + 6, w->Pos,
+                                                   w->cnt + 80, cap_q, w->cnt + 81);
+        else
+            k_electron<false><<<gt(), 256, 0, st>>>(as_traced<false>(a2), w->S, w->cnt + 4, cap_s, w->cnt + 6, w->Pos,
+                                                    w->cnt + 80, cap_q, w->cnt + 81);
+        PSL_NOTE_LAUNCH();
         te(PK_ELECTRON, tk);
     }
 
