@@ -634,18 +634,18 @@ __device__ __forceinline__ bool photon_interact(const AT &A, Acc &acc, Photon &g
     if (g.chan == 0u) {                                           // Compton (Kahn's method)
         acc.ev += EV_COMPTON;
         if (first) { deposit(A, acc, iv, g.e, g.wt, g.root); return false; }
-        const float k = g.e * (1.0f / F_ME), ik = __frcp_rn(k);
+        const float k = g.e * (1.0f / F_ME), ik = __fdividef(1.0f, k);     // (reciprocals: the hardware approximation)
         const float p_first = __fdividef(1.0f + 2.0f * k, 9.0f + 2.0f * k);
         float x = 1.0f, ix = 1.0f;
         for (int it = 0; it < 1000; ++it) {
             const float r1 = rng.next(A.rk, g.p0, g.p1), r2 = rng.next(A.rk, g.p0, g.p1), r3 = rng.next(A.rk, g.p0, g.p1);
             if (r1 <= p_first) {
                 x = 1.0f + 2.0f * k * r2;
-                ix = __frcp_rn(x);
+                ix = __fdividef(1.0f, x);
                 if (r3 <= 4.0f * (ix - ix * ix)) break;
             } else {
                 ix = __fdividef(1.0f + 2.0f * k * r2, 1.0f + 2.0f * k);
-                x = __frcp_rn(ix);
+                x = __fdividef(1.0f, ix);
                 const float cc = 1.0f - (x - 1.0f) * ik;
                 if (r3 <= 0.5f * (cc * cc + ix)) break;
             }
@@ -1004,7 +1004,7 @@ __device__ __forceinline__ int electron_step(const AT &A, Acc &acc, Electron &s)
         }
         const float tlim = fmaxf(0.9f * s.t, A.ecut);
         const float rlim = range_of(A.tab, tlim, sp);
-        const float s_max = (s.r - rlim) * __frcp_rn(rho);
+        const float s_max = __fdividef(s.r - rlim, rho);         // (a step limit: the fast division)
         int which;
         float step;
         if (s_hard <= s_bound && s_hard <= s_max) { which = 0; step = s_hard; }
