@@ -59,7 +59,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #define PSL_G_INNER 3                  // Woodcock steps a photon may take in one pass of the photon loop
 #endif
 #ifndef PSL_E_DEFER
-#define PSL_E_DEFER 4                  // lanes with a pending hard event before a warp runs them
+#define PSL_E_DEFER 2                  // lanes with a pending hard event before a warp runs them
 #endif
 #ifndef PSL_DEP_COMBINE
 #define PSL_DEP_COMBINE 0              // 1: an electron sums its consecutive deposits into one voxel in
