@@ -126,7 +126,8 @@ __device__ __forceinline__ void record_to_phantom(const PslRecord &R, const Beam
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (d[k] != 0.0f) {
-            float t0 = (0.0f - p[k]) / d[k], t1 = (L[k] - p[k]) / d[k];
+            const float id = 1.0f / d[k];             // (one division per axis)
+            float t0 = (0.0f - p[k]) * id, t1 = (L[k] - p[k]) * id;
             tin = fmaxf(tin, fminf(t0, t1));
             tout = fminf(tout, fmaxf(t0, t1));
         } else if (p[k] < 0.0f || p[k] > L[k]) {
