@@ -433,3 +433,35 @@ def test_bin_size_autotuner_picks_a_candidate():
     with pytest.raises(capi.PslError):
         capi.psl_autotune_bins(dw.params, dw.records, dw.beams, w.sad, dw.phantom, capi.physics(),
                                w.n_histories, w.seed, 10, [0.0], 1000)
+
+
+def test_traced_and_production_instances_give_the_same_tally():
+    """transport_trace launches the kernels' instances that record per-history
+    sums; transport_run the production instances compiled without that
+    record.  The same source batch must give the same integer tally and
+    ledger through both."""
+    w = inputs.config1(n_histories=50_000)
+    dw = engine.upload(w)
+    store = capi.psl_build(dw.params, dw.records)
+    plan = capi.psl_plan_create(store, dw.beams, w.sad, w.n_histories, w.seed)
+    n = w.n_histories
+    got = []
+    for traced in (False, True):
+        batch = capi.psl_source_batch(plan, dw.phantom, 0, n)
+        tally = capi.psl_tally_create(dw.phantom, 1)
+        if traced:
+            hd = torch.zeros(n, dtype=torch.int64, device="cuda")
+            he = torch.zeros(n, dtype=torch.int64, device="cuda")
+            hv = torch.zeros(n, dtype=torch.int32, device="cuda")
+            capi.transport_trace(dw.phantom, capi.physics(), batch, tally, 0, hd, he, hv)
+        else:
+            capi.transport_run(dw.phantom, capi.physics(), batch, tally, 0)
+        got.append(_tallies_of(dw, tally, 1))
+        tally.close()
+        batch.close()
+    (t1, l1), (t2, l2) = got
+    assert t1.sum() > 0
+    assert np.array_equal(t1, t2)
+    assert np.array_equal(l1, l2)
+    # the per-history record adds up to the tally
+    assert int(hd.sum().item()) == int(t2.sum())
