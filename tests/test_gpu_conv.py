@@ -120,3 +120,41 @@ def test_conv_rejects_bad_shapes():
     out = torch.zeros(64 * 16, dtype=torch.int16, device="cuda")
     with pytest.raises(capi.PslError):
         capi.conv3d(x, 12, wpk, None, 16, 4, 4, 4, False, out)   # C_in not a multiple of 8
+
+
+@pytest.mark.parametrize("ci,co", [(128, 128), (16, 16)])
+def test_full_volume_sampled_against_direct_sums(ci, co):
+    """The bench's shape (128^3 voxels, the halo form's full grid) checked on
+    sampled output voxels, each against its 27 x C_in-term sum in float64
+    (every output channel of 3000 voxels, borders included)."""
+    n = 128
+    rng = np.random.default_rng(ci + 3 * co)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1000 + ci + co)                       # seeded inputs
+    x = torch.randn(n, n, n, ci, device="cuda", generator=gen).to(torch.bfloat16)
+    w = (torch.randn(27, ci, co, device="cuda", generator=gen) * 0.05).contiguous()
+    b = (torch.randn(co, device="cuda", generator=gen) * 0.1).contiguous()
+    wpk = capi.conv3d_pack(w, ci, co)
+    of = torch.empty(n ** 3 * co, dtype=torch.float32, device="cuda")
+    capi.conv3d(x.view(-1).view(torch.int16), ci, wpk, b, co, n, n, n, False, None, of)
+    torch.cuda.synchronize()
+    pts = rng.integers(0, n, size=(3000, 3))
+    pts[:200, 0] = rng.choice([0, n - 1], 200)           # faces of the volume (the padding)
+    pts[200:400, 2] = rng.choice([0, n - 1], 200)
+    P = torch.from_numpy(pts).cuda()
+    got = of.view(n, n, n, co)[P[:, 0], P[:, 1], P[:, 2]].cpu().numpy().astype(np.float64)
+    # the 27 neighbours of each sampled voxel (zero outside the volume)
+    xf = x.float()
+    nb = []
+    for t in range(27):
+        d = torch.tensor([t // 9 - 1, (t // 3) % 3 - 1, t % 3 - 1], device="cuda")
+        q = P + d
+        inside = ((q >= 0) & (q < n)).all(1)
+        qc = q.clamp(0, n - 1)
+        nb.append(xf[qc[:, 0], qc[:, 1], qc[:, 2]] * inside[:, None])
+    xn = torch.stack(nb, 1).cpu().numpy().astype(np.float64)          # [points, 27, ci]
+    wq = w.to(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+    bq = b.cpu().numpy().astype(np.float64)
+    ref = bq + np.einsum("pti,tio->po", xn, wq)
+    mag = np.abs(bq) + np.einsum("pti,tio->po", np.abs(xn), np.abs(wq))
+    assert np.all(np.abs(got - ref) <= 2e-5 * mag + 1e-6), np.abs(got - ref).max()
