@@ -76,7 +76,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 struct Tables {
     const float4 *ph0, *ph1;   // material 0/1: mu_c, mu_pe, mu_pp, mu_total (cm^2/g)
     const float4 *el;          // [2][NT] S_restricted (MeV cm^2/g), sigma_moller or sigma_bhabha, sigma_brem (cm^2/g), 0
-    const float2 *rng;         // [2][NT] CSDA range R (g/cm^2) and dR/dlnT * dlnT at each node
+    const float4 *rng;         // [2][NT] CSDA range on node interval i: R = c0 + g (c1 + g (c2 + g c3)), g in [0, 1]
     const float *irng;         // [2][NT] ln T at uniform steps of ln R (inverse range)
     float lnE0, inv_dln;
     float dln;                 // 1 / inv_dln, rounded to float (the node spacing in ln E)
@@ -167,12 +167,17 @@ __global__ void k_range_intervals(double *iv, double wcc, double wcb) {
 }
 
 // One block: the running sum of the interval ranges in order (one thread),
-// then the node values and the inverse table (all threads).  The inverse
-// node j takes the same pair of forward nodes as a walk along the nodes
-// would (ln R is increasing), found by binary search.
-__global__ void __launch_bounds__(1024) k_range_table(double *iv, float2 *rt, float *irt, float *igrid, double wcc,
+// then the node values, the forward table and the inverse table (all
+// threads).  The forward table holds, for each pair of neighbouring nodes,
+// the cubic Hermite interpolant of R in g = (ln T - ln T_i) / dlnT through
+// the node values and the exact node slopes dR/dg = T dlnT / S, as the
+// coefficients of its powers of g (one 16-byte load and three FMAs per
+// evaluation).  The inverse node j takes the same pair of forward nodes as a
+// walk along the nodes would (ln R is increasing), found by binary search.
+__global__ void __launch_bounds__(1024) k_range_table(double *iv, float4 *rt, float *irt, float *igrid, double wcc,
                                                       double wcb) {
     __shared__ double liv[NT];
+    __shared__ double slope[NT];
     const int sp = blockIdx.x;                       // one block per species
     iv += sp * NT; rt += sp * NT; irt += sp * NT; igrid += 2 * sp;
     const double l0 = log(T_LO), dl = (log(T_HI) - log(T_LO)) / (NT - 1);
@@ -186,10 +191,18 @@ __global__ void __launch_bounds__(1024) k_range_table(double *iv, float2 *rt, fl
     __syncthreads();
     for (int i = threadIdx.x; i < NT; i += blockDim.x) {
         const double R = iv[i], T = exp(l0 + dl * i);
-        rt[i] = make_float2((float)R, (float)(T * dl / stop_restricted(sp, T, wcc, wcb)));
+        slope[i] = T * dl / stop_restricted(sp, T, wcc, wcb);
         liv[i] = i > 0 ? log(R) : 0.0;
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < NT; i += blockDim.x) {
+        // the last node starts no interval (lookups stop below it): its row
+        // continues the range linearly
+        const double a0 = iv[i], d0 = slope[i];
+        const double a1 = i + 1 < NT ? iv[i + 1] : a0 + d0, d1 = i + 1 < NT ? slope[i + 1] : d0;
+        rt[i] = make_float4((float)a0, (float)d0, (float)(3.0 * (a1 - a0) - 2.0 * d0 - d1),
+                            (float)(2.0 * (a0 - a1) + d0 + d1));
+    }
     // inverse: ln T at NT uniform points of ln R over [R_1, R_{NT-1}], by
     // interpolating ln T linearly in ln R between the forward nodes
     const double a = liv[1], b = liv[NT - 1], dr = (b - a) / (NT - 1);
@@ -244,9 +257,8 @@ __device__ __forceinline__ float4 lerp4(const float4 *a, int i, float f) {
 // R(E): cubic Hermite in ln E with the exact node derivatives dR/dlnE = E/S
 // (i: node index including the species offset)
 __device__ __forceinline__ float range_at(const Tables &T, int i, float f) {
-    const float2 a = __ldg(T.rng + i), b = __ldg(T.rng + i + 1);
-    const float f2 = f * f, f3 = f2 * f;
-    return (2.f * f3 - 3.f * f2 + 1.f) * a.x + (f3 - 2.f * f2 + f) * a.y + (3.f * f2 - 2.f * f3) * b.x + (f3 - f2) * b.y;
+    const float4 c = __ldg(T.rng + i);
+    return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
 }
 
 // sp: the species offset (0 electron, NT positron)
@@ -899,10 +911,9 @@ __device__ __forceinline__ float energy_of_range(const Tables &T, float r, int s
     xf = fminf(fmaxf(xf, 0.0f), (float)(NT - 1) - 1e-3f);
     const int j = (int)xf;
     const float g = xf - (float)j;
-    const float2 p = __ldg(T.rng + j + sp), q = __ldg(T.rng + j + sp + 1);
-    const float g2 = g * g, g3 = g2 * g;
-    const float rg = (2.f * g3 - 3.f * g2 + 1.f) * p.x + (g3 - 2.f * g2 + g) * p.y + (3.f * g2 - 2.f * g3) * q.x + (g3 - g2) * q.y;
-    const float dr = (6.f * g2 - 6.f * g) * p.x + (3.f * g2 - 4.f * g + 1.f) * p.y + (6.f * g - 6.f * g2) * q.x + (3.f * g2 - 2.f * g) * q.y;
+    const float4 c = __ldg(T.rng + j + sp);
+    const float rg = fmaf(g, fmaf(g, fmaf(g, c.w, c.z), c.y), c.x);
+    const float dr = fmaf(g, fmaf(g, 3.0f * c.w, 2.0f * c.z), c.y);
     const float g1 = dr > 0.0f ? g + __fdividef(r - rg, dr) : g;
     return expf(T.lnE0 + ((float)j + g1) * T.dln);
 }
@@ -1460,7 +1471,7 @@ struct TableCache {
     int device = -1;
     float wcc = -1.f, wcb = -1.f;
     float4 *ph0 = nullptr, *ph1 = nullptr, *el = nullptr;
-    float2 *rng = nullptr;
+    float4 *rng = nullptr;
     float *irng = nullptr;
     float igrid[4] = {0.f, 0.f, 0.f, 0.f};   // per species: ln R0, 1 / d ln R
 };
@@ -1478,7 +1489,7 @@ int get_tables(float wcc, float wcb, cudaStream_t st, TableCache &out) {
     PSL_CUDA(cudaMalloc((void **)&t.ph0, NT * sizeof(float4)));
     PSL_CUDA(cudaMalloc((void **)&t.ph1, NT * sizeof(float4)));
     PSL_CUDA(cudaMalloc((void **)&t.el, 2 * NT * sizeof(float4)));
-    PSL_CUDA(cudaMalloc((void **)&t.rng, 2 * NT * sizeof(float2)));
+    PSL_CUDA(cudaMalloc((void **)&t.rng, 2 * NT * sizeof(float4)));
     k_tables<<<(NT + 255) / 256, 256, 0, st>>>(t.ph0, t.ph1, t.el, (double)wcc, (double)wcb); PSL_NOTE_LAUNCH();
     double *iv = nullptr;
     float *ig = nullptr;
