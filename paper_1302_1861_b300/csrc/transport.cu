@@ -53,7 +53,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #define SRC_MIN_BLOCKS 4               // resident 256-thread source blocks per SM (register cap 64)
 #endif
 #ifndef PSL_G_DEFER
-#define PSL_G_DEFER 24                 // lanes with a pending real photon interaction before a warp runs them
+#define PSL_G_DEFER 28                 // lanes with a pending real photon interaction before a warp runs them
 #endif
 #ifndef PSL_G_INNER
 #define PSL_G_INNER 3                  // Woodcock steps a photon may take in one pass of the photon loop
@@ -697,10 +697,12 @@ __device__ __forceinline__ bool photon_interact(const AT &A, Acc &acc, Photon &g
 // a photon whose Woodcock step drew a real interaction (PENDING) or one set
 // aside to make room for such a photon (READY).  A lane whose photon draws a
 // real interaction parks it and steps another photon (from its slot or the
-// feed) instead of idling; the parked interactions run together once enough
-// lanes have one (or every live lane is blocked), so that the interaction
-// code runs with most lanes active while stepping keeps the lanes busy.
-// Every photon keeps its own random stream, so the order changes nothing.
+// feed) instead of idling; a lane whose own slot is taken parks it in the
+// empty slot of another lane of the warp (the k-th such lane in the k-th
+// empty slot); the parked interactions run together once enough lanes have
+// one (or every live lane is blocked), so that the interaction code runs
+// with most lanes active while stepping keeps the lanes busy.  Every photon
+// keeps its own random stream, so the order changes nothing.
 // A slot is 19 words (the 18 of Photon and a pad: an odd stride keeps the
 // 32 slots of a warp free of bank conflicts).
 #ifndef PSL_PHOTON_SLOTS
@@ -815,6 +817,26 @@ __global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(ArgsT<TR>
                     g = q;
                 } else {
                     real = true;                              // blocked until the parked one has run
+                }
+            }
+        }
+        {
+            // a blocked photon parks in another lane's empty slot
+            const unsigned stk = __ballot_sync(FULL, alive && real);
+            if (stk) {
+                const unsigned emp = __ballot_sync(FULL, slot == SLOT_EMPTY);
+                const int m = min(__popc(stk), __popc(emp));
+                if (m) {
+                    if (alive && real) {
+                        const int k = __popc(stk & lt);
+                        if (k < m) {
+                            const int dst = (int)__fns(emp, 0u, k + 1);
+                            slot_store(slots[(threadIdx.x & ~31u) + dst], g);
+                            alive = false; real = false;
+                        }
+                    }
+                    if (slot == SLOT_EMPTY && __popc(emp & lt) < m) slot = SLOT_PENDING;
+                    __syncwarp();
                 }
             }
         }
