@@ -65,7 +65,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #define PSL_DEP_COMBINE 0              // 1: an electron sums its consecutive deposits into one voxel in
 #endif                                 //    registers and adds them with one atomic when it leaves the voxel
 #ifndef PSL_PHOTON_MIN_BLOCKS
-#define PSL_PHOTON_MIN_BLOCKS 4        // resident 256-thread photon blocks per SM (register cap 64)
+#define PSL_PHOTON_MIN_BLOCKS 3        // resident 256-thread photon blocks per SM (register cap 80)
 #endif
 #ifndef PSL_TRANSPORT_MIN_BLOCKS
 #define PSL_TRANSPORT_MIN_BLOCKS 4     // resident 256-thread blocks per SM (register cap 64)
@@ -703,30 +703,33 @@ __device__ __forceinline__ bool photon_interact(const AT &A, Acc &acc, Photon &g
 // one (or every live lane is blocked), so that the interaction code runs
 // with most lanes active while stepping keeps the lanes busy.  Every photon
 // keeps its own random stream, so the order changes nothing.
-// A slot is 19 words (the 18 of Photon and a pad: an odd stride keeps the
-// 32 slots of a warp free of bank conflicts).
+// A slot is 20 words (the 18 of Photon and a pad), moved as four 16-byte
+// and one 8-byte shared-memory access: at an 80-byte stride the eight lanes
+// of each quarter-warp phase of a 16-byte access hit disjoint banks.
 #ifndef PSL_PHOTON_SLOTS
 #define PSL_PHOTON_SLOTS 1
 #endif
 enum { SLOT_EMPTY = 0, SLOT_READY = 1, SLOT_PENDING = 2 };
-constexpr int SLOT_WORDS = 19;
+constexpr int SLOT_WORDS = 20;
 
 __device__ __forceinline__ void slot_store(uint32_t *s, const Photon &g) {
-    s[0] = __float_as_uint(g.x); s[1] = __float_as_uint(g.y); s[2] = __float_as_uint(g.z);
-    s[3] = __float_as_uint(g.u); s[4] = __float_as_uint(g.v); s[5] = __float_as_uint(g.w);
-    s[6] = __float_as_uint(g.e); s[7] = __float_as_uint(g.wt);
-    s[8] = g.p0; s[9] = g.p1; s[10] = g.root; s[11] = g.nchild; s[12] = g.draw;
-    s[13] = __float_as_uint(g.mumax); s[14] = __float_as_uint(g.inv_mumax); s[15] = (uint32_t)g.ti;
-    s[16] = __float_as_uint(g.tf); s[17] = g.chan;
+    uint4 *q = reinterpret_cast<uint4 *>(s);
+    q[0] = make_uint4(__float_as_uint(g.x), __float_as_uint(g.y), __float_as_uint(g.z), __float_as_uint(g.u));
+    q[1] = make_uint4(__float_as_uint(g.v), __float_as_uint(g.w), __float_as_uint(g.e), __float_as_uint(g.wt));
+    q[2] = make_uint4(g.p0, g.p1, g.root, g.nchild);
+    q[3] = make_uint4(g.draw, __float_as_uint(g.mumax), __float_as_uint(g.inv_mumax), (uint32_t)g.ti);
+    reinterpret_cast<uint2 *>(s)[8] = make_uint2(__float_as_uint(g.tf), g.chan);
 }
 
 __device__ __forceinline__ void slot_load(const uint32_t *s, Photon &g) {
-    g.x = __uint_as_float(s[0]); g.y = __uint_as_float(s[1]); g.z = __uint_as_float(s[2]);
-    g.u = __uint_as_float(s[3]); g.v = __uint_as_float(s[4]); g.w = __uint_as_float(s[5]);
-    g.e = __uint_as_float(s[6]); g.wt = __uint_as_float(s[7]);
-    g.p0 = s[8]; g.p1 = s[9]; g.root = s[10]; g.nchild = s[11]; g.draw = s[12];
-    g.mumax = __uint_as_float(s[13]); g.inv_mumax = __uint_as_float(s[14]); g.ti = (int)s[15];
-    g.tf = __uint_as_float(s[16]); g.chan = s[17];
+    const uint4 *q = reinterpret_cast<const uint4 *>(s);
+    const uint4 a = q[0], b = q[1], c = q[2], d = q[3];
+    const uint2 e = reinterpret_cast<const uint2 *>(s)[8];
+    g.x = __uint_as_float(a.x); g.y = __uint_as_float(a.y); g.z = __uint_as_float(a.z); g.u = __uint_as_float(a.w);
+    g.v = __uint_as_float(b.x); g.w = __uint_as_float(b.y); g.e = __uint_as_float(b.z); g.wt = __uint_as_float(b.w);
+    g.p0 = c.x; g.p1 = c.y; g.root = c.z; g.nchild = c.w;
+    g.draw = d.x; g.mumax = __uint_as_float(d.y); g.inv_mumax = __uint_as_float(d.z); g.ti = (int)d.w;
+    g.tf = __uint_as_float(e.x); g.chan = e.y;
 }
 
 template <bool TR>
@@ -737,7 +740,7 @@ __global__ void __launch_bounds__(256, PSL_PHOTON_MIN_BLOCKS) k_photon(ArgsT<TR>
     __shared__ uint32_t bh[NBANDS];
     __shared__ unsigned long long sled[NLEDGER];
 #if PSL_PHOTON_SLOTS
-    __shared__ uint32_t slots[FEED_WARPS * 32][SLOT_WORDS];
+    __shared__ __align__(16) uint32_t slots[FEED_WARPS * 32][SLOT_WORDS];
     uint32_t *my = slots[threadIdx.x];
     uint32_t slot = SLOT_EMPTY;
 #endif
@@ -1064,10 +1067,16 @@ __device__ __forceinline__ int electron_step(const AT &A, Acc &acc, Electron &s)
             rotate_dir(s.u, s.v, s.w, ct, st, sp, cp);
         }
         if (which == 1) {
-            int out = 0;
-            if (axis == 0) { s.x = (float)(cross > 0 ? s.ix + 1 : s.ix) * A.vx; s.ix += cross; out = s.ix < 0 || s.ix >= A.nx; }
-            else if (axis == 1) { s.y = (float)(cross > 0 ? s.iy + 1 : s.iy) * A.vy; s.iy += cross; out = s.iy < 0 || s.iy >= A.ny; }
-            else { s.z = (float)(cross > 0 ? s.iz + 1 : s.iz) * A.vz; s.iz += cross; out = s.iz < 0 || s.iz >= A.nz; }
+            // the crossed axis moves to the shared face and one cell on; the
+            // others stay inside the grid, so one unsigned test finds an exit
+            // (selects, no branch per axis)
+            const int up = cross > 0;
+            const int cx = axis == 0 ? cross : 0, cy = axis == 1 ? cross : 0, cz = axis == 2 ? cross : 0;
+            s.x = axis == 0 ? (float)(s.ix + up) * A.vx : s.x;
+            s.y = axis == 1 ? (float)(s.iy + up) * A.vy : s.y;
+            s.z = axis == 2 ? (float)(s.iz + up) * A.vz : s.z;
+            s.ix += cx; s.iy += cy; s.iz += cz;
+            const int out = (unsigned)s.ix >= (unsigned)A.nx || (unsigned)s.iy >= (unsigned)A.ny || (unsigned)s.iz >= (unsigned)A.nz;
             if (out) {
                 electron_flush(A, acc, s);
                 escape(A, acc, s.t + (POS ? 2.0f * F_ME : 0.0f), s.wt, s.root);
