@@ -58,6 +58,9 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 #ifndef PSL_G_INNER
 #define PSL_G_INNER 3                  // Woodcock steps a photon may take in one pass of the photon loop
 #endif
+#ifndef PSL_E_CLAIM
+#define PSL_E_CLAIM 32                 // electron queue entries a warp claims with one atomic (the refills of
+#endif                                 // ~17 loop passes: one atomic's latency per claim, not per refill)
 #ifndef PSL_E_DEFER
 #define PSL_E_DEFER 2                  // lanes with a pending hard event before a warp runs them
 #endif
@@ -1150,6 +1153,7 @@ __device__ __forceinline__ void electron_loop(const AT &A, Acc &acc, const Parti
     const unsigned lt = (1u << lane) - 1u;
     Electron s;
     bool alive = false, done = false, hard = false;
+    uint32_t cbase = 0, cleft = 0;        // the warp's claimed queue range not yet handed out
     for (;;) {
         // Hard events wait until enough lanes have one (or every live lane
         // waits), so that the long hard-event code runs with most lanes
@@ -1161,12 +1165,20 @@ __device__ __forceinline__ void electron_loop(const AT &A, Acc &acc, const Parti
         // lanes whose particle ended (in this pass's step or before) take the next
         const unsigned need = __ballot_sync(FULL, !alive && !done);
         if (need) {
-            const int leader = __ffs(need) - 1;
-            uint32_t base = 0;
-            if (lane == leader) base = atomicAdd(head, (uint32_t)__popc(need));
-            base = __shfl_sync(FULL, base, leader);
+            // the needing lanes take, in lane order, the rest of the warp's
+            // claim and then a new claim of at least PSL_E_CLAIM entries
+            // (indices past the queue's end mean it is exhausted)
+            const uint32_t nn = __popc(need), k = __popc(need & lt);
+            uint32_t nb = 0, c = 0;
+            if (nn > cleft) {                                 // claim more (warp-uniform)
+                c = max(nn - cleft, (uint32_t)PSL_E_CLAIM);
+                if (lane == 0) nb = atomicAdd(head, c);
+                nb = __shfl_sync(FULL, nb, 0);
+            }
+            const uint32_t ck = cleft, cb = cbase;
+            if (nn > ck) { cbase = nb + (nn - ck); cleft = c - (nn - ck); } else { cbase += nn; cleft -= nn; }
             if (!alive && !done) {
-                const uint32_t idx = base + __popc(need & lt);
+                const uint32_t idx = k < ck ? cb + k : nb + (k - ck);
                 if (idx < n) {
                     const Particle p = load_particle(src + idx);
                     s.x = p.x; s.y = p.y; s.z = p.z; s.u = p.u; s.v = p.v; s.w = p.w; s.t = p.e; s.wt = p.wt;
