@@ -651,9 +651,9 @@ def main():
 #       -k regex:"k_electron|k_photon|k_source" (the same command)
 # They hold for the kernels they were measured on; re-measure after changing
 # the kernels.
-THREAD_INST_PER_ELECTRON_STEP = 512.8
+THREAD_INST_PER_ELECTRON_STEP = 515.3
 THREAD_INST_PER_WOODCOCK_STEP = 339.2
-DRAM_BYTES_PER_HISTORY = {"electron": 22.4, "photon": 57.0, "source": 80.5}
+DRAM_BYTES_PER_HISTORY = {"electron": 22.1, "photon": 57.0, "source": 76.9}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
 
