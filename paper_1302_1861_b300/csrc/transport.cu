@@ -446,12 +446,14 @@ __device__ __forceinline__ void flush_acc(const Args &A, const Acc &a, unsigned 
 }
 
 // ------------------------------------------------------------ warp feed ---
-// A warp claims queue entries 32 at a time and stages each chunk in shared
-// memory with one bulk asynchronous copy (cp.async.bulk completing on an
-// mbarrier), one chunk ahead of use.  A lane that needs a new particle then
-// reads it from shared memory instead of waiting on HBM.  The current chunk
-// is always resident; its successor is in flight or resident.
-#define FEED_CHUNK 32
+// A warp claims queue entries FEED_CHUNK at a time and stages each chunk in
+// shared memory with one bulk asynchronous copy (cp.async.bulk completing on
+// an mbarrier), one chunk ahead of use.  A lane that needs a new particle
+// then reads it from shared memory instead of waiting on HBM.  The current
+// chunk is always resident; its successor is in flight or resident.  (The
+// packed feed state holds counts below 64; a photon warp takes ~12 new
+// photons per loop pass, so a chunk of 48 lasts about four passes.)
+#define FEED_CHUNK 48
 #define FEED_WARPS 8                     // 256-thread blocks
 #define FEED_SPIN (1u << 22)
 
