@@ -652,8 +652,8 @@ def main():
 # They hold for the kernels they were measured on; re-measure after changing
 # the kernels.
 THREAD_INST_PER_ELECTRON_STEP = 515.3
-THREAD_INST_PER_WOODCOCK_STEP = 339.2
-DRAM_BYTES_PER_HISTORY = {"electron": 22.1, "photon": 57.0, "source": 76.9}
+THREAD_INST_PER_WOODCOCK_STEP = 331.9
+DRAM_BYTES_PER_HISTORY = {"electron": 22.1, "photon": 57.0, "source": 77.9}
 # issue speed of light: 148 SMs x 4 schedulers x 1 warp-instruction/clk x 32 lanes x 2.032 GHz
 THREAD_INST_PEAK = 148 * 4 * 32 * 2.032e9
 
